@@ -1,0 +1,197 @@
+/*
+ * plk.h -- C ABI of the B300 profile-likelihood library (libplk.so).
+ *
+ * The library evaluates the profile log-likelihood l_p(omega, lambda) of the
+ * Box-Cox linear geostatistical model with anisotropic Matern correlation
+ * (Xu & Brown, arXiv 2305.04318) at many correlation-parameter points omega and
+ * Box-Cox parameters lambda:
+ *   model        Y' ~ MVN(X beta, sigma^2 V), V = R(omega) + nu^2 I      (Section 2, eq. 1)
+ *   correlation  rho = 2^{1-kappa}/Gamma(kappa) u^kappa K_kappa(u),
+ *                u = sqrt(8 kappa) d(x), d = ||diag(1/phi_X, 1/phi_Y) Rot(phi_A) x||
+ *                                                                     (Section 2, eq. matern)
+ *   statistics   log|V|, log|X'V^-1X|, (y',X)'V^-1(y',X), ssqBetahat,
+ *                ssqResidual                                          (Section 3.3, Table 1)
+ *   closed form  beta-hat, sigma-hat^2 and
+ *                -2 l_p = n log(RSS/n) + log|V| - 2(lambda-1) sum log y + n log(2 pi) + n
+ *                                                                     (eqs. betahat, 4, profile)
+ *   REML         -2 l*_p = (n-p) log(RSS/(n-p)) + log|V| + log|X'V^-1X|
+ *                          - 2(lambda-1) sum log y + n log(2 pi) + n - p   (Appendix, eq. remlpro)
+ *   profile CI   {theta : l_p(theta) >= max l_p - chi2_1(level)/2}    (Section 2.2, eq. likelihood)
+ *
+ * Parameter point layout (one row of 5 doubles, "natural" parameters):
+ *   [0] phi_X   range, > 0
+ *   [1] kappa   Matern shape, > 0
+ *   [2] nu^2    nugget ratio tau^2/sigma^2, >= 0
+ *   [3] phi_R   anisotropy ratio phi_X/phi_Y, > 0 (phi_Y = phi_X / phi_R)
+ *   [4] phi_A   anisotropy angle in radians (rotation matrix as printed in eq. matern)
+ *
+ * Conventions for every call:
+ *   - Returns a plk_status; PLK_OK on success.  On failure nothing is written to
+ *     caller output buffers and plk_last_error() describes the cause.
+ *   - "host" pointers are ordinary CPU memory; "device" pointers are CUDA global
+ *     memory on the context's / call's device.  Row-major layouts throughout.
+ *   - The caller owns every buffer it passes; the library copies inputs it keeps.
+ *   - A numerical failure at one omega point (V or X'V^-1X not positive definite,
+ *     or a non-positive residual sum of squares) is not a call failure: that
+ *     point's status is set and its outputs are NaN.
+ *   - No call falls back to a CPU implementation.  A missing or unusable GPU is
+ *     PLK_E_CUDA.
+ */
+#ifndef PLK_H
+#define PLK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PLK_OK = 0,
+    PLK_E_INVALID = 1,   /* bad argument: sizes, NULL required pointer, y <= 0, non-finite, ... */
+    PLK_E_NOMEM = 2,     /* workspace / HBM budget too small for even one omega point */
+    PLK_E_NOT_READY = 3, /* poll: the job has not finished within the timeout */
+    PLK_E_TIMEOUT = 4,   /* a bounded device-side wait gave up */
+    PLK_E_CUDA = 5,      /* a CUDA runtime or launch error */
+    PLK_E_CANCELLED = 6  /* job cancelled */
+} plk_status;
+
+/* Per-point status codes written to point_status[]. */
+#define PLK_POINT_OK 0
+#define PLK_POINT_NOT_PD 1       /* V (or X'V^-1X) not positive definite in the working precision */
+#define PLK_POINT_BAD_PARAM 2    /* parameter row outside its domain (phi_X<=0, kappa<=0, ...) */
+#define PLK_POINT_RSS_NONPOS 3   /* residual sum of squares <= 0 */
+#define PLK_POINT_FP64_RETRY 16  /* flag bit: mixed mode re-evaluated this point in FP64 */
+
+typedef enum {
+    PLK_FP64 = 0,  /* every step in FP64 arithmetic */
+    PLK_MIXED = 1  /* FP64 build / diagonal blocks / log-det / quadratic forms; trailing
+                      updates and TRSM bulk as exact split-bf16 products on the tensor cores */
+} plk_precision;
+
+typedef struct {
+    int32_t precision;  /* plk_precision */
+    int32_t reml;       /* 0: ML profile (eq. profile); 1: REML profile (eq. remlpro) */
+    int32_t batch;      /* omega points per device batch; 0 = library default */
+    int32_t reserved;
+} plk_options;
+
+/* ------------------------------------------------------------------------ */
+/* Stateless device-pointer evaluation (one dataset, K points)               */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+    int64_t n;               /* sites, n > p */
+    int32_t p;               /* covariates, 1 <= p <= 16 */
+    int32_t M;               /* lambda values, M >= 1, M + p <= 64 */
+    const double *coords;    /* device, n x 2 site coordinates */
+    const double *y;         /* device, n observations, all > 0 */
+    const double *X;         /* device, n x p design matrix */
+    const double *lambdas;   /* device, M Box-Cox parameters */
+    int64_t K;               /* number of parameter points, >= 0 */
+    const double *params;    /* device, K x 5 parameter points (layout above) */
+    /* outputs, device, any may be NULL */
+    double *logL;            /* K x M  l_p(omega_k, lambda_m) (or l*_p if reml) */
+    double *sigma2;          /* K x M  sigma-hat^2 (RSS/n, or RSS/(n-p) if reml) */
+    double *beta;            /* K x M x p beta-hat */
+    double *logdet;          /* K x 2  [log|V|, log|X'V^-1X|] */
+    int32_t *status;         /* K      PLK_POINT_* codes */
+} plk_eval_args;
+
+/* Bytes of device workspace plk_eval_device needs to process `batch` points of
+ * a dataset with n sites, p covariates and M lambdas in the given precision.
+ * Returns 0 for invalid sizes. */
+size_t plk_eval_workspace_bytes(int64_t n, int32_t p, int32_t M, int32_t batch,
+                                int32_t precision);
+
+/* Evaluate all K points of `args` on `stream` (a cudaStream_t, 0 = legacy
+ * default stream), in batches of opts->batch points, using only the caller's
+ * workspace (device, `workspace_bytes` >= plk_eval_workspace_bytes(...), 256-byte
+ * aligned).  Allocates nothing.  Asynchronous: returns after enqueueing; outputs
+ * are valid once the stream reaches this point.  Errors: PLK_E_INVALID (sizes,
+ * NULL inputs), PLK_E_NOMEM (workspace too small for opts->batch), PLK_E_CUDA
+ * (launch failure). */
+plk_status plk_eval_device(const plk_eval_args *args, const plk_options *opts, void *workspace,
+                           size_t workspace_bytes, void *stream);
+
+/* ------------------------------------------------------------------------ */
+/* Context API: device-resident datasets, asynchronous jobs                  */
+/* ------------------------------------------------------------------------ */
+
+typedef struct plk_ctx plk_ctx;
+typedef int64_t plk_dataset;
+typedef int64_t plk_job;
+
+/* Create a context on CUDA device `device`.  `arena` (device memory owned by the
+ * caller, e.g. a PyTorch tensor) of `arena_bytes` is where the context places
+ * datasets and job workspaces; when arena is NULL the context allocates
+ * `arena_bytes` itself with cudaMalloc at creation and frees it at destroy.
+ * All admission of work is bounded by this arena (the HBM budget).
+ * `streams` (cudaStream_t handles, may be NULL) / `n_streams` are the streams
+ * the scheduler launches on; when NULL the context creates `n_streams` (>= 1)
+ * non-blocking streams of its own. */
+plk_status plk_create(plk_ctx **out, int device, void *arena, size_t arena_bytes,
+                      void *const *streams, int n_streams);
+
+/* Copy a dataset (host pointers) to the device: coords n x 2, y n (> 0), X n x p.
+ * Validates: n > p >= 1, p <= 16, finite values, y > 0. */
+plk_status plk_create_dataset(plk_ctx *ctx, const double *coords, const double *y,
+                              const double *X, int64_t n, int32_t p, plk_dataset *out);
+
+/* Submit a profile job: K parameter points (host, K x 5) x M lambdas (host).
+ * The inputs are copied before return; the job runs asynchronously and
+ * interleaves with other jobs as arena space and streams free up.
+ * PLK_E_NOMEM if even one point of this dataset cannot fit in the arena. */
+plk_status plk_submit_profile(plk_ctx *ctx, plk_dataset ds, const double *param_grid, int64_t K,
+                              const double *lambda_grid, int32_t M, const plk_options *opts,
+                              plk_job *out);
+
+/* Wait up to timeout_ms (0 = do not wait, < 0 = wait forever) for `job`; on
+ * completion copy its results into the caller's host buffers (any may be NULL;
+ * layouts as in plk_eval_args) and forget the job.  PLK_E_NOT_READY if still
+ * running.  Timing of the job (host clock, seconds since context creation) is
+ * returned in t_submit/t_start/t_done when non-NULL. */
+plk_status plk_poll(plk_ctx *ctx, plk_job job, int32_t timeout_ms, double *logL, double *sigma2,
+                    double *beta, double *logdet, int32_t *point_status, double *t_submit,
+                    double *t_start, double *t_done);
+
+/* Release a dataset's device memory (after its jobs have completed). */
+plk_status plk_release_dataset(plk_ctx *ctx, plk_dataset ds);
+
+/* Arena statistics: bytes in use now and the high-water mark. */
+plk_status plk_memory_stats(plk_ctx *ctx, size_t *in_use, size_t *high_water);
+
+/* Wait for all jobs, free everything the context owns. */
+plk_status plk_destroy(plk_ctx *ctx);
+
+/* Message describing the last error of the calling thread ("" if none). */
+const char *plk_last_error(void);
+
+/* ------------------------------------------------------------------------ */
+/* Profile reduction and likelihood CI (Section 3.6, eq. likelihood)          */
+/* ------------------------------------------------------------------------ */
+
+/* prof[g] = max over the SM consecutive values vals[g*SM .. (g+1)*SM) that are
+ * not NaN (NaN if all are NaN), for g < G.  Device pointers, runs on `stream`. */
+plk_status plk_profile_max_device(const double *vals, int64_t G, int64_t SM, double *prof,
+                                  void *stream);
+
+/* Likelihood-based CI from a 1-D profile on an ascending grid (device
+ * pointers; results written to the device array out[4] = {lo, hi, argmax,
+ * censored}).  argmax is the lowest index among ties; threshold = max -
+ * chi2_1(level)/2; each endpoint interpolates linearly between the first finite
+ * grid point strictly below the threshold (walking outward from the argmax) and
+ * the finite point just inside it; a side that never drops below is the grid
+ * edge with censored bit 1 (lower) / 2 (upper); out = NaN if no value is
+ * finite.  level in (0, 1). */
+plk_status plk_profile_ci_device(const double *grid, const double *prof, int64_t G, double level,
+                                 double *out, void *stream);
+
+/* chi2_1 quantile used by the CI: c with P(chi2_1 <= c) = level. */
+double plk_chi2_1_quantile(double level);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PLK_H */

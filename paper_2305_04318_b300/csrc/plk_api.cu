@@ -1,0 +1,775 @@
+// plk_api.cu -- host side of the C ABI declared in include/plk.h.
+//
+// Stateless evaluation (plk_eval_device) lays out a caller-provided workspace
+// and enqueues the kernel pipeline batch by batch.  The context API keeps
+// datasets resident in a device arena, admits jobs by the arena bytes their
+// batches need, and runs a scheduler thread that launches batches of any active
+// job on a pool of streams (continuous batching: a job submitted while others
+// are running gets the next free stream slot and arena space; results are
+// independent of the mix because each point's arithmetic order depends only on
+// its own data).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "plk.h"
+#include "plk_common.cuh"
+#include "plk_kernels.cuh"
+
+using namespace plk;
+
+// ---------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------
+static thread_local std::string g_err;
+
+static plk_status fail(plk_status s, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return s;
+}
+
+static plk_status cuda_fail(cudaError_t e, const char *where) {
+    return fail(PLK_E_CUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+extern "C" const char *plk_last_error(void) { return g_err.c_str(); }
+
+// ---------------------------------------------------------------------------
+// workspace layout
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr size_t ALIGN = 256;
+inline size_t align_up(size_t x) { return (x + ALIGN - 1) / ALIGN * ALIGN; }
+
+struct Layout {
+    int64_t n = 0, n_pad = 0;
+    int nb = 0, q = 0, p = 0, M = 0, batch = 0;
+    int64_t tpo = 0;
+    size_t off_Bt = 0, off_sumlog = 0, off_oc = 0, off_coordT = 0, off_tab = 0, off_tiles = 0,
+           off_inv = 0, off_ldv = 0, off_pst = 0, total = 0;
+};
+
+bool sizes_ok(int64_t n, int32_t p, int32_t M) {
+    return n > 0 && p >= 1 && p <= 16 && M >= 1 && M + p <= 64 && n > p;
+}
+
+bool make_layout(int64_t n, int32_t p, int32_t M, int32_t batch, Layout &L) {
+    if (!sizes_ok(n, p, M) || batch < 1) return false;
+    L.n = n;
+    L.p = p;
+    L.M = M;
+    L.q = M + p;
+    L.batch = batch;
+    L.nb = (int)((n + TB - 1) / TB);
+    L.n_pad = (int64_t)L.nb * TB;
+    L.tpo = tiles_per_omega(L.nb);
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        size_t o = off;
+        off = align_up(off + bytes);
+        return o;
+    };
+    L.off_Bt = take(sizeof(double) * (size_t)L.q * L.n_pad);
+    L.off_sumlog = take(sizeof(double));
+    L.off_oc = take(sizeof(double) * OC_N * (size_t)batch);
+    L.off_coordT = take(sizeof(double) * 2 * (size_t)L.n_pad * batch);
+    L.off_tab = take(sizeof(double) * (size_t)TAB_SIZE * batch);
+    L.off_tiles = take(sizeof(double) * (size_t)NT * L.tpo * batch);
+    L.off_inv = take(sizeof(double) * (size_t)NT * batch);
+    L.off_ldv = take(sizeof(double) * (size_t)batch);
+    L.off_pst = take(sizeof(int) * (size_t)batch);
+    L.total = off;
+    return true;
+}
+
+int default_batch(int64_t n, int64_t K) {
+    // enough points in flight to fill 148 SMs in the per-tile kernels while
+    // keeping the workspace modest: ~8 GB of tiles
+    Layout L;
+    if (!make_layout(n, 1, 1, 1, L)) return 1;
+    const double per = (double)L.tpo * NT * sizeof(double);
+    int64_t b = (int64_t)(8e9 / per);
+    b = std::max<int64_t>(1, std::min<int64_t>(b, 296));
+    if (K > 0) b = std::min<int64_t>(b, K);
+    return (int)b;
+}
+
+template <class T>
+T *at(void *base, size_t off) {
+    return reinterpret_cast<T *>(static_cast<char *>(base) + off);
+}
+
+}  // namespace
+
+extern "C" size_t plk_eval_workspace_bytes(int64_t n, int32_t p, int32_t M, int32_t batch,
+                                           int32_t precision) {
+    Layout L;
+    if (precision != PLK_FP64 && precision != PLK_MIXED) return 0;
+    if (!make_layout(n, p, M, batch, L)) return 0;
+    return L.total;
+}
+
+// Enqueue the whole evaluation on `s` given a laid-out workspace.
+static plk_status run_eval(const plk_eval_args *a, int reml, const Layout &L, void *ws,
+                           cudaStream_t s) {
+    cudaError_t e = launch_boxcox(a->n, L.n_pad, a->p, a->M, a->y, a->X, a->lambdas,
+                                  at<double>(ws, L.off_Bt), at<double>(ws, L.off_sumlog), s);
+    if (e != cudaSuccess) return cuda_fail(e, "boxcox launch");
+    for (int64_t k0 = 0; k0 < a->K; k0 += L.batch) {
+        BatchArgs b;
+        b.count = (int)std::min<int64_t>(L.batch, a->K - k0);
+        b.k0 = k0;
+        b.n = a->n;
+        b.n_pad = L.n_pad;
+        b.nb = L.nb;
+        b.q = L.q;
+        b.p = a->p;
+        b.M = a->M;
+        b.reml = reml;
+        b.tpo = L.tpo;
+        b.params = a->params + 5 * k0;
+        b.coords = a->coords;
+        b.lambdas = a->lambdas;
+        b.Bt = at<double>(ws, L.off_Bt);
+        b.sumlogy = at<double>(ws, L.off_sumlog);
+        b.oconst = at<double>(ws, L.off_oc);
+        b.coordT = at<double>(ws, L.off_coordT);
+        b.tab = at<double>(ws, L.off_tab);
+        b.tiles = at<double>(ws, L.off_tiles);
+        b.inv = at<double>(ws, L.off_inv);
+        b.ldv = at<double>(ws, L.off_ldv);
+        b.pstatus = at<int>(ws, L.off_pst);
+        b.logL = a->logL;
+        b.sigma2 = a->sigma2;
+        b.beta = a->beta;
+        b.logdet = a->logdet;
+        b.status = a->status;
+        e = launch_fp64_batch(b, s);
+        if (e != cudaSuccess) return cuda_fail(e, "batch launch");
+    }
+    return PLK_OK;
+}
+
+static plk_status check_args(const plk_eval_args *a) {
+    if (!a) return fail(PLK_E_INVALID, "args is NULL");
+    if (!sizes_ok(a->n, a->p, a->M))
+        return fail(PLK_E_INVALID, "invalid sizes n=%lld p=%d M=%d (need n > p >= 1, p <= 16, M >= 1, M+p <= 64)",
+                    (long long)a->n, a->p, a->M);
+    if (a->K < 0) return fail(PLK_E_INVALID, "K < 0");
+    if (!a->coords || !a->y || !a->X || !a->lambdas || (a->K > 0 && !a->params))
+        return fail(PLK_E_INVALID, "NULL input pointer");
+    return PLK_OK;
+}
+
+extern "C" plk_status plk_eval_device(const plk_eval_args *args, const plk_options *opts,
+                                      void *workspace, size_t workspace_bytes, void *stream) {
+    plk_status st = check_args(args);
+    if (st != PLK_OK) return st;
+    const int prec = opts ? opts->precision : PLK_FP64;
+    if (prec != PLK_FP64 && prec != PLK_MIXED) return fail(PLK_E_INVALID, "unknown precision %d", prec);
+    if (prec == PLK_MIXED) return fail(PLK_E_INVALID, "PLK_MIXED is not available in this build");
+    int batch = (opts && opts->batch > 0) ? opts->batch : default_batch(args->n, args->K);
+    Layout L;
+    make_layout(args->n, args->p, args->M, batch, L);
+    if (!workspace || workspace_bytes < L.total)
+        return fail(PLK_E_NOMEM, "workspace of %zu bytes < %zu needed for batch %d", workspace_bytes,
+                    L.total, batch);
+    if (reinterpret_cast<uintptr_t>(workspace) % ALIGN != 0)
+        return fail(PLK_E_INVALID, "workspace must be 256-byte aligned");
+    if (args->K == 0) return PLK_OK;
+    return run_eval(args, opts ? opts->reml : 0, L, workspace, static_cast<cudaStream_t>(stream));
+}
+
+// ---------------------------------------------------------------------------
+// profile reduction, CI
+// ---------------------------------------------------------------------------
+extern "C" double plk_chi2_1_quantile(double level) {
+    // c = z^2 with P(|Z| <= z) = level, i.e. erf(z / sqrt 2) = level; Newton on erf
+    // from a bisection start.
+    if (!(level > 0.0) || !(level < 1.0)) return NAN;
+    double lo = 0.0, hi = 40.0;
+    for (int i = 0; i < 80; ++i) {
+        double mid = 0.5 * (lo + hi);
+        if (std::erf(mid / std::sqrt(2.0)) < level) lo = mid; else hi = mid;
+    }
+    double z = 0.5 * (lo + hi);
+    for (int i = 0; i < 3; ++i) {
+        const double f = std::erfc(z / std::sqrt(2.0)) - (1.0 - level);
+        const double df = -std::sqrt(2.0 / M_PI) * std::exp(-0.5 * z * z);
+        if (df == 0.0) break;
+        z -= f / df;
+    }
+    return z * z;
+}
+
+extern "C" plk_status plk_profile_max_device(const double *vals, int64_t G, int64_t SM, double *prof,
+                                             void *stream) {
+    if (G < 0 || SM < 1 || (G > 0 && (!vals || !prof))) return fail(PLK_E_INVALID, "bad profile_max args");
+    if (G == 0) return PLK_OK;
+    cudaError_t e = launch_profile_max(vals, G, SM, prof, static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? PLK_OK : cuda_fail(e, "profile_max");
+}
+
+extern "C" plk_status plk_profile_ci_device(const double *grid, const double *prof, int64_t G,
+                                            double level, double *out, void *stream) {
+    if (G < 1 || !grid || !prof || !out || !(level > 0.0 && level < 1.0))
+        return fail(PLK_E_INVALID, "bad profile_ci args");
+    cudaError_t e = launch_profile_ci(grid, prof, G, 0.5 * plk_chi2_1_quantile(level), out,
+                                      static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? PLK_OK : cuda_fail(e, "profile_ci");
+}
+
+// ---------------------------------------------------------------------------
+// context API
+// ---------------------------------------------------------------------------
+namespace {
+
+// First-fit sub-allocator over one device arena (256-byte granules).
+class Arena {
+  public:
+    void init(char *base, size_t size) {
+        base_ = base;
+        size_ = size;
+        free_.clear();
+        free_[0] = size;
+        used_ = high_ = 0;
+    }
+    char *alloc(size_t bytes) {
+        bytes = align_up(std::max<size_t>(bytes, 1));
+        for (auto it = free_.begin(); it != free_.end(); ++it) {
+            if (it->second >= bytes) {
+                size_t off = it->first, len = it->second;
+                free_.erase(it);
+                if (len > bytes) free_[off + bytes] = len - bytes;
+                live_[off] = bytes;
+                used_ += bytes;
+                high_ = std::max(high_, used_);
+                return base_ + off;
+            }
+        }
+        return nullptr;
+    }
+    void release(char *p) {
+        if (!p) return;
+        size_t off = p - base_;
+        auto it = live_.find(off);
+        if (it == live_.end()) return;
+        size_t len = it->second;
+        live_.erase(it);
+        used_ -= len;
+        auto nx = free_.lower_bound(off);
+        if (nx != free_.end() && off + len == nx->first) {
+            len += nx->second;
+            nx = free_.erase(nx);
+        }
+        if (nx != free_.begin()) {
+            auto pv = std::prev(nx);
+            if (pv->first + pv->second == off) {
+                pv->second += len;
+                return;
+            }
+        }
+        free_[off] = len;
+    }
+    size_t largest_free() const {
+        size_t m = 0;
+        for (auto &f : free_) m = std::max(m, f.second);
+        return m;
+    }
+    size_t size() const { return size_; }
+    size_t used() const { return used_; }
+    size_t high() const { return high_; }
+
+  private:
+    char *base_ = nullptr;
+    size_t size_ = 0, used_ = 0, high_ = 0;
+    std::map<size_t, size_t> free_, live_;
+};
+
+struct Dataset {
+    int64_t n = 0;
+    int32_t p = 0;
+    double *coords = nullptr, *y = nullptr, *X = nullptr;
+    int active_jobs = 0;
+};
+
+struct Job {
+    plk_job id = 0;
+    plk_dataset ds = 0;
+    int64_t K = 0;
+    int32_t M = 0, p = 0;
+    int64_t n = 0;
+    plk_options opts{};
+    std::vector<double> params, lambdas;
+    // device buffers (from the arena): inputs, outputs
+    char *dev = nullptr;
+    double *d_params = nullptr, *d_lam = nullptr, *d_logL = nullptr, *d_s2 = nullptr,
+           *d_beta = nullptr, *d_ld = nullptr, *d_bt = nullptr, *d_slog = nullptr;
+    int32_t *d_st = nullptr;
+    cudaEvent_t ready = nullptr;   // B^T and sum log y computed
+    int batch = 1;
+    int64_t next_k = 0;      // first point not yet launched
+    int inflight = 0;
+    bool started = false, done = false, failed = false;
+    std::string error;
+    std::vector<double> logL, s2, beta, ld;
+    std::vector<int32_t> st;
+    double t_submit = 0, t_start = 0, t_done = 0;
+};
+
+struct Item {
+    Job *job;
+    int slot;
+    int64_t k0;
+    int count;
+    char *ws;
+    cudaEvent_t ev;
+};
+
+}  // namespace
+
+struct plk_ctx {
+    int device = 0;
+    char *arena_base = nullptr;
+    bool own_arena = false;
+    Arena arena;
+    std::vector<cudaStream_t> streams;
+    bool own_streams = false;
+    std::vector<int> slot_busy;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::map<plk_dataset, std::unique_ptr<Dataset>> datasets;
+    std::map<plk_job, std::unique_ptr<Job>> jobs;
+    std::deque<Job *> order;   // submission order of unfinished jobs
+    std::vector<Item> inflight;
+    std::vector<cudaEvent_t> event_pool;
+    plk_dataset next_ds = 1;
+    plk_job next_job = 1;
+    bool stop = false;
+    std::thread worker;
+    std::chrono::steady_clock::time_point t0;
+    double now() const {
+        return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    }
+};
+
+namespace {
+
+size_t job_io_bytes(int64_t K, int32_t M, int32_t p, int64_t n) {
+    size_t b = 0;
+    b += align_up(sizeof(double) * 5 * K);
+    b += align_up(sizeof(double) * M);
+    b += align_up(sizeof(double) * K * M) * 2;
+    b += align_up(sizeof(double) * K * M * p);
+    b += align_up(sizeof(double) * 2 * K);
+    b += align_up(sizeof(int32_t) * K);
+    b += align_up(sizeof(double) * (size_t)(M + p) * ((n + TB - 1) / TB * TB));   // B^T rows
+    b += align_up(sizeof(double));
+    return b;
+}
+
+// Per-batch workspace without the shared dataset part (B^T, sum log y live in the job).
+size_t item_bytes(int64_t n, int32_t p, int32_t M, int count) {
+    Layout L;
+    make_layout(n, p, M, count, L);
+    return L.total;
+}
+
+// Start a job: allocate its I/O, upload inputs, compute B^T once.  Caller holds mu.
+bool start_job(plk_ctx *c, Job *j, cudaStream_t s) {
+    size_t bytes = job_io_bytes(j->K, j->M, j->p, j->n);
+    j->dev = c->arena.alloc(bytes);
+    if (!j->dev) return false;
+    char *q = j->dev;
+    auto take = [&](size_t b) {
+        char *r = q;
+        q += align_up(b);
+        return r;
+    };
+    j->d_params = (double *)take(sizeof(double) * 5 * j->K);
+    j->d_lam = (double *)take(sizeof(double) * j->M);
+    j->d_logL = (double *)take(sizeof(double) * j->K * j->M);
+    j->d_s2 = (double *)take(sizeof(double) * j->K * j->M);
+    j->d_beta = (double *)take(sizeof(double) * j->K * j->M * j->p);
+    j->d_ld = (double *)take(sizeof(double) * 2 * j->K);
+    j->d_st = (int32_t *)take(sizeof(int32_t) * j->K);
+    const int64_t n_pad = (j->n + TB - 1) / TB * TB;
+    j->d_bt = (double *)take(sizeof(double) * (size_t)(j->M + j->p) * n_pad);
+    j->d_slog = (double *)take(sizeof(double));
+    Dataset *d = c->datasets[j->ds].get();
+    cudaMemcpyAsync(j->d_params, j->params.data(), sizeof(double) * 5 * j->K, cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(j->d_lam, j->lambdas.data(), sizeof(double) * j->M, cudaMemcpyHostToDevice, s);
+    cudaError_t e = launch_boxcox(j->n, n_pad, j->p, j->M, d->y, d->X, j->d_lam, j->d_bt, j->d_slog, s);
+    if (e != cudaSuccess) {
+        j->failed = true;
+        j->error = cudaGetErrorString(e);
+    }
+    cudaEventCreateWithFlags(&j->ready, cudaEventDisableTiming);
+    cudaEventRecord(j->ready, s);
+    j->started = true;
+    j->t_start = c->now();
+    return true;
+}
+
+void launch_item(plk_ctx *c, Job *j, Item &it, cudaStream_t s) {
+    Layout L;
+    make_layout(j->n, j->p, j->M, it.count, L);
+    Dataset *d = c->datasets[j->ds].get();
+    BatchArgs b;
+    b.count = it.count;
+    b.k0 = it.k0;
+    b.n = j->n;
+    b.n_pad = L.n_pad;
+    b.nb = L.nb;
+    b.q = L.q;
+    b.p = j->p;
+    b.M = j->M;
+    b.reml = j->opts.reml;
+    b.tpo = L.tpo;
+    b.params = j->d_params + 5 * it.k0;
+    b.coords = d->coords;
+    b.lambdas = j->d_lam;
+    b.Bt = j->d_bt;
+    b.sumlogy = j->d_slog;
+    b.oconst = at<double>(it.ws, L.off_oc);
+    b.coordT = at<double>(it.ws, L.off_coordT);
+    b.tab = at<double>(it.ws, L.off_tab);
+    b.tiles = at<double>(it.ws, L.off_tiles);
+    b.inv = at<double>(it.ws, L.off_inv);
+    b.ldv = at<double>(it.ws, L.off_ldv);
+    b.pstatus = at<int>(it.ws, L.off_pst);
+    b.logL = j->d_logL;
+    b.sigma2 = j->d_s2;
+    b.beta = j->d_beta;
+    b.logdet = j->d_ld;
+    b.status = j->d_st;
+    cudaStreamWaitEvent(s, j->ready, 0);   // the job's B^T may come from another stream
+    cudaError_t e = launch_fp64_batch(b, s);
+    if (e != cudaSuccess) {
+        j->failed = true;
+        j->error = cudaGetErrorString(e);
+    }
+    cudaEventRecord(it.ev, s);
+}
+
+void finish_job(plk_ctx *c, Job *j) {
+    // all items retired: read results back (synchronously on the job's last stream)
+    j->logL.resize(j->K * j->M);
+    j->s2.resize(j->K * j->M);
+    j->beta.resize(j->K * j->M * j->p);
+    j->ld.resize(2 * j->K);
+    j->st.resize(j->K);
+    cudaError_t e = cudaSuccess;
+    if (j->K > 0) {
+        e = cudaMemcpy(j->logL.data(), j->d_logL, sizeof(double) * j->K * j->M, cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess) e = cudaMemcpy(j->s2.data(), j->d_s2, sizeof(double) * j->K * j->M, cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess) e = cudaMemcpy(j->beta.data(), j->d_beta, sizeof(double) * j->K * j->M * j->p, cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess) e = cudaMemcpy(j->ld.data(), j->d_ld, sizeof(double) * 2 * j->K, cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess) e = cudaMemcpy(j->st.data(), j->d_st, sizeof(int32_t) * j->K, cudaMemcpyDeviceToHost);
+    }
+    if (e != cudaSuccess) {
+        j->failed = true;
+        j->error = cudaGetErrorString(e);
+    }
+    c->arena.release(j->dev);
+    j->dev = nullptr;
+    if (j->ready) cudaEventDestroy(j->ready);
+    j->ready = nullptr;
+    c->datasets[j->ds]->active_jobs--;
+    j->done = true;
+    j->t_done = c->now();
+}
+
+void worker_main(plk_ctx *c) {
+    cudaSetDevice(c->device);
+    std::unique_lock<std::mutex> lk(c->mu);
+    while (true) {
+        // retire finished items
+        bool progressed = false;
+        for (size_t i = 0; i < c->inflight.size();) {
+            Item &it = c->inflight[i];
+            cudaError_t q = cudaEventQuery(it.ev);
+            if (q == cudaErrorNotReady) {
+                ++i;
+                continue;
+            }
+            if (q != cudaSuccess) {
+                it.job->failed = true;
+                it.job->error = cudaGetErrorString(q);
+            }
+            c->arena.release(it.ws);
+            c->slot_busy[it.slot] = 0;
+            c->event_pool.push_back(it.ev);
+            Job *j = it.job;
+            j->inflight--;
+            c->inflight.erase(c->inflight.begin() + i);
+            progressed = true;
+            if (j->inflight == 0 && j->next_k >= j->K && !j->done) {
+                finish_job(c, j);
+                c->order.erase(std::find(c->order.begin(), c->order.end(), j));
+                c->cv_done.notify_all();
+            }
+        }
+        // launch new items: oldest job first, one item per free stream slot
+        for (int slot = 0; slot < (int)c->streams.size(); ++slot) {
+            if (c->slot_busy[slot]) continue;
+            Job *pick = nullptr;
+            for (Job *j : c->order) {
+                if (j->next_k < j->K || (!j->started && j->K == 0)) {
+                    pick = j;
+                    break;
+                }
+            }
+            if (!pick) break;
+            cudaStream_t s = c->streams[slot];
+            if (!pick->started) {
+                if (!start_job(c, pick, s)) break;   // no arena space for its I/O yet
+                if (pick->K == 0) {
+                    finish_job(c, pick);
+                    c->order.erase(std::find(c->order.begin(), c->order.end(), pick));
+                    c->cv_done.notify_all();
+                    progressed = true;
+                    continue;
+                }
+            }
+            int count = (int)std::min<int64_t>(pick->batch, pick->K - pick->next_k);
+            char *ws = nullptr;
+            while (count >= 1 && !(ws = c->arena.alloc(item_bytes(pick->n, pick->p, pick->M, count))))
+                count /= 2;   // admission by arena bytes: shrink the batch until it fits
+            if (!ws) break;   // wait for memory to free up
+            Item it;
+            it.job = pick;
+            it.slot = slot;
+            it.k0 = pick->next_k;
+            it.count = count;
+            it.ws = ws;
+            if (c->event_pool.empty()) {
+                cudaEvent_t ev;
+                cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+                c->event_pool.push_back(ev);
+            }
+            it.ev = c->event_pool.back();
+            c->event_pool.pop_back();
+            launch_item(c, pick, it, s);
+            pick->next_k += count;
+            pick->inflight++;
+            c->slot_busy[slot] = 1;
+            c->inflight.push_back(it);
+            progressed = true;
+        }
+        if (c->stop && c->order.empty() && c->inflight.empty()) break;
+        if (!progressed) {
+            if (c->inflight.empty())
+                c->cv_work.wait_for(lk, std::chrono::milliseconds(50));
+            else {
+                lk.unlock();
+                std::this_thread::sleep_for(std::chrono::microseconds(100));
+                lk.lock();
+            }
+        }
+    }
+}
+
+}  // namespace
+
+extern "C" plk_status plk_create(plk_ctx **out, int device, void *arena, size_t arena_bytes,
+                                 void *const *streams, int n_streams) {
+    if (!out) return fail(PLK_E_INVALID, "out is NULL");
+    if (arena_bytes < (1u << 20)) return fail(PLK_E_INVALID, "arena_bytes too small");
+    if (n_streams < 1 || n_streams > 64) return fail(PLK_E_INVALID, "n_streams must be in [1, 64]");
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceCount");
+    if (device < 0 || device >= ndev) return fail(PLK_E_INVALID, "no device %d", device);
+    if ((e = cudaSetDevice(device)) != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+    auto c = std::make_unique<plk_ctx>();
+    c->device = device;
+    c->t0 = std::chrono::steady_clock::now();
+    if (arena) {
+        if (reinterpret_cast<uintptr_t>(arena) % ALIGN) return fail(PLK_E_INVALID, "arena must be 256-byte aligned");
+        c->arena_base = static_cast<char *>(arena);
+    } else {
+        if ((e = cudaMalloc(&c->arena_base, arena_bytes)) != cudaSuccess) return cuda_fail(e, "cudaMalloc arena");
+        c->own_arena = true;
+    }
+    c->arena.init(c->arena_base, arena_bytes / ALIGN * ALIGN);
+    if (streams) {
+        for (int i = 0; i < n_streams; ++i) c->streams.push_back(static_cast<cudaStream_t>(streams[i]));
+    } else {
+        for (int i = 0; i < n_streams; ++i) {
+            cudaStream_t s;
+            if ((e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking)) != cudaSuccess) return cuda_fail(e, "stream");
+            c->streams.push_back(s);
+        }
+        c->own_streams = true;
+    }
+    c->slot_busy.assign(c->streams.size(), 0);
+    c->worker = std::thread(worker_main, c.get());
+    *out = c.release();
+    return PLK_OK;
+}
+
+static bool all_finite(const double *p, int64_t m) {
+    for (int64_t i = 0; i < m; ++i)
+        if (!std::isfinite(p[i])) return false;
+    return true;
+}
+
+extern "C" plk_status plk_create_dataset(plk_ctx *c, const double *coords, const double *y,
+                                         const double *X, int64_t n, int32_t p, plk_dataset *out) {
+    if (!c || !coords || !y || !X || !out) return fail(PLK_E_INVALID, "NULL argument");
+    if (!(n > p && p >= 1 && p <= 16)) return fail(PLK_E_INVALID, "need n > p >= 1 and p <= 16");
+    if (!all_finite(coords, 2 * n) || !all_finite(X, n * p) || !all_finite(y, n))
+        return fail(PLK_E_INVALID, "non-finite input");
+    for (int64_t i = 0; i < n; ++i)
+        if (!(y[i] > 0.0)) return fail(PLK_E_INVALID, "y[%lld] = %g is not > 0", (long long)i, y[i]);
+    cudaSetDevice(c->device);
+    std::lock_guard<std::mutex> lk(c->mu);
+    auto d = std::make_unique<Dataset>();
+    d->n = n;
+    d->p = p;
+    const size_t bc = align_up(sizeof(double) * 2 * n), by = align_up(sizeof(double) * n),
+                 bx = align_up(sizeof(double) * n * p);
+    char *m = c->arena.alloc(bc + by + bx);
+    if (!m) return fail(PLK_E_NOMEM, "arena full: dataset needs %zu bytes", bc + by + bx);
+    d->coords = (double *)m;
+    d->y = (double *)(m + bc);
+    d->X = (double *)(m + bc + by);
+    cudaError_t e = cudaMemcpy(d->coords, coords, sizeof(double) * 2 * n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(d->y, y, sizeof(double) * n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(d->X, X, sizeof(double) * n * p, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        c->arena.release(m);
+        return cuda_fail(e, "dataset upload");
+    }
+    *out = c->next_ds++;
+    c->datasets[*out] = std::move(d);
+    return PLK_OK;
+}
+
+extern "C" plk_status plk_submit_profile(plk_ctx *c, plk_dataset ds, const double *param_grid, int64_t K,
+                                         const double *lambda_grid, int32_t M, const plk_options *opts,
+                                         plk_job *out) {
+    if (!c || !out || (K > 0 && !param_grid) || !lambda_grid) return fail(PLK_E_INVALID, "NULL argument");
+    if (K < 0 || M < 1) return fail(PLK_E_INVALID, "need K >= 0 and M >= 1");
+    if (!all_finite(lambda_grid, M)) return fail(PLK_E_INVALID, "non-finite lambda");
+    plk_options o{};
+    if (opts) o = *opts;
+    if (o.precision != PLK_FP64 && o.precision != PLK_MIXED) return fail(PLK_E_INVALID, "unknown precision");
+    if (o.precision == PLK_MIXED) return fail(PLK_E_INVALID, "PLK_MIXED is not available in this build");
+    std::unique_lock<std::mutex> lk(c->mu);
+    auto dit = c->datasets.find(ds);
+    if (dit == c->datasets.end()) return fail(PLK_E_INVALID, "unknown dataset %lld", (long long)ds);
+    Dataset *d = dit->second.get();
+    if (M + d->p > 64) return fail(PLK_E_INVALID, "M + p must be <= 64");
+    const size_t need = job_io_bytes(K, M, d->p, d->n) + item_bytes(d->n, d->p, M, 1);
+    if (need > c->arena.size())
+        return fail(PLK_E_NOMEM, "job needs at least %zu bytes, arena is %zu", need, c->arena.size());
+    auto j = std::make_unique<Job>();
+    j->id = c->next_job++;
+    j->ds = ds;
+    j->K = K;
+    j->M = M;
+    j->p = d->p;
+    j->n = d->n;
+    j->opts = o;
+    j->params.assign(param_grid, param_grid + 5 * K);
+    j->lambdas.assign(lambda_grid, lambda_grid + M);
+    j->batch = o.batch > 0 ? o.batch : default_batch(d->n, K);
+    j->t_submit = c->now();
+    d->active_jobs++;
+    *out = j->id;
+    c->order.push_back(j.get());
+    c->jobs[j->id] = std::move(j);
+    c->cv_work.notify_all();
+    return PLK_OK;
+}
+
+extern "C" plk_status plk_poll(plk_ctx *c, plk_job job, int32_t timeout_ms, double *logL,
+                               double *sigma2, double *beta, double *logdet, int32_t *point_status,
+                               double *t_submit, double *t_start, double *t_done) {
+    if (!c) return fail(PLK_E_INVALID, "ctx is NULL");
+    std::unique_lock<std::mutex> lk(c->mu);
+    auto it = c->jobs.find(job);
+    if (it == c->jobs.end()) return fail(PLK_E_INVALID, "unknown job %lld", (long long)job);
+    Job *j = it->second.get();
+    auto ready = [&] { return j->done; };
+    if (!ready()) {
+        if (timeout_ms == 0) return fail(PLK_E_NOT_READY, "job %lld running", (long long)job);
+        if (timeout_ms < 0)
+            c->cv_done.wait(lk, ready);
+        else if (!c->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), ready))
+            return fail(PLK_E_NOT_READY, "job %lld running", (long long)job);
+    }
+    if (j->failed) {
+        std::string msg = j->error;
+        c->jobs.erase(it);
+        return fail(PLK_E_CUDA, "job failed: %s", msg.c_str());
+    }
+    if (logL) std::memcpy(logL, j->logL.data(), sizeof(double) * j->logL.size());
+    if (sigma2) std::memcpy(sigma2, j->s2.data(), sizeof(double) * j->s2.size());
+    if (beta) std::memcpy(beta, j->beta.data(), sizeof(double) * j->beta.size());
+    if (logdet) std::memcpy(logdet, j->ld.data(), sizeof(double) * j->ld.size());
+    if (point_status) std::memcpy(point_status, j->st.data(), sizeof(int32_t) * j->st.size());
+    if (t_submit) *t_submit = j->t_submit;
+    if (t_start) *t_start = j->t_start;
+    if (t_done) *t_done = j->t_done;
+    c->jobs.erase(it);
+    return PLK_OK;
+}
+
+extern "C" plk_status plk_release_dataset(plk_ctx *c, plk_dataset ds) {
+    if (!c) return fail(PLK_E_INVALID, "ctx is NULL");
+    std::lock_guard<std::mutex> lk(c->mu);
+    auto it = c->datasets.find(ds);
+    if (it == c->datasets.end()) return fail(PLK_E_INVALID, "unknown dataset");
+    if (it->second->active_jobs > 0) return fail(PLK_E_INVALID, "dataset has running jobs");
+    c->arena.release((char *)it->second->coords);
+    c->datasets.erase(it);
+    return PLK_OK;
+}
+
+extern "C" plk_status plk_memory_stats(plk_ctx *c, size_t *in_use, size_t *high_water) {
+    if (!c) return fail(PLK_E_INVALID, "ctx is NULL");
+    std::lock_guard<std::mutex> lk(c->mu);
+    if (in_use) *in_use = c->arena.used();
+    if (high_water) *high_water = c->arena.high();
+    return PLK_OK;
+}
+
+extern "C" plk_status plk_destroy(plk_ctx *c) {
+    if (!c) return PLK_OK;
+    {
+        std::lock_guard<std::mutex> lk(c->mu);
+        c->stop = true;
+        c->cv_work.notify_all();
+    }
+    c->worker.join();
+    cudaSetDevice(c->device);
+    for (auto ev : c->event_pool) cudaEventDestroy(ev);
+    if (c->own_streams)
+        for (auto s : c->streams) cudaStreamDestroy(s);
+    if (c->own_arena) cudaFree(c->arena_base);
+    delete c;
+    return PLK_OK;
+}

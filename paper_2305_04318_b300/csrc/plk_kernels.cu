@@ -1,0 +1,634 @@
+// plk_kernels.cu -- FP64 CUDA kernels of the profile-likelihood hot path
+// (Xu & Brown, arXiv 2305.04318, Section 3.3 "Step 3" and Table 2), for sm_103a.
+//
+// Pipeline for a batch of parameter points omega (one CUDA block grid per step):
+//   k_boxcox_rows   B^T = [y'(lambda_1..lambda_M) | X]^T           (Section 2 Box-Cox)
+//   k_omega_prep    per-omega constants, rotated/scaled coordinates  (eq. matern)
+//   k_matern_table  per-omega piecewise polynomial of rho(w), w = 8 kappa d^2
+//   k_build         bordered matrix tiles: V = R + nu^2 I and B^T     (Step 3 item 1)
+//   for each tile column J:
+//     k_potrf       diagonal tile L_JJ, its inverse, log|V| partial   (item 2)
+//     k_gemm_nt<0>  panel L_IJ = A_IJ L_JJ^-T (also W^T rows)         (items 2-3)
+//     k_gemm_nt<1>  trailing A_IK -= L_IJ L_KJ^T (also -B^T V^-1 B)   (items 2-4)
+//   k_finalize      p x p Cholesky, beta-hat, RSS, sigma-hat^2, l_p    (items 5-8, eqs. betahat,
+//                                                                        4, profile, remlpro)
+// On this part FP64 issues at ~1/67 of the FP32 rate, so every kernel here is
+// bound by FP64 instruction count; the build evaluates rho with a handful of
+// FP64 operations per matrix entry (no exp/sqrt per entry).
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "plk.h"
+#include "plk_common.cuh"
+#include "plk_kernels.cuh"
+
+namespace plk {
+
+// ---------------------------------------------------------------------------
+// Box-Cox rows and sum of log y
+// ---------------------------------------------------------------------------
+
+__global__ void k_boxcox_rows(int64_t n, int64_t n_pad, int p, int M, const double *__restrict__ y,
+                              const double *__restrict__ X, const double *__restrict__ lam,
+                              double *__restrict__ Bt) {
+    const int q = M + p;
+    const int64_t total = (int64_t)q * n_pad;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int r = (int)(e / n_pad);
+        const int64_t i = e - (int64_t)r * n_pad;
+        double v = 0.0;
+        if (i < n) {
+            if (r < M) {
+                const double l = lam[r];
+                const double ly = log(y[i]);
+                v = (l == 0.0) ? ly : expm1(l * ly) / l;   // b(y; lambda), Section 2
+            } else {
+                v = X[i * p + (r - M)];
+            }
+        }
+        Bt[e] = v;
+    }
+}
+
+__global__ void k_sumlog(int64_t n, const double *__restrict__ y, double *__restrict__ out) {
+    __shared__ double red[32];
+    double s = 0.0;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) s += log(y[i]);
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        s = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        if (threadIdx.x == 0) *out = s;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Per-omega constants and transformed coordinates
+// ---------------------------------------------------------------------------
+// a_i = sqrt(8k)/phi_X (cos x_i - sin y_i), b_i = sqrt(8k)/phi_Y (sin x_i + cos y_i), so that
+// w_ij = (a_i - a_j)^2 + (b_i - b_j)^2 = u_ij^2 with u = sqrt(8 kappa) d (eq. matern,
+// rotation matrix as printed, phi_Y = phi_X / phi_R).
+__global__ void k_omega_prep(const double *__restrict__ params, int64_t n, int64_t n_pad,
+                             const double *__restrict__ coords, double *__restrict__ oconst,
+                             double *__restrict__ coordT, double *__restrict__ logdet,
+                             int *__restrict__ pstatus) {
+    const int w = blockIdx.x;
+    const double *om = params + 5 * (int64_t)w;
+    const double phix = om[0], kap = om[1], nug = om[2], ratio = om[3], ang = om[4];
+    const bool ok = (phix > 0.0) && (kap > 0.0) && (nug >= 0.0) && (ratio > 0.0) &&
+                    isfinite(phix) && isfinite(kap) && isfinite(nug) && isfinite(ratio) &&
+                    isfinite(ang);
+    const double c = cos(ang), s = sin(ang);
+    const double s8k = sqrt(8.0 * kap);
+    const double ia = s8k / phix, ib = s8k * ratio / phix;
+    if (threadIdx.x == 0) {
+        double *oc = oconst + OC_N * (int64_t)w;
+        oc[OC_KAPPA] = kap;
+        oc[OC_NUG] = nug;
+        oc[OC_LOGC] = (1.0 - kap) * 0.69314718055994530942 - lgamma(kap);
+        oc[OC_S8K] = s8k;
+        oc[OC_COS] = c;
+        oc[OC_SIN] = s;
+        oc[OC_IA] = ia;
+        oc[OC_IB] = ib;
+        logdet[w] = 0.0;
+        pstatus[w] = ok ? PLK_POINT_OK : PLK_POINT_BAD_PARAM;
+    }
+    double *a = coordT + (int64_t)w * 2 * n_pad;
+    double *b = a + n_pad;
+    for (int64_t i = threadIdx.x; i < n_pad; i += blockDim.x) {
+        double ai = 0.0, bi = 0.0;
+        if (i < n && ok) {
+            const double x = coords[2 * i], yv = coords[2 * i + 1];
+            ai = (c * x - s * yv) * ia;
+            bi = (s * x + c * yv) * ib;
+        }
+        a[i] = ai;
+        b[i] = bi;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// rho(u) by the integral K_kappa(u) = int_0^inf exp(-u cosh t) cosh(kappa t) dt
+// ---------------------------------------------------------------------------
+// rho = exp(log c_kappa + kappa log u - u) * int_0^inf exp(-2u sinh^2(t/2)) cosh(kappa t) dt,
+// trapezoid rule (geometric convergence for this analytic integrand).
+
+// General evaluator: step min(0.1, 0.45/sqrt(u)), integrand formed in log space
+// (no overflow of cosh(kappa t)); used for u > TAB_USPLIT and for tiny w.
+__device__ double rho_integral(double u, double kap, double logc) {
+    if (u < 1e-15 && kap >= 0.5) return 1.0;
+    double h = 0.45 * rsqrt(u);
+    if (h > 0.1) h = 0.1;
+    double sum = 0.5, prev = 1.0;
+    for (int k = 1; k < 20000; ++k) {
+        const double t = k * h;
+        const double sh = sinh(0.5 * t);
+        const double kt = kap * t;
+        const double g = exp(kt + log1p(exp(-2.0 * kt)) - 0.69314718055994530942 - 2.0 * u * sh * sh);
+        sum += g;
+        if (g < prev && g < 1e-18 * sum) break;
+        prev = g;
+    }
+    return exp(logc + kap * log(u) - u) * (h * sum);
+}
+
+// Table builder: one block of 320 threads = 32 sub-intervals x TAB_NC Chebyshev nodes.
+// For u <= TAB_USPLIT the trapezoid nodes are the fixed grid t_k = k QH, whose
+// cosh(t_k) - 1 and log cosh(kappa t_k) are staged in shared memory, so one exp
+// per node remains.
+__global__ void __launch_bounds__(320) k_matern_table(const double *__restrict__ oconst,
+                                                      double *__restrict__ tab) {
+    __shared__ double E1[QNODES];   // cosh(t_k) - 1 = 2 sinh^2(t_k / 2)
+    __shared__ double L2[QNODES];   // log cosh(kappa t_k)
+    __shared__ double F[32][TAB_NC];
+    const int w = blockIdx.y;
+    const double *oc = oconst + OC_N * (int64_t)w;
+    const double kap = oc[OC_KAPPA], logc = oc[OC_LOGC];
+    for (int k = threadIdx.x; k < QNODES; k += blockDim.x) {
+        const double t = k * QH;
+        const double sh = sinh(0.5 * t);
+        E1[k] = 2.0 * sh * sh;
+        const double kt = kap * t;
+        L2[k] = kt + log1p(exp(-2.0 * kt)) - 0.69314718055994530942;
+    }
+    __syncthreads();
+    const int lb = threadIdx.x / TAB_NC, l = threadIdx.x % TAB_NC;
+    const int bucket = blockIdx.x * 32 + lb;
+    const double PI = 3.14159265358979323846;
+    if (bucket < TAB_NBUCKET) {
+        const int e = TAB_ELO + bucket / TAB_S, j = bucket % TAB_S;
+        const double tl = cos(PI * (l + 0.5) / TAB_NC);
+        const double wv = ldexp(1.0 + (j + 0.5 * (tl + 1.0)) / TAB_S, e);
+        const double u = sqrt(wv);
+        double r;
+        if (kap != kap || !(kap > 0.0)) {
+            r = nan("");
+        } else if (u <= TAB_USPLIT) {
+            double sum = 0.5, prev = 1.0;
+            for (int k = 1; k < QNODES; ++k) {
+                const double g = exp(L2[k] - u * E1[k]);
+                sum += g;
+                if (g < prev && g < 1e-18 * sum) break;
+                prev = g;
+            }
+            r = exp(logc + kap * log(u) - u) * (QH * sum);
+        } else {
+            r = rho_integral(u, kap, logc);
+        }
+        F[lb][l] = r;
+    }
+    __syncthreads();
+    if (l == 0 && bucket < TAB_NBUCKET) {
+        // Chebyshev coefficients a_k, then monomial coefficients in t.
+        double a[TAB_NC], c[TAB_NC], Tp[TAB_NC], Tc[TAB_NC], Tn[TAB_NC];
+        for (int k = 0; k < TAB_NC; ++k) {
+            double s = 0.0;
+            for (int m = 0; m < TAB_NC; ++m) s += F[lb][m] * cos(PI * k * (m + 0.5) / TAB_NC);
+            a[k] = (k == 0 ? 1.0 : 2.0) * s / TAB_NC;
+            c[k] = 0.0;
+            Tp[k] = 0.0;
+            Tc[k] = 0.0;
+        }
+        Tp[0] = 1.0;          // T_0
+        Tc[1] = 1.0;          // T_1
+        c[0] += a[0];
+        c[1] += a[1];
+        for (int k = 2; k < TAB_NC; ++k) {
+            for (int m = 0; m < TAB_NC; ++m) Tn[m] = (m > 0 ? 2.0 * Tc[m - 1] : 0.0) - Tp[m];
+            for (int m = 0; m < TAB_NC; ++m) {
+                c[m] += a[k] * Tn[m];
+                Tp[m] = Tc[m];
+                Tc[m] = Tn[m];
+            }
+        }
+        double *dst = tab + (int64_t)w * TAB_SIZE + (int64_t)bucket * TAB_NC;
+        for (int m = 0; m < TAB_NC; ++m) dst[m] = c[m];
+    }
+}
+
+// rho at w = u^2 from the table: exponent/mantissa bits give the sub-interval
+// and an exact local variable t; Horner in t.
+__device__ __forceinline__ double rho_table(const double *__restrict__ tab, double w, double kap,
+                                            double logc) {
+    const int hi = __double2hiint(w);
+    const int lo = __double2loint(w);
+    const int e = ((hi >> 20) & 0x7ff) - 1023;
+    if (e >= TAB_EHI) return 0.0;
+    if (e < TAB_ELO) return (w == 0.0) ? 1.0 : rho_integral(sqrt(w), kap, logc);
+    const int j = (hi >> (20 - TAB_SB)) & (TAB_S - 1);
+    const double m = __hiloint2double((hi & 0x000fffff) | 0x3ff00000, lo);   // in [1, 2)
+    const double t = fma(m, 2.0 * TAB_S, -(2.0 * TAB_S + 2.0 * j + 1.0));    // exact, in [-1, 1)
+    const double *c = tab + ((e - TAB_ELO) * TAB_S + j) * TAB_NC;
+    double r = __ldg(c + TAB_NC - 1);
+#pragma unroll
+    for (int k = TAB_NC - 2; k >= 0; --k) r = fma(r, t, __ldg(c + k));
+    return r;
+}
+
+// ---------------------------------------------------------------------------
+// Build of the bordered matrix tiles (Step 3 item 1)
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_build(int nb, int64_t n, int64_t n_pad, int q, int64_t tpo,
+                                               double *__restrict__ tiles,
+                                               const double *__restrict__ oconst,
+                                               const double *__restrict__ coordT,
+                                               const double *__restrict__ tab,
+                                               const double *__restrict__ Bt) {
+    const int w = blockIdx.y;
+    const int t = blockIdx.x;
+    int I = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
+    while ((I + 1) * (I + 2) / 2 <= t) ++I;
+    while (I * (I + 1) / 2 > t) --I;
+    const int J = t - I * (I + 1) / 2;
+    double *T = tiles + ((int64_t)w * tpo + t) * NT;
+    const int c = threadIdx.x & (TB - 1);
+    const int r0 = threadIdx.x >> 7;
+    const int64_t j = (int64_t)J * TB + c;
+    if (I == nb) {   // right-hand-side rows: B^T, zero beyond q rows / n columns
+        for (int r = r0; r < TB; r += 2) {
+            double v = 0.0;
+            if (J < nb && r < q && j < n) v = Bt[(int64_t)r * n_pad + j];
+            T[r * TB + c] = v;
+        }
+        return;
+    }
+    const double *oc = oconst + OC_N * (int64_t)w;
+    const double nug = oc[OC_NUG], kap = oc[OC_KAPPA], logc = oc[OC_LOGC];
+    const double *ca = coordT + (int64_t)w * 2 * n_pad;
+    const double *cb = ca + n_pad;
+    const double *tw = tab + (int64_t)w * TAB_SIZE;
+    const double aj = ca[j], bj = cb[j];
+    for (int r = r0; r < TB; r += 2) {
+        const int64_t i = (int64_t)I * TB + r;
+        double v;
+        if (i >= n || j >= n) {
+            v = (i == j) ? 1.0 : 0.0;              // identity padding
+        } else if (i == j) {
+            v = 1.0 + nug;
+        } else if (i < j) {
+            v = 0.0;                               // upper part of a diagonal tile, unused
+        } else {
+            const double da = ca[i] - aj, db = cb[i] - bj;
+            const double wv = fma(da, da, db * db);
+            v = rho_table(tw, wv, kap, logc);
+        }
+        T[r * TB + c] = v;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Diagonal tile: Cholesky, inverse of the factor, log-det (Step 3 item 2)
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_potrf(int J, int64_t tpo, double *__restrict__ tiles,
+                                               double *__restrict__ inv,
+                                               double *__restrict__ logdet,
+                                               int *__restrict__ pstatus) {
+    extern __shared__ double sm[];
+    double *P = sm;         // packed lower L
+    double *Wp = sm + PK;   // packed lower L^-1
+    __shared__ double s_ld;
+    __shared__ int s_bad;
+    const int w = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    double *T = tiles + ((int64_t)w * tpo + tile_index(J, J)) * NT;
+    for (int e = tid; e < NT; e += 256) {
+        const int r = e >> 7, c = e & (TB - 1);
+        if (c <= r) P[pk(r, c)] = T[e];
+    }
+    if (tid == 0) {
+        s_ld = 0.0;
+        s_bad = 0;
+    }
+    __syncthreads();
+    for (int j = 0; j < TB; ++j) {
+        if (tid == 0) {
+            const double d = P[pk(j, j)];
+            if (!(d > 0.0)) {
+                s_bad = 1;
+                P[pk(j, j)] = nan("");
+            } else {
+                P[pk(j, j)] = sqrt(d);
+                s_ld += log(d);
+            }
+        }
+        __syncthreads();
+        const double rl = 1.0 / P[pk(j, j)];
+        for (int i = j + 1 + tid; i < TB; i += 256) P[pk(i, j)] *= rl;
+        __syncthreads();
+        for (int i = j + 1 + warp; i < TB; i += 8) {
+            const double lij = P[pk(i, j)];
+            const int bi = pk(i, 0);
+            for (int k = j + 1 + lane; k <= i; k += 32) P[bi + k] -= lij * P[pk(k, j)];
+        }
+        __syncthreads();
+    }
+    // W = L^-1, row by row: W_ii = 1/L_ii, W_ij = -(sum_{k=j}^{i-1} L_ik W_kj) / L_ii
+    for (int i = 0; i < TB; ++i) {
+        const int bi = pk(i, 0);
+        const double lii = P[bi + i];
+        for (int jj = tid; jj <= i; jj += 256) {
+            if (jj == i) {
+                Wp[bi + i] = 1.0 / lii;
+            } else {
+                double s = 0.0;
+                for (int k = jj; k < i; ++k) s = fma(P[bi + k], Wp[pk(k, jj)], s);
+                Wp[bi + jj] = -s / lii;
+            }
+        }
+        __syncthreads();
+    }
+    double *Wg = inv + (int64_t)w * NT;
+    for (int e = tid; e < NT; e += 256) {
+        const int r = e >> 7, c = e & (TB - 1);
+        T[e] = (c <= r) ? P[pk(r, c)] : 0.0;
+        Wg[e] = (c <= r) ? Wp[pk(r, c)] : 0.0;
+    }
+    if (tid == 0) {
+        logdet[w] += s_ld;
+        if (s_bad && pstatus[w] == PLK_POINT_OK) pstatus[w] = PLK_POINT_NOT_PD;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Panel solve (MODE 0: C = A B^T, B = L_JJ^-1, in place) and trailing update
+// (MODE 1: C -= A B^T), FP64, 128 x 128 tiles, 8 x 8 outputs per thread.
+// ---------------------------------------------------------------------------
+template <int MODE>
+__global__ void __launch_bounds__(256, 1) k_gemm_nt(int J, int64_t tpo, double *tiles,
+                                                    const double *__restrict__ inv) {
+    __shared__ double As[16][TB + 2];
+    __shared__ double Bs[16][TB + 2];
+    const int w = blockIdx.y, t = blockIdx.x, tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    double *base = tiles + (int64_t)w * tpo * NT;
+    const double *A;
+    const double *B;
+    double *C;
+    if (MODE == 0) {
+        const int I = J + 1 + t;
+        C = base + tile_index(I, J) * NT;
+        A = C;
+        B = inv + (int64_t)w * NT;
+    } else {
+        int I, K;
+        decode_trailing(t, J, I, K);
+        A = base + tile_index(I, J) * NT;
+        B = base + tile_index(K, J) * NT;
+        C = base + tile_index(I, K) * NT;
+    }
+    double acc[8][8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int jj = 0; jj < 8; ++jj) acc[i][jj] = 0.0;
+    for (int k0 = 0; k0 < TB; k0 += 16) {
+#pragma unroll
+        for (int l = 0; l < 8; ++l) {
+            const int e = tid + 256 * l;
+            const int r = e >> 4, kk = e & 15;
+            As[kk][r] = A[r * TB + k0 + kk];
+            Bs[kk][r] = B[r * TB + k0 + kk];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < 16; ++kk) {
+            double a[8], b[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+            for (int jj = 0; jj < 8; ++jj) b[jj] = Bs[kk][tx + 16 * jj];
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+#pragma unroll
+                for (int jj = 0; jj < 8; ++jj) acc[i][jj] = fma(a[i], b[jj], acc[i][jj]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int jj = 0; jj < 8; ++jj) {
+            const int idx = (ty + 16 * i) * TB + tx + 16 * jj;
+            if (MODE == 0)
+                C[idx] = acc[i][jj];
+            else
+                C[idx] -= acc[i][jj];
+        }
+}
+
+// ---------------------------------------------------------------------------
+// Closed form per omega (Step 3 items 5-8; eqs. betahat, 4, profile, remlpro)
+// ---------------------------------------------------------------------------
+__global__ void k_finalize(int count, int64_t k0, int M, int p, int64_t n, int nb, int reml,
+                           int64_t tpo, const double *__restrict__ tiles,
+                           const double *__restrict__ ldv, const int *__restrict__ pstatus,
+                           const double *__restrict__ sumlogy, const double *__restrict__ lambdas,
+                           double *logL, double *sigma2, double *beta, double *logdet,
+                           int32_t *status) {
+    const int w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= count) return;
+    const int64_t k = k0 + w;
+    const double *S = tiles + ((int64_t)w * tpo + tile_index(nb, nb)) * NT;   // -B^T V^-1 B
+    int st = pstatus[w];
+    const double NaN = nan("");
+    double Q[16 * 16];
+    double cv[16], bv[16];
+    double ldx = NaN;
+    if (st == PLK_POINT_OK) {
+        for (int a = 0; a < p; ++a)
+            for (int b = 0; b <= a; ++b) Q[a * p + b] = -S[(M + a) * TB + (M + b)];
+        for (int jj = 0; jj < p && st == PLK_POINT_OK; ++jj) {
+            double d = Q[jj * p + jj];
+            for (int kk = 0; kk < jj; ++kk) d -= Q[jj * p + kk] * Q[jj * p + kk];
+            if (!(d > 0.0)) {
+                st = PLK_POINT_NOT_PD;
+                break;
+            }
+            const double l = sqrt(d);
+            Q[jj * p + jj] = l;
+            for (int i = jj + 1; i < p; ++i) {
+                double s = Q[i * p + jj];
+                for (int kk = 0; kk < jj; ++kk) s -= Q[i * p + kk] * Q[jj * p + kk];
+                Q[i * p + jj] = s / l;
+            }
+        }
+        if (st == PLK_POINT_OK) {
+            ldx = 0.0;
+            for (int jj = 0; jj < p; ++jj) ldx += 2.0 * log(Q[jj * p + jj]);
+        }
+    }
+    const bool good = (st == PLK_POINT_OK);
+    const double ld = good ? ldv[w] : NaN;
+    const double two_pi_log = 1.8378770664093454836;   // log(2 pi)
+    const double slog = *sumlogy;
+    for (int m = 0; m < M; ++m) {
+        double ll = NaN, s2 = NaN;
+        if (good) {
+            for (int a = 0; a < p; ++a) {
+                double tt = -S[(M + a) * TB + m];
+                for (int kk = 0; kk < a; ++kk) tt -= Q[a * p + kk] * cv[kk];
+                cv[a] = tt / Q[a * p + a];
+            }
+            double sbh = 0.0;
+            for (int a = 0; a < p; ++a) sbh += cv[a] * cv[a];
+            const double rss = -S[m * TB + m] - sbh;
+            for (int a = p - 1; a >= 0; --a) {
+                double tt = cv[a];
+                for (int kk = a + 1; kk < p; ++kk) tt -= Q[kk * p + a] * bv[kk];
+                bv[a] = tt / Q[a * p + a];
+            }
+            const double jac = -2.0 * (lambdas[m] - 1.0) * slog;
+            double m2;
+            if (!reml) {
+                s2 = rss / (double)n;
+                m2 = (double)n * log(s2) + ld + jac + (double)n * two_pi_log + (double)n;
+            } else {
+                const double dof = (double)(n - p);
+                s2 = rss / dof;
+                m2 = dof * log(s2) + ld + ldx + jac + (double)n * two_pi_log + dof;
+            }
+            if (!(rss > 0.0)) {
+                st = PLK_POINT_RSS_NONPOS;
+                m2 = NaN;
+            }
+            ll = -0.5 * m2;
+        }
+        if (logL) logL[k * M + m] = ll;
+        if (sigma2) sigma2[k * M + m] = s2;
+        if (beta)
+            for (int a = 0; a < p; ++a) beta[(k * M + m) * p + a] = good ? bv[a] : NaN;
+    }
+    if (logdet) {
+        logdet[2 * k] = ld;
+        logdet[2 * k + 1] = good ? ldx : NaN;
+    }
+    if (status) status[k] = st;
+}
+
+// ---------------------------------------------------------------------------
+// Profile reduction and likelihood CI (Section 3.6, eq. likelihood)
+// ---------------------------------------------------------------------------
+__global__ void k_profile_max(const double *__restrict__ vals, int64_t G, int64_t SM,
+                              double *__restrict__ prof) {
+    const int64_t g = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (g >= G) return;
+    double best = -INFINITY;
+    int any = 0;
+    for (int64_t j = lane; j < SM; j += 32) {
+        const double v = vals[g * SM + j];
+        if (v == v) {
+            any = 1;
+            best = fmax(best, v);
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        best = fmax(best, __shfl_xor_sync(0xffffffffu, best, o));
+        any |= __shfl_xor_sync(0xffffffffu, any, o);
+    }
+    if (lane == 0) prof[g] = any ? best : nan("");
+}
+
+__global__ void k_profile_ci(const double *__restrict__ grid, const double *__restrict__ prof,
+                             int64_t G, double half_q, double *__restrict__ out) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    int64_t ib = -1;
+    for (int64_t g = 0; g < G; ++g) {
+        const double v = prof[g];
+        if (v != v) continue;
+        if (ib < 0 || v > prof[ib]) ib = g;
+    }
+    if (ib < 0) {
+        out[0] = out[1] = out[2] = out[3] = nan("");
+        return;
+    }
+    const double thr = prof[ib] - half_q;
+    double lo = grid[0], hi = grid[G - 1];
+    int cens = 0;
+    int64_t in = ib;
+    int64_t g = ib - 1;
+    for (; g >= 0; --g) {
+        const double v = prof[g];
+        if (v != v) continue;
+        if (v < thr) break;
+        in = g;
+    }
+    if (g >= 0) {
+        const double f = (thr - prof[g]) / (prof[in] - prof[g]);
+        lo = grid[g] + f * (grid[in] - grid[g]);
+    } else {
+        cens |= 1;
+    }
+    in = ib;
+    for (g = ib + 1; g < G; ++g) {
+        const double v = prof[g];
+        if (v != v) continue;
+        if (v < thr) break;
+        in = g;
+    }
+    if (g < G) {
+        const double f = (thr - prof[g]) / (prof[in] - prof[g]);
+        hi = grid[g] + f * (grid[in] - grid[g]);
+    } else {
+        cens |= 2;
+    }
+    out[0] = lo;
+    out[1] = hi;
+    out[2] = grid[ib];
+    out[3] = (double)cens;
+}
+
+// ---------------------------------------------------------------------------
+// Host launchers
+// ---------------------------------------------------------------------------
+cudaError_t launch_boxcox(int64_t n, int64_t n_pad, int p, int M, const double *y, const double *X,
+                          const double *lam, double *Bt, double *sumlogy, cudaStream_t s) {
+    const int64_t total = (int64_t)(M + p) * n_pad;
+    int blocks = (int)((total + 255) / 256);
+    if (blocks > 4096) blocks = 4096;
+    k_boxcox_rows<<<blocks, 256, 0, s>>>(n, n_pad, p, M, y, X, lam, Bt);
+    k_sumlog<<<1, 1024, 0, s>>>(n, y, sumlogy);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fp64_batch(const BatchArgs &b, cudaStream_t s) {
+    // per function and device; cheap to repeat
+    cudaError_t e = cudaFuncSetAttribute(k_potrf, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(2 * PK * sizeof(double)));
+    if (e != cudaSuccess) return e;
+    const int cnt = b.count;
+    k_omega_prep<<<cnt, 256, 0, s>>>(b.params, b.n, b.n_pad, b.coords, b.oconst, b.coordT, b.ldv,
+                                     b.pstatus);
+    k_matern_table<<<dim3((TAB_NBUCKET + 31) / 32, cnt), 320, 0, s>>>(b.oconst, b.tab);
+    k_build<<<dim3((unsigned)b.tpo, cnt), 256, 0, s>>>(b.nb, b.n, b.n_pad, b.q, b.tpo, b.tiles,
+                                                       b.oconst, b.coordT, b.tab, b.Bt);
+    for (int J = 0; J < b.nb; ++J) {
+        k_potrf<<<cnt, 256, 2 * PK * sizeof(double), s>>>(J, b.tpo, b.tiles, b.inv, b.ldv,
+                                                           b.pstatus);
+        const int m = b.nb - J;   // tile rows below the diagonal, RHS row included
+        k_gemm_nt<0><<<dim3(m, cnt), 256, 0, s>>>(J, b.tpo, b.tiles, b.inv);
+        k_gemm_nt<1><<<dim3(m * (m + 1) / 2, cnt), 256, 0, s>>>(J, b.tpo, b.tiles, b.inv);
+    }
+    k_finalize<<<(cnt + 63) / 64, 64, 0, s>>>(cnt, b.k0, b.M, b.p, b.n, b.nb, b.reml, b.tpo,
+                                              b.tiles, b.ldv, b.pstatus, b.sumlogy, b.lambdas,
+                                              b.logL, b.sigma2, b.beta, b.logdet, b.status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_profile_max(const double *vals, int64_t G, int64_t SM, double *prof,
+                               cudaStream_t s) {
+    const int wpb = 8;
+    k_profile_max<<<(unsigned)((G + wpb - 1) / wpb), 32 * wpb, 0, s>>>(vals, G, SM, prof);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_profile_ci(const double *grid, const double *prof, int64_t G, double half_q,
+                              double *out, cudaStream_t s) {
+    k_profile_ci<<<1, 32, 0, s>>>(grid, prof, G, half_q, out);
+    return cudaGetLastError();
+}
+
+}  // namespace plk

@@ -1,0 +1,41 @@
+// plk_kernels.cuh -- launchers of the CUDA kernels (internal to libplk).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace plk {
+
+// One batch of `count` parameter points of one dataset.  Per-point arrays
+// (oconst, coordT, tab, tiles, inv, ldv, pstatus) are indexed by the point's
+// position w in the batch; outputs by its global index k0 + w.
+struct BatchArgs {
+    int count;
+    int64_t k0;
+    int64_t n, n_pad;
+    int nb, q, p, M, reml;
+    int64_t tpo;
+    const double *params;    // count x 5 (already offset to the batch)
+    const double *coords;    // n x 2
+    const double *lambdas;   // M
+    const double *Bt;        // q x n_pad
+    const double *sumlogy;   // 1
+    double *oconst;          // count x OC_N
+    double *coordT;          // count x 2 x n_pad
+    double *tab;             // count x TAB_SIZE
+    double *tiles;           // count x tpo x NT
+    double *inv;             // count x NT
+    double *ldv;             // count
+    int *pstatus;            // count
+    double *logL, *sigma2, *beta, *logdet;
+    int32_t *status;
+};
+
+cudaError_t launch_boxcox(int64_t n, int64_t n_pad, int p, int M, const double *y, const double *X,
+                          const double *lam, double *Bt, double *sumlogy, cudaStream_t s);
+cudaError_t launch_fp64_batch(const BatchArgs &b, cudaStream_t s);
+cudaError_t launch_profile_max(const double *vals, int64_t G, int64_t SM, double *prof,
+                               cudaStream_t s);
+cudaError_t launch_profile_ci(const double *grid, const double *prof, int64_t G, double half_q,
+                              double *out, cudaStream_t s);
+
+}  // namespace plk

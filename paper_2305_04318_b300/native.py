@@ -1,0 +1,244 @@
+"""ctypes binding of libplk.so (argument marshalling only).
+
+Every computation runs in the library's CUDA kernels; this module only passes
+pointers, sizes and streams.  If the library is missing or cannot be loaded the
+functions raise: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import re
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libplk.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "plk.h")
+
+PLK_OK, PLK_E_INVALID, PLK_E_NOMEM, PLK_E_NOT_READY, PLK_E_TIMEOUT, PLK_E_CUDA, PLK_E_CANCELLED = range(7)
+POINT_OK, POINT_NOT_PD, POINT_BAD_PARAM, POINT_RSS_NONPOS, POINT_FP64_RETRY = 0, 1, 2, 3, 16
+FP64, MIXED = 0, 1
+
+
+class PlkError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"plk status {status}: {msg}")
+        self.status = status
+
+
+class EvalArgs(C.Structure):
+    _fields_ = [("n", C.c_int64), ("p", C.c_int32), ("M", C.c_int32),
+                ("coords", C.c_void_p), ("y", C.c_void_p), ("X", C.c_void_p), ("lambdas", C.c_void_p),
+                ("K", C.c_int64), ("params", C.c_void_p),
+                ("logL", C.c_void_p), ("sigma2", C.c_void_p), ("beta", C.c_void_p),
+                ("logdet", C.c_void_p), ("status", C.c_void_p)]
+
+
+class Options(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("reml", C.c_int32), ("batch", C.c_int32), ("reserved", C.c_int32)]
+
+
+_lib = None
+
+
+def declared_symbols():
+    """Names of the functions include/plk.h declares."""
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(plk_[a-z0-9_]+)\s*\(", text)))
+
+
+def lib():
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with `python -m paper_2305_04318_b300.build`")
+    L = C.CDLL(LIB_PATH)
+    vp, i32, i64, dbl, sz = C.c_void_p, C.c_int32, C.c_int64, C.c_double, C.c_size_t
+    sig = {
+        "plk_eval_workspace_bytes": (sz, [i64, i32, i32, i32, i32]),
+        "plk_eval_device": (C.c_int, [C.POINTER(EvalArgs), C.POINTER(Options), vp, sz, vp]),
+        "plk_create": (C.c_int, [C.POINTER(vp), C.c_int, vp, sz, C.POINTER(vp), C.c_int]),
+        "plk_create_dataset": (C.c_int, [vp, vp, vp, vp, i64, i32, C.POINTER(i64)]),
+        "plk_submit_profile": (C.c_int, [vp, i64, vp, i64, vp, i32, C.POINTER(Options), C.POINTER(i64)]),
+        "plk_poll": (C.c_int, [vp, i64, i32, vp, vp, vp, vp, vp, vp, vp, vp]),
+        "plk_release_dataset": (C.c_int, [vp, i64]),
+        "plk_memory_stats": (C.c_int, [vp, C.POINTER(sz), C.POINTER(sz)]),
+        "plk_destroy": (C.c_int, [vp]),
+        "plk_last_error": (C.c_char_p, []),
+        "plk_profile_max_device": (C.c_int, [vp, i64, i64, vp, vp]),
+        "plk_profile_ci_device": (C.c_int, [vp, vp, i64, dbl, vp, vp]),
+        "plk_chi2_1_quantile": (dbl, [dbl]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def _check(st):
+    if st != PLK_OK:
+        raise PlkError(st, lib().plk_last_error().decode())
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _np_ptr(a):
+    return None if a is None else C.c_void_p(a.ctypes.data)
+
+
+def _stream_handle(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def workspace_bytes(n, p, M, batch, precision=FP64):
+    return int(lib().plk_eval_workspace_bytes(n, p, M, batch, precision))
+
+
+def default_batch(n, K, limit_bytes=8e9):
+    """Points per batch so that the tile workspace stays near limit_bytes."""
+    nb = -(-int(n) // 128)
+    per = (nb + 1) * (nb + 2) // 2 * 128 * 128 * 8
+    return int(max(1, min(296, limit_bytes // per, max(K, 1))))
+
+
+def eval_device(coords, y, X, lambdas, params, precision=FP64, reml=False, batch=0,
+                workspace=None, stream=None, outputs=None):
+    """Evaluate l_p at all rows of `params` (torch CUDA float64 tensors).
+
+    Returns a dict of CUDA tensors logL[K,M], sigma2[K,M], beta[K,M,p],
+    logdet[K,2], status[K] (int32).  The workspace (uint8 CUDA tensor) is
+    allocated with torch when not given.  Asynchronous on `stream`.
+    """
+    import torch
+    dev = coords.device
+    n, p = X.shape
+    M = lambdas.shape[0]
+    K = params.shape[0]
+    for t in (coords, y, X, lambdas, params):
+        assert t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()
+    if batch <= 0:
+        batch = default_batch(n, K)
+    if outputs is None:
+        outputs = dict(logL=torch.empty((K, M), dtype=torch.float64, device=dev),
+                       sigma2=torch.empty((K, M), dtype=torch.float64, device=dev),
+                       beta=torch.empty((K, M, p), dtype=torch.float64, device=dev),
+                       logdet=torch.empty((K, 2), dtype=torch.float64, device=dev),
+                       status=torch.empty((K,), dtype=torch.int32, device=dev))
+    wsb = workspace_bytes(n, p, M, batch, precision)
+    if wsb == 0:
+        raise PlkError(PLK_E_INVALID, f"invalid sizes n={n} p={p} M={M}")
+    if workspace is None:
+        workspace = torch.empty((wsb,), dtype=torch.uint8, device=dev)
+    a = EvalArgs(n, p, M, _ptr(coords), _ptr(y), _ptr(X), _ptr(lambdas), K, _ptr(params),
+                 _ptr(outputs.get("logL")), _ptr(outputs.get("sigma2")), _ptr(outputs.get("beta")),
+                 _ptr(outputs.get("logdet")), _ptr(outputs.get("status")))
+    o = Options(precision, int(bool(reml)), batch, 0)
+    _check(lib().plk_eval_device(C.byref(a), C.byref(o), _ptr(workspace), workspace.numel(),
+                                 _stream_handle(stream)))
+    return outputs
+
+
+def profile_max_device(vals, prof=None, stream=None):
+    """prof[g] = NaN-skipping max of vals[g, ...] (CUDA float64)."""
+    import torch
+    G = vals.shape[0]
+    SM = int(np.prod(vals.shape[1:])) if vals.dim() > 1 else 1
+    if prof is None:
+        prof = torch.empty((G,), dtype=torch.float64, device=vals.device)
+    _check(lib().plk_profile_max_device(_ptr(vals), G, SM, _ptr(prof), _stream_handle(stream)))
+    return prof
+
+
+def profile_ci_device(grid, prof, level=0.95, out=None, stream=None):
+    """CUDA tensor [lo, hi, argmax, censored] of the likelihood CI."""
+    import torch
+    if out is None:
+        out = torch.empty((4,), dtype=torch.float64, device=grid.device)
+    _check(lib().plk_profile_ci_device(_ptr(grid), _ptr(prof), grid.shape[0], float(level), _ptr(out),
+                                       _stream_handle(stream)))
+    return out
+
+
+def chi2_1_quantile(level):
+    return float(lib().plk_chi2_1_quantile(float(level)))
+
+
+class Context:
+    """Device-resident datasets and asynchronous profile jobs (plk_create ... plk_destroy).
+
+    `arena` may be a torch uint8 CUDA tensor (PyTorch owns the memory); if None
+    the library allocates `arena_bytes` itself.
+    """
+
+    def __init__(self, arena_bytes, device=0, arena=None, n_streams=4, streams=None):
+        self._arena = arena
+        h = C.c_void_p()
+        sarr = None
+        if streams is not None:
+            sarr = (C.c_void_p * len(streams))(*[s.cuda_stream for s in streams])
+            n_streams = len(streams)
+            self._streams = streams
+        _check(lib().plk_create(C.byref(h), device, _ptr(arena) if arena is not None else None,
+                                int(arena_bytes), sarr, n_streams))
+        self.h = h
+
+    def create_dataset(self, coords, y, X):
+        coords = np.ascontiguousarray(coords, dtype=np.float64)
+        y = np.ascontiguousarray(y, dtype=np.float64)
+        X = np.ascontiguousarray(X, dtype=np.float64)
+        out = C.c_int64()
+        _check(lib().plk_create_dataset(self.h, _np_ptr(coords), _np_ptr(y), _np_ptr(X), X.shape[0],
+                                        X.shape[1], C.byref(out)))
+        return out.value
+
+    def submit(self, ds, params, lambdas, precision=FP64, reml=False, batch=0):
+        params = np.ascontiguousarray(params, dtype=np.float64).reshape(-1, 5)
+        lambdas = np.ascontiguousarray(lambdas, dtype=np.float64)
+        out = C.c_int64()
+        o = Options(precision, int(bool(reml)), batch, 0)
+        _check(lib().plk_submit_profile(self.h, ds, _np_ptr(params), params.shape[0], _np_ptr(lambdas),
+                                        lambdas.shape[0], C.byref(o), C.byref(out)))
+        return dict(id=out.value, K=params.shape[0], M=lambdas.shape[0])
+
+    def poll(self, job, p, timeout_ms=-1):
+        """Results as numpy arrays, or None if not ready within timeout_ms."""
+        K, M = job["K"], job["M"]
+        r = dict(logL=np.empty((K, M)), sigma2=np.empty((K, M)), beta=np.empty((K, M, p)),
+                 logdet=np.empty((K, 2)), status=np.empty(K, dtype=np.int32))
+        ts, t0, t1 = C.c_double(), C.c_double(), C.c_double()
+        st = lib().plk_poll(self.h, job["id"], int(timeout_ms), _np_ptr(r["logL"]), _np_ptr(r["sigma2"]),
+                            _np_ptr(r["beta"]), _np_ptr(r["logdet"]), _np_ptr(r["status"]),
+                            C.byref(ts), C.byref(t0), C.byref(t1))
+        if st == PLK_E_NOT_READY:
+            return None
+        _check(st)
+        r.update(t_submit=ts.value, t_start=t0.value, t_done=t1.value)
+        return r
+
+    def release_dataset(self, ds):
+        _check(lib().plk_release_dataset(self.h, ds))
+
+    def memory_stats(self):
+        a, b = C.c_size_t(), C.c_size_t()
+        _check(lib().plk_memory_stats(self.h, C.byref(a), C.byref(b)))
+        return a.value, b.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            _check(lib().plk_destroy(self.h))
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

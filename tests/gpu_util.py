@@ -1,0 +1,43 @@
+"""Helpers shared by the GPU tests: move inputs to the device, run the CUDA
+path through the C ABI, run the oracle on the same inputs, compare."""
+import numpy as np
+import torch
+
+from paper_2305_04318_b300 import native as nv
+
+# FP64 mode: |Delta l_p| <= 1e-8 |l_p| (the tolerance the method's FP64 mode
+# promises), with matching per-point status.
+RTOL_LOGL = 1e-8
+
+
+def to_dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64), device="cuda")
+
+
+def gpu_eval(ds, params, lambdas, **kw):
+    out = nv.eval_device(to_dev(ds.coords), to_dev(ds.y), to_dev(ds.X), to_dev(lambdas), to_dev(params), **kw)
+    torch.cuda.synchronize()
+    return {k: v.cpu().numpy() for k, v in out.items()}
+
+
+def oracle_eval(ds, params, lambdas, reml=False):
+    import oracle
+    return oracle.profile_batch(ds.coords, ds.y, ds.X, params, lambdas, reml=reml)
+
+
+def compare(g, o, rtol=RTOL_LOGL, what=""):
+    np.testing.assert_array_equal(g["status"], o["status"], err_msg=f"{what} status")
+    ok = o["status"] == 0
+    gl, ol = g["logL"][ok], o["logL"][ok]
+    fin = np.isfinite(ol)
+    np.testing.assert_array_equal(np.isfinite(gl), fin, err_msg=f"{what} finiteness")
+    err = np.abs(gl[fin] - ol[fin]) / np.abs(ol[fin])
+    assert err.size == 0 or err.max() <= rtol, f"{what} max rel logL err {err.max():.3e}"
+    np.testing.assert_allclose(g["logdet"][ok], o["logdet"][ok], rtol=rtol, atol=1e-9, err_msg=f"{what} logdet")
+    np.testing.assert_allclose(g["sigma2"][ok], o["sigma2"][ok], rtol=100 * rtol, err_msg=f"{what} sigma2")
+    scale = np.abs(o["beta"][ok]).max() if ok.any() else 1.0
+    np.testing.assert_allclose(g["beta"][ok], o["beta"][ok], rtol=100 * rtol, atol=100 * rtol * scale,
+                               err_msg=f"{what} beta")
+    bad = ~ok
+    assert np.all(np.isnan(g["logL"][bad & (o["status"] != 3)]))
+    return float(err.max()) if err.size else 0.0

@@ -1,0 +1,58 @@
+"""Context API on the GPU: device-resident datasets, asynchronous jobs,
+continuous batching; results equal the stateless path's and are the same
+alone and in the mix."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from paper_2305_04318_b300 import native as nv, synth
+from gpu_util import gpu_eval
+
+pytestmark = pytest.mark.gpu
+
+
+def test_jobs_match_stateless_and_mix():
+    dsets = [synth.aniso_dataset(40 + i, n, math.sqrt(n / 10), p) for i, (n, p) in enumerate([(300, 3), (700, 2), (150, 5)])]
+    lams = synth.LAMBDA_GRID_9
+    grids = [synth.omega_from_unit(np.random.default_rng(i).uniform(size=(K, 5))) for i, K in enumerate([37, 20, 50])]
+    ref = [gpu_eval(d, g, lams, batch=8) for d, g in zip(dsets, grids)]
+    arena = torch.empty(6 << 30, dtype=torch.uint8, device="cuda")
+    with nv.Context(arena.numel(), arena=arena, n_streams=3) as ctx:
+        ids = [ctx.create_dataset(d.coords, d.y, d.X) for d in dsets]
+        # alone
+        alone = []
+        for i, d in enumerate(dsets):
+            j = ctx.submit(ids[i], grids[i], lams, batch=8)
+            alone.append(ctx.poll(j, d.p))
+        # all at once (interleaved on 3 streams)
+        jobs = [ctx.submit(ids[i], grids[i], lams, batch=8) for i in range(3)]
+        mix = [ctx.poll(j, dsets[i].p) for i, j in enumerate(jobs)]
+        used, high = ctx.memory_stats()
+        assert high > used > 0
+        for i in range(3):
+            for k in ("logL", "sigma2", "beta", "logdet", "status"):
+                np.testing.assert_array_equal(alone[i][k], ref[i][k])
+                np.testing.assert_array_equal(mix[i][k], ref[i][k])
+            assert mix[i]["t_done"] >= mix[i]["t_start"] >= mix[i]["t_submit"]
+        for i in ids:
+            ctx.release_dataset(i)
+
+
+def test_context_validation_and_nomem():
+    with nv.Context(64 << 20, n_streams=1) as ctx:
+        d = synth.aniso_dataset(1, 50, 2.0, 2)
+        with pytest.raises(nv.PlkError):
+            ctx.create_dataset(d.coords, -d.y, d.X)
+        big = synth.aniso_dataset(2, 4000, 20.0, 3)
+        ds = ctx.create_dataset(big.coords, big.y, big.X)
+        with pytest.raises(nv.PlkError) as e:
+            ctx.submit(ds, np.array([[1.0, 1.0, 0.1, 1.0, 0.0]]), [0.0])
+        assert e.value.status == nv.PLK_E_NOMEM
+        ds2 = ctx.create_dataset(d.coords, d.y, d.X)
+        j = ctx.submit(ds2, np.array([[0.5, 1.0, 0.1, 1.0, 0.0]]), [0.0, 1.0])
+        r = ctx.poll(j, 2)
+        assert r["status"][0] == 0 and np.all(np.isfinite(r["logL"]))
+        j = ctx.submit(ds2, np.zeros((0, 5)), [0.0])
+        assert ctx.poll(j, 2)["logL"].shape == (0, 1)

@@ -1,0 +1,52 @@
+"""Host-side checks of libplk.so that need no GPU: it loads, exports every
+function include/plk.h declares, sizes workspaces, validates arguments."""
+import ctypes as C
+
+import pytest
+import scipy.stats as st
+
+from paper_2305_04318_b300 import build, native as nv
+
+
+@pytest.fixture(scope="module")
+def L():
+    build.build()
+    return nv.lib()
+
+
+def test_exports_every_declared_symbol(L):
+    names = nv.declared_symbols()
+    assert len(names) >= 13
+    for n in names:
+        assert hasattr(L, n), n
+
+
+def test_workspace_sizes(L):
+    assert nv.workspace_bytes(4000, 3, 9, 1) > 0
+    assert nv.workspace_bytes(4000, 3, 9, 8) > 7 * nv.workspace_bytes(4000, 3, 9, 1) * 0.9
+    # tiles: (nb + 1)(nb + 2)/2 tiles of 128 x 128 doubles per point
+    nb = 32
+    assert nv.workspace_bytes(4000, 3, 9, 1) >= (nb + 1) * (nb + 2) // 2 * 128 * 128 * 8
+    for bad in [(3, 3, 1), (10, 0, 1), (10, 17, 1), (100, 3, 0), (100, 10, 60)]:
+        assert nv.workspace_bytes(*bad, 1) == 0
+    assert nv.workspace_bytes(100, 2, 1, 1, precision=7) == 0
+
+
+def test_chi2_quantile(L):
+    for lev in (0.5, 0.9, 0.95, 0.999):
+        assert abs(nv.chi2_1_quantile(lev) - st.chi2.ppf(lev, 1)) < 1e-11
+
+
+def test_eval_device_rejects_bad_arguments_without_touching_the_gpu(L):
+    a = nv.EvalArgs(n=10, p=2, M=1)   # NULL input pointers
+    o = nv.Options(0, 0, 1, 0)
+    assert L.plk_eval_device(C.byref(a), C.byref(o), None, 0, None) == nv.PLK_E_INVALID
+    assert b"NULL" in L.plk_last_error()
+    a = nv.EvalArgs(n=2, p=2, M=1)
+    assert L.plk_eval_device(C.byref(a), C.byref(o), None, 0, None) == nv.PLK_E_INVALID
+    assert L.plk_eval_device(None, C.byref(o), None, 0, None) == nv.PLK_E_INVALID
+
+
+def test_profile_ci_rejects_bad_level(L):
+    assert L.plk_profile_ci_device(None, None, 5, 0.95, None, None) == nv.PLK_E_INVALID
+    assert L.plk_profile_max_device(None, 3, 0, None, None) == nv.PLK_E_INVALID
