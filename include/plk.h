@@ -74,8 +74,12 @@ typedef struct {
     int32_t precision;  /* plk_precision */
     int32_t reml;       /* 0: ML profile (eq. profile); 1: REML profile (eq. remlpro) */
     int32_t batch;      /* omega points per device batch; 0 = library default */
-    int32_t reserved;
+    int32_t flags;      /* PLK_FLAG_* bits */
 } plk_options;
+
+/* flags: bracket every kernel launch with CUDA events on its stream and
+ * accumulate the elapsed time per kernel class (read with plk_kernel_timing). */
+#define PLK_FLAG_KERNEL_TIMING 1
 
 /* ------------------------------------------------------------------------ */
 /* Stateless device-pointer evaluation (one dataset, K points)               */
@@ -190,6 +194,21 @@ plk_status plk_profile_ci_device(const double *grid, const double *prof, int64_t
 
 /* chi2_1 quantile used by the CI: c with P(chi2_1 <= c) = level. */
 double plk_chi2_1_quantile(double level);
+
+/* ------------------------------------------------------------------------ */
+/* Instrumentation (not part of the paper's method)                          */
+/* ------------------------------------------------------------------------ */
+
+/* Per kernel class c < n_classes: total device milliseconds and launch count of
+ * the launches made with PLK_FLAG_KERNEL_TIMING since the last reset.  Waits
+ * for the recorded events (so call it after the work completes).  Returns the
+ * number of classes the library defines in *n_defined when non-NULL.  reset != 0
+ * clears the accumulators afterwards.  Process-wide, thread-safe. */
+plk_status plk_kernel_timing(double *total_ms, int64_t *launches, int32_t n_classes, int32_t reset,
+                             int32_t *n_defined);
+
+/* Name of kernel class c ("" if out of range). */
+const char *plk_kernel_class_name(int32_t c);
 
 #ifdef __cplusplus
 }

@@ -129,11 +129,90 @@ extern "C" size_t plk_eval_workspace_bytes(int64_t n, int32_t p, int32_t M, int3
     return L.total;
 }
 
+// ---------------------------------------------------------------------------
+// optional per-launch event timing
+// ---------------------------------------------------------------------------
+namespace {
+class EventTimer : public KernelTimer {
+  public:
+    void begin(int cls, cudaStream_t s) override {
+        std::lock_guard<std::mutex> lk(mu_);
+        Pending p;
+        p.cls = cls;
+        p.a = get();
+        p.b = get();
+        cudaEventRecord(p.a, s);
+        open_[s] = p;
+    }
+    void end(int cls, cudaStream_t s) override {
+        std::lock_guard<std::mutex> lk(mu_);
+        auto it = open_.find(s);
+        if (it == open_.end()) return;
+        cudaEventRecord(it->second.b, s);
+        pending_.push_back(it->second);
+        open_.erase(it);
+    }
+    void collect(double *ms, int64_t *cnt, int n, bool reset) {
+        std::lock_guard<std::mutex> lk(mu_);
+        for (auto &p : pending_) {
+            float t = 0.f;
+            cudaEventSynchronize(p.b);
+            cudaEventElapsedTime(&t, p.a, p.b);
+            tot_[p.cls] += t;
+            num_[p.cls] += 1;
+            pool_.push_back(p.a);
+            pool_.push_back(p.b);
+        }
+        pending_.clear();
+        for (int c = 0; c < n && c < KC_COUNT; ++c) {
+            if (ms) ms[c] = tot_[c];
+            if (cnt) cnt[c] = num_[c];
+        }
+        if (reset)
+            for (int c = 0; c < KC_COUNT; ++c) tot_[c] = 0.0, num_[c] = 0;
+    }
+
+  private:
+    struct Pending {
+        int cls;
+        cudaEvent_t a, b;
+    };
+    cudaEvent_t get() {
+        if (!pool_.empty()) {
+            cudaEvent_t e = pool_.back();
+            pool_.pop_back();
+            return e;
+        }
+        cudaEvent_t e;
+        cudaEventCreate(&e);
+        return e;
+    }
+    std::mutex mu_;
+    std::vector<cudaEvent_t> pool_;
+    std::vector<Pending> pending_;
+    std::map<cudaStream_t, Pending> open_;
+    double tot_[KC_COUNT] = {};
+    int64_t num_[KC_COUNT] = {};
+};
+EventTimer g_timer;
+}  // namespace
+
+extern "C" plk_status plk_kernel_timing(double *total_ms, int64_t *launches, int32_t n_classes,
+                                        int32_t reset, int32_t *n_defined) {
+    if (n_classes < 0) return fail(PLK_E_INVALID, "n_classes < 0");
+    g_timer.collect(total_ms, launches, n_classes, reset != 0);
+    if (n_defined) *n_defined = KC_COUNT;
+    return PLK_OK;
+}
+
+extern "C" const char *plk_kernel_class_name(int32_t c) { return kernel_class_name(c); }
+
 // Enqueue the whole evaluation on `s` given a laid-out workspace.
-static plk_status run_eval(const plk_eval_args *a, int reml, const Layout &L, void *ws,
+static plk_status run_eval(const plk_eval_args *a, int reml, int flags, const Layout &L, void *ws,
                            cudaStream_t s) {
+    KernelTimer *timer = (flags & PLK_FLAG_KERNEL_TIMING) ? &g_timer : nullptr;
     cudaError_t e = launch_boxcox(a->n, L.n_pad, a->p, a->M, a->y, a->X, a->lambdas,
-                                  at<double>(ws, L.off_Bt), at<double>(ws, L.off_sumlog), s);
+                                  at<double>(ws, L.off_Bt), at<double>(ws, L.off_sumlog), s, timer);
     if (e != cudaSuccess) return cuda_fail(e, "boxcox launch");
     for (int64_t k0 = 0; k0 < a->K; k0 += L.batch) {
         BatchArgs b;
@@ -164,6 +243,7 @@ static plk_status run_eval(const plk_eval_args *a, int reml, const Layout &L, vo
         b.beta = a->beta;
         b.logdet = a->logdet;
         b.status = a->status;
+        b.timer = timer;
         e = launch_fp64_batch(b, s);
         if (e != cudaSuccess) return cuda_fail(e, "batch launch");
     }
@@ -197,7 +277,8 @@ extern "C" plk_status plk_eval_device(const plk_eval_args *args, const plk_optio
     if (reinterpret_cast<uintptr_t>(workspace) % ALIGN != 0)
         return fail(PLK_E_INVALID, "workspace must be 256-byte aligned");
     if (args->K == 0) return PLK_OK;
-    return run_eval(args, opts ? opts->reml : 0, L, workspace, static_cast<cudaStream_t>(stream));
+    return run_eval(args, opts ? opts->reml : 0, opts ? opts->flags : 0, L, workspace,
+                    static_cast<cudaStream_t>(stream));
 }
 
 // ---------------------------------------------------------------------------

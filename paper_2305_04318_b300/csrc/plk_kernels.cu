@@ -584,13 +584,27 @@ __global__ void k_profile_ci(const double *__restrict__ grid, const double *__re
 // ---------------------------------------------------------------------------
 // Host launchers
 // ---------------------------------------------------------------------------
+const char *kernel_class_name(int c) {
+    static const char *names[KC_COUNT] = {"boxcox", "omega_prep", "matern_table", "build", "potrf",
+                                          "panel_trsm", "trailing_gemm", "finalize", "profile"};
+    return (c >= 0 && c < KC_COUNT) ? names[c] : "";
+}
+
+#define TIMED(cls, launch)                  \
+    do {                                    \
+        if (timer) timer->begin(cls, s);    \
+        launch;                             \
+        if (timer) timer->end(cls, s);      \
+    } while (0)
+
 cudaError_t launch_boxcox(int64_t n, int64_t n_pad, int p, int M, const double *y, const double *X,
-                          const double *lam, double *Bt, double *sumlogy, cudaStream_t s) {
+                          const double *lam, double *Bt, double *sumlogy, cudaStream_t s,
+                          KernelTimer *timer) {
     const int64_t total = (int64_t)(M + p) * n_pad;
     int blocks = (int)((total + 255) / 256);
     if (blocks > 4096) blocks = 4096;
-    k_boxcox_rows<<<blocks, 256, 0, s>>>(n, n_pad, p, M, y, X, lam, Bt);
-    k_sumlog<<<1, 1024, 0, s>>>(n, y, sumlogy);
+    TIMED(KC_BOXCOX, (k_boxcox_rows<<<blocks, 256, 0, s>>>(n, n_pad, p, M, y, X, lam, Bt),
+                      k_sumlog<<<1, 1024, 0, s>>>(n, y, sumlogy)));
     return cudaGetLastError();
 }
 
@@ -600,21 +614,22 @@ cudaError_t launch_fp64_batch(const BatchArgs &b, cudaStream_t s) {
                                          (int)(2 * PK * sizeof(double)));
     if (e != cudaSuccess) return e;
     const int cnt = b.count;
-    k_omega_prep<<<cnt, 256, 0, s>>>(b.params, b.n, b.n_pad, b.coords, b.oconst, b.coordT, b.ldv,
-                                     b.pstatus);
-    k_matern_table<<<dim3((TAB_NBUCKET + 31) / 32, cnt), 320, 0, s>>>(b.oconst, b.tab);
-    k_build<<<dim3((unsigned)b.tpo, cnt), 256, 0, s>>>(b.nb, b.n, b.n_pad, b.q, b.tpo, b.tiles,
-                                                       b.oconst, b.coordT, b.tab, b.Bt);
+    KernelTimer *timer = b.timer;
+    TIMED(KC_PREP, (k_omega_prep<<<cnt, 256, 0, s>>>(b.params, b.n, b.n_pad, b.coords, b.oconst,
+                                                      b.coordT, b.ldv, b.pstatus)));
+    TIMED(KC_TABLE, (k_matern_table<<<dim3((TAB_NBUCKET + 31) / 32, cnt), 320, 0, s>>>(b.oconst, b.tab)));
+    TIMED(KC_BUILD, (k_build<<<dim3((unsigned)b.tpo, cnt), 256, 0, s>>>(
+                        b.nb, b.n, b.n_pad, b.q, b.tpo, b.tiles, b.oconst, b.coordT, b.tab, b.Bt)));
     for (int J = 0; J < b.nb; ++J) {
-        k_potrf<<<cnt, 256, 2 * PK * sizeof(double), s>>>(J, b.tpo, b.tiles, b.inv, b.ldv,
-                                                           b.pstatus);
+        TIMED(KC_POTRF, (k_potrf<<<cnt, 256, 2 * PK * sizeof(double), s>>>(J, b.tpo, b.tiles, b.inv,
+                                                                            b.ldv, b.pstatus)));
         const int m = b.nb - J;   // tile rows below the diagonal, RHS row included
-        k_gemm_nt<0><<<dim3(m, cnt), 256, 0, s>>>(J, b.tpo, b.tiles, b.inv);
-        k_gemm_nt<1><<<dim3(m * (m + 1) / 2, cnt), 256, 0, s>>>(J, b.tpo, b.tiles, b.inv);
+        TIMED(KC_TRSM, (k_gemm_nt<0><<<dim3(m, cnt), 256, 0, s>>>(J, b.tpo, b.tiles, b.inv)));
+        TIMED(KC_GEMM, (k_gemm_nt<1><<<dim3(m * (m + 1) / 2, cnt), 256, 0, s>>>(J, b.tpo, b.tiles, b.inv)));
     }
-    k_finalize<<<(cnt + 63) / 64, 64, 0, s>>>(cnt, b.k0, b.M, b.p, b.n, b.nb, b.reml, b.tpo,
-                                              b.tiles, b.ldv, b.pstatus, b.sumlogy, b.lambdas,
-                                              b.logL, b.sigma2, b.beta, b.logdet, b.status);
+    TIMED(KC_FINAL, (k_finalize<<<(cnt + 63) / 64, 64, 0, s>>>(
+                        cnt, b.k0, b.M, b.p, b.n, b.nb, b.reml, b.tpo, b.tiles, b.ldv, b.pstatus,
+                        b.sumlogy, b.lambdas, b.logL, b.sigma2, b.beta, b.logdet, b.status)));
     return cudaGetLastError();
 }
 

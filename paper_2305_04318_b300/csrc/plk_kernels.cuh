@@ -5,6 +5,18 @@
 
 namespace plk {
 
+// Kernel classes for the optional per-launch event timing.
+enum KernelClass { KC_BOXCOX = 0, KC_PREP, KC_TABLE, KC_BUILD, KC_POTRF, KC_TRSM, KC_GEMM, KC_FINAL,
+                   KC_PROFILE, KC_COUNT };
+const char *kernel_class_name(int c);
+
+// Records a CUDA event pair around a launch on its stream (see plk_api.cu).
+struct KernelTimer {
+    virtual void begin(int cls, cudaStream_t s) = 0;
+    virtual void end(int cls, cudaStream_t s) = 0;
+    virtual ~KernelTimer() {}
+};
+
 // One batch of `count` parameter points of one dataset.  Per-point arrays
 // (oconst, coordT, tab, tiles, inv, ldv, pstatus) are indexed by the point's
 // position w in the batch; outputs by its global index k0 + w.
@@ -28,10 +40,12 @@ struct BatchArgs {
     int *pstatus;            // count
     double *logL, *sigma2, *beta, *logdet;
     int32_t *status;
+    KernelTimer *timer = nullptr;
 };
 
 cudaError_t launch_boxcox(int64_t n, int64_t n_pad, int p, int M, const double *y, const double *X,
-                          const double *lam, double *Bt, double *sumlogy, cudaStream_t s);
+                          const double *lam, double *Bt, double *sumlogy, cudaStream_t s,
+                          KernelTimer *timer = nullptr);
 cudaError_t launch_fp64_batch(const BatchArgs &b, cudaStream_t s);
 cudaError_t launch_profile_max(const double *vals, int64_t G, int64_t SM, double *prof,
                                cudaStream_t s);

@@ -36,7 +36,7 @@ class EvalArgs(C.Structure):
 
 
 class Options(C.Structure):
-    _fields_ = [("precision", C.c_int32), ("reml", C.c_int32), ("batch", C.c_int32), ("reserved", C.c_int32)]
+    _fields_ = [("precision", C.c_int32), ("reml", C.c_int32), ("batch", C.c_int32), ("flags", C.c_int32)]
 
 
 _lib = None
@@ -71,6 +71,8 @@ def lib():
         "plk_profile_max_device": (C.c_int, [vp, i64, i64, vp, vp]),
         "plk_profile_ci_device": (C.c_int, [vp, vp, i64, dbl, vp, vp]),
         "plk_chi2_1_quantile": (dbl, [dbl]),
+        "plk_kernel_timing": (C.c_int, [C.POINTER(dbl), C.POINTER(i64), i32, i32, C.POINTER(i32)]),
+        "plk_kernel_class_name": (C.c_char_p, [i32]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -110,8 +112,21 @@ def default_batch(n, K, limit_bytes=8e9):
     return int(max(1, min(296, limit_bytes // per, max(K, 1))))
 
 
+FLAG_KERNEL_TIMING = 1
+
+
+def kernel_timing(reset=True):
+    """{class name: (total ms, launches)} of launches made with FLAG_KERNEL_TIMING."""
+    n = 32
+    ms = (C.c_double * n)()
+    cnt = (C.c_int64 * n)()
+    nd = C.c_int32()
+    _check(lib().plk_kernel_timing(ms, cnt, n, int(bool(reset)), C.byref(nd)))
+    return {lib().plk_kernel_class_name(c).decode(): (ms[c], cnt[c]) for c in range(nd.value)}
+
+
 def eval_device(coords, y, X, lambdas, params, precision=FP64, reml=False, batch=0,
-                workspace=None, stream=None, outputs=None):
+                workspace=None, stream=None, outputs=None, flags=0):
     """Evaluate l_p at all rows of `params` (torch CUDA float64 tensors).
 
     Returns a dict of CUDA tensors logL[K,M], sigma2[K,M], beta[K,M,p],
@@ -141,7 +156,7 @@ def eval_device(coords, y, X, lambdas, params, precision=FP64, reml=False, batch
     a = EvalArgs(n, p, M, _ptr(coords), _ptr(y), _ptr(X), _ptr(lambdas), K, _ptr(params),
                  _ptr(outputs.get("logL")), _ptr(outputs.get("sigma2")), _ptr(outputs.get("beta")),
                  _ptr(outputs.get("logdet")), _ptr(outputs.get("status")))
-    o = Options(precision, int(bool(reml)), batch, 0)
+    o = Options(precision, int(bool(reml)), batch, int(flags))
     _check(lib().plk_eval_device(C.byref(a), C.byref(o), _ptr(workspace), workspace.numel(),
                                  _stream_handle(stream)))
     return outputs
