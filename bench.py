@@ -1,0 +1,359 @@
+#!/usr/bin/env python
+"""Benchmark of the profile-likelihood hot path on B300.
+
+Metric: profile log-likelihood evaluations per second at n = 4000 (one
+evaluation = one correlation-parameter point omega, its n x n Matern matrix
+built, factored and solved against 9 Box-Cox columns + 3 covariates, giving
+l_p at all 9 lambdas), with p50/p99 latency of end-to-end steps.
+
+Workload ("mixed4000"): n = 4000 sites uniform on [0,20]^2, p = 3, M = 9
+lambdas in [-0.5, 1.5], K = 1024 omega (960 Halton points of the parameter box
++ 64 ill-conditioned points).  A step is one batch of `--batch` points of that
+grid (cycling through it) through the whole path: Box-Cox rows, build,
+blocked Cholesky with the bordered right-hand side, closed form.  Inputs are
+synthetic (paper_2305_04318_b300.synth), resident in HBM when the timed region
+starts; each step's tile workspace is several GB, far larger than L2.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|mixed]
+  python bench.py --impl reference      # the FP64 CPU oracle on the host cores
+
+Under torchrun (N > 1) every rank evaluates its own slice of points (weak
+scaling, no data-path collective); the step time is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "profile-logL evals/s at n=4000 (FP64 vs mixed, |ΔlogL|≤1e-3); p50/p99 latency"
+UNIT = "evals/s"
+WORKLOAD = ("mixed4000: n=4000 sites on [0,20]^2, p=3, M=9 lambdas in [-0.5,1.5], "
+            "K=1024 omega (960 Halton + 64 ill-conditioned), anisotropic Matern")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="auto", choices=["auto", "fp64", "mixed"])
+    ap.add_argument("--batch", type=int, default=0, help="omega points per step (default: 128 fp64, 512 mixed)")
+    ap.add_argument("--n", type=int, default=4000)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample", type=int, default=0, help="oracle points in the CPU sample (default: cores)")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# helpers
+# ---------------------------------------------------------------------------
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank_gpu{index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        return json.load(open(path))
+    except Exception:
+        return {}
+
+
+def probe_fp64_peak():
+    """Live FP64 FMA-pipe throughput (TFLOP/s) on this GPU."""
+    import ctypes as C
+    from paper_2305_04318_b300 import build
+    L = C.CDLL(build.build_probe())
+    L.plk_probe_fp64_fma_tflops.restype = C.c_double
+    L.plk_probe_fp32_fma_tflops.restype = C.c_double
+    return L.plk_probe_fp64_fma_tflops(5), L.plk_probe_fp32_fma_tflops(5)
+
+
+def trailing_flops(n, q, TB=128):
+    """Algorithmic flops of the trailing updates, per omega, per step J of the
+    blocked factorisation: the rank-TB update of the lower triangle of the true
+    (unpadded) r x r trailing matrix (TB r^2) plus the q right-hand-side rows
+    (2 TB q r).  Summed over J this is n^3/3 + n^2 q to leading order."""
+    nb = -(-n // TB)
+    out = []
+    for J in range(nb):
+        r = max(0, n - (J + 1) * TB)
+        out.append(TB * r * r + 2 * TB * q * r)
+    return out
+
+
+def cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the FP64 CPU oracle
+# ---------------------------------------------------------------------------
+
+def oracle_rate(ds, P, lambdas, npts, threads):
+    import oracle
+    t0 = time.perf_counter()
+    r = oracle.profile_batch(ds.coords, ds.y, ds.X, P[:npts], lambdas, nthreads=threads)
+    dt = time.perf_counter() - t0
+    return npts / dt, dt, r["threads"]
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    from paper_2305_04318_b300 import synth
+    w = synth.mixed4000(n=args.n)
+    ds, P, lam = w.datasets[0], w.params[0], w.lambdas
+    cores = cpu_cores()
+    npts = args.cpu_sample or cores
+    for s in range(args.warmup):   # untimed warm-up steps (same sample size)
+        idx = (np.arange(npts) + (args.steps + s) * npts) % P.shape[0]
+        oracle_rate(ds, P[idx], lam, npts, cores)
+    rates, times = [], []
+    for s in range(args.steps):
+        idx = (np.arange(npts) + s * npts) % P.shape[0]
+        r, dt, used = oracle_rate(ds, P[idx], lam, npts, cores)
+        rates.append(r)
+        times.append(dt)
+    value = npts * len(times) / sum(times)
+    sample = f"{npts} omega points per step of the n=4000 workload, one per thread"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "precision": "fp64", "device": "cpu"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    import torch.distributed as dist
+    from paper_2305_04318_b300 import native as nv, synth
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(x):
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    prec = args.precision
+    if prec == "auto":
+        prec = "fp64"
+    precision = nv.FP64 if prec == "fp64" else nv.MIXED
+    B = args.batch or (128 if prec == "fp64" else 512)
+
+    w = synth.mixed4000(n=args.n)
+    ds, P, lam = w.datasets[0], w.params[0], w.lambdas
+    K = P.shape[0]
+    n, p, M = ds.n, ds.p, len(lam)
+    q = M + p
+    dev = torch.device("cuda", local)
+    T = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64), device=dev)
+    coords, y, X, lamd, Pd = T(ds.coords), T(ds.y), T(ds.X), T(lam), T(P)
+    stream = torch.cuda.current_stream()
+    wsb = nv.workspace_bytes(n, p, M, B, precision)
+    workspace = torch.empty((wsb,), dtype=torch.uint8, device=dev)
+    outs = dict(logL=torch.empty((B, M), dtype=torch.float64, device=dev),
+                sigma2=torch.empty((B, M), dtype=torch.float64, device=dev),
+                beta=torch.empty((B, M, p), dtype=torch.float64, device=dev),
+                logdet=torch.empty((B, 2), dtype=torch.float64, device=dev),
+                status=torch.empty((B,), dtype=torch.int32, device=dev))
+
+    def step_params(s):
+        # rank r evaluates its own slice: points (s * world + r) * B ... cycling through the grid
+        start = ((s * world + rank) * B) % K
+        idx = (torch.arange(B, device=dev) + start) % K
+        return Pd.index_select(0, idx).contiguous()
+
+    batches = [step_params(s) for s in range(args.warmup + args.steps)]
+
+    def one_step(s, flags=0):
+        nv.eval_device(coords, y, X, lamd, batches[s], precision=precision, batch=B, workspace=workspace,
+                       stream=stream, outputs=outs, flags=flags)
+
+    for s in range(args.warmup):
+        one_step(s)
+    barrier()
+    nv.kernel_timing(reset=True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    barrier()
+    e0.record(stream)
+    for s in range(args.warmup, args.warmup + args.steps):
+        one_step(s, flags=nv.FLAG_KERNEL_TIMING)
+    e1.record(stream)
+    barrier()
+    clk = clocks.stop()
+    ms_total = max_over_ranks(e0.elapsed_time(e1))
+    timing = nv.kernel_timing(reset=True)
+    ms_per_step = ms_total / args.steps
+    value = world * B * args.steps / (ms_total * 1e-3)
+    st = outs["status"].cpu().numpy()
+
+    # dominant kernel and its roofline
+    dom = max(timing, key=lambda k: timing[k][0])
+    dom_ms, dom_launches = timing[dom]
+    launches = int(sum(c for _, c in timing.values()))
+    roof = None
+    fp64_peak, fp32_peak = probe_fp64_peak()
+    if dom == "trailing_gemm":
+        flops = sum(trailing_flops(n, q)) * B * args.steps
+        achieved = flops / (dom_ms * 1e-3) / 1e12
+        if prec == "fp64":
+            roof = {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
+                    "frac": achieved / fp64_peak, "traffic": None, "kernel": "k_gemm_nt<1> (trailing update)",
+                    "peak_source": "FP64 FMA pipe measured live by libplk_probe (no FP64 figure in MEASURED_PEAKS.json)"}
+    kernel_share = {k: round(v[0] / max(1e-9, sum(x[0] for x in timing.values())), 4) for k, v in timing.items() if v[1]}
+
+    # ---- end to end through the C ABI with host buffers ----
+    e2e = None
+    lat = None
+    if not args.no_e2e:
+        arena = torch.empty((wsb + (256 << 20),), dtype=torch.uint8, device=dev)
+        ctx = nv.Context(arena.numel(), device=local, arena=arena, n_streams=1)
+        hostP = [np.ascontiguousarray(batches[s].cpu().numpy()) for s in range(len(batches))]
+        def e2e_step(s):
+            t0 = time.perf_counter()
+            did = ctx.create_dataset(ds.coords, ds.y, ds.X)
+            job = ctx.submit(did, hostP[s], lam, precision=precision, batch=B)
+            r = ctx.poll(job, p)
+            ctx.release_dataset(did)
+            return time.perf_counter() - t0, r
+        for s in range(args.warmup):
+            e2e_step(s)
+        barrier()
+        times = []
+        for s in range(args.warmup, args.warmup + args.steps):
+            dt, r = e2e_step(s)
+            times.append(dt)
+        tot = max_over_ranks(sum(times))
+        ctx.close()
+        h2d = ds.coords.nbytes + ds.y.nbytes + ds.X.nbytes + hostP[0].nbytes + lam.nbytes
+        d2h = r["logL"].nbytes + r["sigma2"].nbytes + r["beta"].nbytes + r["logdet"].nbytes + r["status"].nbytes
+        e2e = {"value": world * B * args.steps / tot, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h)}
+        lat = {"p50": 1e3 * float(np.percentile(times, 50)), "p99": 1e3 * float(np.percentile(times, 99)),
+               "what": f"end-to-end step latency (host inputs -> host results) of a {B}-point job"}
+
+    # ---- CPU baseline (oracle on the host cores), rank 0 at N = 1 only ----
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cores = cpu_cores()
+        npts = args.cpu_sample or cores
+        r, dt, used = oracle_rate(ds, P, lam, npts, cores)
+        cpu = {"value": r, "unit": UNIT, "cores": used, "kind": "oracle",
+               "sample": f"first {npts} omega points of the n=4000 workload ({dt:.1f} s wall, one point per thread)"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "precision": prec, "batch_per_step": B, "n": n, "p": p, "M": M,
+                           "l2": f"inputs larger than L2: {wsb / 1e9:.1f} GB tile workspace per step",
+                           "parallelism": f"omega-sharded x{world}"},
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "latency_ms": lat,
+                "gpu_launches": launches, "kernel_ms": {k: round(v[0], 3) for k, v in timing.items() if v[1]},
+                "kernel_share": kernel_share, "clocks": clk,
+                "fp64_fma_peak_tflops": fp64_peak, "fp32_fma_peak_tflops": fp32_peak,
+                "points_not_ok_last_step": int((st != 0).sum())}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -15,6 +15,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libplk.so")
+PROBE_SRC = os.path.join(HERE, "csrc_probe", "peak_probe.cu")
+PROBE_LIB = os.path.join(HERE, "libplk_probe.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -33,7 +35,19 @@ def up_to_date() -> bool:
     return all(os.path.getmtime(f) <= t for f in _deps())
 
 
+def build_probe(force: bool = False) -> str:
+    """libplk_probe.so: FMA-pipe throughput probe used by the benchmark."""
+    if not force and os.path.exists(PROBE_LIB) and os.path.getmtime(PROBE_LIB) >= os.path.getmtime(PROBE_SRC):
+        return PROBE_LIB
+    tmp = PROBE_LIB + f".tmp{os.getpid()}"
+    subprocess.run([os.environ.get("NVCC", "nvcc"), *ARCH, "-O3", "-shared", "-Xcompiler", "-fPIC",
+                    "-o", tmp, PROBE_SRC], check=True)
+    os.replace(tmp, PROBE_LIB)
+    return PROBE_LIB
+
+
 def build(force: bool = False, verbose: bool = False) -> str:
+    build_probe(force)
     if not force and up_to_date():
         return LIB
     nvcc = os.environ.get("NVCC", "nvcc")
