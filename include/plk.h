@@ -119,6 +119,33 @@ size_t plk_eval_workspace_bytes(int64_t n, int32_t p, int32_t M, int32_t batch,
 plk_status plk_eval_device(const plk_eval_args *args, const plk_options *opts, void *workspace,
                            size_t workspace_bytes, void *stream);
 
+/* Evaluation without any device allocation (the paper has no counterpart).
+ *
+ * For callers that cannot allocate device memory when they evaluate -- for
+ * example a plugin whose host application owns the entire device-memory
+ * budget, or a latency-critical loop that must not call cudaMalloc/cudaFree
+ * because those calls can stall or synchronize other work on the device.
+ * Same computation and outputs as plk_eval_device in PLK_FP64 (ML if reml == 0,
+ * REML otherwise); the scratch it needs lives in one device array of
+ * PLK_STATIC_SCRATCH_BYTES inside the library, which every GPU that loads the
+ * library holds until the process exits.  The caller passes inputs and outputs
+ * (device pointers, as for plk_eval_device) and a stream.
+ *   - The first call on a device looks up the array's device address (once per
+ *     device, with that device current); make that first call before any
+ *     stream capture.
+ *   - Every call on a device shares the same array.  Calls that overlap on the
+ *     GPU (other streams, other host threads) race on it and give wrong
+ *     results; serialize them.  Nothing needs to start at zero: each call
+ *     writes every scratch byte before it reads it, so contents left by the
+ *     previous call do not matter.
+ *   - Points are processed in batches as large as fit in the array.  Sizes for
+ *     which even one point does not fit (n above about 3840) are rejected with
+ *     PLK_E_NOMEM before any work is queued; use plk_eval_device then.
+ *   - Allocates nothing and calls no allocating routine.  Asynchronous on
+ *     `stream` like plk_eval_device. */
+#define PLK_STATIC_SCRATCH_BYTES ((size_t)64 << 20)
+plk_status plk_eval_device_static(const plk_eval_args *args, int32_t reml, void *stream);
+
 /* ------------------------------------------------------------------------ */
 /* Context API: device-resident datasets, asynchronous jobs                  */
 /* ------------------------------------------------------------------------ */

@@ -53,6 +53,8 @@ static plk_status cuda_fail(cudaError_t e, const char *where) {
 
 extern "C" const char *plk_last_error(void) { return g_err.c_str(); }
 
+void plk::set_last_error(const char *msg) { g_err = msg ? msg : ""; }
+
 // ---------------------------------------------------------------------------
 // workspace layout
 // ---------------------------------------------------------------------------

@@ -43,6 +43,9 @@ struct BatchArgs {
     KernelTimer *timer = nullptr;
 };
 
+// Sets the calling thread's message returned by plk_last_error().
+void set_last_error(const char *msg);
+
 cudaError_t launch_boxcox(int64_t n, int64_t n_pad, int p, int M, const double *y, const double *X,
                           const double *lam, double *Bt, double *sumlogy, cudaStream_t s,
                           KernelTimer *timer = nullptr);

@@ -60,6 +60,7 @@ def lib():
     sig = {
         "plk_eval_workspace_bytes": (sz, [i64, i32, i32, i32, i32]),
         "plk_eval_device": (C.c_int, [C.POINTER(EvalArgs), C.POINTER(Options), vp, sz, vp]),
+        "plk_eval_device_static": (C.c_int, [C.POINTER(EvalArgs), i32, vp]),
         "plk_create": (C.c_int, [C.POINTER(vp), C.c_int, vp, sz, C.POINTER(vp), C.c_int]),
         "plk_create_dataset": (C.c_int, [vp, vp, vp, vp, i64, i32, C.POINTER(i64)]),
         "plk_submit_profile": (C.c_int, [vp, i64, vp, i64, vp, i32, C.POINTER(Options), C.POINTER(i64)]),
@@ -159,6 +160,31 @@ def eval_device(coords, y, X, lambdas, params, precision=FP64, reml=False, batch
     o = Options(precision, int(bool(reml)), batch, int(flags))
     _check(lib().plk_eval_device(C.byref(a), C.byref(o), _ptr(workspace), workspace.numel(),
                                  _stream_handle(stream)))
+    return outputs
+
+
+STATIC_SCRATCH_BYTES = 64 << 20
+
+
+def eval_device_static(coords, y, X, lambdas, params, reml=False, stream=None, outputs=None):
+    """FP64 evaluation through plk_eval_device_static: the library uses its own
+    fixed device scratch array, so this call allocates no device memory beyond
+    the output tensors (pass `outputs` to allocate none at all)."""
+    import torch
+    dev = coords.device
+    n, p = X.shape
+    M = lambdas.shape[0]
+    K = params.shape[0]
+    if outputs is None:
+        outputs = dict(logL=torch.empty((K, M), dtype=torch.float64, device=dev),
+                       sigma2=torch.empty((K, M), dtype=torch.float64, device=dev),
+                       beta=torch.empty((K, M, p), dtype=torch.float64, device=dev),
+                       logdet=torch.empty((K, 2), dtype=torch.float64, device=dev),
+                       status=torch.empty((K,), dtype=torch.int32, device=dev))
+    a = EvalArgs(n, p, M, _ptr(coords), _ptr(y), _ptr(X), _ptr(lambdas), K, _ptr(params),
+                 _ptr(outputs.get("logL")), _ptr(outputs.get("sigma2")), _ptr(outputs.get("beta")),
+                 _ptr(outputs.get("logdet")), _ptr(outputs.get("status")))
+    _check(lib().plk_eval_device_static(C.byref(a), int(bool(reml)), _stream_handle(stream)))
     return outputs
 
 
