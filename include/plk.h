@@ -62,7 +62,8 @@ typedef enum {
 #define PLK_POINT_NOT_PD 1       /* V (or X'V^-1X) not positive definite in the working precision */
 #define PLK_POINT_BAD_PARAM 2    /* parameter row outside its domain (phi_X<=0, kappa<=0, ...) */
 #define PLK_POINT_RSS_NONPOS 3   /* residual sum of squares <= 0 */
-#define PLK_POINT_FP64_RETRY 16  /* flag bit: mixed mode re-evaluated this point in FP64 */
+#define PLK_POINT_RETRIED 16     /* flag bit: mixed mode re-evaluated this point with the 7-slice
+                                    (~48-bit) split because the 5-slice error bound was too large */
 
 typedef enum {
     PLK_FP64 = 0,  /* every step in FP64 arithmetic */
@@ -80,6 +81,9 @@ typedef struct {
 /* flags: bracket every kernel launch with CUDA events on its stream and
  * accumulate the elapsed time per kernel class (read with plk_kernel_timing). */
 #define PLK_FLAG_KERNEL_TIMING 1
+/* flags: PLK_MIXED without the 7-slice re-evaluation of points whose error bound
+ * exceeds the tolerance (for measuring the 5-slice error itself). */
+#define PLK_FLAG_NO_RETRY 2
 
 /* ------------------------------------------------------------------------ */
 /* Stateless device-pointer evaluation (one dataset, K points)               */
@@ -101,6 +105,8 @@ typedef struct {
     double *beta;            /* K x M x p beta-hat */
     double *logdet;          /* K x 2  [log|V|, log|X'V^-1X|] */
     int32_t *status;         /* K      PLK_POINT_* codes */
+    double *err_bound;       /* K      PLK_MIXED: a-posteriori bound on the log-likelihood error of
+                                       the split-product factorisation; PLK_FP64: 0 */
 } plk_eval_args;
 
 /* Bytes of device workspace plk_eval_device needs to process `batch` points of

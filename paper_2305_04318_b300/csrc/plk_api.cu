@@ -69,14 +69,19 @@ struct Layout {
     int64_t tpo = 0;
     size_t off_Bt = 0, off_sumlog = 0, off_oc = 0, off_coordT = 0, off_tab = 0, off_tiles = 0,
            off_inv = 0, off_ldv = 0, off_pst = 0, total = 0;
+    // mixed precision only
+    bool mixed = false;
+    size_t img = 0, off_wimg = 0, off_pimg = 0, off_invsum = 0, off_flags = 0, off_idx = 0,
+           off_cparams = 0, off_err = 0;
 };
 
 bool sizes_ok(int64_t n, int32_t p, int32_t M) {
     return n > 0 && p >= 1 && p <= 16 && M >= 1 && M + p <= 64 && n > p;
 }
 
-bool make_layout(int64_t n, int32_t p, int32_t M, int32_t batch, Layout &L) {
+bool make_layout(int64_t n, int32_t p, int32_t M, int32_t batch, Layout &L, int precision = PLK_FP64) {
     if (!sizes_ok(n, p, M) || batch < 1) return false;
+    if (precision != PLK_FP64 && precision != PLK_MIXED) return false;
     L.n = n;
     L.p = p;
     L.M = M;
@@ -100,6 +105,17 @@ bool make_layout(int64_t n, int32_t p, int32_t M, int32_t batch, Layout &L) {
     L.off_inv = take(sizeof(double) * (size_t)NT * batch);
     L.off_ldv = take(sizeof(double) * (size_t)batch);
     L.off_pst = take(sizeof(int) * (size_t)batch);
+    if (precision == PLK_MIXED) {
+        L.mixed = true;
+        L.img = align_up(mixed_img_bytes(7));   // sized for the 7-slice pass, used by both
+        L.off_wimg = take(L.img * batch);
+        L.off_pimg = take(L.img * (size_t)(L.nb + 1) * batch);
+        L.off_invsum = take(sizeof(double) * (size_t)batch);
+        L.off_flags = take(sizeof(int) * (size_t)batch);
+        L.off_idx = take(sizeof(int) * (size_t)batch);
+        L.off_cparams = take(sizeof(double) * 5 * (size_t)batch);
+        L.off_err = take(sizeof(int));
+    }
     L.total = off;
     return true;
 }
@@ -126,8 +142,7 @@ T *at(void *base, size_t off) {
 extern "C" size_t plk_eval_workspace_bytes(int64_t n, int32_t p, int32_t M, int32_t batch,
                                            int32_t precision) {
     Layout L;
-    if (precision != PLK_FP64 && precision != PLK_MIXED) return 0;
-    if (!make_layout(n, p, M, batch, L)) return 0;
+    if (!make_layout(n, p, M, batch, L, precision)) return 0;
     return L.total;
 }
 
@@ -209,6 +224,54 @@ extern "C" plk_status plk_kernel_timing(double *total_ms, int64_t *launches, int
 
 extern "C" const char *plk_kernel_class_name(int32_t c) { return kernel_class_name(c); }
 
+// Mixed precision: 5-slice pass over the batch, then (unless PLK_FLAG_NO_RETRY)
+// a 7-slice pass over the points whose error bound exceeded the tolerance or
+// whose factorisation failed.  Deciding the retry set reads the flags back, so
+// this synchronizes the stream once per batch.
+static const double kMixedTol = 1e-4;   // bound on |Delta log L| that triggers the retry
+
+static plk_status run_mixed_batch(BatchArgs b, const Layout &L, void *ws, const double *params_all, int flags,
+                                  double *err_bound, cudaStream_t s) {
+    MixedArgs x;
+    x.wimg = at<uint8_t>(ws, L.off_wimg);
+    x.pimg = at<uint8_t>(ws, L.off_pimg);
+    x.invsum = at<double>(ws, L.off_invsum);
+    x.flags = at<int>(ws, L.off_flags);
+    x.err = at<int>(ws, L.off_err);
+    x.err_bound = err_bound;
+    x.tol = kMixedTol;
+    cudaError_t e = cudaMemsetAsync(x.err, 0, sizeof(int), s);
+    if (e == cudaSuccess) e = launch_mixed_batch(b, x, 5, s);
+    if (e != cudaSuccess) return cuda_fail(e, "mixed batch launch");
+    std::vector<int> hf(b.count + 1);
+    e = cudaMemcpyAsync(hf.data(), x.flags, sizeof(int) * b.count, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hf.data() + b.count, x.err, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "mixed batch");
+    if (hf[b.count]) return fail(PLK_E_TIMEOUT, "a tensor-core wait gave up (device error flag set)");
+    if (flags & PLK_FLAG_NO_RETRY) return PLK_OK;
+    std::vector<int> idx;
+    for (int w = 0; w < b.count; ++w)
+        if (hf[w]) idx.push_back((int)(b.k0 + w));
+    if (idx.empty()) return PLK_OK;
+    int *d_idx = at<int>(ws, L.off_idx);
+    double *d_par = at<double>(ws, L.off_cparams);
+    e = cudaMemcpyAsync(d_idx, idx.data(), sizeof(int) * idx.size(), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = launch_gather_params((int)idx.size(), d_idx, params_all, d_par, s);
+    if (e != cudaSuccess) return cuda_fail(e, "mixed retry gather");
+    BatchArgs r = b;
+    r.count = (int)idx.size();
+    r.params = d_par;
+    r.out_index = d_idx;
+    r.status_or = PLK_POINT_RETRIED;
+    e = launch_mixed_batch(r, x, 7, s);
+    if (e != cudaSuccess) return cuda_fail(e, "mixed retry launch");
+    // the host vector idx must outlive the copy: wait for it
+    e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "mixed retry");
+    return PLK_OK;
+}
+
 // Enqueue the whole evaluation on `s` given a laid-out workspace.
 static plk_status run_eval(const plk_eval_args *a, int reml, int flags, const Layout &L, void *ws,
                            cudaStream_t s) {
@@ -246,8 +309,17 @@ static plk_status run_eval(const plk_eval_args *a, int reml, int flags, const La
         b.logdet = a->logdet;
         b.status = a->status;
         b.timer = timer;
-        e = launch_fp64_batch(b, s);
-        if (e != cudaSuccess) return cuda_fail(e, "batch launch");
+        if (L.mixed) {
+            plk_status st = run_mixed_batch(b, L, ws, a->params, flags, a->err_bound, s);
+            if (st != PLK_OK) return st;
+        } else {
+            e = launch_fp64_batch(b, s);
+            if (e != cudaSuccess) return cuda_fail(e, "batch launch");
+        }
+    }
+    if (!L.mixed && a->err_bound) {
+        e = cudaMemsetAsync(a->err_bound, 0, sizeof(double) * a->K, s);
+        if (e != cudaSuccess) return cuda_fail(e, "err_bound");
     }
     return PLK_OK;
 }
@@ -269,10 +341,9 @@ extern "C" plk_status plk_eval_device(const plk_eval_args *args, const plk_optio
     if (st != PLK_OK) return st;
     const int prec = opts ? opts->precision : PLK_FP64;
     if (prec != PLK_FP64 && prec != PLK_MIXED) return fail(PLK_E_INVALID, "unknown precision %d", prec);
-    if (prec == PLK_MIXED) return fail(PLK_E_INVALID, "PLK_MIXED is not available in this build");
     int batch = (opts && opts->batch > 0) ? opts->batch : default_batch(args->n, args->K);
     Layout L;
-    make_layout(args->n, args->p, args->M, batch, L);
+    make_layout(args->n, args->p, args->M, batch, L, prec);
     if (!workspace || workspace_bytes < L.total)
         return fail(PLK_E_NOMEM, "workspace of %zu bytes < %zu needed for batch %d", workspace_bytes,
                     L.total, batch);
@@ -472,9 +543,9 @@ size_t job_io_bytes(int64_t K, int32_t M, int32_t p, int64_t n) {
 }
 
 // Per-batch workspace without the shared dataset part (B^T, sum log y live in the job).
-size_t item_bytes(int64_t n, int32_t p, int32_t M, int count) {
+size_t item_bytes(int64_t n, int32_t p, int32_t M, int count, int precision) {
     Layout L;
-    make_layout(n, p, M, count, L);
+    make_layout(n, p, M, count, L, precision);
     return L.total;
 }
 
@@ -516,7 +587,7 @@ bool start_job(plk_ctx *c, Job *j, cudaStream_t s) {
 
 void launch_item(plk_ctx *c, Job *j, Item &it, cudaStream_t s) {
     Layout L;
-    make_layout(j->n, j->p, j->M, it.count, L);
+    make_layout(j->n, j->p, j->M, it.count, L, j->opts.precision);
     Dataset *d = c->datasets[j->ds].get();
     BatchArgs b;
     b.count = it.count;
@@ -547,10 +618,19 @@ void launch_item(plk_ctx *c, Job *j, Item &it, cudaStream_t s) {
     b.logdet = j->d_ld;
     b.status = j->d_st;
     cudaStreamWaitEvent(s, j->ready, 0);   // the job's B^T may come from another stream
-    cudaError_t e = launch_fp64_batch(b, s);
-    if (e != cudaSuccess) {
-        j->failed = true;
-        j->error = cudaGetErrorString(e);
+    if (L.mixed) {
+        // synchronous on this stream (the retry set is decided on the host)
+        plk_status st = run_mixed_batch(b, L, it.ws, j->d_params, j->opts.flags, nullptr, s);
+        if (st != PLK_OK) {
+            j->failed = true;
+            j->error = plk_last_error();
+        }
+    } else {
+        cudaError_t e = launch_fp64_batch(b, s);
+        if (e != cudaSuccess) {
+            j->failed = true;
+            j->error = cudaGetErrorString(e);
+        }
     }
     cudaEventRecord(it.ev, s);
 }
@@ -637,7 +717,7 @@ void worker_main(plk_ctx *c) {
             }
             int count = (int)std::min<int64_t>(pick->batch, pick->K - pick->next_k);
             char *ws = nullptr;
-            while (count >= 1 && !(ws = c->arena.alloc(item_bytes(pick->n, pick->p, pick->M, count))))
+            while (count >= 1 && !(ws = c->arena.alloc(item_bytes(pick->n, pick->p, pick->M, count, pick->opts.precision))))
                 count /= 2;   // admission by arena bytes: shrink the batch until it fits
             if (!ws) break;   // wait for memory to free up
             Item it;
@@ -759,13 +839,12 @@ extern "C" plk_status plk_submit_profile(plk_ctx *c, plk_dataset ds, const doubl
     plk_options o{};
     if (opts) o = *opts;
     if (o.precision != PLK_FP64 && o.precision != PLK_MIXED) return fail(PLK_E_INVALID, "unknown precision");
-    if (o.precision == PLK_MIXED) return fail(PLK_E_INVALID, "PLK_MIXED is not available in this build");
     std::unique_lock<std::mutex> lk(c->mu);
     auto dit = c->datasets.find(ds);
     if (dit == c->datasets.end()) return fail(PLK_E_INVALID, "unknown dataset %lld", (long long)ds);
     Dataset *d = dit->second.get();
     if (M + d->p > 64) return fail(PLK_E_INVALID, "M + p must be <= 64");
-    const size_t need = job_io_bytes(K, M, d->p, d->n) + item_bytes(d->n, d->p, M, 1);
+    const size_t need = job_io_bytes(K, M, d->p, d->n) + item_bytes(d->n, d->p, M, 1, o.precision);
     if (need > c->arena.size())
         return fail(PLK_E_NOMEM, "job needs at least %zu bytes, arena is %zu", need, c->arena.size());
     auto j = std::make_unique<Job>();

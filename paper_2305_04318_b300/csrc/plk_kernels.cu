@@ -427,10 +427,10 @@ __global__ void k_finalize(int count, int64_t k0, int M, int p, int64_t n, int n
                            const double *__restrict__ ldv, const int *__restrict__ pstatus,
                            const double *__restrict__ sumlogy, const double *__restrict__ lambdas,
                            double *logL, double *sigma2, double *beta, double *logdet,
-                           int32_t *status) {
+                           int32_t *status, const int *__restrict__ out_index, int32_t status_or) {
     const int w = blockIdx.x * blockDim.x + threadIdx.x;
     if (w >= count) return;
-    const int64_t k = k0 + w;
+    const int64_t k = out_index ? (int64_t)out_index[w] : k0 + w;
     const double *S = tiles + ((int64_t)w * tpo + tile_index(nb, nb)) * NT;   // -B^T V^-1 B
     int st = pstatus[w];
     const double NaN = nan("");
@@ -505,7 +505,7 @@ __global__ void k_finalize(int count, int64_t k0, int M, int p, int64_t n, int n
         logdet[2 * k] = ld;
         logdet[2 * k + 1] = good ? ldx : NaN;
     }
-    if (status) status[k] = st;
+    if (status) status[k] = st | status_or;
 }
 
 // ---------------------------------------------------------------------------
@@ -586,7 +586,7 @@ __global__ void k_profile_ci(const double *__restrict__ grid, const double *__re
 // ---------------------------------------------------------------------------
 const char *kernel_class_name(int c) {
     static const char *names[KC_COUNT] = {"boxcox", "omega_prep", "matern_table", "build", "potrf",
-                                          "panel_trsm", "trailing_gemm", "finalize", "profile"};
+                                          "panel_trsm", "trailing_gemm", "finalize", "profile", "convert"};
     return (c >= 0 && c < KC_COUNT) ? names[c] : "";
 }
 
@@ -608,11 +608,7 @@ cudaError_t launch_boxcox(int64_t n, int64_t n_pad, int p, int M, const double *
     return cudaGetLastError();
 }
 
-cudaError_t launch_fp64_batch(const BatchArgs &b, cudaStream_t s) {
-    // per function and device; cheap to repeat
-    cudaError_t e = cudaFuncSetAttribute(k_potrf, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)(2 * PK * sizeof(double)));
-    if (e != cudaSuccess) return e;
+cudaError_t launch_front(const BatchArgs &b, cudaStream_t s) {
     const int cnt = b.count;
     KernelTimer *timer = b.timer;
     TIMED(KC_PREP, (k_omega_prep<<<cnt, 256, 0, s>>>(b.params, b.n, b.n_pad, b.coords, b.oconst,
@@ -620,6 +616,27 @@ cudaError_t launch_fp64_batch(const BatchArgs &b, cudaStream_t s) {
     TIMED(KC_TABLE, (k_matern_table<<<dim3((TAB_NBUCKET + 31) / 32, cnt), 320, 0, s>>>(b.oconst, b.tab)));
     TIMED(KC_BUILD, (k_build<<<dim3((unsigned)b.tpo, cnt), 256, 0, s>>>(
                         b.nb, b.n, b.n_pad, b.q, b.tpo, b.tiles, b.oconst, b.coordT, b.tab, b.Bt)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finalize(const BatchArgs &b, cudaStream_t s) {
+    const int cnt = b.count;
+    KernelTimer *timer = b.timer;
+    TIMED(KC_FINAL, (k_finalize<<<(cnt + 63) / 64, 64, 0, s>>>(
+                        cnt, b.k0, b.M, b.p, b.n, b.nb, b.reml, b.tpo, b.tiles, b.ldv, b.pstatus,
+                        b.sumlogy, b.lambdas, b.logL, b.sigma2, b.beta, b.logdet, b.status, b.out_index,
+                        b.status_or)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fp64_batch(const BatchArgs &b, cudaStream_t s) {
+    // per function and device; cheap to repeat
+    cudaError_t e = cudaFuncSetAttribute(k_potrf, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(2 * PK * sizeof(double)));
+    if (e != cudaSuccess) return e;
+    const int cnt = b.count;
+    KernelTimer *timer = b.timer;
+    if ((e = launch_front(b, s)) != cudaSuccess) return e;
     for (int J = 0; J < b.nb; ++J) {
         TIMED(KC_POTRF, (k_potrf<<<cnt, 256, 2 * PK * sizeof(double), s>>>(J, b.tpo, b.tiles, b.inv,
                                                                             b.ldv, b.pstatus)));
@@ -627,10 +644,7 @@ cudaError_t launch_fp64_batch(const BatchArgs &b, cudaStream_t s) {
         TIMED(KC_TRSM, (k_gemm_nt<0><<<dim3(m, cnt), 256, 0, s>>>(J, b.tpo, b.tiles, b.inv)));
         TIMED(KC_GEMM, (k_gemm_nt<1><<<dim3(m * (m + 1) / 2, cnt), 256, 0, s>>>(J, b.tpo, b.tiles, b.inv)));
     }
-    TIMED(KC_FINAL, (k_finalize<<<(cnt + 63) / 64, 64, 0, s>>>(
-                        cnt, b.k0, b.M, b.p, b.n, b.nb, b.reml, b.tpo, b.tiles, b.ldv, b.pstatus,
-                        b.sumlogy, b.lambdas, b.logL, b.sigma2, b.beta, b.logdet, b.status)));
-    return cudaGetLastError();
+    return launch_finalize(b, s);
 }
 
 cudaError_t launch_profile_max(const double *vals, int64_t G, int64_t SM, double *prof,

@@ -7,7 +7,7 @@ namespace plk {
 
 // Kernel classes for the optional per-launch event timing.
 enum KernelClass { KC_BOXCOX = 0, KC_PREP, KC_TABLE, KC_BUILD, KC_POTRF, KC_TRSM, KC_GEMM, KC_FINAL,
-                   KC_PROFILE, KC_COUNT };
+                   KC_PROFILE, KC_CONVERT, KC_COUNT };
 const char *kernel_class_name(int c);
 
 // Records a CUDA event pair around a launch on its stream (see plk_api.cu).
@@ -41,6 +41,8 @@ struct BatchArgs {
     double *logL, *sigma2, *beta, *logdet;
     int32_t *status;
     KernelTimer *timer = nullptr;
+    const int *out_index = nullptr;   // when set, batch slot w writes output row out_index[w]
+    int32_t status_or = 0;            // bits OR-ed into every written status
 };
 
 // Sets the calling thread's message returned by plk_last_error().
@@ -50,6 +52,23 @@ cudaError_t launch_boxcox(int64_t n, int64_t n_pad, int p, int M, const double *
                           const double *lam, double *Bt, double *sumlogy, cudaStream_t s,
                           KernelTimer *timer = nullptr);
 cudaError_t launch_fp64_batch(const BatchArgs &b, cudaStream_t s);
+// pieces of the batch pipeline shared with the mixed path
+cudaError_t launch_front(const BatchArgs &b, cudaStream_t s);      // prep, table, build (FP64 tiles)
+cudaError_t launch_finalize(const BatchArgs &b, cudaStream_t s);   // closed form from FP64 tile (nb, nb)
+// Buffers of the mixed-precision path (per batch slot w unless noted).
+struct MixedArgs {
+    uint8_t *wimg;       // count x img: slices of L_JJ^-1
+    uint8_t *pimg;       // count x (nb + 1) x img: slices of the current panel
+    double *invsum;      // count: sum of 1 / pivot
+    int *flags;          // count: 1 = re-evaluate with 7 slices
+    int *err;            // 1: set by a kernel whose bounded wait gave up
+    double *err_bound;   // K (global output, may be NULL)
+    double tol;          // retry when the bound exceeds this
+};
+size_t mixed_img_bytes(int S);
+cudaError_t launch_mixed_batch(const BatchArgs &b, const MixedArgs &x, int S, cudaStream_t s);
+cudaError_t launch_gather_params(int count, const int *idx, const double *params, double *out, cudaStream_t s);
+
 cudaError_t launch_profile_max(const double *vals, int64_t G, int64_t SM, double *prof,
                                cudaStream_t s);
 cudaError_t launch_profile_ci(const double *grid, const double *prof, int64_t G, double half_q,

@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(HERE, "libplk.so")
 HEADER = os.path.join(os.path.dirname(HERE), "include", "plk.h")
 
 PLK_OK, PLK_E_INVALID, PLK_E_NOMEM, PLK_E_NOT_READY, PLK_E_TIMEOUT, PLK_E_CUDA, PLK_E_CANCELLED = range(7)
-POINT_OK, POINT_NOT_PD, POINT_BAD_PARAM, POINT_RSS_NONPOS, POINT_FP64_RETRY = 0, 1, 2, 3, 16
+POINT_OK, POINT_NOT_PD, POINT_BAD_PARAM, POINT_RSS_NONPOS, POINT_RETRIED = 0, 1, 2, 3, 16
 FP64, MIXED = 0, 1
 
 
@@ -32,7 +32,7 @@ class EvalArgs(C.Structure):
                 ("coords", C.c_void_p), ("y", C.c_void_p), ("X", C.c_void_p), ("lambdas", C.c_void_p),
                 ("K", C.c_int64), ("params", C.c_void_p),
                 ("logL", C.c_void_p), ("sigma2", C.c_void_p), ("beta", C.c_void_p),
-                ("logdet", C.c_void_p), ("status", C.c_void_p)]
+                ("logdet", C.c_void_p), ("status", C.c_void_p), ("err_bound", C.c_void_p)]
 
 
 class Options(C.Structure):
@@ -114,6 +114,7 @@ def default_batch(n, K, limit_bytes=8e9):
 
 
 FLAG_KERNEL_TIMING = 1
+FLAG_NO_RETRY = 2
 
 
 def kernel_timing(reset=True):
@@ -148,7 +149,8 @@ def eval_device(coords, y, X, lambdas, params, precision=FP64, reml=False, batch
                        sigma2=torch.empty((K, M), dtype=torch.float64, device=dev),
                        beta=torch.empty((K, M, p), dtype=torch.float64, device=dev),
                        logdet=torch.empty((K, 2), dtype=torch.float64, device=dev),
-                       status=torch.empty((K,), dtype=torch.int32, device=dev))
+                       status=torch.empty((K,), dtype=torch.int32, device=dev),
+                       err_bound=torch.empty((K,), dtype=torch.float64, device=dev))
     wsb = workspace_bytes(n, p, M, batch, precision)
     if wsb == 0:
         raise PlkError(PLK_E_INVALID, f"invalid sizes n={n} p={p} M={M}")
@@ -156,7 +158,7 @@ def eval_device(coords, y, X, lambdas, params, precision=FP64, reml=False, batch
         workspace = torch.empty((wsb,), dtype=torch.uint8, device=dev)
     a = EvalArgs(n, p, M, _ptr(coords), _ptr(y), _ptr(X), _ptr(lambdas), K, _ptr(params),
                  _ptr(outputs.get("logL")), _ptr(outputs.get("sigma2")), _ptr(outputs.get("beta")),
-                 _ptr(outputs.get("logdet")), _ptr(outputs.get("status")))
+                 _ptr(outputs.get("logdet")), _ptr(outputs.get("status")), _ptr(outputs.get("err_bound")))
     o = Options(precision, int(bool(reml)), batch, int(flags))
     _check(lib().plk_eval_device(C.byref(a), C.byref(o), _ptr(workspace), workspace.numel(),
                                  _stream_handle(stream)))
@@ -183,7 +185,7 @@ def eval_device_static(coords, y, X, lambdas, params, reml=False, stream=None, o
                        status=torch.empty((K,), dtype=torch.int32, device=dev))
     a = EvalArgs(n, p, M, _ptr(coords), _ptr(y), _ptr(X), _ptr(lambdas), K, _ptr(params),
                  _ptr(outputs.get("logL")), _ptr(outputs.get("sigma2")), _ptr(outputs.get("beta")),
-                 _ptr(outputs.get("logdet")), _ptr(outputs.get("status")))
+                 _ptr(outputs.get("logdet")), _ptr(outputs.get("status")), None)
     _check(lib().plk_eval_device_static(C.byref(a), int(bool(reml)), _stream_handle(stream)))
     return outputs
 

@@ -1,0 +1,104 @@
+"""GPU parity of the mixed-precision path (split-bf16 tensor-core factorisation)
+against the FP64 oracle: |Delta l_p| <= 1e-3 absolute per (omega, lambda)."""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+from paper_2305_04318_b300 import native as nv, synth
+from gpu_util import gpu_eval, oracle_eval
+
+pytestmark = pytest.mark.gpu
+ATOL_LOGL = 1e-3
+
+
+def mixed_compare(g, o, what, atol=ATOL_LOGL):
+    st_g = g["status"] & ~nv.POINT_RETRIED
+    both = (st_g == 0) & (o["status"] == 0)
+    # a point only one side could factor must be a (near-)singular one
+    disagree = np.flatnonzero(st_g != o["status"])
+    err = np.abs(g["logL"][both] - o["logL"][both])
+    stats = dict(what=what, points=int(len(st_g)), compared=int(both.sum()), status_disagree=int(len(disagree)),
+                 max_abs_logL=float(err.max()) if err.size else 0.0,
+                 retried=int(((g["status"] & nv.POINT_RETRIED) != 0).sum()))
+    if both.any():
+        s2 = np.abs(g["sigma2"][both] / o["sigma2"][both] - 1)
+        stats["max_rel_sigma2"] = float(s2.max())
+        bscale = np.abs(o["beta"][both]).max()
+        stats["max_abs_beta_rel_to_max"] = float(np.abs(g["beta"][both] - o["beta"][both]).max() / bscale)
+        stats["max_abs_logdet"] = float(np.abs(g["logdet"][both] - o["logdet"][both]).max())
+    print(json.dumps(stats))
+    assert err.size == 0 or err.max() <= atol, stats
+    return stats
+
+
+def test_mixed_iso100():
+    w = synth.iso100()
+    ds, P = w.datasets[0], w.params[0]
+    o = oracle_eval(ds, P, w.lambdas)
+    g = gpu_eval(ds, P, w.lambdas, precision=nv.MIXED)
+    s = mixed_compare(g, o, "iso100")
+    assert s["status_disagree"] <= 2
+
+
+def test_mixed_aniso1000_subset():
+    w = synth.aniso1000(K=96)
+    ds, P = w.datasets[0], w.params[0]
+    o = oracle_eval(ds, P, w.lambdas)
+    g = gpu_eval(ds, P, w.lambdas, precision=nv.MIXED, batch=40)
+    s = mixed_compare(g, o, "aniso1000")
+    assert s["status_disagree"] == 0
+
+
+@pytest.mark.parametrize("n,p,M", [(3, 2, 1), (129, 5, 9), (300, 2, 3)])
+def test_mixed_ragged(n, p, M):
+    ds = synth.aniso_dataset(100 + n, n, math.sqrt(n / 10), p)
+    P = synth.omega_from_unit(np.random.default_rng(n).uniform(size=(7, 5)))
+    lams = np.linspace(-0.5, 1.5, M)
+    o = oracle_eval(ds, P, lams)
+    g = gpu_eval(ds, P, lams, precision=nv.MIXED, batch=3)
+    mixed_compare(g, o, f"n={n}")
+
+
+def test_mixed_error_bound_covers_five_slice_error():
+    """Without the 7-slice re-evaluation, every point whose bound is below the
+    tolerance is within it (the bound decides the retries)."""
+    w = synth.aniso1000(K=64)
+    ds, P = w.datasets[0], w.params[0]
+    o = oracle_eval(ds, P, w.lambdas)
+    g = gpu_eval(ds, P, w.lambdas, precision=nv.MIXED, flags=nv.FLAG_NO_RETRY)
+    ok = (g["status"] == 0) & (o["status"] == 0)
+    err = np.max(np.abs(g["logL"] - o["logL"]), axis=1)
+    eb = g["err_bound"]
+    print(json.dumps(dict(bound_quantiles=np.quantile(eb[ok], [0, .5, .9, 1]).tolist(),
+                          err_quantiles=np.quantile(err[ok], [0, .5, .9, 1]).tolist(),
+                          ratio_max=float(np.max(err[ok] / np.maximum(eb[ok], 1e-300))))))
+    small = ok & (eb <= 1e-4)
+    assert np.all(err[small] <= ATOL_LOGL)
+
+
+def test_mixed_deterministic_and_batch_independent():
+    w = synth.aniso1000(K=12)
+    ds, P = w.datasets[0], w.params[0]
+    a = gpu_eval(ds, P, w.lambdas, precision=nv.MIXED, batch=12)
+    b = gpu_eval(ds, P, w.lambdas, precision=nv.MIXED, batch=12)
+    c = gpu_eval(ds, P, w.lambdas, precision=nv.MIXED, batch=5)
+    for k in ("logL", "sigma2", "beta", "logdet", "status"):
+        np.testing.assert_array_equal(a[k], b[k])
+        np.testing.assert_array_equal(a[k], c[k])
+
+
+@pytest.mark.slow
+def test_mixed4000_full_size_sampled():
+    """The n=4000 workload at full size in the bench's launch configuration:
+    sampled points against the oracle, all points against the FP64 GPU path."""
+    w = synth.mixed4000()
+    ds, P = w.datasets[0], w.params[0]
+    g = gpu_eval(ds, P, w.lambdas, precision=nv.MIXED, batch=512)
+    idx = np.array([0, 1, 333, 959, 960, 990, 1000, 1023])
+    o = oracle_eval(ds, P[idx], w.lambdas)
+    mixed_compare({k: v[idx] for k, v in g.items()}, o, "mixed4000 sampled vs oracle")
+    f = gpu_eval(ds, P, w.lambdas, precision=nv.FP64)
+    mixed_compare(g, f, "mixed4000 all vs FP64 GPU")
