@@ -49,7 +49,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="auto", choices=["auto", "fp64", "mixed"])
-    ap.add_argument("--batch", type=int, default=0, help="omega points per step (default: 128 fp64, 512 mixed)")
+    ap.add_argument("--batch", type=int, default=0, help="omega points per step (default: 512 mixed, 128 fp64)")
     ap.add_argument("--n", type=int, default=4000)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -202,6 +202,10 @@ def run_reference(args):
 # our arm
 # ---------------------------------------------------------------------------
 
+def split_pairs(S):
+    return S * (S + 1) // 2
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -228,84 +232,131 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         return float(t.item())
 
-    prec = args.precision
-    if prec == "auto":
-        prec = "fp64"
-    precision = nv.FP64 if prec == "fp64" else nv.MIXED
-    B = args.batch or (128 if prec == "fp64" else 512)
-
+    head = "mixed" if args.precision in ("auto", "mixed") else "fp64"
     w = synth.mixed4000(n=args.n)
     ds, P, lam = w.datasets[0], w.params[0], w.lambdas
     K = P.shape[0]
     n, p, M = ds.n, ds.p, len(lam)
     q = M + p
+    nb = -(-n // 128)
     dev = torch.device("cuda", local)
     T = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64), device=dev)
     coords, y, X, lamd, Pd = T(ds.coords), T(ds.y), T(ds.X), T(lam), T(P)
     stream = torch.cuda.current_stream()
-    wsb = nv.workspace_bytes(n, p, M, B, precision)
-    workspace = torch.empty((wsb,), dtype=torch.uint8, device=dev)
-    outs = dict(logL=torch.empty((B, M), dtype=torch.float64, device=dev),
-                sigma2=torch.empty((B, M), dtype=torch.float64, device=dev),
-                beta=torch.empty((B, M, p), dtype=torch.float64, device=dev),
-                logdet=torch.empty((B, 2), dtype=torch.float64, device=dev),
-                status=torch.empty((B,), dtype=torch.int32, device=dev))
+    peaks = measured_peaks()
 
-    def step_params(s):
+    def outputs(B):
+        return dict(logL=torch.empty((B, M), dtype=torch.float64, device=dev),
+                    sigma2=torch.empty((B, M), dtype=torch.float64, device=dev),
+                    beta=torch.empty((B, M, p), dtype=torch.float64, device=dev),
+                    logdet=torch.empty((B, 2), dtype=torch.float64, device=dev),
+                    status=torch.empty((B,), dtype=torch.int32, device=dev),
+                    err_bound=torch.empty((B,), dtype=torch.float64, device=dev))
+
+    def step_params(s, B):
         # rank r evaluates its own slice: points (s * world + r) * B ... cycling through the grid
         start = ((s * world + rank) * B) % K
         idx = (torch.arange(B, device=dev) + start) % K
         return Pd.index_select(0, idx).contiguous()
 
-    batches = [step_params(s) for s in range(args.warmup + args.steps)]
+    def measure(prec_name, B, steps, warmup, sample_clocks):
+        precision = nv.MIXED if prec_name == "mixed" else nv.FP64
+        wsb = nv.workspace_bytes(n, p, M, B, precision)
+        workspace = torch.empty((wsb,), dtype=torch.uint8, device=dev)
+        batches = [step_params(s, B) for s in range(warmup + steps)]
+        outs = [outputs(B) for _ in range(warmup + steps)]
 
-    def one_step(s, flags=0):
-        nv.eval_device(coords, y, X, lamd, batches[s], precision=precision, batch=B, workspace=workspace,
-                       stream=stream, outputs=outs, flags=flags)
+        def one(s, flags=0):
+            nv.eval_device(coords, y, X, lamd, batches[s], precision=precision, batch=B, workspace=workspace,
+                           stream=stream, outputs=outs[s], flags=flags)
 
-    for s in range(args.warmup):
-        one_step(s)
-    barrier()
-    nv.kernel_timing(reset=True)
-    clocks = ClockSampler(local)
-    clocks.start()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    barrier()
-    e0.record(stream)
-    for s in range(args.warmup, args.warmup + args.steps):
-        one_step(s, flags=nv.FLAG_KERNEL_TIMING)
-    e1.record(stream)
-    barrier()
-    clk = clocks.stop()
-    ms_total = max_over_ranks(e0.elapsed_time(e1))
-    timing = nv.kernel_timing(reset=True)
-    ms_per_step = ms_total / args.steps
-    value = world * B * args.steps / (ms_total * 1e-3)
-    st = outs["status"].cpu().numpy()
+        for s in range(warmup):
+            one(s)
+        barrier()
+        nv.kernel_timing(reset=True)
+        clocks = ClockSampler(local) if sample_clocks else None
+        if clocks:
+            clocks.start()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        barrier()
+        e0.record(stream)
+        for s in range(warmup, warmup + steps):
+            one(s, flags=nv.FLAG_KERNEL_TIMING)
+        e1.record(stream)
+        barrier()
+        clk = clocks.stop() if clocks else None
+        ms_total = max_over_ranks(e0.elapsed_time(e1))
+        timing = nv.kernel_timing(reset=True)
+        status = np.concatenate([outs[s]["status"].cpu().numpy() for s in range(warmup, warmup + steps)])
+        res = dict(value=world * B * steps / (ms_total * 1e-3), ms_per_step=ms_total / steps, timing=timing,
+                   clocks=clk, status=status, wsb=wsb, B=B, steps=steps, warmup=warmup,
+                   first=({k: v.cpu().numpy() for k, v in outs[warmup].items()}), first_params=batches[warmup])
+        del workspace
+        torch.cuda.empty_cache()
+        return res
 
-    # dominant kernel and its roofline
+    Bm = args.batch or (512 if head == "mixed" else 128)
+    main_res = measure(head, Bm, args.steps, args.warmup, True)
+    fp64_res = None
+    if head == "mixed":
+        # the FP64 path on the first 128 points of the same steps, for the comparison
+        fp64_res = measure("fp64", 128, max(1, min(args.steps, 2)), 1, False)
+
+    timing = main_res["timing"]
     dom = max(timing, key=lambda k: timing[k][0])
-    dom_ms, dom_launches = timing[dom]
+    dom_ms = timing[dom][0]
     launches = int(sum(c for _, c in timing.values()))
-    roof = None
     fp64_peak, fp32_peak = probe_fp64_peak()
-    if dom == "trailing_gemm":
-        flops = sum(trailing_flops(n, q)) * B * args.steps
-        achieved = flops / (dom_ms * 1e-3) / 1e12
-        if prec == "fp64":
-            roof = {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
-                    "frac": achieved / fp64_peak, "traffic": None, "kernel": "k_gemm_nt<1> (trailing update)",
-                    "peak_source": "FP64 FMA pipe measured live by libplk_probe (no FP64 figure in MEASURED_PEAKS.json)"}
-    kernel_share = {k: round(v[0] / max(1e-9, sum(x[0] for x in timing.values())), 4) for k, v in timing.items() if v[1]}
+    tf = sum(trailing_flops(n, q))   # algorithmic trailing-update flops per omega
+    roof = None
+    st = main_res["status"]
+    n_pts = len(st)
+    if dom in ("trailing_gemm",):
+        achieved = tf * n_pts / (dom_ms * 1e-3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
+                "frac": achieved / fp64_peak, "traffic": None, "kernel": "k_gemm_nt<1> (FP64 trailing update)",
+                "peak_source": "FP64 FMA pipe measured live by libplk_probe (no FP64 figure in MEASURED_PEAKS.json)"}
+    elif dom == "trailing_split":
+        n7 = int(((st & nv.POINT_RETRIED) != 0).sum())
+        n64 = int(((st & nv.POINT_FP64) != 0).sum())
+        # every point runs the 5-slice pass; retried points also run the 7-slice pass
+        tiles = sum((nb - J) * (nb - J + 1) // 2 for J in range(nb))
+        executed = 2.0 * 128 ** 3 * tiles * (split_pairs(5) * n_pts + split_pairs(7) * n7)
+        peak = peaks.get("bf16_tflops_sustained") or 1341.1
+        alg = tf * (n_pts + n7) / (dom_ms * 1e-3) / 1e12
+        roof = {"bound": "tensor", "achieved": alg, "peak": peak, "unit": "TFLOP/s", "frac": alg / peak,
+                "traffic": None, "kernel": "k_trail_split<5> (split-bf16 trailing update, tcgen05)",
+                "achieved_is": "algorithmic FP64-equivalent trailing-update flops (n^3/3 + n^2 q per omega) / kernel time",
+                "executed_bf16_tflops": executed / (dom_ms * 1e-3) / 1e12,
+                "executed_frac": executed / (dom_ms * 1e-3) / 1e12 / peak,
+                "executed_is": "bf16 MMA flops issued: 15 slice products per multiply at 5 slices, 28 at 7",
+                "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (kernel timed inside a long step)",
+                "points_7slice": n7, "points_fp64": n64}
+    share_tot = max(1e-9, sum(x[0] for x in timing.values()))
+    kernel_share = {k: round(v[0] / share_tot, 4) for k, v in timing.items() if v[1]}
+
+    # agreement of mixed with the FP64 path on the same points
+    agree = None
+    if fp64_res is not None:
+        gm, gf = main_res["first"], fp64_res["first"]
+        m = min(len(gf["status"]), len(gm["status"]))
+        okp = ((gm["status"][:m] & 15) == 0) & (gf["status"][:m] == 0)
+        d = np.abs(gm["logL"][:m][okp] - gf["logL"][:m][okp])
+        agree = {"points": int(m), "compared": int(okp.sum()), "max_abs_dlogL_vs_fp64": float(d.max()) if d.size else None,
+                 "status_mismatch": int((((gm["status"][:m] & 15) != 0) != (gf["status"][:m] != 0)).sum())}
 
     # ---- end to end through the C ABI with host buffers ----
     e2e = None
     lat = None
     if not args.no_e2e:
+        precision = nv.MIXED if head == "mixed" else nv.FP64
+        B = Bm
+        wsb = nv.workspace_bytes(n, p, M, B, precision)
         arena = torch.empty((wsb + (256 << 20),), dtype=torch.uint8, device=dev)
         ctx = nv.Context(arena.numel(), device=local, arena=arena, n_streams=1)
-        hostP = [np.ascontiguousarray(batches[s].cpu().numpy()) for s in range(len(batches))]
+        hostP = [np.ascontiguousarray(step_params(s, B).cpu().numpy()) for s in range(args.warmup + args.steps)]
+
         def e2e_step(s):
             t0 = time.perf_counter()
             did = ctx.create_dataset(ds.coords, ds.y, ds.X)
@@ -313,6 +364,7 @@ def main():
             r = ctx.poll(job, p)
             ctx.release_dataset(did)
             return time.perf_counter() - t0, r
+
         for s in range(args.warmup):
             e2e_step(s)
         barrier()
@@ -322,12 +374,13 @@ def main():
             times.append(dt)
         tot = max_over_ranks(sum(times))
         ctx.close()
+        del arena
         h2d = ds.coords.nbytes + ds.y.nbytes + ds.X.nbytes + hostP[0].nbytes + lam.nbytes
         d2h = r["logL"].nbytes + r["sigma2"].nbytes + r["beta"].nbytes + r["logdet"].nbytes + r["status"].nbytes
         e2e = {"value": world * B * args.steps / tot, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h)}
         lat = {"p50": 1e3 * float(np.percentile(times, 50)), "p99": 1e3 * float(np.percentile(times, 99)),
-               "what": f"end-to-end step latency (host inputs -> host results) of a {B}-point job"}
+               "what": f"end-to-end latency of one {B}-point job (host inputs -> host results)"}
 
     # ---- CPU baseline (oracle on the host cores), rank 0 at N = 1 only ----
     cpu = None
@@ -339,17 +392,26 @@ def main():
                "sample": f"first {npts} omega points of the n=4000 workload ({dt:.1f} s wall, one point per thread)"}
 
     if rank == 0:
-        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-                "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": {"workload": WORKLOAD, "precision": prec, "batch_per_step": B, "n": n, "p": p, "M": M,
-                           "l2": f"inputs larger than L2: {wsb / 1e9:.1f} GB tile workspace per step",
+        fp64_line = None
+        if fp64_res is not None:
+            tm = fp64_res["timing"]
+            gms = tm.get("trailing_gemm", (0.0, 0))[0]
+            ach = tf * len(fp64_res["status"]) / (gms * 1e-3) / 1e12 if gms else None
+            fp64_line = {"value": fp64_res["value"], "unit": UNIT, "ms_per_step": fp64_res["ms_per_step"],
+                         "batch_per_step": fp64_res["B"], "steps": fp64_res["steps"],
+                         "trailing_gemm_tflops": ach, "trailing_gemm_frac_of_fp64_peak": (ach / fp64_peak) if ach else None}
+        line = {"metric": METRIC, "value": main_res["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": main_res["ms_per_step"], "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "precision": head, "batch_per_step": Bm, "n": n, "p": p, "M": M,
+                           "l2": f"inputs larger than L2: {main_res['wsb'] / 1e9:.1f} GB workspace per step",
                            "parallelism": f"omega-sharded x{world}"},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "latency_ms": lat,
                 "gpu_launches": launches, "kernel_ms": {k: round(v[0], 3) for k, v in timing.items() if v[1]},
-                "kernel_share": kernel_share, "clocks": clk,
+                "kernel_share": kernel_share, "clocks": main_res["clocks"],
+                "fp64_path": fp64_line, "mixed_vs_fp64": agree,
                 "fp64_fma_peak_tflops": fp64_peak, "fp32_fma_peak_tflops": fp32_peak,
-                "points_not_ok_last_step": int((st != 0).sum())}
+                "points_not_ok": int(((st & 15) != 0).sum()), "points_evaluated": int(n_pts)}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

@@ -64,6 +64,8 @@ typedef enum {
 #define PLK_POINT_RSS_NONPOS 3   /* residual sum of squares <= 0 */
 #define PLK_POINT_RETRIED 16     /* flag bit: mixed mode re-evaluated this point with the 7-slice
                                     (~48-bit) split because the 5-slice error bound was too large */
+#define PLK_POINT_FP64 32        /* flag bit: mixed mode re-evaluated this point in FP64 because the
+                                    7-slice error bound was still too large */
 
 typedef enum {
     PLK_FP64 = 0,  /* every step in FP64 arithmetic */
@@ -105,8 +107,9 @@ typedef struct {
     double *beta;            /* K x M x p beta-hat */
     double *logdet;          /* K x 2  [log|V|, log|X'V^-1X|] */
     int32_t *status;         /* K      PLK_POINT_* codes */
-    double *err_bound;       /* K      PLK_MIXED: a-posteriori bound on the log-likelihood error of
-                                       the split-product factorisation; PLK_FP64: 0 */
+    double *err_bound;       /* K      PLK_MIXED: a-posteriori bound on |Delta l_p| of the split-product
+                                       factorisation that produced the result (0 for points
+                                       re-evaluated in FP64); PLK_FP64: 0 */
 } plk_eval_args;
 
 /* Bytes of device workspace plk_eval_device needs to process `batch` points of

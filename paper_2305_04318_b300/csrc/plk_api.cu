@@ -266,9 +266,29 @@ static plk_status run_mixed_batch(BatchArgs b, const Layout &L, void *ws, const 
     r.status_or = PLK_POINT_RETRIED;
     e = launch_mixed_batch(r, x, 7, s);
     if (e != cudaSuccess) return cuda_fail(e, "mixed retry launch");
-    // the host vector idx must outlive the copy: wait for it
-    e = cudaStreamSynchronize(s);
+    // third tier: points whose 7-slice bound is still above the tolerance, in FP64
+    std::vector<int> hf7(r.count + 1);
+    e = cudaMemcpyAsync(hf7.data(), x.flags, sizeof(int) * r.count, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hf7.data() + r.count, x.err, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);   // also keeps idx alive until its copy is done
     if (e != cudaSuccess) return cuda_fail(e, "mixed retry");
+    if (hf7[r.count]) return fail(PLK_E_TIMEOUT, "a tensor-core wait gave up (device error flag set)");
+    std::vector<int> idx2;
+    for (int w = 0; w < r.count; ++w)
+        if (hf7[w]) idx2.push_back(idx[w]);
+    if (idx2.empty()) return PLK_OK;
+    e = cudaMemcpyAsync(d_idx, idx2.data(), sizeof(int) * idx2.size(), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = launch_gather_params((int)idx2.size(), d_idx, params_all, d_par, s);
+    if (e != cudaSuccess) return cuda_fail(e, "fp64 retry gather");
+    BatchArgs f = b;
+    f.count = (int)idx2.size();
+    f.params = d_par;
+    f.out_index = d_idx;
+    f.status_or = PLK_POINT_RETRIED | PLK_POINT_FP64;
+    e = launch_fp64_batch(f, s);
+    if (e == cudaSuccess && err_bound) e = launch_scatter_value(f.count, d_idx, 0.0, err_bound, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);   // idx2 must outlive its copy
+    if (e != cudaSuccess) return cuda_fail(e, "fp64 retry");
     return PLK_OK;
 }
 

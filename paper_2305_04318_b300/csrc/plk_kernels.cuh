@@ -7,7 +7,7 @@ namespace plk {
 
 // Kernel classes for the optional per-launch event timing.
 enum KernelClass { KC_BOXCOX = 0, KC_PREP, KC_TABLE, KC_BUILD, KC_POTRF, KC_TRSM, KC_GEMM, KC_FINAL,
-                   KC_PROFILE, KC_CONVERT, KC_COUNT };
+                   KC_PROFILE, KC_CONVERT, KC_POTRF_MIXED, KC_TRSM_SPLIT, KC_GEMM_SPLIT, KC_COUNT };
 const char *kernel_class_name(int c);
 
 // Records a CUDA event pair around a launch on its stream (see plk_api.cu).
@@ -68,6 +68,7 @@ struct MixedArgs {
 size_t mixed_img_bytes(int S);
 cudaError_t launch_mixed_batch(const BatchArgs &b, const MixedArgs &x, int S, cudaStream_t s);
 cudaError_t launch_gather_params(int count, const int *idx, const double *params, double *out, cudaStream_t s);
+cudaError_t launch_scatter_value(int count, const int *idx, double v, double *out, cudaStream_t s);
 
 cudaError_t launch_profile_max(const double *vals, int64_t G, int64_t SM, double *prof,
                                cudaStream_t s);

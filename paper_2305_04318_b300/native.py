@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(HERE, "libplk.so")
 HEADER = os.path.join(os.path.dirname(HERE), "include", "plk.h")
 
 PLK_OK, PLK_E_INVALID, PLK_E_NOMEM, PLK_E_NOT_READY, PLK_E_TIMEOUT, PLK_E_CUDA, PLK_E_CANCELLED = range(7)
-POINT_OK, POINT_NOT_PD, POINT_BAD_PARAM, POINT_RSS_NONPOS, POINT_RETRIED = 0, 1, 2, 3, 16
+POINT_OK, POINT_NOT_PD, POINT_BAD_PARAM, POINT_RSS_NONPOS, POINT_RETRIED, POINT_FP64 = 0, 1, 2, 3, 16, 32
 FP64, MIXED = 0, 1
 
 

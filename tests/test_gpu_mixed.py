@@ -15,14 +15,15 @@ ATOL_LOGL = 1e-3
 
 
 def mixed_compare(g, o, what, atol=ATOL_LOGL):
-    st_g = g["status"] & ~nv.POINT_RETRIED
+    st_g = g["status"] & ~(nv.POINT_RETRIED | nv.POINT_FP64)
     both = (st_g == 0) & (o["status"] == 0)
     # a point only one side could factor must be a (near-)singular one
     disagree = np.flatnonzero(st_g != o["status"])
     err = np.abs(g["logL"][both] - o["logL"][both])
     stats = dict(what=what, points=int(len(st_g)), compared=int(both.sum()), status_disagree=int(len(disagree)),
                  max_abs_logL=float(err.max()) if err.size else 0.0,
-                 retried=int(((g["status"] & nv.POINT_RETRIED) != 0).sum()))
+                 retried=int(((g["status"] & nv.POINT_RETRIED) != 0).sum()),
+                 fp64=int(((g["status"] & nv.POINT_FP64) != 0).sum()))
     if both.any():
         s2 = np.abs(g["sigma2"][both] / o["sigma2"][both] - 1)
         stats["max_rel_sigma2"] = float(s2.max())
