@@ -259,11 +259,12 @@ def main():
         idx = (torch.arange(B, device=dev) + start) % K
         return Pd.index_select(0, idx).contiguous()
 
-    def measure(prec_name, B, steps, warmup, sample_clocks):
+    def measure(prec_name, B, steps, warmup, sample_clocks, batches=None):
         precision = nv.MIXED if prec_name == "mixed" else nv.FP64
         wsb = nv.workspace_bytes(n, p, M, B, precision)
         workspace = torch.empty((wsb,), dtype=torch.uint8, device=dev)
-        batches = [step_params(s, B) for s in range(warmup + steps)]
+        if batches is None:
+            batches = [step_params(s, B) for s in range(warmup + steps)]
         outs = [outputs(B) for _ in range(warmup + steps)]
 
         def one(s, flags=0):
@@ -300,8 +301,12 @@ def main():
     main_res = measure(head, Bm, args.steps, args.warmup, True)
     fp64_res = None
     if head == "mixed":
-        # the FP64 path on the first 128 points of the same steps, for the comparison
-        fp64_res = measure("fp64", 128, max(1, min(args.steps, 2)), 1, False)
+        # the FP64 path on 128-point slices of the mixed run's timed steps (its
+        # first timed step starts with the first 128 points of the mixed run's)
+        fs = max(1, min(args.steps, 2))
+        src = [step_params(args.warmup + s, Bm) for s in range(fs)]
+        fb = [src[0][:128].contiguous()] + [src[s][:128].contiguous() for s in range(fs)]
+        fp64_res = measure("fp64", 128, fs, 1, False, batches=fb)
 
     timing = main_res["timing"]
     dom = max(timing, key=lambda k: timing[k][0])

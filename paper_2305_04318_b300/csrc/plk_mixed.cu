@@ -258,11 +258,40 @@ __global__ void __launch_bounds__(256) k_potrf_mixed(int J, int64_t tpo, double 
 }
 
 // ---------------------------------------------------------------------------
+// Shared pieces of the two split-product kernels (512 threads = 16 warps).
+// Warp w reads TMEM lanes 32 (w % 4) .. +31 (its rows) and columns
+// 32 (w / 4) .. +31 of each accumulator.
+// ---------------------------------------------------------------------------
+constexpr int NTH = 512;
+constexpr int SPAD = TB + 1;   // padded shared row: (r, c) -> bank (r + c) mod 32
+
+__device__ __forceinline__ void load_groups(uint32_t tb, int warp, int c0, uint32_t (&p0)[16], uint32_t (&p1)[16],
+                                            uint32_t (&p2)[16], uint32_t (&p3)[16]) {
+    const uint32_t a = tb + ((uint32_t)(32 * (warp & 3)) << 16) + 32 * (warp >> 2) + c0;
+    tc::tmem_ld16(a + 0 * 128, p0);
+    tc::tmem_ld16(a + 1 * 128, p1);
+    tc::tmem_ld16(a + 2 * 128, p2);
+    tc::tmem_ld16(a + 3 * 128, p3);
+    tc::tmem_wait_ld();
+}
+
+// Thread's value of the product at (row r, column c): double-float of
+// 2^(ea + eb) (P0 + P1 + (P2 + P3)), ea + eb including the -14.
+__device__ __forceinline__ void group_value(uint32_t p0, uint32_t p1, uint32_t p2, uint32_t p3, int e, float &hi,
+                                            float &lo) {
+    const float sc = pow2f(e);
+    hi = __uint_as_float(p0) * sc;
+    lo = 0.0f;
+    df_add(hi, lo, __uint_as_float(p1) * sc);
+    df_add(hi, lo, (__uint_as_float(p2) + __uint_as_float(p3)) * sc);
+}
+
+// ---------------------------------------------------------------------------
 // Panel solve L_IJ = A_IJ W^T on the tensor cores; the result is only kept as
 // the slice image of panel slot I (the A / B operand of the trailing update).
 // ---------------------------------------------------------------------------
 template <int S>
-__global__ void __launch_bounds__(128, 1) k_trsm_split(int J, int nb, int64_t tpo, const double *__restrict__ tiles,
+__global__ void __launch_bounds__(NTH, 1) k_trsm_split(int J, int nb, int64_t tpo, const double *__restrict__ tiles,
                                                        const uint8_t *__restrict__ wimg, uint8_t *__restrict__ pimg,
                                                        int *__restrict__ err) {
     extern __shared__ uint8_t smraw[];
@@ -271,7 +300,8 @@ __global__ void __launch_bounds__(128, 1) k_trsm_split(int J, int nb, int64_t tp
     uint8_t *sW = sbase + S * SBLK;  // S blocks of the current K half of W
     __shared__ uint64_t bar_load, bar_mma;
     __shared__ uint32_t tmem_base;
-    __shared__ int sEA[TB], sEW[TB], sEO[TB];
+    __shared__ short sEA[TB], sEW[TB], sEO[TB];   // row exponents, |e| <= 120
+    __shared__ int sMx[TB];                         // row max |value| as float bits (>= 0)
     __shared__ int s_ok;
     const int w = blockIdx.y, I = J + 1 + blockIdx.x;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -288,15 +318,19 @@ __global__ void __launch_bounds__(128, 1) k_trsm_split(int J, int nb, int64_t tp
         tc::fence_mbar_init();
         s_ok = 1;
     }
-    sEW[tid] = reinterpret_cast<const int *>(wi + (size_t)S * 2 * SBLK)[tid];
-    // row exponents of A_IJ
-    for (int rr = 0; rr < 32; ++rr) {
-        const int r = warp * 32 + rr;
+    if (tid < TB) {
+        sEW[tid] = (short)reinterpret_cast<const int *>(wi + (size_t)S * 2 * SBLK)[tid];
+        sMx[tid] = 0;
+    }
+    // row exponents of A_IJ: warp w handles rows 8w .. 8w + 7
+#pragma unroll
+    for (int rr = 0; rr < 8; ++rr) {
+        const int r = warp * 8 + rr;
         float mx = 0.0f;
 #pragma unroll
         for (int q = 0; q < 4; ++q) mx = fmaxf(mx, fabsf(H[r * TB + lane + 32 * q]));
         for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-        if (lane == 0) sEA[r] = row_exp(mx);
+        if (lane == 0) sEA[r] = (short)row_exp(mx);
     }
     tc::fence_before_sync();
     __syncthreads();
@@ -305,15 +339,21 @@ __global__ void __launch_bounds__(128, 1) k_trsm_split(int J, int nb, int64_t tp
     uint32_t phase = 0;
     for (int h = 0; h < 2; ++h) {
         // slice the K half h of A_IJ into shared memory
-        for (int rr = 0; rr < 32; ++rr) {
-            const int r = warp * 32 + rr;
-            const int e = sEA[r];
+        float2 hv[8], lv[8];
+#pragma unroll
+        for (int rr = 0; rr < 8; ++rr) {
+            const int r = warp * 8 + rr;
             const int k = 64 * h + 2 * lane;
+            hv[rr] = *reinterpret_cast<const float2 *>(H + r * TB + k);
+            lv[rr] = *reinterpret_cast<const float2 *>(Lo + r * TB + k);
+        }
+#pragma unroll
+        for (int rr = 0; rr < 8; ++rr) {
+            const int r = warp * 8 + rr;
+            const int e = sEA[r];
             float m0[S], m1[S];
-            const float2 hv = *reinterpret_cast<const float2 *>(H + r * TB + k);
-            const float2 lv = *reinterpret_cast<const float2 *>(Lo + r * TB + k);
-            slice_df<S>(hv.x, lv.x, e, m0);
-            slice_df<S>(hv.y, lv.y, e, m1);
+            slice_df<S>(hv[rr].x, lv[rr].x, e, m0);
+            slice_df<S>(hv[rr].y, lv[rr].y, e, m1);
             const uint32_t off = tc::sw128_offset(r, 2 * lane);
 #pragma unroll
             for (int j = 0; j < S; ++j) *reinterpret_cast<uint32_t *>(sA + j * SBLK + off) = pack_bf16x2(m0[j], m1[j]);
@@ -343,47 +383,43 @@ __global__ void __launch_bounds__(128, 1) k_trsm_split(int J, int nb, int64_t tp
         tc::fence_after_sync();
     }
     const bool ok = s_ok != 0;
-    // epilogue: thread tid owns row tid of L_IJ (TMEM lane tid)
-    const int r = tid;
-    const uint32_t trow = tb + ((uint32_t)(warp * 32) << 16);
+    const int r = 32 * (warp & 3) + lane;   // this thread's row, columns 32 (warp / 4) .. +31
+    const int cb = 32 * (warp >> 2);
     if (ok) {
         float mx = 0.0f;
-        for (int c0 = 0; c0 < TB; c0 += 16) {
+#pragma unroll 1
+        for (int c0 = 0; c0 < 32; c0 += 16) {
             uint32_t p0[16], p1[16], p2[16], p3[16];
-            tc::tmem_ld16(trow + 0 * 128 + c0, p0);
-            tc::tmem_ld16(trow + 1 * 128 + c0, p1);
-            tc::tmem_ld16(trow + 2 * 128 + c0, p2);
-            tc::tmem_ld16(trow + 3 * 128 + c0, p3);
-            tc::tmem_wait_ld();
+            load_groups(tb, warp, c0, p0, p1, p2, p3);
 #pragma unroll
             for (int c = 0; c < 16; ++c) {
-                const float sc = pow2f(sEA[r] + sEW[c0 + c] - 14);
+                const float sc = pow2f(sEA[r] + sEW[cb + c0 + c] - 14);
                 const float v = (__uint_as_float(p0[c]) + __uint_as_float(p1[c]) +
                                  (__uint_as_float(p2[c]) + __uint_as_float(p3[c]))) * sc;
                 mx = fmaxf(mx, fabsf(v));
             }
         }
+        atomicMax(&sMx[r], __float_as_int(mx));
+    }
+    __syncthreads();
+    if (ok) {
+        const float mx = __int_as_float(sMx[r]);
         const int eo = row_exp(mx * (1.0f + 1.0f / 1024.0f));
-        sEO[r] = eo;
-        for (int c0 = 0; c0 < TB; c0 += 16) {
+        if (warp < 4) sEO[r] = (short)eo;
+#pragma unroll 1
+        for (int c0 = 0; c0 < 32; c0 += 16) {
             uint32_t p0[16], p1[16], p2[16], p3[16];
-            tc::tmem_ld16(trow + 0 * 128 + c0, p0);
-            tc::tmem_ld16(trow + 1 * 128 + c0, p1);
-            tc::tmem_ld16(trow + 2 * 128 + c0, p2);
-            tc::tmem_ld16(trow + 3 * 128 + c0, p3);
-            tc::tmem_wait_ld();
+            load_groups(tb, warp, c0, p0, p1, p2, p3);
 #pragma unroll
             for (int c = 0; c < 16; c += 2) {
                 float m[2][S];
 #pragma unroll
                 for (int u = 0; u < 2; ++u) {
-                    const float sc = pow2f(sEA[r] + sEW[c0 + c + u] - 14);
-                    float hi = __uint_as_float(p0[c + u]) * sc, lo = 0.0f;
-                    df_add(hi, lo, __uint_as_float(p1[c + u]) * sc);
-                    df_add(hi, lo, (__uint_as_float(p2[c + u]) + __uint_as_float(p3[c + u])) * sc);
+                    float hi, lo;
+                    group_value(p0[c + u], p1[c + u], p2[c + u], p3[c + u], sEA[r] + sEW[cb + c0 + c + u] - 14, hi, lo);
                     slice_df<S>(hi, lo, eo, m[u]);
                 }
-                store_pair<S>(sbase, r, c0 + c, m[0], m[1]);
+                store_pair<S>(sbase, r, cb + c0 + c, m[0], m[1]);
             }
         }
     }
@@ -392,8 +428,9 @@ __global__ void __launch_bounds__(128, 1) k_trsm_split(int J, int nb, int64_t tp
     if (ok) {
         const uint4 *src4 = reinterpret_cast<const uint4 *>(sbase);
         uint4 *dst4 = reinterpret_cast<uint4 *>(dst);
-        for (int e = tid; e < S * 2 * SBLK / 16; e += 128) dst4[e] = src4[e];
-        reinterpret_cast<int *>(dst + (size_t)S * 2 * SBLK)[tid] = sEO[tid];
+#pragma unroll 4
+        for (int e = tid; e < S * 2 * SBLK / 16; e += NTH) dst4[e] = src4[e];
+        if (tid < TB) reinterpret_cast<int *>(dst + (size_t)S * 2 * SBLK)[tid] = (int)sEO[tid];
     }
     tc::fence_before_sync();
     __syncthreads();
@@ -403,9 +440,12 @@ __global__ void __launch_bounds__(128, 1) k_trsm_split(int J, int nb, int64_t tp
 
 // ---------------------------------------------------------------------------
 // Trailing update A_IK -= L_IJ L_KJ^T (double-float tiles) on the tensor cores.
+// Epilogue in two phases: TMEM -> double-float deltas in padded shared rows
+// (thread per row), then a coalesced read-modify-write of the tile (thread per
+// column) with 8 loads in flight per thread.
 // ---------------------------------------------------------------------------
 template <int S>
-__global__ void __launch_bounds__(128, 1) k_trail_split(int J, int nb, int64_t tpo, double *__restrict__ tiles,
+__global__ void __launch_bounds__(NTH, 1) k_trail_split(int J, int nb, int64_t tpo, double *__restrict__ tiles,
                                                         const uint8_t *__restrict__ pimg, int *__restrict__ err) {
     extern __shared__ uint8_t smraw[];
     uint8_t *sbase = align1024(smraw);
@@ -418,7 +458,7 @@ __global__ void __launch_bounds__(128, 1) k_trail_split(int J, int nb, int64_t t
     const int w = blockIdx.y;
     int I, K;
     decode_trailing(blockIdx.x, J, I, K);
-    const int tid = threadIdx.x, warp = tid >> 5;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint8_t *ia = pimg + ((int64_t)w * (nb + 1) + I) * img_bytes<S>();
     const uint8_t *ib = pimg + ((int64_t)w * (nb + 1) + K) * img_bytes<S>();
     if (warp == 0) {
@@ -431,8 +471,10 @@ __global__ void __launch_bounds__(128, 1) k_trail_split(int J, int nb, int64_t t
         tc::fence_mbar_init();
         s_ok = 1;
     }
-    sEA[tid] = reinterpret_cast<const int *>(ia + (size_t)S * 2 * SBLK)[tid];
-    sEB[tid] = reinterpret_cast<const int *>(ib + (size_t)S * 2 * SBLK)[tid];
+    if (tid < TB) {
+        sEA[tid] = reinterpret_cast<const int *>(ia + (size_t)S * 2 * SBLK)[tid];
+        sEB[tid] = reinterpret_cast<const int *>(ib + (size_t)S * 2 * SBLK)[tid];
+    }
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
@@ -465,49 +507,46 @@ __global__ void __launch_bounds__(128, 1) k_trail_split(int J, int nb, int64_t t
         tc::fence_after_sync();
     }
     const bool ok = s_ok != 0;
-    // epilogue: stage the double-float tile (padded rows), update, write back
-    float *sH = reinterpret_cast<float *>(sbase);
-    float *sL = sH + TB * (TB + 1);
-    float *gH = reinterpret_cast<float *>(tiles + ((int64_t)w * tpo + tile_index(I, K)) * NT);
-    float *gL = gH + NT;
+    float *sDh = reinterpret_cast<float *>(sbase);   // deltas, padded rows
+    float *sDl = sDh + TB * SPAD;
     if (ok) {
-        for (int e = tid; e < NT; e += 128) {
-            const int rr = e >> 7, cc = e & (TB - 1);
-            sH[rr * (TB + 1) + cc] = gH[e];
-            sL[rr * (TB + 1) + cc] = gL[e];
-        }
-    }
-    __syncthreads();
-    if (ok) {
-        const int r = tid;
-        const uint32_t trow = tb + ((uint32_t)(warp * 32) << 16);
+        const int r = 32 * (warp & 3) + lane;
+        const int cb = 32 * (warp >> 2);
         const int ea = sEA[r] - 14;
-        for (int c0 = 0; c0 < TB; c0 += 16) {
+#pragma unroll 1
+        for (int c0 = 0; c0 < 32; c0 += 16) {
             uint32_t p0[16], p1[16], p2[16], p3[16];
-            tc::tmem_ld16(trow + 0 * 128 + c0, p0);
-            tc::tmem_ld16(trow + 1 * 128 + c0, p1);
-            tc::tmem_ld16(trow + 2 * 128 + c0, p2);
-            tc::tmem_ld16(trow + 3 * 128 + c0, p3);
-            tc::tmem_wait_ld();
+            load_groups(tb, warp, c0, p0, p1, p2, p3);
 #pragma unroll
             for (int c = 0; c < 16; ++c) {
-                const float sc = pow2f(ea + sEB[c0 + c]);
-                const int idx = r * (TB + 1) + c0 + c;
-                float hi = sH[idx], lo = sL[idx];
-                df_add(hi, lo, -(__uint_as_float(p0[c]) * sc));
-                df_add(hi, lo, -(__uint_as_float(p1[c]) * sc));
-                df_add(hi, lo, -((__uint_as_float(p2[c]) + __uint_as_float(p3[c])) * sc));
-                sH[idx] = hi;
-                sL[idx] = lo;
+                float hi, lo;
+                group_value(p0[c], p1[c], p2[c], p3[c], ea + sEB[cb + c0 + c], hi, lo);
+                sDh[r * SPAD + cb + c0 + c] = hi;
+                sDl[r * SPAD + cb + c0 + c] = lo;
             }
         }
     }
     __syncthreads();
     if (ok) {
-        for (int e = tid; e < NT; e += 128) {
-            const int rr = e >> 7, cc = e & (TB - 1);
-            gH[e] = sH[rr * (TB + 1) + cc];
-            gL[e] = sL[rr * (TB + 1) + cc];
+        float *gH = reinterpret_cast<float *>(tiles + ((int64_t)w * tpo + tile_index(I, K)) * NT);
+        float *gL = gH + NT;
+#pragma unroll 1
+        for (int base = 0; base < NT; base += NTH * 8) {
+            float h8[8], l8[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                h8[u] = gH[base + tid + NTH * u];
+                l8[u] = gL[base + tid + NTH * u];
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int e = base + tid + NTH * u;
+                const int idx = (e >> 7) * SPAD + (e & (TB - 1));
+                df_add(h8[u], l8[u], -sDh[idx]);
+                df_add(h8[u], l8[u], -sDl[idx]);
+                gH[e] = h8[u];
+                gL[e] = l8[u];
+            }
         }
     }
     tc::fence_before_sync();
@@ -579,9 +618,9 @@ static cudaError_t launch_mixed_steps(const BatchArgs &b, const MixedArgs &x, cu
         TIMED(KC_POTRF_MIXED, (k_potrf_mixed<S><<<cnt, 256, 2 * PK * sizeof(double), s>>>(
                             J, b.tpo, b.tiles, x.wimg, b.ldv, x.invsum, b.pstatus)));
         const int m = b.nb - J;
-        TIMED(KC_TRSM_SPLIT, (k_trsm_split<S><<<dim3(m, cnt), 128, smem_split, s>>>(J, b.nb, b.tpo, b.tiles, x.wimg,
+        TIMED(KC_TRSM_SPLIT, (k_trsm_split<S><<<dim3(m, cnt), NTH, smem_split, s>>>(J, b.nb, b.tpo, b.tiles, x.wimg,
                                                                                 x.pimg, x.err)));
-        TIMED(KC_GEMM_SPLIT, (k_trail_split<S><<<dim3(m * (m + 1) / 2, cnt), 128, smem_split, s>>>(J, b.nb, b.tpo, b.tiles,
+        TIMED(KC_GEMM_SPLIT, (k_trail_split<S><<<dim3(m * (m + 1) / 2, cnt), NTH, smem_split, s>>>(J, b.nb, b.tpo, b.tiles,
                                                                                            x.pimg, x.err)));
     }
     TIMED(KC_CONVERT, (k_tile_to_fp64<<<cnt, 256, 0, s>>>(b.tpo, tile_index(b.nb, b.nb), b.tiles)));
