@@ -305,8 +305,9 @@ def main():
         # first timed step starts with the first 128 points of the mixed run's)
         fs = max(1, min(args.steps, 2))
         src = [step_params(args.warmup + s, Bm) for s in range(fs)]
-        fb = [src[0][:128].contiguous()] + [src[s][:128].contiguous() for s in range(fs)]
-        fp64_res = measure("fp64", 128, fs, 1, False, batches=fb)
+        fB = min(128, Bm)
+        fb = [src[0][:fB].contiguous()] + [src[s][:fB].contiguous() for s in range(fs)]
+        fp64_res = measure("fp64", fB, fs, 1, False, batches=fb)
 
     timing = main_res["timing"]
     dom = max(timing, key=lambda k: timing[k][0])
