@@ -213,7 +213,7 @@ def main():
         return
     import torch
     import torch.distributed as dist
-    from paper_2305_04318_b300 import native as nv, synth
+    from paper_2305_04318_b300 import native as nv, shard, synth
 
     world, rank, local = dist_env()
     torch.cuda.set_device(local)
@@ -254,9 +254,8 @@ def main():
                     err_bound=torch.empty((B,), dtype=torch.float64, device=dev))
 
     def step_params(s, B):
-        # rank r evaluates its own slice: points (s * world + r) * B ... cycling through the grid
-        start = ((s * world + rank) * B) % K
-        idx = (torch.arange(B, device=dev) + start) % K
+        # rank r evaluates its own slice of the grid (shard.step_indices)
+        idx = torch.as_tensor(shard.step_indices(s, rank, world, B, K), device=dev)
         return Pd.index_select(0, idx).contiguous()
 
     def measure(prec_name, B, steps, warmup, sample_clocks, batches=None):
