@@ -54,6 +54,14 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=0, help="oracle points in the CPU sample (default: cores)")
+    ap.add_argument("--workload", default="mixed4000", choices=["mixed4000", "uneven", "serving"],
+                    help="mixed4000: the metric's n=4000 workload (default); uneven: 256 datasets of "
+                         "n in [200,3000] x 512 points through the job scheduler; serving: Poisson "
+                         "stream of profile jobs over a pool of resident datasets")
+    ap.add_argument("--datasets", type=int, default=0, help="uneven/serving: number of datasets (default 256 / 32)")
+    ap.add_argument("--points", type=int, default=512, help="uneven: points per dataset")
+    ap.add_argument("--jobs", type=int, default=40, help="serving: jobs per load level")
+    ap.add_argument("--streams", type=int, default=4, help="uneven/serving: scheduler streams")
     return ap.parse_args()
 
 
@@ -202,6 +210,135 @@ def run_reference(args):
 # our arm
 # ---------------------------------------------------------------------------
 
+def run_uneven(args):
+    """Config 4: 256 datasets with n log-uniform in [200, 3000] and p in {2,3,5},
+    512 points each, all submitted at once to one context; the scheduler
+    interleaves their batches over the stream pool (continuous batching)."""
+    import torch
+    from paper_2305_04318_b300 import native as nv, synth
+    D = args.datasets or 256
+    w = synth.uneven(D=D, per=args.points)
+    prec = nv.MIXED if args.precision in ("auto", "mixed") else nv.FP64
+    sizes = [nv.workspace_bytes(d.n, d.p, len(w.lambdas), 64, prec) for d in w.datasets]
+    arena_bytes = int(args.streams * max(sizes) * 1.2 + (2 << 30))
+    arena = torch.empty((arena_bytes,), dtype=torch.uint8, device="cuda")
+    with nv.Context(arena_bytes, arena=arena, n_streams=args.streams) as ctx:
+        ids = [ctx.create_dataset(d.coords, d.y, d.X) for d in w.datasets]
+        # warm-up: one small job
+        j = ctx.submit(ids[0], w.params[0][:4], w.lambdas, precision=prec, batch=4)
+        ctx.poll(j, w.datasets[0].p)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        jobs = [ctx.submit(ids[i], w.params[i], w.lambdas, precision=prec, batch=64) for i in range(D)]
+        res = [ctx.poll(jb, w.datasets[i].p) for i, jb in enumerate(jobs)]
+        dt = time.perf_counter() - t0
+        _, high = ctx.memory_stats()
+    npts = sum(len(P) for P in w.params)
+    st = np.concatenate([r["status"] for r in res])
+    ns = np.array([d.n for d in w.datasets])
+    line = {"metric": "profile-logL evals/s, batched uneven datasets", "value": npts / dt, "unit": UNIT,
+            "n_gpus": 1, "steps": 1, "warmup": 1, "ms_per_step": dt * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"uneven: {D} datasets, n log-uniform in [200,3000] (median {int(np.median(ns))}), "
+                                   f"p in {{2,3,5}}, {args.points} points each, 9 lambdas",
+                       "precision": "mixed" if prec == nv.MIXED else "fp64", "streams": args.streams,
+                       "batch_per_item": 64, "arena_gb": arena_bytes / 1e9},
+            "points": int(npts), "points_not_ok": int(((st & 15) != 0).sum()),
+            "points_7slice": int(((st & 16) != 0).sum()), "points_fp64": int(((st & 32) != 0).sum()),
+            "hbm_high_water_gb": high / 1e9, "e2e": {"value": npts / dt, "unit": UNIT,
+            "h2d_bytes_per_step": int(sum(P.nbytes for P in w.params)), "d2h_bytes_per_step": int(
+                sum(r["logL"].nbytes + r["sigma2"].nbytes + r["beta"].nbytes + r["logdet"].nbytes + r["status"].nbytes
+                    for r in res))}}
+    print(json.dumps(line), flush=True)
+
+
+def run_serving(args):
+    """Config 5: a Poisson stream of profile jobs over a pool of device-resident
+    datasets (n log-uniform in [500, 8000]).  A job profiles one parameter:
+    G grid values x sub^4 values of the other four x 9 lambdas, then the
+    profile maximum and the likelihood CI on the device.  Jobs arrive at an
+    offered load of 0.5 and 0.9 of the measured single-stream capacity."""
+    import torch
+    from paper_2305_04318_b300 import native as nv, synth
+    D = args.datasets or 32
+    G, sub = 16, 2     # jobs reduced from 64 x 4^4 omega so that a run ends in minutes
+    pool = synth.serving_pool(D=D)
+    lam = synth.LAMBDA_GRID_9
+    prec = nv.MIXED if args.precision in ("auto", "mixed") else nv.FP64
+    rng = np.random.default_rng(55)
+    grids = [synth.profile_job_grid(which, G=G, sub=sub) for which in range(5)]
+    arena_bytes = int(args.streams * nv.workspace_bytes(8000, 3, 9, 16, prec) * 1.1 + (4 << 30))
+    arena = torch.empty((arena_bytes,), dtype=torch.uint8, device="cuda")
+    results = {}
+    with nv.Context(arena_bytes, arena=arena, n_streams=args.streams) as ctx:
+        ids = [ctx.create_dataset(d.coords, d.y, d.X) for d in pool]
+
+        def job_spec(k):
+            return int(rng.integers(D)), k % 5
+
+        def finish(job, ds_i, which):
+            r = ctx.poll(job, 3)
+            gv, _ = grids[which]
+            vals = torch.as_tensor(r["logL"].reshape(G, -1), device="cuda")
+            prof = nv.profile_max_device(vals)
+            ci = nv.profile_ci_device(torch.as_tensor(gv, device="cuda"), prof, 0.95).cpu().numpy()
+            return r, ci
+
+        # capacity: jobs one after another
+        t0 = time.perf_counter()
+        cap_jobs = 6
+        for k in range(cap_jobs):
+            d_i, which = job_spec(k)
+            jb = ctx.submit(ids[d_i], grids[which][1], lam, precision=prec, batch=16)
+            finish(jb, d_i, which)
+        cap = cap_jobs / (time.perf_counter() - t0)
+        levels = {}
+        for rho in (0.5, 0.9):
+            rate = rho * cap
+            arrivals = np.cumsum(rng.exponential(1.0 / rate, size=args.jobs))
+            lat = []
+            pending = []
+            t0 = time.perf_counter()
+            k = 0
+            done = 0
+            while done < args.jobs:
+                now = time.perf_counter() - t0
+                while k < args.jobs and arrivals[k] <= now:
+                    d_i, which = job_spec(k)
+                    jb = ctx.submit(ids[d_i], grids[which][1], lam, precision=prec, batch=16)
+                    pending.append((jb, d_i, which, t0 + arrivals[k]))
+                    k += 1
+                still = []
+                for jb, d_i, which, ta in pending:
+                    r = ctx.poll(jb, 3, timeout_ms=0)
+                    if r is None:
+                        still.append((jb, d_i, which, ta))
+                        continue
+                    gv, _ = grids[which]
+                    prof = nv.profile_max_device(torch.as_tensor(r["logL"].reshape(G, -1), device="cuda"))
+                    nv.profile_ci_device(torch.as_tensor(gv, device="cuda"), prof, 0.95).cpu()
+                    lat.append(time.perf_counter() - ta)
+                    done += 1
+                pending = still
+                time.sleep(0.001)
+            span = time.perf_counter() - t0
+            levels[str(rho)] = {"offered_jobs_per_s": rate, "jobs": args.jobs, "throughput_jobs_per_s": args.jobs / span,
+                                "evals_per_s": args.jobs * G * sub ** 4 / span,
+                                "p50_ms": 1e3 * float(np.percentile(lat, 50)), "p99_ms": 1e3 * float(np.percentile(lat, 99))}
+        _, high = ctx.memory_stats()
+    top = levels["0.9"]
+    line = {"metric": "profile jobs: throughput and p50/p99 job latency (serving)", "value": top["evals_per_s"],
+            "unit": UNIT, "n_gpus": 1, "steps": args.jobs, "warmup": cap_jobs, "ms_per_step": top["p50_ms"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"serving: {D} resident datasets, n log-uniform in [500,8000], p=3; job = one "
+                                   f"parameter's {G}-point profile x {sub}^4 sub-grid x 9 lambdas ({G * sub ** 4} omega), "
+                                   "then profile max + 95% CI on the device; Poisson arrivals",
+                       "precision": "mixed" if prec == nv.MIXED else "fp64", "streams": args.streams},
+            "capacity_jobs_per_s": cap, "levels": levels, "hbm_high_water_gb": high / 1e9,
+            "latency_ms": {"p50": top["p50_ms"], "p99": top["p99_ms"], "what": "job latency at offered load 0.9"}}
+    print(json.dumps(line), flush=True)
+
+
 def split_pairs(S):
     return S * (S + 1) // 2
 
@@ -210,6 +347,12 @@ def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.workload == "uneven":
+        run_uneven(args)
+        return
+    if args.workload == "serving":
+        run_serving(args)
         return
     import torch
     import torch.distributed as dist

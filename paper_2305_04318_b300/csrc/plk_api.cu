@@ -513,11 +513,10 @@ struct Job {
 
 struct Item {
     Job *job;
-    int slot;
+    Dataset *ds;
     int64_t k0;
     int count;
     char *ws;
-    cudaEvent_t ev;
 };
 
 }  // namespace
@@ -529,18 +528,15 @@ struct plk_ctx {
     Arena arena;
     std::vector<cudaStream_t> streams;
     bool own_streams = false;
-    std::vector<int> slot_busy;
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
     std::map<plk_dataset, std::unique_ptr<Dataset>> datasets;
     std::map<plk_job, std::unique_ptr<Job>> jobs;
     std::deque<Job *> order;   // submission order of unfinished jobs
-    std::vector<Item> inflight;
-    std::vector<cudaEvent_t> event_pool;
     plk_dataset next_ds = 1;
     plk_job next_job = 1;
     bool stop = false;
-    std::thread worker;
+    std::vector<std::thread> workers;   // one per stream
     std::chrono::steady_clock::time_point t0;
     double now() const {
         return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -605,10 +601,12 @@ bool start_job(plk_ctx *c, Job *j, cudaStream_t s) {
     return true;
 }
 
-void launch_item(plk_ctx *c, Job *j, Item &it, cudaStream_t s) {
+// Runs one batch of a job on stream s and waits for it (called without the
+// context lock).  Returns an error message, empty on success.
+std::string run_item(Job *j, Item &it, cudaStream_t s) {
     Layout L;
     make_layout(j->n, j->p, j->M, it.count, L, j->opts.precision);
-    Dataset *d = c->datasets[j->ds].get();
+    Dataset *d = it.ds;
     BatchArgs b;
     b.count = it.count;
     b.k0 = it.k0;
@@ -638,21 +636,16 @@ void launch_item(plk_ctx *c, Job *j, Item &it, cudaStream_t s) {
     b.logdet = j->d_ld;
     b.status = j->d_st;
     cudaStreamWaitEvent(s, j->ready, 0);   // the job's B^T may come from another stream
+    std::string err;
     if (L.mixed) {
-        // synchronous on this stream (the retry set is decided on the host)
         plk_status st = run_mixed_batch(b, L, it.ws, j->d_params, j->opts.flags, nullptr, s);
-        if (st != PLK_OK) {
-            j->failed = true;
-            j->error = plk_last_error();
-        }
+        if (st != PLK_OK) err = plk_last_error();
     } else {
         cudaError_t e = launch_fp64_batch(b, s);
-        if (e != cudaSuccess) {
-            j->failed = true;
-            j->error = cudaGetErrorString(e);
-        }
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) err = cudaGetErrorString(e);
     }
-    cudaEventRecord(it.ev, s);
+    return err;
 }
 
 void finish_job(plk_ctx *c, Job *j) {
@@ -683,93 +676,66 @@ void finish_job(plk_ctx *c, Job *j) {
     j->t_done = c->now();
 }
 
-void worker_main(plk_ctx *c) {
+// One worker per stream: take the next batch of the oldest job that has work
+// left (admission: its workspace must fit in the arena; the batch shrinks until
+// it does), run it, retire it.  Jobs submitted while others run are picked up
+// as soon as a worker and arena space free up, so batches of different jobs
+// overlap on the device.
+void stream_worker(plk_ctx *c, int slot) {
     cudaSetDevice(c->device);
+    cudaStream_t s = c->streams[slot];
     std::unique_lock<std::mutex> lk(c->mu);
     while (true) {
-        // retire finished items
-        bool progressed = false;
-        for (size_t i = 0; i < c->inflight.size();) {
-            Item &it = c->inflight[i];
-            cudaError_t q = cudaEventQuery(it.ev);
-            if (q == cudaErrorNotReady) {
-                ++i;
+        Job *pick = nullptr;
+        for (Job *j : c->order) {
+            if (j->next_k < j->K || (!j->started && j->K == 0)) {
+                pick = j;
+                break;
+            }
+        }
+        if (!pick) {
+            if (c->stop && c->order.empty()) break;
+            c->cv_work.wait_for(lk, std::chrono::milliseconds(20));
+            continue;
+        }
+        if (!pick->started) {
+            if (!start_job(c, pick, s)) {   // no arena space for its inputs/outputs yet
+                c->cv_work.wait_for(lk, std::chrono::milliseconds(2));
                 continue;
             }
-            if (q != cudaSuccess) {
-                it.job->failed = true;
-                it.job->error = cudaGetErrorString(q);
-            }
-            c->arena.release(it.ws);
-            c->slot_busy[it.slot] = 0;
-            c->event_pool.push_back(it.ev);
-            Job *j = it.job;
-            j->inflight--;
-            c->inflight.erase(c->inflight.begin() + i);
-            progressed = true;
-            if (j->inflight == 0 && j->next_k >= j->K && !j->done) {
-                finish_job(c, j);
-                c->order.erase(std::find(c->order.begin(), c->order.end(), j));
+            if (pick->K == 0) {
+                finish_job(c, pick);
+                c->order.erase(std::find(c->order.begin(), c->order.end(), pick));
                 c->cv_done.notify_all();
+                continue;
             }
         }
-        // launch new items: oldest job first, one item per free stream slot
-        for (int slot = 0; slot < (int)c->streams.size(); ++slot) {
-            if (c->slot_busy[slot]) continue;
-            Job *pick = nullptr;
-            for (Job *j : c->order) {
-                if (j->next_k < j->K || (!j->started && j->K == 0)) {
-                    pick = j;
-                    break;
-                }
-            }
-            if (!pick) break;
-            cudaStream_t s = c->streams[slot];
-            if (!pick->started) {
-                if (!start_job(c, pick, s)) break;   // no arena space for its I/O yet
-                if (pick->K == 0) {
-                    finish_job(c, pick);
-                    c->order.erase(std::find(c->order.begin(), c->order.end(), pick));
-                    c->cv_done.notify_all();
-                    progressed = true;
-                    continue;
-                }
-            }
-            int count = (int)std::min<int64_t>(pick->batch, pick->K - pick->next_k);
-            char *ws = nullptr;
-            while (count >= 1 && !(ws = c->arena.alloc(item_bytes(pick->n, pick->p, pick->M, count, pick->opts.precision))))
-                count /= 2;   // admission by arena bytes: shrink the batch until it fits
-            if (!ws) break;   // wait for memory to free up
-            Item it;
-            it.job = pick;
-            it.slot = slot;
-            it.k0 = pick->next_k;
-            it.count = count;
-            it.ws = ws;
-            if (c->event_pool.empty()) {
-                cudaEvent_t ev;
-                cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
-                c->event_pool.push_back(ev);
-            }
-            it.ev = c->event_pool.back();
-            c->event_pool.pop_back();
-            launch_item(c, pick, it, s);
-            pick->next_k += count;
-            pick->inflight++;
-            c->slot_busy[slot] = 1;
-            c->inflight.push_back(it);
-            progressed = true;
+        int count = (int)std::min<int64_t>(pick->batch, pick->K - pick->next_k);
+        char *ws = nullptr;
+        while (count >= 1 && !(ws = c->arena.alloc(item_bytes(pick->n, pick->p, pick->M, count, pick->opts.precision))))
+            count /= 2;
+        if (!ws) {
+            c->cv_work.wait_for(lk, std::chrono::milliseconds(2));
+            continue;
         }
-        if (c->stop && c->order.empty() && c->inflight.empty()) break;
-        if (!progressed) {
-            if (c->inflight.empty())
-                c->cv_work.wait_for(lk, std::chrono::milliseconds(50));
-            else {
-                lk.unlock();
-                std::this_thread::sleep_for(std::chrono::microseconds(100));
-                lk.lock();
-            }
+        Item it{pick, c->datasets[pick->ds].get(), pick->next_k, count, ws};
+        pick->next_k += count;
+        pick->inflight++;
+        lk.unlock();
+        const std::string err = run_item(pick, it, s);
+        lk.lock();
+        if (!err.empty()) {
+            pick->failed = true;
+            pick->error = err;
         }
+        c->arena.release(ws);
+        pick->inflight--;
+        if (pick->inflight == 0 && pick->next_k >= pick->K && !pick->done) {
+            finish_job(c, pick);
+            c->order.erase(std::find(c->order.begin(), c->order.end(), pick));
+            c->cv_done.notify_all();
+        }
+        c->cv_work.notify_all();
     }
 }
 
@@ -806,8 +772,7 @@ extern "C" plk_status plk_create(plk_ctx **out, int device, void *arena, size_t 
         }
         c->own_streams = true;
     }
-    c->slot_busy.assign(c->streams.size(), 0);
-    c->worker = std::thread(worker_main, c.get());
+    for (int i = 0; i < (int)c->streams.size(); ++i) c->workers.emplace_back(stream_worker, c.get(), i);
     *out = c.release();
     return PLK_OK;
 }
@@ -946,9 +911,8 @@ extern "C" plk_status plk_destroy(plk_ctx *c) {
         c->stop = true;
         c->cv_work.notify_all();
     }
-    c->worker.join();
+    for (auto &t : c->workers) t.join();
     cudaSetDevice(c->device);
-    for (auto ev : c->event_pool) cudaEventDestroy(ev);
     if (c->own_streams)
         for (auto s : c->streams) cudaStreamDestroy(s);
     if (c->own_arena) cudaFree(c->arena_base);

@@ -56,3 +56,22 @@ def test_context_validation_and_nomem():
         assert r["status"][0] == 0 and np.all(np.isfinite(r["logL"]))
         j = ctx.submit(ds2, np.zeros((0, 5)), [0.0])
         assert ctx.poll(j, 2)["logL"].shape == (0, 1)
+
+
+def test_mixed_jobs_same_alone_and_in_the_mix():
+    """Continuous batching in mixed precision: three jobs run alone, then
+    submitted together over three streams; every result is identical."""
+    dsets = [synth.aniso_dataset(70 + i, n, math.sqrt(n / 10), 3) for i, n in enumerate([500, 900, 260])]
+    lams = synth.LAMBDA_GRID_9
+    grids = [synth.omega_from_unit(np.random.default_rng(10 + i).uniform(size=(K, 5))) for i, K in enumerate([30, 18, 41])]
+    arena = torch.empty(8 << 30, dtype=torch.uint8, device="cuda")
+    with nv.Context(arena.numel(), arena=arena, n_streams=3) as ctx:
+        ids = [ctx.create_dataset(d.coords, d.y, d.X) for d in dsets]
+        alone = [ctx.poll(ctx.submit(ids[i], grids[i], lams, precision=nv.MIXED, batch=8), 3) for i in range(3)]
+        jobs = [ctx.submit(ids[i], grids[i], lams, precision=nv.MIXED, batch=8) for i in range(3)]
+        mix = [ctx.poll(j, 3) for j in jobs]
+    for i in range(3):
+        for k in ("logL", "sigma2", "beta", "logdet", "status"):
+            np.testing.assert_array_equal(alone[i][k], mix[i][k])
+        ref = gpu_eval(dsets[i], grids[i], lams, precision=nv.MIXED, batch=8)
+        np.testing.assert_array_equal(alone[i]["logL"], ref["logL"])
