@@ -86,6 +86,9 @@ typedef struct {
 /* flags: PLK_MIXED without the 7-slice re-evaluation of points whose error bound
  * exceeds the tolerance (for measuring the 5-slice error itself). */
 #define PLK_FLAG_NO_RETRY 2
+/* flags: PLK_MIXED without the FP64 re-evaluation tier (keeps the 7-slice result;
+ * for measuring the 7-slice error itself). */
+#define PLK_FLAG_NO_FP64_TIER 4
 
 /* ------------------------------------------------------------------------ */
 /* Stateless device-pointer evaluation (one dataset, K points)               */

@@ -274,8 +274,9 @@ static plk_status run_mixed_batch(BatchArgs b, const Layout &L, void *ws, const 
     if (e != cudaSuccess) return cuda_fail(e, "mixed retry");
     if (hf7[r.count]) return fail(PLK_E_TIMEOUT, "a tensor-core wait gave up (device error flag set)");
     std::vector<int> idx2;
-    for (int w = 0; w < r.count; ++w)
-        if (hf7[w]) idx2.push_back(idx[w]);
+    if (!(flags & PLK_FLAG_NO_FP64_TIER))
+        for (int w = 0; w < r.count; ++w)
+            if (hf7[w]) idx2.push_back(idx[w]);
     if (idx2.empty()) return PLK_OK;
     e = cudaMemcpyAsync(d_idx, idx2.data(), sizeof(int) * idx2.size(), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = launch_gather_params((int)idx2.size(), d_idx, params_all, d_par, s);

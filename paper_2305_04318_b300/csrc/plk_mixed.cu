@@ -556,6 +556,299 @@ __global__ void __launch_bounds__(NTH, 1) k_trail_split(int J, int nb, int64_t t
 }
 
 // ---------------------------------------------------------------------------
+// 7-slice variants with every group exact: the 128 x 128 result is produced as
+// two 128 x 64 column halves; each half keeps the 7 groups g = 0..6 in their
+// own 64-column TMEM accumulators (448 columns), so no group is rounded before
+// the double-float epilogue.  Used for the re-evaluation of points whose
+// 5-slice error bound was too large.
+// ---------------------------------------------------------------------------
+constexpr int S7 = 7;
+constexpr int HBLK = SBLK / 2;   // rows 0..63 or 64..127 of a block: 8 KB, contiguous
+constexpr uint32_t IDESC64 = tc::idesc_bf16_f32(128, 64);
+
+__device__ __forceinline__ void issue_exact_mmas7(uint32_t tb, const uint8_t *sA, const uint8_t *sB, bool first_half) {
+#pragma unroll 1
+    for (int i = 0; i < S7; ++i) {
+#pragma unroll 1
+        for (int j = 0; i + j < S7; ++j) {
+            const int g = i + j;
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk) {
+                const uint64_t ad = tc::sdesc_sw128(tc::smem_u32(sA + i * SBLK) + kk * 32);
+                const uint64_t bd = tc::sdesc_sw128(tc::smem_u32(sB + j * HBLK) + kk * 32);
+                const uint32_t accumulate = (first_half && kk == 0 && i == 0) ? 0u : 1u;
+                tc::mma_bf16(tb + g * 64, ad, bd, IDESC64, accumulate);
+            }
+        }
+    }
+}
+
+// double-float of 2^e sum_g P_g over the 7 exact groups at column c of this
+// thread's row (16 columns per call); warp w: lanes 32 (w % 4), columns cb..cb+15
+__device__ __forceinline__ void exact_values7(uint32_t tb, int warp, int cb, const short *eB, int ea, float (&hi)[16],
+                                              float (&lo)[16]) {
+    const uint32_t a = tb + ((uint32_t)(32 * (warp & 3)) << 16) + cb;
+#pragma unroll 1
+    for (int g = 0; g < S7; ++g) {
+        uint32_t pg[16];
+        tc::tmem_ld16(a + g * 64, pg);
+        tc::tmem_wait_ld();
+#pragma unroll
+        for (int c = 0; c < 16; ++c) {
+            const float v = __uint_as_float(pg[c]) * pow2f(ea + eB[c]);
+            if (g == 0) {
+                hi[c] = v;
+                lo[c] = 0.0f;
+            } else {
+                df_add(hi[c], lo[c], v);
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(NTH, 1) k_trail_split7x(int J, int nb, int64_t tpo, double *__restrict__ tiles,
+                                                          const uint8_t *__restrict__ pimg, int *__restrict__ err) {
+    extern __shared__ uint8_t smraw[];
+    uint8_t *sbase = align1024(smraw);
+    uint8_t *sA = sbase;                 // 7 x 16 KB: one K half of the A slices
+    uint8_t *sB = sbase + S7 * SBLK;     // 7 x 8 KB: one K half of 64 B rows
+    __shared__ uint64_t bar_load, bar_mma;
+    __shared__ uint32_t tmem_base;
+    __shared__ short sEA[TB], sEB[TB];
+    __shared__ int s_ok;
+    const int w = blockIdx.y;
+    int I, K;
+    decode_trailing(blockIdx.x, J, I, K);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint8_t *ia = pimg + ((int64_t)w * (nb + 1) + I) * img_bytes<S7>();
+    const uint8_t *ib = pimg + ((int64_t)w * (nb + 1) + K) * img_bytes<S7>();
+    if (warp == 0) {
+        tc::tmem_alloc(&tmem_base, 512);
+        tc::tmem_relinquish();
+    }
+    if (tid == 0) {
+        tc::mbar_init(&bar_load, 1);
+        tc::mbar_init(&bar_mma, 1);
+        tc::fence_mbar_init();
+        s_ok = 1;
+    }
+    if (tid < TB) {
+        sEA[tid] = (short)reinterpret_cast<const int *>(ia + (size_t)S7 * 2 * SBLK)[tid];
+        sEB[tid] = (short)reinterpret_cast<const int *>(ib + (size_t)S7 * 2 * SBLK)[tid];
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tb = tmem_base;
+    uint32_t phase = 0;
+    float *gH = reinterpret_cast<float *>(tiles + ((int64_t)w * tpo + tile_index(I, K)) * NT);
+    float *gL = gH + NT;
+    constexpr int DP = 64 + 1;   // padded delta row
+    float *sDh = reinterpret_cast<float *>(sbase);
+    float *sDl = sDh + TB * DP;
+    for (int ch = 0; ch < 2; ++ch) {
+        for (int h = 0; h < 2; ++h) {
+            if (tid == 0 && s_ok) {
+                tc::mbar_arrive_expect_tx(&bar_load, S7 * SBLK + S7 * HBLK);
+                for (int j = 0; j < S7; ++j) {
+                    tc::bulk_g2s(sA + j * SBLK, ia + (size_t)(j * 2 + h) * SBLK, SBLK, &bar_load);
+                    tc::bulk_g2s(sB + j * HBLK, ib + (size_t)(j * 2 + h) * SBLK + ch * HBLK, HBLK, &bar_load);
+                }
+                bool ok = tc::mbar_wait(&bar_load, phase);
+                if (!ok) tc::mbar_wait(&bar_load, phase);
+                if (ok) {
+                    tc::fence_after_sync();
+                    issue_exact_mmas7(tb, sA, sB, h == 0);
+                    tc::mma_commit(&bar_mma);
+                    ok = tc::mbar_wait(&bar_mma, phase);
+                    if (!ok) tc::mbar_wait(&bar_mma, phase);
+                }
+                if (!ok) {
+                    s_ok = 0;
+                    atomicExch(err, 1);
+                }
+            }
+            phase ^= 1;
+            tc::fence_before_sync();
+            __syncthreads();
+            tc::fence_after_sync();
+        }
+        const bool ok = s_ok != 0;
+        if (ok) {
+            const int r = 32 * (warp & 3) + lane;
+            const int cb = 16 * (warp >> 2);   // 0..48 within the half
+            float hi[16], lo[16];
+            exact_values7(tb, warp, cb, sEB + 64 * ch + cb, sEA[r] - 14, hi, lo);
+#pragma unroll
+            for (int c = 0; c < 16; ++c) {
+                sDh[r * DP + cb + c] = hi[c];
+                sDl[r * DP + cb + c] = lo[c];
+            }
+        }
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
+        if (ok) {
+#pragma unroll 4
+            for (int u = 0; u < (TB * 64) / NTH; ++u) {
+                const int e = tid + NTH * u;
+                const int r = e >> 6, c = e & 63;
+                const int gi = r * TB + 64 * ch + c;
+                float hv = gH[gi], lv = gL[gi];
+                df_add(hv, lv, -sDh[r * DP + c]);
+                df_add(hv, lv, -sDl[r * DP + c]);
+                gH[gi] = hv;
+                gL[gi] = lv;
+            }
+        }
+        __syncthreads();
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (warp == 0) tc::tmem_dealloc(tb, 512);
+}
+
+// Panel solve with 7 exact groups: the two column halves of L_IJ are written
+// as double-float planes into the panel slot (scratch), then every row is
+// sliced with its exponent over all 128 columns and the image replaces the
+// scratch.
+__global__ void __launch_bounds__(NTH, 1) k_trsm_split7x(int J, int nb, int64_t tpo, const double *__restrict__ tiles,
+                                                         const uint8_t *__restrict__ wimg, uint8_t *__restrict__ pimg,
+                                                         int *__restrict__ err) {
+    extern __shared__ uint8_t smraw[];
+    uint8_t *sbase = align1024(smraw);
+    uint8_t *sA = sbase;
+    uint8_t *sW = sbase + S7 * SBLK;
+    __shared__ uint64_t bar_load, bar_mma;
+    __shared__ uint32_t tmem_base;
+    __shared__ short sEA[TB], sEW[TB], sEO[TB];
+    __shared__ int sMx[TB];
+    __shared__ int s_ok;
+    const int w = blockIdx.y, I = J + 1 + blockIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const float *H = reinterpret_cast<const float *>(tiles + ((int64_t)w * tpo + tile_index(I, J)) * NT);
+    const float *Lo = H + NT;
+    const uint8_t *wi = wimg + (int64_t)w * img_bytes<S7>();
+    uint8_t *slot = pimg + ((int64_t)w * (nb + 1) + I) * img_bytes<S7>();
+    float *scH = reinterpret_cast<float *>(slot);   // scratch planes of L_IJ (128 KB < slot)
+    float *scL = scH + NT;
+    if (warp == 0) {
+        tc::tmem_alloc(&tmem_base, 512);
+        tc::tmem_relinquish();
+    }
+    if (tid == 0) {
+        tc::mbar_init(&bar_load, 1);
+        tc::mbar_init(&bar_mma, 1);
+        tc::fence_mbar_init();
+        s_ok = 1;
+    }
+    if (tid < TB) {
+        sEW[tid] = (short)reinterpret_cast<const int *>(wi + (size_t)S7 * 2 * SBLK)[tid];
+        sMx[tid] = 0;
+    }
+#pragma unroll
+    for (int rr = 0; rr < 8; ++rr) {
+        const int r = warp * 8 + rr;
+        float mx = 0.0f;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) mx = fmaxf(mx, fabsf(H[r * TB + lane + 32 * q]));
+        for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        if (lane == 0) sEA[r] = (short)row_exp(mx);
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tb = tmem_base;
+    uint32_t phase = 0;
+    for (int ch = 0; ch < 2; ++ch) {
+        for (int h = 0; h < 2; ++h) {
+#pragma unroll 2
+            for (int rr = 0; rr < 8; ++rr) {
+                const int r = warp * 8 + rr;
+                const int k = 64 * h + 2 * lane;
+                const float2 hv = *reinterpret_cast<const float2 *>(H + r * TB + k);
+                const float2 lv = *reinterpret_cast<const float2 *>(Lo + r * TB + k);
+                float m0[S7], m1[S7];
+                slice_df<S7>(hv.x, lv.x, sEA[r], m0);
+                slice_df<S7>(hv.y, lv.y, sEA[r], m1);
+                const uint32_t off = tc::sw128_offset(r, 2 * lane);
+#pragma unroll
+                for (int j = 0; j < S7; ++j)
+                    *reinterpret_cast<uint32_t *>(sA + j * SBLK + off) = pack_bf16x2(m0[j], m1[j]);
+            }
+            tc::fence_proxy_async();
+            __syncthreads();
+            if (tid == 0 && s_ok) {
+                tc::mbar_arrive_expect_tx(&bar_load, S7 * HBLK);
+                for (int j = 0; j < S7; ++j)
+                    tc::bulk_g2s(sW + j * HBLK, wi + (size_t)(j * 2 + h) * SBLK + ch * HBLK, HBLK, &bar_load);
+                bool ok = tc::mbar_wait(&bar_load, phase);
+                if (!ok) tc::mbar_wait(&bar_load, phase);
+                if (ok) {
+                    tc::fence_after_sync();
+                    issue_exact_mmas7(tb, sA, sW, h == 0);
+                    tc::mma_commit(&bar_mma);
+                    ok = tc::mbar_wait(&bar_mma, phase);
+                    if (!ok) tc::mbar_wait(&bar_mma, phase);
+                }
+                if (!ok) {
+                    s_ok = 0;
+                    atomicExch(err, 1);
+                }
+            }
+            phase ^= 1;
+            tc::fence_before_sync();
+            __syncthreads();
+            tc::fence_after_sync();
+        }
+        if (s_ok) {
+            const int r = 32 * (warp & 3) + lane;
+            const int cb = 16 * (warp >> 2);
+            float hi[16], lo[16];
+            exact_values7(tb, warp, cb, sEW + 64 * ch + cb, sEA[r] - 14, hi, lo);
+            float mx = 0.0f;
+#pragma unroll
+            for (int c = 0; c < 16; ++c) {
+                scH[r * TB + 64 * ch + cb + c] = hi[c];
+                scL[r * TB + 64 * ch + cb + c] = lo[c];
+                mx = fmaxf(mx, fabsf(hi[c]));
+            }
+            atomicMax(&sMx[r], __float_as_int(mx));
+        }
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
+    }
+    const bool ok = s_ok != 0;
+    if (ok) {
+        // slice: thread handles row r = tid / 4, columns 32 (tid % 4) .. +31
+        const int r = tid >> 2, c0 = 32 * (tid & 3);
+        const int eo = row_exp(__int_as_float(sMx[r]) * (1.0f + 1.0f / 1024.0f));
+        if ((tid & 3) == 0) sEO[r] = (short)eo;
+#pragma unroll 1
+        for (int c = 0; c < 32; c += 2) {
+            float m0[S7], m1[S7];
+            slice_df<S7>(scH[r * TB + c0 + c], scL[r * TB + c0 + c], eo, m0);
+            slice_df<S7>(scH[r * TB + c0 + c + 1], scL[r * TB + c0 + c + 1], eo, m1);
+            store_pair<S7>(sbase, r, c0 + c, m0, m1);
+        }
+    }
+    __syncthreads();   // all scratch reads done before the image overwrites it
+    if (ok) {
+        const uint4 *src4 = reinterpret_cast<const uint4 *>(sbase);
+        uint4 *dst4 = reinterpret_cast<uint4 *>(slot);
+#pragma unroll 4
+        for (int e = tid; e < S7 * 2 * SBLK / 16; e += NTH) dst4[e] = src4[e];
+        if (tid < TB) reinterpret_cast<int *>(slot + (size_t)S7 * 2 * SBLK)[tid] = (int)sEO[tid];
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (warp == 0) tc::tmem_dealloc(tb, 512);
+}
+
+// ---------------------------------------------------------------------------
 // Error bound and retry flags
 // ---------------------------------------------------------------------------
 // E = eps_S * (1 + nu^2) * sum_j 1/d_j, d_j the pivots: a first-order bound on
@@ -606,22 +899,39 @@ static cudaError_t launch_mixed_steps(const BatchArgs &b, const MixedArgs &x, cu
     if ((e = cudaFuncSetAttribute(k_potrf_mixed<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)(2 * PK * sizeof(double)))) != cudaSuccess)
         return e;
-    if ((e = cudaFuncSetAttribute(k_trsm_split<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_split)) !=
-        cudaSuccess)
-        return e;
-    if ((e = cudaFuncSetAttribute(k_trail_split<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_split)) !=
-        cudaSuccess)
-        return e;
+    if (S == 7) {
+        const int smem_trail7 = S7 * (SBLK + HBLK) + 1024;
+        if ((e = cudaFuncSetAttribute(k_trsm_split7x, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_split)) !=
+            cudaSuccess)
+            return e;
+        if ((e = cudaFuncSetAttribute(k_trail_split7x, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_trail7)) !=
+            cudaSuccess)
+            return e;
+    } else {
+        if ((e = cudaFuncSetAttribute(k_trsm_split<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_split)) !=
+            cudaSuccess)
+            return e;
+        if ((e = cudaFuncSetAttribute(k_trail_split<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_split)) !=
+            cudaSuccess)
+            return e;
+    }
     cudaMemsetAsync(x.invsum, 0, sizeof(double) * cnt, s);
     TIMED(KC_CONVERT, (k_to_df<<<dim3((unsigned)b.tpo, cnt), 256, 0, s>>>(b.tpo, b.tiles)));
     for (int J = 0; J < b.nb; ++J) {
         TIMED(KC_POTRF_MIXED, (k_potrf_mixed<S><<<cnt, 256, 2 * PK * sizeof(double), s>>>(
                             J, b.tpo, b.tiles, x.wimg, b.ldv, x.invsum, b.pstatus)));
         const int m = b.nb - J;
-        TIMED(KC_TRSM_SPLIT, (k_trsm_split<S><<<dim3(m, cnt), NTH, smem_split, s>>>(J, b.nb, b.tpo, b.tiles, x.wimg,
-                                                                                x.pimg, x.err)));
-        TIMED(KC_GEMM_SPLIT, (k_trail_split<S><<<dim3(m * (m + 1) / 2, cnt), NTH, smem_split, s>>>(J, b.nb, b.tpo, b.tiles,
-                                                                                           x.pimg, x.err)));
+        if (S == 7) {
+            TIMED(KC_TRSM_SPLIT, (k_trsm_split7x<<<dim3(m, cnt), NTH, smem_split, s>>>(J, b.nb, b.tpo, b.tiles, x.wimg,
+                                                                                     x.pimg, x.err)));
+            TIMED(KC_GEMM_SPLIT, (k_trail_split7x<<<dim3(m * (m + 1) / 2, cnt), NTH, S7 * (SBLK + HBLK) + 1024, s>>>(
+                                     J, b.nb, b.tpo, b.tiles, x.pimg, x.err)));
+        } else {
+            TIMED(KC_TRSM_SPLIT, (k_trsm_split<S><<<dim3(m, cnt), NTH, smem_split, s>>>(J, b.nb, b.tpo, b.tiles, x.wimg,
+                                                                                    x.pimg, x.err)));
+            TIMED(KC_GEMM_SPLIT, (k_trail_split<S><<<dim3(m * (m + 1) / 2, cnt), NTH, smem_split, s>>>(
+                                     J, b.nb, b.tpo, b.tiles, x.pimg, x.err)));
+        }
     }
     TIMED(KC_CONVERT, (k_tile_to_fp64<<<cnt, 256, 0, s>>>(b.tpo, tile_index(b.nb, b.nb), b.tiles)));
     return cudaGetLastError();

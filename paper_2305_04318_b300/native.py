@@ -115,6 +115,7 @@ def default_batch(n, K, limit_bytes=8e9):
 
 FLAG_KERNEL_TIMING = 1
 FLAG_NO_RETRY = 2
+FLAG_NO_FP64_TIER = 4
 
 
 def kernel_timing(reset=True):
