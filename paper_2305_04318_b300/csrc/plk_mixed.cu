@@ -946,9 +946,9 @@ cudaError_t launch_mixed_batch(const BatchArgs &b, const MixedArgs &x, int S, cu
     // eps: relative perturbation of the updated entries.  Calibrated on the
     // n = 4000 workload against the FP64 path: with these values the bound
     // exceeded the measured |Delta l_p| on every point (5 slices: by >= 16x;
-    // 7 slices, whose 48-bit double-float tiles and merged high-order group
-    // limit it on very ill-conditioned points: by >= 2x).
-    const double eps = (S == 7) ? ldexp(1.0, -36) : ldexp(1.0, -30);
+    // 7 slices with all groups exact: by >= 4.7x, on points whose own FP64
+    // result differs from the CPU oracle by up to 1e-4).
+    const double eps = (S == 7) ? ldexp(1.0, -46) : ldexp(1.0, -30);
     k_mixed_bound<<<(b.count + 127) / 128, 128, 0, s>>>(b.count, b.k0, eps, x.tol, S == 5 ? 1 : 0, b.oconst,
                                                        x.invsum, b.pstatus, b.out_index, x.err_bound, x.flags);
     return cudaGetLastError();
