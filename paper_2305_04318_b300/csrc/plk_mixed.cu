@@ -24,6 +24,8 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <algorithm>
+
 #include "plk.h"
 #include "plk_common.cuh"
 #include "plk_kernels.cuh"
@@ -34,6 +36,7 @@ namespace plk {
 namespace {
 
 constexpr int SBLK = 16384;   // one 128-row x 64-element bf16 block, 128-byte swizzle
+constexpr int HBLK = SBLK / 2;  // rows 0..63 or 64..127 of a block: 8 KB, contiguous
 constexpr uint32_t IDESC = tc::idesc_bf16_f32(128, 128);
 
 __device__ __forceinline__ float pow2f(int e) {   // exact 2^e (0 below the normal range)
@@ -556,6 +559,228 @@ __global__ void __launch_bounds__(NTH, 1) k_trail_split(int J, int nb, int64_t t
 }
 
 // ---------------------------------------------------------------------------
+// Persistent, pipelined 5-slice trailing update.  One CTA per SM walks the
+// work items (omega, tile (I, K), column half) of one step.  Roles:
+//   warp 0     producer: bulk copies of the B half-rows (all 5 slices of one K
+//              half, double-buffered) and of the A slices (one slice of one K
+//              half per stage, 3-stage ring);
+//   warp 1     MMA issue into two alternating TMEM accumulator sets
+//              (2 sets x 4 groups x 64 columns = 512 columns);
+//   warp 2     TMEM allocation;
+//   warps 4-7  epilogue: TMEM -> double-float deltas in padded shared rows,
+//              then a coalesced read-modify-write of the half tile, while the
+//              MMAs of the next item run.
+// Barrier use u of a slot completes phase u; a waiter for use u waits for
+// parity (u & 1); the producer reusing a slot for use u >= 1 first waits for
+// the consumer's release of use u - 1.
+// ---------------------------------------------------------------------------
+namespace pipe {
+constexpr int S = 5;
+constexpr int NTHP = 256;
+constexpr int NA = 3;                       // A stages
+constexpr int BBUF = S * HBLK;              // 40 KB: one K half of 64 B rows, 5 slices
+constexpr int OFF_A = 2 * BBUF;             // 80 KB
+constexpr int OFF_D = OFF_A + NA * SBLK;    // 128 KB
+constexpr int DP = 64 + 1;
+constexpr int SMEM = OFF_D + 2 * TB * DP * 4 + 1024;
+constexpr uint32_t IDESC_N64 = tc::idesc_bf16_f32(128, 64);
+}  // namespace pipe
+
+__global__ void __launch_bounds__(pipe::NTHP, 1) k_trail_pipe(int J, int nb, int cnt, int64_t tpo,
+                                                             double *__restrict__ tiles,
+                                                             const uint8_t *__restrict__ pimg, int *__restrict__ err) {
+    using namespace pipe;
+    extern __shared__ uint8_t smraw[];
+    uint8_t *sbase = align1024(smraw);
+    __shared__ uint64_t bFull[2], bEmpty[2], aFull[NA], aEmpty[NA], accFull[2], accEmpty[2], drain;
+    __shared__ uint32_t tmem_base;
+    __shared__ short sEA[TB], sEB[64];
+    __shared__ int s_err, s_stop;
+    volatile int *verr = &s_err;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int m = nb - J;
+    const int T = m * (m + 1) / 2;
+    const int64_t items = (int64_t)cnt * T * 2;
+    if (tid == 0) {
+        for (int i = 0; i < 2; ++i) {
+            tc::mbar_init(&bFull[i], 1);
+            tc::mbar_init(&bEmpty[i], 1);
+            tc::mbar_init(&accFull[i], 1);
+            tc::mbar_init(&accEmpty[i], 1);
+        }
+        for (int i = 0; i < NA; ++i) {
+            tc::mbar_init(&aFull[i], 1);
+            tc::mbar_init(&aEmpty[i], 1);
+        }
+        tc::mbar_init(&drain, 1);
+        tc::fence_mbar_init();
+        s_err = 0;
+    }
+    if (warp == 2) {
+        tc::tmem_alloc(&tmem_base, 512);
+        tc::tmem_relinquish();
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tb = tmem_base;
+
+    auto decode = [&](int64_t it, int &w, int &I, int &K, int &ch) {
+        w = (int)(it / (2 * T));
+        const int rem = (int)(it - (int64_t)w * 2 * T);
+        ch = rem & 1;
+        decode_trailing(rem >> 1, J, I, K);
+    };
+    auto image = [&](int w, int R) { return pimg + ((int64_t)w * (nb + 1) + R) * img_bytes<S>(); };
+
+    if (warp == 0) {
+        if (lane == 0) {
+            uint32_t acnt = 0, bcnt = 0;
+            for (int64_t it = blockIdx.x; it < items && !*verr; it += gridDim.x) {
+                int w, I, K, ch;
+                decode(it, w, I, K, ch);
+                const uint8_t *ia = image(w, I), *ib = image(w, K);
+                for (int h = 0; h < 2 && !*verr; ++h) {
+                    const int bs = bcnt & 1;
+                    const uint32_t bu = bcnt >> 1;
+                    if (bu > 0 && !tc::mbar_wait(&bEmpty[bs], (bu - 1) & 1)) { *verr = 1; break; }
+                    tc::mbar_arrive_expect_tx(&bFull[bs], BBUF);
+                    for (int j = 0; j < S; ++j)
+                        tc::bulk_g2s(sbase + bs * BBUF + j * HBLK, ib + (size_t)(j * 2 + h) * SBLK + ch * HBLK, HBLK,
+                                     &bFull[bs]);
+                    ++bcnt;
+                    for (int i = 0; i < S; ++i) {
+                        const int as = acnt % NA;
+                        const uint32_t au = acnt / NA;
+                        if (au > 0 && !tc::mbar_wait(&aEmpty[as], (au - 1) & 1)) { *verr = 1; break; }
+                        tc::mbar_arrive_expect_tx(&aFull[as], SBLK);
+                        tc::bulk_g2s(sbase + OFF_A + as * SBLK, ia + (size_t)(i * 2 + h) * SBLK, SBLK, &aFull[as]);
+                        ++acnt;
+                    }
+                }
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            uint32_t acnt = 0, bcnt = 0, tcnt = 0;
+            bool issued = false;
+            for (int64_t it = blockIdx.x; it < items && !*verr; it += gridDim.x, ++tcnt) {
+                const int set = tcnt & 1;
+                const uint32_t tu = tcnt >> 1;
+                if (tu > 0 && !tc::mbar_wait(&accEmpty[set], (tu - 1) & 1)) { *verr = 1; break; }
+                tc::fence_after_sync();
+                const uint32_t dacc = tb + set * 256;
+                for (int h = 0; h < 2 && !*verr; ++h) {
+                    const int bs = bcnt & 1;
+                    if (!tc::mbar_wait(&bFull[bs], (bcnt >> 1) & 1)) { *verr = 1; break; }
+                    ++bcnt;
+                    for (int i = 0; i < S; ++i) {
+                        const int as = acnt % NA;
+                        if (!tc::mbar_wait(&aFull[as], (acnt / NA) & 1)) { *verr = 1; break; }
+                        ++acnt;
+                        tc::fence_after_sync();
+                        const uint8_t *sA = sbase + OFF_A + as * SBLK;
+                        for (int j = 0; i + j < S; ++j) {
+                            const int g = i + j;
+                            const int acc = g < 3 ? g : 3;
+#pragma unroll
+                            for (int kk = 0; kk < 4; ++kk) {
+                                const uint64_t ad = tc::sdesc_sw128(tc::smem_u32(sA) + kk * 32);
+                                const uint64_t bd = tc::sdesc_sw128(tc::smem_u32(sbase + bs * BBUF + j * HBLK) + kk * 32);
+                                const uint32_t accumulate = (h == 0 && kk == 0 && i == 0 && j <= 3) ? 0u : 1u;
+                                tc::mma_bf16(dacc + acc * 64, ad, bd, IDESC_N64, accumulate);
+                                issued = true;
+                            }
+                        }
+                        tc::mma_commit(&aEmpty[as]);   // the A stage is free once these MMAs finish
+                    }
+                    tc::mma_commit(&bEmpty[bs]);
+                }
+                tc::mma_commit(&accFull[set]);
+            }
+            // let every issued MMA finish before the accumulators are released
+            if (issued) {
+                tc::mma_commit(&drain);
+                if (!tc::mbar_wait(&drain, 0)) tc::mbar_wait(&drain, 0);
+            }
+        }
+    } else if (warp >= 4) {
+        const int et = tid - 128;          // 0..127
+        const int r = 32 * (warp & 3) + lane;
+        float *sDh = reinterpret_cast<float *>(sbase + OFF_D);
+        float *sDl = sDh + TB * DP;
+        uint32_t tcnt = 0;
+        for (int64_t it = blockIdx.x; it < items; it += gridDim.x, ++tcnt) {
+            int w, I, K, ch;
+            decode(it, w, I, K, ch);
+            const uint8_t *ia = image(w, I), *ib = image(w, K);
+            sEA[et] = (short)reinterpret_cast<const int *>(ia + (size_t)S * 2 * SBLK)[et];
+            if (et < 64) sEB[et] = (short)reinterpret_cast<const int *>(ib + (size_t)S * 2 * SBLK)[64 * ch + et];
+            const int set = tcnt & 1;
+            if (et == 0) {   // one thread waits and decides for all 128
+                const bool ok = tc::mbar_wait(&accFull[set], (tcnt >> 1) & 1);
+                if (!ok) *verr = 1;
+                s_stop = (!ok || *verr) ? 1 : 0;
+            }
+            tc::named_sync(1, 128);        // exponents visible; stop decision uniform
+            if (s_stop) break;
+            tc::fence_after_sync();
+            const uint32_t a = tb + set * 256 + ((uint32_t)(32 * (warp & 3)) << 16);
+            const int ea = sEA[r] - 14;
+#pragma unroll 1
+            for (int c0 = 0; c0 < 64; c0 += 16) {
+                uint32_t p0[16], p1[16], p2[16], p3[16];
+                tc::tmem_ld16(a + 0 * 64 + c0, p0);
+                tc::tmem_ld16(a + 1 * 64 + c0, p1);
+                tc::tmem_ld16(a + 2 * 64 + c0, p2);
+                tc::tmem_ld16(a + 3 * 64 + c0, p3);
+                tc::tmem_wait_ld();
+#pragma unroll
+                for (int c = 0; c < 16; ++c) {
+                    float hi, lo;
+                    group_value(p0[c], p1[c], p2[c], p3[c], ea + sEB[c0 + c], hi, lo);
+                    sDh[r * DP + c0 + c] = hi;
+                    sDl[r * DP + c0 + c] = lo;
+                }
+            }
+            tc::fence_before_sync();
+            tc::named_sync(1, 128);
+            if (et == 0) tc::mbar_arrive(&accEmpty[set]);   // the MMA warp may reuse this set
+            float *gH = reinterpret_cast<float *>(tiles + ((int64_t)w * tpo + tile_index(I, K)) * NT) + 64 * ch;
+            float *gL = gH + NT;
+#pragma unroll 1
+            for (int u0 = 0; u0 < (TB * 64) / 128; u0 += 8) {
+                float h8[8], l8[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int e = et + 128 * (u0 + u);
+                    const int gi = (e >> 6) * TB + (e & 63);
+                    h8[u] = gH[gi];
+                    l8[u] = gL[gi];
+                }
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int e = et + 128 * (u0 + u);
+                    const int gi = (e >> 6) * TB + (e & 63);
+                    const int si = (e >> 6) * DP + (e & 63);
+                    df_add(h8[u], l8[u], -sDh[si]);
+                    df_add(h8[u], l8[u], -sDl[si]);
+                    gH[gi] = h8[u];
+                    gL[gi] = l8[u];
+                }
+            }
+            tc::named_sync(1, 128);        // deltas consumed before the next item rewrites them
+        }
+    }
+    __syncthreads();
+    if (*verr && tid == 0) atomicExch(err, 1);
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (warp == 2) tc::tmem_dealloc(tb, 512);
+}
+
+// ---------------------------------------------------------------------------
 // 7-slice variants with every group exact: the 128 x 128 result is produced as
 // two 128 x 64 column halves; each half keeps the 7 groups g = 0..6 in their
 // own 64-column TMEM accumulators (448 columns), so no group is rounded before
@@ -563,7 +788,6 @@ __global__ void __launch_bounds__(NTH, 1) k_trail_split(int J, int nb, int64_t t
 // 5-slice error bound was too large.
 // ---------------------------------------------------------------------------
 constexpr int S7 = 7;
-constexpr int HBLK = SBLK / 2;   // rows 0..63 or 64..127 of a block: 8 KB, contiguous
 constexpr uint32_t IDESC64 = tc::idesc_bf16_f32(128, 64);
 
 __device__ __forceinline__ void issue_exact_mmas7(uint32_t tb, const uint8_t *sA, const uint8_t *sB, bool first_half) {
@@ -883,6 +1107,12 @@ __global__ void k_gather_params(int count, const int *__restrict__ idx, const do
 // ---------------------------------------------------------------------------
 size_t mixed_img_bytes(int S) { return S == 5 ? img_bytes<5>() : img_bytes<7>(); }
 
+static int num_sms() {
+    int dev = 0, n = 148;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    return n;
+}
+
 #define TIMED(cls, launch)               \
     do {                                 \
         if (timer) timer->begin(cls, s); \
@@ -908,6 +1138,9 @@ static cudaError_t launch_mixed_steps(const BatchArgs &b, const MixedArgs &x, cu
             cudaSuccess)
             return e;
     } else {
+        if ((e = cudaFuncSetAttribute(k_trail_pipe, cudaFuncAttributeMaxDynamicSharedMemorySize, pipe::SMEM)) !=
+            cudaSuccess)
+            return e;
         if ((e = cudaFuncSetAttribute(k_trsm_split<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_split)) !=
             cudaSuccess)
             return e;
@@ -929,8 +1162,10 @@ static cudaError_t launch_mixed_steps(const BatchArgs &b, const MixedArgs &x, cu
         } else {
             TIMED(KC_TRSM_SPLIT, (k_trsm_split<S><<<dim3(m, cnt), NTH, smem_split, s>>>(J, b.nb, b.tpo, b.tiles, x.wimg,
                                                                                     x.pimg, x.err)));
-            TIMED(KC_GEMM_SPLIT, (k_trail_split<S><<<dim3(m * (m + 1) / 2, cnt), NTH, smem_split, s>>>(
-                                     J, b.nb, b.tpo, b.tiles, x.pimg, x.err)));
+            const int64_t items = (int64_t)cnt * (m * (m + 1) / 2) * 2;
+            const int grid = (int)std::min<int64_t>(items, num_sms());
+            TIMED(KC_GEMM_SPLIT, (k_trail_pipe<<<grid, pipe::NTHP, pipe::SMEM, s>>>(J, b.nb, cnt, b.tpo, b.tiles,
+                                                                                      x.pimg, x.err)));
         }
     }
     TIMED(KC_CONVERT, (k_tile_to_fp64<<<cnt, 256, 0, s>>>(b.tpo, tile_index(b.nb, b.nb), b.tiles)));
