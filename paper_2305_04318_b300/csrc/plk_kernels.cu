@@ -587,7 +587,8 @@ __global__ void k_profile_ci(const double *__restrict__ grid, const double *__re
 const char *kernel_class_name(int c) {
     static const char *names[KC_COUNT] = {"boxcox", "omega_prep", "matern_table", "build", "potrf",
                                           "panel_trsm", "trailing_gemm", "finalize", "profile", "convert",
-                                          "potrf_mixed", "panel_split", "trailing_split"};
+                                          "potrf_mixed", "panel_split", "trailing_split", "panel_split7",
+                                          "trailing_split7"};
     return (c >= 0 && c < KC_COUNT) ? names[c] : "";
 }
 

@@ -7,7 +7,7 @@ namespace plk {
 
 // Kernel classes for the optional per-launch event timing.
 enum KernelClass { KC_BOXCOX = 0, KC_PREP, KC_TABLE, KC_BUILD, KC_POTRF, KC_TRSM, KC_GEMM, KC_FINAL,
-                   KC_PROFILE, KC_CONVERT, KC_POTRF_MIXED, KC_TRSM_SPLIT, KC_GEMM_SPLIT, KC_COUNT };
+                   KC_PROFILE, KC_CONVERT, KC_POTRF_MIXED, KC_TRSM_SPLIT, KC_GEMM_SPLIT, KC_TRSM_SPLIT7, KC_GEMM_SPLIT7, KC_COUNT };
 const char *kernel_class_name(int c);
 
 // Records a CUDA event pair around a launch on its stream (see plk_api.cu).

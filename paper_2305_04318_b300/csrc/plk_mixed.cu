@@ -576,7 +576,8 @@ __global__ void __launch_bounds__(NTH, 1) k_trail_split(int J, int nb, int64_t t
 // ---------------------------------------------------------------------------
 namespace pipe {
 constexpr int S = 5;
-constexpr int NTHP = 256;
+constexpr int NTHP = 384;                   // warps 0-3 roles, warps 4-11 epilogue
+constexpr int NEPI = NTHP - 128;
 constexpr int NA = 3;                       // A stages
 constexpr int BBUF = S * HBLK;              // 40 KB: one K half of 64 B rows, 5 slices
 constexpr int OFF_A = 2 * BBUF;             // 80 KB
@@ -705,8 +706,9 @@ __global__ void __launch_bounds__(pipe::NTHP, 1) k_trail_pipe(int J, int nb, int
             }
         }
     } else if (warp >= 4) {
-        const int et = tid - 128;          // 0..127
+        const int et = tid - 128;          // 0..NEPI-1
         const int r = 32 * (warp & 3) + lane;
+        const int cpart = (warp - 4) >> 2;   // columns 32 cpart .. +31 of the half
         float *sDh = reinterpret_cast<float *>(sbase + OFF_D);
         float *sDl = sDh + TB * DP;
         uint32_t tcnt = 0;
@@ -714,21 +716,21 @@ __global__ void __launch_bounds__(pipe::NTHP, 1) k_trail_pipe(int J, int nb, int
             int w, I, K, ch;
             decode(it, w, I, K, ch);
             const uint8_t *ia = image(w, I), *ib = image(w, K);
-            sEA[et] = (short)reinterpret_cast<const int *>(ia + (size_t)S * 2 * SBLK)[et];
-            if (et < 64) sEB[et] = (short)reinterpret_cast<const int *>(ib + (size_t)S * 2 * SBLK)[64 * ch + et];
+            if (et < TB) sEA[et] = (short)reinterpret_cast<const int *>(ia + (size_t)S * 2 * SBLK)[et];
+            else if (et < TB + 64) sEB[et - TB] = (short)reinterpret_cast<const int *>(ib + (size_t)S * 2 * SBLK)[64 * ch + et - TB];
             const int set = tcnt & 1;
             if (et == 0) {   // one thread waits and decides for all 128
                 const bool ok = tc::mbar_wait(&accFull[set], (tcnt >> 1) & 1);
                 if (!ok) *verr = 1;
                 s_stop = (!ok || *verr) ? 1 : 0;
             }
-            tc::named_sync(1, 128);        // exponents visible; stop decision uniform
+            tc::named_sync(1, NEPI);       // exponents visible; stop decision uniform
             if (s_stop) break;
             tc::fence_after_sync();
             const uint32_t a = tb + set * 256 + ((uint32_t)(32 * (warp & 3)) << 16);
             const int ea = sEA[r] - 14;
 #pragma unroll 1
-            for (int c0 = 0; c0 < 64; c0 += 16) {
+            for (int c0 = 32 * cpart; c0 < 32 * cpart + 32; c0 += 16) {
                 uint32_t p0[16], p1[16], p2[16], p3[16];
                 tc::tmem_ld16(a + 0 * 64 + c0, p0);
                 tc::tmem_ld16(a + 1 * 64 + c0, p1);
@@ -744,23 +746,23 @@ __global__ void __launch_bounds__(pipe::NTHP, 1) k_trail_pipe(int J, int nb, int
                 }
             }
             tc::fence_before_sync();
-            tc::named_sync(1, 128);
+            tc::named_sync(1, NEPI);
             if (et == 0) tc::mbar_arrive(&accEmpty[set]);   // the MMA warp may reuse this set
             float *gH = reinterpret_cast<float *>(tiles + ((int64_t)w * tpo + tile_index(I, K)) * NT) + 64 * ch;
             float *gL = gH + NT;
 #pragma unroll 1
-            for (int u0 = 0; u0 < (TB * 64) / 128; u0 += 8) {
-                float h8[8], l8[8];
+            for (int u0 = 0; u0 < (TB * 64) / NEPI; u0 += 16) {
+                float h8[16], l8[16];
 #pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    const int e = et + 128 * (u0 + u);
+                for (int u = 0; u < 16; ++u) {
+                    const int e = et + NEPI * (u0 + u);
                     const int gi = (e >> 6) * TB + (e & 63);
                     h8[u] = gH[gi];
                     l8[u] = gL[gi];
                 }
 #pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    const int e = et + 128 * (u0 + u);
+                for (int u = 0; u < 16; ++u) {
+                    const int e = et + NEPI * (u0 + u);
                     const int gi = (e >> 6) * TB + (e & 63);
                     const int si = (e >> 6) * DP + (e & 63);
                     df_add(h8[u], l8[u], -sDh[si]);
@@ -769,7 +771,7 @@ __global__ void __launch_bounds__(pipe::NTHP, 1) k_trail_pipe(int J, int nb, int
                     gL[gi] = l8[u];
                 }
             }
-            tc::named_sync(1, 128);        // deltas consumed before the next item rewrites them
+            tc::named_sync(1, NEPI);       // deltas consumed before the next item rewrites them
         }
     }
     __syncthreads();
@@ -1155,9 +1157,9 @@ static cudaError_t launch_mixed_steps(const BatchArgs &b, const MixedArgs &x, cu
                             J, b.tpo, b.tiles, x.wimg, b.ldv, x.invsum, b.pstatus)));
         const int m = b.nb - J;
         if (S == 7) {
-            TIMED(KC_TRSM_SPLIT, (k_trsm_split7x<<<dim3(m, cnt), NTH, smem_split, s>>>(J, b.nb, b.tpo, b.tiles, x.wimg,
+            TIMED(KC_TRSM_SPLIT7, (k_trsm_split7x<<<dim3(m, cnt), NTH, smem_split, s>>>(J, b.nb, b.tpo, b.tiles, x.wimg,
                                                                                      x.pimg, x.err)));
-            TIMED(KC_GEMM_SPLIT, (k_trail_split7x<<<dim3(m * (m + 1) / 2, cnt), NTH, S7 * (SBLK + HBLK) + 1024, s>>>(
+            TIMED(KC_GEMM_SPLIT7, (k_trail_split7x<<<dim3(m * (m + 1) / 2, cnt), NTH, S7 * (SBLK + HBLK) + 1024, s>>>(
                                      J, b.nb, b.tpo, b.tiles, x.pimg, x.err)));
         } else {
             TIMED(KC_TRSM_SPLIT, (k_trsm_split<S><<<dim3(m, cnt), NTH, smem_split, s>>>(J, b.nb, b.tpo, b.tiles, x.wimg,
