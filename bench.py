@@ -49,7 +49,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="auto", choices=["auto", "fp64", "mixed"])
-    ap.add_argument("--batch", type=int, default=0, help="omega points per step (default: 512 mixed, 128 fp64)")
+    ap.add_argument("--batch", type=int, default=0, help="omega points per step (default: 592 = 4 x 148 mixed, 128 fp64)")
     ap.add_argument("--n", type=int, default=4000)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -439,7 +439,7 @@ def main():
         torch.cuda.empty_cache()
         return res
 
-    Bm = args.batch or (512 if head == "mixed" else 128)
+    Bm = args.batch or (592 if head == "mixed" else 128)   # mixed: 4 x 148 SMs per step
     main_res = measure(head, Bm, args.steps, args.warmup, True)
     fp64_res = None
     if head == "mixed":

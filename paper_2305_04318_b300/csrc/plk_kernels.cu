@@ -233,6 +233,27 @@ __device__ __forceinline__ double rho_table(const double *__restrict__ tab, doub
 // ---------------------------------------------------------------------------
 // Build of the bordered matrix tiles (Step 3 item 1)
 // ---------------------------------------------------------------------------
+// Double-float split of a double without FP64-pipe instructions: hi keeps the
+// sign, exponent and top 23 mantissa bits (truncated), lo the remaining 29 bits
+// rounded to 24 (hi + lo carries ~48 bits).  Values below 2^-100 become 0.
+__device__ __forceinline__ void split_df_bits(double v, float &hi, float &lo) {
+    const unsigned long long u = (unsigned long long)__double_as_longlong(v);
+    const int e = (int)((u >> 52) & 0x7ff) - 1023;
+    const unsigned int sgn = (unsigned int)(u >> 63) << 31;
+    if (e < -100 || e > 127) {   // (our values are in [-1e4, 1e4] or exactly 0)
+        hi = (e > 127) ? __int_as_float(sgn | 0x7f800000u) : 0.0f;
+        lo = 0.0f;
+        return;
+    }
+    const unsigned long long m = u & 0xFFFFFFFFFFFFFull;
+    hi = __int_as_float(sgn | ((unsigned int)(e + 127) << 23) | (unsigned int)(m >> 29));
+    const float r = __uint2float_rn((unsigned int)(m & 0x1FFFFFFFull));   // remainder, units of 2^(e-52)
+    const int es = e - 52;
+    const float sc = (es < -126) ? 0.0f : __int_as_float((es + 127) << 23);
+    lo = __int_as_float(__float_as_int(r * sc) | sgn);
+}
+
+template <bool DF>
 __global__ void __launch_bounds__(256) k_build(int nb, int64_t n, int64_t n_pad, int q, int64_t tpo,
                                                double *__restrict__ tiles,
                                                const double *__restrict__ oconst,
@@ -246,14 +267,26 @@ __global__ void __launch_bounds__(256) k_build(int nb, int64_t n, int64_t n_pad,
     while (I * (I + 1) / 2 > t) --I;
     const int J = t - I * (I + 1) / 2;
     double *T = tiles + ((int64_t)w * tpo + t) * NT;
+    float *TH = reinterpret_cast<float *>(T);   // double-float planes (DF)
+    float *TL = TH + NT;
     const int c = threadIdx.x & (TB - 1);
     const int r0 = threadIdx.x >> 7;
     const int64_t j = (int64_t)J * TB + c;
+    auto put = [&](int r, double v) {
+        if (DF) {
+            float h, l;
+            split_df_bits(v, h, l);
+            TH[r * TB + c] = h;
+            TL[r * TB + c] = l;
+        } else {
+            T[r * TB + c] = v;
+        }
+    };
     if (I == nb) {   // right-hand-side rows: B^T, zero beyond q rows / n columns
         for (int r = r0; r < TB; r += 2) {
             double v = 0.0;
             if (J < nb && r < q && j < n) v = Bt[(int64_t)r * n_pad + j];
-            T[r * TB + c] = v;
+            put(r, v);
         }
         return;
     }
@@ -277,7 +310,7 @@ __global__ void __launch_bounds__(256) k_build(int nb, int64_t n, int64_t n_pad,
             const double wv = fma(da, da, db * db);
             v = rho_table(tw, wv, kap, logc);
         }
-        T[r * TB + c] = v;
+        put(r, v);
     }
 }
 
@@ -610,14 +643,18 @@ cudaError_t launch_boxcox(int64_t n, int64_t n_pad, int p, int M, const double *
     return cudaGetLastError();
 }
 
-cudaError_t launch_front(const BatchArgs &b, cudaStream_t s) {
+cudaError_t launch_front(const BatchArgs &b, cudaStream_t s, bool double_float) {
     const int cnt = b.count;
     KernelTimer *timer = b.timer;
     TIMED(KC_PREP, (k_omega_prep<<<cnt, 256, 0, s>>>(b.params, b.n, b.n_pad, b.coords, b.oconst,
                                                       b.coordT, b.ldv, b.pstatus)));
     TIMED(KC_TABLE, (k_matern_table<<<dim3((TAB_NBUCKET + 31) / 32, cnt), 320, 0, s>>>(b.oconst, b.tab)));
-    TIMED(KC_BUILD, (k_build<<<dim3((unsigned)b.tpo, cnt), 256, 0, s>>>(
-                        b.nb, b.n, b.n_pad, b.q, b.tpo, b.tiles, b.oconst, b.coordT, b.tab, b.Bt)));
+    if (double_float)
+        TIMED(KC_BUILD, (k_build<true><<<dim3((unsigned)b.tpo, cnt), 256, 0, s>>>(
+                            b.nb, b.n, b.n_pad, b.q, b.tpo, b.tiles, b.oconst, b.coordT, b.tab, b.Bt)));
+    else
+        TIMED(KC_BUILD, (k_build<false><<<dim3((unsigned)b.tpo, cnt), 256, 0, s>>>(
+                            b.nb, b.n, b.n_pad, b.q, b.tpo, b.tiles, b.oconst, b.coordT, b.tab, b.Bt)));
     return cudaGetLastError();
 }
 
@@ -638,7 +675,7 @@ cudaError_t launch_fp64_batch(const BatchArgs &b, cudaStream_t s) {
     if (e != cudaSuccess) return e;
     const int cnt = b.count;
     KernelTimer *timer = b.timer;
-    if ((e = launch_front(b, s)) != cudaSuccess) return e;
+    if ((e = launch_front(b, s, false)) != cudaSuccess) return e;
     for (int J = 0; J < b.nb; ++J) {
         TIMED(KC_POTRF, (k_potrf<<<cnt, 256, 2 * PK * sizeof(double), s>>>(J, b.tpo, b.tiles, b.inv,
                                                                             b.ldv, b.pstatus)));

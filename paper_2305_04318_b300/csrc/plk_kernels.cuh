@@ -53,7 +53,8 @@ cudaError_t launch_boxcox(int64_t n, int64_t n_pad, int p, int M, const double *
                           KernelTimer *timer = nullptr);
 cudaError_t launch_fp64_batch(const BatchArgs &b, cudaStream_t s);
 // pieces of the batch pipeline shared with the mixed path
-cudaError_t launch_front(const BatchArgs &b, cudaStream_t s);      // prep, table, build (FP64 tiles)
+// prep, table, build (FP64 tiles, or double-float planes for the mixed path)
+cudaError_t launch_front(const BatchArgs &b, cudaStream_t s, bool double_float);
 cudaError_t launch_finalize(const BatchArgs &b, cudaStream_t s);   // closed form from FP64 tile (nb, nb)
 // Buffers of the mixed-precision path (per batch slot w unless noted).
 struct MixedArgs {

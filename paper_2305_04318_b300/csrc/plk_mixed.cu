@@ -133,25 +133,8 @@ __device__ __forceinline__ void issue_split_mmas(uint32_t tb, const uint8_t *sA,
 }  // namespace
 
 // ---------------------------------------------------------------------------
-// FP64 tiles <-> double-float planes
+// double-float planes -> FP64 (the last diagonal tile, read by the closed form)
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_to_df(int64_t tpo, double *tiles) {
-    double *T = tiles + ((int64_t)blockIdx.y * tpo + blockIdx.x) * NT;
-    double v[NT / 256];
-#pragma unroll
-    for (int l = 0; l < NT / 256; ++l) v[l] = T[threadIdx.x + 256 * l];
-    __syncthreads();
-    float *H = reinterpret_cast<float *>(T);
-    float *L = H + NT;
-#pragma unroll
-    for (int l = 0; l < NT / 256; ++l) {
-        const int e = threadIdx.x + 256 * l;
-        const float hi = __double2float_rn(v[l]);
-        H[e] = hi;
-        L[e] = __double2float_rn(v[l] - (double)hi);
-    }
-}
-
 __global__ void __launch_bounds__(256) k_tile_to_fp64(int64_t tpo, int64_t tile, double *tiles) {
     double *T = tiles + ((int64_t)blockIdx.x * tpo + tile) * NT;
     const float *H = reinterpret_cast<const float *>(T);
@@ -650,6 +633,13 @@ __global__ void __launch_bounds__(pipe::NTHP, 1) k_trail_pipe(int J, int nb, int
                         tc::bulk_g2s(sbase + bs * BBUF + j * HBLK, ib + (size_t)(j * 2 + h) * SBLK + ch * HBLK, HBLK,
                                      &bFull[bs]);
                     ++bcnt;
+                    if (h == 0) {   // the epilogue's read-modify-write will find the half tile in L2
+                        const char *gc = reinterpret_cast<const char *>(tiles + ((int64_t)w * tpo + tile_index(I, K)) * NT);
+                        for (int rr = 0; rr < TB; ++rr) {
+                            tc::prefetch_l2(gc + (size_t)rr * TB * 4 + ch * 256, 256);
+                            tc::prefetch_l2(gc + (size_t)NT * 4 + (size_t)rr * TB * 4 + ch * 256, 256);
+                        }
+                    }
                     for (int i = 0; i < S; ++i) {
                         const int as = acnt % NA;
                         const uint32_t au = acnt / NA;
@@ -675,6 +665,13 @@ __global__ void __launch_bounds__(pipe::NTHP, 1) k_trail_pipe(int J, int nb, int
                     const int bs = bcnt & 1;
                     if (!tc::mbar_wait(&bFull[bs], (bcnt >> 1) & 1)) { *verr = 1; break; }
                     ++bcnt;
+                    if (h == 0) {   // the epilogue's read-modify-write will find the half tile in L2
+                        const char *gc = reinterpret_cast<const char *>(tiles + ((int64_t)w * tpo + tile_index(I, K)) * NT);
+                        for (int rr = 0; rr < TB; ++rr) {
+                            tc::prefetch_l2(gc + (size_t)rr * TB * 4 + ch * 256, 256);
+                            tc::prefetch_l2(gc + (size_t)NT * 4 + (size_t)rr * TB * 4 + ch * 256, 256);
+                        }
+                    }
                     for (int i = 0; i < S; ++i) {
                         const int as = acnt % NA;
                         if (!tc::mbar_wait(&aFull[as], (acnt / NA) & 1)) { *verr = 1; break; }
@@ -1151,7 +1148,6 @@ static cudaError_t launch_mixed_steps(const BatchArgs &b, const MixedArgs &x, cu
             return e;
     }
     cudaMemsetAsync(x.invsum, 0, sizeof(double) * cnt, s);
-    TIMED(KC_CONVERT, (k_to_df<<<dim3((unsigned)b.tpo, cnt), 256, 0, s>>>(b.tpo, b.tiles)));
     for (int J = 0; J < b.nb; ++J) {
         TIMED(KC_POTRF_MIXED, (k_potrf_mixed<S><<<cnt, 256, 2 * PK * sizeof(double), s>>>(
                             J, b.tpo, b.tiles, x.wimg, b.ldv, x.invsum, b.pstatus)));
@@ -1175,7 +1171,7 @@ static cudaError_t launch_mixed_steps(const BatchArgs &b, const MixedArgs &x, cu
 }
 
 cudaError_t launch_mixed_batch(const BatchArgs &b, const MixedArgs &x, int S, cudaStream_t s) {
-    cudaError_t e = launch_front(b, s);
+    cudaError_t e = launch_front(b, s, true);   // builds double-float tiles directly
     if (e != cudaSuccess) return e;
     e = (S == 7) ? launch_mixed_steps<7>(b, x, s) : launch_mixed_steps<5>(b, x, s);
     if (e != cudaSuccess) return e;
