@@ -665,13 +665,6 @@ __global__ void __launch_bounds__(pipe::NTHP, 1) k_trail_pipe(int J, int nb, int
                     const int bs = bcnt & 1;
                     if (!tc::mbar_wait(&bFull[bs], (bcnt >> 1) & 1)) { *verr = 1; break; }
                     ++bcnt;
-                    if (h == 0) {   // the epilogue's read-modify-write will find the half tile in L2
-                        const char *gc = reinterpret_cast<const char *>(tiles + ((int64_t)w * tpo + tile_index(I, K)) * NT);
-                        for (int rr = 0; rr < TB; ++rr) {
-                            tc::prefetch_l2(gc + (size_t)rr * TB * 4 + ch * 256, 256);
-                            tc::prefetch_l2(gc + (size_t)NT * 4 + (size_t)rr * TB * 4 + ch * 256, 256);
-                        }
-                    }
                     for (int i = 0; i < S; ++i) {
                         const int as = acnt % NA;
                         if (!tc::mbar_wait(&aFull[as], (acnt / NA) & 1)) { *verr = 1; break; }
