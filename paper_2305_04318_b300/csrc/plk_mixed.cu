@@ -633,13 +633,6 @@ __global__ void __launch_bounds__(pipe::NTHP, 1) k_trail_pipe(int J, int nb, int
                         tc::bulk_g2s(sbase + bs * BBUF + j * HBLK, ib + (size_t)(j * 2 + h) * SBLK + ch * HBLK, HBLK,
                                      &bFull[bs]);
                     ++bcnt;
-                    if (h == 0) {   // the epilogue's read-modify-write will find the half tile in L2
-                        const char *gc = reinterpret_cast<const char *>(tiles + ((int64_t)w * tpo + tile_index(I, K)) * NT);
-                        for (int rr = 0; rr < TB; ++rr) {
-                            tc::prefetch_l2(gc + (size_t)rr * TB * 4 + ch * 256, 256);
-                            tc::prefetch_l2(gc + (size_t)NT * 4 + (size_t)rr * TB * 4 + ch * 256, 256);
-                        }
-                    }
                     for (int i = 0; i < S; ++i) {
                         const int as = acnt % NA;
                         const uint32_t au = acnt / NA;
