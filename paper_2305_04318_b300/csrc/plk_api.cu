@@ -107,9 +107,9 @@ bool make_layout(int64_t n, int32_t p, int32_t M, int32_t batch, Layout &L, int 
     L.off_pst = take(sizeof(int) * (size_t)batch);
     if (precision == PLK_MIXED) {
         L.mixed = true;
-        L.img = align_up(mixed_img_bytes(7));   // sized for the 7-slice pass, used by both
+        L.img = align_up(mixed_img_bytes(7));   // L_JJ^-1 image, sized for the 7-slice pass
         L.off_wimg = take(L.img * batch);
-        L.off_pimg = take(L.img * (size_t)(L.nb + 1) * batch);
+        L.off_pimg = take(align_up(mixed_slot_bytes()) * (size_t)(L.nb + 1) * batch);
         L.off_invsum = take(sizeof(double) * (size_t)batch);
         L.off_flags = take(sizeof(int) * (size_t)batch);
         L.off_idx = take(sizeof(int) * (size_t)batch);

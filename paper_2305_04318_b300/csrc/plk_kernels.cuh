@@ -67,6 +67,7 @@ struct MixedArgs {
     double tol;          // retry when the bound exceeds this
 };
 size_t mixed_img_bytes(int S);
+size_t mixed_slot_bytes();   // panel slot of one tile row
 cudaError_t launch_mixed_batch(const BatchArgs &b, const MixedArgs &x, int S, cudaStream_t s);
 cudaError_t launch_gather_params(int count, const int *idx, const double *params, double *out, cudaStream_t s);
 cudaError_t launch_scatter_value(int count, const int *idx, double v, double *out, cudaStream_t s);

@@ -97,6 +97,16 @@ __host__ __device__ constexpr size_t img_bytes() {
     return (size_t)S * 2 * SBLK + 1024;
 }
 
+// Panel slot of one tile row: two 5-slice images (panels J with J % 2 = 0, 1;
+// the two-panel trailing update needs both) or one 7-slice image.
+constexpr size_t SLOT = 2 * img_bytes<5>() > img_bytes<7>() ? 2 * img_bytes<5>() : img_bytes<7>();
+
+// Exponent shared by every row and panel of L (data rows): |L_rk| <= sqrt(V_rr)
+// = sqrt(1 + nu^2), with a margin for the rounding of the computed factor.
+__device__ __forceinline__ int common_exp(double nug) {
+    return row_exp((float)sqrt(1.0 + nug) * (1.0f + 1.0f / 1024.0f));
+}
+
 template <int S>
 __device__ __forceinline__ void store_pair(uint8_t *img, int r, int k, const float (&m0)[S], const float (&m1)[S]) {
     const int h = k >> 6;
@@ -279,7 +289,7 @@ __device__ __forceinline__ void group_value(uint32_t p0, uint32_t p1, uint32_t p
 template <int S>
 __global__ void __launch_bounds__(NTH, 1) k_trsm_split(int J, int nb, int64_t tpo, const double *__restrict__ tiles,
                                                        const uint8_t *__restrict__ wimg, uint8_t *__restrict__ pimg,
-                                                       int *__restrict__ err) {
+                                                       const double *__restrict__ oconst, int *__restrict__ err) {
     extern __shared__ uint8_t smraw[];
     uint8_t *sbase = align1024(smraw);
     uint8_t *sA = sbase;             // S blocks of the current K half of A_IJ
@@ -390,7 +400,9 @@ __global__ void __launch_bounds__(NTH, 1) k_trsm_split(int J, int nb, int64_t tp
     __syncthreads();
     if (ok) {
         const float mx = __int_as_float(sMx[r]);
-        const int eo = row_exp(mx * (1.0f + 1.0f / 1024.0f));
+        // data rows: the common exponent (lets two panels share one accumulator);
+        // right-hand-side rows: their own maximum
+        const int eo = (I < nb) ? common_exp(oconst[OC_N * (int64_t)w + OC_NUG]) : row_exp(mx * (1.0f + 1.0f / 1024.0f));
         if (warp < 4) sEO[r] = (short)eo;
 #pragma unroll 1
         for (int c0 = 0; c0 < 32; c0 += 16) {
@@ -410,130 +422,13 @@ __global__ void __launch_bounds__(NTH, 1) k_trsm_split(int J, int nb, int64_t tp
         }
     }
     __syncthreads();
-    uint8_t *dst = pimg + ((int64_t)w * (nb + 1) + I) * img_bytes<S>();
+    uint8_t *dst = pimg + ((int64_t)w * (nb + 1) + I) * SLOT + (size_t)(J & 1) * img_bytes<S>();
     if (ok) {
         const uint4 *src4 = reinterpret_cast<const uint4 *>(sbase);
         uint4 *dst4 = reinterpret_cast<uint4 *>(dst);
 #pragma unroll 4
         for (int e = tid; e < S * 2 * SBLK / 16; e += NTH) dst4[e] = src4[e];
         if (tid < TB) reinterpret_cast<int *>(dst + (size_t)S * 2 * SBLK)[tid] = (int)sEO[tid];
-    }
-    tc::fence_before_sync();
-    __syncthreads();
-    tc::fence_after_sync();
-    if (warp == 0) tc::tmem_dealloc(tb, 512);
-}
-
-// ---------------------------------------------------------------------------
-// Trailing update A_IK -= L_IJ L_KJ^T (double-float tiles) on the tensor cores.
-// Epilogue in two phases: TMEM -> double-float deltas in padded shared rows
-// (thread per row), then a coalesced read-modify-write of the tile (thread per
-// column) with 8 loads in flight per thread.
-// ---------------------------------------------------------------------------
-template <int S>
-__global__ void __launch_bounds__(NTH, 1) k_trail_split(int J, int nb, int64_t tpo, double *__restrict__ tiles,
-                                                        const uint8_t *__restrict__ pimg, int *__restrict__ err) {
-    extern __shared__ uint8_t smraw[];
-    uint8_t *sbase = align1024(smraw);
-    uint8_t *sA = sbase;
-    uint8_t *sB = sbase + S * SBLK;
-    __shared__ uint64_t bar_load, bar_mma;
-    __shared__ uint32_t tmem_base;
-    __shared__ int sEA[TB], sEB[TB];
-    __shared__ int s_ok;
-    const int w = blockIdx.y;
-    int I, K;
-    decode_trailing(blockIdx.x, J, I, K);
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const uint8_t *ia = pimg + ((int64_t)w * (nb + 1) + I) * img_bytes<S>();
-    const uint8_t *ib = pimg + ((int64_t)w * (nb + 1) + K) * img_bytes<S>();
-    if (warp == 0) {
-        tc::tmem_alloc(&tmem_base, 512);
-        tc::tmem_relinquish();
-    }
-    if (tid == 0) {
-        tc::mbar_init(&bar_load, 1);
-        tc::mbar_init(&bar_mma, 1);
-        tc::fence_mbar_init();
-        s_ok = 1;
-    }
-    if (tid < TB) {
-        sEA[tid] = reinterpret_cast<const int *>(ia + (size_t)S * 2 * SBLK)[tid];
-        sEB[tid] = reinterpret_cast<const int *>(ib + (size_t)S * 2 * SBLK)[tid];
-    }
-    tc::fence_before_sync();
-    __syncthreads();
-    tc::fence_after_sync();
-    const uint32_t tb = tmem_base;
-    uint32_t phase = 0;
-    for (int h = 0; h < 2; ++h) {
-        if (tid == 0 && s_ok) {
-            tc::mbar_arrive_expect_tx(&bar_load, 2 * S * SBLK);
-            for (int j = 0; j < S; ++j) {
-                tc::bulk_g2s(sA + j * SBLK, ia + (size_t)(j * 2 + h) * SBLK, SBLK, &bar_load);
-                tc::bulk_g2s(sB + j * SBLK, ib + (size_t)(j * 2 + h) * SBLK, SBLK, &bar_load);
-            }
-            bool ok = tc::mbar_wait(&bar_load, phase);
-            if (!ok) tc::mbar_wait(&bar_load, phase);
-            if (ok) {
-                tc::fence_after_sync();
-                issue_split_mmas<S>(tb, sA, sB, h == 0);
-                tc::mma_commit(&bar_mma);
-                ok = tc::mbar_wait(&bar_mma, phase);
-                if (!ok) tc::mbar_wait(&bar_mma, phase);
-            }
-            if (!ok) {
-                s_ok = 0;
-                atomicExch(err, 1);
-            }
-        }
-        phase ^= 1;
-        tc::fence_before_sync();
-        __syncthreads();
-        tc::fence_after_sync();
-    }
-    const bool ok = s_ok != 0;
-    float *sDh = reinterpret_cast<float *>(sbase);   // deltas, padded rows
-    float *sDl = sDh + TB * SPAD;
-    if (ok) {
-        const int r = 32 * (warp & 3) + lane;
-        const int cb = 32 * (warp >> 2);
-        const int ea = sEA[r] - 14;
-#pragma unroll 1
-        for (int c0 = 0; c0 < 32; c0 += 16) {
-            uint32_t p0[16], p1[16], p2[16], p3[16];
-            load_groups(tb, warp, c0, p0, p1, p2, p3);
-#pragma unroll
-            for (int c = 0; c < 16; ++c) {
-                float hi, lo;
-                group_value(p0[c], p1[c], p2[c], p3[c], ea + sEB[cb + c0 + c], hi, lo);
-                sDh[r * SPAD + cb + c0 + c] = hi;
-                sDl[r * SPAD + cb + c0 + c] = lo;
-            }
-        }
-    }
-    __syncthreads();
-    if (ok) {
-        float *gH = reinterpret_cast<float *>(tiles + ((int64_t)w * tpo + tile_index(I, K)) * NT);
-        float *gL = gH + NT;
-#pragma unroll 1
-        for (int base = 0; base < NT; base += NTH * 8) {
-            float h8[8], l8[8];
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                h8[u] = gH[base + tid + NTH * u];
-                l8[u] = gL[base + tid + NTH * u];
-            }
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                const int e = base + tid + NTH * u;
-                const int idx = (e >> 7) * SPAD + (e & (TB - 1));
-                df_add(h8[u], l8[u], -sDh[idx]);
-                df_add(h8[u], l8[u], -sDl[idx]);
-                gH[e] = h8[u];
-                gL[e] = l8[u];
-            }
-        }
     }
     tc::fence_before_sync();
     __syncthreads();
@@ -570,9 +465,14 @@ constexpr int SMEM = OFF_D + 2 * TB * DP * 4 + 1024;
 constexpr uint32_t IDESC_N64 = tc::idesc_bf16_f32(128, 64);
 }  // namespace pipe
 
-__global__ void __launch_bounds__(pipe::NTHP, 1) k_trail_pipe(int J, int nb, int cnt, int64_t tpo,
-                                                             double *__restrict__ tiles,
-                                                             const uint8_t *__restrict__ pimg, int *__restrict__ err) {
+// Item sets: mode 0 = the triangle Klo <= K <= I <= Ihi; mode 1 = the column
+// K = Klo, Klo <= I <= Ihi; mode 2 = the row I = Ihi, Klo <= K <= Ihi.  Each
+// item applies the P (1 or 2) panels in sub-slots sub0, sub1; with P = 2 both
+// operands use the common exponent (data rows only).
+__global__ void __launch_bounds__(pipe::NTHP, 1) k_trail_pipe(int mode, int Klo, int Ihi, int P, int sub0, int sub1,
+                                                             int nb, int cnt, int64_t tpo, double *__restrict__ tiles,
+                                                             const uint8_t *__restrict__ pimg,
+                                                             const double *__restrict__ oconst, int *__restrict__ err) {
     using namespace pipe;
     extern __shared__ uint8_t smraw[];
     uint8_t *sbase = align1024(smraw);
@@ -582,8 +482,8 @@ __global__ void __launch_bounds__(pipe::NTHP, 1) k_trail_pipe(int J, int nb, int
     __shared__ int s_err, s_stop;
     volatile int *verr = &s_err;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int m = nb - J;
-    const int T = m * (m + 1) / 2;
+    const int m = Ihi - Klo + 1;
+    const int T = (mode == 0) ? m * (m + 1) / 2 : m;
     const int64_t items = (int64_t)cnt * T * 2;
     if (tid == 0) {
         for (int i = 0; i < 2; ++i) {
@@ -613,9 +513,20 @@ __global__ void __launch_bounds__(pipe::NTHP, 1) k_trail_pipe(int J, int nb, int
         w = (int)(it / (2 * T));
         const int rem = (int)(it - (int64_t)w * 2 * T);
         ch = rem & 1;
-        decode_trailing(rem >> 1, J, I, K);
+        const int t = rem >> 1;
+        if (mode == 0) {
+            decode_trailing(t, Klo - 1, I, K);
+        } else if (mode == 1) {
+            K = Klo;
+            I = Klo + t;
+        } else {
+            I = Ihi;
+            K = Klo + t;
+        }
     };
-    auto image = [&](int w, int R) { return pimg + ((int64_t)w * (nb + 1) + R) * img_bytes<S>(); };
+    auto image = [&](int w, int R, int p) {
+        return pimg + ((int64_t)w * (nb + 1) + R) * SLOT + (size_t)(p ? sub1 : sub0) * img_bytes<S>();
+    };
 
     if (warp == 0) {
         if (lane == 0) {
@@ -623,8 +534,9 @@ __global__ void __launch_bounds__(pipe::NTHP, 1) k_trail_pipe(int J, int nb, int
             for (int64_t it = blockIdx.x; it < items && !*verr; it += gridDim.x) {
                 int w, I, K, ch;
                 decode(it, w, I, K, ch);
-                const uint8_t *ia = image(w, I), *ib = image(w, K);
-                for (int h = 0; h < 2 && !*verr; ++h) {
+                for (int ph = 0; ph < 2 * P && !*verr; ++ph) {
+                    const int h = ph & 1;
+                    const uint8_t *ia = image(w, I, ph >> 1), *ib = image(w, K, ph >> 1);
                     const int bs = bcnt & 1;
                     const uint32_t bu = bcnt >> 1;
                     if (bu > 0 && !tc::mbar_wait(&bEmpty[bs], (bu - 1) & 1)) { *verr = 1; break; }
@@ -654,7 +566,8 @@ __global__ void __launch_bounds__(pipe::NTHP, 1) k_trail_pipe(int J, int nb, int
                 if (tu > 0 && !tc::mbar_wait(&accEmpty[set], (tu - 1) & 1)) { *verr = 1; break; }
                 tc::fence_after_sync();
                 const uint32_t dacc = tb + set * 256;
-                for (int h = 0; h < 2 && !*verr; ++h) {
+                for (int ph = 0; ph < 2 * P && !*verr; ++ph) {
+                    const int h = ph;   // first K half of the first panel starts the accumulators
                     const int bs = bcnt & 1;
                     if (!tc::mbar_wait(&bFull[bs], (bcnt >> 1) & 1)) { *verr = 1; break; }
                     ++bcnt;
@@ -698,9 +611,16 @@ __global__ void __launch_bounds__(pipe::NTHP, 1) k_trail_pipe(int J, int nb, int
         for (int64_t it = blockIdx.x; it < items; it += gridDim.x, ++tcnt) {
             int w, I, K, ch;
             decode(it, w, I, K, ch);
-            const uint8_t *ia = image(w, I), *ib = image(w, K);
-            if (et < TB) sEA[et] = (short)reinterpret_cast<const int *>(ia + (size_t)S * 2 * SBLK)[et];
-            else if (et < TB + 64) sEB[et - TB] = (short)reinterpret_cast<const int *>(ib + (size_t)S * 2 * SBLK)[64 * ch + et - TB];
+            if (P == 2) {
+                const short ec = (short)common_exp(oconst[OC_N * (int64_t)w + OC_NUG]);
+                if (et < TB) sEA[et] = ec;
+                else if (et < TB + 64) sEB[et - TB] = ec;
+            } else {
+                const uint8_t *ia = image(w, I, 0), *ib = image(w, K, 0);
+                if (et < TB) sEA[et] = (short)reinterpret_cast<const int *>(ia + (size_t)S * 2 * SBLK)[et];
+                else if (et < TB + 64)
+                    sEB[et - TB] = (short)reinterpret_cast<const int *>(ib + (size_t)S * 2 * SBLK)[64 * ch + et - TB];
+            }
             const int set = tcnt & 1;
             if (et == 0) {   // one thread waits and decides for all 128
                 const bool ok = tc::mbar_wait(&accFull[set], (tcnt >> 1) & 1);
@@ -829,8 +749,8 @@ __global__ void __launch_bounds__(NTH, 1) k_trail_split7x(int J, int nb, int64_t
     int I, K;
     decode_trailing(blockIdx.x, J, I, K);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const uint8_t *ia = pimg + ((int64_t)w * (nb + 1) + I) * img_bytes<S7>();
-    const uint8_t *ib = pimg + ((int64_t)w * (nb + 1) + K) * img_bytes<S7>();
+    const uint8_t *ia = pimg + ((int64_t)w * (nb + 1) + I) * SLOT;
+    const uint8_t *ib = pimg + ((int64_t)w * (nb + 1) + K) * SLOT;
     if (warp == 0) {
         tc::tmem_alloc(&tmem_base, 512);
         tc::tmem_relinquish();
@@ -939,7 +859,7 @@ __global__ void __launch_bounds__(NTH, 1) k_trsm_split7x(int J, int nb, int64_t 
     const float *H = reinterpret_cast<const float *>(tiles + ((int64_t)w * tpo + tile_index(I, J)) * NT);
     const float *Lo = H + NT;
     const uint8_t *wi = wimg + (int64_t)w * img_bytes<S7>();
-    uint8_t *slot = pimg + ((int64_t)w * (nb + 1) + I) * img_bytes<S7>();
+    uint8_t *slot = pimg + ((int64_t)w * (nb + 1) + I) * SLOT;
     float *scH = reinterpret_cast<float *>(slot);   // scratch planes of L_IJ (128 KB < slot)
     float *scL = scH + NT;
     if (warp == 0) {
@@ -1091,6 +1011,7 @@ __global__ void k_gather_params(int count, const int *__restrict__ idx, const do
 // launchers
 // ---------------------------------------------------------------------------
 size_t mixed_img_bytes(int S) { return S == 5 ? img_bytes<5>() : img_bytes<7>(); }
+size_t mixed_slot_bytes() { return SLOT; }
 
 static int num_sms() {
     int dev = 0, n = 148;
@@ -1108,12 +1029,13 @@ static int num_sms() {
 template <int S>
 static cudaError_t launch_mixed_steps(const BatchArgs &b, const MixedArgs &x, cudaStream_t s) {
     KernelTimer *timer = b.timer;
-    const int cnt = b.count;
+    const int cnt = b.count, nb = b.nb;
     const int smem_split = 2 * S * SBLK + 1024;
     cudaError_t e;
     if ((e = cudaFuncSetAttribute(k_potrf_mixed<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)(2 * PK * sizeof(double)))) != cudaSuccess)
         return e;
+    cudaMemsetAsync(x.invsum, 0, sizeof(double) * cnt, s);
     if (S == 7) {
         const int smem_trail7 = S7 * (SBLK + HBLK) + 1024;
         if ((e = cudaFuncSetAttribute(k_trsm_split7x, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_split)) !=
@@ -1122,37 +1044,57 @@ static cudaError_t launch_mixed_steps(const BatchArgs &b, const MixedArgs &x, cu
         if ((e = cudaFuncSetAttribute(k_trail_split7x, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_trail7)) !=
             cudaSuccess)
             return e;
+        for (int J = 0; J < nb; ++J) {
+            TIMED(KC_POTRF_MIXED, (k_potrf_mixed<S><<<cnt, 256, 2 * PK * sizeof(double), s>>>(
+                                      J, b.tpo, b.tiles, x.wimg, b.ldv, x.invsum, b.pstatus)));
+            const int m = nb - J;
+            TIMED(KC_TRSM_SPLIT7, (k_trsm_split7x<<<dim3(m, cnt), NTH, smem_split, s>>>(J, nb, b.tpo, b.tiles, x.wimg,
+                                                                                      x.pimg, x.err)));
+            TIMED(KC_GEMM_SPLIT7, (k_trail_split7x<<<dim3(m * (m + 1) / 2, cnt), NTH, smem_trail7, s>>>(
+                                      J, nb, b.tpo, b.tiles, x.pimg, x.err)));
+        }
     } else {
-        if ((e = cudaFuncSetAttribute(k_trail_pipe, cudaFuncAttributeMaxDynamicSharedMemorySize, pipe::SMEM)) !=
-            cudaSuccess)
-            return e;
         if ((e = cudaFuncSetAttribute(k_trsm_split<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_split)) !=
             cudaSuccess)
             return e;
-        if ((e = cudaFuncSetAttribute(k_trail_split<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_split)) !=
+        if ((e = cudaFuncSetAttribute(k_trail_pipe, cudaFuncAttributeMaxDynamicSharedMemorySize, pipe::SMEM)) !=
             cudaSuccess)
             return e;
-    }
-    cudaMemsetAsync(x.invsum, 0, sizeof(double) * cnt, s);
-    for (int J = 0; J < b.nb; ++J) {
-        TIMED(KC_POTRF_MIXED, (k_potrf_mixed<S><<<cnt, 256, 2 * PK * sizeof(double), s>>>(
-                            J, b.tpo, b.tiles, x.wimg, b.ldv, x.invsum, b.pstatus)));
-        const int m = b.nb - J;
-        if (S == 7) {
-            TIMED(KC_TRSM_SPLIT7, (k_trsm_split7x<<<dim3(m, cnt), NTH, smem_split, s>>>(J, b.nb, b.tpo, b.tiles, x.wimg,
-                                                                                     x.pimg, x.err)));
-            TIMED(KC_GEMM_SPLIT7, (k_trail_split7x<<<dim3(m * (m + 1) / 2, cnt), NTH, S7 * (SBLK + HBLK) + 1024, s>>>(
-                                     J, b.nb, b.tpo, b.tiles, x.pimg, x.err)));
-        } else {
-            TIMED(KC_TRSM_SPLIT, (k_trsm_split<S><<<dim3(m, cnt), NTH, smem_split, s>>>(J, b.nb, b.tpo, b.tiles, x.wimg,
-                                                                                    x.pimg, x.err)));
-            const int64_t items = (int64_t)cnt * (m * (m + 1) / 2) * 2;
-            const int grid = (int)std::min<int64_t>(items, num_sms());
-            TIMED(KC_GEMM_SPLIT, (k_trail_pipe<<<grid, pipe::NTHP, pipe::SMEM, s>>>(J, b.nb, cnt, b.tpo, b.tiles,
-                                                                                      x.pimg, x.err)));
+        const int sms = num_sms();
+        auto trail = [&](int mode, int Klo, int Ihi, int P, int sub0, int sub1) {
+            const int m = Ihi - Klo + 1;
+            if (m <= 0) return;
+            const int64_t items = (int64_t)cnt * ((mode == 0) ? m * (m + 1) / 2 : m) * 2;
+            const int grid = (int)std::min<int64_t>(items, sms);
+            TIMED(KC_GEMM_SPLIT, (k_trail_pipe<<<grid, pipe::NTHP, pipe::SMEM, s>>>(
+                                     mode, Klo, Ihi, P, sub0, sub1, nb, cnt, b.tpo, b.tiles, x.pimg, b.oconst, x.err)));
+        };
+        auto factor_panel = [&](int J) {
+            TIMED(KC_POTRF_MIXED, (k_potrf_mixed<S><<<cnt, 256, 2 * PK * sizeof(double), s>>>(
+                                      J, b.tpo, b.tiles, x.wimg, b.ldv, x.invsum, b.pstatus)));
+            TIMED(KC_TRSM_SPLIT, (k_trsm_split<S><<<dim3(nb - J, cnt), NTH, smem_split, s>>>(
+                                     J, nb, b.tpo, b.tiles, x.wimg, x.pimg, b.oconst, x.err)));
+        };
+        // Two-panel look-ahead: factor panel J0, bring tile column J0+1 up to
+        // date with it, factor J0+1, then update the right-hand-side row with
+        // each panel (own exponents) and the data triangle with both panels
+        // at once (K = 256 in one accumulator set: one read-modify-write
+        // of every trailing tile per two panels).
+        for (int J0 = 0; J0 < nb; J0 += 2) {
+            const int J1 = J0 + 1;
+            factor_panel(J0);
+            if (J1 >= nb) {
+                trail(0, J0 + 1, nb, 1, J0 & 1, 0);   // remaining: the right-hand-side block
+                break;
+            }
+            trail(1, J1, nb, 1, J0 & 1, 0);           // column J1 (data rows and the RHS row)
+            factor_panel(J1);
+            trail(2, J1 + 1, nb, 1, J0 & 1, 0);       // RHS row with panel J0
+            trail(2, J1 + 1, nb, 1, J1 & 1, 0);       // RHS row with panel J1
+            trail(0, J1 + 1, nb - 1, 2, J0 & 1, J1 & 1);   // data triangle with both panels
         }
     }
-    TIMED(KC_CONVERT, (k_tile_to_fp64<<<cnt, 256, 0, s>>>(b.tpo, tile_index(b.nb, b.nb), b.tiles)));
+    TIMED(KC_CONVERT, (k_tile_to_fp64<<<cnt, 256, 0, s>>>(b.tpo, tile_index(nb, nb), b.tiles)));
     return cudaGetLastError();
 }
 
