@@ -456,10 +456,12 @@ namespace pipe {
 constexpr int S = 5;
 constexpr int NTHP = 384;                   // warps 0-3 roles, warps 4-11 epilogue
 constexpr int NEPI = NTHP - 128;
-constexpr int NA = 7;                       // A stages (16 KB each)
+constexpr int NA = 3;                       // A stages
 constexpr int BBUF = S * HBLK;              // 40 KB: one K half of 64 B rows, 5 slices
 constexpr int OFF_A = 2 * BBUF;             // 80 KB
-constexpr int SMEM = OFF_A + NA * SBLK + 1024;
+constexpr int OFF_D = OFF_A + NA * SBLK;    // 128 KB
+constexpr int DP = 64 + 1;
+constexpr int SMEM = OFF_D + 2 * TB * DP * 4 + 1024;
 constexpr uint32_t IDESC_N64 = tc::idesc_bf16_f32(128, 64);
 }  // namespace pipe
 
@@ -600,11 +602,11 @@ __global__ void __launch_bounds__(pipe::NTHP, 1) k_trail_pipe(int mode, int Klo,
             }
         }
     } else if (warp >= 4) {
-        // epilogue: thread = one row, 32 columns of the half tile; the tile rows
-        // are read straight from global memory (issued before the TMEM reads)
-        const int et = tid - 128;            // 0..NEPI-1
+        const int et = tid - 128;          // 0..NEPI-1
         const int r = 32 * (warp & 3) + lane;
         const int cpart = (warp - 4) >> 2;   // columns 32 cpart .. +31 of the half
+        float *sDh = reinterpret_cast<float *>(sbase + OFF_D);
+        float *sDl = sDh + TB * DP;
         uint32_t tcnt = 0;
         for (int64_t it = blockIdx.x; it < items; it += gridDim.x, ++tcnt) {
             int w, I, K, ch;
@@ -619,54 +621,60 @@ __global__ void __launch_bounds__(pipe::NTHP, 1) k_trail_pipe(int mode, int Klo,
                 else if (et < TB + 64)
                     sEB[et - TB] = (short)reinterpret_cast<const int *>(ib + (size_t)S * 2 * SBLK)[64 * ch + et - TB];
             }
-            float *gH = reinterpret_cast<float *>(tiles + ((int64_t)w * tpo + tile_index(I, K)) * NT) + r * TB +
-                        64 * ch + 32 * cpart;
-            float *gL = gH + NT;
-            float4 ch4[8], cl4[8];
-#pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                ch4[q] = reinterpret_cast<const float4 *>(gH)[q];
-                cl4[q] = reinterpret_cast<const float4 *>(gL)[q];
-            }
             const int set = tcnt & 1;
-            if (et == 0) {   // one thread waits and decides for all
+            if (et == 0) {   // one thread waits and decides for all 128
                 const bool ok = tc::mbar_wait(&accFull[set], (tcnt >> 1) & 1);
                 if (!ok) *verr = 1;
                 s_stop = (!ok || *verr) ? 1 : 0;
             }
-            tc::named_sync(1, NEPI);         // exponents visible; stop decision uniform
+            tc::named_sync(1, NEPI);       // exponents visible; stop decision uniform
             if (s_stop) break;
             tc::fence_after_sync();
-            const uint32_t a = tb + set * 256 + ((uint32_t)(32 * (warp & 3)) << 16) + 32 * cpart;
+            const uint32_t a = tb + set * 256 + ((uint32_t)(32 * (warp & 3)) << 16);
             const int ea = sEA[r] - 14;
-            float *hv = reinterpret_cast<float *>(ch4), *lv = reinterpret_cast<float *>(cl4);
-#pragma unroll
-            for (int c0 = 0; c0 < 32; c0 += 16) {
+#pragma unroll 1
+            for (int c0 = 32 * cpart; c0 < 32 * cpart + 32; c0 += 16) {
                 uint32_t p0[16], p1[16], p2[16], p3[16];
                 tc::tmem_ld16(a + 0 * 64 + c0, p0);
                 tc::tmem_ld16(a + 1 * 64 + c0, p1);
                 tc::tmem_ld16(a + 2 * 64 + c0, p2);
                 tc::tmem_ld16(a + 3 * 64 + c0, p3);
                 tc::tmem_wait_ld();
-                if (c0 == 16) {   // both chunks read: release the accumulator set
-                    tc::fence_before_sync();
-                    tc::named_sync(1, NEPI);
-                    if (et == 0) tc::mbar_arrive(&accEmpty[set]);
-                }
 #pragma unroll
                 for (int c = 0; c < 16; ++c) {
-                    float dh, dl;
-                    group_value(p0[c], p1[c], p2[c], p3[c], ea + sEB[32 * cpart + c0 + c], dh, dl);
-                    df_add(hv[c0 + c], lv[c0 + c], -dh);
-                    df_add(hv[c0 + c], lv[c0 + c], -dl);
+                    float hi, lo;
+                    group_value(p0[c], p1[c], p2[c], p3[c], ea + sEB[c0 + c], hi, lo);
+                    sDh[r * DP + c0 + c] = hi;
+                    sDl[r * DP + c0 + c] = lo;
                 }
             }
+            tc::fence_before_sync();
+            tc::named_sync(1, NEPI);
+            if (et == 0) tc::mbar_arrive(&accEmpty[set]);   // the MMA warp may reuse this set
+            float *gH = reinterpret_cast<float *>(tiles + ((int64_t)w * tpo + tile_index(I, K)) * NT) + 64 * ch;
+            float *gL = gH + NT;
+#pragma unroll 1
+            for (int u0 = 0; u0 < (TB * 64) / NEPI; u0 += 16) {
+                float h8[16], l8[16];
 #pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                reinterpret_cast<float4 *>(gH)[q] = ch4[q];
-                reinterpret_cast<float4 *>(gL)[q] = cl4[q];
+                for (int u = 0; u < 16; ++u) {
+                    const int e = et + NEPI * (u0 + u);
+                    const int gi = (e >> 6) * TB + (e & 63);
+                    h8[u] = gH[gi];
+                    l8[u] = gL[gi];
+                }
+#pragma unroll
+                for (int u = 0; u < 16; ++u) {
+                    const int e = et + NEPI * (u0 + u);
+                    const int gi = (e >> 6) * TB + (e & 63);
+                    const int si = (e >> 6) * DP + (e & 63);
+                    df_add(h8[u], l8[u], -sDh[si]);
+                    df_add(h8[u], l8[u], -sDl[si]);
+                    gH[gi] = h8[u];
+                    gL[gi] = l8[u];
+                }
             }
-            tc::named_sync(1, NEPI);         // exponents consumed before the next item rewrites them
+            tc::named_sync(1, NEPI);       // deltas consumed before the next item rewrites them
         }
     }
     __syncthreads();
