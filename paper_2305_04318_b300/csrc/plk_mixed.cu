@@ -164,15 +164,38 @@ __global__ void __launch_bounds__(256) k_tile_to_fp64(int64_t tpo, int64_t tile,
 // Diagonal tile in FP64: L_JJ, W = L_JJ^-1 (sliced for the tensor cores),
 // log-det and the pivot sum for the error bound.
 // ---------------------------------------------------------------------------
+// Row of the t-th entry of a packed lower triangle (t = r (r + 1) / 2 + c, c <= r).
+__device__ __forceinline__ int tri_row(int t) {
+    int r = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
+    if ((r + 1) * (r + 2) / 2 <= t) ++r;
+    if (r * (r + 1) / 2 > t) --r;
+    return r;
+}
+
+// Dynamic shared memory of k_potrf_mixed: the packed tile (66 KB) padded so
+// that at most two blocks share an SM (the default batch is four tiles per SM;
+// three per SM would leave a partial second wave).
+constexpr size_t POTRF_MIXED_SMEM = 80 * 1024;
+
+// The FP64 pipe is the bound here, so every step spreads its multiply-adds
+// evenly over all threads (flat index over the packed entries it touches) and
+// the serial per-column part (pivot, 1/sqrt, column scale) is one warp's work.
+// L is formed in place; W = L^-1 then overwrites it, row by row, right-looking:
+// row k of W is final once rows < k have been applied; applying it subtracts
+// L[i][k] W[k][c] from rows i > k.  Column k of L is staged in shared memory
+// a step ahead because its slots become W's; the thread that applies the last
+// update to row k+1 also scales it by 1/L[k+1][k+1].
 template <int S>
-__global__ void __launch_bounds__(256) k_potrf_mixed(int J, int64_t tpo, double *__restrict__ tiles,
-                                                     uint8_t *__restrict__ wimg, double *__restrict__ logdet,
-                                                     double *__restrict__ invsum, int *__restrict__ pstatus) {
+__global__ void __launch_bounds__(256, 2) k_potrf_mixed(int J, int64_t tpo, double *__restrict__ tiles,
+                                                        uint8_t *__restrict__ wimg, double *__restrict__ logdet,
+                                                        double *__restrict__ invsum, int *__restrict__ pstatus) {
     extern __shared__ double sm[];
-    double *P = sm;
-    double *Wp = sm + PK;
-    __shared__ double s_ld, s_inv;
-    __shared__ int s_bad;
+    double *P = sm;   // packed lower triangle: the tile, then L, then W = L^-1
+    __shared__ double colb[2][TB];   // scaled column j of L / finished row k of W
+    __shared__ double lcol[2][TB];   // column k of L, staged before W overwrites it
+    __shared__ double piv[TB];       // pivots d_j
+    __shared__ double rd[TB];        // 1 / L[j][j]
+    __shared__ double red[2][4];
     const int w = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     double *T = tiles + ((int64_t)w * tpo + tile_index(J, J)) * NT;
     const float *H = reinterpret_cast<const float *>(T);
@@ -181,49 +204,83 @@ __global__ void __launch_bounds__(256) k_potrf_mixed(int J, int64_t tpo, double 
         const int r = e >> 7, c = e & (TB - 1);
         if (c <= r) P[pk(r, c)] = (double)H[e] + (double)Lo[e];
     }
-    if (tid == 0) {
-        s_ld = 0.0;
-        s_inv = 0.0;
-        s_bad = 0;
+    __syncthreads();
+    // Cholesky (a non-positive pivot leaves NaN behind it; the pivot is kept
+    // so the status is set below)
+    for (int j = 0; j < TB; ++j) {
+        if (warp == 0) {
+            const double d = P[pk(j, j)];
+            const double rl = rsqrt(d);
+            if (lane == 0) {
+                piv[j] = d;
+                P[pk(j, j)] = d * rl;
+            }
+            for (int i = j + 1 + lane; i < TB; i += 32) {
+                const double v = P[pk(i, j)] * rl;
+                P[pk(i, j)] = v;
+                colb[0][i] = v;
+            }
+        }
+        __syncthreads();
+        const int m = TB - 1 - j, cnt = m * (m + 1) / 2;
+        for (int t = tid; t < cnt; t += 256) {
+            const int ii = tri_row(t), kk = t - ii * (ii + 1) / 2;
+            const int i = j + 1 + ii, k = j + 1 + kk;
+            P[pk(i, k)] = fma(-colb[0][i], colb[0][k], P[pk(i, k)]);
+        }
+        __syncthreads();
+    }
+    // W = L^-1 in place
+    if (tid < TB) {
+        rd[tid] = 1.0 / P[pk(tid, tid)];
+        lcol[0][tid] = P[pk(tid, 0)];
     }
     __syncthreads();
-    for (int j = 0; j < TB; ++j) {
+    if (tid == 0) {
+        P[0] = rd[0];
+        colb[0][0] = rd[0];
+    }
+    __syncthreads();
+    for (int k = 0; k < TB - 1; ++k) {
+        const double *ck = colb[k & 1], *lk = lcol[k & 1];
+        double *cn = colb[(k + 1) & 1], *ln = lcol[(k + 1) & 1];
+        const int ncol = k + 1, cnt = (TB - 1 - k) * ncol;
+        if (tid > k + 1 && tid < TB) ln[tid] = P[pk(tid, k + 1)];
+        const double rn = rd[k + 1];
+        for (int t = tid; t < cnt; t += 256) {
+            const int ii = t / ncol, c = t - ii * ncol, i = k + 1 + ii;
+            const double acc = (c == k) ? 0.0 : P[pk(i, c)];   // slot (i, k) still holds L[i][k]
+            double v = fma(-lk[i], ck[c], acc);
+            if (ii == 0) {
+                v *= rn;
+                cn[c] = v;
+            }
+            P[pk(i, c)] = v;
+        }
         if (tid == 0) {
-            const double d = P[pk(j, j)];
-            if (!(d > 0.0)) {
-                s_bad = 1;
-                P[pk(j, j)] = nan("");
-            } else {
-                P[pk(j, j)] = sqrt(d);
-                s_ld += log(d);
-                s_inv += 1.0 / d;
-            }
-        }
-        __syncthreads();
-        const double rl = 1.0 / P[pk(j, j)];
-        for (int i = j + 1 + tid; i < TB; i += 256) P[pk(i, j)] *= rl;
-        __syncthreads();
-        for (int i = j + 1 + warp; i < TB; i += 8) {
-            const double lij = P[pk(i, j)];
-            const int bi = pk(i, 0);
-            for (int k = j + 1 + lane; k <= i; k += 32) P[bi + k] -= lij * P[pk(k, j)];
+            P[pk(k + 1, k + 1)] = rn;
+            cn[k + 1] = rn;
         }
         __syncthreads();
     }
-    for (int i = 0; i < TB; ++i) {
-        const int bi = pk(i, 0);
-        const double lii = P[bi + i];
-        for (int jj = tid; jj <= i; jj += 256) {
-            if (jj == i) {
-                Wp[bi + i] = 1.0 / lii;
-            } else {
-                double s = 0.0;
-                for (int k = jj; k < i; ++k) s = fma(P[bi + k], Wp[pk(k, jj)], s);
-                Wp[bi + jj] = -s / lii;
-            }
+    // log|tile| and sum 1/d over the pivots
+    {
+        double a = 0.0, bsum = 0.0;
+        if (tid < TB) {
+            a = log(piv[tid]);
+            bsum = 1.0 / piv[tid];
         }
-        __syncthreads();
+        for (int o = 16; o > 0; o >>= 1) {
+            a += __shfl_down_sync(0xffffffffu, a, o);
+            bsum += __shfl_down_sync(0xffffffffu, bsum, o);
+        }
+        if (lane == 0 && warp < 4) {
+            red[0][warp] = a;
+            red[1][warp] = bsum;
+        }
     }
+    const bool bad = __syncthreads_or(tid < TB && !(piv[tid] > 0.0));
+    const double *Wp = P;
     // slice the rows of W (B operand of the panel solve: C = A W^T)
     uint8_t *img = wimg + (int64_t)w * img_bytes<S>();
     int *exps = reinterpret_cast<int *>(img + (size_t)S * 2 * SBLK);
@@ -247,9 +304,14 @@ __global__ void __launch_bounds__(256) k_potrf_mixed(int J, int64_t tpo, double 
         }
     }
     if (tid == 0) {
-        logdet[w] += s_ld;
-        invsum[w] += s_inv;
-        if (s_bad && pstatus[w] == PLK_POINT_OK) pstatus[w] = PLK_POINT_NOT_PD;
+        double a = 0.0, bsum = 0.0;
+        for (int q = 0; q < 4; ++q) {
+            a += red[0][q];
+            bsum += red[1][q];
+        }
+        logdet[w] += a;
+        invsum[w] += bsum;
+        if (bad && pstatus[w] == PLK_POINT_OK) pstatus[w] = PLK_POINT_NOT_PD;
     }
 }
 
@@ -1033,7 +1095,7 @@ static cudaError_t launch_mixed_steps(const BatchArgs &b, const MixedArgs &x, cu
     const int smem_split = 2 * S * SBLK + 1024;
     cudaError_t e;
     if ((e = cudaFuncSetAttribute(k_potrf_mixed<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)(2 * PK * sizeof(double)))) != cudaSuccess)
+                                  (int)POTRF_MIXED_SMEM)) != cudaSuccess)
         return e;
     cudaMemsetAsync(x.invsum, 0, sizeof(double) * cnt, s);
     if (S == 7) {
@@ -1045,7 +1107,7 @@ static cudaError_t launch_mixed_steps(const BatchArgs &b, const MixedArgs &x, cu
             cudaSuccess)
             return e;
         for (int J = 0; J < nb; ++J) {
-            TIMED(KC_POTRF_MIXED, (k_potrf_mixed<S><<<cnt, 256, 2 * PK * sizeof(double), s>>>(
+            TIMED(KC_POTRF_MIXED, (k_potrf_mixed<S><<<cnt, 256, POTRF_MIXED_SMEM, s>>>(
                                       J, b.tpo, b.tiles, x.wimg, b.ldv, x.invsum, b.pstatus)));
             const int m = nb - J;
             TIMED(KC_TRSM_SPLIT7, (k_trsm_split7x<<<dim3(m, cnt), NTH, smem_split, s>>>(J, nb, b.tpo, b.tiles, x.wimg,
@@ -1070,7 +1132,7 @@ static cudaError_t launch_mixed_steps(const BatchArgs &b, const MixedArgs &x, cu
                                      mode, Klo, Ihi, P, sub0, sub1, nb, cnt, b.tpo, b.tiles, x.pimg, b.oconst, x.err)));
         };
         auto factor_panel = [&](int J) {
-            TIMED(KC_POTRF_MIXED, (k_potrf_mixed<S><<<cnt, 256, 2 * PK * sizeof(double), s>>>(
+            TIMED(KC_POTRF_MIXED, (k_potrf_mixed<S><<<cnt, 256, POTRF_MIXED_SMEM, s>>>(
                                       J, b.tpo, b.tiles, x.wimg, b.ldv, x.invsum, b.pstatus)));
             TIMED(KC_TRSM_SPLIT, (k_trsm_split<S><<<dim3(nb - J, cnt), NTH, smem_split, s>>>(
                                      J, nb, b.tpo, b.tiles, x.wimg, x.pimg, b.oconst, x.err)));
