@@ -418,9 +418,12 @@ __global__ void __launch_bounds__(NTH, 1) k_trsm_split(int J, int nb, int64_t tp
         }
         tc::fence_proxy_async();
         __syncthreads();
+        if (warp == 0 && s_ok) {   // one copy per lane: a thread's copies run one after another
+            if (lane == 0) tc::mbar_arrive_expect_tx(&bar_load, S * SBLK);
+            __syncwarp();
+            if (lane < S) tc::bulk_g2s(sW + lane * SBLK, wi + (size_t)(lane * 2 + h) * SBLK, SBLK, &bar_load);
+        }
         if (tid == 0 && s_ok) {
-            tc::mbar_arrive_expect_tx(&bar_load, S * SBLK);
-            for (int j = 0; j < S; ++j) tc::bulk_g2s(sW + j * SBLK, wi + (size_t)(j * 2 + h) * SBLK, SBLK, &bar_load);
             bool ok = tc::mbar_wait(&bar_load, phase);
             if (!ok) tc::mbar_wait(&bar_load, phase);
             if (ok) {
@@ -503,7 +506,7 @@ __global__ void __launch_bounds__(NTH, 1) k_trsm_split(int J, int nb, int64_t tp
 // work items (omega, tile (I, K), column half) of one step.  Roles:
 //   warp 0     producer: bulk copies of the B half-rows (all 5 slices of one K
 //              half, double-buffered) and of the A slices (one slice of one K
-//              half per stage, 3-stage ring);
+//              half per stage, 4-stage ring);
 //   warp 1     MMA issue into two alternating TMEM accumulator sets
 //              (2 sets x 4 groups x 64 columns = 512 columns);
 //   warp 2     TMEM allocation;
@@ -518,7 +521,7 @@ namespace pipe {
 constexpr int S = 5;
 constexpr int NTHP = 384;                   // warps 0-3 roles, warps 4-11 epilogue
 constexpr int NEPI = NTHP - 128;
-constexpr int NA = 3;                       // A stages
+constexpr int NA = 4;                       // A stages
 constexpr int BBUF = S * HBLK;              // 40 KB: one K half of 64 B rows, 5 slices
 constexpr int OFF_A = 2 * BBUF;             // 80 KB
 constexpr int OFF_D = OFF_A + NA * SBLK;    // 128 KB
@@ -549,7 +552,7 @@ __global__ void __launch_bounds__(pipe::NTHP, 1) k_trail_pipe(int mode, int Klo,
     const int64_t items = (int64_t)cnt * T * 2;
     if (tid == 0) {
         for (int i = 0; i < 2; ++i) {
-            tc::mbar_init(&bFull[i], 1);
+            tc::mbar_init(&bFull[i], S);   // one arrival (with its bytes) per slice lane
             tc::mbar_init(&bEmpty[i], 1);
             tc::mbar_init(&accFull[i], 1);
             tc::mbar_init(&accEmpty[i], 1);
@@ -591,29 +594,45 @@ __global__ void __launch_bounds__(pipe::NTHP, 1) k_trail_pipe(int mode, int Klo,
     };
 
     if (warp == 0) {
-        if (lane == 0) {
+        // Copies run from independent lanes with no warp-wide sync in between:
+        // a lane that issues a bulk copy stalls until the copy is under way, so
+        // one thread (or lanes that reconverge after each copy) would serialise
+        // them.  Lane s < NA owns A ring stage s; lane 8 + j loads B slice j.
+        const bool a_lane = lane < NA, b_lane = lane >= 8 && lane < 8 + S;
+        if (a_lane || b_lane) {
             uint32_t acnt = 0, bcnt = 0;
-            for (int64_t it = blockIdx.x; it < items && !*verr; it += gridDim.x) {
+            bool stop = false;
+            for (int64_t it = blockIdx.x; it < items && !stop; it += gridDim.x) {
                 int w, I, K, ch;
                 decode(it, w, I, K, ch);
-                for (int ph = 0; ph < 2 * P && !*verr; ++ph) {
+                for (int ph = 0; ph < 2 * P && !stop; ++ph) {
                     const int h = ph & 1;
                     const uint8_t *ia = image(w, I, ph >> 1), *ib = image(w, K, ph >> 1);
                     const int bs = bcnt & 1;
                     const uint32_t bu = bcnt >> 1;
-                    if (bu > 0 && !tc::mbar_wait(&bEmpty[bs], (bu - 1) & 1)) { *verr = 1; break; }
-                    tc::mbar_arrive_expect_tx(&bFull[bs], BBUF);
-                    for (int j = 0; j < S; ++j)
+                    ++bcnt;
+                    if (b_lane) {
+                        const int j = lane - 8;
+                        if (*verr || (bu > 0 && !tc::mbar_wait(&bEmpty[bs], (bu - 1) & 1))) {
+                            *verr = 1;
+                            stop = true;
+                            break;
+                        }
+                        tc::mbar_arrive_expect_tx(&bFull[bs], HBLK);
                         tc::bulk_g2s(sbase + bs * BBUF + j * HBLK, ib + (size_t)(j * 2 + h) * SBLK + ch * HBLK, HBLK,
                                      &bFull[bs]);
-                    ++bcnt;
-                    for (int i = 0; i < S; ++i) {
+                    }
+                    for (int i = 0; i < S; ++i, ++acnt) {
                         const int as = acnt % NA;
+                        if (!a_lane || as != lane) continue;
                         const uint32_t au = acnt / NA;
-                        if (au > 0 && !tc::mbar_wait(&aEmpty[as], (au - 1) & 1)) { *verr = 1; break; }
+                        if (*verr || (au > 0 && !tc::mbar_wait(&aEmpty[as], (au - 1) & 1))) {
+                            *verr = 1;
+                            stop = true;
+                            break;
+                        }
                         tc::mbar_arrive_expect_tx(&aFull[as], SBLK);
                         tc::bulk_g2s(sbase + OFF_A + as * SBLK, ia + (size_t)(i * 2 + h) * SBLK, SBLK, &aFull[as]);
-                        ++acnt;
                     }
                 }
             }
@@ -633,24 +652,28 @@ __global__ void __launch_bounds__(pipe::NTHP, 1) k_trail_pipe(int mode, int Klo,
                     const int bs = bcnt & 1;
                     if (!tc::mbar_wait(&bFull[bs], (bcnt >> 1) & 1)) { *verr = 1; break; }
                     ++bcnt;
+                    const uint64_t b0 = tc::sdesc_sw128(tc::smem_u32(sbase + bs * BBUF));
+#pragma unroll
                     for (int i = 0; i < S; ++i) {
                         const int as = acnt % NA;
                         if (!tc::mbar_wait(&aFull[as], (acnt / NA) & 1)) { *verr = 1; break; }
                         ++acnt;
                         tc::fence_after_sync();
-                        const uint8_t *sA = sbase + OFF_A + as * SBLK;
-                        for (int j = 0; i + j < S; ++j) {
-                            const int g = i + j;
-                            const int acc = g < 3 ? g : 3;
+                        const uint64_t a0 = tc::sdesc_sw128(tc::smem_u32(sbase + OFF_A + as * SBLK));
+                        // The B slices sit back to back (64 rows each), so slices
+                        // j = 0 .. 3 - i, whose groups g = i + j are 0..3, go in one
+                        // MMA of N = 64 (4 - i) into accumulators i .. 3; slice 4 - i
+                        // (group 4) adds into accumulator 3.  Descriptor address
+                        // fields count 16 bytes: +2 per 16-element K step.
 #pragma unroll
-                            for (int kk = 0; kk < 4; ++kk) {
-                                const uint64_t ad = tc::sdesc_sw128(tc::smem_u32(sA) + kk * 32);
-                                const uint64_t bd = tc::sdesc_sw128(tc::smem_u32(sbase + bs * BBUF + j * HBLK) + kk * 32);
-                                const uint32_t accumulate = (h == 0 && kk == 0 && i == 0 && j <= 3) ? 0u : 1u;
-                                tc::mma_bf16(dacc + acc * 64, ad, bd, IDESC_N64, accumulate);
-                                issued = true;
-                            }
+                        for (int kk = 0; kk < 4; ++kk) {
+                            const uint64_t ad = a0 + 2 * kk, bk = b0 + 2 * kk;
+                            if (i < 4)
+                                tc::mma_bf16(dacc + 64 * i, ad, bk, tc::idesc_bf16_f32(128, 64 * (4 - i)),
+                                             (h == 0 && kk == 0 && i == 0) ? 0u : 1u);
+                            tc::mma_bf16(dacc + 3 * 64, ad, bk + (uint64_t)(((4 - i) * HBLK) >> 4), IDESC_N64, 1u);
                         }
+                        issued = true;
                         tc::mma_commit(&aEmpty[as]);   // the A stage is free once these MMAs finish
                     }
                     tc::mma_commit(&bEmpty[bs]);
@@ -839,12 +862,15 @@ __global__ void __launch_bounds__(NTH, 1) k_trail_split7x(int J, int nb, int64_t
     float *sDl = sDh + TB * DP;
     for (int ch = 0; ch < 2; ++ch) {
         for (int h = 0; h < 2; ++h) {
+            if (warp == 0 && s_ok) {   // one copy per lane: a thread's copies run one after another
+                if (lane == 0) tc::mbar_arrive_expect_tx(&bar_load, S7 * SBLK + S7 * HBLK);
+                __syncwarp();
+                if (lane < S7) tc::bulk_g2s(sA + lane * SBLK, ia + (size_t)(lane * 2 + h) * SBLK, SBLK, &bar_load);
+                else if (lane >= 8 && lane < 8 + S7)
+                    tc::bulk_g2s(sB + (lane - 8) * HBLK, ib + (size_t)((lane - 8) * 2 + h) * SBLK + ch * HBLK, HBLK,
+                                 &bar_load);
+            }
             if (tid == 0 && s_ok) {
-                tc::mbar_arrive_expect_tx(&bar_load, S7 * SBLK + S7 * HBLK);
-                for (int j = 0; j < S7; ++j) {
-                    tc::bulk_g2s(sA + j * SBLK, ia + (size_t)(j * 2 + h) * SBLK, SBLK, &bar_load);
-                    tc::bulk_g2s(sB + j * HBLK, ib + (size_t)(j * 2 + h) * SBLK + ch * HBLK, HBLK, &bar_load);
-                }
                 bool ok = tc::mbar_wait(&bar_load, phase);
                 if (!ok) tc::mbar_wait(&bar_load, phase);
                 if (ok) {
@@ -970,10 +996,13 @@ __global__ void __launch_bounds__(NTH, 1) k_trsm_split7x(int J, int nb, int64_t 
             }
             tc::fence_proxy_async();
             __syncthreads();
+            if (warp == 0 && s_ok) {   // one copy per lane: a thread's copies run one after another
+                if (lane == 0) tc::mbar_arrive_expect_tx(&bar_load, S7 * HBLK);
+                __syncwarp();
+                if (lane < S7)
+                    tc::bulk_g2s(sW + lane * HBLK, wi + (size_t)(lane * 2 + h) * SBLK + ch * HBLK, HBLK, &bar_load);
+            }
             if (tid == 0 && s_ok) {
-                tc::mbar_arrive_expect_tx(&bar_load, S7 * HBLK);
-                for (int j = 0; j < S7; ++j)
-                    tc::bulk_g2s(sW + j * HBLK, wi + (size_t)(j * 2 + h) * SBLK + ch * HBLK, HBLK, &bar_load);
                 bool ok = tc::mbar_wait(&bar_load, phase);
                 if (!ok) tc::mbar_wait(&bar_load, phase);
                 if (ok) {
