@@ -466,11 +466,6 @@ class Arena {
         }
         free_[off] = len;
     }
-    size_t largest_free() const {
-        size_t m = 0;
-        for (auto &f : free_) m = std::max(m, f.second);
-        return m;
-    }
     size_t size() const { return size_; }
     size_t used() const { return used_; }
     size_t high() const { return high_; }

@@ -321,7 +321,6 @@ __global__ void __launch_bounds__(256, 2) k_potrf_mixed(int J, int64_t tpo, doub
 // 32 (w / 4) .. +31 of each accumulator.
 // ---------------------------------------------------------------------------
 constexpr int NTH = 512;
-constexpr int SPAD = TB + 1;   // padded shared row: (r, c) -> bank (r + c) mod 32
 
 __device__ __forceinline__ void load_groups(uint32_t tb, int warp, int c0, uint32_t (&p0)[16], uint32_t (&p1)[16],
                                             uint32_t (&p2)[16], uint32_t (&p3)[16]) {
@@ -502,43 +501,51 @@ __global__ void __launch_bounds__(NTH, 1) k_trsm_split(int J, int nb, int64_t tp
 }
 
 // ---------------------------------------------------------------------------
-// Persistent, pipelined 5-slice trailing update.  One CTA per SM walks the
-// work items (omega, tile (I, K), column half) of one step.  Roles:
-//   warp 0     producer: bulk copies of the B half-rows (all 5 slices of one K
+// Persistent, pipelined trailing update with S = 5 or 7 slices.  One CTA per
+// SM walks the work items (omega, tile (I, K), column half) of one step.
+// Roles:
+//   warp 0     producer: bulk copies of the B half-rows (all S slices of one K
 //              half, double-buffered) and of the A slices (one slice of one K
-//              half per stage, 4-stage ring);
-//   warp 1     MMA issue into two alternating TMEM accumulator sets
-//              (2 sets x 4 groups x 64 columns = 512 columns);
+//              half per stage, NA-stage ring);
+//   warp 1     MMA issue.  S = 5: groups 0, 1, 2 and 3+ in two alternating
+//              TMEM accumulator sets (2 sets x 4 groups x 64 columns = 512);
+//              S = 7: the 7 groups each exact in one set (7 x 64 columns);
 //   warp 2     TMEM allocation;
-//   warps 4-7  epilogue: TMEM -> double-float deltas in padded shared rows,
-//              then a coalesced read-modify-write of the half tile, while the
-//              MMAs of the next item run.
+//   warps 4-11 epilogue: TMEM -> double-float deltas in padded shared rows,
+//              then a coalesced read-modify-write of the half tile (with two
+//              sets, while the MMAs of the next item run).
 // Barrier use u of a slot completes phase u; a waiter for use u waits for
 // parity (u & 1); the producer reusing a slot for use u >= 1 first waits for
 // the consumer's release of use u - 1.
 // ---------------------------------------------------------------------------
 namespace pipe {
-constexpr int S = 5;
 constexpr int NTHP = 384;                   // warps 0-3 roles, warps 4-11 epilogue
 constexpr int NEPI = NTHP - 128;
-constexpr int NA = 4;                       // A stages
-constexpr int BBUF = S * HBLK;              // 40 KB: one K half of 64 B rows, 5 slices
-constexpr int OFF_A = 2 * BBUF;             // 80 KB
-constexpr int OFF_D = OFF_A + NA * SBLK;    // 128 KB
 constexpr int DP = 64 + 1;
-constexpr int SMEM = OFF_D + 2 * TB * DP * 4 + 1024;
 constexpr uint32_t IDESC_N64 = tc::idesc_bf16_f32(128, 64);
+template <int S>
+struct Cfg {
+    static constexpr int NSET = (S == 5) ? 2 : 1;          // TMEM accumulator sets
+    static constexpr int NA = (S == 5) ? 4 : 2;            // A stages
+    static constexpr int BBUF = S * HBLK;                  // one K half of 64 B rows, S slices
+    static constexpr int OFF_A = 2 * BBUF;
+    static constexpr int OFF_D = OFF_A + NA * SBLK;
+    static constexpr int SMEM = OFF_D + 2 * TB * DP * 4 + 1024;
+};
 }  // namespace pipe
 
 // Item sets: mode 0 = the triangle Klo <= K <= I <= Ihi; mode 1 = the column
 // K = Klo, Klo <= I <= Ihi; mode 2 = the row I = Ihi, Klo <= K <= Ihi.  Each
 // item applies the P (1 or 2) panels in sub-slots sub0, sub1; with P = 2 both
-// operands use the common exponent (data rows only).
+// operands use the common exponent (data rows only; 5 slices only).
+template <int S>
 __global__ void __launch_bounds__(pipe::NTHP, 1) k_trail_pipe(int mode, int Klo, int Ihi, int P, int sub0, int sub1,
                                                              int nb, int cnt, int64_t tpo, double *__restrict__ tiles,
                                                              const uint8_t *__restrict__ pimg,
                                                              const double *__restrict__ oconst, int *__restrict__ err) {
     using namespace pipe;
+    constexpr int NSET = Cfg<S>::NSET, NA = Cfg<S>::NA, BBUF = Cfg<S>::BBUF, OFF_A = Cfg<S>::OFF_A,
+                  OFF_D = Cfg<S>::OFF_D;
     extern __shared__ uint8_t smraw[];
     uint8_t *sbase = align1024(smraw);
     __shared__ uint64_t bFull[2], bEmpty[2], aFull[NA], aEmpty[NA], accFull[2], accEmpty[2], drain;
@@ -642,8 +649,8 @@ __global__ void __launch_bounds__(pipe::NTHP, 1) k_trail_pipe(int mode, int Klo,
             uint32_t acnt = 0, bcnt = 0, tcnt = 0;
             bool issued = false;
             for (int64_t it = blockIdx.x; it < items && !*verr; it += gridDim.x, ++tcnt) {
-                const int set = tcnt & 1;
-                const uint32_t tu = tcnt >> 1;
+                const int set = (NSET == 2) ? (int)(tcnt & 1) : 0;
+                const uint32_t tu = (NSET == 2) ? tcnt >> 1 : tcnt;
                 if (tu > 0 && !tc::mbar_wait(&accEmpty[set], (tu - 1) & 1)) { *verr = 1; break; }
                 tc::fence_after_sync();
                 const uint32_t dacc = tb + set * 256;
@@ -668,10 +675,19 @@ __global__ void __launch_bounds__(pipe::NTHP, 1) k_trail_pipe(int mode, int Klo,
 #pragma unroll
                         for (int kk = 0; kk < 4; ++kk) {
                             const uint64_t ad = a0 + 2 * kk, bk = b0 + 2 * kk;
-                            if (i < 4)
-                                tc::mma_bf16(dacc + 64 * i, ad, bk, tc::idesc_bf16_f32(128, 64 * (4 - i)),
-                                             (h == 0 && kk == 0 && i == 0) ? 0u : 1u);
-                            tc::mma_bf16(dacc + 3 * 64, ad, bk + (uint64_t)(((4 - i) * HBLK) >> 4), IDESC_N64, 1u);
+                            const uint32_t acc = (h == 0 && kk == 0 && i == 0) ? 0u : 1u;
+                            if (S == 5) {
+                                if (i < 4) tc::mma_bf16(dacc + 64 * i, ad, bk, tc::idesc_bf16_f32(128, 64 * (4 - i)), acc);
+                                tc::mma_bf16(dacc + 3 * 64, ad, bk + (uint64_t)(((4 - i) * HBLK) >> 4), IDESC_N64, 1u);
+                            } else {
+                                // every group exact: slices j = 0 .. S-1-i into accumulators
+                                // i .. S-1, at most four slices (N = 256) per MMA
+                                const int nj = S - i, n1 = nj < 4 ? nj : 4;
+                                tc::mma_bf16(dacc + 64 * i, ad, bk, tc::idesc_bf16_f32(128, 64 * n1), acc);
+                                if (nj > 4)
+                                    tc::mma_bf16(dacc + 64 * (i + 4), ad, bk + (uint64_t)((4 * HBLK) >> 4),
+                                                 tc::idesc_bf16_f32(128, 64 * (nj - 4)), acc);
+                            }
                         }
                         issued = true;
                         tc::mma_commit(&aEmpty[as]);   // the A stage is free once these MMAs finish
@@ -706,9 +722,9 @@ __global__ void __launch_bounds__(pipe::NTHP, 1) k_trail_pipe(int mode, int Klo,
                 else if (et < TB + 64)
                     sEB[et - TB] = (short)reinterpret_cast<const int *>(ib + (size_t)S * 2 * SBLK)[64 * ch + et - TB];
             }
-            const int set = tcnt & 1;
+            const int set = (NSET == 2) ? (int)(tcnt & 1) : 0;
             if (et == 0) {   // one thread waits and decides for all 128
-                const bool ok = tc::mbar_wait(&accFull[set], (tcnt >> 1) & 1);
+                const bool ok = tc::mbar_wait(&accFull[set], ((NSET == 2) ? tcnt >> 1 : tcnt) & 1);
                 if (!ok) *verr = 1;
                 s_stop = (!ok || *verr) ? 1 : 0;
             }
@@ -719,18 +735,43 @@ __global__ void __launch_bounds__(pipe::NTHP, 1) k_trail_pipe(int mode, int Klo,
             const int ea = sEA[r] - 14;
 #pragma unroll 1
             for (int c0 = 32 * cpart; c0 < 32 * cpart + 32; c0 += 16) {
-                uint32_t p0[16], p1[16], p2[16], p3[16];
-                tc::tmem_ld16(a + 0 * 64 + c0, p0);
-                tc::tmem_ld16(a + 1 * 64 + c0, p1);
-                tc::tmem_ld16(a + 2 * 64 + c0, p2);
-                tc::tmem_ld16(a + 3 * 64 + c0, p3);
-                tc::tmem_wait_ld();
+                if (S == 5) {
+                    uint32_t p0[16], p1[16], p2[16], p3[16];
+                    tc::tmem_ld16(a + 0 * 64 + c0, p0);
+                    tc::tmem_ld16(a + 1 * 64 + c0, p1);
+                    tc::tmem_ld16(a + 2 * 64 + c0, p2);
+                    tc::tmem_ld16(a + 3 * 64 + c0, p3);
+                    tc::tmem_wait_ld();
 #pragma unroll
-                for (int c = 0; c < 16; ++c) {
-                    float hi, lo;
-                    group_value(p0[c], p1[c], p2[c], p3[c], ea + sEB[c0 + c], hi, lo);
-                    sDh[r * DP + c0 + c] = hi;
-                    sDl[r * DP + c0 + c] = lo;
+                    for (int c = 0; c < 16; ++c) {
+                        float hi, lo;
+                        group_value(p0[c], p1[c], p2[c], p3[c], ea + sEB[c0 + c], hi, lo);
+                        sDh[r * DP + c0 + c] = hi;
+                        sDl[r * DP + c0 + c] = lo;
+                    }
+                } else {
+                    float hi[16], lo[16];
+#pragma unroll 1
+                    for (int g = 0; g < S; ++g) {
+                        uint32_t pg[16];
+                        tc::tmem_ld16(a + g * 64 + c0, pg);
+                        tc::tmem_wait_ld();
+#pragma unroll
+                        for (int c = 0; c < 16; ++c) {
+                            const float v = __uint_as_float(pg[c]) * pow2f(ea + sEB[c0 + c]);
+                            if (g == 0) {
+                                hi[c] = v;
+                                lo[c] = 0.0f;
+                            } else {
+                                df_add(hi[c], lo[c], v);
+                            }
+                        }
+                    }
+#pragma unroll
+                    for (int c = 0; c < 16; ++c) {
+                        sDh[r * DP + c0 + c] = hi[c];
+                        sDl[r * DP + c0 + c] = lo[c];
+                    }
                 }
             }
             tc::fence_before_sync();
@@ -778,21 +819,22 @@ __global__ void __launch_bounds__(pipe::NTHP, 1) k_trail_pipe(int mode, int Klo,
 // 5-slice error bound was too large.
 // ---------------------------------------------------------------------------
 constexpr int S7 = 7;
-constexpr uint32_t IDESC64 = tc::idesc_bf16_f32(128, 64);
 
 __device__ __forceinline__ void issue_exact_mmas7(uint32_t tb, const uint8_t *sA, const uint8_t *sB, bool first_half) {
-#pragma unroll 1
-    for (int i = 0; i < S7; ++i) {
-#pragma unroll 1
-        for (int j = 0; i + j < S7; ++j) {
-            const int g = i + j;
+    // B slices are back to back (64 rows each): slices j = 0 .. 6 - i go into
+    // accumulators i .. 6 in at most two MMAs of N <= 256.
+    const uint64_t a0 = tc::sdesc_sw128(tc::smem_u32(sA)), b0 = tc::sdesc_sw128(tc::smem_u32(sB));
 #pragma unroll
-            for (int kk = 0; kk < 4; ++kk) {
-                const uint64_t ad = tc::sdesc_sw128(tc::smem_u32(sA + i * SBLK) + kk * 32);
-                const uint64_t bd = tc::sdesc_sw128(tc::smem_u32(sB + j * HBLK) + kk * 32);
-                const uint32_t accumulate = (first_half && kk == 0 && i == 0) ? 0u : 1u;
-                tc::mma_bf16(tb + g * 64, ad, bd, IDESC64, accumulate);
-            }
+    for (int i = 0; i < S7; ++i) {
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) {
+            const uint64_t ad = a0 + (uint64_t)((i * SBLK + kk * 32) >> 4), bk = b0 + 2 * kk;
+            const uint32_t accumulate = (first_half && kk == 0 && i == 0) ? 0u : 1u;
+            const int nj = S7 - i, n1 = nj < 4 ? nj : 4;
+            tc::mma_bf16(tb + i * 64, ad, bk, tc::idesc_bf16_f32(128, 64 * n1), accumulate);
+            if (nj > 4)
+                tc::mma_bf16(tb + (i + 4) * 64, ad, bk + (uint64_t)((4 * HBLK) >> 4),
+                             tc::idesc_bf16_f32(128, 64 * (nj - 4)), accumulate);
         }
     }
 }
@@ -818,112 +860,6 @@ __device__ __forceinline__ void exact_values7(uint32_t tb, int warp, int cb, con
             }
         }
     }
-}
-
-__global__ void __launch_bounds__(NTH, 1) k_trail_split7x(int J, int nb, int64_t tpo, double *__restrict__ tiles,
-                                                          const uint8_t *__restrict__ pimg, int *__restrict__ err) {
-    extern __shared__ uint8_t smraw[];
-    uint8_t *sbase = align1024(smraw);
-    uint8_t *sA = sbase;                 // 7 x 16 KB: one K half of the A slices
-    uint8_t *sB = sbase + S7 * SBLK;     // 7 x 8 KB: one K half of 64 B rows
-    __shared__ uint64_t bar_load, bar_mma;
-    __shared__ uint32_t tmem_base;
-    __shared__ short sEA[TB], sEB[TB];
-    __shared__ int s_ok;
-    const int w = blockIdx.y;
-    int I, K;
-    decode_trailing(blockIdx.x, J, I, K);
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const uint8_t *ia = pimg + ((int64_t)w * (nb + 1) + I) * SLOT;
-    const uint8_t *ib = pimg + ((int64_t)w * (nb + 1) + K) * SLOT;
-    if (warp == 0) {
-        tc::tmem_alloc(&tmem_base, 512);
-        tc::tmem_relinquish();
-    }
-    if (tid == 0) {
-        tc::mbar_init(&bar_load, 1);
-        tc::mbar_init(&bar_mma, 1);
-        tc::fence_mbar_init();
-        s_ok = 1;
-    }
-    if (tid < TB) {
-        sEA[tid] = (short)reinterpret_cast<const int *>(ia + (size_t)S7 * 2 * SBLK)[tid];
-        sEB[tid] = (short)reinterpret_cast<const int *>(ib + (size_t)S7 * 2 * SBLK)[tid];
-    }
-    tc::fence_before_sync();
-    __syncthreads();
-    tc::fence_after_sync();
-    const uint32_t tb = tmem_base;
-    uint32_t phase = 0;
-    float *gH = reinterpret_cast<float *>(tiles + ((int64_t)w * tpo + tile_index(I, K)) * NT);
-    float *gL = gH + NT;
-    constexpr int DP = 64 + 1;   // padded delta row
-    float *sDh = reinterpret_cast<float *>(sbase);
-    float *sDl = sDh + TB * DP;
-    for (int ch = 0; ch < 2; ++ch) {
-        for (int h = 0; h < 2; ++h) {
-            if (warp == 0 && s_ok) {   // one copy per lane: a thread's copies run one after another
-                if (lane == 0) tc::mbar_arrive_expect_tx(&bar_load, S7 * SBLK + S7 * HBLK);
-                __syncwarp();
-                if (lane < S7) tc::bulk_g2s(sA + lane * SBLK, ia + (size_t)(lane * 2 + h) * SBLK, SBLK, &bar_load);
-                else if (lane >= 8 && lane < 8 + S7)
-                    tc::bulk_g2s(sB + (lane - 8) * HBLK, ib + (size_t)((lane - 8) * 2 + h) * SBLK + ch * HBLK, HBLK,
-                                 &bar_load);
-            }
-            if (tid == 0 && s_ok) {
-                bool ok = tc::mbar_wait(&bar_load, phase);
-                if (!ok) tc::mbar_wait(&bar_load, phase);
-                if (ok) {
-                    tc::fence_after_sync();
-                    issue_exact_mmas7(tb, sA, sB, h == 0);
-                    tc::mma_commit(&bar_mma);
-                    ok = tc::mbar_wait(&bar_mma, phase);
-                    if (!ok) tc::mbar_wait(&bar_mma, phase);
-                }
-                if (!ok) {
-                    s_ok = 0;
-                    atomicExch(err, 1);
-                }
-            }
-            phase ^= 1;
-            tc::fence_before_sync();
-            __syncthreads();
-            tc::fence_after_sync();
-        }
-        const bool ok = s_ok != 0;
-        if (ok) {
-            const int r = 32 * (warp & 3) + lane;
-            const int cb = 16 * (warp >> 2);   // 0..48 within the half
-            float hi[16], lo[16];
-            exact_values7(tb, warp, cb, sEB + 64 * ch + cb, sEA[r] - 14, hi, lo);
-#pragma unroll
-            for (int c = 0; c < 16; ++c) {
-                sDh[r * DP + cb + c] = hi[c];
-                sDl[r * DP + cb + c] = lo[c];
-            }
-        }
-        tc::fence_before_sync();
-        __syncthreads();
-        tc::fence_after_sync();
-        if (ok) {
-#pragma unroll 4
-            for (int u = 0; u < (TB * 64) / NTH; ++u) {
-                const int e = tid + NTH * u;
-                const int r = e >> 6, c = e & 63;
-                const int gi = r * TB + 64 * ch + c;
-                float hv = gH[gi], lv = gL[gi];
-                df_add(hv, lv, -sDh[r * DP + c]);
-                df_add(hv, lv, -sDl[r * DP + c]);
-                gH[gi] = hv;
-                gL[gi] = lv;
-            }
-        }
-        __syncthreads();
-    }
-    tc::fence_before_sync();
-    __syncthreads();
-    tc::fence_after_sync();
-    if (warp == 0) tc::tmem_dealloc(tb, 512);
 }
 
 // Panel solve with 7 exact groups: the two column halves of L_IJ are written
@@ -1127,13 +1063,13 @@ static cudaError_t launch_mixed_steps(const BatchArgs &b, const MixedArgs &x, cu
                                   (int)POTRF_MIXED_SMEM)) != cudaSuccess)
         return e;
     cudaMemsetAsync(x.invsum, 0, sizeof(double) * cnt, s);
+    const int sms = num_sms();
     if (S == 7) {
-        const int smem_trail7 = S7 * (SBLK + HBLK) + 1024;
         if ((e = cudaFuncSetAttribute(k_trsm_split7x, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_split)) !=
             cudaSuccess)
             return e;
-        if ((e = cudaFuncSetAttribute(k_trail_split7x, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_trail7)) !=
-            cudaSuccess)
+        if ((e = cudaFuncSetAttribute(k_trail_pipe<7>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      pipe::Cfg<7>::SMEM)) != cudaSuccess)
             return e;
         for (int J = 0; J < nb; ++J) {
             TIMED(KC_POTRF_MIXED, (k_potrf_mixed<S><<<cnt, 256, POTRF_MIXED_SMEM, s>>>(
@@ -1141,23 +1077,25 @@ static cudaError_t launch_mixed_steps(const BatchArgs &b, const MixedArgs &x, cu
             const int m = nb - J;
             TIMED(KC_TRSM_SPLIT7, (k_trsm_split7x<<<dim3(m, cnt), NTH, smem_split, s>>>(J, nb, b.tpo, b.tiles, x.wimg,
                                                                                       x.pimg, x.err)));
-            TIMED(KC_GEMM_SPLIT7, (k_trail_split7x<<<dim3(m * (m + 1) / 2, cnt), NTH, smem_trail7, s>>>(
-                                      J, nb, b.tpo, b.tiles, x.pimg, x.err)));
+            // trailing triangle J+1 <= K <= I <= nb (data rows and the right-hand-side row)
+            const int64_t items = (int64_t)cnt * (m * (m + 1) / 2) * 2;
+            const int grid = (int)std::min<int64_t>(items, sms);
+            TIMED(KC_GEMM_SPLIT7, (k_trail_pipe<7><<<grid, pipe::NTHP, pipe::Cfg<7>::SMEM, s>>>(
+                                      0, J + 1, nb, 1, 0, 0, nb, cnt, b.tpo, b.tiles, x.pimg, b.oconst, x.err)));
         }
     } else {
         if ((e = cudaFuncSetAttribute(k_trsm_split<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_split)) !=
             cudaSuccess)
             return e;
-        if ((e = cudaFuncSetAttribute(k_trail_pipe, cudaFuncAttributeMaxDynamicSharedMemorySize, pipe::SMEM)) !=
-            cudaSuccess)
+        if ((e = cudaFuncSetAttribute(k_trail_pipe<5>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      pipe::Cfg<5>::SMEM)) != cudaSuccess)
             return e;
-        const int sms = num_sms();
         auto trail = [&](int mode, int Klo, int Ihi, int P, int sub0, int sub1) {
             const int m = Ihi - Klo + 1;
             if (m <= 0) return;
             const int64_t items = (int64_t)cnt * ((mode == 0) ? m * (m + 1) / 2 : m) * 2;
             const int grid = (int)std::min<int64_t>(items, sms);
-            TIMED(KC_GEMM_SPLIT, (k_trail_pipe<<<grid, pipe::NTHP, pipe::SMEM, s>>>(
+            TIMED(KC_GEMM_SPLIT, (k_trail_pipe<5><<<grid, pipe::NTHP, pipe::Cfg<5>::SMEM, s>>>(
                                      mode, Klo, Ihi, P, sub0, sub1, nb, cnt, b.tpo, b.tiles, x.pimg, b.oconst, x.err)));
         };
         auto factor_panel = [&](int J) {
