@@ -230,8 +230,103 @@ extern "C" const char *plk_kernel_class_name(int32_t c) { return kernel_class_na
 // this synchronizes the stream once per batch.
 static const double kMixedTol = 1e-4;   // bound on |Delta log L| that triggers the retry
 
+// Slots [off, off + cnt) of a mixed batch as a batch of their own.
+static void sub_batch(const BatchArgs &b, const MixedArgs &x, int off, int cnt, BatchArgs &bo, MixedArgs &xo) {
+    bo = b;
+    xo = x;
+    bo.count = cnt;
+    bo.k0 = b.k0 + off;
+    bo.params = b.params + 5 * (size_t)off;
+    bo.oconst = b.oconst + (size_t)OC_N * off;
+    bo.coordT = b.coordT + (size_t)2 * b.n_pad * off;
+    bo.tab = b.tab + (size_t)TAB_SIZE * off;
+    bo.tiles = b.tiles + (size_t)b.tpo * NT * off;
+    bo.inv = b.inv + (size_t)NT * off;
+    bo.ldv = b.ldv + off;
+    bo.pstatus = b.pstatus + off;
+    xo.wimg = x.wimg + mixed_img_bytes(5) * (size_t)off;   // slot stride of the 5-slice pass
+    xo.pimg = x.pimg + mixed_slot_bytes() * (size_t)(b.nb + 1) * off;
+    xo.invsum = x.invsum + off;
+    xo.flags = x.flags + off;
+}
+
+// Two streams of the calling thread on the current device, created on first
+// use and kept for the thread's lifetime: [0] at the highest priority (the
+// factorisation), [1] at the lowest (the overlapped build).  With the build on
+// the low-priority stream, the block scheduler hands freed SM resources to the
+// factorisation kernels first.
+struct AuxStreams {
+    cudaStream_t hi = nullptr, lo = nullptr;
+};
+static AuxStreams aux_streams() {
+    struct Table {
+        std::map<int, AuxStreams> m;
+        ~Table() {
+            for (auto &kv : m) {
+                cudaStreamDestroy(kv.second.hi);
+                cudaStreamDestroy(kv.second.lo);
+            }
+        }
+    };
+    thread_local Table t;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return {};
+    auto it = t.m.find(dev);
+    if (it != t.m.end()) return it->second;
+    int least = 0, greatest = 0;
+    AuxStreams st;
+    if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess ||
+        cudaStreamCreateWithPriority(&st.hi, cudaStreamNonBlocking, greatest) != cudaSuccess)
+        return {};
+    if (cudaStreamCreateWithPriority(&st.lo, cudaStreamNonBlocking, least) != cudaSuccess) {
+        cudaStreamDestroy(st.hi);
+        return {};
+    }
+    t.m[dev] = st;
+    return st;
+}
+
+// 5-slice pass over the batch.  With `overlap` and enough points, the batch is
+// cut in two halves and the build of the second half (FP64 pipe, no shared
+// memory) runs beside the factorisation of the first half (tensor cores); the
+// second half is factored after both.  The work is forked from `s` onto the
+// two internal streams and joined back into `s`.
+static cudaError_t mixed_first_pass(const BatchArgs &b, const MixedArgs &x, bool overlap, cudaStream_t s) {
+    constexpr int kOverlapMin = 256;
+    const AuxStreams st = overlap && b.count >= kOverlapMin ? aux_streams() : AuxStreams{};
+    if (!st.hi) return launch_mixed_batch(b, x, 5, s);
+    const int c0 = b.count / 2;
+    BatchArgs b0, b1;
+    MixedArgs x0, x1;
+    sub_batch(b, x, 0, c0, b0, x0);
+    sub_batch(b, x, c0, b.count - c0, b1, x1);
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < 4 && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[0], s);               // fork
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st.hi, ev[0], 0);
+    if (e == cudaSuccess) e = launch_front(b0, st.hi, true);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[1], st.hi);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st.lo, ev[1], 0);
+    if (e == cudaSuccess) e = launch_front(b1, st.lo, true);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[2], st.lo);
+    if (e == cudaSuccess) e = launch_mixed_back(b0, x0, 5, st.hi);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st.hi, ev[2], 0);
+    if (e == cudaSuccess) e = launch_mixed_back(b1, x1, 5, st.hi);
+    if (ev[3]) {   // join, also after a failed launch: nothing may run on past `s`
+        cudaEventRecord(ev[1], st.lo);
+        cudaStreamWaitEvent(st.hi, ev[1], 0);
+        const cudaError_t j = cudaEventRecord(ev[3], st.hi);
+        const cudaError_t k = j == cudaSuccess ? cudaStreamWaitEvent(s, ev[3], 0) : j;
+        if (e == cudaSuccess) e = k;
+    }
+    for (int i = 0; i < 4; ++i)
+        if (ev[i]) cudaEventDestroy(ev[i]);   // released once the recorded work completes
+    return e;
+}
+
 static plk_status run_mixed_batch(BatchArgs b, const Layout &L, void *ws, const double *params_all, int flags,
-                                  double *err_bound, cudaStream_t s) {
+                                  double *err_bound, bool overlap, cudaStream_t s) {
     MixedArgs x;
     x.wimg = at<uint8_t>(ws, L.off_wimg);
     x.pimg = at<uint8_t>(ws, L.off_pimg);
@@ -241,7 +336,7 @@ static plk_status run_mixed_batch(BatchArgs b, const Layout &L, void *ws, const 
     x.err_bound = err_bound;
     x.tol = kMixedTol;
     cudaError_t e = cudaMemsetAsync(x.err, 0, sizeof(int), s);
-    if (e == cudaSuccess) e = launch_mixed_batch(b, x, 5, s);
+    if (e == cudaSuccess) e = mixed_first_pass(b, x, overlap, s);
     if (e != cudaSuccess) return cuda_fail(e, "mixed batch launch");
     std::vector<int> hf(b.count + 1);
     e = cudaMemcpyAsync(hf.data(), x.flags, sizeof(int) * b.count, cudaMemcpyDeviceToHost, s);
@@ -331,7 +426,7 @@ static plk_status run_eval(const plk_eval_args *a, int reml, int flags, const La
         b.status = a->status;
         b.timer = timer;
         if (L.mixed) {
-            plk_status st = run_mixed_batch(b, L, ws, a->params, flags, a->err_bound, s);
+            plk_status st = run_mixed_batch(b, L, ws, a->params, flags, a->err_bound, true, s);
             if (st != PLK_OK) return st;
         } else {
             e = launch_fp64_batch(b, s);
@@ -634,7 +729,7 @@ std::string run_item(Job *j, Item &it, cudaStream_t s) {
     cudaStreamWaitEvent(s, j->ready, 0);   // the job's B^T may come from another stream
     std::string err;
     if (L.mixed) {
-        plk_status st = run_mixed_batch(b, L, it.ws, j->d_params, j->opts.flags, nullptr, s);
+        plk_status st = run_mixed_batch(b, L, it.ws, j->d_params, j->opts.flags, nullptr, false, s);
         if (st != PLK_OK) err = plk_last_error();
     } else {
         cudaError_t e = launch_fp64_batch(b, s);

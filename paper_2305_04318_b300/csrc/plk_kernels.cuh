@@ -69,6 +69,8 @@ struct MixedArgs {
 size_t mixed_img_bytes(int S);
 size_t mixed_slot_bytes();   // panel slot of one tile row
 cudaError_t launch_mixed_batch(const BatchArgs &b, const MixedArgs &x, int S, cudaStream_t s);
+// the batch after launch_front(b, s, true): factorisation, closed form, error bound
+cudaError_t launch_mixed_back(const BatchArgs &b, const MixedArgs &x, int S, cudaStream_t s);
 cudaError_t launch_gather_params(int count, const int *idx, const double *params, double *out, cudaStream_t s);
 cudaError_t launch_scatter_value(int count, const int *idx, double v, double *out, cudaStream_t s);
 

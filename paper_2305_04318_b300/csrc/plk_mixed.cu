@@ -1130,7 +1130,11 @@ static cudaError_t launch_mixed_steps(const BatchArgs &b, const MixedArgs &x, cu
 cudaError_t launch_mixed_batch(const BatchArgs &b, const MixedArgs &x, int S, cudaStream_t s) {
     cudaError_t e = launch_front(b, s, true);   // builds double-float tiles directly
     if (e != cudaSuccess) return e;
-    e = (S == 7) ? launch_mixed_steps<7>(b, x, s) : launch_mixed_steps<5>(b, x, s);
+    return launch_mixed_back(b, x, S, s);
+}
+
+cudaError_t launch_mixed_back(const BatchArgs &b, const MixedArgs &x, int S, cudaStream_t s) {
+    cudaError_t e = (S == 7) ? launch_mixed_steps<7>(b, x, s) : launch_mixed_steps<5>(b, x, s);
     if (e != cudaSuccess) return e;
     if ((e = launch_finalize(b, s)) != cudaSuccess) return e;
     // eps: relative perturbation of the updated entries.  Calibrated on the

@@ -91,6 +91,20 @@ def test_mixed_deterministic_and_batch_independent():
         np.testing.assert_array_equal(a[k], c[k])
 
 
+def test_mixed_overlapped_halves_identical():
+    """A batch of >= 256 points runs in two halves, the second half's build
+    beside the first half's factorisation on a second stream; the results are
+    those of small batches that run without overlap, bit for bit."""
+    ds = synth.aniso_dataset(77, 700, math.sqrt(70), 3)
+    P = synth.omega_from_unit(np.random.default_rng(77).uniform(size=(300, 5)))
+    lams = synth.LAMBDA_GRID_9
+    a = gpu_eval(ds, P, lams, precision=nv.MIXED, batch=300)
+    b = gpu_eval(ds, P, lams, precision=nv.MIXED, batch=100)
+    for k in ("logL", "sigma2", "beta", "logdet", "status", "err_bound"):
+        np.testing.assert_array_equal(a[k], b[k], err_msg=k)
+    assert (a["status"] & 15 == 0).sum() > 250
+
+
 @pytest.mark.slow
 def test_mixed4000_full_size_sampled():
     """The n=4000 workload at full size in the bench's launch configuration:
