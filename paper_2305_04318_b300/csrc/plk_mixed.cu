@@ -19,12 +19,15 @@
 // The product is 2^(eA + eB - 14) (P0 + P1 + P2 + P3).  S = 5 slices keep
 // about 39 bits of every row, S = 7 about 55; the double-float epilogue keeps
 // about 48.
+#include <cuda.h>   // CUtensorMap (the driver function is looked up at run time)
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
+#include <cudaTypedefs.h>
 #include <math.h>
 #include <stdint.h>
 
 #include <algorithm>
+#include <mutex>
 
 #include "plk.h"
 #include "plk_common.cuh"
@@ -123,18 +126,28 @@ __device__ __forceinline__ uint8_t *align1024(uint8_t *p) {
 // Issue the S-slice split products of one K half into the four accumulators.
 template <int S>
 __device__ __forceinline__ void issue_split_mmas(uint32_t tb, const uint8_t *sA, const uint8_t *sB, bool first_half) {
-#pragma unroll 1
-    for (int i = 0; i < S; ++i) {
-#pragma unroll 1
-        for (int j = 0; i + j < S; ++j) {
-            const int g = i + j;
-            const int acc = g < 3 ? g : 3;
+    // B slices are back to back (128 rows each): two adjacent slices whose
+    // groups both have their own accumulator (g + 1 <= 3) go in one MMA of
+    // N = 256 into two adjacent accumulators; the rest add into accumulator
+    // min(g, 3) with N = 128.
+    const uint64_t a0 = tc::sdesc_sw128(tc::smem_u32(sA)), b0 = tc::sdesc_sw128(tc::smem_u32(sB));
 #pragma unroll
-            for (int kk = 0; kk < 4; ++kk) {
-                const uint64_t ad = tc::sdesc_sw128(tc::smem_u32(sA + i * SBLK) + kk * 32);
-                const uint64_t bd = tc::sdesc_sw128(tc::smem_u32(sB + j * SBLK) + kk * 32);
+    for (int i = 0; i < S; ++i) {
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) {
+            const uint64_t ad = a0 + (uint64_t)((i * SBLK + kk * 32) >> 4);
+#pragma unroll
+            for (int j = 0; i + j < S;) {
+                const int g = i + j;
+                const uint64_t bd = b0 + (uint64_t)((j * SBLK + kk * 32) >> 4);
                 const uint32_t accumulate = (first_half && kk == 0 && i == 0 && j <= 3) ? 0u : 1u;
-                tc::mma_bf16(tb + acc * 128, ad, bd, IDESC, accumulate);
+                if (g + 1 <= 3 && g + 1 < S) {
+                    tc::mma_bf16(tb + g * 128, ad, bd, tc::idesc_bf16_f32(128, 256), accumulate);
+                    j += 2;
+                } else {
+                    tc::mma_bf16(tb + (g < 3 ? g : 3) * 128, ad, bd, IDESC, accumulate);
+                    j += 1;
+                }
             }
         }
     }
@@ -445,7 +458,8 @@ __global__ void __launch_bounds__(NTH, 1) k_trsm_split(int J, int nb, int64_t tp
     const bool ok = s_ok != 0;
     const int r = 32 * (warp & 3) + lane;   // this thread's row, columns 32 (warp / 4) .. +31
     const int cb = 32 * (warp >> 2);
-    if (ok) {
+    const bool data_rows = I < nb;          // common exponent: no row maximum needed
+    if (ok && !data_rows) {
         float mx = 0.0f;
 #pragma unroll 1
         for (int c0 = 0; c0 < 32; c0 += 16) {
@@ -466,7 +480,7 @@ __global__ void __launch_bounds__(NTH, 1) k_trsm_split(int J, int nb, int64_t tp
         const float mx = __int_as_float(sMx[r]);
         // data rows: the common exponent (lets two panels share one accumulator);
         // right-hand-side rows: their own maximum
-        const int eo = (I < nb) ? common_exp(oconst[OC_N * (int64_t)w + OC_NUG]) : row_exp(mx * (1.0f + 1.0f / 1024.0f));
+        const int eo = data_rows ? common_exp(oconst[OC_N * (int64_t)w + OC_NUG]) : row_exp(mx * (1.0f + 1.0f / 1024.0f));
         if (warp < 4) sEO[r] = (short)eo;
 #pragma unroll 1
         for (int c0 = 0; c0 < 32; c0 += 16) {
@@ -511,9 +525,12 @@ __global__ void __launch_bounds__(NTH, 1) k_trsm_split(int J, int nb, int64_t tp
 //              TMEM accumulator sets (2 sets x 4 groups x 64 columns = 512);
 //              S = 7: the 7 groups each exact in one set (7 x 64 columns);
 //   warp 2     TMEM allocation;
-//   warps 4-11 epilogue: TMEM -> double-float deltas in padded shared rows,
-//              then a coalesced read-modify-write of the half tile (with two
-//              sets, while the MMAs of the next item run).
+//   warps 4-11 epilogue: the half tile of C (double-float planes) arrives by
+//              TMA (tensor map over the tile array, 128-byte swizzle) while
+//              the item's MMAs run; each thread subtracts its row's TMEM
+//              values in shared memory and one thread stores the half tile
+//              back by TMA (with two sets, while the MMAs of the next item
+//              run).
 // Barrier use u of a slot completes phase u; a waiter for use u waits for
 // parity (u & 1); the producer reusing a slot for use u >= 1 first waits for
 // the consumer's release of use u - 1.
@@ -521,16 +538,16 @@ __global__ void __launch_bounds__(NTH, 1) k_trsm_split(int J, int nb, int64_t tp
 namespace pipe {
 constexpr int NTHP = 384;                   // warps 0-3 roles, warps 4-11 epilogue
 constexpr int NEPI = NTHP - 128;
-constexpr int DP = 64 + 1;
 constexpr uint32_t IDESC_N64 = tc::idesc_bf16_f32(128, 64);
+constexpr int CBOX = TB * 32 * 4;   // one tensor-map box: 128 rows x 32 floats (128-byte swizzle)
 template <int S>
 struct Cfg {
     static constexpr int NSET = (S == 5) ? 2 : 1;          // TMEM accumulator sets
-    static constexpr int NA = (S == 5) ? 4 : 2;            // A stages
+    static constexpr int NA = (S == 5) ? 5 : 3;            // A stages
     static constexpr int BBUF = S * HBLK;                  // one K half of 64 B rows, S slices
     static constexpr int OFF_A = 2 * BBUF;
-    static constexpr int OFF_D = OFF_A + NA * SBLK;
-    static constexpr int SMEM = OFF_D + 2 * TB * DP * 4 + 1024;
+    static constexpr int OFF_C = OFF_A + NA * SBLK;        // C half tile: 4 boxes of 128 x 32 floats
+    static constexpr int SMEM = OFF_C + 4 * CBOX + 1024;
 };
 }  // namespace pipe
 
@@ -540,15 +557,16 @@ struct Cfg {
 // operands use the common exponent (data rows only; 5 slices only).
 template <int S>
 __global__ void __launch_bounds__(pipe::NTHP, 1) k_trail_pipe(int mode, int Klo, int Ihi, int P, int sub0, int sub1,
-                                                             int nb, int cnt, int64_t tpo, double *__restrict__ tiles,
+                                                             int nb, int cnt, int64_t tpo,
+                                                             const __grid_constant__ CUtensorMap tmapC,
                                                              const uint8_t *__restrict__ pimg,
                                                              const double *__restrict__ oconst, int *__restrict__ err) {
     using namespace pipe;
     constexpr int NSET = Cfg<S>::NSET, NA = Cfg<S>::NA, BBUF = Cfg<S>::BBUF, OFF_A = Cfg<S>::OFF_A,
-                  OFF_D = Cfg<S>::OFF_D;
+                  OFF_C = Cfg<S>::OFF_C;
     extern __shared__ uint8_t smraw[];
     uint8_t *sbase = align1024(smraw);
-    __shared__ uint64_t bFull[2], bEmpty[2], aFull[NA], aEmpty[NA], accFull[2], accEmpty[2], drain;
+    __shared__ uint64_t bFull[2], bEmpty[2], aFull[NA], aEmpty[NA], accFull[2], accEmpty[2], cFull, drain;
     __shared__ uint32_t tmem_base;
     __shared__ short sEA[TB], sEB[64];
     __shared__ int s_err, s_stop;
@@ -569,6 +587,7 @@ __global__ void __launch_bounds__(pipe::NTHP, 1) k_trail_pipe(int mode, int Klo,
             tc::mbar_init(&aEmpty[i], 1);
         }
         tc::mbar_init(&drain, 1);
+        tc::mbar_init(&cFull, 1);
         tc::fence_mbar_init();
         s_err = 0;
     }
@@ -703,15 +722,29 @@ __global__ void __launch_bounds__(pipe::NTHP, 1) k_trail_pipe(int mode, int Klo,
             }
         }
     } else if (warp >= 4) {
-        const int et = tid - 128;          // 0..NEPI-1
-        const int r = 32 * (warp & 3) + lane;
-        const int cpart = (warp - 4) >> 2;   // columns 32 cpart .. +31 of the half
-        float *sDh = reinterpret_cast<float *>(sbase + OFF_D);
-        float *sDl = sDh + TB * DP;
+        const int et = tid - 128;            // 0..NEPI-1
+        const int r = 32 * (warp & 3) + lane;   // this thread's row (its TMEM lane)
+        const int q = (warp - 4) >> 2;       // columns 32 q .. 32 q + 31 of the half: box q
+        uint8_t *sC = sbase + OFF_C;         // boxes [H, q = 0 | H, q = 1 | L, q = 0 | L, q = 1]
+        float4 *rowH = reinterpret_cast<float4 *>(sC + q * CBOX + r * 128);
+        float4 *rowL = reinterpret_cast<float4 *>(sC + (2 + q) * CBOX + r * 128);
+        const int sw = r & 7;                // 16-byte chunk k of the row sits at k ^ (r % 8)
         uint32_t tcnt = 0;
+        bool c_pending = false;              // loads issued and not yet waited for
         for (int64_t it = blockIdx.x; it < items; it += gridDim.x, ++tcnt) {
             int w, I, K, ch;
             decode(it, w, I, K, ch);
+            // rows of the tile in the tensor map: H plane T*256 .. +127, L plane T*256+128 .. +255
+            const int yH = (int)(((int64_t)w * tpo + tile_index(I, K)) * 256);
+            if (et == 0) {
+                // the previous item's stores have read the buffer: load this item's half tile
+                tc::bulk_wait_read_all();
+                tc::mbar_arrive_expect_tx(&cFull, 4 * CBOX);
+#pragma unroll
+                for (int bx = 0; bx < 4; ++bx)
+                    tc::tma_load_2d(sC + bx * CBOX, &tmapC, 64 * ch + 32 * (bx & 1), yH + 128 * (bx >> 1), &cFull);
+                c_pending = true;
+            }
             if (P == 2) {
                 const short ec = (short)common_exp(oconst[OC_N * (int64_t)w + OC_NUG]);
                 if (et < TB) sEA[et] = ec;
@@ -723,18 +756,22 @@ __global__ void __launch_bounds__(pipe::NTHP, 1) k_trail_pipe(int mode, int Klo,
                     sEB[et - TB] = (short)reinterpret_cast<const int *>(ib + (size_t)S * 2 * SBLK)[64 * ch + et - TB];
             }
             const int set = (NSET == 2) ? (int)(tcnt & 1) : 0;
-            if (et == 0) {   // one thread waits and decides for all 128
-                const bool ok = tc::mbar_wait(&accFull[set], ((NSET == 2) ? tcnt >> 1 : tcnt) & 1);
+            if (et == 0) {   // one thread waits and decides for all
+                const bool ok = tc::mbar_wait(&accFull[set], ((NSET == 2) ? tcnt >> 1 : tcnt) & 1) &&
+                                tc::mbar_wait(&cFull, tcnt & 1);
+                if (ok) c_pending = false;
                 if (!ok) *verr = 1;
                 s_stop = (!ok || *verr) ? 1 : 0;
             }
-            tc::named_sync(1, NEPI);       // exponents visible; stop decision uniform
+            tc::named_sync(1, NEPI);       // exponents and C visible; stop decision uniform
             if (s_stop) break;
             tc::fence_after_sync();
-            const uint32_t a = tb + set * 256 + ((uint32_t)(32 * (warp & 3)) << 16);
+            const uint32_t a = tb + set * 256 + ((uint32_t)(32 * (warp & 3)) << 16) + 32 * q;
             const int ea = sEA[r] - 14;
+            const short *eb = sEB + 32 * q;
 #pragma unroll 1
-            for (int c0 = 32 * cpart; c0 < 32 * cpart + 32; c0 += 16) {
+            for (int c0 = 0; c0 < 32; c0 += 16) {
+                float dh[16], dl[16];
                 if (S == 5) {
                     uint32_t p0[16], p1[16], p2[16], p3[16];
                     tc::tmem_ld16(a + 0 * 64 + c0, p0);
@@ -743,14 +780,8 @@ __global__ void __launch_bounds__(pipe::NTHP, 1) k_trail_pipe(int mode, int Klo,
                     tc::tmem_ld16(a + 3 * 64 + c0, p3);
                     tc::tmem_wait_ld();
 #pragma unroll
-                    for (int c = 0; c < 16; ++c) {
-                        float hi, lo;
-                        group_value(p0[c], p1[c], p2[c], p3[c], ea + sEB[c0 + c], hi, lo);
-                        sDh[r * DP + c0 + c] = hi;
-                        sDl[r * DP + c0 + c] = lo;
-                    }
+                    for (int c = 0; c < 16; ++c) group_value(p0[c], p1[c], p2[c], p3[c], ea + eb[c0 + c], dh[c], dl[c]);
                 } else {
-                    float hi[16], lo[16];
 #pragma unroll 1
                     for (int g = 0; g < S; ++g) {
                         uint32_t pg[16];
@@ -758,49 +789,46 @@ __global__ void __launch_bounds__(pipe::NTHP, 1) k_trail_pipe(int mode, int Klo,
                         tc::tmem_wait_ld();
 #pragma unroll
                         for (int c = 0; c < 16; ++c) {
-                            const float v = __uint_as_float(pg[c]) * pow2f(ea + sEB[c0 + c]);
+                            const float v = __uint_as_float(pg[c]) * pow2f(ea + eb[c0 + c]);
                             if (g == 0) {
-                                hi[c] = v;
-                                lo[c] = 0.0f;
+                                dh[c] = v;
+                                dl[c] = 0.0f;
                             } else {
-                                df_add(hi[c], lo[c], v);
+                                df_add(dh[c], dl[c], v);
                             }
                         }
                     }
+                }
 #pragma unroll
-                    for (int c = 0; c < 16; ++c) {
-                        sDh[r * DP + c0 + c] = hi[c];
-                        sDl[r * DP + c0 + c] = lo[c];
-                    }
+                for (int k4 = 0; k4 < 4; ++k4) {
+                    const int kc = ((c0 >> 2) + k4) ^ sw;
+                    float4 h = rowH[kc], l = rowL[kc];
+                    df_add(h.x, l.x, -dh[4 * k4 + 0]);
+                    df_add(h.x, l.x, -dl[4 * k4 + 0]);
+                    df_add(h.y, l.y, -dh[4 * k4 + 1]);
+                    df_add(h.y, l.y, -dl[4 * k4 + 1]);
+                    df_add(h.z, l.z, -dh[4 * k4 + 2]);
+                    df_add(h.z, l.z, -dl[4 * k4 + 2]);
+                    df_add(h.w, l.w, -dh[4 * k4 + 3]);
+                    df_add(h.w, l.w, -dl[4 * k4 + 3]);
+                    rowH[kc] = h;
+                    rowL[kc] = l;
                 }
             }
+            tc::fence_proxy_async();        // these writes are read by the TMA store
             tc::fence_before_sync();
             tc::named_sync(1, NEPI);
-            if (et == 0) tc::mbar_arrive(&accEmpty[set]);   // the MMA warp may reuse this set
-            float *gH = reinterpret_cast<float *>(tiles + ((int64_t)w * tpo + tile_index(I, K)) * NT) + 64 * ch;
-            float *gL = gH + NT;
-#pragma unroll 1
-            for (int u0 = 0; u0 < (TB * 64) / NEPI; u0 += 16) {
-                float h8[16], l8[16];
+            if (et == 0) {
+                tc::mbar_arrive(&accEmpty[set]);   // the MMA warp may reuse this set
 #pragma unroll
-                for (int u = 0; u < 16; ++u) {
-                    const int e = et + NEPI * (u0 + u);
-                    const int gi = (e >> 6) * TB + (e & 63);
-                    h8[u] = gH[gi];
-                    l8[u] = gL[gi];
-                }
-#pragma unroll
-                for (int u = 0; u < 16; ++u) {
-                    const int e = et + NEPI * (u0 + u);
-                    const int gi = (e >> 6) * TB + (e & 63);
-                    const int si = (e >> 6) * DP + (e & 63);
-                    df_add(h8[u], l8[u], -sDh[si]);
-                    df_add(h8[u], l8[u], -sDl[si]);
-                    gH[gi] = h8[u];
-                    gL[gi] = l8[u];
-                }
+                for (int bx = 0; bx < 4; ++bx)
+                    tc::tma_store_2d(&tmapC, 64 * ch + 32 * (bx & 1), yH + 128 * (bx >> 1), sC + bx * CBOX);
+                tc::bulk_commit();
             }
-            tc::named_sync(1, NEPI);       // deltas consumed before the next item rewrites them
+        }
+        if (et == 0) {
+            tc::bulk_wait_all();
+            if (c_pending) tc::mbar_wait(&cFull, tcnt & 1);   // error exit: let the loads land first
         }
     }
     __syncthreads();
@@ -1053,6 +1081,34 @@ static int num_sms() {
         if (timer) timer->end(cls, s);   \
     } while (0)
 
+// Tensor map over the batch's tile array seen as float rows of 128: tile T
+// (global index w * tpo + t) holds its H plane in rows 256 T .. 256 T + 127 and
+// its L plane in the next 128 rows.  Box: 32 floats x 128 rows, 128-byte
+// swizzle (the trailing update's C half tile is four boxes).
+static cudaError_t make_tile_map(CUtensorMap *m, double *tiles, int count, int64_t tpo) {
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    });
+    if (!encode) return cudaErrorNotSupported;
+    const int64_t rows = (int64_t)count * tpo * 256;
+    if (rows > (int64_t)INT32_MAX) return cudaErrorInvalidValue;   // row coordinates are 32-bit
+    const cuuint64_t dims[2] = {(cuuint64_t)TB, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)TB * sizeof(float)};
+    const cuuint32_t box[2] = {32, (cuuint32_t)TB};
+    const cuuint32_t estr[2] = {1, 1};
+    const CUresult r = encode(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, tiles, dims, strides, box, estr,
+                              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
 template <int S>
 static cudaError_t launch_mixed_steps(const BatchArgs &b, const MixedArgs &x, cudaStream_t s) {
     KernelTimer *timer = b.timer;
@@ -1063,6 +1119,8 @@ static cudaError_t launch_mixed_steps(const BatchArgs &b, const MixedArgs &x, cu
                                   (int)POTRF_MIXED_SMEM)) != cudaSuccess)
         return e;
     cudaMemsetAsync(x.invsum, 0, sizeof(double) * cnt, s);
+    CUtensorMap tmapC;
+    if ((e = make_tile_map(&tmapC, b.tiles, cnt, b.tpo)) != cudaSuccess) return e;
     const int sms = num_sms();
     if (S == 7) {
         if ((e = cudaFuncSetAttribute(k_trsm_split7x, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_split)) !=
@@ -1081,7 +1139,7 @@ static cudaError_t launch_mixed_steps(const BatchArgs &b, const MixedArgs &x, cu
             const int64_t items = (int64_t)cnt * (m * (m + 1) / 2) * 2;
             const int grid = (int)std::min<int64_t>(items, sms);
             TIMED(KC_GEMM_SPLIT7, (k_trail_pipe<7><<<grid, pipe::NTHP, pipe::Cfg<7>::SMEM, s>>>(
-                                      0, J + 1, nb, 1, 0, 0, nb, cnt, b.tpo, b.tiles, x.pimg, b.oconst, x.err)));
+                                      0, J + 1, nb, 1, 0, 0, nb, cnt, b.tpo, tmapC, x.pimg, b.oconst, x.err)));
         }
     } else {
         if ((e = cudaFuncSetAttribute(k_trsm_split<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_split)) !=
@@ -1096,7 +1154,7 @@ static cudaError_t launch_mixed_steps(const BatchArgs &b, const MixedArgs &x, cu
             const int64_t items = (int64_t)cnt * ((mode == 0) ? m * (m + 1) / 2 : m) * 2;
             const int grid = (int)std::min<int64_t>(items, sms);
             TIMED(KC_GEMM_SPLIT, (k_trail_pipe<5><<<grid, pipe::NTHP, pipe::Cfg<5>::SMEM, s>>>(
-                                     mode, Klo, Ihi, P, sub0, sub1, nb, cnt, b.tpo, b.tiles, x.pimg, b.oconst, x.err)));
+                                     mode, Klo, Ihi, P, sub0, sub1, nb, cnt, b.tpo, tmapC, x.pimg, b.oconst, x.err)));
         };
         auto factor_panel = [&](int J) {
             TIMED(KC_POTRF_MIXED, (k_potrf_mixed<S><<<cnt, 256, POTRF_MIXED_SMEM, s>>>(
