@@ -392,6 +392,14 @@ __global__ void __launch_bounds__(NTH, 1) k_trsm_split(int J, int nb, int64_t tp
         sEW[tid] = (short)reinterpret_cast<const int *>(wi + (size_t)S * 2 * SBLK)[tid];
         sMx[tid] = 0;
     }
+    __syncthreads();   // barriers initialised
+    // the L_JJ^-1 slices of K half 0 load while A_IJ is scanned and sliced
+    // (one copy per lane: a thread's copies run one after another)
+    if (warp == 0) {
+        if (lane == 0) tc::mbar_arrive_expect_tx(&bar_load, S * SBLK);
+        __syncwarp();
+        if (lane < S) tc::bulk_g2s(sW + lane * SBLK, wi + (size_t)(lane * 2) * SBLK, SBLK, &bar_load);
+    }
     // row exponents of A_IJ: warp w handles rows 8w .. 8w + 7
 #pragma unroll
     for (int rr = 0; rr < 8; ++rr) {
@@ -407,9 +415,9 @@ __global__ void __launch_bounds__(NTH, 1) k_trsm_split(int J, int nb, int64_t tp
     tc::fence_after_sync();
     const uint32_t tb = tmem_base;
     uint32_t phase = 0;
-    for (int h = 0; h < 2; ++h) {
-        // slice the K half h of A_IJ into shared memory
-        float2 hv[8], lv[8];
+    // df values of this thread's rows (8 rows, 2 columns each) for K half h
+    float2 hv[8], lv[8];
+    auto load_half = [&](int h) {
 #pragma unroll
         for (int rr = 0; rr < 8; ++rr) {
             const int r = warp * 8 + rr;
@@ -417,6 +425,10 @@ __global__ void __launch_bounds__(NTH, 1) k_trsm_split(int J, int nb, int64_t tp
             hv[rr] = *reinterpret_cast<const float2 *>(H + r * TB + k);
             lv[rr] = *reinterpret_cast<const float2 *>(Lo + r * TB + k);
         }
+    };
+    load_half(0);
+    for (int h = 0; h < 2; ++h) {
+        // slice the K half h of A_IJ into shared memory
 #pragma unroll
         for (int rr = 0; rr < 8; ++rr) {
             const int r = warp * 8 + rr;
@@ -430,11 +442,6 @@ __global__ void __launch_bounds__(NTH, 1) k_trsm_split(int J, int nb, int64_t tp
         }
         tc::fence_proxy_async();
         __syncthreads();
-        if (warp == 0 && s_ok) {   // one copy per lane: a thread's copies run one after another
-            if (lane == 0) tc::mbar_arrive_expect_tx(&bar_load, S * SBLK);
-            __syncwarp();
-            if (lane < S) tc::bulk_g2s(sW + lane * SBLK, wi + (size_t)(lane * 2 + h) * SBLK, SBLK, &bar_load);
-        }
         if (tid == 0 && s_ok) {
             bool ok = tc::mbar_wait(&bar_load, phase);
             if (!ok) tc::mbar_wait(&bar_load, phase);
@@ -442,9 +449,15 @@ __global__ void __launch_bounds__(NTH, 1) k_trsm_split(int J, int nb, int64_t tp
                 tc::fence_after_sync();
                 issue_split_mmas<S>(tb, sA, sW, h == 0);
                 tc::mma_commit(&bar_mma);
-                ok = tc::mbar_wait(&bar_mma, phase);
-                if (!ok) tc::mbar_wait(&bar_mma, phase);
+            } else {
+                s_ok = 0;
+                atomicExch(err, 1);
             }
+        }
+        if (h == 0) load_half(1);   // next K half's values arrive while the MMAs run
+        if (tid == 0 && s_ok) {
+            bool ok = tc::mbar_wait(&bar_mma, phase);
+            if (!ok) tc::mbar_wait(&bar_mma, phase);
             if (!ok) {
                 s_ok = 0;
                 atomicExch(err, 1);
@@ -454,6 +467,11 @@ __global__ void __launch_bounds__(NTH, 1) k_trsm_split(int J, int nb, int64_t tp
         tc::fence_before_sync();
         __syncthreads();
         tc::fence_after_sync();
+        if (h == 0 && warp == 0 && s_ok) {   // shared A and W are free again: K half 1 of W
+            if (lane == 0) tc::mbar_arrive_expect_tx(&bar_load, S * SBLK);
+            __syncwarp();
+            if (lane < S) tc::bulk_g2s(sW + lane * SBLK, wi + (size_t)(lane * 2 + 1) * SBLK, SBLK, &bar_load);
+        }
     }
     const bool ok = s_ok != 0;
     const int r = 32 * (warp & 3) + lane;   // this thread's row, columns 32 (warp / 4) .. +31
