@@ -110,6 +110,14 @@ __device__ __forceinline__ int common_exp(double nug) {
     return row_exp((float)sqrt(1.0 + nug) * (1.0f + 1.0f / 1024.0f));
 }
 
+// Exponent shared by all data rows of a Schur complement (the trailing matrix
+// before a panel solve): |S_ij| <= sqrt(S_ii S_jj) <= 1 + nu^2.  Slicing with it
+// instead of each row's own maximum adds an absolute error of 2^-40 (1 + nu^2)
+// per entry, far below what the earlier trailing updates already left there.
+__device__ __forceinline__ int common_exp_schur(double nug) {
+    return row_exp((float)(1.0 + nug) * (1.0f + 1.0f / 1024.0f));
+}
+
 template <int S>
 __device__ __forceinline__ void store_pair(uint8_t *img, int r, int k, const float (&m0)[S], const float (&m1)[S]) {
     const int h = k >> 6;
@@ -400,15 +408,21 @@ __global__ void __launch_bounds__(NTH, 1) k_trsm_split(int J, int nb, int64_t tp
         __syncwarp();
         if (lane < S) tc::bulk_g2s(sW + lane * SBLK, wi + (size_t)(lane * 2) * SBLK, SBLK, &bar_load);
     }
-    // row exponents of A_IJ: warp w handles rows 8w .. 8w + 7
+    // row exponents of A_IJ: data rows share one; right-hand-side rows use
+    // their own maximum (warp w scans rows 8w .. 8w + 7)
+    const bool data_rows = I < nb;
+    if (data_rows) {
+        if (tid < TB) sEA[tid] = (short)common_exp_schur(oconst[OC_N * (int64_t)w + OC_NUG]);
+    } else {
 #pragma unroll
-    for (int rr = 0; rr < 8; ++rr) {
-        const int r = warp * 8 + rr;
-        float mx = 0.0f;
+        for (int rr = 0; rr < 8; ++rr) {
+            const int r = warp * 8 + rr;
+            float mx = 0.0f;
 #pragma unroll
-        for (int q = 0; q < 4; ++q) mx = fmaxf(mx, fabsf(H[r * TB + lane + 32 * q]));
-        for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-        if (lane == 0) sEA[r] = (short)row_exp(mx);
+            for (int q = 0; q < 4; ++q) mx = fmaxf(mx, fabsf(H[r * TB + lane + 32 * q]));
+            for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+            if (lane == 0) sEA[r] = (short)row_exp(mx);
+        }
     }
     tc::fence_before_sync();
     __syncthreads();
@@ -476,7 +490,6 @@ __global__ void __launch_bounds__(NTH, 1) k_trsm_split(int J, int nb, int64_t tp
     const bool ok = s_ok != 0;
     const int r = 32 * (warp & 3) + lane;   // this thread's row, columns 32 (warp / 4) .. +31
     const int cb = 32 * (warp >> 2);
-    const bool data_rows = I < nb;          // common exponent: no row maximum needed
     if (ok && !data_rows) {
         float mx = 0.0f;
 #pragma unroll 1
