@@ -193,29 +193,35 @@ __device__ __forceinline__ int tri_row(int t) {
     return r;
 }
 
-// Dynamic shared memory of k_potrf_mixed: the packed tile (66 KB) padded so
-// that at most two blocks share an SM (the default batch is four tiles per SM;
-// three per SM would leave a partial second wave).
-constexpr size_t POTRF_MIXED_SMEM = 80 * 1024;
+// Dynamic shared memory of k_potrf_mixed: the packed tile (66 KB) and three
+// 32 x 32 FP64 temporaries (24 KB); two blocks share an SM.
+constexpr int DB = 32;   // block size of the diagonal-tile factorisation
+constexpr size_t POTRF_MIXED_SMEM = (size_t)(PK + 3 * DB * DB) * sizeof(double);
 
-// The FP64 pipe is the bound here, so every step spreads its multiply-adds
-// evenly over all threads (flat index over the packed entries it touches) and
-// the serial per-column part (pivot, 1/sqrt, column scale) is one warp's work.
-// L is formed in place; W = L^-1 then overwrites it, row by row, right-looking:
-// row k of W is final once rows < k have been applied; applying it subtracts
-// L[i][k] W[k][c] from rows i > k.  Column k of L is staged in shared memory
-// a step ahead because its slots become W's; the thread that applies the last
-// update to row k+1 also scales it by 1/L[k+1][k+1].
+// The FP64 pipe is the bound here (FP64 issues at 1/68 of FP32 on this part),
+// so the kernel keeps every FP64 instruction lane-full and blocks the work:
+// - Cholesky in 32-column panels: each column's pivot and scale by one warp,
+//   the update of the remaining panel columns spread evenly over the block
+//   (flat index over the entries it touches); then the trailing lower triangle
+//   gets the panel's rank-32 update in 4 x 4 register tiles;
+// - W = L^-1 in place: the four 32 x 32 diagonal blocks are inverted at once
+//   (two warps each, right-looking by rows: row k of W is final once rows < k
+//   are applied; column k of L is staged a step ahead because its slots become
+//   W's), then the off-diagonal blocks column by column from the right:
+//   W_bc = -(sum_{d=c+1..b} W_bd L_dc) W_cc, the sums first (into temporaries,
+//   while L_dc is still intact), then the products with W_cc over L_bc.
 template <int S>
 __global__ void __launch_bounds__(256, 2) k_potrf_mixed(int J, int64_t tpo, double *__restrict__ tiles,
                                                         uint8_t *__restrict__ wimg, double *__restrict__ logdet,
                                                         double *__restrict__ invsum, int *__restrict__ pstatus) {
     extern __shared__ double sm[];
-    double *P = sm;   // packed lower triangle: the tile, then L, then W = L^-1
-    __shared__ double colb[2][TB];   // scaled column j of L / finished row k of W
-    __shared__ double lcol[2][TB];   // column k of L, staged before W overwrites it
-    __shared__ double piv[TB];       // pivots d_j
-    __shared__ double rd[TB];        // 1 / L[j][j]
+    double *P = sm;                   // packed lower triangle: the tile, then L, then W = L^-1
+    double *Tm = sm + PK;             // 3 x 32 x 32 temporaries of the block inverse
+    __shared__ double col[TB];        // scaled column j of L
+    __shared__ double piv[TB];        // pivots d_j
+    __shared__ double rd[TB];         // 1 / L[j][j]
+    __shared__ double dcol[4][2][DB];   // per diagonal block: finished row k of W
+    __shared__ double dlc[4][2][DB];    // per diagonal block: column k of L, staged
     __shared__ double red[2][4];
     const int w = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     double *T = tiles + ((int64_t)w * tpo + tile_index(J, J)) * NT;
@@ -226,61 +232,182 @@ __global__ void __launch_bounds__(256, 2) k_potrf_mixed(int J, int64_t tpo, doub
         if (c <= r) P[pk(r, c)] = (double)H[e] + (double)Lo[e];
     }
     __syncthreads();
-    // Cholesky (a non-positive pivot leaves NaN behind it; the pivot is kept
-    // so the status is set below)
-    for (int j = 0; j < TB; ++j) {
-        if (warp == 0) {
-            const double d = P[pk(j, j)];
-            const double rl = rsqrt(d);
-            if (lane == 0) {
-                piv[j] = d;
-                P[pk(j, j)] = d * rl;
+    // ---- Cholesky (a non-positive pivot leaves NaN behind it; the pivot is
+    // kept so the status is set below)
+    for (int kb = 0; kb < TB; kb += DB) {
+        const int kend = kb + DB - 1;
+        for (int j = kb; j <= kend; ++j) {
+            if (warp == 0) {
+                const double d = P[pk(j, j)];
+                const double rl = rsqrt(d);
+                if (lane == 0) {
+                    piv[j] = d;
+                    P[pk(j, j)] = d * rl;
+                }
+                for (int i = j + 1 + lane; i < TB; i += 32) {
+                    const double v = P[pk(i, j)] * rl;
+                    P[pk(i, j)] = v;
+                    col[i] = v;
+                }
             }
-            for (int i = j + 1 + lane; i < TB; i += 32) {
-                const double v = P[pk(i, j)] * rl;
-                P[pk(i, j)] = v;
-                colb[0][i] = v;
+            __syncthreads();
+            const int nk = kend - j;   // panel columns right of j
+            if (nk > 0) {
+                // rows j+1 .. kend (k <= i: a triangle), then rows below the panel (all nk columns)
+                const int tri = nk * (nk + 1) / 2;
+                const int total = tri + (TB - 1 - kend) * nk;
+                for (int t = tid; t < total; t += 256) {
+                    int i, k;
+                    if (t < tri) {
+                        const int ii = tri_row(t);
+                        i = j + 1 + ii;
+                        k = j + 1 + (t - ii * (ii + 1) / 2);
+                    } else {
+                        const int t2 = t - tri, q = t2 / nk;
+                        i = kend + 1 + q;
+                        k = j + 1 + (t2 - q * nk);
+                    }
+                    P[pk(i, k)] = fma(-col[i], col[k], P[pk(i, k)]);
+                }
+                __syncthreads();
             }
         }
-        __syncthreads();
-        const int m = TB - 1 - j, cnt = m * (m + 1) / 2;
-        for (int t = tid; t < cnt; t += 256) {
-            const int ii = tri_row(t), kk = t - ii * (ii + 1) / 2;
-            const int i = j + 1 + ii, k = j + 1 + kk;
-            P[pk(i, k)] = fma(-colb[0][i], colb[0][k], P[pk(i, k)]);
+        const int m = TB - 1 - kend;   // rank-32 update of the trailing lower triangle
+        if (m > 0) {
+            const int nbl = m / 4, nblocks = nbl * (nbl + 1) / 2;
+            for (int bq = tid; bq < nblocks; bq += 256) {
+                const int bi = tri_row(bq), bk = bq - bi * (bi + 1) / 2;
+                const int i0 = kend + 1 + 4 * bi, k0 = kend + 1 + 4 * bk;
+                int ra[4], rb[4];
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    ra[r] = pk(i0 + r, 0);
+                    rb[r] = pk(k0 + r, 0);
+                }
+                double acc[4][4];
+#pragma unroll
+                for (int r = 0; r < 4; ++r)
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) acc[r][c] = 0.0;
+#pragma unroll 4
+                for (int q = kb; q <= kend; ++q) {
+                    double x[4], y[4];
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) {
+                        x[r] = P[ra[r] + q];
+                        y[r] = P[rb[r] + q];
+                    }
+#pragma unroll
+                    for (int r = 0; r < 4; ++r)
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) acc[r][c] = fma(x[r], y[c], acc[r][c]);
+                }
+#pragma unroll
+                for (int r = 0; r < 4; ++r)
+#pragma unroll
+                    for (int c = 0; c < 4; ++c)
+                        if (k0 + c <= i0 + r) P[ra[r] + k0 + c] -= acc[r][c];
+            }
+            __syncthreads();
         }
-        __syncthreads();
     }
-    // W = L^-1 in place
-    if (tid < TB) {
-        rd[tid] = 1.0 / P[pk(tid, tid)];
-        lcol[0][tid] = P[pk(tid, 0)];
+    // ---- W = L^-1 in place
+    if (tid < TB) rd[tid] = 1.0 / P[pk(tid, tid)];
+    __syncthreads();
+    {   // diagonal blocks: block b by warps 2b, 2b+1 (named barrier 1 + b)
+        const int b = warp >> 1, lt = tid & 63, base = DB * b;
+        if (lt < DB) dlc[b][0][lt] = P[pk(base + lt, base)];
+        if (lt == 0) {
+            P[pk(base, base)] = rd[base];
+            dcol[b][0][0] = rd[base];
+        }
+        tc::named_sync(1 + b, 64);
+        for (int k = 0; k < DB - 1; ++k) {
+            const double *ck = dcol[b][k & 1], *lk = dlc[b][k & 1];
+            double *cn = dcol[b][(k + 1) & 1], *ln = dlc[b][(k + 1) & 1];
+            const int ncol = k + 1, cnt = (DB - 1 - k) * ncol;
+            if (lt > k + 1 && lt < DB) ln[lt] = P[pk(base + lt, base + k + 1)];
+            const double rn = rd[base + k + 1];
+            for (int t = lt; t < cnt; t += 64) {
+                const int ii = t / ncol, c = t - ii * ncol, i = k + 1 + ii;
+                const int e = pk(base + i, base + c);
+                const double acc = (c == k) ? 0.0 : P[e];   // slot (i, k) still holds L[i][k]
+                double v = fma(-lk[i], ck[c], acc);
+                if (ii == 0) {
+                    v *= rn;
+                    cn[c] = v;
+                }
+                P[e] = v;
+            }
+            if (lt == 0) {
+                P[pk(base + k + 1, base + k + 1)] = rn;
+                cn[k + 1] = rn;
+            }
+            tc::named_sync(1 + b, 64);
+        }
     }
     __syncthreads();
-    if (tid == 0) {
-        P[0] = rd[0];
-        colb[0][0] = rd[0];
-    }
-    __syncthreads();
-    for (int k = 0; k < TB - 1; ++k) {
-        const double *ck = colb[k & 1], *lk = lcol[k & 1];
-        double *cn = colb[(k + 1) & 1], *ln = lcol[(k + 1) & 1];
-        const int ncol = k + 1, cnt = (TB - 1 - k) * ncol;
-        if (tid > k + 1 && tid < TB) ln[tid] = P[pk(tid, k + 1)];
-        const double rn = rd[k + 1];
-        for (int t = tid; t < cnt; t += 256) {
-            const int ii = t / ncol, c = t - ii * ncol, i = k + 1 + ii;
-            const double acc = (c == k) ? 0.0 : P[pk(i, c)];   // slot (i, k) still holds L[i][k]
-            double v = fma(-lk[i], ck[c], acc);
-            if (ii == 0) {
-                v *= rn;
-                cn[c] = v;
+    for (int c = 2; c >= 0; --c) {   // off-diagonal blocks of block column c, in 4 x 4 register tiles
+        const int nres = 3 - c;
+        for (int u = tid; u < nres * 64; u += 256) {   // sums: T_bc = sum_d W_bd L_dc
+            const int b = c + 1 + u / 64, bl = u & 63;
+            const int i0 = 4 * (bl >> 3), k0 = 4 * (bl & 7);
+            double acc[4][4];
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int cc = 0; cc < 4; ++cc) acc[r][cc] = 0.0;
+            int ra[4];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) ra[r] = pk(DB * b + i0 + r, 0);
+            for (int d = c + 1; d <= b; ++d) {
+                const bool diag = (d == b);   // W_bb is lower triangular
+                const int qend = diag ? i0 + 3 : DB - 1;
+                for (int q = 0; q <= qend; ++q) {
+                    double x[4], y[4];
+                    const int rq = pk(DB * d + q, 0) + DB * c + k0;
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) x[r] = (diag && q > i0 + r) ? 0.0 : P[ra[r] + DB * d + q];
+#pragma unroll
+                    for (int cc = 0; cc < 4; ++cc) y[cc] = P[rq + cc];
+#pragma unroll
+                    for (int r = 0; r < 4; ++r)
+#pragma unroll
+                        for (int cc = 0; cc < 4; ++cc) acc[r][cc] = fma(x[r], y[cc], acc[r][cc]);
+                }
             }
-            P[pk(i, c)] = v;
+            double *Tb = Tm + (b - c - 1) * DB * DB;
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int cc = 0; cc < 4; ++cc) Tb[(i0 + r) * DB + k0 + cc] = acc[r][cc];
         }
-        if (tid == 0) {
-            P[pk(k + 1, k + 1)] = rn;
-            cn[k + 1] = rn;
+        __syncthreads();
+        for (int u = tid; u < nres * 64; u += 256) {   // W_bc = -T_bc W_cc (W_cc lower triangular)
+            const int b = c + 1 + u / 64, bl = u & 63;
+            const int i0 = 4 * (bl >> 3), k0 = 4 * (bl & 7);
+            const double *Tb = Tm + (b - c - 1) * DB * DB;
+            double acc[4][4];
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int cc = 0; cc < 4; ++cc) acc[r][cc] = 0.0;
+            for (int q = k0; q < DB; ++q) {
+                double x[4], y[4];
+                const int rq = pk(DB * c + q, 0) + DB * c + k0;
+#pragma unroll
+                for (int r = 0; r < 4; ++r) x[r] = Tb[(i0 + r) * DB + q];
+#pragma unroll
+                for (int cc = 0; cc < 4; ++cc) y[cc] = (q >= k0 + cc) ? P[rq + cc] : 0.0;
+#pragma unroll
+                for (int r = 0; r < 4; ++r)
+#pragma unroll
+                    for (int cc = 0; cc < 4; ++cc) acc[r][cc] = fma(x[r], y[cc], acc[r][cc]);
+            }
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int cc = 0; cc < 4; ++cc) P[pk(DB * b + i0 + r, DB * c + k0 + cc)] = -acc[r][cc];
         }
         __syncthreads();
     }
