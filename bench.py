@@ -37,9 +37,11 @@ import numpy as np
 # capture (dram__bytes_read.sum + dram__bytes_write.sum, a one-pass metric set)
 # of `python bench.py --precision mixed --steps 1 --warmup 1 --no-cpu-baseline
 # --no-e2e`: mean bytes per launch over the 126 launches of one 592-point
-# evaluation at n = 4000.  Valid only for that workload and for the kernel
-# sources it was taken on (their SHA-256 below); otherwise traffic is null.
-TRAIL_TRAFFIC = {"n": 4000, "batch": 592, "bytes_per_launch": 5.105e9, "read": 3.067e9, "write": 2.038e9,
+# evaluation at n = 4000 (two parts of 296 points; every launch covers one
+# part).  Valid for that workload with parts of 296 points (batches that are
+# multiples of 296 from 592 up) and for the kernel sources it was taken on
+# (their SHA-256 below); otherwise traffic is null.
+TRAIL_TRAFFIC = {"n": 4000, "part": 296, "bytes_per_launch": 5.105e9, "read": 3.067e9, "write": 2.038e9,
                  "launches_per_eval": 126, "sources_sha256": "56f324550cc150d32e7288662f411add4348ac731884f1d86a7c1d4c06d0e8fd"}
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -58,7 +60,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="auto", choices=["auto", "fp64", "mixed"])
-    ap.add_argument("--batch", type=int, default=0, help="omega points per step (default: 592 = 4 x 148 mixed, 128 fp64)")
+    ap.add_argument("--batch", type=int, default=0, help="omega points per step (default: 1184 = 8 x 148 mixed, 128 fp64)")
     ap.add_argument("--n", type=int, default=4000)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -352,7 +354,7 @@ def trail_traffic(n, B):
     """Measured DRAM bytes per k_trail_pipe<5> launch, or None when the workload
     or the kernel sources differ from the ones the counters were taken on."""
     import hashlib
-    if n != TRAIL_TRAFFIC["n"] or B != TRAIL_TRAFFIC["batch"]:
+    if n != TRAIL_TRAFFIC["n"] or B < 2 * TRAIL_TRAFFIC["part"] or B % TRAIL_TRAFFIC["part"]:
         return None
     h = hashlib.sha256()
     root = os.path.dirname(os.path.abspath(__file__))
@@ -462,7 +464,7 @@ def main():
         torch.cuda.empty_cache()
         return res
 
-    Bm = args.batch or (592 if head == "mixed" else 128)   # mixed: 4 x 148 SMs per step
+    Bm = args.batch or (1184 if head == "mixed" else 128)   # mixed: 8 x 148 SMs per step, parts of 296
     main_res = measure(head, Bm, args.steps, args.warmup, True)
     fp64_res = None
     if head == "mixed":

@@ -287,41 +287,53 @@ static AuxStreams aux_streams() {
 }
 
 // 5-slice pass over the batch.  With `overlap` and enough points, the batch is
-// cut in two halves and the build of the second half (FP64 pipe, no shared
-// memory) runs beside the factorisation of the first half (tensor cores); the
-// second half is factored after both.  The work is forked from `s` onto the
-// two internal streams and joined back into `s`.
+// cut into parts of about 296 points (two diagonal-tile blocks per SM); the
+// front of every part after the first (prep, table, build: FP64 pipe, no
+// shared memory) runs on a low-priority stream beside the factorisations of
+// the earlier parts (tensor cores) on a high-priority stream, so only the first
+// part's build is exposed.  The work is forked from `s` onto the two internal
+// streams and joined back into `s`.
 static cudaError_t mixed_first_pass(const BatchArgs &b, const MixedArgs &x, bool overlap, cudaStream_t s) {
-    constexpr int kOverlapMin = 256;
+    constexpr int kOverlapMin = 256, kPart = 296;
     const AuxStreams st = overlap && b.count >= kOverlapMin ? aux_streams() : AuxStreams{};
     if (!st.hi) return launch_mixed_batch(b, x, 5, s);
-    const int c0 = b.count / 2;
-    BatchArgs b0, b1;
-    MixedArgs x0, x1;
-    sub_batch(b, x, 0, c0, b0, x0);
-    sub_batch(b, x, c0, b.count - c0, b1, x1);
-    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    const int nparts = std::max(2, (b.count + kPart - 1) / kPart);
+    std::vector<cudaEvent_t> ev(nparts + 2, nullptr);   // [0] fork, [1 + p] front of part p done, [nparts + 1] join
     cudaError_t e = cudaSuccess;
-    for (int i = 0; i < 4 && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaEventRecord(ev[0], s);               // fork
+    for (size_t i = 0; i < ev.size() && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming);
+    auto part = [&](int p, BatchArgs &bp, MixedArgs &xp) {
+        const int lo = (int)((int64_t)b.count * p / nparts), hi = (int)((int64_t)b.count * (p + 1) / nparts);
+        sub_batch(b, x, lo, hi - lo, bp, xp);
+    };
+    bool forked = false;
+    if (e == cudaSuccess) e = cudaEventRecord(ev[0], s);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(st.hi, ev[0], 0);
-    if (e == cudaSuccess) e = launch_front(b0, st.hi, true);
-    if (e == cudaSuccess) e = cudaEventRecord(ev[1], st.hi);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(st.lo, ev[1], 0);
-    if (e == cudaSuccess) e = launch_front(b1, st.lo, true);
-    if (e == cudaSuccess) e = cudaEventRecord(ev[2], st.lo);
-    if (e == cudaSuccess) e = launch_mixed_back(b0, x0, 5, st.hi);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(st.hi, ev[2], 0);
-    if (e == cudaSuccess) e = launch_mixed_back(b1, x1, 5, st.hi);
-    if (ev[3]) {   // join, also after a failed launch: nothing may run on past `s`
-        cudaEventRecord(ev[1], st.lo);
-        cudaStreamWaitEvent(st.hi, ev[1], 0);
-        const cudaError_t j = cudaEventRecord(ev[3], st.hi);
-        const cudaError_t k = j == cudaSuccess ? cudaStreamWaitEvent(s, ev[3], 0) : j;
+    forked = e == cudaSuccess;
+    for (int p = 0; p < nparts && e == cudaSuccess; ++p) {   // fronts: part 0 on hi, the rest on lo
+        BatchArgs bp;
+        MixedArgs xp;
+        part(p, bp, xp);
+        cudaStream_t fs = p == 0 ? st.hi : st.lo;
+        if (p == 1) e = cudaStreamWaitEvent(st.lo, ev[1], 0);
+        if (e == cudaSuccess) e = launch_front(bp, fs, true);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[1 + p], fs);
+    }
+    for (int p = 0; p < nparts && e == cudaSuccess; ++p) {   // factorisations, in order, on hi
+        BatchArgs bp;
+        MixedArgs xp;
+        part(p, bp, xp);
+        if (p > 0) e = cudaStreamWaitEvent(st.hi, ev[1 + p], 0);
+        if (e == cudaSuccess) e = launch_mixed_back(bp, xp, 5, st.hi);
+    }
+    if (forked) {   // join, also after a failed launch: nothing may run on past `s`
+        cudaEventRecord(ev[nparts], st.lo);
+        cudaStreamWaitEvent(st.hi, ev[nparts], 0);
+        const cudaError_t j = cudaEventRecord(ev[nparts + 1], st.hi);
+        const cudaError_t k = j == cudaSuccess ? cudaStreamWaitEvent(s, ev[nparts + 1], 0) : j;
         if (e == cudaSuccess) e = k;
     }
-    for (int i = 0; i < 4; ++i)
-        if (ev[i]) cudaEventDestroy(ev[i]);   // released once the recorded work completes
+    for (auto &v : ev)
+        if (v) cudaEventDestroy(v);   // released once the recorded work completes
     return e;
 }
 

@@ -91,18 +91,20 @@ def test_mixed_deterministic_and_batch_independent():
         np.testing.assert_array_equal(a[k], c[k])
 
 
-def test_mixed_overlapped_halves_identical():
-    """A batch of >= 256 points runs in two halves, the second half's build
-    beside the first half's factorisation on a second stream; the results are
-    those of small batches that run without overlap, bit for bit."""
+@pytest.mark.parametrize("K", [300, 600])
+def test_mixed_overlapped_parts_identical(K):
+    """A batch of >= 256 points runs in parts of about 296 (two parts for 300
+    points, three for 600): each later part's build runs beside the earlier
+    parts' factorisations on a second stream; the results are those of small
+    batches that run without overlap, bit for bit."""
     ds = synth.aniso_dataset(77, 700, math.sqrt(70), 3)
-    P = synth.omega_from_unit(np.random.default_rng(77).uniform(size=(300, 5)))
+    P = synth.omega_from_unit(np.random.default_rng(77).uniform(size=(K, 5)))
     lams = synth.LAMBDA_GRID_9
-    a = gpu_eval(ds, P, lams, precision=nv.MIXED, batch=300)
+    a = gpu_eval(ds, P, lams, precision=nv.MIXED, batch=K)
     b = gpu_eval(ds, P, lams, precision=nv.MIXED, batch=100)
     for k in ("logL", "sigma2", "beta", "logdet", "status", "err_bound"):
         np.testing.assert_array_equal(a[k], b[k], err_msg=k)
-    assert (a["status"] & 15 == 0).sum() > 250
+    assert (a["status"] & 15 == 0).sum() > 0.8 * K
 
 
 @pytest.mark.slow
