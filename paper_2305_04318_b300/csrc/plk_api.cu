@@ -741,7 +741,7 @@ std::string run_item(Job *j, Item &it, cudaStream_t s) {
     cudaStreamWaitEvent(s, j->ready, 0);   // the job's B^T may come from another stream
     std::string err;
     if (L.mixed) {
-        plk_status st = run_mixed_batch(b, L, it.ws, j->d_params, j->opts.flags, nullptr, false, s);
+        plk_status st = run_mixed_batch(b, L, it.ws, j->d_params, j->opts.flags, nullptr, true, s);
         if (st != PLK_OK) err = plk_last_error();
     } else {
         cudaError_t e = launch_fp64_batch(b, s);
