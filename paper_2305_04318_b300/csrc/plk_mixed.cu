@@ -1355,7 +1355,7 @@ cudaError_t launch_mixed_back(const BatchArgs &b, const MixedArgs &x, int S, cud
     if ((e = launch_finalize(b, s)) != cudaSuccess) return e;
     // eps: relative perturbation of the updated entries.  Calibrated on the
     // n = 4000 workload against the FP64 path: with these values the bound
-    // exceeded the measured |Delta l_p| on every point (5 slices: by >= 16x;
+    // exceeded the measured |Delta l_p| on every point (5 slices: by >= 3x;
     // 7 slices with all groups exact: by >= 4.7x, on points whose own FP64
     // result differs from the CPU oracle by up to 1e-4).
     const double eps = (S == 7) ? ldexp(1.0, -46) : ldexp(1.0, -30);
