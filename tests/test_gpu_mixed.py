@@ -78,6 +78,7 @@ def test_mixed_error_bound_covers_five_slice_error():
                           ratio_max=float(np.max(err[ok] / np.maximum(eb[ok], 1e-300))))))
     small = ok & (eb <= 1e-4)
     assert np.all(err[small] <= ATOL_LOGL)
+    assert np.all(err[ok] <= eb[ok])   # the bound covers the 5-slice error on every point
 
 
 def test_mixed_deterministic_and_batch_independent():
@@ -119,3 +120,10 @@ def test_mixed4000_full_size_sampled():
     mixed_compare({k: v[idx] for k, v in g.items()}, o, "mixed4000 sampled vs oracle")
     f = gpu_eval(ds, P, w.lambdas, precision=nv.FP64)
     mixed_compare(g, f, "mixed4000 all vs FP64 GPU")
+    # the 5-slice pass alone: its error bound covers the measured error on every point
+    g5 = gpu_eval(ds, P, w.lambdas, precision=nv.MIXED, batch=512, flags=nv.FLAG_NO_RETRY)
+    ok = (g5["status"] == 0) & (f["status"] == 0)
+    err = np.max(np.abs(g5["logL"] - f["logL"]), axis=1)
+    print(json.dumps(dict(what="mixed4000 5-slice bound", points=int(ok.sum()),
+                          max_err_over_bound=float(np.max(err[ok] / g5["err_bound"][ok])))))
+    assert np.all(err[ok] <= g5["err_bound"][ok])
