@@ -92,12 +92,12 @@ def test_mixed_deterministic_and_batch_independent():
         np.testing.assert_array_equal(a[k], c[k])
 
 
-@pytest.mark.parametrize("K", [300, 600])
+@pytest.mark.parametrize("K", [300, 600, 900])
 def test_mixed_overlapped_parts_identical(K):
     """A batch of >= 256 points runs in parts of about 296 (two parts for 300
-    points, three for 600): each later part's build runs beside the earlier
-    parts' factorisations on a second stream; the results are those of small
-    batches that run without overlap, bit for bit."""
+    points, three for 600, four for 900): each later part's build runs beside
+    the earlier parts' factorisations on a second stream; the results are those
+    of small batches that run without overlap, bit for bit."""
     ds = synth.aniso_dataset(77, 700, math.sqrt(70), 3)
     P = synth.omega_from_unit(np.random.default_rng(77).uniform(size=(K, 5)))
     lams = synth.LAMBDA_GRID_9
