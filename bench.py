@@ -72,6 +72,7 @@ def parse():
                          "stream of profile jobs over a pool of resident datasets")
     ap.add_argument("--datasets", type=int, default=0, help="uneven/serving: number of datasets (default 256 / 32)")
     ap.add_argument("--points", type=int, default=512, help="uneven: points per dataset")
+    ap.add_argument("--item-batch", type=int, default=64, help="uneven: points per scheduled batch")
     ap.add_argument("--jobs", type=int, default=40, help="serving: jobs per load level")
     ap.add_argument("--streams", type=int, default=4, help="uneven/serving: scheduler streams")
     return ap.parse_args()
@@ -231,7 +232,7 @@ def run_uneven(args):
     D = args.datasets or 256
     w = synth.uneven(D=D, per=args.points)
     prec = nv.MIXED if args.precision in ("auto", "mixed") else nv.FP64
-    sizes = [nv.workspace_bytes(d.n, d.p, len(w.lambdas), 64, prec) for d in w.datasets]
+    sizes = [nv.workspace_bytes(d.n, d.p, len(w.lambdas), args.item_batch, prec) for d in w.datasets]
     arena_bytes = int(args.streams * max(sizes) * 1.2 + (2 << 30))
     arena = torch.empty((arena_bytes,), dtype=torch.uint8, device="cuda")
     with nv.Context(arena_bytes, arena=arena, n_streams=args.streams) as ctx:
@@ -241,7 +242,7 @@ def run_uneven(args):
         ctx.poll(j, w.datasets[0].p)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        jobs = [ctx.submit(ids[i], w.params[i], w.lambdas, precision=prec, batch=64) for i in range(D)]
+        jobs = [ctx.submit(ids[i], w.params[i], w.lambdas, precision=prec, batch=args.item_batch) for i in range(D)]
         res = [ctx.poll(jb, w.datasets[i].p) for i, jb in enumerate(jobs)]
         dt = time.perf_counter() - t0
         _, high = ctx.memory_stats()
@@ -254,7 +255,7 @@ def run_uneven(args):
             "config": {"workload": f"uneven: {D} datasets, n log-uniform in [200,3000] (median {int(np.median(ns))}), "
                                    f"p in {{2,3,5}}, {args.points} points each, 9 lambdas",
                        "precision": "mixed" if prec == nv.MIXED else "fp64", "streams": args.streams,
-                       "batch_per_item": 64, "arena_gb": arena_bytes / 1e9},
+                       "batch_per_item": args.item_batch, "arena_gb": arena_bytes / 1e9},
             "points": int(npts), "points_not_ok": int(((st & 15) != 0).sum()),
             "points_7slice": int(((st & 16) != 0).sum()), "points_fp64": int(((st & 32) != 0).sum()),
             "hbm_high_water_gb": high / 1e9, "e2e": {"value": npts / dt, "unit": UNIT,

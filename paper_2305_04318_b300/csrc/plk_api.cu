@@ -97,7 +97,7 @@ bool make_layout(int64_t n, int32_t p, int32_t M, int32_t batch, Layout &L, int 
         return o;
     };
     L.off_Bt = take(sizeof(double) * (size_t)L.q * L.n_pad);
-    L.off_sumlog = take(sizeof(double));
+    L.off_sumlog = take(2 * sizeof(double));   // sum log y, smallest squared site distance
     L.off_oc = take(sizeof(double) * OC_N * (size_t)batch);
     L.off_coordT = take(sizeof(double) * 2 * (size_t)L.n_pad * batch);
     L.off_tab = take(sizeof(double) * (size_t)TAB_SIZE * batch);
@@ -404,7 +404,7 @@ static plk_status run_mixed_batch(BatchArgs b, const Layout &L, void *ws, const 
 static plk_status run_eval(const plk_eval_args *a, int reml, int flags, const Layout &L, void *ws,
                            cudaStream_t s) {
     KernelTimer *timer = (flags & PLK_FLAG_KERNEL_TIMING) ? &g_timer : nullptr;
-    cudaError_t e = launch_boxcox(a->n, L.n_pad, a->p, a->M, a->y, a->X, a->lambdas,
+    cudaError_t e = launch_boxcox(a->n, L.n_pad, a->p, a->M, a->y, a->X, a->coords, a->lambdas,
                                   at<double>(ws, L.off_Bt), at<double>(ws, L.off_sumlog), s, timer);
     if (e != cudaSuccess) return cuda_fail(e, "boxcox launch");
     for (int64_t k0 = 0; k0 < a->K; k0 += L.batch) {
@@ -688,11 +688,11 @@ bool start_job(plk_ctx *c, Job *j, cudaStream_t s) {
     j->d_st = (int32_t *)take(sizeof(int32_t) * j->K);
     const int64_t n_pad = (j->n + TB - 1) / TB * TB;
     j->d_bt = (double *)take(sizeof(double) * (size_t)(j->M + j->p) * n_pad);
-    j->d_slog = (double *)take(sizeof(double));
+    j->d_slog = (double *)take(2 * sizeof(double));
     Dataset *d = c->datasets[j->ds].get();
     cudaMemcpyAsync(j->d_params, j->params.data(), sizeof(double) * 5 * j->K, cudaMemcpyHostToDevice, s);
     cudaMemcpyAsync(j->d_lam, j->lambdas.data(), sizeof(double) * j->M, cudaMemcpyHostToDevice, s);
-    cudaError_t e = launch_boxcox(j->n, n_pad, j->p, j->M, d->y, d->X, j->d_lam, j->d_bt, j->d_slog, s);
+    cudaError_t e = launch_boxcox(j->n, n_pad, j->p, j->M, d->y, d->X, d->coords, j->d_lam, j->d_bt, j->d_slog, s);
     if (e != cudaSuccess) {
         j->failed = true;
         j->error = cudaGetErrorString(e);

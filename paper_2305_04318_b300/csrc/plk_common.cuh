@@ -24,10 +24,12 @@ constexpr int TB = 128;                 // tile edge
 constexpr int NT = TB * TB;             // doubles per tile
 constexpr int PK = TB * (TB + 1) / 2;   // packed lower triangle of one tile
 
-// Per-omega constants (8 doubles): kappa, nu^2, log c_kappa, sqrt(8 kappa),
-// cos phi_A, sin phi_A, sqrt(8 kappa)/phi_X, sqrt(8 kappa)/phi_Y.
+// Per-omega constants (10 doubles): kappa, nu^2, log c_kappa, sqrt(8 kappa),
+// cos phi_A, sin phi_A, sqrt(8 kappa)/phi_X, sqrt(8 kappa)/phi_Y, and the
+// octaves [e_lo, e_hi) of w = u^2 that the point's site pairs can reach (the
+// rho table is built and read there only).
 constexpr int OC_KAPPA = 0, OC_NUG = 1, OC_LOGC = 2, OC_S8K = 3, OC_COS = 4, OC_SIN = 5,
-              OC_IA = 6, OC_IB = 7, OC_N = 8;
+              OC_IA = 6, OC_IB = 7, OC_ELO = 8, OC_EHI = 9, OC_N = 10;
 
 // Piecewise-polynomial table of rho as a function of w = u^2 = 8 kappa d^2.
 // Octaves [2^e, 2^(e+1)) for e in [TAB_ELO, TAB_EHI), each cut into TAB_S equal

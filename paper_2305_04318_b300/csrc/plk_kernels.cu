@@ -72,10 +72,11 @@ __global__ void k_sumlog(int64_t n, const double *__restrict__ y, double *__rest
 // a_i = sqrt(8k)/phi_X (cos x_i - sin y_i), b_i = sqrt(8k)/phi_Y (sin x_i + cos y_i), so that
 // w_ij = (a_i - a_j)^2 + (b_i - b_j)^2 = u_ij^2 with u = sqrt(8 kappa) d (eq. matern,
 // rotation matrix as printed, phi_Y = phi_X / phi_R).
-__global__ void k_omega_prep(const double *__restrict__ params, int64_t n, int64_t n_pad,
-                             const double *__restrict__ coords, double *__restrict__ oconst,
-                             double *__restrict__ coordT, double *__restrict__ logdet,
-                             int *__restrict__ pstatus) {
+__global__ void __launch_bounds__(256) k_omega_prep(const double *__restrict__ params, int64_t n, int64_t n_pad,
+                                                    const double *__restrict__ coords,
+                                                    const double *__restrict__ sumlogy, double *__restrict__ oconst,
+                                                    double *__restrict__ coordT, double *__restrict__ logdet,
+                                                    int *__restrict__ pstatus) {
     const int w = blockIdx.x;
     const double *om = params + 5 * (int64_t)w;
     const double phix = om[0], kap = om[1], nug = om[2], ratio = om[3], ang = om[4];
@@ -100,16 +101,97 @@ __global__ void k_omega_prep(const double *__restrict__ params, int64_t n, int64
     }
     double *a = coordT + (int64_t)w * 2 * n_pad;
     double *b = a + n_pad;
+    // bounding box of the transformed sites: w = |a_i - a_j|^2 + |b_i - b_j|^2 is
+    // at most its squared diagonal, and at least min(ia, ib)^2 times the
+    // smallest squared site distance (the rotation keeps lengths)
+    double alo = INFINITY, ahi = -INFINITY, blo = INFINITY, bhi = -INFINITY;
     for (int64_t i = threadIdx.x; i < n_pad; i += blockDim.x) {
         double ai = 0.0, bi = 0.0;
         if (i < n && ok) {
             const double x = coords[2 * i], yv = coords[2 * i + 1];
             ai = (c * x - s * yv) * ia;
             bi = (s * x + c * yv) * ib;
+            alo = fmin(alo, ai);
+            ahi = fmax(ahi, ai);
+            blo = fmin(blo, bi);
+            bhi = fmax(bhi, bi);
         }
         a[i] = ai;
         b[i] = bi;
     }
+    __shared__ double red[4][8];
+    for (int o = 16; o > 0; o >>= 1) {
+        alo = fmin(alo, __shfl_xor_sync(0xffffffffu, alo, o));
+        ahi = fmax(ahi, __shfl_xor_sync(0xffffffffu, ahi, o));
+        blo = fmin(blo, __shfl_xor_sync(0xffffffffu, blo, o));
+        bhi = fmax(bhi, __shfl_xor_sync(0xffffffffu, bhi, o));
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) {
+        red[0][warp] = alo;
+        red[1][warp] = ahi;
+        red[2][warp] = blo;
+        red[3][warp] = bhi;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int q = 1; q < (int)(blockDim.x >> 5); ++q) {
+            alo = fmin(alo, red[0][q]);
+            ahi = fmax(ahi, red[1][q]);
+            blo = fmin(blo, red[2][q]);
+            bhi = fmax(bhi, red[3][q]);
+        }
+        int elo = TAB_ELO, ehi = TAB_EHI;
+        if (ok && n > 1) {
+            const double da = ahi - alo, db = bhi - blo;
+            const double whi = da * da + db * db;
+            const double sc = fmin(ia, ib);
+            const double wlo = sc * sc * sumlogy[1];
+            int e;
+            if (whi > 0.0 && isfinite(whi)) {
+                frexp(whi, &e);          // whi < 2^e
+                ehi = min(TAB_EHI, max(TAB_ELO, e + 1));
+            }
+            if (wlo > 0.0 && isfinite(wlo)) {
+                frexp(wlo, &e);          // wlo >= 2^(e - 1)
+                elo = min(ehi, max(TAB_ELO, e - 2));
+            }
+        }
+        double *oc = oconst + OC_N * (int64_t)w;
+        oc[OC_ELO] = elo;
+        oc[OC_EHI] = ehi;
+    }
+}
+
+// Smallest squared distance between two sites (min over i < j), into *out
+// (which holds a large positive value beforehand): one block per pair of
+// 128-site tiles, non-negative doubles compared through their bit patterns.
+__global__ void __launch_bounds__(256) k_min_dist2(int64_t n, const double *__restrict__ coords,
+                                                   double *__restrict__ out) {
+    const int t = blockIdx.x;
+    int I = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
+    while ((I + 1) * (I + 2) / 2 <= t) ++I;
+    while (I * (I + 1) / 2 > t) --I;
+    const int J = t - I * (I + 1) / 2;   // tile pair J <= I
+    __shared__ double xj[128], yj[128];
+    const int64_t j0 = (int64_t)J * 128, i0 = (int64_t)I * 128;
+    if (threadIdx.x < 128) {
+        const int64_t j = j0 + threadIdx.x;
+        xj[threadIdx.x] = j < n ? coords[2 * j] : 0.0;
+        yj[threadIdx.x] = j < n ? coords[2 * j + 1] : 0.0;
+    }
+    __syncthreads();
+    double best = INFINITY;
+    for (int r = threadIdx.x; r < 128 * 128; r += blockDim.x) {
+        const int64_t i = i0 + (r >> 7), j = j0 + (r & 127);
+        if (i < n && j < i) {
+            const double dx = coords[2 * i] - xj[r & 127], dy = coords[2 * i + 1] - yj[r & 127];
+            best = fmin(best, fma(dx, dx, dy * dy));
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) best = fmin(best, __shfl_xor_sync(0xffffffffu, best, o));
+    if ((threadIdx.x & 31) == 0 && best < INFINITY)
+        atomicMin(reinterpret_cast<unsigned long long *>(out), (unsigned long long)__double_as_longlong(best));
 }
 
 // ---------------------------------------------------------------------------
@@ -149,6 +231,12 @@ __global__ void __launch_bounds__(320) k_matern_table(const double *__restrict__
     const int w = blockIdx.y;
     const double *oc = oconst + OC_N * (int64_t)w;
     const double kap = oc[OC_KAPPA], logc = oc[OC_LOGC];
+    const int elo = (int)oc[OC_ELO], ehi = (int)oc[OC_EHI];
+    {   // this block's buckets: octaves TAB_ELO + 32 blockIdx.x / TAB_S .. + 32 / TAB_S - 1
+        const int bx = (int)blockIdx.x;
+        const int e0 = TAB_ELO + (bx * 32) / TAB_S, e1 = TAB_ELO + (bx * 32 + 31) / TAB_S;
+        if (e1 < elo || e0 >= ehi) return;   // none of them is read
+    }
     for (int k = threadIdx.x; k < QNODES; k += blockDim.x) {
         const double t = k * QH;
         const double sh = sinh(0.5 * t);
@@ -160,7 +248,9 @@ __global__ void __launch_bounds__(320) k_matern_table(const double *__restrict__
     const int lb = threadIdx.x / TAB_NC, l = threadIdx.x % TAB_NC;
     const int bucket = blockIdx.x * 32 + lb;
     const double PI = 3.14159265358979323846;
-    if (bucket < TAB_NBUCKET) {
+    const int eb = TAB_ELO + bucket / TAB_S;
+    const bool used = bucket < TAB_NBUCKET && eb >= elo && eb < ehi;
+    if (used) {
         const int e = TAB_ELO + bucket / TAB_S, j = bucket % TAB_S;
         const double tl = cos(PI * (l + 0.5) / TAB_NC);
         const double wv = ldexp(1.0 + (j + 0.5 * (tl + 1.0)) / TAB_S, e);
@@ -183,7 +273,7 @@ __global__ void __launch_bounds__(320) k_matern_table(const double *__restrict__
         F[lb][l] = r;
     }
     __syncthreads();
-    if (l == 0 && bucket < TAB_NBUCKET) {
+    if (l == 0 && used) {
         // Chebyshev coefficients a_k, then monomial coefficients in t.
         double a[TAB_NC], c[TAB_NC], Tp[TAB_NC], Tc[TAB_NC], Tn[TAB_NC];
         for (int k = 0; k < TAB_NC; ++k) {
@@ -214,12 +304,14 @@ __global__ void __launch_bounds__(320) k_matern_table(const double *__restrict__
 // rho at w = u^2 from the table: exponent/mantissa bits give the sub-interval
 // and an exact local variable t; Horner in t.
 __device__ __forceinline__ double rho_table(const double *__restrict__ tab, double w, double kap,
-                                            double logc) {
+                                            double logc, int elo, int ehi) {
     const int hi = __double2hiint(w);
     const int lo = __double2loint(w);
     const int e = ((hi >> 20) & 0x7ff) - 1023;
     if (e >= TAB_EHI) return 0.0;
-    if (e < TAB_ELO) return (w == 0.0) ? 1.0 : rho_integral(sqrt(w), kap, logc);
+    // below the table, or outside the octaves built for this point (the range
+    // bounds every site pair, so this is a safety net): the integral itself
+    if (e < elo || e >= ehi) return (w == 0.0) ? 1.0 : rho_integral(sqrt(w), kap, logc);
     const int j = (hi >> (20 - TAB_SB)) & (TAB_S - 1);
     const double m = __hiloint2double((hi & 0x000fffff) | 0x3ff00000, lo);   // in [1, 2)
     const double t = fma(m, 2.0 * TAB_S, -(2.0 * TAB_S + 2.0 * j + 1.0));    // exact, in [-1, 1)
@@ -292,6 +384,7 @@ __global__ void __launch_bounds__(256) k_build(int nb, int64_t n, int64_t n_pad,
     }
     const double *oc = oconst + OC_N * (int64_t)w;
     const double nug = oc[OC_NUG], kap = oc[OC_KAPPA], logc = oc[OC_LOGC];
+    const int elo = (int)oc[OC_ELO], ehi = (int)oc[OC_EHI];
     const double *ca = coordT + (int64_t)w * 2 * n_pad;
     const double *cb = ca + n_pad;
     const double *tw = tab + (int64_t)w * TAB_SIZE;
@@ -308,7 +401,7 @@ __global__ void __launch_bounds__(256) k_build(int nb, int64_t n, int64_t n_pad,
         } else {
             const double da = ca[i] - aj, db = cb[i] - bj;
             const double wv = fma(da, da, db * db);
-            v = rho_table(tw, wv, kap, logc);
+            v = rho_table(tw, wv, kap, logc, elo, ehi);
         }
         put(r, v);
     }
@@ -633,20 +726,24 @@ const char *kernel_class_name(int c) {
     } while (0)
 
 cudaError_t launch_boxcox(int64_t n, int64_t n_pad, int p, int M, const double *y, const double *X,
-                          const double *lam, double *Bt, double *sumlogy, cudaStream_t s,
+                          const double *coords, const double *lam, double *Bt, double *sumlogy, cudaStream_t s,
                           KernelTimer *timer) {
     const int64_t total = (int64_t)(M + p) * n_pad;
     int blocks = (int)((total + 255) / 256);
     if (blocks > 4096) blocks = 4096;
+    const int64_t nt = (n + 127) / 128;
+    cudaError_t e = cudaMemsetAsync(sumlogy + 1, 0x7f, sizeof(double), s);   // 0x7f7f.. ~ 1.4e306
+    if (e != cudaSuccess) return e;
     TIMED(KC_BOXCOX, (k_boxcox_rows<<<blocks, 256, 0, s>>>(n, n_pad, p, M, y, X, lam, Bt),
-                      k_sumlog<<<1, 1024, 0, s>>>(n, y, sumlogy)));
+                      k_sumlog<<<1, 1024, 0, s>>>(n, y, sumlogy),
+                      k_min_dist2<<<(unsigned)(nt * (nt + 1) / 2), 256, 0, s>>>(n, coords, sumlogy + 1)));
     return cudaGetLastError();
 }
 
 cudaError_t launch_front(const BatchArgs &b, cudaStream_t s, bool double_float) {
     const int cnt = b.count;
     KernelTimer *timer = b.timer;
-    TIMED(KC_PREP, (k_omega_prep<<<cnt, 256, 0, s>>>(b.params, b.n, b.n_pad, b.coords, b.oconst,
+    TIMED(KC_PREP, (k_omega_prep<<<cnt, 256, 0, s>>>(b.params, b.n, b.n_pad, b.coords, b.sumlogy, b.oconst,
                                                       b.coordT, b.ldv, b.pstatus)));
     TIMED(KC_TABLE, (k_matern_table<<<dim3((TAB_NBUCKET + 31) / 32, cnt), 320, 0, s>>>(b.oconst, b.tab)));
     if (double_float)

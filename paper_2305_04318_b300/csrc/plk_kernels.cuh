@@ -30,7 +30,7 @@ struct BatchArgs {
     const double *coords;    // n x 2
     const double *lambdas;   // M
     const double *Bt;        // q x n_pad
-    const double *sumlogy;   // 1
+    const double *sumlogy;   // 2: sum log y, smallest squared site distance
     double *oconst;          // count x OC_N
     double *coordT;          // count x 2 x n_pad
     double *tab;             // count x TAB_SIZE
@@ -49,7 +49,7 @@ struct BatchArgs {
 void set_last_error(const char *msg);
 
 cudaError_t launch_boxcox(int64_t n, int64_t n_pad, int p, int M, const double *y, const double *X,
-                          const double *lam, double *Bt, double *sumlogy, cudaStream_t s,
+                          const double *coords, const double *lam, double *Bt, double *sumlogy, cudaStream_t s,
                           KernelTimer *timer = nullptr);
 cudaError_t launch_fp64_batch(const BatchArgs &b, cudaStream_t s);
 // pieces of the batch pipeline shared with the mixed path
