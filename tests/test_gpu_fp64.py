@@ -64,6 +64,25 @@ def test_not_pd_and_bad_params():
     compare({k: v[:2] for k, v in g.items()}, o, what="not_pd")
 
 
+def test_table_range_extremes():
+    """The rho table is built only over the octaves of w a point's site pairs
+    reach (from the transformed bounding box and the smallest site distance):
+    near-duplicate sites and extreme ranges and anisotropies, against the
+    oracle."""
+    ds = synth.aniso_dataset(21, 150, 5.0, 2)
+    ds.coords[7] = ds.coords[6] + np.array([1e-6, 0.0])     # near-duplicate pairs
+    ds.coords[9] = ds.coords[8] + np.array([0.0, 3e-4])
+    P = np.array([[0.02, 0.3, 0.2, 1.0, 0.0],       # short range: most w beyond the table's top
+                  [50.0, 8.0, 0.1, 1.0, 0.0],       # long range, smooth: tiny w
+                  [0.5, 0.1, 0.05, 4.0, 2.6],       # rough, strongly anisotropic
+                  [3.0, 2.5, 0.01, 3.5, 1.1],
+                  [0.2, 5.0, 0.3, 0.3, 0.7]])       # ratio < 1
+    lams = np.array([-0.5, 0.0, 1.0])
+    g = gpu_eval(ds, P, lams)
+    o = oracle_eval(ds, P, lams)
+    compare(g, o, what="table range extremes")
+
+
 def test_deterministic_and_batch_independent():
     w = synth.aniso1000(K=20)
     ds, P = w.datasets[0], w.params[0]
