@@ -1280,7 +1280,7 @@ static cudaError_t launch_mixed_steps(const BatchArgs &b, const MixedArgs &x, cu
     CUtensorMap tmapC;
     if ((e = make_tile_map(&tmapC, b.tiles, cnt, b.tpo)) != cudaSuccess) return e;
     const int sms = num_sms();
-    if (S == 7) {
+    if constexpr (S == 7) {
         if ((e = cudaFuncSetAttribute(k_trsm_split7x, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_split)) !=
             cudaSuccess)
             return e;
