@@ -23,6 +23,11 @@
  * log-likelihood l_p(omega, lambda) (eq. profile); the REML variant follows
  * eq. remlpro of the Appendix.
  *
+ * Post-processing of the Table-1 statistics (Sections 3.2, 3.4-3.6):
+ *   profile of one beta_j (eq. profilebetai), of sigma (eq. profileSigma), of
+ *   lambda (max over the omega points) and of any coordinate of the point
+ *   cloud by its upper convex hull; internal parameters omega' (Section 3.2).
+ *
  * Readings of the paper taken here (each also listed in the design notes):
  *   - Matern normaliser 2^{1-kappa}/Gamma(kappa) (the printed 2^{kappa-1} makes
  *     rho(0+) != 1); argument u = sqrt(8 kappa) d as printed.
@@ -31,6 +36,14 @@
  *   - Likelihood CI: {theta : l_p(theta) >= max l_p - chi2_1(level)/2}, endpoints
  *     by linear interpolation between bracketing grid points; a side that never
  *     crosses the threshold is censored at the grid edge.
+ *   - beta_j profile: (X^T V^-1 X)^-1_[-j,-j] is the inverse of the submatrix
+ *     (the GLS fit of the offset model y' - X_j b on X_-j), and the residual
+ *     sum of squares is the difference of the two printed quadratic forms.
+ *   - sigma profile: the grid is in sigma (not sigma^2); ML form only.
+ *   - Hull profile: per distinct x only the largest value counts; points on a
+ *     hull edge are not vertices; NaN outside the cloud's x range.
+ *   - Internal parameters: a ratio phi_X/phi_Y below one is mapped to the same
+ *     correlation with the axes exchanged before the square root is taken.
  *
  * Modified Bessel function K_nu(x) (needed by eq. matern):
  *   x <= 2 : Temme's series for K_mu, K_{mu+1}, |mu| <= 1/2 (N. M. Temme,
@@ -410,11 +423,13 @@ fail:
 
 /* Batch over K omega points (rows of params, K x 5), OpenMP-parallel over the
  * points.  Per-point outputs are laid out point-major: logL[K*M], sigma2[K*M],
- * beta[K*M*p], logdet[K*2], status[K].  Returns the number of threads used. */
+ * beta[K*M*p], logdet[K*2], ssq[K*(M+p)^2] (Table 1 ssqYX), status[K]; any
+ * output may be NULL.  Returns the number of threads used. */
 int oracle_profile_batch(int64_t n, int32_t p, const double *coords, const double *y,
                          const double *X, int64_t K, const double *params, int32_t M,
                          const double *lambdas, int reml, int nthreads, double *logL,
-                         double *sigma2, double *beta, double *logdet, int32_t *status)
+                         double *sigma2, double *beta, double *logdet, double *ssq,
+                         int32_t *status)
 {
     int used = 1;
 #ifdef _OPENMP
@@ -427,7 +442,8 @@ int oracle_profile_batch(int64_t n, int32_t p, const double *coords, const doubl
         int st = oracle_profile_point(n, p, coords, y, X, params + 5 * k, M, lambdas, reml,
                                       logL ? logL + k * M : NULL,
                                       sigma2 ? sigma2 + k * M : NULL,
-                                      beta ? beta + k * M * p : NULL, NULL, NULL,
+                                      beta ? beta + k * M * p : NULL, NULL,
+                                      ssq ? ssq + k * (M + p) * (M + p) : NULL,
                                       logdet ? logdet + 2 * k : NULL);
         if (status)
             status[k] = st;
@@ -530,4 +546,310 @@ int oracle_profile_ci(const double *grid, const double *prof, int64_t G, double 
     *argmax = grid[ib];
     *censored = cens;
     return OR_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Post-processing of the Table-1 statistics (Sections 3.4-3.6)               */
+/* ------------------------------------------------------------------------ */
+
+/* Inverse of the d x d matrix A (row-major) by Gauss-Jordan elimination with
+ * partial pivoting; Ainv receives it.  Returns OR_NOT_PD when a pivot is zero
+ * (A singular).  d == 0 is a valid empty matrix. */
+static int oracle_invert(int32_t d, const double *A, double *Ainv)
+{
+    double *T = (double *)malloc(sizeof(double) * (d > 0 ? d * 2 * d : 1));
+    if (!T)
+        return OR_INVALID;
+    for (int32_t r = 0; r < d; ++r)
+        for (int32_t c = 0; c < 2 * d; ++c)
+            T[r * 2 * d + c] = (c < d) ? A[r * d + c] : (c - d == r ? 1.0 : 0.0);
+    for (int32_t c = 0; c < d; ++c) {
+        int32_t piv = c;
+        for (int32_t r = c + 1; r < d; ++r)
+            if (fabs(T[r * 2 * d + c]) > fabs(T[piv * 2 * d + c]))
+                piv = r;
+        if (T[piv * 2 * d + c] == 0.0) {
+            free(T);
+            return OR_NOT_PD;
+        }
+        if (piv != c)
+            for (int32_t k = 0; k < 2 * d; ++k) {
+                double t = T[c * 2 * d + k];
+                T[c * 2 * d + k] = T[piv * 2 * d + k];
+                T[piv * 2 * d + k] = t;
+            }
+        double dv = T[c * 2 * d + c];
+        for (int32_t k = 0; k < 2 * d; ++k)
+            T[c * 2 * d + k] /= dv;
+        for (int32_t r = 0; r < d; ++r) {
+            if (r == c)
+                continue;
+            double f = T[r * 2 * d + c];
+            for (int32_t k = 0; k < 2 * d; ++k)
+                T[r * 2 * d + k] -= f * T[c * 2 * d + k];
+        }
+    }
+    for (int32_t r = 0; r < d; ++r)
+        for (int32_t c = 0; c < d; ++c)
+            Ainv[r * d + c] = T[r * 2 * d + d + c];
+    free(T);
+    return OR_OK;
+}
+
+/* Profile log-likelihood of one regression coefficient beta_j (Section 3.4,
+ * eq. profilebetai): for each grid value b = grid[g],
+ *   prof[g] = max over points k (status 0) and lambdas m of
+ *             l(beta_j = b, beta_-j-hat(b), sigma-hat(b), omega_k, lambda_m).
+ * With beta_j fixed, X_j b is an offset and beta_-j-hat(b) is the GLS fit of
+ * y' - X_j b on X_-j.  The two quadratic forms the section expands,
+ *   t1 = (y' - X_j b)^T V^-1 (y' - X_j b)
+ *      = y'^T V^-1 y' - 2 b (X^T V^-1 y')_j + b^2 (X^T V^-1 X)_jj,
+ *   t2 = (X_-j beta_-j-hat)^T V^-1 (X_-j beta_-j-hat)
+ *      = (q_y - b q_x)^T A^-1 (q_y - b q_x),   A = (X^T V^-1 X)_[-j,-j],
+ *        q_y = (X^T V^-1 y')_[-j], q_x = (X^T V^-1 X)_[-j,j],
+ * are read off ssqYX; their difference is the residual sum of squares
+ * RSS(b) (as in Step 3 item 8), sigma-hat^2(b) = RSS(b)/n, and
+ *   -2 l = n log sigma-hat^2(b) + log|V| - 2(lambda-1) sum log y + n log(2 pi) + n.
+ * A^-1 is the inverse of the submatrix: the GLS normal equations of the
+ * offset model involve only the columns X_-j.
+ * ssq: K x (M+p) x (M+p) (Table 1 ssqYX, y' columns first); logdet: K x 2
+ * ([0] = log|V|); status: K (NULL = all valid; a point counts when
+ * (status & 15) == 0).  NaN where no point gives a finite value. */
+int oracle_profile_beta(int64_t n, int32_t p, int32_t M, int64_t K, const double *ssq,
+                        const double *logdet, const int32_t *status, const double *lambdas,
+                        double sumlogy, int32_t j, int64_t G, const double *grid, double *prof)
+{
+    if (j < 0 || j >= p)
+        return OR_INVALID;
+    int32_t q = M + p, d = p - 1;
+    double *A = (double *)malloc(sizeof(double) * (d > 0 ? d * d : 1));
+    double *Ai = (double *)malloc(sizeof(double) * (d > 0 ? d * d : 1));
+    int32_t *idx = (int32_t *)malloc(sizeof(int32_t) * (d > 0 ? d : 1));
+    if (!A || !Ai || !idx) {
+        free(A); free(Ai); free(idx);
+        return OR_INVALID;
+    }
+    for (int64_t g = 0; g < G; ++g)
+        prof[g] = NAN;
+    for (int32_t a = 0, t = 0; a < p; ++a)
+        if (a != j)
+            idx[t++] = a;
+    for (int64_t k = 0; k < K; ++k) {
+        if (status && (status[k] & 15) != 0)
+            continue;
+        const double *S = ssq + k * q * q;
+        double ldv = logdet[2 * k];
+        for (int32_t a = 0; a < d; ++a)
+            for (int32_t b = 0; b < d; ++b)
+                A[a * d + b] = S[(M + idx[a]) * q + (M + idx[b])];
+        if (oracle_invert(d, A, Ai) != OR_OK)
+            continue;
+        for (int32_t m = 0; m < M; ++m) {
+            double yy = S[m * q + m];
+            double xyj = S[(M + j) * q + m];
+            double xxjj = S[(M + j) * q + (M + j)];
+            for (int64_t g = 0; g < G; ++g) {
+                double b = grid[g];
+                double t1 = yy - 2.0 * b * xyj + b * b * xxjj;
+                double t2 = 0.0;
+                for (int32_t a = 0; a < d; ++a) {
+                    double ra = S[(M + idx[a]) * q + m] - b * S[(M + idx[a]) * q + (M + j)];
+                    for (int32_t c = 0; c < d; ++c) {
+                        double rc = S[(M + idx[c]) * q + m] - b * S[(M + idx[c]) * q + (M + j)];
+                        t2 += ra * Ai[a * d + c] * rc;
+                    }
+                }
+                double rss = t1 - t2;
+                if (!(rss > 0.0))
+                    continue;
+                double m2l = (double)n * log(rss / (double)n) + ldv
+                           - 2.0 * (lambdas[m] - 1.0) * sumlogy
+                           + (double)n * log(2.0 * OR_PI) + (double)n;
+                double ll = -0.5 * m2l;
+                if (ll == ll && (isnan(prof[g]) || ll > prof[g]))
+                    prof[g] = ll;
+            }
+        }
+    }
+    free(A); free(Ai); free(idx);
+    return OR_OK;
+}
+
+/* Profile log-likelihood of sigma (Section 3.5, eq. profileSigma): for each
+ * grid value s = sgrid[g] > 0,
+ *   prof[g] = max over valid points k and lambdas m of l_p(s, omega_k, lambda_m),
+ *   -2 l_p - n log(2 pi) = RSS / s^2 + n log s^2 + log|V| - 2(lambda-1) sum log y,
+ * with RSS = (y' - X beta-hat)^T V^-1 (y' - X beta-hat) expanded from ssqYX as
+ * y'^T V^-1 y' - 2 beta-hat^T X^T V^-1 y' + beta-hat^T X^T V^-1 X beta-hat and
+ * beta-hat = (X^T V^-1 X)^-1 X^T V^-1 y' (eq. betahat).  Arguments as for
+ * oracle_profile_beta. */
+int oracle_profile_sigma(int64_t n, int32_t p, int32_t M, int64_t K, const double *ssq,
+                         const double *logdet, const int32_t *status, const double *lambdas,
+                         double sumlogy, int64_t G, const double *sgrid, double *prof)
+{
+    int32_t q = M + p;
+    double *A = (double *)malloc(sizeof(double) * p * p);
+    double *Ai = (double *)malloc(sizeof(double) * p * p);
+    double *bh = (double *)malloc(sizeof(double) * p);
+    if (!A || !Ai || !bh) {
+        free(A); free(Ai); free(bh);
+        return OR_INVALID;
+    }
+    for (int64_t g = 0; g < G; ++g)
+        prof[g] = NAN;
+    for (int64_t k = 0; k < K; ++k) {
+        if (status && (status[k] & 15) != 0)
+            continue;
+        const double *S = ssq + k * q * q;
+        double ldv = logdet[2 * k];
+        for (int32_t a = 0; a < p; ++a)
+            for (int32_t b = 0; b < p; ++b)
+                A[a * p + b] = S[(M + a) * q + (M + b)];
+        if (oracle_invert(p, A, Ai) != OR_OK)
+            continue;
+        for (int32_t m = 0; m < M; ++m) {
+            for (int32_t a = 0; a < p; ++a) {
+                double t = 0.0;
+                for (int32_t c = 0; c < p; ++c)
+                    t += Ai[a * p + c] * S[(M + c) * q + m];
+                bh[a] = t;
+            }
+            double rss = S[m * q + m];
+            for (int32_t a = 0; a < p; ++a) {
+                rss -= 2.0 * bh[a] * S[(M + a) * q + m];
+                for (int32_t c = 0; c < p; ++c)
+                    rss += bh[a] * A[a * p + c] * bh[c];
+            }
+            if (!(rss > 0.0))
+                continue;
+            for (int64_t g = 0; g < G; ++g) {
+                double s2 = sgrid[g] * sgrid[g];
+                double m2l = rss / s2 + (double)n * log(s2) + ldv
+                           - 2.0 * (lambdas[m] - 1.0) * sumlogy + (double)n * log(2.0 * OR_PI);
+                double ll = -0.5 * m2l;
+                if (ll == ll && (isnan(prof[g]) || ll > prof[g]))
+                    prof[g] = ll;
+            }
+        }
+    }
+    free(A); free(Ai); free(bh);
+    return OR_OK;
+}
+
+typedef struct { double x, v; int64_t i; } oracle_xv;
+
+static int oracle_xv_cmp(const void *pa, const void *pb)
+{
+    const oracle_xv *a = (const oracle_xv *)pa, *b = (const oracle_xv *)pb;
+    if (a->x != b->x)
+        return a->x < b->x ? -1 : 1;
+    if (a->v != b->v)
+        return a->v > b->v ? -1 : 1;   /* larger value first */
+    return (a->i > b->i) - (a->i < b->i);
+}
+
+/* 1-D profile from a point cloud by its upper convex hull (Section 3.6): the
+ * points (x[k], v[k]) with finite v, sorted by x; per distinct x only the
+ * largest v (lowest k among equal values) is kept; the upper hull is built
+ * left to right by the monotone chain, dropping a point whenever it does not
+ * make a strict right turn (so points on a hull edge are not vertices); the
+ * profile is the linear interpolation of the hull vertices.
+ *   out[t] = that interpolant at xq[t] (NaN outside [min x, max x] or when no
+ *            v is finite);
+ *   on_hull[k] = 1 for hull vertices, else 0 (may be NULL).
+ * Returns the number of hull vertices (0 if none), or -1 on allocation failure. */
+int64_t oracle_profile_hull(int64_t K, const double *x, const double *v, int64_t Q,
+                            const double *xq, double *out, int32_t *on_hull)
+{
+    oracle_xv *P = (oracle_xv *)malloc(sizeof(oracle_xv) * (K > 0 ? K : 1));
+    int64_t *H = (int64_t *)malloc(sizeof(int64_t) * (K > 0 ? K : 1));
+    if (!P || !H) {
+        free(P); free(H);
+        return -1;
+    }
+    int64_t np = 0;
+    for (int64_t k = 0; k < K; ++k) {
+        if (on_hull)
+            on_hull[k] = 0;
+        if (isfinite(v[k]) && isfinite(x[k])) {
+            P[np].x = x[k]; P[np].v = v[k]; P[np].i = k;
+            ++np;
+        }
+    }
+    qsort(P, (size_t)np, sizeof(oracle_xv), oracle_xv_cmp);
+    int64_t nh = 0;
+    for (int64_t t = 0; t < np; ++t) {
+        if (t > 0 && P[t].x == P[t - 1].x)
+            continue;   /* a lower (or later) point at the same x */
+        while (nh >= 2) {
+            const oracle_xv *o = &P[H[nh - 2]], *a = &P[H[nh - 1]];
+            double cross = (a->x - o->x) * (P[t].v - o->v) - (a->v - o->v) * (P[t].x - o->x);
+            if (cross >= 0.0)
+                --nh;   /* a lies on or below the segment o -> P[t] */
+            else
+                break;
+        }
+        H[nh++] = t;
+    }
+    if (on_hull)
+        for (int64_t h = 0; h < nh; ++h)
+            on_hull[P[H[h]].i] = 1;
+    for (int64_t t = 0; t < Q; ++t) {
+        double xv = xq[t], r = NAN;
+        if (nh > 0 && xv >= P[H[0]].x && xv <= P[H[nh - 1]].x) {
+            for (int64_t h = 0; h < nh; ++h) {
+                const oracle_xv *a = &P[H[h]];
+                if (a->x == xv) {
+                    r = a->v;
+                    break;
+                }
+                if (h + 1 < nh && xv < P[H[h + 1]].x) {
+                    const oracle_xv *b = &P[H[h + 1]];
+                    r = a->v + (b->v - a->v) * (xv - a->x) / (b->x - a->x);
+                    break;
+                }
+            }
+        }
+        out[t] = r;
+    }
+    free(P); free(H);
+    return nh;
+}
+
+/* Internal parameters omega' = (gamma_1, kappa~, nu, gamma_2, gamma_3) of a
+ * natural parameter row omega = (phi_X, kappa, nu^2, phi_R, phi_A) (Section
+ * 3.2, eq. shapeTransform and the range/anisotropy transform):
+ *   gamma_1 = log phi_X + log phi_Y, phi_Y = phi_X / phi_R
+ *   kappa~  = log kappa (kappa_hat_large == 0) or 1/sqrt(kappa) (otherwise)
+ *   nu      = sqrt(nu^2)
+ *   gamma_2 = sqrt(phi_X/phi_Y - 1) cos(2 phi_A),  gamma_3 = ... sin(2 phi_A).
+ * A ratio below one is first mapped to the same correlation with the axes
+ * exchanged, (phi_X, phi_Y, phi_A) -> (phi_Y, phi_X, phi_A + pi/2), so
+ * gamma_2, gamma_3 = -sqrt(phi_Y/phi_X - 1) (cos 2 phi_A, sin 2 phi_A). */
+void oracle_internal_params(const double *omega, int kappa_hat_large, double *out)
+{
+    double phx = omega[0], kap = omega[1], nug = omega[2], rat = omega[3], ang = omega[4];
+    double phy = phx / rat;
+    out[0] = log(phx) + log(phy);
+    out[1] = kappa_hat_large ? 1.0 / sqrt(kap) : log(kap);
+    out[2] = sqrt(nug);
+    double r, sgn;
+    if (phx / phy >= 1.0) {
+        r = sqrt(phx / phy - 1.0);
+        sgn = 1.0;
+    } else {
+        r = sqrt(phy / phx - 1.0);
+        sgn = -1.0;
+    }
+    out[3] = sgn * r * cos(2.0 * ang);
+    out[4] = sgn * r * sin(2.0 * ang);
+}
+
+/* Sum of log y_i: the Box-Cox Jacobian's data term (Section 2, eq. 2). */
+double oracle_sum_log(int64_t n, const double *y)
+{
+    double s = 0.0;
+    for (int64_t i = 0; i < n; ++i)
+        s += log(y[i]);
+    return s;
 }
