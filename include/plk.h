@@ -113,6 +113,11 @@ typedef struct {
     double *err_bound;       /* K      PLK_MIXED: a-posteriori bound on |Delta l_p| of the split-product
                                        factorisation that produced the result (0 for points
                                        re-evaluated in FP64); PLK_FP64: 0 */
+    double *ssq_yx;          /* K x (M+p) x (M+p)  (y',X)^T V^-1 (y',X), the ssqYX of Table 1
+                                       (Section 3.3 Step 3 item 4): symmetric, row-major per
+                                       point, the M columns y'(lambda_m) first, then X; NaN
+                                       where V or X^T V^-1 X is not positive definite or the
+                                       parameter row is invalid */
 } plk_eval_args;
 
 /* Bytes of device workspace plk_eval_device needs to process `batch` points of
@@ -233,6 +238,79 @@ plk_status plk_profile_ci_device(const double *grid, const double *prof, int64_t
 
 /* chi2_1 quantile used by the CI: c with P(chi2_1 <= c) = level. */
 double plk_chi2_1_quantile(double level);
+
+/* ------------------------------------------------------------------------ */
+/* Post-processing of the Table-1 statistics (Sections 3.2, 3.4-3.6)          */
+/* ------------------------------------------------------------------------ */
+
+/* Statistics of K points of one dataset, as plk_eval_device writes them. */
+typedef struct {
+    int64_t n;               /* sites, n > p */
+    int32_t p;               /* covariates, 1 <= p <= 16 */
+    int32_t M;               /* lambda values, M >= 1, M + p <= 64 */
+    int64_t K;               /* parameter points, >= 0 */
+    const double *y;         /* device, n observations (> 0): the Box-Cox Jacobian's sum log y */
+    const double *lambdas;   /* device, M */
+    const double *ssq_yx;    /* device, K x (M+p) x (M+p) (plk_eval_args.ssq_yx) */
+    const double *logdet;    /* device, K x 2 (only [k][0] = log|V| is read) */
+    const int32_t *status;   /* device, K, or NULL: a point is used when (status & 15) == 0 */
+} plk_stats_args;
+
+/* Profile log-likelihood of one regression coefficient beta_j (Section 3.4,
+ * eq. profilebetai), for each of the G grid values b = grid[g]:
+ *   prof[g] = max over the used points k and all lambdas m of
+ *             l(beta_j = b, beta_-j-hat(b), sigma-hat(b), omega_k, lambda_m),
+ * where beta_-j-hat(b) and sigma-hat^2(b) = RSS(b)/n are the ML estimates of
+ * the model with the offset X_j b (GLS of y' - X_j b on X_-j):
+ *   -2 l = n log(RSS(b)/n) + log|V| - 2(lambda-1) sum log y + n log(2 pi) + n.
+ * The ML form whatever the reml option of the evaluation was (the statistics
+ * do not depend on it).  prof: device, G doubles, NaN where no pair gives a
+ * finite value.  0 <= j < p.  grid, prof: device.  Runs on `stream`.
+ * Errors: PLK_E_INVALID (sizes, NULL pointers, j), PLK_E_CUDA. */
+plk_status plk_profile_beta_device(const plk_stats_args *stats, int32_t j, const double *grid,
+                                   int64_t G, double *prof, void *stream);
+
+/* Profile log-likelihood of sigma (Section 3.5, eq. profileSigma) at the G
+ * grid values s = grid[g] (standard deviations, > 0; other values give NaN):
+ *   prof[g] = max over the used points and all lambdas of
+ *   -(1/2) [RSS/s^2 + n log s^2 + log|V| - 2(lambda-1) sum log y + n log(2 pi)],
+ * RSS the residual sum of squares at beta-hat (Table 1 ssqResidual).  ML form.
+ * Device pointers, `stream`; errors as plk_profile_beta_device. */
+plk_status plk_profile_sigma_device(const plk_stats_args *stats, const double *grid, int64_t G,
+                                    double *prof, void *stream);
+
+/* Profile of lambda (Section 3.6): prof[m] = max over k of logL[k*M + m],
+ * NaN values skipped (NaN if all are).  logL: device K x M (plk_eval_args.logL);
+ * prof: device M.  1 <= M <= 65535.  The CI over the lambda grid then follows
+ * from plk_profile_ci_device. */
+plk_status plk_profile_lambda_device(const double *logL, int64_t K, int32_t M, double *prof,
+                                     void *stream);
+
+/* 1-D profile of any coordinate of the point cloud by its upper convex hull
+ * (Section 3.6): the cloud is (x[k * x_stride], v[k]) for k < K (e.g. x = one
+ * column of the K x 5 parameter rows with x_stride 5, v = the max over lambda
+ * from plk_profile_max_device(logL, K, M, v)); points with a non-finite
+ * coordinate are ignored.  Writes
+ *   on_hull[k] = 1 if point k is a vertex of the upper hull, else 0 (device, K;
+ *                required).  Per distinct x only the largest v can be a vertex
+ *                (lowest k among equal values); points on a hull edge are not
+ *                vertices;
+ *   out[t]     = the linear interpolation of the vertices at xq[t] (device, Q),
+ *                NaN outside the vertices' x range.
+ * Work O(K^2) for the vertices, O(Q K) for the queries.  Runs on `stream`. */
+plk_status plk_profile_hull_device(const double *x, int64_t x_stride, const double *v, int64_t K,
+                                   const double *xq, int64_t Q, double *out, int32_t *on_hull,
+                                   void *stream);
+
+/* Internal parameters omega' = (gamma_1, kappa~, nu, gamma_2, gamma_3) of K
+ * natural parameter rows (Section 3.2): gamma_1 = log phi_X + log phi_Y;
+ * kappa~ = log kappa, or 1/sqrt(kappa) when kappa_hat_large != 0 (the MLE of
+ * kappa is 4 or more); nu = sqrt(nu^2); gamma_2, gamma_3 = sqrt(phi_X/phi_Y - 1)
+ * (cos 2 phi_A, sin 2 phi_A).  A ratio phi_X/phi_Y below one is first written
+ * with the axes exchanged, (phi_Y, phi_X, phi_A + pi/2), the same correlation,
+ * which negates (gamma_2, gamma_3).  params, out: device K x 5. */
+plk_status plk_internal_params_device(const double *params, int64_t K, int32_t kappa_hat_large,
+                                      double *out, void *stream);
 
 /* ------------------------------------------------------------------------ */
 /* Instrumentation (not part of the paper's method)                          */

@@ -435,6 +435,7 @@ static plk_status run_eval(const plk_eval_args *a, int reml, int flags, const La
         b.sigma2 = a->sigma2;
         b.beta = a->beta;
         b.logdet = a->logdet;
+        b.ssq = a->ssq_yx;
         b.status = a->status;
         b.timer = timer;
         if (L.mixed) {

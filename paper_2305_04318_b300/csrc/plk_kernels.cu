@@ -553,7 +553,8 @@ __global__ void k_finalize(int count, int64_t k0, int M, int p, int64_t n, int n
                            const double *__restrict__ ldv, const int *__restrict__ pstatus,
                            const double *__restrict__ sumlogy, const double *__restrict__ lambdas,
                            double *logL, double *sigma2, double *beta, double *logdet,
-                           int32_t *status, const int *__restrict__ out_index, int32_t status_or) {
+                           double *ssq, int32_t *status, const int *__restrict__ out_index,
+                           int32_t status_or) {
     const int w = blockIdx.x * blockDim.x + threadIdx.x;
     if (w >= count) return;
     const int64_t k = out_index ? (int64_t)out_index[w] : k0 + w;
@@ -630,6 +631,14 @@ __global__ void k_finalize(int count, int64_t k0, int M, int p, int64_t n, int n
     if (logdet) {
         logdet[2 * k] = ld;
         logdet[2 * k + 1] = good ? ldx : NaN;
+    }
+    if (ssq) {
+        // Table 1 ssqYX = B^T V^-1 B, from the lower triangle of the tile
+        const int q = M + p;
+        double *o = ssq + k * q * q;
+        for (int a = 0; a < q; ++a)
+            for (int c = 0; c < q; ++c)
+                o[a * q + c] = good ? -S[(a >= c ? a : c) * TB + (a >= c ? c : a)] : NaN;
     }
     if (status) status[k] = st | status_or;
 }
@@ -760,7 +769,7 @@ cudaError_t launch_finalize(const BatchArgs &b, cudaStream_t s) {
     KernelTimer *timer = b.timer;
     TIMED(KC_FINAL, (k_finalize<<<(cnt + 63) / 64, 64, 0, s>>>(
                         cnt, b.k0, b.M, b.p, b.n, b.nb, b.reml, b.tpo, b.tiles, b.ldv, b.pstatus,
-                        b.sumlogy, b.lambdas, b.logL, b.sigma2, b.beta, b.logdet, b.status, b.out_index,
+                        b.sumlogy, b.lambdas, b.logL, b.sigma2, b.beta, b.logdet, b.ssq, b.status, b.out_index,
                         b.status_or)));
     return cudaGetLastError();
 }

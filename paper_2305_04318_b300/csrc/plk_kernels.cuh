@@ -39,6 +39,7 @@ struct BatchArgs {
     double *ldv;             // count
     int *pstatus;            // count
     double *logL, *sigma2, *beta, *logdet;
+    double *ssq = nullptr;   // K x q x q (Table 1 ssqYX), may be NULL
     int32_t *status;
     KernelTimer *timer = nullptr;
     const int *out_index = nullptr;   // when set, batch slot w writes output row out_index[w]

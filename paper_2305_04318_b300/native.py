@@ -32,7 +32,14 @@ class EvalArgs(C.Structure):
                 ("coords", C.c_void_p), ("y", C.c_void_p), ("X", C.c_void_p), ("lambdas", C.c_void_p),
                 ("K", C.c_int64), ("params", C.c_void_p),
                 ("logL", C.c_void_p), ("sigma2", C.c_void_p), ("beta", C.c_void_p),
-                ("logdet", C.c_void_p), ("status", C.c_void_p), ("err_bound", C.c_void_p)]
+                ("logdet", C.c_void_p), ("status", C.c_void_p), ("err_bound", C.c_void_p),
+                ("ssq_yx", C.c_void_p)]
+
+
+class StatsArgs(C.Structure):
+    _fields_ = [("n", C.c_int64), ("p", C.c_int32), ("M", C.c_int32), ("K", C.c_int64),
+                ("y", C.c_void_p), ("lambdas", C.c_void_p), ("ssq_yx", C.c_void_p),
+                ("logdet", C.c_void_p), ("status", C.c_void_p)]
 
 
 class Options(C.Structure):
@@ -72,6 +79,11 @@ def lib():
         "plk_profile_max_device": (C.c_int, [vp, i64, i64, vp, vp]),
         "plk_profile_ci_device": (C.c_int, [vp, vp, i64, dbl, vp, vp]),
         "plk_chi2_1_quantile": (dbl, [dbl]),
+        "plk_profile_beta_device": (C.c_int, [C.POINTER(StatsArgs), i32, vp, i64, vp, vp]),
+        "plk_profile_sigma_device": (C.c_int, [C.POINTER(StatsArgs), vp, i64, vp, vp]),
+        "plk_profile_lambda_device": (C.c_int, [vp, i64, i32, vp, vp]),
+        "plk_profile_hull_device": (C.c_int, [vp, i64, vp, i64, vp, i64, vp, vp, vp]),
+        "plk_internal_params_device": (C.c_int, [vp, i64, i32, vp, vp]),
         "plk_kernel_timing": (C.c_int, [C.POINTER(dbl), C.POINTER(i64), i32, i32, C.POINTER(i32)]),
         "plk_kernel_class_name": (C.c_char_p, [i32]),
     }
@@ -129,12 +141,13 @@ def kernel_timing(reset=True):
 
 
 def eval_device(coords, y, X, lambdas, params, precision=FP64, reml=False, batch=0,
-                workspace=None, stream=None, outputs=None, flags=0):
+                workspace=None, stream=None, outputs=None, flags=0, with_ssq=False):
     """Evaluate l_p at all rows of `params` (torch CUDA float64 tensors).
 
     Returns a dict of CUDA tensors logL[K,M], sigma2[K,M], beta[K,M,p],
-    logdet[K,2], status[K] (int32).  The workspace (uint8 CUDA tensor) is
-    allocated with torch when not given.  Asynchronous on `stream`.
+    logdet[K,2], status[K] (int32), err_bound[K], and ssq_yx[K,M+p,M+p] (the
+    Table-1 cross-products) when with_ssq.  The workspace (uint8 CUDA tensor)
+    is allocated with torch when not given.  Asynchronous on `stream`.
     """
     import torch
     dev = coords.device
@@ -152,6 +165,8 @@ def eval_device(coords, y, X, lambdas, params, precision=FP64, reml=False, batch
                        logdet=torch.empty((K, 2), dtype=torch.float64, device=dev),
                        status=torch.empty((K,), dtype=torch.int32, device=dev),
                        err_bound=torch.empty((K,), dtype=torch.float64, device=dev))
+        if with_ssq:
+            outputs["ssq_yx"] = torch.empty((K, M + p, M + p), dtype=torch.float64, device=dev)
     wsb = workspace_bytes(n, p, M, batch, precision)
     if wsb == 0:
         raise PlkError(PLK_E_INVALID, f"invalid sizes n={n} p={p} M={M}")
@@ -159,7 +174,8 @@ def eval_device(coords, y, X, lambdas, params, precision=FP64, reml=False, batch
         workspace = torch.empty((wsb,), dtype=torch.uint8, device=dev)
     a = EvalArgs(n, p, M, _ptr(coords), _ptr(y), _ptr(X), _ptr(lambdas), K, _ptr(params),
                  _ptr(outputs.get("logL")), _ptr(outputs.get("sigma2")), _ptr(outputs.get("beta")),
-                 _ptr(outputs.get("logdet")), _ptr(outputs.get("status")), _ptr(outputs.get("err_bound")))
+                 _ptr(outputs.get("logdet")), _ptr(outputs.get("status")), _ptr(outputs.get("err_bound")),
+                 _ptr(outputs.get("ssq_yx")))
     o = Options(precision, int(bool(reml)), batch, int(flags))
     _check(lib().plk_eval_device(C.byref(a), C.byref(o), _ptr(workspace), workspace.numel(),
                                  _stream_handle(stream)))
@@ -186,7 +202,8 @@ def eval_device_static(coords, y, X, lambdas, params, reml=False, stream=None, o
                        status=torch.empty((K,), dtype=torch.int32, device=dev))
     a = EvalArgs(n, p, M, _ptr(coords), _ptr(y), _ptr(X), _ptr(lambdas), K, _ptr(params),
                  _ptr(outputs.get("logL")), _ptr(outputs.get("sigma2")), _ptr(outputs.get("beta")),
-                 _ptr(outputs.get("logdet")), _ptr(outputs.get("status")), None)
+                 _ptr(outputs.get("logdet")), _ptr(outputs.get("status")), None,
+                 _ptr(outputs.get("ssq_yx")))
     _check(lib().plk_eval_device_static(C.byref(a), int(bool(reml)), _stream_handle(stream)))
     return outputs
 
@@ -214,6 +231,71 @@ def profile_ci_device(grid, prof, level=0.95, out=None, stream=None):
 
 def chi2_1_quantile(level):
     return float(lib().plk_chi2_1_quantile(float(level)))
+
+
+def _stats_args(y, lambdas, ssq_yx, logdet, status):
+    K, q = ssq_yx.shape[0], ssq_yx.shape[1]
+    M = lambdas.shape[0]
+    return StatsArgs(y.shape[0], q - M, M, K, _ptr(y), _ptr(lambdas), _ptr(ssq_yx), _ptr(logdet),
+                     _ptr(status))
+
+
+def profile_beta_device(y, lambdas, ssq_yx, logdet, status, j, grid, prof=None, stream=None):
+    """Profile of beta_j at the CUDA float64 `grid` from the evaluation's
+    statistics (ssq_yx [K,M+p,M+p], logdet [K,2], status [K] or None)."""
+    import torch
+    if prof is None:
+        prof = torch.empty((grid.shape[0],), dtype=torch.float64, device=grid.device)
+    a = _stats_args(y, lambdas, ssq_yx, logdet, status)
+    _check(lib().plk_profile_beta_device(C.byref(a), int(j), _ptr(grid), grid.shape[0], _ptr(prof),
+                                         _stream_handle(stream)))
+    return prof
+
+
+def profile_sigma_device(y, lambdas, ssq_yx, logdet, status, grid, prof=None, stream=None):
+    """Profile of sigma at the CUDA float64 `grid` (standard deviations)."""
+    import torch
+    if prof is None:
+        prof = torch.empty((grid.shape[0],), dtype=torch.float64, device=grid.device)
+    a = _stats_args(y, lambdas, ssq_yx, logdet, status)
+    _check(lib().plk_profile_sigma_device(C.byref(a), _ptr(grid), grid.shape[0], _ptr(prof),
+                                          _stream_handle(stream)))
+    return prof
+
+
+def profile_lambda_device(logL, prof=None, stream=None):
+    """prof[m] = NaN-skipping max over the omega points of logL[:, m]."""
+    import torch
+    K, M = logL.shape
+    if prof is None:
+        prof = torch.empty((M,), dtype=torch.float64, device=logL.device)
+    _check(lib().plk_profile_lambda_device(_ptr(logL), K, M, _ptr(prof), _stream_handle(stream)))
+    return prof
+
+
+def profile_hull_device(x, v, xq, x_stride=1, out=None, on_hull=None, stream=None):
+    """Upper-hull profile of the cloud (x[k * x_stride], v[k]) at the points xq.
+
+    Returns (out [Q] float64, on_hull [K] int32), CUDA tensors."""
+    import torch
+    K = v.shape[0]
+    if out is None:
+        out = torch.empty((xq.shape[0],), dtype=torch.float64, device=v.device)
+    if on_hull is None:
+        on_hull = torch.empty((K,), dtype=torch.int32, device=v.device)
+    _check(lib().plk_profile_hull_device(_ptr(x), int(x_stride), _ptr(v), K, _ptr(xq), xq.shape[0],
+                                         _ptr(out), _ptr(on_hull), _stream_handle(stream)))
+    return out, on_hull
+
+
+def internal_params_device(params, kappa_hat_large=False, out=None, stream=None):
+    """omega' = (gamma_1, kappa~, nu, gamma_2, gamma_3) of each parameter row."""
+    import torch
+    if out is None:
+        out = torch.empty_like(params)
+    _check(lib().plk_internal_params_device(_ptr(params), params.shape[0], int(bool(kappa_hat_large)),
+                                            _ptr(out), _stream_handle(stream)))
+    return out
 
 
 class Context:

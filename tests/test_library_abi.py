@@ -50,3 +50,17 @@ def test_eval_device_rejects_bad_arguments_without_touching_the_gpu(L):
 def test_profile_ci_rejects_bad_level(L):
     assert L.plk_profile_ci_device(None, None, 5, 0.95, None, None) == nv.PLK_E_INVALID
     assert L.plk_profile_max_device(None, 3, 0, None, None) == nv.PLK_E_INVALID
+
+
+def test_post_processing_rejects_bad_arguments_without_touching_the_gpu(L):
+    a = nv.StatsArgs(n=10, p=2, M=1, K=4)   # NULL input pointers
+    assert L.plk_profile_beta_device(C.byref(a), 0, None, 3, None, None) == nv.PLK_E_INVALID
+    assert L.plk_profile_sigma_device(None, None, 3, None, None) == nv.PLK_E_INVALID
+    a = nv.StatsArgs(n=10, p=17, M=1, K=4)
+    assert L.plk_profile_sigma_device(C.byref(a), None, 3, None, None) == nv.PLK_E_INVALID
+    assert b"bad sizes" in L.plk_last_error()
+    assert L.plk_profile_lambda_device(None, 5, 0, None, None) == nv.PLK_E_INVALID
+    assert L.plk_profile_hull_device(None, 0, None, 5, None, 0, None, None, None) == nv.PLK_E_INVALID
+    assert L.plk_internal_params_device(None, 3, 0, None, None) == nv.PLK_E_INVALID
+    # nothing to do is not an error and launches nothing
+    assert L.plk_internal_params_device(None, 0, 0, None, None) == nv.PLK_OK
