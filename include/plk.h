@@ -76,7 +76,7 @@ typedef enum {
 typedef struct {
     int32_t precision;  /* plk_precision */
     int32_t reml;       /* 0: ML profile (eq. profile); 1: REML profile (eq. remlpro) */
-    int32_t batch;      /* omega points per device batch; 0 = library default */
+    int32_t batch;      /* omega points per device batch, <= 65535; 0 = library default */
     int32_t flags;      /* PLK_FLAG_* bits */
 } plk_options;
 
@@ -135,6 +135,27 @@ size_t plk_eval_workspace_bytes(int64_t n, int32_t p, int32_t M, int32_t batch,
  * (launch failure). */
 plk_status plk_eval_device(const plk_eval_args *args, const plk_options *opts, void *workspace,
                            size_t workspace_bytes, void *stream);
+
+/* Covariance matrices V(omega_k) = R(omega_k) + nu_k^2 I of eq. (matern)
+ * (Section 2; the first item of Step 3 in Section 3.3), as the evaluation
+ * builds them, written out densely.
+ *   coords    device, n x 2 site coordinates (n >= 2)
+ *   params    device, K x 5 parameter points (layout above), 1 <= K <= 65535
+ *   mode      0: FP64 entries (the PLK_FP64 path's build);
+ *             1: double-float entries evaluated in FP32 pair arithmetic (the
+ *                first, 5-slice pass of the PLK_MIXED path);
+ *             2: double-float entries evaluated in FP64 (the 7-slice tier of
+ *                the PLK_MIXED path); modes 1 and 2 return hi + lo as doubles
+ *   V         device, K x n x n row-major, both triangles (caller-owned); rows
+ *             of a point whose parameters are invalid hold the build's fill
+ *   workspace device, >= plk_eval_workspace_bytes(n, 1, 1, K, PLK_FP64) bytes,
+ *             256-byte aligned (caller-owned scratch)
+ * Allocates nothing; asynchronous on `stream`.  Errors: PLK_E_INVALID (sizes,
+ * NULL pointers, mode, alignment), PLK_E_NOMEM (workspace too small),
+ * PLK_E_CUDA (launch failure). */
+plk_status plk_build_covariance_device(const double *coords, int64_t n, const double *params, int64_t K,
+                                       int32_t mode, double *V, void *workspace, size_t workspace_bytes,
+                                       void *stream);
 
 /* Evaluation without any device allocation (the paper has no counterpart).
  *

@@ -80,7 +80,7 @@ bool sizes_ok(int64_t n, int32_t p, int32_t M) {
 }
 
 bool make_layout(int64_t n, int32_t p, int32_t M, int32_t batch, Layout &L, int precision = PLK_FP64) {
-    if (!sizes_ok(n, p, M) || batch < 1) return false;
+    if (!sizes_ok(n, p, M) || batch < 1 || batch > 65535) return false;   // batch is a grid dimension
     if (precision != PLK_FP64 && precision != PLK_MIXED) return false;
     L.n = n;
     L.p = p;
@@ -315,7 +315,7 @@ static cudaError_t mixed_first_pass(const BatchArgs &b, const MixedArgs &x, bool
         part(p, bp, xp);
         cudaStream_t fs = p == 0 ? st.hi : st.lo;
         if (p == 1) e = cudaStreamWaitEvent(st.lo, ev[1], 0);
-        if (e == cudaSuccess) e = launch_front(bp, fs, true);
+        if (e == cudaSuccess) e = launch_front(bp, fs, FRONT_DF_FAST);
         if (e == cudaSuccess) e = cudaEventRecord(ev[1 + p], fs);
     }
     for (int p = 0; p < nparts && e == cudaSuccess; ++p) {   // factorisations, in order, on hi
@@ -472,7 +472,8 @@ extern "C" plk_status plk_eval_device(const plk_eval_args *args, const plk_optio
     if (prec != PLK_FP64 && prec != PLK_MIXED) return fail(PLK_E_INVALID, "unknown precision %d", prec);
     int batch = (opts && opts->batch > 0) ? opts->batch : default_batch(args->n, args->K);
     Layout L;
-    make_layout(args->n, args->p, args->M, batch, L, prec);
+    if (!make_layout(args->n, args->p, args->M, batch, L, prec))
+        return fail(PLK_E_INVALID, "batch %d outside [1, 65535]", batch);
     if (!workspace || workspace_bytes < L.total)
         return fail(PLK_E_NOMEM, "workspace of %zu bytes < %zu needed for batch %d", workspace_bytes,
                     L.total, batch);
@@ -481,6 +482,45 @@ extern "C" plk_status plk_eval_device(const plk_eval_args *args, const plk_optio
     if (args->K == 0) return PLK_OK;
     return run_eval(args, opts ? opts->reml : 0, opts ? opts->flags : 0, L, workspace,
                     static_cast<cudaStream_t>(stream));
+}
+
+extern "C" plk_status plk_build_covariance_device(const double *coords, int64_t n, const double *params, int64_t K,
+                                                  int32_t mode, double *V, void *workspace, size_t workspace_bytes,
+                                                  void *stream) {
+    if (!coords || !params || !V) return fail(PLK_E_INVALID, "NULL pointer");
+    if (n < 2 || K < 1 || K > 65535) return fail(PLK_E_INVALID, "need n >= 2 and 1 <= K <= 65535");
+    if (mode < 0 || mode > 2) return fail(PLK_E_INVALID, "unknown build mode %d", mode);
+    Layout L;
+    if (!make_layout(n, 1, 1, (int32_t)K, L, PLK_FP64)) return fail(PLK_E_INVALID, "invalid sizes");
+    if (!workspace || workspace_bytes < L.total)
+        return fail(PLK_E_NOMEM, "workspace of %zu bytes < %zu needed", workspace_bytes, L.total);
+    if (reinterpret_cast<uintptr_t>(workspace) % ALIGN != 0)
+        return fail(PLK_E_INVALID, "workspace must be 256-byte aligned");
+    BatchArgs b{};
+    b.count = (int)K;
+    b.k0 = 0;
+    b.n = n;
+    b.n_pad = L.n_pad;
+    b.nb = L.nb;
+    b.q = 0;   // no right-hand-side rows: the build reads no B^T
+    b.p = 1;
+    b.M = 1;
+    b.tpo = L.tpo;
+    b.params = params;
+    b.coords = coords;
+    b.Bt = at<double>(workspace, L.off_Bt);
+    b.sumlogy = at<double>(workspace, L.off_sumlog);
+    b.oconst = at<double>(workspace, L.off_oc);
+    b.coordT = at<double>(workspace, L.off_coordT);
+    b.tab = at<double>(workspace, L.off_tab);
+    b.tiles = at<double>(workspace, L.off_tiles);
+    b.inv = at<double>(workspace, L.off_inv);
+    b.ldv = at<double>(workspace, L.off_ldv);
+    b.pstatus = at<int>(workspace, L.off_pst);
+    const FrontMode fm = mode == 0 ? FRONT_FP64 : (mode == 1 ? FRONT_DF_FAST : FRONT_DF);
+    cudaError_t e = launch_covariance(b, fm, at<double>(workspace, L.off_sumlog) + 1, V,
+                                      static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? PLK_OK : cuda_fail(e, "covariance build");
 }
 
 // ---------------------------------------------------------------------------
@@ -946,7 +986,7 @@ extern "C" plk_status plk_submit_profile(plk_ctx *c, plk_dataset ds, const doubl
     j->opts = o;
     j->params.assign(param_grid, param_grid + 5 * K);
     j->lambdas.assign(lambda_grid, lambda_grid + M);
-    j->batch = o.batch > 0 ? o.batch : default_batch(d->n, K);
+    j->batch = o.batch > 0 ? std::min(o.batch, 65535) : default_batch(d->n, K);
     j->t_submit = c->now();
     d->active_jobs++;
     *out = j->id;

@@ -42,6 +42,13 @@ constexpr int TAB_S = 1 << TAB_SB;
 constexpr int TAB_NC = 10;              // coefficients per sub-interval
 constexpr int TAB_NBUCKET = (TAB_EHI - TAB_ELO) * TAB_S;
 constexpr int TAB_SIZE = TAB_NBUCKET * TAB_NC;
+// Float layout of one sub-interval (first pass of the mixed path): the TAB_DF
+// leading coefficients as (hi, lo) pairs, the rest as single floats, padded to
+// TAB_F32 floats (64 bytes: two 32-byte vector loads).
+constexpr int TAB_DF = 4;
+constexpr int TAB_F32 = 16;
+static_assert(2 * TAB_DF + (TAB_NC - TAB_DF) <= TAB_F32, "float table layout");
+static_assert(TAB_NBUCKET * TAB_F32 * 4 <= TAB_SIZE * 8, "float table fits the per-point region");
 
 // Fixed trapezoid grid used by the table builder for u <= TAB_USPLIT.
 constexpr double QH = 0.125;

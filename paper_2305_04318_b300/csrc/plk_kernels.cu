@@ -6,6 +6,8 @@
 //   k_omega_prep    per-omega constants, rotated/scaled coordinates  (eq. matern)
 //   k_matern_table  per-omega piecewise polynomial of rho(w), w = 8 kappa d^2
 //   k_build         bordered matrix tiles: V = R + nu^2 I and B^T     (Step 3 item 1)
+//   k_build_f32     the same tiles as double-float planes, evaluated in FP32
+//                   pair arithmetic (first pass of the mixed-precision path)
 //   for each tile column J:
 //     k_potrf       diagonal tile L_JJ, its inverse, log|V| partial   (item 2)
 //     k_gemm_nt<0>  panel L_IJ = A_IJ L_JJ^-T (also W^T rows)         (items 2-3)
@@ -76,7 +78,7 @@ __global__ void __launch_bounds__(256) k_omega_prep(const double *__restrict__ p
                                                     const double *__restrict__ coords,
                                                     const double *__restrict__ sumlogy, double *__restrict__ oconst,
                                                     double *__restrict__ coordT, double *__restrict__ logdet,
-                                                    int *__restrict__ pstatus) {
+                                                    int *__restrict__ pstatus, int f32coords) {
     const int w = blockIdx.x;
     const double *om = params + 5 * (int64_t)w;
     const double phix = om[0], kap = om[1], nug = om[2], ratio = om[3], ang = om[4];
@@ -101,6 +103,8 @@ __global__ void __launch_bounds__(256) k_omega_prep(const double *__restrict__ p
     }
     double *a = coordT + (int64_t)w * 2 * n_pad;
     double *b = a + n_pad;
+    // f32coords: the same region as four float arrays [a_hi | a_lo | b_hi | b_lo]
+    float *af = reinterpret_cast<float *>(a);
     // bounding box of the transformed sites: w = |a_i - a_j|^2 + |b_i - b_j|^2 is
     // at most its squared diagonal, and at least min(ia, ib)^2 times the
     // smallest squared site distance (the rotation keeps lengths)
@@ -116,8 +120,16 @@ __global__ void __launch_bounds__(256) k_omega_prep(const double *__restrict__ p
             blo = fmin(blo, bi);
             bhi = fmax(bhi, bi);
         }
-        a[i] = ai;
-        b[i] = bi;
+        if (f32coords) {
+            const float ah = __double2float_rn(ai), bh = __double2float_rn(bi);
+            af[i] = ah;
+            af[n_pad + i] = __double2float_rn(ai - (double)ah);
+            af[2 * n_pad + i] = bh;
+            af[3 * n_pad + i] = __double2float_rn(bi - (double)bh);
+        } else {
+            a[i] = ai;
+            b[i] = bi;
+        }
     }
     __shared__ double red[4][8];
     for (int o = 16; o > 0; o >>= 1) {
@@ -220,9 +232,13 @@ __device__ double rho_integral(double u, double kap, double logc) {
 }
 
 // Table builder: one block of 320 threads = 32 sub-intervals x TAB_NC Chebyshev nodes.
+// F32TAB writes each sub-interval's coefficients as TAB_F32 floats instead of
+// TAB_NC doubles: c_0..c_3 as double-float pairs, c_4..c_9 rounded to FP32
+// (the layout k_build_f32 reads; it fits in the same per-point region).
 // For u <= TAB_USPLIT the trapezoid nodes are the fixed grid t_k = k QH, whose
 // cosh(t_k) - 1 and log cosh(kappa t_k) are staged in shared memory, so one exp
 // per node remains.
+template <bool F32TAB>
 __global__ void __launch_bounds__(320) k_matern_table(const double *__restrict__ oconst,
                                                       double *__restrict__ tab) {
     __shared__ double E1[QNODES];   // cosh(t_k) - 1 = 2 sinh^2(t_k / 2)
@@ -296,8 +312,19 @@ __global__ void __launch_bounds__(320) k_matern_table(const double *__restrict__
                 Tc[m] = Tn[m];
             }
         }
-        double *dst = tab + (int64_t)w * TAB_SIZE + (int64_t)bucket * TAB_NC;
-        for (int m = 0; m < TAB_NC; ++m) dst[m] = c[m];
+        if (F32TAB) {
+            float *dst = reinterpret_cast<float *>(tab + (int64_t)w * TAB_SIZE) + (int64_t)bucket * TAB_F32;
+            for (int m = 0; m < TAB_DF; ++m) {
+                const float h = __double2float_rn(c[m]);
+                dst[2 * m] = h;
+                dst[2 * m + 1] = __double2float_rn(c[m] - (double)h);
+            }
+            for (int m = TAB_DF; m < TAB_NC; ++m) dst[TAB_DF + m] = __double2float_rn(c[m]);
+            for (int m = TAB_DF + TAB_NC; m < TAB_F32; ++m) dst[m] = 0.0f;
+        } else {
+            double *dst = tab + (int64_t)w * TAB_SIZE + (int64_t)bucket * TAB_NC;
+            for (int m = 0; m < TAB_NC; ++m) dst[m] = c[m];
+        }
     }
 }
 
@@ -404,6 +431,143 @@ __global__ void __launch_bounds__(256) k_build(int nb, int64_t n, int64_t n_pad,
             v = rho_table(tw, wv, kap, logc, elo, ehi);
         }
         put(r, v);
+    }
+}
+
+// Double-float build for the first (5-slice) pass of the mixed path: the same
+// tiles as k_build<true>, evaluated in FP32 pair arithmetic (FP32 issues at
+// ~68x the FP64 rate here).  Per entry:
+//   w = (a_i - a_j)^2 + (b_i - b_j)^2 from double-float coordinates (error-free
+//       differences and squares, a positive sum: relative error ~2^-44);
+//   sub-interval from the FP32 bits of w_hi, local variable t = t_hi + t_lo with
+//       t_hi exact (fma of the mantissa) and t_lo = w_lo scaled by a power of 2;
+//   Horner: c_9..c_4 in FP32 on t_hi (these terms are below ~1e-6 of rho),
+//       c_3..c_0 in double-float on (t_hi, t_lo).
+// Against the FP64 evaluation of the same polynomial the entries differ by
+// ~1e-13 absolute, four orders below the 5-slice products' 2^-30 relative
+// error.  Pairs outside the table's octaves take the FP64 integral (rare).
+__device__ __forceinline__ void two_sum_f(float a, float b, float &s, float &e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+__device__ __forceinline__ void fast_two_sum_f(float a, float b, float &s, float &e) {   // |a| >= |b| or a = 0
+    s = __fadd_rn(a, b);
+    e = __fsub_rn(b, __fsub_rn(s, a));
+}
+// (ph, pl) <- (ph, pl) * (th, tl) + (ch, cl), dropping pl * tl
+__device__ __forceinline__ void df_horner_step(float &ph, float &pl, float th, float tl, float ch, float cl) {
+    const float x = __fmul_rn(ph, th);
+    float ex = __fmaf_rn(ph, th, -x);
+    ex = __fmaf_rn(ph, tl, ex);
+    ex = __fmaf_rn(pl, th, ex);
+    float s, es;
+    two_sum_f(x, ch, s, es);
+    ph = s;
+    pl = __fadd_rn(__fadd_rn(es, ex), cl);
+}
+__device__ __forceinline__ void ldg_v8(const float *p, float (&v)[8]) {   // 32-byte aligned
+    asm("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]), "=f"(v[7])
+                 : "l"(p));
+}
+
+__global__ void __launch_bounds__(256) k_build_f32(int nb, int64_t n, int64_t n_pad, int q, int64_t tpo,
+                                                   double *__restrict__ tiles,
+                                                   const double *__restrict__ oconst,
+                                                   const double *__restrict__ coordT,
+                                                   const double *__restrict__ tab,
+                                                   const double *__restrict__ Bt) {
+    const int w = blockIdx.y;
+    const int t = blockIdx.x;
+    int I = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
+    while ((I + 1) * (I + 2) / 2 <= t) ++I;
+    while (I * (I + 1) / 2 > t) --I;
+    const int J = t - I * (I + 1) / 2;
+    double *T = tiles + ((int64_t)w * tpo + t) * NT;
+    float *TH = reinterpret_cast<float *>(T);
+    float *TL = TH + NT;
+    const int c = threadIdx.x & (TB - 1);
+    const int r0 = threadIdx.x >> 7;
+    const int64_t j = (int64_t)J * TB + c;
+    if (I == nb) {   // right-hand-side rows: B^T, zero beyond q rows / n columns
+        for (int r = r0; r < TB; r += 2) {
+            double v = 0.0;
+            if (J < nb && r < q && j < n) v = Bt[(int64_t)r * n_pad + j];
+            float h, l;
+            split_df_bits(v, h, l);
+            TH[r * TB + c] = h;
+            TL[r * TB + c] = l;
+        }
+        return;
+    }
+    const double *oc = oconst + OC_N * (int64_t)w;
+    const double nug = oc[OC_NUG], kap = oc[OC_KAPPA], logc = oc[OC_LOGC];
+    const int elo = (int)oc[OC_ELO], ehi = (int)oc[OC_EHI];
+    float dgh, dgl;   // 1 + nu^2
+    split_df_bits(1.0 + nug, dgh, dgl);
+    const float *cf = reinterpret_cast<const float *>(coordT + (int64_t)w * 2 * n_pad);
+    const float *tf = reinterpret_cast<const float *>(tab + (int64_t)w * TAB_SIZE);
+    const float ajh = cf[j], ajl = cf[n_pad + j], bjh = cf[2 * n_pad + j], bjl = cf[3 * n_pad + j];
+    for (int r = r0; r < TB; r += 2) {
+        const int64_t i = (int64_t)I * TB + r;
+        float vh, vl = 0.0f;
+        if (i >= n || j >= n) {
+            vh = (i == j) ? 1.0f : 0.0f;           // identity padding
+        } else if (i == j) {
+            vh = dgh;
+            vl = dgl;
+        } else if (i < j) {
+            vh = 0.0f;                             // upper part of a diagonal tile, unused
+        } else {
+            float s, e, dah, dal, dbh, dbl;
+            two_sum_f(cf[i], -ajh, s, e);
+            e = __fadd_rn(e, __fsub_rn(cf[n_pad + i], ajl));
+            two_sum_f(s, e, dah, dal);
+            two_sum_f(cf[2 * n_pad + i], -bjh, s, e);
+            e = __fadd_rn(e, __fsub_rn(cf[3 * n_pad + i], bjl));
+            two_sum_f(s, e, dbh, dbl);
+            const float p1 = __fmul_rn(dah, dah), p2 = __fmul_rn(dbh, dbh);
+            float e1 = __fmaf_rn(dah, dah, -p1), e2 = __fmaf_rn(dbh, dbh, -p2);
+            e1 = __fmaf_rn(dah + dah, dal, e1);
+            e2 = __fmaf_rn(dbh + dbh, dbl, e2);
+            two_sum_f(p1, p2, s, e);
+            float wh, wl;
+            fast_two_sum_f(s, __fadd_rn(e, __fadd_rn(e1, e2)), wh, wl);
+            const unsigned bits = __float_as_uint(wh);
+            const int ew = (int)(bits >> 23) - 127;   // w >= 0
+            if (wh == 0.0f) {
+                vh = 1.0f;                         // coincident sites
+            } else if (ew >= TAB_EHI) {
+                vh = 0.0f;
+            } else if (ew < elo || ew >= ehi) {    // outside the octaves built for this point
+                split_df_bits(rho_integral(sqrt((double)wh + (double)wl), kap, logc), vh, vl);
+            } else {
+                const int jb = (int)(bits >> (23 - TAB_SB)) & (TAB_S - 1);
+                const float m = __uint_as_float((bits & 0x007fffffu) | 0x3f800000u);   // [1, 2)
+                const float th = __fmaf_rn(m, 2.0f * TAB_S, -(float)(2 * TAB_S + 2 * jb + 1));   // exact
+                const float tl = __fmul_rn(wl, __uint_as_float((unsigned)(127 + TAB_SB + 1 - ew) << 23));
+                const float *cb = tf + ((ew - TAB_ELO) * TAB_S + jb) * TAB_F32;
+                float q0[8], q1[8];
+                ldg_v8(cb, q0);
+                ldg_v8(cb + 8, q1);
+                // c_9 .. c_4 in FP32
+                float ph = __fmaf_rn(q1[5], th, q1[4]);
+                ph = __fmaf_rn(ph, th, q1[3]);
+                ph = __fmaf_rn(ph, th, q1[2]);
+                ph = __fmaf_rn(ph, th, q1[1]);
+                ph = __fmaf_rn(ph, th, q1[0]);
+                float pl = 0.0f;
+                // c_3 .. c_0 in double-float
+                df_horner_step(ph, pl, th, tl, q0[6], q0[7]);
+                df_horner_step(ph, pl, th, tl, q0[4], q0[5]);
+                df_horner_step(ph, pl, th, tl, q0[2], q0[3]);
+                df_horner_step(ph, pl, th, tl, q0[0], q0[1]);
+                fast_two_sum_f(ph, pl, vh, vl);
+            }
+        }
+        TH[r * TB + c] = vh;
+        TL[r * TB + c] = vl;
     }
 }
 
@@ -749,18 +913,61 @@ cudaError_t launch_boxcox(int64_t n, int64_t n_pad, int p, int M, const double *
     return cudaGetLastError();
 }
 
-cudaError_t launch_front(const BatchArgs &b, cudaStream_t s, bool double_float) {
+cudaError_t launch_front(const BatchArgs &b, cudaStream_t s, FrontMode mode) {
     const int cnt = b.count;
     KernelTimer *timer = b.timer;
+    const int f32 = mode == FRONT_DF_FAST ? 1 : 0;
     TIMED(KC_PREP, (k_omega_prep<<<cnt, 256, 0, s>>>(b.params, b.n, b.n_pad, b.coords, b.sumlogy, b.oconst,
-                                                      b.coordT, b.ldv, b.pstatus)));
-    TIMED(KC_TABLE, (k_matern_table<<<dim3((TAB_NBUCKET + 31) / 32, cnt), 320, 0, s>>>(b.oconst, b.tab)));
-    if (double_float)
-        TIMED(KC_BUILD, (k_build<true><<<dim3((unsigned)b.tpo, cnt), 256, 0, s>>>(
-                            b.nb, b.n, b.n_pad, b.q, b.tpo, b.tiles, b.oconst, b.coordT, b.tab, b.Bt)));
-    else
-        TIMED(KC_BUILD, (k_build<false><<<dim3((unsigned)b.tpo, cnt), 256, 0, s>>>(
-                            b.nb, b.n, b.n_pad, b.q, b.tpo, b.tiles, b.oconst, b.coordT, b.tab, b.Bt)));
+                                                      b.coordT, b.ldv, b.pstatus, f32)));
+    const dim3 tg((TAB_NBUCKET + 31) / 32, cnt), bg((unsigned)b.tpo, cnt);
+    if (f32) {
+        TIMED(KC_TABLE, (k_matern_table<true><<<tg, 320, 0, s>>>(b.oconst, b.tab)));
+        TIMED(KC_BUILD, (k_build_f32<<<bg, 256, 0, s>>>(b.nb, b.n, b.n_pad, b.q, b.tpo, b.tiles, b.oconst,
+                                                         b.coordT, b.tab, b.Bt)));
+    } else {
+        TIMED(KC_TABLE, (k_matern_table<false><<<tg, 320, 0, s>>>(b.oconst, b.tab)));
+        if (mode == FRONT_DF)
+            TIMED(KC_BUILD, (k_build<true><<<bg, 256, 0, s>>>(b.nb, b.n, b.n_pad, b.q, b.tpo, b.tiles, b.oconst,
+                                                               b.coordT, b.tab, b.Bt)));
+        else
+            TIMED(KC_BUILD, (k_build<false><<<bg, 256, 0, s>>>(b.nb, b.n, b.n_pad, b.q, b.tpo, b.tiles, b.oconst,
+                                                                b.coordT, b.tab, b.Bt)));
+    }
+    return cudaGetLastError();
+}
+
+// Dense row-major V (both triangles) of every point of a batch from its data
+// tiles: one block per lower tile (I, J), I < nb; df = tiles hold hi/lo planes.
+__global__ void __launch_bounds__(256) k_tiles_to_dense(int nb, int64_t n, int64_t tpo, const double *__restrict__ tiles,
+                                                        int df, double *__restrict__ V) {
+    const int w = blockIdx.y;
+    const int t = blockIdx.x;
+    int I = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
+    while ((I + 1) * (I + 2) / 2 <= t) ++I;
+    while (I * (I + 1) / 2 > t) --I;
+    const int J = t - I * (I + 1) / 2;
+    const double *T = tiles + ((int64_t)w * tpo + t) * NT;
+    const float *TH = reinterpret_cast<const float *>(T), *TL = TH + NT;
+    double *Vw = V + (int64_t)w * n * n;
+    for (int e = threadIdx.x; e < NT; e += blockDim.x) {
+        const int r = e >> 7, c = e & (TB - 1);
+        const int64_t i = (int64_t)I * TB + r, j = (int64_t)J * TB + c;
+        if (i >= n || j >= n || j > i) continue;
+        const double v = df ? (double)TH[e] + (double)TL[e] : T[e];
+        Vw[i * n + j] = v;
+        Vw[j * n + i] = v;
+    }
+}
+
+cudaError_t launch_covariance(const BatchArgs &b, FrontMode mode, double *min_dist2, double *V, cudaStream_t s) {
+    const int64_t nt = (b.n + 127) / 128;
+    cudaError_t e = cudaMemsetAsync(min_dist2, 0x7f, sizeof(double), s);   // 0x7f7f.. ~ 1.4e306
+    if (e != cudaSuccess) return e;
+    k_min_dist2<<<(unsigned)(nt * (nt + 1) / 2), 256, 0, s>>>(b.n, b.coords, min_dist2);
+    if ((e = launch_front(b, s, mode)) != cudaSuccess) return e;
+    const unsigned data_tiles = (unsigned)((int64_t)b.nb * (b.nb + 1) / 2);
+    k_tiles_to_dense<<<dim3(data_tiles, b.count), 256, 0, s>>>(b.nb, b.n, b.tpo, b.tiles, mode == FRONT_FP64 ? 0 : 1,
+                                                                V);
     return cudaGetLastError();
 }
 
@@ -781,7 +988,7 @@ cudaError_t launch_fp64_batch(const BatchArgs &b, cudaStream_t s) {
     if (e != cudaSuccess) return e;
     const int cnt = b.count;
     KernelTimer *timer = b.timer;
-    if ((e = launch_front(b, s, false)) != cudaSuccess) return e;
+    if ((e = launch_front(b, s, FRONT_FP64)) != cudaSuccess) return e;
     for (int J = 0; J < b.nb; ++J) {
         TIMED(KC_POTRF, (k_potrf<<<cnt, 256, 2 * PK * sizeof(double), s>>>(J, b.tpo, b.tiles, b.inv,
                                                                             b.ldv, b.pstatus)));

@@ -54,9 +54,15 @@ cudaError_t launch_boxcox(int64_t n, int64_t n_pad, int p, int M, const double *
                           KernelTimer *timer = nullptr);
 cudaError_t launch_fp64_batch(const BatchArgs &b, cudaStream_t s);
 // pieces of the batch pipeline shared with the mixed path
-// prep, table, build (FP64 tiles, or double-float planes for the mixed path)
-cudaError_t launch_front(const BatchArgs &b, cudaStream_t s, bool double_float);
-cudaError_t launch_finalize(const BatchArgs &b, cudaStream_t s);   // closed form from FP64 tile (nb, nb)
+// prep, table, build: FP64 tiles; double-float planes evaluated in FP64 (the
+// mixed path's 7-slice tier); double-float planes evaluated in FP32 pair
+// arithmetic (the mixed path's 5-slice pass)
+enum FrontMode { FRONT_FP64 = 0, FRONT_DF = 1, FRONT_DF_FAST = 2 };
+cudaError_t launch_front(const BatchArgs &b, cudaStream_t s, FrontMode mode);
+cudaError_t launch_finalize(const BatchArgs &b, cudaStream_t s);
+// smallest squared site distance into *min_dist2, the front in `mode`, then
+// the dense n x n matrices V of the batch into V (count x n x n)
+cudaError_t launch_covariance(const BatchArgs &b, FrontMode mode, double *min_dist2, double *V, cudaStream_t s);   // closed form from FP64 tile (nb, nb)
 // Buffers of the mixed-precision path (per batch slot w unless noted).
 struct MixedArgs {
     uint8_t *wimg;       // count x img: slices of L_JJ^-1
@@ -70,7 +76,7 @@ struct MixedArgs {
 size_t mixed_img_bytes(int S);
 size_t mixed_slot_bytes();   // panel slot of one tile row
 cudaError_t launch_mixed_batch(const BatchArgs &b, const MixedArgs &x, int S, cudaStream_t s);
-// the batch after launch_front(b, s, true): factorisation, closed form, error bound
+// the batch after launch_front(b, s, FRONT_DF or FRONT_DF_FAST): factorisation, closed form, error bound
 cudaError_t launch_mixed_back(const BatchArgs &b, const MixedArgs &x, int S, cudaStream_t s);
 cudaError_t launch_gather_params(int count, const int *idx, const double *params, double *out, cudaStream_t s);
 cudaError_t launch_scatter_value(int count, const int *idx, double v, double *out, cudaStream_t s);

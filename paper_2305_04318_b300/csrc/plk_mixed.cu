@@ -1344,7 +1344,9 @@ static cudaError_t launch_mixed_steps(const BatchArgs &b, const MixedArgs &x, cu
 }
 
 cudaError_t launch_mixed_batch(const BatchArgs &b, const MixedArgs &x, int S, cudaStream_t s) {
-    cudaError_t e = launch_front(b, s, true);   // builds double-float tiles directly
+    // double-float tiles: FP32 pair arithmetic for the 5-slice pass, FP64 for
+    // the 7-slice tier (whose 2^-46 products need entries good to ~1e-16)
+    cudaError_t e = launch_front(b, s, S == 5 ? FRONT_DF_FAST : FRONT_DF);
     if (e != cudaSuccess) return e;
     return launch_mixed_back(b, x, S, s);
 }

@@ -68,6 +68,7 @@ def lib():
         "plk_eval_workspace_bytes": (sz, [i64, i32, i32, i32, i32]),
         "plk_eval_device": (C.c_int, [C.POINTER(EvalArgs), C.POINTER(Options), vp, sz, vp]),
         "plk_eval_device_static": (C.c_int, [C.POINTER(EvalArgs), i32, vp]),
+        "plk_build_covariance_device": (C.c_int, [vp, i64, vp, i64, i32, vp, vp, sz, vp]),
         "plk_create": (C.c_int, [C.POINTER(vp), C.c_int, vp, sz, C.POINTER(vp), C.c_int]),
         "plk_create_dataset": (C.c_int, [vp, vp, vp, vp, i64, i32, C.POINTER(i64)]),
         "plk_submit_profile": (C.c_int, [vp, i64, vp, i64, vp, i32, C.POINTER(Options), C.POINTER(i64)]),
@@ -180,6 +181,28 @@ def eval_device(coords, y, X, lambdas, params, precision=FP64, reml=False, batch
     _check(lib().plk_eval_device(C.byref(a), C.byref(o), _ptr(workspace), workspace.numel(),
                                  _stream_handle(stream)))
     return outputs
+
+
+BUILD_FP64, BUILD_DF_FAST, BUILD_DF = 0, 1, 2
+
+
+def build_covariance_device(coords, params, mode=BUILD_FP64, workspace=None, stream=None, out=None):
+    """Dense V(omega_k) = R + nu^2 I for every row of `params` (CUDA float64),
+    as the evaluation builds it: mode BUILD_FP64 (FP64 path), BUILD_DF_FAST
+    (mixed path, first pass), BUILD_DF (mixed path, 7-slice tier).  Returns a
+    [K, n, n] CUDA float64 tensor."""
+    import torch
+    n = coords.shape[0]
+    K = params.shape[0]
+    for t in (coords, params):
+        assert t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()
+    if out is None:
+        out = torch.empty((K, n, n), dtype=torch.float64, device=coords.device)
+    if workspace is None:
+        workspace = torch.empty((workspace_bytes(n, 1, 1, K, FP64),), dtype=torch.uint8, device=coords.device)
+    _check(lib().plk_build_covariance_device(_ptr(coords), n, _ptr(params), K, int(mode), _ptr(out),
+                                             _ptr(workspace), workspace.numel(), _stream_handle(stream)))
+    return out
 
 
 STATIC_SCRATCH_BYTES = 64 << 20
