@@ -72,7 +72,8 @@ def parse():
                          "stream of profile jobs over a pool of resident datasets")
     ap.add_argument("--datasets", type=int, default=0, help="uneven/serving: number of datasets (default 256 / 32)")
     ap.add_argument("--points", type=int, default=512, help="uneven: points per dataset")
-    ap.add_argument("--item-batch", type=int, default=64, help="uneven: points per scheduled batch")
+    ap.add_argument("--item-batch", type=int, default=0,
+                    help="uneven: points per scheduled batch (default 0: chosen by the autotuner per dataset size)")
     ap.add_argument("--jobs", type=int, default=40, help="serving: jobs per load level")
     ap.add_argument("--streams", type=int, default=4, help="uneven/serving: scheduler streams")
     return ap.parse_args()
@@ -226,23 +227,36 @@ def run_reference(args):
 def run_uneven(args):
     """Config 4: 256 datasets with n log-uniform in [200, 3000] and p in {2,3,5},
     512 points each, all submitted at once to one context; the scheduler
-    interleaves their batches over the stream pool (continuous batching)."""
+    interleaves their batches over the stream pool (continuous batching).  The
+    points per batch come from the library's autotuner (plk_autotune), run once
+    per half-octave of n before the timed region, unless --item-batch is set."""
     import torch
     from paper_2305_04318_b300 import native as nv, synth
     D = args.datasets or 256
     w = synth.uneven(D=D, per=args.points)
     prec = nv.MIXED if args.precision in ("auto", "mixed") else nv.FP64
-    sizes = [nv.workspace_bytes(d.n, d.p, len(w.lambdas), args.item_batch, prec) for d in w.datasets]
-    arena_bytes = int(args.streams * max(sizes) * 1.2 + (2 << 30))
+    M = len(w.lambdas)
+    free, _ = torch.cuda.mem_get_info()
+    arena_bytes = int(min(free - (8 << 30), 200e9))
     arena = torch.empty((arena_bytes,), dtype=torch.uint8, device="cuda")
+    tune = {}
     with nv.Context(arena_bytes, arena=arena, n_streams=args.streams) as ctx:
+        t_tune = time.perf_counter()
+        if args.item_batch <= 0:
+            buckets = sorted({int(round(2 * math.log2(d.n))) for d in w.datasets})
+            for b in buckets:
+                n_rep = int(round(2 ** (b / 2)))
+                bb, rate = ctx.autotune(n_rep, 3, M, prec)
+                tune[str(n_rep)] = {"batch": bb, "points_per_s": round(rate, 1)}
+        t_tune = time.perf_counter() - t_tune
         ids = [ctx.create_dataset(d.coords, d.y, d.X) for d in w.datasets]
         # warm-up: one small job
         j = ctx.submit(ids[0], w.params[0][:4], w.lambdas, precision=prec, batch=4)
         ctx.poll(j, w.datasets[0].p)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        jobs = [ctx.submit(ids[i], w.params[i], w.lambdas, precision=prec, batch=args.item_batch) for i in range(D)]
+        jobs = [ctx.submit(ids[i], w.params[i], w.lambdas, precision=prec, batch=max(0, args.item_batch))
+                for i in range(D)]
         res = [ctx.poll(jb, w.datasets[i].p) for i, jb in enumerate(jobs)]
         dt = time.perf_counter() - t0
         _, high = ctx.memory_stats()
@@ -255,7 +269,10 @@ def run_uneven(args):
             "config": {"workload": f"uneven: {D} datasets, n log-uniform in [200,3000] (median {int(np.median(ns))}), "
                                    f"p in {{2,3,5}}, {args.points} points each, 9 lambdas",
                        "precision": "mixed" if prec == nv.MIXED else "fp64", "streams": args.streams,
-                       "batch_per_item": args.item_batch, "arena_gb": arena_bytes / 1e9},
+                       "batch_per_item": args.item_batch if args.item_batch > 0 else "autotuned",
+                       "arena_gb": arena_bytes / 1e9},
+            "autotune": {"seconds": round(t_tune, 2), "by_n": tune,
+                         "what": "plk_autotune per half-octave of n, before the timed region"},
             "points": int(npts), "points_not_ok": int(((st & 15) != 0).sum()),
             "points_7slice": int(((st & 16) != 0).sum()), "points_fp64": int(((st & 32) != 0).sum()),
             "hbm_high_water_gb": high / 1e9, "e2e": {"value": npts / dt, "unit": UNIT,
@@ -530,6 +547,13 @@ def main():
         d = np.abs(gm["logL"][:m][okp] - gf["logL"][:m][okp])
         agree = {"points": int(m), "compared": int(okp.sum()), "max_abs_dlogL_vs_fp64": float(d.max()) if d.size else None,
                  "status_mismatch": int((((gm["status"][:m] & 15) != 0) != (gf["status"][:m] != 0)).sum())}
+        if d.size:
+            s2 = np.abs(gm["sigma2"][:m][okp] / gf["sigma2"][:m][okp] - 1.0)
+            bd = np.abs(gm["beta"][:m][okp] - gf["beta"][:m][okp]) / np.abs(gf["beta"][:m][okp]).max()
+            ld = np.abs(gm["logdet"][:m][okp] - gf["logdet"][:m][okp])
+            agree.update({"max_rel_dsigma2_vs_fp64": float(s2.max()), "max_dbeta_rel_to_max_beta_vs_fp64": float(bd.max()),
+                          "max_abs_dlogdet_vs_fp64": float(ld.max()),
+                          "what": "per-result errors of the mixed path against the FP64 path on the same points"})
 
     # ---- end to end through the C ABI with host buffers ----
     e2e = None

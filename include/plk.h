@@ -234,6 +234,29 @@ plk_status plk_memory_stats(plk_ctx *ctx, size_t *in_use, size_t *high_water);
 /* Wait for all jobs, free everything the context owns. */
 plk_status plk_destroy(plk_ctx *ctx);
 
+/* Autotuner of the batch schedule (the paper fixes its batch, NparamPerIter,
+ * by hand for its unnamed GPU; Section 4).  Times this context's scheduler on a
+ * synthetic dataset of n sites with p covariates and M lambdas: for each
+ * candidate batch size b (NULL / 0 candidates: 32, 64, 148, 296, 592), one
+ * job of 2 b x (number of streams) points from submit to host results; keeps the
+ * fastest b for n's half-octave bucket and precision.  Later jobs submitted
+ * with opts->batch == 0 on datasets whose n falls in that bucket or a
+ * neighbouring one use it.  Candidates whose batches do not fit in the free
+ * arena are skipped.  Blocking; runs the context's own kernels (its datasets
+ * and jobs stay valid).  The tile size is fixed at 128 by the tensor-core
+ * shapes; the batch is what is tuned.  Outputs (may be NULL): the chosen
+ * batch and its points per second.  Errors: PLK_E_INVALID, PLK_E_NOMEM (no
+ * candidate fits), PLK_E_CUDA. */
+plk_status plk_autotune(plk_ctx *ctx, int64_t n, int32_t p, int32_t M, int32_t precision,
+                        const int32_t *candidates, int32_t n_candidates, int32_t *best_batch,
+                        double *best_rate);
+
+/* Batch size the scheduler uses for a job of K points on a dataset of n sites
+ * in `precision` when opts->batch == 0; *tuned (may be NULL) = 1 if it comes
+ * from plk_autotune, 0 if it is the library default. */
+plk_status plk_scheduled_batch(plk_ctx *ctx, int64_t n, int32_t precision, int64_t K, int32_t *batch,
+                               int32_t *tuned);
+
 /* Message describing the last error of the calling thread ("" if none). */
 const char *plk_last_error(void);
 

@@ -22,6 +22,7 @@
 #include <map>
 #include <memory>
 #include <mutex>
+#include <random>
 #include <string>
 #include <thread>
 #include <vector>
@@ -681,6 +682,8 @@ struct plk_ctx {
     plk_job next_job = 1;
     bool stop = false;
     std::vector<std::thread> workers;   // one per stream
+    // autotuned points per scheduled batch: (half-octave bucket of n, precision) -> (batch, points/s)
+    std::map<std::pair<int, int>, std::pair<int, double>> tuned;
     std::chrono::steady_clock::time_point t0;
     double now() const {
         return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -885,6 +888,26 @@ void stream_worker(plk_ctx *c, int slot) {
 
 }  // namespace
 
+namespace {
+int n_bucket(int64_t n) { return (int)std::lround(2.0 * std::log2((double)std::max<int64_t>(n, 1))); }
+
+// Points per batch for a job of K points on a dataset of n sites: the tuned
+// value of the nearest tuned half-octave bucket (at most one bucket away),
+// else the library default.  Caller holds mu.
+int scheduled_batch(plk_ctx *c, int64_t n, int precision, int64_t K, int *tuned) {
+    const int b = n_bucket(n);
+    for (int d : {0, -1, 1}) {
+        auto it = c->tuned.find({b + d, precision});
+        if (it != c->tuned.end()) {
+            if (tuned) *tuned = 1;
+            return (int)std::max<int64_t>(1, std::min<int64_t>(it->second.first, std::max<int64_t>(K, 1)));
+        }
+    }
+    if (tuned) *tuned = 0;
+    return default_batch(n, K);
+}
+}  // namespace
+
 extern "C" plk_status plk_create(plk_ctx **out, int device, void *arena, size_t arena_bytes,
                                  void *const *streams, int n_streams) {
     if (!out) return fail(PLK_E_INVALID, "out is NULL");
@@ -986,7 +1009,7 @@ extern "C" plk_status plk_submit_profile(plk_ctx *c, plk_dataset ds, const doubl
     j->opts = o;
     j->params.assign(param_grid, param_grid + 5 * K);
     j->lambdas.assign(lambda_grid, lambda_grid + M);
-    j->batch = o.batch > 0 ? std::min(o.batch, 65535) : default_batch(d->n, K);
+    j->batch = o.batch > 0 ? std::min(o.batch, 65535) : scheduled_batch(c, d->n, o.precision, K, nullptr);
     j->t_submit = c->now();
     d->active_jobs++;
     *out = j->id;
@@ -1061,5 +1084,115 @@ extern "C" plk_status plk_destroy(plk_ctx *c) {
         for (auto s : c->streams) cudaStreamDestroy(s);
     if (c->own_arena) cudaFree(c->arena_base);
     delete c;
+    return PLK_OK;
+}
+
+// ---------------------------------------------------------------------------
+// autotuner
+// ---------------------------------------------------------------------------
+// Times the scheduler itself on a synthetic dataset of n sites: for each
+// candidate batch size b, one job of 2 b x (number of streams) points (two
+// batches per stream) from submit to results on the host, and keeps the b with
+// the most points per second for n's half-octave bucket.
+extern "C" plk_status plk_autotune(plk_ctx *c, int64_t n, int32_t p, int32_t M, int32_t precision,
+                                   const int32_t *candidates, int32_t n_candidates, int32_t *best_batch,
+                                   double *best_rate) {
+    if (!c) return fail(PLK_E_INVALID, "ctx is NULL");
+    if (!sizes_ok(n, p, M)) return fail(PLK_E_INVALID, "invalid sizes n=%lld p=%d M=%d", (long long)n, p, M);
+    if (precision != PLK_FP64 && precision != PLK_MIXED) return fail(PLK_E_INVALID, "unknown precision");
+    std::vector<int> cand;
+    if (candidates && n_candidates > 0) {
+        for (int i = 0; i < n_candidates; ++i)
+            if (candidates[i] >= 1 && candidates[i] <= 65535) cand.push_back(candidates[i]);
+    } else {
+        cand = {32, 64, 148, 296, 592};
+    }
+    std::sort(cand.begin(), cand.end());
+    cand.erase(std::unique(cand.begin(), cand.end()), cand.end());
+    if (cand.empty()) return fail(PLK_E_INVALID, "no valid candidate batch size");
+    const int ns = (int)c->streams.size();
+    // synthetic dataset: sites uniform on a square of side sqrt(n / 10), X = [1, N(0,1)...],
+    // y > 0; parameter points spread over the box phi_X in [0.5, 8], kappa in [0.1, 8]
+    // (log-uniform), nu^2 in [0, 0.5], ratio in [1, 4] (log-uniform), angle in [0, pi)
+    std::mt19937_64 rng(0x9e3779b97f4a7c15ull ^ (uint64_t)n);
+    std::uniform_real_distribution<double> U(0.0, 1.0);
+    std::normal_distribution<double> N01(0.0, 1.0);
+    const double side = std::sqrt((double)n / 10.0);
+    std::vector<double> coords(2 * n), y(n), X(n * p), lam(M);
+    for (int64_t i = 0; i < n; ++i) {
+        coords[2 * i] = side * U(rng);
+        coords[2 * i + 1] = side * U(rng);
+        X[i * p] = 1.0;
+        double eta = 1.0;
+        for (int k = 1; k < p; ++k) {
+            X[i * p + k] = N01(rng);
+            eta += 0.5 * X[i * p + k];
+        }
+        y[i] = std::exp(eta + 0.3 * std::sin(coords[2 * i]) + 0.3 * N01(rng));
+    }
+    for (int m = 0; m < M; ++m) lam[m] = M > 1 ? -0.5 + 2.0 * m / (M - 1) : 0.0;
+    const int64_t kmax = 2 * (int64_t)cand.back() * ns;
+    std::vector<double> P(5 * kmax);
+    for (int64_t k = 0; k < kmax; ++k) {
+        P[5 * k + 0] = 0.5 * std::pow(16.0, U(rng));
+        P[5 * k + 1] = 0.1 * std::pow(80.0, U(rng));
+        P[5 * k + 2] = 0.5 * U(rng);
+        P[5 * k + 3] = std::pow(4.0, U(rng));
+        P[5 * k + 4] = M_PI * U(rng);
+    }
+    plk_dataset ds = 0;
+    plk_status st = plk_create_dataset(c, coords.data(), y.data(), X.data(), n, p, &ds);
+    if (st != PLK_OK) return st;
+    auto run = [&](int b, int64_t K, double *secs) -> plk_status {
+        plk_options o{};
+        o.precision = precision;
+        o.batch = b;
+        plk_job job = 0;
+        const auto t0 = std::chrono::steady_clock::now();
+        plk_status r = plk_submit_profile(c, ds, P.data(), K, lam.data(), M, &o, &job);
+        if (r == PLK_OK) r = plk_poll(c, job, -1, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr);
+        *secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        return r;
+    };
+    double secs = 0.0;
+    st = run(cand.front(), std::min<int64_t>(kmax, cand.front()), &secs);   // warm-up (module load, streams)
+    int best = 0;
+    double rate = 0.0;
+    for (int b : cand) {
+        if (st != PLK_OK) break;
+        size_t free_bytes;
+        {
+            std::lock_guard<std::mutex> lk(c->mu);
+            free_bytes = c->arena.size() - c->arena.used();
+        }
+        const int64_t K = 2 * (int64_t)b * ns;
+        if (item_bytes(n, p, M, b, precision) * ns + job_io_bytes(K, M, p, n) > free_bytes) break;
+        st = run(b, K, &secs);
+        if (st == PLK_OK && secs > 0.0 && K / secs > rate) {
+            rate = K / secs;
+            best = b;
+        }
+    }
+    std::string err = st != PLK_OK ? std::string(plk_last_error()) : std::string();
+    plk_release_dataset(c, ds);
+    if (st != PLK_OK) return fail(st, "autotune: %s", err.c_str());
+    if (best == 0) return fail(PLK_E_NOMEM, "autotune: no candidate batch fits in the arena");
+    {
+        std::lock_guard<std::mutex> lk(c->mu);
+        c->tuned[{n_bucket(n), precision}] = {best, rate};
+    }
+    if (best_batch) *best_batch = best;
+    if (best_rate) *best_rate = rate;
+    return PLK_OK;
+}
+
+extern "C" plk_status plk_scheduled_batch(plk_ctx *c, int64_t n, int32_t precision, int64_t K, int32_t *batch,
+                                          int32_t *tuned) {
+    if (!c || !batch) return fail(PLK_E_INVALID, "NULL argument");
+    if (n < 1) return fail(PLK_E_INVALID, "n < 1");
+    std::lock_guard<std::mutex> lk(c->mu);
+    int t = 0;
+    *batch = scheduled_batch(c, n, precision, K, &t);
+    if (tuned) *tuned = t;
     return PLK_OK;
 }

@@ -76,6 +76,8 @@ def lib():
         "plk_release_dataset": (C.c_int, [vp, i64]),
         "plk_memory_stats": (C.c_int, [vp, C.POINTER(sz), C.POINTER(sz)]),
         "plk_destroy": (C.c_int, [vp]),
+        "plk_autotune": (C.c_int, [vp, i64, i32, i32, i32, vp, i32, C.POINTER(i32), C.POINTER(dbl)]),
+        "plk_scheduled_batch": (C.c_int, [vp, i64, i32, i64, C.POINTER(i32), C.POINTER(i32)]),
         "plk_last_error": (C.c_char_p, []),
         "plk_profile_max_device": (C.c_int, [vp, i64, i64, vp, vp]),
         "plk_profile_ci_device": (C.c_int, [vp, vp, i64, dbl, vp, vp]),
@@ -375,6 +377,23 @@ class Context:
 
     def release_dataset(self, ds):
         _check(lib().plk_release_dataset(self.h, ds))
+
+    def autotune(self, n, p, M, precision=FP64, candidates=None):
+        """Tune the points per scheduled batch for datasets of about n sites
+        (plk_autotune).  Returns (batch, points per second)."""
+        arr, k = None, 0
+        if candidates is not None:
+            k = len(candidates)
+            arr = (C.c_int32 * k)(*[int(x) for x in candidates])
+        b, r = C.c_int32(), C.c_double()
+        _check(lib().plk_autotune(self.h, int(n), int(p), int(M), int(precision), arr, k, C.byref(b), C.byref(r)))
+        return b.value, r.value
+
+    def scheduled_batch(self, n, precision=FP64, K=1 << 30):
+        """(batch, tuned) the scheduler uses for a job on n sites with opts.batch = 0."""
+        b, t = C.c_int32(), C.c_int32()
+        _check(lib().plk_scheduled_batch(self.h, int(n), int(precision), int(K), C.byref(b), C.byref(t)))
+        return b.value, bool(t.value)
 
     def memory_stats(self):
         a, b = C.c_size_t(), C.c_size_t()

@@ -75,3 +75,28 @@ def test_mixed_jobs_same_alone_and_in_the_mix():
             np.testing.assert_array_equal(alone[i][k], mix[i][k])
         ref = gpu_eval(dsets[i], grids[i], lams, precision=nv.MIXED, batch=8)
         np.testing.assert_array_equal(alone[i]["logL"], ref["logL"])
+
+
+@pytest.mark.parametrize("precision", [nv.FP64, nv.MIXED])
+def test_autotuned_batch_is_used_and_results_unchanged(precision):
+    """plk_autotune picks one of the candidate batch sizes for n's half-octave
+    bucket; jobs submitted with batch = 0 on a dataset in that bucket use it,
+    and their results equal those of an explicit batch size bit for bit (each
+    point's arithmetic depends only on its own data)."""
+    ds = synth.aniso_dataset(61, 300, math.sqrt(30.0), 3)
+    lams = synth.LAMBDA_GRID_9
+    P = synth.omega_from_unit(np.random.default_rng(61).uniform(size=(45, 5)))
+    arena = torch.empty(4 << 30, dtype=torch.uint8, device="cuda")
+    with nv.Context(arena.numel(), arena=arena, n_streams=2) as ctx:
+        assert ctx.scheduled_batch(300, precision)[1] is False
+        b, rate = ctx.autotune(300, 3, len(lams), precision, candidates=[4, 8, 16])
+        assert b in (4, 8, 16) and rate > 0
+        assert ctx.scheduled_batch(300, precision) == (b, True)
+        assert ctx.scheduled_batch(330, precision) == (b, True)      # same or neighbouring bucket
+        assert ctx.scheduled_batch(2000, precision)[1] is False      # far away: library default
+        d = ctx.create_dataset(ds.coords, ds.y, ds.X)
+        tuned = ctx.poll(ctx.submit(d, P, lams, precision=precision), ds.p)
+        explicit = ctx.poll(ctx.submit(d, P, lams, precision=precision, batch=7), ds.p)
+        for k in ("logL", "sigma2", "beta", "logdet", "status"):
+            np.testing.assert_array_equal(tuned[k], explicit[k], err_msg=k)
+        ctx.release_dataset(d)

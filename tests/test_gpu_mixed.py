@@ -108,6 +108,34 @@ def test_mixed_overlapped_parts_identical(K):
     assert (a["status"] & 15 == 0).sum() > 0.8 * K
 
 
+@pytest.mark.parametrize("which", [0, 2])
+def test_mixed_profile_ci_endpoints(which):
+    """Likelihood-CI endpoints (eq. likelihood) from a profile job in mixed
+    precision against the oracle's: within 1 % of the oracle's CI width (the
+    mixed mode's stated target); the FP64 path's within 1e-6 of it."""
+    import oracle
+    ds = synth.aniso_dataset(41 + which, 300, math.sqrt(30.0), 3)
+    G, sub = 12, 2
+    gvals, P = synth.profile_job_grid(which, G=G, sub=sub)
+    lams = synth.LAMBDA_GRID_9
+    o = oracle_eval(ds, P, lams)
+    oprof = oracle.profile_max(o["logL"].reshape(G, -1))
+    r = oracle.profile_ci(gvals, oprof, 0.95)
+    oci = np.array([r["lo"], r["hi"]])
+    width = oci[1] - oci[0]
+    assert width > 0
+    for prec, tol in ((nv.MIXED, 0.01 * width), (nv.FP64, 1e-6 * width)):
+        g = gpu_eval(ds, P, lams, precision=prec)
+        gl = g["logL"].reshape(G, -1)
+        from gpu_util import to_dev
+        prof = nv.profile_max_device(to_dev(gl))
+        ci = nv.profile_ci_device(to_dev(gvals), prof, 0.95).cpu().numpy()
+        d = np.abs(ci[:2] - oci)
+        print(json.dumps(dict(which=which, precision=int(prec), oracle_ci=oci.tolist(), gpu_ci=ci[:2].tolist(),
+                              max_abs_endpoint_err=float(d.max()), width=float(width))))
+        assert np.all(d <= tol), (prec, ci[:2], oci)
+
+
 @pytest.mark.slow
 def test_mixed4000_full_size_sampled():
     """The n=4000 workload at full size in the bench's launch configuration:
