@@ -76,6 +76,8 @@ def parse():
                     help="uneven: points per scheduled batch (default 0: chosen by the autotuner per dataset size)")
     ap.add_argument("--jobs", type=int, default=40, help="serving: jobs per load level")
     ap.add_argument("--streams", type=int, default=4, help="uneven/serving: scheduler streams")
+    ap.add_argument("--graph", type=int, default=0,
+                    help="uneven: launch batches as CUDA graphs (1) or eagerly (0, default: measured faster)")
     return ap.parse_args()
 
 
@@ -255,7 +257,8 @@ def run_uneven(args):
         ctx.poll(j, w.datasets[0].p)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        jobs = [ctx.submit(ids[i], w.params[i], w.lambdas, precision=prec, batch=max(0, args.item_batch))
+        gflag = nv.FLAG_GRAPH if args.graph else 0
+        jobs = [ctx.submit(ids[i], w.params[i], w.lambdas, precision=prec, batch=max(0, args.item_batch), flags=gflag)
                 for i in range(D)]
         res = [ctx.poll(jb, w.datasets[i].p) for i, jb in enumerate(jobs)]
         dt = time.perf_counter() - t0
@@ -270,6 +273,7 @@ def run_uneven(args):
                                    f"p in {{2,3,5}}, {args.points} points each, 9 lambdas",
                        "precision": "mixed" if prec == nv.MIXED else "fp64", "streams": args.streams,
                        "batch_per_item": args.item_batch if args.item_batch > 0 else "autotuned",
+                       "cuda_graphs": bool(args.graph),
                        "arena_gb": arena_bytes / 1e9},
             "autotune": {"seconds": round(t_tune, 2), "by_n": tune,
                          "what": "plk_autotune per half-octave of n, before the timed region"},

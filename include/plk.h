@@ -89,6 +89,13 @@ typedef struct {
 /* flags: PLK_MIXED without the FP64 re-evaluation tier (keeps the 7-slice result;
  * for measuring the 7-slice error itself). */
 #define PLK_FLAG_NO_FP64_TIER 4
+/* flags: launch each batch's kernel sequence as one CUDA graph (PLK_FP64: the
+ * whole batch; PLK_MIXED: the 5-slice first pass, whose retry tiers depend on
+ * flags read back to the host and stay eager).  The sequence is captured from
+ * the stream with the same launch code and replayed; between batches of the
+ * same shape the executable graph is only updated.  Results are identical to
+ * the eager launches.  Ignored together with PLK_FLAG_KERNEL_TIMING. */
+#define PLK_FLAG_GRAPH 8
 
 /* ------------------------------------------------------------------------ */
 /* Stateless device-pointer evaluation (one dataset, K points)               */

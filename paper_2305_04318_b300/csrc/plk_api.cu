@@ -287,6 +287,50 @@ static AuxStreams aux_streams() {
     return st;
 }
 
+// Launches the sequence `enqueue` puts on stream s as one CUDA graph: the
+// sequence is captured from s (thread-local capture mode, so other threads'
+// CUDA calls are unaffected), and the executable graph this thread keeps for s
+// is updated in place when the capture has the same topology (only kernel
+// arguments changed, as between batches of one shape), else instantiated anew.
+template <class F>
+static cudaError_t launch_as_graph(cudaStream_t s, F &&enqueue) {
+    struct Cache {
+        std::map<std::pair<int, cudaStream_t>, cudaGraphExec_t> m;
+        ~Cache() {
+            for (auto &kv : m)
+                if (kv.second) cudaGraphExecDestroy(kv.second);
+        }
+    };
+    thread_local Cache cache;
+    if (s == nullptr || s == cudaStreamLegacy) return enqueue();   // the legacy stream cannot be captured
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if ((e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) return e;
+    const cudaError_t le = enqueue();
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(s, &g);
+    if (le != cudaSuccess || e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return le != cudaSuccess ? le : e;
+    }
+    cudaGraphExec_t &x = cache.m[{dev, s}];
+    if (x) {
+        cudaGraphExecUpdateResultInfo info;
+        if (cudaGraphExecUpdate(x, g, &info) != cudaSuccess) {
+            (void)cudaGetLastError();
+            cudaGraphExecDestroy(x);
+            x = nullptr;
+        }
+    }
+    if (!x) e = cudaGraphInstantiate(&x, g, 0);
+    if (e == cudaSuccess) e = cudaGraphLaunch(x, s);
+    cudaGraphDestroy(g);
+    return e;
+}
+
+static bool use_graph(int flags) { return (flags & PLK_FLAG_GRAPH) && !(flags & PLK_FLAG_KERNEL_TIMING); }
+
 // 5-slice pass over the batch.  With `overlap` and enough points, the batch is
 // cut into parts of about 296 points (two diagonal-tile blocks per SM); the
 // front of every part after the first (prep, table, build: FP64 pipe, no
@@ -348,8 +392,12 @@ static plk_status run_mixed_batch(BatchArgs b, const Layout &L, void *ws, const 
     x.err = at<int>(ws, L.off_err);
     x.err_bound = err_bound;
     x.tol = kMixedTol;
-    cudaError_t e = cudaMemsetAsync(x.err, 0, sizeof(int), s);
-    if (e == cudaSuccess) e = mixed_first_pass(b, x, overlap, s);
+    auto first = [&]() {
+        cudaError_t r = cudaMemsetAsync(x.err, 0, sizeof(int), s);
+        return r == cudaSuccess ? mixed_first_pass(b, x, overlap, s) : r;
+    };
+    if (use_graph(flags) && overlap) aux_streams();   // create the helper streams outside the capture
+    cudaError_t e = use_graph(flags) ? launch_as_graph(s, first) : first();
     if (e != cudaSuccess) return cuda_fail(e, "mixed batch launch");
     std::vector<int> hf(b.count + 1);
     e = cudaMemcpyAsync(hf.data(), x.flags, sizeof(int) * b.count, cudaMemcpyDeviceToHost, s);
@@ -443,7 +491,8 @@ static plk_status run_eval(const plk_eval_args *a, int reml, int flags, const La
             plk_status st = run_mixed_batch(b, L, ws, a->params, flags, a->err_bound, true, s);
             if (st != PLK_OK) return st;
         } else {
-            e = launch_fp64_batch(b, s);
+            e = use_graph(flags) ? launch_as_graph(s, [&]() { return launch_fp64_batch(b, s); })
+                                 : launch_fp64_batch(b, s);
             if (e != cudaSuccess) return cuda_fail(e, "batch launch");
         }
     }
@@ -788,7 +837,8 @@ std::string run_item(Job *j, Item &it, cudaStream_t s) {
         plk_status st = run_mixed_batch(b, L, it.ws, j->d_params, j->opts.flags, nullptr, true, s);
         if (st != PLK_OK) err = plk_last_error();
     } else {
-        cudaError_t e = launch_fp64_batch(b, s);
+        cudaError_t e = use_graph(j->opts.flags) ? launch_as_graph(s, [&]() { return launch_fp64_batch(b, s); })
+                                                 : launch_fp64_batch(b, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) err = cudaGetErrorString(e);
     }

@@ -131,6 +131,7 @@ def default_batch(n, K, limit_bytes=8e9):
 FLAG_KERNEL_TIMING = 1
 FLAG_NO_RETRY = 2
 FLAG_NO_FP64_TIER = 4
+FLAG_GRAPH = 8
 
 
 def kernel_timing(reset=True):
@@ -351,11 +352,11 @@ class Context:
                                         X.shape[1], C.byref(out)))
         return out.value
 
-    def submit(self, ds, params, lambdas, precision=FP64, reml=False, batch=0):
+    def submit(self, ds, params, lambdas, precision=FP64, reml=False, batch=0, flags=0):
         params = np.ascontiguousarray(params, dtype=np.float64).reshape(-1, 5)
         lambdas = np.ascontiguousarray(lambdas, dtype=np.float64)
         out = C.c_int64()
-        o = Options(precision, int(bool(reml)), batch, 0)
+        o = Options(precision, int(bool(reml)), batch, int(flags))
         _check(lib().plk_submit_profile(self.h, ds, _np_ptr(params), params.shape[0], _np_ptr(lambdas),
                                         lambdas.shape[0], C.byref(o), C.byref(out)))
         return dict(id=out.value, K=params.shape[0], M=lambdas.shape[0])

@@ -155,3 +155,25 @@ def test_mixed4000_full_size_sampled():
     print(json.dumps(dict(what="mixed4000 5-slice bound", points=int(ok.sum()),
                           max_err_over_bound=float(np.max(err[ok] / g5["err_bound"][ok])))))
     assert np.all(err[ok] <= g5["err_bound"][ok])
+
+
+@pytest.mark.parametrize("precision", [nv.FP64, nv.MIXED])
+def test_graph_launch_identical_to_eager(precision):
+    """PLK_FLAG_GRAPH: the batch captured and replayed as a CUDA graph gives the
+    eager launches' results bit for bit; a second call of the same shape
+    updates the executable graph in place, a third with a ragged last batch
+    re-instantiates it."""
+    import torch
+    from gpu_util import to_dev
+    ds = synth.aniso_dataset(91, 400, math.sqrt(40.0), 3)
+    lams = synth.LAMBDA_GRID_9
+    rng = np.random.default_rng(91)
+    s = torch.cuda.Stream()
+    for K in (300, 300, 290):      # two parts of the overlapped first pass when K >= 256
+        P = synth.omega_from_unit(rng.uniform(size=(K, 5)))
+        args = (to_dev(ds.coords), to_dev(ds.y), to_dev(ds.X), to_dev(lams), to_dev(P))
+        a = nv.eval_device(*args, precision=precision, batch=300, stream=s)
+        b = nv.eval_device(*args, precision=precision, batch=300, stream=s, flags=nv.FLAG_GRAPH)
+        s.synchronize()
+        for k in ("logL", "sigma2", "beta", "logdet", "status", "err_bound"):
+            np.testing.assert_array_equal(a[k].cpu().numpy(), b[k].cpu().numpy(), err_msg=f"K={K} {k}")
