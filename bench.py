@@ -66,10 +66,11 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=0, help="oracle points in the CPU sample (default: cores)")
-    ap.add_argument("--workload", default="mixed4000", choices=["mixed4000", "uneven", "serving"],
+    ap.add_argument("--workload", default="mixed4000", choices=["mixed4000", "uneven", "serving", "pipeline"],
                     help="mixed4000: the metric's n=4000 workload (default); uneven: 256 datasets of "
                          "n in [200,3000] x 512 points through the job scheduler; serving: Poisson "
-                         "stream of profile jobs over a pool of resident datasets")
+                         "stream of profile jobs over a pool of resident datasets; pipeline: Steps 1-6 of "
+                         "the method on one dataset (MLE, representative points, evaluation, profiles)")
     ap.add_argument("--datasets", type=int, default=0, help="uneven/serving: number of datasets (default 256 / 32)")
     ap.add_argument("--points", type=int, default=512, help="uneven: points per dataset")
     ap.add_argument("--item-batch", type=int, default=0,
@@ -373,6 +374,96 @@ def run_serving(args):
     print(json.dumps(line), flush=True)
 
 
+def run_pipeline(args):
+    """Steps 1-6 of the method on one synthetic dataset shaped like the paper's
+    rainfall example (n = 100 sites on the unit square, p = 2): Step 1 the MLE
+    and two fits with kappa held at 0.5 and 10 (batched Newton iterations on the
+    GPU), Step 2 the representative points (5-D cloud of 726 points x 11
+    contour levels around the MLE, 4-D clouds of 120 x 11 around the two
+    constrained fits) and 30 lambdas, Step 3 all of them on the GPU, Steps 4-6
+    the profiles of lambda, of phi_X (upper hull of the cloud), of beta_1 and of
+    sigma on the device.  Reports the time of every step."""
+    import torch
+    from paper_2305_04318_b300 import native as nv, synth
+    n = args.n if args.n != 4000 else 100
+    prec = nv.MIXED if args.precision == "mixed" else nv.FP64
+    ds = synth.simulate_dataset(101, n, math.sqrt(n / 100.0), 2, beta=(1.0, 0.5), sigma=1.0, kappa=1.0, phi_x=0.2,
+                                nug=0.1, phi_r=1.5, phi_a=0.5, lam=0.5, name="pipeline")
+    dev = torch.device("cuda")
+    T = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64), device=dev)
+    arena = torch.empty((16 << 30,), dtype=torch.uint8, device=dev)
+    times = {}
+    with nv.Context(arena.numel(), arena=arena, n_streams=2) as ctx:
+        did = ctx.create_dataset(ds.coords, ds.y, ds.X)
+        w0 = np.array([0.3, 1.0, 0.2, 1.2, 0.3])
+        nv.fit_mle(ctx, did, w0, 0.3, precision=prec, max_iter=2)          # warm-up
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        fit = nv.fit_mle(ctx, did, w0, 0.3, precision=prec)
+        fits_k = [nv.fit_mle(ctx, did, w0, fit["lam"], precision=prec, kappa_fixed=True, kappa=k) for k in (0.5, 10.0)]
+        times["step1_mle_s"] = time.perf_counter() - t
+        t = time.perf_counter()
+        c5 = nv.quadratic_cloud(ctx, did, fit["omega"], fit["lam"], precision=prec, n_lambda=30, seed=1)
+        ck = [nv.quadratic_cloud(ctx, did, f["omega"], f["lam"], precision=prec, kappa_fixed=True, n_lambda=0, seed=2 + i)
+              for i, f in enumerate(fits_k)]
+        P = np.vstack([c5["params"]] + [c["params"] for c in ck])
+        lam = c5["lambdas"]
+        times["step2_points_s"] = time.perf_counter() - t
+        ctx.release_dataset(did)
+    del arena
+    torch.cuda.synchronize()
+    K, M = P.shape[0], len(lam)
+    coords, y, X, lamd, Pd = T(ds.coords), T(ds.y), T(ds.X), T(lam), T(P)
+    nv.eval_device(coords, y, X, lamd, Pd[:64], precision=prec, with_ssq=True)   # warm-up
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    out = nv.eval_device(coords, y, X, lamd, Pd, precision=prec, with_ssq=True)
+    e1.record()
+    torch.cuda.synchronize()
+    times["step3_eval_s"] = e0.elapsed_time(e1) * 1e-3
+
+    def profiles():
+        lam_prof = nv.profile_lambda_device(out["logL"])
+        lam_ci = nv.profile_ci_device(lamd, lam_prof, 0.95)
+        best = nv.profile_max_device(out["logL"])                     # max over lambda per point
+        ok = torch.isfinite(best)
+        xq = T(np.exp(np.linspace(np.log(P[:, 0].min()), np.log(P[:, 0].max()), 64)))
+        hull, _ = nv.profile_hull_device(Pd[:, 0][ok].contiguous(), best[ok].contiguous(), xq)
+        phi_ci = nv.profile_ci_device(xq, hull, 0.95)
+        bgrid = T(np.linspace(-1.0, 2.0, 64))
+        bprof = nv.profile_beta_device(y, lamd, out["ssq_yx"], out["logdet"], out["status"], 1, bgrid)
+        beta_ci = nv.profile_ci_device(bgrid, bprof, 0.95)
+        sgrid = T(np.linspace(0.05, 3.0, 64))
+        sprof = nv.profile_sigma_device(y, lamd, out["ssq_yx"], out["logdet"], out["status"], sgrid)
+        sig_ci = nv.profile_ci_device(sgrid, sprof, 0.95)
+        return {k: v.cpu().numpy()[:2].tolist() for k, v in
+                dict(lambda_=lam_ci, phi_x=phi_ci, beta_1=beta_ci, sigma=sig_ci).items()}
+
+    profiles()                                                  # warm-up (first use of these kernels)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    cis = profiles()
+    torch.cuda.synchronize()
+    times["steps4_6_profiles_s"] = time.perf_counter() - t
+    st = out["status"].cpu().numpy()
+    total = sum(times.values())
+    line = {"metric": "profile-likelihood method, Steps 1-6 on one dataset", "value": K * M / times["step3_eval_s"],
+            "unit": "(omega, lambda) evals/s in Step 3", "n_gpus": 1, "steps": 1, "warmup": 1,
+            "ms_per_step": 1e3 * total, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"pipeline: n={n} sites on a square of side {math.sqrt(n / 100.0):.2f}, p=2, "
+                                   "truth kappa=1, phi_X=0.2, nu^2=0.1, ratio 1.5, lambda 0.5",
+                       "precision": "mixed" if prec == nv.MIXED else "fp64", "K": int(K), "M": int(M)},
+            "times_s": {k: round(v, 4) for k, v in times.items()},
+            "mle": {"omega": fit["omega"].tolist(), "lambda": fit["lam"], "logL": fit["logL"],
+                    "iterations": fit["iterations"],
+                    "kappa_fixed": [{"kappa": k, "logL": f["logL"], "iterations": f["iterations"]}
+                                    for k, f in zip((0.5, 10.0), fits_k)]},
+            "ci95": cis, "points_not_ok": int(((st & 15) != 0).sum())}
+    print(json.dumps(line), flush=True)
+
+
 def trail_kernel_sha256(root):
     """SHA-256 of the trailing-update kernel's source (its configuration, the
     kernel and the PTX wrappers it uses)."""
@@ -410,6 +501,9 @@ def main():
         return
     if args.workload == "serving":
         run_serving(args)
+        return
+    if args.workload == "pipeline":
+        run_pipeline(args)
         return
     import torch
     import torch.distributed as dist

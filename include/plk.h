@@ -264,6 +264,132 @@ plk_status plk_autotune(plk_ctx *ctx, int64_t n, int32_t p, int32_t M, int32_t p
 plk_status plk_scheduled_batch(plk_ctx *ctx, int64_t n, int32_t precision, int64_t K, int32_t *batch,
                                int32_t *tuned);
 
+/* ------------------------------------------------------------------------ */
+/* Steps 1 and 2 of the method (Sections 3.1-3.2): the maximum-likelihood     */
+/* estimate and the representative parameter points                          */
+/* ------------------------------------------------------------------------ */
+
+/* Internal parameters (Section 3.2), one row of 5 doubles:
+ *   [0] gamma_1 = log phi_X + log phi_Y            (sumLogRange)
+ *   [1] kappa~  = log kappa, or 1/sqrt(kappa) when the fitted kappa >= 4
+ *   [2] nu      = sqrt(nu^2)
+ *   [3] gamma_2 = sqrt(phi_X/phi_Y - 1) cos(2 phi_A) (aniso1)
+ *   [4] gamma_3 = sqrt(phi_X/phi_Y - 1) sin(2 phi_A) (aniso2)
+ * (natural -> internal: plk_internal_params_device.)  Host: natural rows of K
+ * internal rows; phi_R = 1 + gamma_2^2 + gamma_3^2 >= 1, phi_A =
+ * atan2(gamma_3, gamma_2)/2 in [0, pi), nu^2 = nu^2.  Errors: PLK_E_INVALID. */
+plk_status plk_natural_params(const double *internal, int64_t K, int32_t kappa_hat_large, double *out);
+
+/* chi^2 quantile: x with P(chi^2_dof <= x) = p (host; NaN for
+ * dof < 1 or p outside (0, 1)).  The contour levels of Section 3.2. */
+double plk_chi2_quantile(int32_t dof, double p);
+
+/* The numerical-Hessian stencil of Section 3.2 around `center_internal` (host,
+ * 5 doubles) in the free internal coordinates (all five, or all but kappa~
+ * when kappa_fixed): the centre, +-delta e_i, and +-delta e_i +-delta e_j for
+ * every pair i < j in the order (+,+), (+,-), (-,+), (-,-): S = 2 d^2 + 1 rows
+ * (51 for d = 5, 33 for d = 4) of internal parameters written to `out`
+ * (host, S x 5); *S_out = S.  Errors: PLK_E_INVALID. */
+plk_status plk_hessian_stencil(const double *center_internal, int32_t kappa_fixed, double delta, double *out,
+                               int32_t *S_out);
+
+/* Hessian H (d x d) and gradient (d) of L(omega') = max over lambda of l_p,
+ * from l_p at the stencil rows (host, S x 3: lambda-hat - dl, lambda-hat,
+ * lambda-hat + dl per row).  Per row, L is the maximum of the parabola through
+ * the three values over lambda-hat + t dl, |t| <= tmax (the largest of the
+ * three when the parabola is not concave; NaN if any is NaN); then central
+ * differences: H_ii = (L(+i) - 2 L(0) + L(-i))/delta^2, H_ij = (L(++) - L(+-)
+ * - L(-+) + L(--))/(4 delta^2), g_i = (L(+i) - L(-i))/(2 delta).  Optional
+ * outputs: the profiled L (S) and the offsets t (S).  Host; PLK_E_INVALID. */
+plk_status plk_hessian_from_stencil(int32_t kappa_fixed, double delta, const double *logL3, double tmax, double *H,
+                                   double *grad, double *L_profiled, double *t_lambda);
+
+/* Eigen-decomposition -H = E diag(D) E^T (host, d <= 5; E's columns the
+ * eigenvectors) with the fix-up of Section 3.2: negative eigenvalues replaced
+ * by their absolute values; if the largest exceeds 100, eigenvalues below 0.1
+ * become 0.1; numerically zero ones (below 1e-8 max(1, largest)) or non-finite
+ * ones become 0.1.  PLK_E_INVALID. */
+plk_status plk_fix_hessian(int32_t d, const double *H, double *E, double *D);
+
+/* n points on the unit sphere in R^d spread by a stochastic maximin optimiser
+ * (maximises the smallest pairwise distance, Section 3.2), seeded; `rounds`
+ * passes over the points.  Host, x: n x d; *min_distance (may be NULL) the
+ * smallest pairwise distance reached.  PLK_E_INVALID. */
+plk_status plk_sphere_points(int32_t d, int32_t n, uint64_t seed, int32_t rounds, double *x,
+                             double *min_distance);
+
+/* Likelihood evaluator for the two steps below: l_p (K x M, row-major) at K
+ * natural parameter rows (K x 5) and M lambdas; returns 0 on success, else a
+ * plk_status.  plk_fit_mle / plk_quadratic_cloud use the library's own GPU
+ * evaluation through a context; the _cb forms take any evaluator. */
+typedef int32_t (*plk_eval_fn)(void *user, const double *params, int64_t K, const double *lambdas, int32_t M,
+                               double *logL);
+
+typedef struct {
+    int32_t precision;    /* plk_precision of the evaluations (context forms) */
+    int32_t kappa_fixed;  /* 1: kappa held at `kappa` (the constrained fits of Section 3.1) */
+    double kappa;
+    double delta;         /* stencil step in internal coordinates; <= 0: 0.05 */
+    double delta_lambda;  /* lambda step; <= 0: 0.05 */
+    int32_t max_iter;     /* <= 0: 60 */
+    double tol;           /* stop when an iteration gains less than tol in l_p; <= 0: 1e-7 */
+} plk_fit_options;
+
+/* Step 1 (Section 3.1): maximise l_p(omega, lambda) from (omega0, lambda0).
+ * Batched Newton iteration in the internal parameters: each iteration
+ * evaluates the Hessian stencil at three lambdas (one batch), takes the Newton
+ * direction of the lambda-profiled likelihood with the eigenvalues of -H made
+ * positive (trust radius 1 in internal units), and evaluates a batch of step
+ * lengths at the lambda of the centre's parabola; the best evaluated point of
+ * both batches becomes the next iterate (kappa projected onto [0.1, 20], the
+ * shapes the method explores).  When an iteration
+ * gains less than opts->tol both finite-difference steps shrink by 4 (at most
+ * twice); it stops when that no longer helps or after opts->max_iter.  Outputs (host): omega_hat (5, natural), lambda_hat,
+ * logL_hat (l_p evaluated at them, may be NULL), iterations (may be NULL).
+ * Errors: PLK_E_INVALID (start outside the domain or l_p not finite there),
+ * evaluation errors. */
+plk_status plk_fit_mle(plk_ctx *ctx, plk_dataset ds, const double *omega0, double lambda0,
+                       const plk_fit_options *opts, double *omega_hat, double *lambda_hat, double *logL_hat,
+                       int32_t *iterations);
+plk_status plk_fit_mle_cb(plk_eval_fn fn, void *user, const double *omega0, double lambda0,
+                          const plk_fit_options *opts, double *omega_hat, double *lambda_hat, double *logL_hat,
+                          int32_t *iterations);
+
+typedef struct {
+    int32_t precision;          /* plk_precision of the stencil evaluations (context form) */
+    int32_t kappa_fixed;        /* 1: 4-D cloud with kappa held at omega_hat's kappa */
+    int32_t n_sphere;           /* points per contour level; <= 0: 726 (5-D) or 120 (4-D) */
+    int32_t n_levels;           /* contour levels (with level_probs) */
+    const double *level_probs;  /* chi^2_d probabilities of the levels; NULL: 0.05, 0.15, ..., 0.95, 0.99 */
+    int32_t n_lambda;           /* lambda grid size (0: none written) */
+    double delta;               /* Hessian stencil step; <= 0: 0.05 */
+    double delta_lambda;        /* <= 0: 0.05 */
+    uint64_t seed;              /* sphere points and the nugget repair */
+    int32_t sphere_rounds;      /* <= 0: 200 */
+} plk_cloud_options;
+
+/* Step 2 (Section 3.2): representative points around (omega_hat, lambda_hat).
+ * Evaluates the Hessian stencil (one batch of S x 3 evaluations; with steps of
+ * 1/4, at most twice more, while a stencil value is not finite), fixes the
+ * eigenvalues of -H, spreads n_sphere maximin points on the unit sphere and
+ * maps them to every contour level: x' = omega'-hat + sqrt(c_l) E D^{-1/2} E^T x
+ * with c_l the chi^2_d quantile of the level, in internal coordinates, then to
+ * natural rows.  A point whose nu comes out negative (a negative nugget) gets
+ * nu^2 = 0 or, alternately, a uniform draw on (0, 2).  The lambda grid has
+ * n_lambda values evenly spaced between the 0.01 and 0.99 quantiles of the
+ * normal approximation N(lambda_hat, -1/l''(lambda)) at the centre (sd 0.5 if
+ * l'' >= 0).  Outputs (host): params_out (capacity x 5; *K_out = levels x
+ * n_sphere rows; with params_out NULL only *K_out is set), lambdas_out
+ * (n_lambda), hessian_out (d x d), eig_out (d, the fixed eigenvalues of -H);
+ * any but K_out may be NULL.  Errors: PLK_E_INVALID, PLK_E_NOMEM (capacity
+ * below K), evaluation errors. */
+plk_status plk_quadratic_cloud(plk_ctx *ctx, plk_dataset ds, const double *omega_hat, double lambda_hat,
+                               const plk_cloud_options *opts, double *params_out, int64_t capacity, int64_t *K_out,
+                               double *lambdas_out, double *hessian_out, double *eig_out);
+plk_status plk_quadratic_cloud_cb(plk_eval_fn fn, void *user, const double *omega_hat, double lambda_hat,
+                                  const plk_cloud_options *opts, double *params_out, int64_t capacity,
+                                  int64_t *K_out, double *lambdas_out, double *hessian_out, double *eig_out);
+
 /* Message describing the last error of the calling thread ("" if none). */
 const char *plk_last_error(void);
 

@@ -46,6 +46,21 @@ class Options(C.Structure):
     _fields_ = [("precision", C.c_int32), ("reml", C.c_int32), ("batch", C.c_int32), ("flags", C.c_int32)]
 
 
+class FitOptions(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("kappa_fixed", C.c_int32), ("kappa", C.c_double),
+                ("delta", C.c_double), ("delta_lambda", C.c_double), ("max_iter", C.c_int32), ("tol", C.c_double)]
+
+
+class CloudOptions(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("kappa_fixed", C.c_int32), ("n_sphere", C.c_int32),
+                ("n_levels", C.c_int32), ("level_probs", C.c_void_p), ("n_lambda", C.c_int32),
+                ("delta", C.c_double), ("delta_lambda", C.c_double), ("seed", C.c_uint64),
+                ("sphere_rounds", C.c_int32)]
+
+
+EVAL_FN = C.CFUNCTYPE(C.c_int32, C.c_void_p, C.POINTER(C.c_double), C.c_int64, C.POINTER(C.c_double), C.c_int32,
+                      C.POINTER(C.c_double))
+
 _lib = None
 
 
@@ -88,6 +103,20 @@ def lib():
         "plk_profile_hull_device": (C.c_int, [vp, i64, vp, i64, vp, i64, vp, vp, vp]),
         "plk_internal_params_device": (C.c_int, [vp, i64, i32, vp, vp]),
         "plk_kernel_timing": (C.c_int, [C.POINTER(dbl), C.POINTER(i64), i32, i32, C.POINTER(i32)]),
+        "plk_natural_params": (C.c_int, [vp, i64, i32, vp]),
+        "plk_chi2_quantile": (dbl, [i32, dbl]),
+        "plk_hessian_stencil": (C.c_int, [vp, i32, dbl, vp, C.POINTER(i32)]),
+        "plk_hessian_from_stencil": (C.c_int, [i32, dbl, vp, dbl, vp, vp, vp, vp]),
+        "plk_fix_hessian": (C.c_int, [i32, vp, vp, vp]),
+        "plk_sphere_points": (C.c_int, [i32, i32, C.c_uint64, i32, vp, C.POINTER(dbl)]),
+        "plk_fit_mle": (C.c_int, [vp, i64, vp, dbl, C.POINTER(FitOptions), vp, C.POINTER(dbl), C.POINTER(dbl),
+                                  C.POINTER(i32)]),
+        "plk_fit_mle_cb": (C.c_int, [EVAL_FN, vp, vp, dbl, C.POINTER(FitOptions), vp, C.POINTER(dbl),
+                                     C.POINTER(dbl), C.POINTER(i32)]),
+        "plk_quadratic_cloud": (C.c_int, [vp, i64, vp, dbl, C.POINTER(CloudOptions), vp, i64, C.POINTER(i64), vp,
+                                          vp, vp]),
+        "plk_quadratic_cloud_cb": (C.c_int, [EVAL_FN, vp, vp, dbl, C.POINTER(CloudOptions), vp, i64,
+                                             C.POINTER(i64), vp, vp, vp]),
         "plk_kernel_class_name": (C.c_char_p, [i32]),
     }
     for name, (res, args) in sig.items():
@@ -411,3 +440,132 @@ class Context:
 
     def __exit__(self, *a):
         self.close()
+
+
+# ---------------------------------------------------------------------------
+# Steps 1 and 2 (Sections 3.1-3.2): host logic in the library
+# ---------------------------------------------------------------------------
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def natural_params(internal, kappa_hat_large=False):
+    v = _f64(internal).reshape(-1, 5)
+    out = np.empty_like(v)
+    _check(lib().plk_natural_params(_np_ptr(v), v.shape[0], int(bool(kappa_hat_large)), _np_ptr(out)))
+    return out
+
+
+def chi2_quantile(dof, p):
+    return float(lib().plk_chi2_quantile(int(dof), float(p)))
+
+
+def hessian_stencil(center_internal, kappa_fixed=False, delta=0.05):
+    c = _f64(center_internal)
+    out = np.empty((51, 5))
+    S = C.c_int32()
+    _check(lib().plk_hessian_stencil(_np_ptr(c), int(bool(kappa_fixed)), float(delta), _np_ptr(out), C.byref(S)))
+    return out[:S.value].copy()
+
+
+def hessian_from_stencil(logL3, kappa_fixed=False, delta=0.05, tmax=1.0):
+    f = _f64(logL3).reshape(-1, 3)
+    d = 4 if kappa_fixed else 5
+    H, g = np.empty((d, d)), np.empty(d)
+    L, T = np.empty(f.shape[0]), np.empty(f.shape[0])
+    _check(lib().plk_hessian_from_stencil(int(bool(kappa_fixed)), float(delta), _np_ptr(f), float(tmax), _np_ptr(H),
+                                          _np_ptr(g), _np_ptr(L), _np_ptr(T)))
+    return H, g, L, T
+
+
+def fix_hessian(H):
+    H = _f64(H)
+    d = H.shape[0]
+    E, D = np.empty((d, d)), np.empty(d)
+    _check(lib().plk_fix_hessian(d, _np_ptr(H), _np_ptr(E), _np_ptr(D)))
+    return E, D
+
+
+def sphere_points(d, n, seed=1, rounds=200):
+    x = np.empty((n, d))
+    m = C.c_double()
+    _check(lib().plk_sphere_points(int(d), int(n), int(seed), int(rounds), _np_ptr(x), C.byref(m)))
+    return x, m.value
+
+
+def _eval_callback(fn):
+    """Wrap a Python evaluator fn(params[K,5], lambdas[M]) -> logL[K,M]."""
+    def cb(user, params, K, lambdas, M, out):
+        try:
+            P = np.ctypeslib.as_array(params, shape=(K, 5)).copy()
+            lam = np.ctypeslib.as_array(lambdas, shape=(M,)).copy()
+            r = np.asarray(fn(P, lam), dtype=np.float64).reshape(K, M)
+            np.ctypeslib.as_array(out, shape=(K, M))[:] = r
+            return 0
+        except Exception:
+            return PLK_E_INVALID
+    return EVAL_FN(cb)
+
+
+def _fit_opts(precision, kappa_fixed, kappa, delta, delta_lambda, max_iter, tol):
+    return FitOptions(int(precision), int(bool(kappa_fixed)), float(kappa or 0.0), float(delta), float(delta_lambda),
+                      int(max_iter), float(tol))
+
+
+def _fit_result(w, lam, L, it):
+    return dict(omega=w, lam=lam.value, logL=L.value, iterations=it.value)
+
+
+def fit_mle(ctx, ds, omega0, lambda0, precision=FP64, kappa_fixed=False, kappa=None, delta=0.05, delta_lambda=0.05,
+            max_iter=60, tol=1e-7):
+    """Step 1 on the context's GPU evaluation (plk_fit_mle)."""
+    w0 = _f64(omega0)
+    w, lam, L, it = np.empty(5), C.c_double(), C.c_double(), C.c_int32()
+    o = _fit_opts(precision, kappa_fixed, kappa, delta, delta_lambda, max_iter, tol)
+    _check(lib().plk_fit_mle(ctx.h, ds, _np_ptr(w0), float(lambda0), C.byref(o), _np_ptr(w), C.byref(lam),
+                             C.byref(L), C.byref(it)))
+    return _fit_result(w, lam, L, it)
+
+
+def fit_mle_cb(evaluate, omega0, lambda0, kappa_fixed=False, kappa=None, delta=0.05, delta_lambda=0.05,
+               max_iter=60, tol=1e-7):
+    """Step 1 with a Python evaluator evaluate(params[K,5], lambdas[M]) -> logL[K,M]."""
+    w0 = _f64(omega0)
+    w, lam, L, it = np.empty(5), C.c_double(), C.c_double(), C.c_int32()
+    o = _fit_opts(FP64, kappa_fixed, kappa, delta, delta_lambda, max_iter, tol)
+    cb = _eval_callback(evaluate)
+    _check(lib().plk_fit_mle_cb(cb, None, _np_ptr(w0), float(lambda0), C.byref(o), _np_ptr(w), C.byref(lam),
+                                C.byref(L), C.byref(it)))
+    return _fit_result(w, lam, L, it)
+
+
+def _cloud_call(fn, first, omega_hat, lambda_hat, precision, kappa_fixed, n_sphere, level_probs, n_lambda, delta,
+                delta_lambda, seed, sphere_rounds):
+    w = _f64(omega_hat)
+    probs = None if level_probs is None else _f64(level_probs)
+    o = CloudOptions(int(precision), int(bool(kappa_fixed)), int(n_sphere), 0 if probs is None else len(probs),
+                     None if probs is None else _np_ptr(probs), int(n_lambda), float(delta), float(delta_lambda),
+                     int(seed), int(sphere_rounds))
+    K = C.c_int64()
+    _check(fn(*first, _np_ptr(w), float(lambda_hat), C.byref(o), None, 0, C.byref(K), None, None, None))
+    d = 4 if kappa_fixed else 5
+    P, lam, H, D = np.empty((K.value, 5)), np.empty(max(n_lambda, 1)), np.empty((d, d)), np.empty(d)
+    _check(fn(*first, _np_ptr(w), float(lambda_hat), C.byref(o), _np_ptr(P), K.value, C.byref(K), _np_ptr(lam),
+              _np_ptr(H), _np_ptr(D)))
+    return dict(params=P, lambdas=lam[:n_lambda], hessian=H, eigenvalues=D)
+
+
+def quadratic_cloud(ctx, ds, omega_hat, lambda_hat, precision=FP64, kappa_fixed=False, n_sphere=0, level_probs=None,
+                    n_lambda=30, delta=0.05, delta_lambda=0.05, seed=1, sphere_rounds=0):
+    """Step 2 on the context's GPU evaluation (plk_quadratic_cloud)."""
+    return _cloud_call(lib().plk_quadratic_cloud, (ctx.h, ds), omega_hat, lambda_hat, precision, kappa_fixed,
+                       n_sphere, level_probs, n_lambda, delta, delta_lambda, seed, sphere_rounds)
+
+
+def quadratic_cloud_cb(evaluate, omega_hat, lambda_hat, kappa_fixed=False, n_sphere=0, level_probs=None,
+                       n_lambda=30, delta=0.05, delta_lambda=0.05, seed=1, sphere_rounds=0):
+    """Step 2 with a Python evaluator evaluate(params[K,5], lambdas[M]) -> logL[K,M]."""
+    cb = _eval_callback(evaluate)
+    return _cloud_call(lib().plk_quadratic_cloud_cb, (cb, None), omega_hat, lambda_hat, FP64, kappa_fixed,
+                       n_sphere, level_probs, n_lambda, delta, delta_lambda, seed, sphere_rounds)

@@ -75,6 +75,18 @@ def test_build_ill_conditioned_and_edges(mode):
     assert np.all(g[:, 7, 3] == 1.0)
 
 
+@pytest.mark.parametrize("mode", MODES)
+def test_build_large_shapes(mode):
+    # kappa up to 20, the largest shape the fitting step explores
+    ds = synth.aniso_dataset(34, 200, math.sqrt(20.0), 2)
+    P = np.array([[0.3, k, 0.05, 1.5, 0.4] for k in (8.0, 12.0, 16.0, 20.0)] +
+                 [[3.0, k, 0.0, 2.0, 1.0] for k in (8.0, 12.0, 16.0, 20.0)])
+    o = oracle_v(ds.coords, P)
+    g = gpu_v(ds.coords, P, mode)
+    err = np.abs(g - o)
+    assert err.max() <= ATOL, f"mode {mode}: max |dV| {err.max():.3e}"
+
+
 def test_fast_double_float_build_against_fp64_build():
     # the FP32-pair evaluation against the FP64 evaluation of the same
     # polynomial: only the arithmetic differs

@@ -25,7 +25,7 @@ def test_scaled_k_matches_scipy(nu):
     np.testing.assert_allclose(got, ref, rtol=2e-13, atol=0)
 
 
-@pytest.mark.parametrize("nu", [0.1, 0.13675, 0.5, 0.9, 1.0, 2.3, 4.75, 8.0])
+@pytest.mark.parametrize("nu", [0.1, 0.13675, 0.5, 0.9, 1.0, 2.3, 4.75, 8.0, 12.0, 16.5, 20.0])
 def test_scaled_k_matches_mpmath(nu):
     # 30-digit reference from mpmath's besselk (an independent library routine)
     mpmath.mp.dps = 30
