@@ -632,6 +632,7 @@ def main():
                 "executed_frac": executed / (dom_ms * 1e-3) / 1e12 / peak,
                 "executed_is": "bf16 MMA flops issued by this kernel: 15 slice products per multiply-add, 128x128 tiles",
                 "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (kernel timed inside a long step)",
+                "fp64_equivalent_over_fp64_fma_peak": alg / fp64_peak,
                 "points_7slice": n7, "points_fp64": n64}
     share_tot = max(1e-9, sum(x[0] for x in timing.values()))
     kernel_share = {k: round(v[0] / share_tot, 4) for k, v in timing.items() if v[1]}
