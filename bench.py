@@ -76,6 +76,10 @@ def parse():
     ap.add_argument("--item-batch", type=int, default=0,
                     help="uneven: points per scheduled batch (default 0: chosen by the autotuner per dataset size)")
     ap.add_argument("--jobs", type=int, default=40, help="serving: jobs per load level")
+    ap.add_argument("--job-grid", type=int, default=16,
+                    help="serving: grid values of the profiled parameter (the full job: 64)")
+    ap.add_argument("--job-sub", type=int, default=2,
+                    help="serving: sub-grid values of each other parameter (the full job: 4)")
     ap.add_argument("--streams", type=int, default=4, help="uneven/serving: scheduler streams")
     ap.add_argument("--graph", type=int, default=0,
                     help="uneven: launch batches as CUDA graphs (1) or eagerly (0, default: measured faster)")
@@ -232,59 +236,83 @@ def run_uneven(args):
     512 points each, all submitted at once to one context; the scheduler
     interleaves their batches over the stream pool (continuous batching).  The
     points per batch come from the library's autotuner (plk_autotune), run once
-    per half-octave of n before the timed region, unless --item-batch is set."""
+    per half-octave of n before the timed region, unless --item-batch is set.
+    Under torchrun every rank takes whole datasets, balanced by points x n^3
+    (shard.balance_by_cost); the time is the max over ranks."""
     import torch
-    from paper_2305_04318_b300 import native as nv, synth
+    import torch.distributed as dist
+    from paper_2305_04318_b300 import native as nv, shard, synth
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
     D = args.datasets or 256
     w = synth.uneven(D=D, per=args.points)
+    owner = shard.balance_by_cost([len(P) * float(d.n) ** 3 for d, P in zip(w.datasets, w.params)], world)
+    mine = [i for i in range(D) if owner[i] == rank]
     prec = nv.MIXED if args.precision in ("auto", "mixed") else nv.FP64
     M = len(w.lambdas)
     free, _ = torch.cuda.mem_get_info()
     arena_bytes = int(min(free - (8 << 30), 200e9))
     arena = torch.empty((arena_bytes,), dtype=torch.uint8, device="cuda")
     tune = {}
-    with nv.Context(arena_bytes, arena=arena, n_streams=args.streams) as ctx:
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    with nv.Context(arena_bytes, device=local, arena=arena, n_streams=args.streams) as ctx:
         t_tune = time.perf_counter()
         if args.item_batch <= 0:
-            buckets = sorted({int(round(2 * math.log2(d.n))) for d in w.datasets})
+            buckets = sorted({int(round(2 * math.log2(w.datasets[i].n))) for i in mine})
             for b in buckets:
                 n_rep = int(round(2 ** (b / 2)))
                 bb, rate = ctx.autotune(n_rep, 3, M, prec)
                 tune[str(n_rep)] = {"batch": bb, "points_per_s": round(rate, 1)}
         t_tune = time.perf_counter() - t_tune
-        ids = [ctx.create_dataset(d.coords, d.y, d.X) for d in w.datasets]
+        ids = {i: ctx.create_dataset(w.datasets[i].coords, w.datasets[i].y, w.datasets[i].X) for i in mine}
         # warm-up: one small job
-        j = ctx.submit(ids[0], w.params[0][:4], w.lambdas, precision=prec, batch=4)
-        ctx.poll(j, w.datasets[0].p)
-        torch.cuda.synchronize()
+        if mine:
+            j = ctx.submit(ids[mine[0]], w.params[mine[0]][:4], w.lambdas, precision=prec, batch=4)
+            ctx.poll(j, w.datasets[mine[0]].p)
+        barrier()
         t0 = time.perf_counter()
         gflag = nv.FLAG_GRAPH if args.graph else 0
-        jobs = [ctx.submit(ids[i], w.params[i], w.lambdas, precision=prec, batch=max(0, args.item_batch), flags=gflag)
-                for i in range(D)]
-        res = [ctx.poll(jb, w.datasets[i].p) for i, jb in enumerate(jobs)]
+        jobs = {i: ctx.submit(ids[i], w.params[i], w.lambdas, precision=prec, batch=max(0, args.item_batch),
+                              flags=gflag) for i in mine}
+        res = [ctx.poll(jobs[i], w.datasets[i].p) for i in mine]
         dt = time.perf_counter() - t0
+        barrier()
         _, high = ctx.memory_stats()
+    if world > 1:
+        t = torch.tensor([dt], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dt = float(t.item())
     npts = sum(len(P) for P in w.params)
-    st = np.concatenate([r["status"] for r in res])
+    st = np.concatenate([r["status"] for r in res]) if res else np.zeros(0, dtype=np.int32)
     ns = np.array([d.n for d in w.datasets])
     line = {"metric": "profile-logL evals/s, batched uneven datasets", "value": npts / dt, "unit": UNIT,
-            "n_gpus": 1, "steps": 1, "warmup": 1, "ms_per_step": dt * 1e3, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "n_gpus": world, "steps": 1, "warmup": 1, "ms_per_step": dt * 1e3, "higher_is_better": True,
+            "scaling": "strong", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": f"uneven: {D} datasets, n log-uniform in [200,3000] (median {int(np.median(ns))}), "
                                    f"p in {{2,3,5}}, {args.points} points each, 9 lambdas",
                        "precision": "mixed" if prec == nv.MIXED else "fp64", "streams": args.streams,
                        "batch_per_item": args.item_batch if args.item_batch > 0 else "autotuned",
-                       "cuda_graphs": bool(args.graph),
-                       "arena_gb": arena_bytes / 1e9},
+                       "cuda_graphs": bool(args.graph), "arena_gb": arena_bytes / 1e9,
+                       "parallelism": f"datasets balanced by points x n^3 over {world} rank(s)"},
             "autotune": {"seconds": round(t_tune, 2), "by_n": tune,
-                         "what": "plk_autotune per half-octave of n, before the timed region"},
-            "points": int(npts), "points_not_ok": int(((st & 15) != 0).sum()),
-            "points_7slice": int(((st & 16) != 0).sum()), "points_fp64": int(((st & 32) != 0).sum()),
+                         "what": "plk_autotune per half-octave of n, before the timed region (rank 0's)"},
+            "points": int(npts), "points_not_ok_rank0": int(((st & 15) != 0).sum()),
+            "points_7slice_rank0": int(((st & 16) != 0).sum()), "points_fp64_rank0": int(((st & 32) != 0).sum()),
             "hbm_high_water_gb": high / 1e9, "e2e": {"value": npts / dt, "unit": UNIT,
             "h2d_bytes_per_step": int(sum(P.nbytes for P in w.params)), "d2h_bytes_per_step": int(
                 sum(r["logL"].nbytes + r["sigma2"].nbytes + r["beta"].nbytes + r["logdet"].nbytes + r["status"].nbytes
-                    for r in res))}}
-    print(json.dumps(line), flush=True)
+                    for r in res) * world)}}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
 
 
 def run_serving(args):
@@ -296,7 +324,7 @@ def run_serving(args):
     import torch
     from paper_2305_04318_b300 import native as nv, synth
     D = args.datasets or 32
-    G, sub = 16, 2     # jobs reduced from 64 x 4^4 omega so that a run ends in minutes
+    G, sub = args.job_grid, args.job_sub   # default 16 x 2^4 (the full job, 64 x 4^4, takes ~25 s each)
     pool = synth.serving_pool(D=D)
     lam = synth.LAMBDA_GRID_9
     prec = nv.MIXED if args.precision in ("auto", "mixed") else nv.FP64

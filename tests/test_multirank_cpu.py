@@ -85,3 +85,18 @@ def test_shards_disjoint_within_a_step_and_cover_the_grid():
             for b in blocks:
                 seen |= b
         assert seen == set(range(K))
+
+
+def test_balance_by_cost():
+    rng = np.random.default_rng(4)
+    n = np.round(np.exp(rng.uniform(np.log(200), np.log(3000), 256)))
+    cost = 512 * n ** 3
+    for world in (1, 2, 4, 8):
+        owner = shard.balance_by_cost(cost, world)
+        assert owner.min() >= 0 and owner.max() < world
+        loads = np.bincount(owner, weights=cost, minlength=world)
+        # greedy largest-first: no rank exceeds the ideal share by more than the largest item
+        assert loads.max() <= cost.sum() / world + cost.max() + 1e-6
+    # a single dominant item gets a rank of its own
+    owner = shard.balance_by_cost([100.0, 1.0, 1.0, 1.0], 2)
+    assert (owner == owner[0]).sum() == 1
