@@ -66,11 +66,12 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=0, help="oracle points in the CPU sample (default: cores)")
-    ap.add_argument("--workload", default="mixed4000", choices=["mixed4000", "uneven", "serving", "pipeline"],
+    ap.add_argument("--workload", default="mixed4000", choices=["mixed4000", "uneven", "serving", "pipeline", "iso100", "aniso1000"],
                     help="mixed4000: the metric's n=4000 workload (default); uneven: 256 datasets of "
                          "n in [200,3000] x 512 points through the job scheduler; serving: Poisson "
                          "stream of profile jobs over a pool of resident datasets; pipeline: Steps 1-6 of "
-                         "the method on one dataset (MLE, representative points, evaluation, profiles)")
+                         "the method on one dataset (MLE, representative points, evaluation, profiles); "
+                         "iso100 / aniso1000: the two smaller configurations, both precisions against the oracle")
     ap.add_argument("--datasets", type=int, default=0, help="uneven/serving: number of datasets (default 256 / 32)")
     ap.add_argument("--points", type=int, default=512, help="uneven: points per dataset")
     ap.add_argument("--item-batch", type=int, default=0,
@@ -492,6 +493,88 @@ def run_pipeline(args):
     print(json.dumps(line), flush=True)
 
 
+def run_small_config(args):
+    """Configs 1-2: iso100 (n = 100, K = 100 grid points, lambda = 0) and
+    aniso1000 (n = 1000, K = 4096 Halton points, 9 lambdas), all K points per
+    step in FP64 and in mixed precision; the oracle on the host cores on all
+    (iso100) or a sample (aniso1000) of the points, which also gives the
+    largest relative |Delta l_p| of each precision."""
+    import torch
+    from paper_2305_04318_b300 import native as nv, synth
+    import oracle
+    w = synth.iso100() if args.workload == "iso100" else synth.aniso1000()
+    ds, P, lam = w.datasets[0], w.params[0], w.lambdas
+    K, n, M = P.shape[0], ds.n, len(lam)
+    dev = torch.device("cuda")
+    T = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64), device=dev)
+    coords, y, X, lamd, Pd = T(ds.coords), T(ds.y), T(ds.X), T(lam), T(P)
+    cores = cpu_cores()
+    sample = np.arange(K) if K <= 128 else np.linspace(0, K - 1, 4 * cores).astype(int)
+    t0 = time.perf_counter()
+    o = oracle.profile_batch(ds.coords, ds.y, ds.X, P[sample], lam, nthreads=cores)
+    t_or = time.perf_counter() - t0
+    peaks = measured_peaks()
+    fp64_peak, _ = probe_fp64_peak()
+    out = {}
+    for name, prec in (("fp64", nv.FP64), ("mixed", nv.MIXED)):
+        batch = min(K, 1184 if n <= 1500 else 296)
+        wsb = nv.workspace_bytes(n, ds.p, M, batch, prec)
+        ws = torch.empty((wsb,), dtype=torch.uint8, device=dev)
+        for _ in range(args.warmup):
+            nv.eval_device(coords, y, X, lamd, Pd, precision=prec, batch=batch, workspace=ws)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            r = nv.eval_device(coords, y, X, lamd, Pd, precision=prec, batch=batch, workspace=ws)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        # per-kernel-class times from one more step with event timing around every launch
+        nv.kernel_timing(reset=True)
+        nv.eval_device(coords, y, X, lamd, Pd, precision=prec, batch=batch, workspace=ws, flags=nv.FLAG_KERNEL_TIMING)
+        torch.cuda.synchronize()
+        tm = nv.kernel_timing(reset=True)
+        g = {k: v.cpu().numpy() for k, v in r.items()}
+        st = g["status"] & 15
+        ok = (st[sample] == 0) & (o["status"] == 0)
+        err = np.abs(g["logL"][sample][ok] - o["logL"][ok])
+        rel = err / np.abs(o["logL"][ok])
+        dom = max(tm, key=lambda k: tm[k][0])
+        entry = {"evals_per_s": K / (ms * 1e-3), "ms_per_step": ms, "batch": batch,
+                 "max_rel_dlogL_vs_oracle": float(rel.max()) if rel.size else None,
+                 "max_abs_dlogL_vs_oracle": float(err.max()) if err.size else None,
+                 "status_mismatch": int(((st[sample] != 0) != (o["status"] != 0)).sum()),
+                 "compared": int(ok.sum()), "dominant_kernel": dom,
+                 "kernel_share": {k: round(v[0] / max(1e-9, sum(x[0] for x in tm.values())), 4)
+                                  for k, v in tm.items() if v[1]}}
+        if dom == "trailing_gemm":
+            tf = sum(trailing_flops(n, ds.p + M)) * K
+            ach = tf / (tm[dom][0] * 1e-3) / 1e12
+            entry["roofline"] = {"bound": "alu", "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s",
+                                 "frac": ach / fp64_peak, "kernel": "k_gemm_nt<1> (FP64 trailing update)",
+                                 "peak_source": "FP64 FMA pipe measured live"}
+        elif dom == "build":
+            # Matern entries per second against the FP64 pipe: ~14 FP64 operations per entry
+            ent = n * (n - 1) / 2 * K / (tm[dom][0] * 1e-3)
+            entry["roofline"] = {"bound": "alu", "achieved": ent * 14 * 2 / 1e12, "peak": fp64_peak, "unit": "TFLOP/s",
+                                 "frac": ent * 14 * 2 / 1e12 / fp64_peak, "kernel": "k_build (Matern tiles)",
+                                 "achieved_is": "14 FP64 ops per lower-triangle entry, counted as 2 flops each "
+                                                "(FMA-equivalent), over the build's event time",
+                                 "entries_per_s": ent}
+        out[name] = entry
+        del ws
+        torch.cuda.empty_cache()
+    line = {"metric": f"profile-logL evals/s, {args.workload}", "value": out["fp64"]["evals_per_s"], "unit": UNIT,
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": out["fp64"]["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"{args.workload}: n={n}, p={ds.p}, K={K}, M={M}", "precision": "fp64 (headline), mixed"},
+            "fp64": out["fp64"], "mixed": out["mixed"],
+            "cpu_baseline": {"value": len(sample) / t_or, "unit": UNIT, "cores": o["threads"], "kind": "oracle",
+                             "sample": f"{len(sample)} of the {K} points ({t_or:.1f} s wall)"}}
+    print(json.dumps(line), flush=True)
+
+
 def trail_kernel_sha256(root):
     """SHA-256 of the trailing-update kernel's source (its configuration, the
     kernel and the PTX wrappers it uses)."""
@@ -532,6 +615,9 @@ def main():
         return
     if args.workload == "pipeline":
         run_pipeline(args)
+        return
+    if args.workload in ("iso100", "aniso1000"):
+        run_small_config(args)
         return
     import torch
     import torch.distributed as dist

@@ -33,6 +33,12 @@
 
 using namespace plk;
 
+// Points per part of the mixed path's overlapped first pass (two diagonal-tile
+// blocks per SM of a 148-SM B300); a build-time constant.
+#ifndef PLK_MIXED_PART
+#define PLK_MIXED_PART 296
+#endif
+
 // ---------------------------------------------------------------------------
 // errors
 // ---------------------------------------------------------------------------
@@ -339,7 +345,7 @@ static bool use_graph(int flags) { return (flags & PLK_FLAG_GRAPH) && !(flags & 
 // part's build is exposed.  The work is forked from `s` onto the two internal
 // streams and joined back into `s`.
 static cudaError_t mixed_first_pass(const BatchArgs &b, const MixedArgs &x, bool overlap, cudaStream_t s) {
-    constexpr int kOverlapMin = 256, kPart = 296;
+    constexpr int kOverlapMin = 256, kPart = PLK_MIXED_PART;
     const AuxStreams st = overlap && b.count >= kOverlapMin ? aux_streams() : AuxStreams{};
     if (!st.hi) return launch_mixed_batch(b, x, 5, s);
     const int nparts = std::max(2, (b.count + kPart - 1) / kPart);

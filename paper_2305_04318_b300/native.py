@@ -13,7 +13,7 @@ import re
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libplk.so")
+LIB_PATH = os.environ.get("PLK_LIBRARY") or os.path.join(HERE, "libplk.so")   # PLK_LIBRARY: another build
 HEADER = os.path.join(os.path.dirname(HERE), "include", "plk.h")
 
 PLK_OK, PLK_E_INVALID, PLK_E_NOMEM, PLK_E_NOT_READY, PLK_E_TIMEOUT, PLK_E_CUDA, PLK_E_CANCELLED = range(7)
