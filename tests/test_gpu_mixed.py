@@ -177,3 +177,27 @@ def test_graph_launch_identical_to_eager(precision):
         s.synchronize()
         for k in ("logL", "sigma2", "beta", "logdet", "status", "err_bound"):
             np.testing.assert_array_equal(a[k].cpu().numpy(), b[k].cpu().numpy(), err_msg=f"K={K} {k}")
+
+
+@pytest.mark.slow
+def test_largest_serving_size_sampled():
+    """n = 8000, the largest dataset of the serving pool (512 MB per FP64
+    matrix): three points of a serving profile job in both precisions against
+    the oracle (FP64 within 1e-8 relative, mixed within 1e-3), through the
+    context API as the serving workload runs them."""
+    import torch
+    ds = synth.aniso_dataset(5 * 100000 + 99, 8000, math.sqrt(800.0), 3)
+    _, P = synth.profile_job_grid(0, G=4, sub=2)
+    P = P[[0, 21, 63]]
+    lams = synth.LAMBDA_GRID_9
+    o = oracle_eval(ds, P, lams)
+    arena = torch.empty((int(nv.workspace_bytes(8000, 3, 9, 3, nv.MIXED) * 1.2) + (1 << 30),), dtype=torch.uint8,
+                        device="cuda")
+    with nv.Context(arena.numel(), arena=arena, n_streams=1) as ctx:
+        d = ctx.create_dataset(ds.coords, ds.y, ds.X)
+        f = ctx.poll(ctx.submit(d, P, lams, precision=nv.FP64, batch=3), 3)
+        m = ctx.poll(ctx.submit(d, P, lams, precision=nv.MIXED, batch=3), 3)
+        ctx.release_dataset(d)
+    from gpu_util import compare
+    compare(f, o, what="n=8000 fp64")
+    mixed_compare(m, o, "n=8000 mixed")
