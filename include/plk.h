@@ -327,6 +327,7 @@ typedef int32_t (*plk_eval_fn)(void *user, const double *params, int64_t K, cons
 
 typedef struct {
     int32_t precision;    /* plk_precision of the evaluations (context forms) */
+    int32_t reml;         /* 1: maximise the REML profile likelihood (eq. remlpro; context forms) */
     int32_t kappa_fixed;  /* 1: kappa held at `kappa` (the constrained fits of Section 3.1) */
     double kappa;
     double delta;         /* stencil step in internal coordinates; <= 0: 0.05 */
@@ -357,6 +358,7 @@ plk_status plk_fit_mle_cb(plk_eval_fn fn, void *user, const double *omega0, doub
 
 typedef struct {
     int32_t precision;          /* plk_precision of the stencil evaluations (context form) */
+    int32_t reml;               /* 1: the REML profile likelihood (eq. remlpro; context form) */
     int32_t kappa_fixed;        /* 1: 4-D cloud with kappa held at omega_hat's kappa */
     int32_t n_sphere;           /* points per contour level; <= 0: 726 (5-D) or 120 (4-D) */
     int32_t n_levels;           /* contour levels (with level_probs) */

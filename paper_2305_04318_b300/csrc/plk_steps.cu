@@ -745,12 +745,13 @@ namespace {
 struct CtxEval {
     plk_ctx *ctx;
     plk_dataset ds;
-    int32_t precision;
+    int32_t precision, reml;
 };
 int32_t ctx_eval(void *u, const double *params, int64_t K, const double *lam, int32_t M, double *logL) {
     CtxEval *e = static_cast<CtxEval *>(u);
     plk_options o{};
     o.precision = e->precision;
+    o.reml = e->reml;
     plk_job job = 0;
     plk_status st = plk_submit_profile(e->ctx, e->ds, params, K, lam, M, &o, &job);
     if (st == PLK_OK) st = plk_poll(e->ctx, job, -1, logL, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr);
@@ -762,7 +763,7 @@ extern "C" plk_status plk_fit_mle(plk_ctx *ctx, plk_dataset ds, const double *om
                                   const plk_fit_options *opts, double *omega_hat, double *lambda_hat, double *logL_hat,
                                   int32_t *iterations) {
     if (!ctx) return bad("plk_fit_mle: ctx is NULL");
-    CtxEval e{ctx, ds, opts ? opts->precision : PLK_FP64};
+    CtxEval e{ctx, ds, opts ? opts->precision : PLK_FP64, opts ? opts->reml : 0};
     return plk_fit_mle_cb(ctx_eval, &e, omega0, lambda0, opts, omega_hat, lambda_hat, logL_hat, iterations);
 }
 
@@ -770,7 +771,7 @@ extern "C" plk_status plk_quadratic_cloud(plk_ctx *ctx, plk_dataset ds, const do
                                           const plk_cloud_options *opts, double *params_out, int64_t capacity,
                                           int64_t *K_out, double *lambdas_out, double *hessian_out, double *eig_out) {
     if (!ctx) return bad("plk_quadratic_cloud: ctx is NULL");
-    CtxEval e{ctx, ds, opts ? opts->precision : PLK_FP64};
+    CtxEval e{ctx, ds, opts ? opts->precision : PLK_FP64, opts ? opts->reml : 0};
     return plk_quadratic_cloud_cb(ctx_eval, &e, omega_hat, lambda_hat, opts, params_out, capacity, K_out, lambdas_out,
                                   hessian_out, eig_out);
 }

@@ -47,12 +47,12 @@ class Options(C.Structure):
 
 
 class FitOptions(C.Structure):
-    _fields_ = [("precision", C.c_int32), ("kappa_fixed", C.c_int32), ("kappa", C.c_double),
+    _fields_ = [("precision", C.c_int32), ("reml", C.c_int32), ("kappa_fixed", C.c_int32), ("kappa", C.c_double),
                 ("delta", C.c_double), ("delta_lambda", C.c_double), ("max_iter", C.c_int32), ("tol", C.c_double)]
 
 
 class CloudOptions(C.Structure):
-    _fields_ = [("precision", C.c_int32), ("kappa_fixed", C.c_int32), ("n_sphere", C.c_int32),
+    _fields_ = [("precision", C.c_int32), ("reml", C.c_int32), ("kappa_fixed", C.c_int32), ("n_sphere", C.c_int32),
                 ("n_levels", C.c_int32), ("level_probs", C.c_void_p), ("n_lambda", C.c_int32),
                 ("delta", C.c_double), ("delta_lambda", C.c_double), ("seed", C.c_uint64),
                 ("sphere_rounds", C.c_int32)]
@@ -508,9 +508,9 @@ def _eval_callback(fn):
     return EVAL_FN(cb)
 
 
-def _fit_opts(precision, kappa_fixed, kappa, delta, delta_lambda, max_iter, tol):
-    return FitOptions(int(precision), int(bool(kappa_fixed)), float(kappa or 0.0), float(delta), float(delta_lambda),
-                      int(max_iter), float(tol))
+def _fit_opts(precision, kappa_fixed, kappa, delta, delta_lambda, max_iter, tol, reml=False):
+    return FitOptions(int(precision), int(bool(reml)), int(bool(kappa_fixed)), float(kappa or 0.0), float(delta),
+                      float(delta_lambda), int(max_iter), float(tol))
 
 
 def _fit_result(w, lam, L, it):
@@ -518,11 +518,11 @@ def _fit_result(w, lam, L, it):
 
 
 def fit_mle(ctx, ds, omega0, lambda0, precision=FP64, kappa_fixed=False, kappa=None, delta=0.05, delta_lambda=0.05,
-            max_iter=60, tol=1e-7):
-    """Step 1 on the context's GPU evaluation (plk_fit_mle)."""
+            max_iter=60, tol=1e-7, reml=False):
+    """Step 1 on the context's GPU evaluation (plk_fit_mle); reml: the REML profile likelihood."""
     w0 = _f64(omega0)
     w, lam, L, it = np.empty(5), C.c_double(), C.c_double(), C.c_int32()
-    o = _fit_opts(precision, kappa_fixed, kappa, delta, delta_lambda, max_iter, tol)
+    o = _fit_opts(precision, kappa_fixed, kappa, delta, delta_lambda, max_iter, tol, reml)
     _check(lib().plk_fit_mle(ctx.h, ds, _np_ptr(w0), float(lambda0), C.byref(o), _np_ptr(w), C.byref(lam),
                              C.byref(L), C.byref(it)))
     return _fit_result(w, lam, L, it)
@@ -541,10 +541,11 @@ def fit_mle_cb(evaluate, omega0, lambda0, kappa_fixed=False, kappa=None, delta=0
 
 
 def _cloud_call(fn, first, omega_hat, lambda_hat, precision, kappa_fixed, n_sphere, level_probs, n_lambda, delta,
-                delta_lambda, seed, sphere_rounds):
+                delta_lambda, seed, sphere_rounds, reml=False):
     w = _f64(omega_hat)
     probs = None if level_probs is None else _f64(level_probs)
-    o = CloudOptions(int(precision), int(bool(kappa_fixed)), int(n_sphere), 0 if probs is None else len(probs),
+    o = CloudOptions(int(precision), int(bool(reml)), int(bool(kappa_fixed)), int(n_sphere),
+                     0 if probs is None else len(probs),
                      None if probs is None else _np_ptr(probs), int(n_lambda), float(delta), float(delta_lambda),
                      int(seed), int(sphere_rounds))
     K = C.c_int64()
@@ -557,10 +558,10 @@ def _cloud_call(fn, first, omega_hat, lambda_hat, precision, kappa_fixed, n_sphe
 
 
 def quadratic_cloud(ctx, ds, omega_hat, lambda_hat, precision=FP64, kappa_fixed=False, n_sphere=0, level_probs=None,
-                    n_lambda=30, delta=0.05, delta_lambda=0.05, seed=1, sphere_rounds=0):
-    """Step 2 on the context's GPU evaluation (plk_quadratic_cloud)."""
+                    n_lambda=30, delta=0.05, delta_lambda=0.05, seed=1, sphere_rounds=0, reml=False):
+    """Step 2 on the context's GPU evaluation (plk_quadratic_cloud); reml: the REML profile likelihood."""
     return _cloud_call(lib().plk_quadratic_cloud, (ctx.h, ds), omega_hat, lambda_hat, precision, kappa_fixed,
-                       n_sphere, level_probs, n_lambda, delta, delta_lambda, seed, sphere_rounds)
+                       n_sphere, level_probs, n_lambda, delta, delta_lambda, seed, sphere_rounds, reml)
 
 
 def quadratic_cloud_cb(evaluate, omega_hat, lambda_hat, kappa_fixed=False, n_sphere=0, level_probs=None,

@@ -21,7 +21,7 @@ def test_hessian_stencil_sizes():
 def _cloud_size(kappa_fixed, levels, n_sphere=0):
     # size query only (no evaluation is made): params_out NULL
     import ctypes as C
-    o = nv.CloudOptions(0, int(kappa_fixed), int(n_sphere), len(levels) if levels is not None else 0,
+    o = nv.CloudOptions(0, 0, int(kappa_fixed), int(n_sphere), len(levels) if levels is not None else 0,
                         None if levels is None else nv._np_ptr(levels), 0, 0.0, 0.0, 1, 0)
     K = C.c_int64()
     cb = nv._eval_callback(lambda P, lam: np.zeros((len(P), len(lam))))

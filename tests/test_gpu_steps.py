@@ -66,3 +66,16 @@ def test_quadratic_cloud_gpu_matches_oracle_driven(problem, kappa_fixed):
     np.testing.assert_allclose(g["eigenvalues"], o["eigenvalues"], rtol=1e-6)
     np.testing.assert_allclose(g["lambdas"], o["lambdas"], rtol=1e-8, atol=1e-8)
     np.testing.assert_allclose(g["params"], o["params"], rtol=1e-5, atol=1e-6)
+
+
+def test_fit_mle_reml_gpu_matches_oracle_driven(problem):
+    """Step 1 on the REML profile likelihood (eq. remlpro)."""
+    ds, ctx, did = problem
+    w0 = np.array([1.0, 1.0, 0.2, 1.5, 0.3])
+    ev = lambda P, lam: oracle.profile_batch(ds.coords, ds.y, ds.X, P, lam, reml=True)["logL"]
+    g = nv.fit_mle(ctx, did, w0, 0.8, kappa_fixed=True, kappa=1.0, reml=True)
+    o = nv.fit_mle_cb(ev, w0, 0.8, kappa_fixed=True, kappa=1.0)
+    assert g["logL"] == pytest.approx(o["logL"], abs=1e-6)
+    np.testing.assert_allclose(g["omega"], o["omega"], rtol=2e-3, atol=2e-3)
+    ml = nv.fit_mle(ctx, did, w0, 0.8, kappa_fixed=True, kappa=1.0)
+    assert ml["logL"] != pytest.approx(g["logL"], abs=1e-3)     # a different objective
