@@ -75,7 +75,7 @@ struct Layout {
     int nb = 0, q = 0, p = 0, M = 0, batch = 0;
     int64_t tpo = 0;
     size_t off_Bt = 0, off_sumlog = 0, off_oc = 0, off_coordT = 0, off_tab = 0, off_tiles = 0,
-           off_inv = 0, off_ldv = 0, off_pst = 0, total = 0;
+           off_inv = 0, off_ldv = 0, off_pst = 0, off_owner = 0, total = 0;
     // mixed precision only
     bool mixed = false;
     size_t img = 0, off_wimg = 0, off_pimg = 0, off_invsum = 0, off_flags = 0, off_idx = 0,
@@ -112,6 +112,7 @@ bool make_layout(int64_t n, int32_t p, int32_t M, int32_t batch, Layout &L, int 
     L.off_inv = take(sizeof(double) * (size_t)NT * batch);
     L.off_ldv = take(sizeof(double) * (size_t)batch);
     L.off_pst = take(sizeof(int) * (size_t)batch);
+    L.off_owner = take(sizeof(int) * (size_t)batch);
     if (precision == PLK_MIXED) {
         L.mixed = true;
         L.img = align_up(mixed_img_bytes(7));   // L_JJ^-1 image, sized for the 7-slice pass
@@ -251,6 +252,7 @@ static void sub_batch(const BatchArgs &b, const MixedArgs &x, int off, int cnt, 
     bo.inv = b.inv + (size_t)NT * off;
     bo.ldv = b.ldv + off;
     bo.pstatus = b.pstatus + off;
+    bo.owner = b.owner ? b.owner + off : nullptr;
     xo.wimg = x.wimg + mixed_img_bytes(5) * (size_t)off;   // slot stride of the 5-slice pass
     xo.pimg = x.pimg + mixed_slot_bytes() * (size_t)(b.nb + 1) * off;
     xo.invsum = x.invsum + off;
@@ -486,6 +488,7 @@ static plk_status run_eval(const plk_eval_args *a, int reml, int flags, const La
         b.inv = at<double>(ws, L.off_inv);
         b.ldv = at<double>(ws, L.off_ldv);
         b.pstatus = at<int>(ws, L.off_pst);
+        b.owner = at<int>(ws, L.off_owner);
         b.logL = a->logL;
         b.sigma2 = a->sigma2;
         b.beta = a->beta;
@@ -573,6 +576,7 @@ extern "C" plk_status plk_build_covariance_device(const double *coords, int64_t 
     b.inv = at<double>(workspace, L.off_inv);
     b.ldv = at<double>(workspace, L.off_ldv);
     b.pstatus = at<int>(workspace, L.off_pst);
+    b.owner = at<int>(workspace, L.off_owner);
     const FrontMode fm = mode == 0 ? FRONT_FP64 : (mode == 1 ? FRONT_DF_FAST : FRONT_DF);
     cudaError_t e = launch_covariance(b, fm, at<double>(workspace, L.off_sumlog) + 1, V,
                                       static_cast<cudaStream_t>(stream));
@@ -832,6 +836,7 @@ std::string run_item(Job *j, Item &it, cudaStream_t s) {
     b.inv = at<double>(it.ws, L.off_inv);
     b.ldv = at<double>(it.ws, L.off_ldv);
     b.pstatus = at<int>(it.ws, L.off_pst);
+    b.owner = at<int>(it.ws, L.off_owner);
     b.logL = j->d_logL;
     b.sigma2 = j->d_s2;
     b.beta = j->d_beta;

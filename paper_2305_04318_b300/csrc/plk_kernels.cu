@@ -231,6 +231,63 @@ __device__ double rho_integral(double u, double kap, double logc) {
     return exp(logc + kap * log(u) - u) * (h * sum);
 }
 
+// Table sharing: the rho table depends on the point only through kappa (and
+// log c_kappa, a function of kappa), so slots of a batch with the same kappa
+// read one table.  owner[w] = the smallest slot with the same kappa (bit
+// pattern) and a valid parameter row; an invalid row keeps its own.
+__global__ void __launch_bounds__(256) k_table_owner(int cnt, const double *__restrict__ oconst,
+                                                     const int *__restrict__ pstatus, int *__restrict__ owner) {
+    const int w = blockIdx.x;
+    __shared__ int best[8];
+    int b = w;
+    if (pstatus[w] == PLK_POINT_OK) {
+        const unsigned long long kw = (unsigned long long)__double_as_longlong(oconst[OC_N * (int64_t)w + OC_KAPPA]);
+        for (int v = threadIdx.x; v < w; v += blockDim.x)
+            if (pstatus[v] == PLK_POINT_OK &&
+                (unsigned long long)__double_as_longlong(oconst[OC_N * (int64_t)v + OC_KAPPA]) == kw) {
+                b = v;
+                break;   // v grows with the loop: the first match is this thread's smallest
+            }
+    }
+    for (int o = 16; o > 0; o >>= 1) b = min(b, __shfl_xor_sync(0xffffffffu, b, o));
+    if ((threadIdx.x & 31) == 0) best[threadIdx.x >> 5] = b;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int i = 1; i < (int)(blockDim.x >> 5); ++i) b = min(b, best[i]);
+        owner[w] = b;
+    }
+}
+
+// The owner's table covers the union of its sharers' octave ranges.
+__global__ void __launch_bounds__(256) k_table_union(int cnt, double *__restrict__ oconst, const int *__restrict__ owner) {
+    const int w = blockIdx.x;
+    if (owner[w] != w) return;
+    __shared__ int sl[8], sh[8];
+    int lo = (int)oconst[OC_N * (int64_t)w + OC_ELO], hi = (int)oconst[OC_N * (int64_t)w + OC_EHI];
+    for (int v = w + 1 + threadIdx.x; v < cnt; v += blockDim.x)
+        if (owner[v] == w) {
+            lo = min(lo, (int)oconst[OC_N * (int64_t)v + OC_ELO]);
+            hi = max(hi, (int)oconst[OC_N * (int64_t)v + OC_EHI]);
+        }
+    for (int o = 16; o > 0; o >>= 1) {
+        lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+        hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        sl[threadIdx.x >> 5] = lo;
+        sh[threadIdx.x >> 5] = hi;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int i = 1; i < (int)(blockDim.x >> 5); ++i) {
+            lo = min(lo, sl[i]);
+            hi = max(hi, sh[i]);
+        }
+        oconst[OC_N * (int64_t)w + OC_ELO] = lo;
+        oconst[OC_N * (int64_t)w + OC_EHI] = hi;
+    }
+}
+
 // Table builder: one block of 320 threads = 32 sub-intervals x TAB_NC Chebyshev nodes.
 // F32TAB writes each sub-interval's coefficients as TAB_F32 floats instead of
 // TAB_NC doubles: c_0..c_3 as double-float pairs, c_4..c_9 rounded to FP32
@@ -240,11 +297,12 @@ __device__ double rho_integral(double u, double kap, double logc) {
 // per node remains.
 template <bool F32TAB>
 __global__ void __launch_bounds__(320) k_matern_table(const double *__restrict__ oconst,
-                                                      double *__restrict__ tab) {
+                                                      double *__restrict__ tab, const int *__restrict__ owner) {
     __shared__ double E1[QNODES];   // cosh(t_k) - 1 = 2 sinh^2(t_k / 2)
     __shared__ double L2[QNODES];   // log cosh(kappa t_k)
     __shared__ double F[32][TAB_NC];
     const int w = blockIdx.y;
+    if (owner && owner[w] != w) return;   // this slot reads another slot's table (same kappa)
     const double *oc = oconst + OC_N * (int64_t)w;
     const double kap = oc[OC_KAPPA], logc = oc[OC_LOGC];
     const int elo = (int)oc[OC_ELO], ehi = (int)oc[OC_EHI];
@@ -378,7 +436,7 @@ __global__ void __launch_bounds__(256) k_build(int nb, int64_t n, int64_t n_pad,
                                                const double *__restrict__ oconst,
                                                const double *__restrict__ coordT,
                                                const double *__restrict__ tab,
-                                               const double *__restrict__ Bt) {
+                                               const double *__restrict__ Bt, const int *__restrict__ owner) {
     const int w = blockIdx.y;
     const int t = blockIdx.x;
     int I = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
@@ -411,10 +469,11 @@ __global__ void __launch_bounds__(256) k_build(int nb, int64_t n, int64_t n_pad,
     }
     const double *oc = oconst + OC_N * (int64_t)w;
     const double nug = oc[OC_NUG], kap = oc[OC_KAPPA], logc = oc[OC_LOGC];
-    const int elo = (int)oc[OC_ELO], ehi = (int)oc[OC_EHI];
+    const int ow = owner ? owner[w] : w;   // the table (and its octave range) of the slot that built it
+    const int elo = (int)oconst[OC_N * (int64_t)ow + OC_ELO], ehi = (int)oconst[OC_N * (int64_t)ow + OC_EHI];
     const double *ca = coordT + (int64_t)w * 2 * n_pad;
     const double *cb = ca + n_pad;
-    const double *tw = tab + (int64_t)w * TAB_SIZE;
+    const double *tw = tab + (int64_t)ow * TAB_SIZE;
     const double aj = ca[j], bj = cb[j];
     for (int r = r0; r < TB; r += 2) {
         const int64_t i = (int64_t)I * TB + r;
@@ -477,7 +536,7 @@ __global__ void __launch_bounds__(256) k_build_f32(int nb, int64_t n, int64_t n_
                                                    const double *__restrict__ oconst,
                                                    const double *__restrict__ coordT,
                                                    const double *__restrict__ tab,
-                                                   const double *__restrict__ Bt) {
+                                                   const double *__restrict__ Bt, const int *__restrict__ owner) {
     const int w = blockIdx.y;
     const int t = blockIdx.x;
     int I = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
@@ -503,11 +562,12 @@ __global__ void __launch_bounds__(256) k_build_f32(int nb, int64_t n, int64_t n_
     }
     const double *oc = oconst + OC_N * (int64_t)w;
     const double nug = oc[OC_NUG], kap = oc[OC_KAPPA], logc = oc[OC_LOGC];
-    const int elo = (int)oc[OC_ELO], ehi = (int)oc[OC_EHI];
+    const int ow = owner ? owner[w] : w;   // the table (and its octave range) of the slot that built it
+    const int elo = (int)oconst[OC_N * (int64_t)ow + OC_ELO], ehi = (int)oconst[OC_N * (int64_t)ow + OC_EHI];
     float dgh, dgl;   // 1 + nu^2
     split_df_bits(1.0 + nug, dgh, dgl);
     const float *cf = reinterpret_cast<const float *>(coordT + (int64_t)w * 2 * n_pad);
-    const float *tf = reinterpret_cast<const float *>(tab + (int64_t)w * TAB_SIZE);
+    const float *tf = reinterpret_cast<const float *>(tab + (int64_t)ow * TAB_SIZE);
     const float ajh = cf[j], ajl = cf[n_pad + j], bjh = cf[2 * n_pad + j], bjl = cf[3 * n_pad + j];
     for (int r = r0; r < TB; r += 2) {
         const int64_t i = (int64_t)I * TB + r;
@@ -920,18 +980,22 @@ cudaError_t launch_front(const BatchArgs &b, cudaStream_t s, FrontMode mode) {
     TIMED(KC_PREP, (k_omega_prep<<<cnt, 256, 0, s>>>(b.params, b.n, b.n_pad, b.coords, b.sumlogy, b.oconst,
                                                       b.coordT, b.ldv, b.pstatus, f32)));
     const dim3 tg((TAB_NBUCKET + 31) / 32, cnt), bg((unsigned)b.tpo, cnt);
+    if (b.owner) {   // slots with the same kappa share one table
+        k_table_owner<<<cnt, 256, 0, s>>>(cnt, b.oconst, b.pstatus, b.owner);
+        k_table_union<<<cnt, 256, 0, s>>>(cnt, b.oconst, b.owner);
+    }
     if (f32) {
-        TIMED(KC_TABLE, (k_matern_table<true><<<tg, 320, 0, s>>>(b.oconst, b.tab)));
+        TIMED(KC_TABLE, (k_matern_table<true><<<tg, 320, 0, s>>>(b.oconst, b.tab, b.owner)));
         TIMED(KC_BUILD, (k_build_f32<<<bg, 256, 0, s>>>(b.nb, b.n, b.n_pad, b.q, b.tpo, b.tiles, b.oconst,
-                                                         b.coordT, b.tab, b.Bt)));
+                                                         b.coordT, b.tab, b.Bt, b.owner)));
     } else {
-        TIMED(KC_TABLE, (k_matern_table<false><<<tg, 320, 0, s>>>(b.oconst, b.tab)));
+        TIMED(KC_TABLE, (k_matern_table<false><<<tg, 320, 0, s>>>(b.oconst, b.tab, b.owner)));
         if (mode == FRONT_DF)
             TIMED(KC_BUILD, (k_build<true><<<bg, 256, 0, s>>>(b.nb, b.n, b.n_pad, b.q, b.tpo, b.tiles, b.oconst,
-                                                               b.coordT, b.tab, b.Bt)));
+                                                               b.coordT, b.tab, b.Bt, b.owner)));
         else
             TIMED(KC_BUILD, (k_build<false><<<bg, 256, 0, s>>>(b.nb, b.n, b.n_pad, b.q, b.tpo, b.tiles, b.oconst,
-                                                                b.coordT, b.tab, b.Bt)));
+                                                                b.coordT, b.tab, b.Bt, b.owner)));
     }
     return cudaGetLastError();
 }

@@ -44,6 +44,7 @@ struct BatchArgs {
     KernelTimer *timer = nullptr;
     const int *out_index = nullptr;   // when set, batch slot w writes output row out_index[w]
     int32_t status_or = 0;            // bits OR-ed into every written status
+    int *owner = nullptr;             // count: slot whose rho table this slot reads (NULL: its own)
 };
 
 // Sets the calling thread's message returned by plk_last_error().

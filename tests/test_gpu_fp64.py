@@ -134,3 +134,26 @@ def test_mixed4000_full_size_fp64_sampled():
     o = oracle_eval(ds, P[idx], w.lambdas)
     compare({k: v[idx] for k, v in g.items()}, o, what="mixed4000 fp64")
     assert np.all(g["status"][:960] == 0)
+
+
+@pytest.mark.parametrize("precision", [nv.FP64, nv.MIXED])
+def test_shared_tables_match_single_point_batches(precision):
+    """Points of a batch with the same kappa share one rho table, built over
+    the union of their octave ranges (very different ranges and anisotropies
+    here); every point's results equal those of a batch of that point alone,
+    bit for bit, and the oracle's within the tolerance."""
+    ds = synth.aniso_dataset(71, 300, math.sqrt(30.0), 2)
+    rng = np.random.default_rng(71)
+    K = 24
+    P = synth.omega_from_unit(rng.uniform(size=(K, 5)))
+    P[:, 1] = np.array([0.5, 1.5, 2.5])[np.arange(K) % 3]     # three kappa values
+    P[::4, 0] = 0.05                                            # short and long ranges share a table
+    P[1::4, 0] = 40.0
+    lams = synth.LAMBDA_GRID_9
+    a = gpu_eval(ds, P, lams, precision=precision, batch=K)
+    for k in range(0, K, 5):
+        b = gpu_eval(ds, P[k:k + 1], lams, precision=precision, batch=1)
+        for key in ("logL", "sigma2", "beta", "logdet", "status"):
+            np.testing.assert_array_equal(a[key][k:k + 1], b[key], err_msg=f"point {k} {key}")
+    if precision == nv.FP64:
+        compare(a, oracle_eval(ds, P, lams), what="shared tables")
