@@ -81,6 +81,8 @@ def parse():
                     help="serving: grid values of the profiled parameter (the full job: 64)")
     ap.add_argument("--job-sub", type=int, default=2,
                     help="serving: sub-grid values of each other parameter (the full job: 4)")
+    ap.add_argument("--serve-batch", type=int, default=16, help="serving: points per scheduled batch")
+    ap.add_argument("--capacity-jobs", type=int, default=6, help="serving: jobs run one after another for the capacity")
     ap.add_argument("--streams", type=int, default=4, help="uneven/serving: scheduler streams")
     ap.add_argument("--graph", type=int, default=0,
                     help="uneven: launch batches as CUDA graphs (1) or eagerly (0, default: measured faster)")
@@ -331,7 +333,7 @@ def run_serving(args):
     prec = nv.MIXED if args.precision in ("auto", "mixed") else nv.FP64
     rng = np.random.default_rng(55)
     grids = [synth.profile_job_grid(which, G=G, sub=sub) for which in range(5)]
-    arena_bytes = int(args.streams * nv.workspace_bytes(8000, 3, 9, 16, prec) * 1.1 + (4 << 30))
+    arena_bytes = int(args.streams * nv.workspace_bytes(8000, 3, 9, args.serve_batch, prec) * 1.1 + (4 << 30))
     arena = torch.empty((arena_bytes,), dtype=torch.uint8, device="cuda")
     results = {}
     with nv.Context(arena_bytes, arena=arena, n_streams=args.streams) as ctx:
@@ -350,10 +352,10 @@ def run_serving(args):
 
         # capacity: jobs one after another
         t0 = time.perf_counter()
-        cap_jobs = 6
+        cap_jobs = args.capacity_jobs
         for k in range(cap_jobs):
             d_i, which = job_spec(k)
-            jb = ctx.submit(ids[d_i], grids[which][1], lam, precision=prec, batch=16)
+            jb = ctx.submit(ids[d_i], grids[which][1], lam, precision=prec, batch=args.serve_batch)
             finish(jb, d_i, which)
         cap = cap_jobs / (time.perf_counter() - t0)
         levels = {}
@@ -369,7 +371,7 @@ def run_serving(args):
                 now = time.perf_counter() - t0
                 while k < args.jobs and arrivals[k] <= now:
                     d_i, which = job_spec(k)
-                    jb = ctx.submit(ids[d_i], grids[which][1], lam, precision=prec, batch=16)
+                    jb = ctx.submit(ids[d_i], grids[which][1], lam, precision=prec, batch=args.serve_batch)
                     pending.append((jb, d_i, which, t0 + arrivals[k]))
                     k += 1
                 still = []
@@ -397,7 +399,8 @@ def run_serving(args):
             "config": {"workload": f"serving: {D} resident datasets, n log-uniform in [500,8000], p=3; job = one "
                                    f"parameter's {G}-point profile x {sub}^4 sub-grid x 9 lambdas ({G * sub ** 4} omega), "
                                    "then profile max + 95% CI on the device; Poisson arrivals",
-                       "precision": "mixed" if prec == nv.MIXED else "fp64", "streams": args.streams},
+                       "precision": "mixed" if prec == nv.MIXED else "fp64", "streams": args.streams,
+                       "batch_per_item": args.serve_batch},
             "capacity_jobs_per_s": cap, "levels": levels, "hbm_high_water_gb": high / 1e9,
             "latency_ms": {"p50": top["p50_ms"], "p99": top["p99_ms"], "what": "job latency at offered load 0.9"}}
     print(json.dumps(line), flush=True)
