@@ -525,8 +525,10 @@ __device__ __forceinline__ void df_horner_step(float &ph, float &pl, float th, f
     ph = s;
     pl = __fadd_rn(__fadd_rn(es, ex), cl);
 }
+// (volatile: the load must not be moved ahead of the range checks that guard
+// its address)
 __device__ __forceinline__ void ldg_v8(const float *p, float (&v)[8]) {   // 32-byte aligned
-    asm("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+    asm volatile("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
                  : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]), "=f"(v[7])
                  : "l"(p));
 }
