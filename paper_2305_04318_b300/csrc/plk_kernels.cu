@@ -305,6 +305,9 @@ __global__ void __launch_bounds__(320) k_matern_table(const double *__restrict__
     __shared__ double E1[QNODES];   // cosh(t_k) - 1 = 2 sinh^2(t_k / 2)
     __shared__ double L2[QNODES];   // log cosh(kappa t_k)
     __shared__ double F[32][TAB_NC];
+    __shared__ double A[32][TAB_NC];          // Chebyshev coefficients per bucket
+    __shared__ double CT[TAB_NC][TAB_NC];     // cos(pi k (m + 1/2) / NC)
+    __shared__ double TM[TAB_NC][TAB_NC];     // T_k(t) = sum_m TM[k][m] t^m
     const int w = blockIdx.y;
     if (owner && owner[w] != w) return;   // this slot reads another slot's table (same kappa)
     const double *oc = oconst + OC_N * (int64_t)w;
@@ -315,6 +318,7 @@ __global__ void __launch_bounds__(320) k_matern_table(const double *__restrict__
         const int e0 = TAB_ELO + (bx * 32) / TAB_S, e1 = TAB_ELO + (bx * 32 + 31) / TAB_S;
         if (e1 < elo || e0 >= ehi) return;   // none of them is read
     }
+    const double PI = 3.14159265358979323846;
     for (int k = threadIdx.x; k < QNODES; k += blockDim.x) {
         const double t = k * QH;
         const double sh = sinh(0.5 * t);
@@ -322,27 +326,49 @@ __global__ void __launch_bounds__(320) k_matern_table(const double *__restrict__
         const double kt = kap * t;
         L2[k] = kt + log1p(exp(-2.0 * kt)) - 0.69314718055994530942;
     }
+    if (threadIdx.x < TAB_NC * TAB_NC) {
+        const int k = threadIdx.x / TAB_NC, m = threadIdx.x % TAB_NC;
+        CT[k][m] = cos(PI * k * (m + 0.5) / TAB_NC);
+    }
+    if (threadIdx.x == 0) {   // T_0 = 1, T_1 = t, T_k = 2 t T_{k-1} - T_{k-2} (small integers)
+        for (int k = 0; k < TAB_NC; ++k)
+            for (int m = 0; m < TAB_NC; ++m)
+                TM[k][m] = k == 0 ? (m == 0 ? 1.0 : 0.0)
+                         : k == 1 ? (m == 1 ? 1.0 : 0.0)
+                                  : (m > 0 ? 2.0 * TM[k - 1][m - 1] : 0.0) - TM[k - 2][m];
+    }
     __syncthreads();
     const int lb = threadIdx.x / TAB_NC, l = threadIdx.x % TAB_NC;
     const int bucket = blockIdx.x * 32 + lb;
-    const double PI = 3.14159265358979323846;
     const int eb = TAB_ELO + bucket / TAB_S;
     const bool used = bucket < TAB_NBUCKET && eb >= elo && eb < ehi;
     if (used) {
         const int e = TAB_ELO + bucket / TAB_S, j = bucket % TAB_S;
-        const double tl = cos(PI * (l + 0.5) / TAB_NC);
+        const double tl = CT[1][l];   // cos(pi (l + 1/2) / NC): the Chebyshev node
         const double wv = ldexp(1.0 + (j + 0.5 * (tl + 1.0)) / TAB_S, e);
         const double u = sqrt(wv);
         double r;
         if (kap != kap || !(kap > 0.0)) {
             r = nan("");
         } else if (u <= TAB_USPLIT) {
+            // the terms of four nodes are computed ahead (independent exps),
+            // then added in order with the same stopping rule
             double sum = 0.5, prev = 1.0;
-            for (int k = 1; k < QNODES; ++k) {
-                const double g = exp(L2[k] - u * E1[k]);
-                sum += g;
-                if (g < prev && g < 1e-18 * sum) break;
-                prev = g;
+            bool stop = false;
+            for (int k = 1; k < QNODES && !stop; k += 4) {
+                double g[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) g[i] = (k + i < QNODES) ? exp(L2[k + i] - u * E1[k + i]) : 0.0;
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    if (stop || k + i >= QNODES) {
+                        stop = true;
+                        continue;
+                    }
+                    sum += g[i];
+                    if (g[i] < prev && g[i] < 1e-18 * sum) stop = true;
+                    prev = g[i];
+                }
             }
             r = exp(logc + kap * log(u) - u) * (QH * sum);
         } else {
@@ -351,41 +377,30 @@ __global__ void __launch_bounds__(320) k_matern_table(const double *__restrict__
         F[lb][l] = r;
     }
     __syncthreads();
-    if (l == 0 && used) {
-        // Chebyshev coefficients a_k, then monomial coefficients in t.
-        double a[TAB_NC], c[TAB_NC], Tp[TAB_NC], Tc[TAB_NC], Tn[TAB_NC];
-        for (int k = 0; k < TAB_NC; ++k) {
-            double s = 0.0;
-            for (int m = 0; m < TAB_NC; ++m) s += F[lb][m] * cos(PI * k * (m + 0.5) / TAB_NC);
-            a[k] = (k == 0 ? 1.0 : 2.0) * s / TAB_NC;
-            c[k] = 0.0;
-            Tp[k] = 0.0;
-            Tc[k] = 0.0;
-        }
-        Tp[0] = 1.0;          // T_0
-        Tc[1] = 1.0;          // T_1
-        c[0] += a[0];
-        c[1] += a[1];
-        for (int k = 2; k < TAB_NC; ++k) {
-            for (int m = 0; m < TAB_NC; ++m) Tn[m] = (m > 0 ? 2.0 * Tc[m - 1] : 0.0) - Tp[m];
-            for (int m = 0; m < TAB_NC; ++m) {
-                c[m] += a[k] * Tn[m];
-                Tp[m] = Tc[m];
-                Tc[m] = Tn[m];
-            }
-        }
+    // Chebyshev coefficient a_l of the bucket's interpolant (thread l), then the
+    // monomial coefficient c_l of t^l (thread l)
+    if (used) {
+        double s2 = 0.0;
+        for (int m = 0; m < TAB_NC; ++m) s2 += F[lb][m] * CT[l][m];
+        A[lb][l] = (l == 0 ? 1.0 : 2.0) * s2 / TAB_NC;
+    }
+    __syncthreads();
+    if (used) {
+        double c = 0.0;
+        for (int k = 0; k < TAB_NC; ++k) c += A[lb][k] * TM[k][l];
         if (F32TAB) {
             float *dst = reinterpret_cast<float *>(tab + (int64_t)w * TAB_SIZE) + (int64_t)bucket * TAB_F32;
-            for (int m = 0; m < TAB_DF; ++m) {
-                const float h = __double2float_rn(c[m]);
-                dst[2 * m] = h;
-                dst[2 * m + 1] = __double2float_rn(c[m] - (double)h);
+            if (l < TAB_DF) {
+                const float h = __double2float_rn(c);
+                dst[2 * l] = h;
+                dst[2 * l + 1] = __double2float_rn(c - (double)h);
+            } else {
+                dst[TAB_DF + l] = __double2float_rn(c);
             }
-            for (int m = TAB_DF; m < TAB_NC; ++m) dst[TAB_DF + m] = __double2float_rn(c[m]);
-            for (int m = TAB_DF + TAB_NC; m < TAB_F32; ++m) dst[m] = 0.0f;
+            if (l == 0)
+                for (int m = TAB_DF + TAB_NC; m < TAB_F32; ++m) dst[m] = 0.0f;
         } else {
-            double *dst = tab + (int64_t)w * TAB_SIZE + (int64_t)bucket * TAB_NC;
-            for (int m = 0; m < TAB_NC; ++m) dst[m] = c[m];
+            tab[(int64_t)w * TAB_SIZE + (int64_t)bucket * TAB_NC + l] = c;
         }
     }
 }
