@@ -392,6 +392,17 @@ plk_status plk_quadratic_cloud_cb(plk_eval_fn fn, void *user, const double *omeg
                                   const plk_cloud_options *opts, double *params_out, int64_t capacity,
                                   int64_t *K_out, double *lambdas_out, double *hessian_out, double *eig_out);
 
+/* Failure-detection self-test (the paper has no counterpart).  Every wait of
+ * the tensor-core kernels on an mbarrier is bounded: when it gives up, the
+ * kernel sets a device error flag, drains its own work and returns, and the
+ * host call reports PLK_E_TIMEOUT with the device still usable.  This call
+ * runs one block that waits, with the same bounded wait limited to max_iter
+ * tries (1 .. 1e6; each try takes well under a microsecond), on a barrier that
+ * nothing completes, so it always gives up: the expected result is
+ * PLK_E_TIMEOUT.  Blocking on `stream`.  PLK_E_INVALID for max_iter outside
+ * its range, PLK_E_CUDA for a CUDA error. */
+plk_status plk_selftest_bounded_wait(int32_t max_iter, void *stream);
+
 /* Message describing the last error of the calling thread ("" if none). */
 const char *plk_last_error(void);
 

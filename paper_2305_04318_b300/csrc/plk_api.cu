@@ -1257,3 +1257,23 @@ extern "C" plk_status plk_scheduled_batch(plk_ctx *c, int64_t n, int32_t precisi
     if (tuned) *tuned = t;
     return PLK_OK;
 }
+
+// ---------------------------------------------------------------------------
+// failure detection self-test
+// ---------------------------------------------------------------------------
+static __device__ int g_selftest_err;
+
+extern "C" plk_status plk_selftest_bounded_wait(int32_t max_iter, void *stream) {
+    if (max_iter < 1 || max_iter > 1000000) return fail(PLK_E_INVALID, "max_iter must be in [1, 1e6]");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int *err = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(reinterpret_cast<void **>(&err), g_selftest_err);
+    if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, sizeof(int), s);
+    if (e == cudaSuccess) e = launch_wait_selftest((uint32_t)max_iter, err, s);
+    int h = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "bounded-wait self-test");
+    if (h) return fail(PLK_E_TIMEOUT, "a bounded device wait gave up after %d tries (self-test)", max_iter);
+    return PLK_OK;
+}

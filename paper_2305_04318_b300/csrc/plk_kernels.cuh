@@ -80,6 +80,8 @@ cudaError_t launch_mixed_batch(const BatchArgs &b, const MixedArgs &x, int S, cu
 // the batch after launch_front(b, s, FRONT_DF or FRONT_DF_FAST): factorisation, closed form, error bound
 cudaError_t launch_mixed_back(const BatchArgs &b, const MixedArgs &x, int S, cudaStream_t s);
 cudaError_t launch_gather_params(int count, const int *idx, const double *params, double *out, cudaStream_t s);
+// one block whose bounded wait on a barrier that nothing completes gives up and sets *err
+cudaError_t launch_wait_selftest(uint32_t max_iter, int *err, cudaStream_t s);
 cudaError_t launch_scatter_value(int count, const int *idx, double v, double *out, cudaStream_t s);
 
 cudaError_t launch_profile_max(const double *vals, int64_t G, int64_t SM, double *prof,

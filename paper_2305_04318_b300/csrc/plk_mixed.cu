@@ -1366,6 +1366,24 @@ cudaError_t launch_mixed_back(const BatchArgs &b, const MixedArgs &x, int S, cud
     return cudaGetLastError();
 }
 
+// Self-test of the bounded waits: thread 0 waits on a barrier that nothing
+// completes, with the same bounded wait the tensor-core kernels use; when it
+// gives up, the kernel records the failure in *err and returns.
+__global__ void k_wait_selftest(uint32_t max_iter, int *err) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        tc::mbar_init(&bar, 1);
+        tc::fence_mbar_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && !tc::mbar_wait(&bar, 0, max_iter)) atomicExch(err, 1);
+}
+
+cudaError_t launch_wait_selftest(uint32_t max_iter, int *err, cudaStream_t s) {
+    k_wait_selftest<<<1, 32, 0, s>>>(max_iter, err);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_scatter_value(int count, const int *idx, double v, double *out, cudaStream_t s) {
     k_scatter_value<<<(count + 127) / 128, 128, 0, s>>>(count, idx, v, out);
     return cudaGetLastError();

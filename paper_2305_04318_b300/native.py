@@ -118,6 +118,7 @@ def lib():
         "plk_quadratic_cloud_cb": (C.c_int, [EVAL_FN, vp, vp, dbl, C.POINTER(CloudOptions), vp, i64,
                                              C.POINTER(i64), vp, vp, vp]),
         "plk_kernel_class_name": (C.c_char_p, [i32]),
+        "plk_selftest_bounded_wait": (C.c_int, [i32, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -238,6 +239,12 @@ def build_covariance_device(coords, params, mode=BUILD_FP64, workspace=None, str
 
 
 STATIC_SCRATCH_BYTES = 64 << 20
+
+
+def selftest_bounded_wait(max_iter=1000, stream=None):
+    """Run the bounded-wait self-test (plk_selftest_bounded_wait); returns the
+    status (PLK_E_TIMEOUT expected) without raising."""
+    return int(lib().plk_selftest_bounded_wait(int(max_iter), _stream_handle(stream)))
 
 
 def eval_device_static(coords, y, X, lambdas, params, reml=False, stream=None, outputs=None):

@@ -100,3 +100,21 @@ def test_autotuned_batch_is_used_and_results_unchanged(precision):
         for k in ("logL", "sigma2", "beta", "logdet", "status"):
             np.testing.assert_array_equal(tuned[k], explicit[k], err_msg=k)
         ctx.release_dataset(d)
+
+
+def test_bounded_wait_gives_up_and_device_stays_usable():
+    """Failure detection without a fault: a bounded wait on a barrier that
+    nothing completes gives up, the call reports PLK_E_TIMEOUT, and the device
+    keeps working (an evaluation right after matches the oracle)."""
+    import oracle
+    assert nv.selftest_bounded_wait(1000) == nv.PLK_E_TIMEOUT
+    assert nv.selftest_bounded_wait(50) == nv.PLK_E_TIMEOUT
+    with pytest.raises(nv.PlkError):
+        nv._check(nv.lib().plk_selftest_bounded_wait(0, None))
+    ds = synth.aniso_dataset(62, 140, math.sqrt(14.0), 2)
+    P = synth.omega_from_unit(np.random.default_rng(62).uniform(size=(6, 5)))
+    lams = synth.LAMBDA_GRID_9
+    g = gpu_eval(ds, P, lams, precision=nv.MIXED)
+    o = oracle.profile_batch(ds.coords, ds.y, ds.X, P, lams)
+    ok = o["status"] == 0
+    assert np.max(np.abs(g["logL"][ok] - o["logL"][ok])) <= 1e-3
