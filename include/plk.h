@@ -399,8 +399,9 @@ plk_status plk_quadratic_cloud_cb(plk_eval_fn fn, void *user, const double *omeg
  * runs one block that waits, with the same bounded wait limited to max_iter
  * tries (1 .. 1e6; each try takes well under a microsecond), on a barrier that
  * nothing completes, so it always gives up: the expected result is
- * PLK_E_TIMEOUT.  Blocking on `stream`.  PLK_E_INVALID for max_iter outside
- * its range, PLK_E_CUDA for a CUDA error. */
+ * PLK_E_TIMEOUT.  Blocking on `stream`; concurrent calls share one device
+ * flag (run them one at a time).  PLK_E_INVALID for max_iter outside its
+ * range, PLK_E_CUDA for a CUDA error. */
 plk_status plk_selftest_bounded_wait(int32_t max_iter, void *stream);
 
 /* Message describing the last error of the calling thread ("" if none). */
