@@ -427,6 +427,17 @@ plk_status plk_profile_max_device(const double *vals, int64_t G, int64_t SM, dou
 plk_status plk_profile_ci_device(const double *grid, const double *prof, int64_t G, double level,
                                  double *out, void *stream);
 
+/* The same likelihood CI (Section 2.2, eq. likelihood) for a caller holding the
+ * grid and the profile in host memory: grid and profile_logL host arrays of G
+ * values; outputs (host) lo, hi, argmax (the grid value at the maximum) and
+ * censored (bit 1 lower, bit 2 upper), any of them may be NULL.  The CI is
+ * computed by the device kernel behind plk_profile_ci_device: the call copies
+ * the G values to the current device (allocating 8 (2G + 4) bytes there for
+ * the call) and blocks until the result is back.  Errors: PLK_E_INVALID (G < 1,
+ * NULL input, level outside (0, 1)), PLK_E_CUDA. */
+plk_status plk_profile_ci(const double *grid, const double *profile_logL, int64_t G, double level, double *lo,
+                          double *hi, double *argmax, int32_t *censored);
+
 /* chi2_1 quantile used by the CI: c with P(chi2_1 <= c) = level. */
 double plk_chi2_1_quantile(double level);
 

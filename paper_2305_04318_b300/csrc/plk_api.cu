@@ -622,6 +622,27 @@ extern "C" plk_status plk_profile_ci_device(const double *grid, const double *pr
     return e == cudaSuccess ? PLK_OK : cuda_fail(e, "profile_ci");
 }
 
+extern "C" plk_status plk_profile_ci(const double *grid, const double *profile_logL, int64_t G, double level,
+                                     double *lo, double *hi, double *argmax, int32_t *censored) {
+    if (G < 1 || !grid || !profile_logL || !(level > 0.0 && level < 1.0))
+        return fail(PLK_E_INVALID, "bad profile_ci args");
+    double *d = nullptr;
+    cudaError_t e = cudaMalloc(&d, sizeof(double) * (2 * (size_t)G + 4));
+    if (e != cudaSuccess) return cuda_fail(e, "profile_ci cudaMalloc");
+    double out[4];
+    e = cudaMemcpy(d, grid, sizeof(double) * G, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(d + G, profile_logL, sizeof(double) * G, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = launch_profile_ci(d, d + G, G, 0.5 * plk_chi2_1_quantile(level), d + 2 * G, nullptr);
+    if (e == cudaSuccess) e = cudaMemcpy(out, d + 2 * G, sizeof out, cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    if (e != cudaSuccess) return cuda_fail(e, "profile_ci");
+    if (lo) *lo = out[0];
+    if (hi) *hi = out[1];
+    if (argmax) *argmax = out[2];
+    if (censored) *censored = out[3] == out[3] ? (int32_t)out[3] : 0;
+    return PLK_OK;
+}
+
 // ---------------------------------------------------------------------------
 // context API
 // ---------------------------------------------------------------------------

@@ -96,6 +96,8 @@ def lib():
         "plk_last_error": (C.c_char_p, []),
         "plk_profile_max_device": (C.c_int, [vp, i64, i64, vp, vp]),
         "plk_profile_ci_device": (C.c_int, [vp, vp, i64, dbl, vp, vp]),
+        "plk_profile_ci": (C.c_int, [vp, vp, i64, dbl, C.POINTER(dbl), C.POINTER(dbl), C.POINTER(dbl),
+                                     C.POINTER(i32)]),
         "plk_chi2_1_quantile": (dbl, [dbl]),
         "plk_profile_beta_device": (C.c_int, [C.POINTER(StatsArgs), i32, vp, i64, vp, vp]),
         "plk_profile_sigma_device": (C.c_int, [C.POINTER(StatsArgs), vp, i64, vp, vp]),
@@ -289,6 +291,16 @@ def profile_ci_device(grid, prof, level=0.95, out=None, stream=None):
     _check(lib().plk_profile_ci_device(_ptr(grid), _ptr(prof), grid.shape[0], float(level), _ptr(out),
                                        _stream_handle(stream)))
     return out
+
+
+def profile_ci(grid, prof, level=0.95):
+    """Likelihood CI from host arrays (plk_profile_ci): dict(lo, hi, argmax, censored)."""
+    g = np.ascontiguousarray(grid, dtype=np.float64)
+    v = np.ascontiguousarray(prof, dtype=np.float64)
+    lo, hi, am, cens = C.c_double(), C.c_double(), C.c_double(), C.c_int32()
+    _check(lib().plk_profile_ci(_np_ptr(g), _np_ptr(v), g.shape[0], float(level), C.byref(lo), C.byref(hi),
+                                C.byref(am), C.byref(cens)))
+    return dict(lo=lo.value, hi=hi.value, argmax=am.value, censored=cens.value)
 
 
 def chi2_1_quantile(level):

@@ -213,3 +213,22 @@ def test_end_to_end_profiles(precision):
     out, _ = nv.profile_hull_device(dev[4][:, 1:], vmax, to_dev(xq), x_stride=5)
     ref, _, _ = oracle.profile_hull(P[:, 1], oracle.profile_max(o["logL"]), xq)
     assert np.max(np.abs(out.cpu().numpy() - ref)) <= (tol * np.abs(ref).max() if precision == nv.FP64 else tol)
+
+
+def test_profile_ci_host_arrays_match_oracle():
+    """plk_profile_ci (host arrays, device kernel) against the oracle's CI:
+    an exactly quadratic profile (endpoints theta0 +- s sqrt(chi2_1)), a
+    profile censored on both sides, and NaN entries."""
+    import oracle
+    grid = np.linspace(-3.0, 5.0, 81)
+    prof = -(grid - 1.0) ** 2 / (2 * 0.7 ** 2)
+    prof[[3, 50]] = np.nan
+    for g, v in ((grid, prof), (grid, 0.01 * prof)):
+        r = nv.profile_ci(g, v, 0.95)
+        o = oracle.profile_ci(g, v, 0.95)
+        for k in ("lo", "hi", "argmax"):
+            assert r[k] == pytest.approx(o[k], abs=1e-12), k
+        assert r["censored"] == o["censored"]
+    assert nv.profile_ci(grid, 0.01 * prof, 0.95)["censored"] == 3
+    with pytest.raises(nv.PlkError):
+        nv.profile_ci(grid, prof, 1.5)
