@@ -644,16 +644,30 @@ __global__ void __launch_bounds__(NTH, 1) k_trsm_split(int J, int nb, int64_t tp
         for (int c0 = 0; c0 < 32; c0 += 16) {
             uint32_t p0[16], p1[16], p2[16], p3[16];
             load_groups(tb, warp, c0, p0, p1, p2, p3);
+            // eight columns (one 16-byte chunk of the row) per slice and store:
+            // the warp's 32 rows at one chunk hit 32 distinct banks per 8 lanes
 #pragma unroll
-            for (int c = 0; c < 16; c += 2) {
-                float m[2][S];
+            for (int c8 = 0; c8 < 16; c8 += 8) {
+                uint32_t pk2[S][4];
 #pragma unroll
-                for (int u = 0; u < 2; ++u) {
-                    float hi, lo;
-                    group_value(p0[c + u], p1[c + u], p2[c + u], p3[c + u], sEA[r] + sEW[cb + c0 + c + u] - 14, hi, lo);
-                    slice_df<S>(hi, lo, eo, m[u]);
+                for (int c = 0; c < 8; c += 2) {
+                    float m[2][S];
+#pragma unroll
+                    for (int u = 0; u < 2; ++u) {
+                        float hi, lo;
+                        const int cc = c8 + c + u;
+                        group_value(p0[cc], p1[cc], p2[cc], p3[cc], sEA[r] + sEW[cb + c0 + cc] - 14, hi, lo);
+                        slice_df<S>(hi, lo, eo, m[u]);
+                    }
+#pragma unroll
+                    for (int j = 0; j < S; ++j) pk2[j][c >> 1] = pack_bf16x2(m[0][j], m[1][j]);
                 }
-                store_pair<S>(sbase, r, cb + c0 + c, m[0], m[1]);
+                const int k = cb + c0 + c8;
+                const uint32_t off = tc::sw128_offset(r, k & 63);
+#pragma unroll
+                for (int j = 0; j < S; ++j)
+                    *reinterpret_cast<uint4 *>(sbase + (size_t)(j * 2 + (k >> 6)) * SBLK + off) =
+                        make_uint4(pk2[j][0], pk2[j][1], pk2[j][2], pk2[j][3]);
             }
         }
     }
