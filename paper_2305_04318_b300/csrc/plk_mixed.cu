@@ -76,15 +76,36 @@ template <int S>
 __device__ __forceinline__ void slice_df(float hi, float lo, int e, float (&m)[S]) {
     const float sc = pow2f(7 - e);
     float th = hi * sc, tl = lo * sc;
+    if constexpr (S == 5) {
+        // Digits 0-2 from the high part alone (r - rint(r) and the scaling by
+        // 256 are exact, |r| <= 128); the low part then joins the residual
+        // with one rounding (at most 2^-17 of a unit of digit 3, 1/256 of the
+        // last digit's own truncation), and digits 3-4 follow.  Digits 0-2 stay
+        // within +-128 (their groups are exact in the accumulators); digit 3
+        // may reach +-192, still exact in bf16, and only enters groups >= 3,
+        // which share a rounded accumulator anyway.
+        float r = th;
 #pragma unroll
-    for (int j = 0; j < S; ++j) {
-        const float mi = rintf(th);
-        m[j] = mi * pow2f(-8 * j);
-        const float r = __fsub_rn(th, mi);
-        float s_, e_;
-        two_sum(r, tl, s_, e_);
-        th = s_ * 256.0f;
-        tl = e_ * 256.0f;
+        for (int j = 0; j < 3; ++j) {
+            const float mi = rintf(r);
+            m[j] = mi * pow2f(-8 * j);
+            r = __fmul_rn(__fsub_rn(r, mi), 256.0f);
+        }
+        r = __fmaf_rn(tl, 16777216.0f, r);   // + tl 2^24
+        const float m3 = rintf(r);
+        m[3] = m3 * pow2f(-24);
+        m[4] = rintf(__fmul_rn(__fsub_rn(r, m3), 256.0f)) * pow2f(-32);
+    } else {
+#pragma unroll
+        for (int j = 0; j < S; ++j) {
+            const float mi = rintf(th);
+            m[j] = mi * pow2f(-8 * j);
+            const float r = __fsub_rn(th, mi);
+            float s_, e_;
+            two_sum(r, tl, s_, e_);
+            th = s_ * 256.0f;
+            tl = e_ * 256.0f;
+        }
     }
 }
 
