@@ -70,6 +70,23 @@ __device__ __forceinline__ void df_add(float &hi, float &lo, float x) {
     lo = __fsub_rn(e, __fsub_rn(hi, s));
 }
 
+// (acc_h, acc_l) += x y for double-float x, y (x_lo y_lo dropped; acc_l not
+// renormalised until df_norm)
+__device__ __forceinline__ void df_fma_acc(float &ah, float &al, float2 x, float2 y) {
+    const float p = __fmul_rn(x.x, y.x);
+    float e = __fmaf_rn(x.x, y.x, -p);
+    e = __fmaf_rn(x.x, y.y, e);
+    e = __fmaf_rn(x.y, y.x, e);
+    float s, es;
+    two_sum(ah, p, s, es);
+    ah = s;
+    al = __fadd_rn(al, __fadd_rn(es, e));
+}
+__device__ __forceinline__ float2 df_norm(float h, float l) {
+    const float s = __fadd_rn(h, l);
+    return make_float2(s, __fsub_rn(l, __fsub_rn(s, h)));
+}
+
 // The S slice values m_j 2^(-8j) of the double-float value (hi, lo) of a row with
 // exponent e.
 template <int S>
@@ -368,69 +385,152 @@ __global__ void __launch_bounds__(256, 2) k_potrf_mixed(int J, int64_t tpo, doub
         }
     }
     __syncthreads();
-    for (int c = 2; c >= 0; --c) {   // off-diagonal blocks of block column c, in 4 x 4 register tiles
-        const int nres = 3 - c;
-        for (int u = tid; u < nres * 64; u += 256) {   // sums: T_bc = sum_d W_bd L_dc
-            const int b = c + 1 + u / 64, bl = u & 63;
-            const int i0 = 4 * (bl >> 3), k0 = 4 * (bl & 7);
-            double acc[4][4];
+    if constexpr (S == 5) {
+        // 5 slices keep ~40 bits of L_JJ^-1: the off-diagonal blocks of the
+        // inverse (most of its work) run in double-float FP32 arithmetic
+        // (~2^-46 per product, FP32 issues at 68x the FP64 rate), from the FP64
+        // factor and diagonal-block inverses converted in place
+        float2 *P2 = reinterpret_cast<float2 *>(P);
+        float2 *Tm2 = reinterpret_cast<float2 *>(Tm);
+        for (int e = tid; e < PK; e += 256) {
+            const double x = P[e];
+            const float h = __double2float_rn(x);
+            P2[e] = make_float2(h, __double2float_rn(x - (double)h));
+        }
+        __syncthreads();
+        const float2 z2 = make_float2(0.0f, 0.0f);
+        for (int c = 2; c >= 0; --c) {
+            const int nres = 3 - c;
+            for (int u = tid; u < nres * 64; u += 256) {   // sums: T_bc = sum_d W_bd L_dc
+                const int b = c + 1 + u / 64, bl = u & 63;
+                const int i0 = 4 * (bl >> 3), k0 = 4 * (bl & 7);
+                float ah[4][4], al[4][4];
 #pragma unroll
-            for (int r = 0; r < 4; ++r)
+                for (int r = 0; r < 4; ++r)
 #pragma unroll
-                for (int cc = 0; cc < 4; ++cc) acc[r][cc] = 0.0;
-            int ra[4];
+                    for (int cc = 0; cc < 4; ++cc) ah[r][cc] = al[r][cc] = 0.0f;
+                int ra[4];
 #pragma unroll
-            for (int r = 0; r < 4; ++r) ra[r] = pk(DB * b + i0 + r, 0);
-            for (int d = c + 1; d <= b; ++d) {
-                const bool diag = (d == b);   // W_bb is lower triangular
-                const int qend = diag ? i0 + 3 : DB - 1;
-                for (int q = 0; q <= qend; ++q) {
+                for (int r = 0; r < 4; ++r) ra[r] = pk(DB * b + i0 + r, 0);
+                for (int d = c + 1; d <= b; ++d) {
+                    const bool diag = (d == b);
+                    const int qend = diag ? i0 + 3 : DB - 1;
+                    for (int q = 0; q <= qend; ++q) {
+                        float2 x[4], y[4];
+                        const int rq = pk(DB * d + q, 0) + DB * c + k0;
+#pragma unroll
+                        for (int r = 0; r < 4; ++r) x[r] = (diag && q > i0 + r) ? z2 : P2[ra[r] + DB * d + q];
+#pragma unroll
+                        for (int cc = 0; cc < 4; ++cc) y[cc] = P2[rq + cc];
+#pragma unroll
+                        for (int r = 0; r < 4; ++r)
+#pragma unroll
+                            for (int cc = 0; cc < 4; ++cc) df_fma_acc(ah[r][cc], al[r][cc], x[r], y[cc]);
+                    }
+                }
+                float2 *Tb = Tm2 + (b - c - 1) * DB * DB;
+#pragma unroll
+                for (int r = 0; r < 4; ++r)
+#pragma unroll
+                    for (int cc = 0; cc < 4; ++cc) Tb[(i0 + r) * DB + k0 + cc] = df_norm(ah[r][cc], al[r][cc]);
+            }
+            __syncthreads();
+            for (int u = tid; u < nres * 64; u += 256) {   // W_bc = -T_bc W_cc
+                const int b = c + 1 + u / 64, bl = u & 63;
+                const int i0 = 4 * (bl >> 3), k0 = 4 * (bl & 7);
+                const float2 *Tb = Tm2 + (b - c - 1) * DB * DB;
+                float ah[4][4], al[4][4];
+#pragma unroll
+                for (int r = 0; r < 4; ++r)
+#pragma unroll
+                    for (int cc = 0; cc < 4; ++cc) ah[r][cc] = al[r][cc] = 0.0f;
+                for (int q = k0; q < DB; ++q) {
+                    float2 x[4], y[4];
+                    const int rq = pk(DB * c + q, 0) + DB * c + k0;
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) x[r] = Tb[(i0 + r) * DB + q];
+#pragma unroll
+                    for (int cc = 0; cc < 4; ++cc) y[cc] = (q >= k0 + cc) ? P2[rq + cc] : z2;
+#pragma unroll
+                    for (int r = 0; r < 4; ++r)
+#pragma unroll
+                        for (int cc = 0; cc < 4; ++cc) df_fma_acc(ah[r][cc], al[r][cc], x[r], y[cc]);
+                }
+#pragma unroll
+                for (int r = 0; r < 4; ++r)
+#pragma unroll
+                    for (int cc = 0; cc < 4; ++cc) {
+                        const float2 v = df_norm(ah[r][cc], al[r][cc]);
+                        P2[pk(DB * b + i0 + r, DB * c + k0 + cc)] = make_float2(-v.x, -v.y);
+                    }
+            }
+            __syncthreads();
+        }
+    } else {
+        for (int c = 2; c >= 0; --c) {   // off-diagonal blocks of block column c, in 4 x 4 register tiles
+            const int nres = 3 - c;
+            for (int u = tid; u < nres * 64; u += 256) {   // sums: T_bc = sum_d W_bd L_dc
+                const int b = c + 1 + u / 64, bl = u & 63;
+                const int i0 = 4 * (bl >> 3), k0 = 4 * (bl & 7);
+                double acc[4][4];
+#pragma unroll
+                for (int r = 0; r < 4; ++r)
+#pragma unroll
+                    for (int cc = 0; cc < 4; ++cc) acc[r][cc] = 0.0;
+                int ra[4];
+#pragma unroll
+                for (int r = 0; r < 4; ++r) ra[r] = pk(DB * b + i0 + r, 0);
+                for (int d = c + 1; d <= b; ++d) {
+                    const bool diag = (d == b);   // W_bb is lower triangular
+                    const int qend = diag ? i0 + 3 : DB - 1;
+                    for (int q = 0; q <= qend; ++q) {
+                        double x[4], y[4];
+                        const int rq = pk(DB * d + q, 0) + DB * c + k0;
+#pragma unroll
+                        for (int r = 0; r < 4; ++r) x[r] = (diag && q > i0 + r) ? 0.0 : P[ra[r] + DB * d + q];
+#pragma unroll
+                        for (int cc = 0; cc < 4; ++cc) y[cc] = P[rq + cc];
+#pragma unroll
+                        for (int r = 0; r < 4; ++r)
+#pragma unroll
+                            for (int cc = 0; cc < 4; ++cc) acc[r][cc] = fma(x[r], y[cc], acc[r][cc]);
+                    }
+                }
+                double *Tb = Tm + (b - c - 1) * DB * DB;
+#pragma unroll
+                for (int r = 0; r < 4; ++r)
+#pragma unroll
+                    for (int cc = 0; cc < 4; ++cc) Tb[(i0 + r) * DB + k0 + cc] = acc[r][cc];
+            }
+            __syncthreads();
+            for (int u = tid; u < nres * 64; u += 256) {   // W_bc = -T_bc W_cc (W_cc lower triangular)
+                const int b = c + 1 + u / 64, bl = u & 63;
+                const int i0 = 4 * (bl >> 3), k0 = 4 * (bl & 7);
+                const double *Tb = Tm + (b - c - 1) * DB * DB;
+                double acc[4][4];
+#pragma unroll
+                for (int r = 0; r < 4; ++r)
+#pragma unroll
+                    for (int cc = 0; cc < 4; ++cc) acc[r][cc] = 0.0;
+                for (int q = k0; q < DB; ++q) {
                     double x[4], y[4];
-                    const int rq = pk(DB * d + q, 0) + DB * c + k0;
+                    const int rq = pk(DB * c + q, 0) + DB * c + k0;
 #pragma unroll
-                    for (int r = 0; r < 4; ++r) x[r] = (diag && q > i0 + r) ? 0.0 : P[ra[r] + DB * d + q];
+                    for (int r = 0; r < 4; ++r) x[r] = Tb[(i0 + r) * DB + q];
 #pragma unroll
-                    for (int cc = 0; cc < 4; ++cc) y[cc] = P[rq + cc];
+                    for (int cc = 0; cc < 4; ++cc) y[cc] = (q >= k0 + cc) ? P[rq + cc] : 0.0;
 #pragma unroll
                     for (int r = 0; r < 4; ++r)
 #pragma unroll
                         for (int cc = 0; cc < 4; ++cc) acc[r][cc] = fma(x[r], y[cc], acc[r][cc]);
                 }
-            }
-            double *Tb = Tm + (b - c - 1) * DB * DB;
-#pragma unroll
-            for (int r = 0; r < 4; ++r)
-#pragma unroll
-                for (int cc = 0; cc < 4; ++cc) Tb[(i0 + r) * DB + k0 + cc] = acc[r][cc];
-        }
-        __syncthreads();
-        for (int u = tid; u < nres * 64; u += 256) {   // W_bc = -T_bc W_cc (W_cc lower triangular)
-            const int b = c + 1 + u / 64, bl = u & 63;
-            const int i0 = 4 * (bl >> 3), k0 = 4 * (bl & 7);
-            const double *Tb = Tm + (b - c - 1) * DB * DB;
-            double acc[4][4];
-#pragma unroll
-            for (int r = 0; r < 4; ++r)
-#pragma unroll
-                for (int cc = 0; cc < 4; ++cc) acc[r][cc] = 0.0;
-            for (int q = k0; q < DB; ++q) {
-                double x[4], y[4];
-                const int rq = pk(DB * c + q, 0) + DB * c + k0;
-#pragma unroll
-                for (int r = 0; r < 4; ++r) x[r] = Tb[(i0 + r) * DB + q];
-#pragma unroll
-                for (int cc = 0; cc < 4; ++cc) y[cc] = (q >= k0 + cc) ? P[rq + cc] : 0.0;
 #pragma unroll
                 for (int r = 0; r < 4; ++r)
 #pragma unroll
-                    for (int cc = 0; cc < 4; ++cc) acc[r][cc] = fma(x[r], y[cc], acc[r][cc]);
+                    for (int cc = 0; cc < 4; ++cc) P[pk(DB * b + i0 + r, DB * c + k0 + cc)] = -acc[r][cc];
             }
-#pragma unroll
-            for (int r = 0; r < 4; ++r)
-#pragma unroll
-                for (int cc = 0; cc < 4; ++cc) P[pk(DB * b + i0 + r, DB * c + k0 + cc)] = -acc[r][cc];
+            __syncthreads();
         }
-        __syncthreads();
     }
     // log|tile| and sum 1/d over the pivots
     {
@@ -450,13 +550,15 @@ __global__ void __launch_bounds__(256, 2) k_potrf_mixed(int J, int64_t tpo, doub
     }
     const bool bad = __syncthreads_or(tid < TB && !(piv[tid] > 0.0));
     const double *Wp = P;
+    const float2 *W2 = reinterpret_cast<const float2 *>(P);   // S == 5: W as double-float pairs
     // slice the rows of W (B operand of the panel solve: C = A W^T)
     uint8_t *img = wimg + (int64_t)w * img_bytes<S>();
     int *exps = reinterpret_cast<int *>(img + (size_t)S * 2 * SBLK);
     for (int r = warp; r < TB; r += 8) {
         const int bi = pk(r, 0);
         float mx = 0.0f;
-        for (int k = lane; k <= r; k += 32) mx = fmaxf(mx, fabsf(__double2float_rn(Wp[bi + k])));
+        for (int k = lane; k <= r; k += 32)
+            mx = fmaxf(mx, fabsf(S == 5 ? W2[bi + k].x : __double2float_rn(Wp[bi + k])));
         for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
         const int e = row_exp(mx * (1.0f + 1.0f / 1024.0f));
         if (lane == 0) exps[r] = e;
@@ -464,11 +566,19 @@ __global__ void __launch_bounds__(256, 2) k_potrf_mixed(int J, int64_t tpo, doub
         for (int q = 0; q < 2; ++q) {
             const int k = 64 * q + 2 * lane;
             float m0[S], m1[S];
-            const double x0 = (k <= r) ? Wp[bi + k] : 0.0;
-            const double x1 = (k + 1 <= r) ? Wp[bi + k + 1] : 0.0;
-            const float h0 = __double2float_rn(x0), h1 = __double2float_rn(x1);
-            slice_df<S>(h0, __double2float_rn(x0 - (double)h0), e, m0);
-            slice_df<S>(h1, __double2float_rn(x1 - (double)h1), e, m1);
+            if constexpr (S == 5) {
+                const float2 z2 = make_float2(0.0f, 0.0f);
+                const float2 x0 = (k <= r) ? W2[bi + k] : z2;
+                const float2 x1 = (k + 1 <= r) ? W2[bi + k + 1] : z2;
+                slice_df<S>(x0.x, x0.y, e, m0);
+                slice_df<S>(x1.x, x1.y, e, m1);
+            } else {
+                const double x0 = (k <= r) ? Wp[bi + k] : 0.0;
+                const double x1 = (k + 1 <= r) ? Wp[bi + k + 1] : 0.0;
+                const float h0 = __double2float_rn(x0), h1 = __double2float_rn(x1);
+                slice_df<S>(h0, __double2float_rn(x0 - (double)h0), e, m0);
+                slice_df<S>(h1, __double2float_rn(x1 - (double)h1), e, m1);
+            }
             store_pair<S>(img, r, k, m0, m1);
         }
     }
