@@ -59,6 +59,9 @@ def lib():
         L.oracle_profile_beta.restype = C.c_int
         L.oracle_profile_beta.argtypes = [_I64, _I32, _I32, _I64, _PD, _PD, _PI32, _PD, _D, _I32,
                                           _I64, _PD, _PD]
+        L.oracle_profile_beta_reml.restype = C.c_int
+        L.oracle_profile_beta_reml.argtypes = [_I64, _I32, _I32, _I64, _PD, _PD, _PI32, _PD, _D, _I32,
+                                               _I64, _PD, _PD, _I32]
         L.oracle_profile_sigma.restype = C.c_int
         L.oracle_profile_sigma.argtypes = [_I64, _I32, _I32, _I64, _PD, _PD, _PI32, _PD, _D,
                                            _I64, _PD, _PD]
@@ -192,8 +195,9 @@ def _status_ptr(status):
     return s, s.ctypes.data_as(_PI32)
 
 
-def profile_beta(n, ssq, logdet, lambdas, sumlogy, j, grid, status=None):
-    """Profile of beta_j on `grid` from Table-1 statistics (Section 3.4).
+def profile_beta(n, ssq, logdet, lambdas, sumlogy, j, grid, status=None, reml=False):
+    """Profile of beta_j on `grid` from Table-1 statistics (Section 3.4; with
+    reml, the Appendix's REML form).
 
     ssq: [K, M+p, M+p]; logdet: [K, 2]; lambdas: [M]; status: [K] or None."""
     ssq, logdet, lambdas, grid = map(_f64, (ssq, logdet, lambdas, grid))
@@ -201,8 +205,9 @@ def profile_beta(n, ssq, logdet, lambdas, sumlogy, j, grid, status=None):
     M = lambdas.shape[0]
     s, sp = _status_ptr(status)
     prof = np.empty(grid.shape[0])
-    st = lib().oracle_profile_beta(int(n), q - M, M, K, _p(ssq), _p(logdet), sp, _p(lambdas),
-                                   float(sumlogy), int(j), grid.shape[0], _p(grid), _p(prof))
+    st = lib().oracle_profile_beta_reml(int(n), q - M, M, K, _p(ssq), _p(logdet), sp, _p(lambdas),
+                                        float(sumlogy), int(j), grid.shape[0], _p(grid), _p(prof),
+                                        int(bool(reml)))
     if st != OR_OK:
         raise ValueError("oracle_profile_beta: invalid arguments")
     return prof

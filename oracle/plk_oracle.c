@@ -615,9 +615,27 @@ static int oracle_invert(int32_t d, const double *A, double *Ainv)
  * ssq: K x (M+p) x (M+p) (Table 1 ssqYX, y' columns first); logdet: K x 2
  * ([0] = log|V|); status: K (NULL = all valid; a point counts when
  * (status & 15) == 0).  NaN where no point gives a finite value. */
+int oracle_profile_beta_reml(int64_t n, int32_t p, int32_t M, int64_t K, const double *ssq,
+                             const double *logdet, const int32_t *status, const double *lambdas,
+                             double sumlogy, int32_t j, int64_t G, const double *grid, double *prof,
+                             int32_t reml);
+
 int oracle_profile_beta(int64_t n, int32_t p, int32_t M, int64_t K, const double *ssq,
                         const double *logdet, const int32_t *status, const double *lambdas,
                         double sumlogy, int32_t j, int64_t G, const double *grid, double *prof)
+{
+    return oracle_profile_beta_reml(n, p, M, K, ssq, logdet, status, lambdas, sumlogy, j, G, grid, prof, 0);
+}
+
+/* The same profile with the REML criterion when reml != 0 (Appendix,
+ * subsection on beta_p with REML, eq. remlprofileytilde): with RSS(b) as above,
+ *   -2 l* = (n-p) log(RSS(b)/(n-p)) + log|V| + log|X^T V^-1 X|
+ *           - 2(lambda-1) sum log y + n log(2 pi) + n - p,
+ * log|X^T V^-1 X| of the full X, as printed (logdet[2k+1]). */
+int oracle_profile_beta_reml(int64_t n, int32_t p, int32_t M, int64_t K, const double *ssq,
+                             const double *logdet, const int32_t *status, const double *lambdas,
+                             double sumlogy, int32_t j, int64_t G, const double *grid, double *prof,
+                             int32_t reml)
 {
     if (j < 0 || j >= p)
         return OR_INVALID;
@@ -662,9 +680,17 @@ int oracle_profile_beta(int64_t n, int32_t p, int32_t M, int64_t K, const double
                 double rss = t1 - t2;
                 if (!(rss > 0.0))
                     continue;
-                double m2l = (double)n * log(rss / (double)n) + ldv
-                           - 2.0 * (lambdas[m] - 1.0) * sumlogy
-                           + (double)n * log(2.0 * OR_PI) + (double)n;
+                double m2l;
+                if (reml) {
+                    double ne = (double)(n - p);
+                    m2l = ne * log(rss / ne) + ldv + logdet[2 * k + 1]
+                        - 2.0 * (lambdas[m] - 1.0) * sumlogy
+                        + (double)n * log(2.0 * OR_PI) + ne;
+                } else {
+                    m2l = (double)n * log(rss / (double)n) + ldv
+                        - 2.0 * (lambdas[m] - 1.0) * sumlogy
+                        + (double)n * log(2.0 * OR_PI) + (double)n;
+                }
                 double ll = -0.5 * m2l;
                 if (ll == ll && (isnan(prof[g]) || ll > prof[g]))
                     prof[g] = ll;

@@ -303,3 +303,47 @@ def test_internal_params_axis_exchange(rat, ang):
     w1 = oracle.internal_params([[phx, 1.0, 0.1, rat, ang]])[0]
     w2 = oracle.internal_params([swapped])[0]
     assert np.allclose(w1, w2, rtol=0, atol=1e-13)
+
+
+def dense_beta_profile_reml_point(coords, y, X, om, lam, j, b):
+    """REML criterion of the Appendix (eq. remlprofileytilde) at beta_j = b:
+    (n-p) log(RSS(b)/(n-p)) + log|V| + log|X^T V^-1 X| - 2(lambda-1) sum log y
+    + n log(2 pi) + n - p, with RSS(b) from a direct GLS fit of the offset
+    response on X_-j and the log-determinants by numpy.linalg.slogdet."""
+    n, p = X.shape
+    V = oracle.build_v(coords, om)
+    Vi = np.linalg.inv(V)
+    yp = boxcox_np(y, lam)
+    r = yp - X[:, j] * b
+    Xm = np.delete(X, j, axis=1)
+    bm = np.linalg.solve(Xm.T @ Vi @ Xm, Xm.T @ Vi @ r) if p > 1 else np.zeros(0)
+    e = r - Xm @ bm
+    rss = float(e @ Vi @ e)
+    m2 = ((n - p) * math.log(rss / (n - p)) + np.linalg.slogdet(V)[1] + np.linalg.slogdet(X.T @ Vi @ X)[1]
+          - 2 * (lam - 1) * np.log(y).sum() + n * math.log(2 * math.pi) + n - p)
+    return -0.5 * m2
+
+
+@pytest.mark.parametrize("j", [0, 2])
+def test_beta_profile_reml_equals_dense(j):
+    coords, y, X = small_problem(3)
+    ssq, ld, st, logL, beta, _ = stats(coords, y, X, OMEGAS, LAMS)
+    grid = np.linspace(-1.5, 2.5, 9)
+    prof = oracle.profile_beta(len(y), ssq, ld, LAMS, oracle.sum_log(y), j, grid, st, reml=True)
+    for g, b in enumerate(grid):
+        dense = max(dense_beta_profile_reml_point(coords, y, X, om, lam, j, b) for om in OMEGAS for lam in LAMS)
+        assert abs(prof[g] - dense) <= 1e-9 * max(1.0, abs(dense)), (g, prof[g], dense)
+
+
+def test_beta_profile_reml_at_gls_estimate_is_remlpro():
+    # at b = beta-hat_j the offset fit leaves RSS(b) = RSS: the REML beta profile
+    # of one point and lambda equals its REML profile likelihood (eq. remlpro)
+    coords, y, X = small_problem(4)
+    om, lam = OMEGAS[1], np.array([0.5])
+    o = oracle.profile_point(coords, y, X, om, lam, reml=True)
+    bj = o["beta"][0][1]
+    prof = oracle.profile_beta(len(y), o["ssq"][None], o["logdet"][None], lam, oracle.sum_log(y), 1,
+                               np.array([bj]), reml=True)
+    assert prof[0] == pytest.approx(o["logL"][0], rel=1e-12)
+    ml = oracle.profile_beta(len(y), o["ssq"][None], o["logdet"][None], lam, oracle.sum_log(y), 1, np.array([bj]))
+    assert ml[0] != pytest.approx(prof[0], abs=1e-6)
