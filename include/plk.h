@@ -472,6 +472,15 @@ typedef struct {
 plk_status plk_profile_beta_device(const plk_stats_args *stats, int32_t j, const double *grid,
                                    int64_t G, double *prof, void *stream);
 
+/* The same profile with the REML criterion (Appendix, the subsection on beta_p
+ * with REML, eq. remlprofileytilde):
+ *   -2 l* = (n-p) log(RSS(b)/(n-p)) + log|V| + log|X^T V^-1 X|
+ *           - 2(lambda-1) sum log y + n log(2 pi) + n - p,
+ * RSS(b) as above and log|X^T V^-1 X| of the full X, as printed (stats->logdet
+ * [k][1] is read as well).  Arguments and errors as plk_profile_beta_device. */
+plk_status plk_profile_beta_reml_device(const plk_stats_args *stats, int32_t j, const double *grid,
+                                        int64_t G, double *prof, void *stream);
+
 /* Profile log-likelihood of sigma (Section 3.5, eq. profileSigma) at the G
  * grid values s = grid[g] (standard deviations, > 0; other values give NaN):
  *   prof[g] = max over the used points and all lambdas of

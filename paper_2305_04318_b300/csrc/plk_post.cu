@@ -101,7 +101,7 @@ __device__ void small_fwd(int d, const double *A, const double *b, double *z) {
 //   l(s) = -(1/2) [RSS / s^2 + n log s^2 + C] (eq. profileSigma).
 // One thread per (k, m) pair; the block's pairs are then swept for every grid
 // value.  keys: G order-preserving keys, zero on entry.
-__global__ void __launch_bounds__(NTP) k_prof_closed(int mode, int64_t n, int p, int M, int64_t K,
+__global__ void __launch_bounds__(NTP) k_prof_closed(int mode, int reml, int64_t n, int p, int M, int64_t K,
                                                      const double *__restrict__ y,
                                                      const double *__restrict__ lambdas,
                                                      const double *__restrict__ ssq,
@@ -123,7 +123,8 @@ __global__ void __launch_bounds__(NTP) k_prof_closed(int mode, int64_t n, int p,
         const int m = (int)(pr - k * M);
         const double *S = ssq + k * (int64_t)q * q;
         const double ldv = logdet[2 * k];
-        ok = (status == nullptr || (status[k] & 15) == 0) && isfinite(ldv);
+        const double ldx = logdet[2 * k + 1];   // log|X^T V^-1 X| (REML only)
+        ok = (status == nullptr || (status[k] & 15) == 0) && isfinite(ldv) && (!reml || isfinite(ldx));
         double A[PMAX * PMAX], zy[PMAX], zx[PMAX], by[PMAX], bx[PMAX];
         const double two_pi_log = 1.8378770664093454836;   // log(2 pi)
         const double jac = -2.0 * (lambdas[m] - 1.0) * J;
@@ -155,7 +156,12 @@ __global__ void __launch_bounds__(NTP) k_prof_closed(int mode, int64_t n, int p,
                 c1 = S[(M + j) * q + m] - xy;
                 c2 = S[(M + j) * q + (M + j)] - xx;
                 const double dn = (double)n;
-                h = -0.5 * (ldv + jac + dn * two_pi_log + dn - dn * log(dn));
+                if (reml) {   // Appendix, eq. remlprofileytilde
+                    const double de = (double)(n - p);
+                    h = -0.5 * (ldv + ldx + jac + dn * two_pi_log + de - de * log(de));
+                } else {
+                    h = -0.5 * (ldv + jac + dn * two_pi_log + dn - dn * log(dn));
+                }
             }
         } else if (ok) {
             for (int a = 0; a < p; ++a) {
@@ -183,6 +189,7 @@ __global__ void __launch_bounds__(NTP) k_prof_closed(int mode, int64_t n, int p,
     const int64_t first = (int64_t)blockIdx.x * NTP;
     const int np = (int)((pairs - first) < NTP ? (pairs - first) : NTP);
     const double dn = (double)n;
+    const double de = reml ? (double)(n - p) : dn;   // the log term's weight
     for (int64_t g = threadIdx.x; g < G; g += NTP) {
         const double b = grid[g];
         double best = -INFINITY;
@@ -192,7 +199,7 @@ __global__ void __launch_bounds__(NTP) k_prof_closed(int mode, int64_t n, int p,
             double v;
             if (mode == 0) {
                 const double rss = cf[0][i] - 2.0 * cf[1][i] * b + cf[2][i] * b * b;
-                v = rss > 0.0 ? cf[3][i] - 0.5 * dn * log(rss) : NAN;
+                v = rss > 0.0 ? cf[3][i] - 0.5 * de * log(rss) : NAN;
             } else {
                 const double s2 = b * b;
                 v = b > 0.0 ? -0.5 * (cf[0][i] / s2 + dn * log(s2) + cf[3][i]) : NAN;
@@ -396,7 +403,7 @@ plk_status check_stats(const plk_stats_args *a, const char *who) {
     return PLK_OK;
 }
 
-plk_status run_closed(int mode, const plk_stats_args *a, int32_t j, const double *grid, int64_t G,
+plk_status run_closed(int mode, int reml, const plk_stats_args *a, int32_t j, const double *grid, int64_t G,
                       double *prof, void *stream, const char *who) {
     plk_status st = check_stats(a, who);
     if (st != PLK_OK) return st;
@@ -410,7 +417,7 @@ plk_status run_closed(int mode, const plk_stats_args *a, int32_t j, const double
     if (pairs > 0) {
         const int64_t blocks = (pairs + NTP - 1) / NTP;
         if (blocks > INT32_MAX) return post_fail(PLK_E_INVALID, std::string(who) + ": K too large");
-        k_prof_closed<<<(unsigned)blocks, NTP, 0, s>>>(mode, a->n, a->p, a->M, a->K, a->y, a->lambdas, a->ssq_yx,
+        k_prof_closed<<<(unsigned)blocks, NTP, 0, s>>>(mode, reml, a->n, a->p, a->M, a->K, a->y, a->lambdas, a->ssq_yx,
                                                        a->logdet, a->status, j, G, grid,
                                                        reinterpret_cast<unsigned long long *>(prof));
         if ((e = cudaGetLastError()) != cudaSuccess) return post_cuda(e, who);
@@ -427,12 +434,17 @@ using namespace plk;
 
 extern "C" plk_status plk_profile_beta_device(const plk_stats_args *stats, int32_t j, const double *grid,
                                               int64_t G, double *prof, void *stream) {
-    return run_closed(0, stats, j, grid, G, prof, stream, "plk_profile_beta_device");
+    return run_closed(0, 0, stats, j, grid, G, prof, stream, "plk_profile_beta_device");
+}
+
+extern "C" plk_status plk_profile_beta_reml_device(const plk_stats_args *stats, int32_t j, const double *grid,
+                                                   int64_t G, double *prof, void *stream) {
+    return run_closed(0, 1, stats, j, grid, G, prof, stream, "plk_profile_beta_reml_device");
 }
 
 extern "C" plk_status plk_profile_sigma_device(const plk_stats_args *stats, const double *grid, int64_t G,
                                                double *prof, void *stream) {
-    return run_closed(1, stats, 0, grid, G, prof, stream, "plk_profile_sigma_device");
+    return run_closed(1, 0, stats, 0, grid, G, prof, stream, "plk_profile_sigma_device");
 }
 
 extern "C" plk_status plk_profile_lambda_device(const double *logL, int64_t K, int32_t M, double *prof,

@@ -100,6 +100,7 @@ def lib():
                                      C.POINTER(i32)]),
         "plk_chi2_1_quantile": (dbl, [dbl]),
         "plk_profile_beta_device": (C.c_int, [C.POINTER(StatsArgs), i32, vp, i64, vp, vp]),
+        "plk_profile_beta_reml_device": (C.c_int, [C.POINTER(StatsArgs), i32, vp, i64, vp, vp]),
         "plk_profile_sigma_device": (C.c_int, [C.POINTER(StatsArgs), vp, i64, vp, vp]),
         "plk_profile_lambda_device": (C.c_int, [vp, i64, i32, vp, vp]),
         "plk_profile_hull_device": (C.c_int, [vp, i64, vp, i64, vp, i64, vp, vp, vp]),
@@ -314,15 +315,16 @@ def _stats_args(y, lambdas, ssq_yx, logdet, status):
                      _ptr(status))
 
 
-def profile_beta_device(y, lambdas, ssq_yx, logdet, status, j, grid, prof=None, stream=None):
+def profile_beta_device(y, lambdas, ssq_yx, logdet, status, j, grid, prof=None, stream=None, reml=False):
     """Profile of beta_j at the CUDA float64 `grid` from the evaluation's
-    statistics (ssq_yx [K,M+p,M+p], logdet [K,2], status [K] or None)."""
+    statistics (ssq_yx [K,M+p,M+p], logdet [K,2], status [K] or None); reml:
+    the Appendix's REML criterion."""
     import torch
     if prof is None:
         prof = torch.empty((grid.shape[0],), dtype=torch.float64, device=grid.device)
     a = _stats_args(y, lambdas, ssq_yx, logdet, status)
-    _check(lib().plk_profile_beta_device(C.byref(a), int(j), _ptr(grid), grid.shape[0], _ptr(prof),
-                                         _stream_handle(stream)))
+    fn = lib().plk_profile_beta_reml_device if reml else lib().plk_profile_beta_device
+    _check(fn(C.byref(a), int(j), _ptr(grid), grid.shape[0], _ptr(prof), _stream_handle(stream)))
     return prof
 
 

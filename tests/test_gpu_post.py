@@ -232,3 +232,23 @@ def test_profile_ci_host_arrays_match_oracle():
     assert nv.profile_ci(grid, 0.01 * prof, 0.95)["censored"] == 3
     with pytest.raises(nv.PlkError):
         nv.profile_ci(grid, prof, 1.5)
+
+
+@pytest.mark.parametrize("p", [1, 3])
+def test_profile_beta_reml_matches_oracle(p):
+    """REML profile of beta_j (the Appendix's criterion) from the statistics on
+    the device against the oracle's, status-excluded points included."""
+    ds, P, lams = workload(seed=40 + p, p=p)
+    o = oracle_stats(ds, P, lams)
+    st = o["status"].copy()
+    st[[3]] = [nv.POINT_NOT_PD]
+    y, l, s, ld, sd = dev_stats(ds, lams, o, st)
+    sl = oracle.sum_log(ds.y)
+    for j in range(p):
+        bh = o["beta"][:, :, j][o["status"] == 0]
+        grid = np.linspace(bh.min() - 1.0, bh.max() + 1.0, 120)
+        ref = oracle.profile_beta(len(ds.y), o["ssq"], o["logdet"], lams, sl, j, grid, st, reml=True)
+        got = nv.profile_beta_device(y, l, s, ld, sd, j, to_dev(grid), reml=True).cpu().numpy()
+        assert_prof_close(got, ref, what=f"reml beta_{j}")
+        ml = nv.profile_beta_device(y, l, s, ld, sd, j, to_dev(grid)).cpu().numpy()
+        assert not np.allclose(ml, got)
