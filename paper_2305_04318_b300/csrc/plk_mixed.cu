@@ -256,6 +256,7 @@ __global__ void __launch_bounds__(256, 2) k_potrf_mixed(int J, int64_t tpo, doub
     double *P = sm;                   // packed lower triangle: the tile, then L, then W = L^-1
     double *Tm = sm + PK;             // 3 x 32 x 32 temporaries of the block inverse
     __shared__ double col[TB];        // scaled column j of L
+    __shared__ double col2[TB];       // scaled column j + 1 of L
     __shared__ double piv[TB];        // pivots d_j
     __shared__ double rd[TB];         // 1 / L[j][j]
     __shared__ double dcol[4][2][DB];   // per diagonal block: finished row k of W
@@ -274,10 +275,16 @@ __global__ void __launch_bounds__(256, 2) k_potrf_mixed(int J, int64_t tpo, doub
     // kept so the status is set below)
     for (int kb = 0; kb < TB; kb += DB) {
         const int kend = kb + DB - 1;
-        for (int j = kb; j <= kend; ++j) {
+        for (int j = kb; j <= kend; j += 2) {
+            // two columns per step: warp 0 factors column j, applies it to
+            // column j + 1 (the same FMA the block update would make) and
+            // factors column j + 1; then the block applies both to the rest of
+            // the panel, each entry's two FMAs in column order (the operations
+            // of a column-by-column factorisation, with half the barriers)
             if (warp == 0) {
                 const double d = P[pk(j, j)];
                 const double rl = rsqrt(d);
+                __syncwarp();   // every lane has read the pivot before lane 0 replaces it
                 if (lane == 0) {
                     piv[j] = d;
                     P[pk(j, j)] = d * rl;
@@ -287,25 +294,42 @@ __global__ void __launch_bounds__(256, 2) k_potrf_mixed(int J, int64_t tpo, doub
                     P[pk(i, j)] = v;
                     col[i] = v;
                 }
+                __syncwarp();
+                const double cj1 = col[j + 1];
+                for (int i = j + 1 + lane; i < TB; i += 32) P[pk(i, j + 1)] = fma(-col[i], cj1, P[pk(i, j + 1)]);
+                __syncwarp();
+                const double d2 = P[pk(j + 1, j + 1)];
+                const double rl2 = rsqrt(d2);
+                __syncwarp();
+                if (lane == 0) {
+                    piv[j + 1] = d2;
+                    P[pk(j + 1, j + 1)] = d2 * rl2;
+                }
+                for (int i = j + 2 + lane; i < TB; i += 32) {
+                    const double v = P[pk(i, j + 1)] * rl2;
+                    P[pk(i, j + 1)] = v;
+                    col2[i] = v;
+                }
             }
             __syncthreads();
-            const int nk = kend - j;   // panel columns right of j
+            const int nk = kend - j - 1;   // panel columns right of j + 1
             if (nk > 0) {
-                // rows j+1 .. kend (k <= i: a triangle), then rows below the panel (all nk columns)
+                // rows j+2 .. kend (k <= i: a triangle), then rows below the panel (all nk columns)
                 const int tri = nk * (nk + 1) / 2;
                 const int total = tri + (TB - 1 - kend) * nk;
                 for (int t = tid; t < total; t += 256) {
                     int i, k;
                     if (t < tri) {
                         const int ii = tri_row(t);
-                        i = j + 1 + ii;
-                        k = j + 1 + (t - ii * (ii + 1) / 2);
+                        i = j + 2 + ii;
+                        k = j + 2 + (t - ii * (ii + 1) / 2);
                     } else {
                         const int t2 = t - tri, q = t2 / nk;
                         i = kend + 1 + q;
-                        k = j + 1 + (t2 - q * nk);
+                        k = j + 2 + (t2 - q * nk);
                     }
-                    P[pk(i, k)] = fma(-col[i], col[k], P[pk(i, k)]);
+                    const double a = fma(-col[i], col[k], P[pk(i, k)]);
+                    P[pk(i, k)] = fma(-col2[i], col2[k], a);
                 }
                 __syncthreads();
             }
