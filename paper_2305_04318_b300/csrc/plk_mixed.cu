@@ -2,7 +2,8 @@
 //
 // The blocked right-looking Cholesky of the bordered matrix (Section 3.3,
 // Step 3 items 2-4) with
-//   * the diagonal tile factorised and inverted in FP64 (as in the FP64 path),
+//   * the diagonal tile factorised in double-float FP32 (5 slices) or FP64
+//     (7 slices), its inverse's off-diagonal blocks in double-float at 5 slices,
 //   * the panel solve  L_IJ = A_IJ L_JJ^-T  and the trailing update
 //     A_IK -= L_IJ L_KJ^T  computed as exact products of bf16 "slices",
 //   * the trailing matrix held as double-float (two FP32 planes per tile).
@@ -86,6 +87,85 @@ __device__ __forceinline__ float2 df_norm(float h, float l) {
     const float s = __fadd_rn(h, l);
     return make_float2(s, __fsub_rn(l, __fsub_rn(s, h)));
 }
+// (h, l) renormalised without assuming |h| >= |l| (after a cancellation)
+__device__ __forceinline__ float2 df_renorm(float h, float l) {
+    float s, e;
+    two_sum(h, l, s, e);
+    return make_float2(s, e);
+}
+
+// Arithmetic of the diagonal-tile Cholesky (one template, two number types).
+// FP64 for the 7-slice tier (its products keep ~2^-46 of each entry, so the
+// factor must be better than double-float); double-float FP32 pairs (~2^-44
+// per operation) for the 5-slice pass, whose products are only good to 2^-30.
+struct ArithF64 {
+    using T = double;
+    double v;   // rank-32 accumulator
+    static __device__ __forceinline__ T load(float h, float l) { return (double)h + (double)l; }
+    static __device__ __forceinline__ double value(T x) { return x; }
+    static __device__ __forceinline__ T rsqrt_(T d) { return rsqrt(d); }
+    static __device__ __forceinline__ T mul(T a, T b) { return a * b; }
+    static __device__ __forceinline__ T fms(T a, T x, T y) { return fma(-x, y, a); }   // a - x y
+    static __device__ __forceinline__ T recip(T x) { return 1.0 / x; }
+    static __device__ __forceinline__ T zero_value() { return 0.0; }
+    __device__ __forceinline__ void zero() { v = 0.0; }
+    __device__ __forceinline__ void fma_acc(T x, T y) { v = fma(x, y, v); }
+    __device__ __forceinline__ T sub_from(T p) const { return p - v; }
+};
+struct ArithDF {
+    using T = float2;
+    float h, l;   // rank-32 accumulator, l renormalised in sub_from
+    static __device__ __forceinline__ T load(float hi, float lo) { return make_float2(hi, lo); }
+    static __device__ __forceinline__ double value(T x) { return (double)x.x + (double)x.y; }
+    // d^(-1/2): FP32 estimate y, then one Newton step y (1 + r / 2) with the
+    // residual r = 1 - d y^2 formed to ~2^-46 (y^2 and d_hi y^2 split exactly;
+    // 1 - t is exact for t within a factor 2 of 1).  Relative error ~1.5 (2^-22)^2.
+    // d <= 0 gives NaN (or inf at 0) as in FP64.
+    static __device__ __forceinline__ T rsqrt_(T d) {
+        const float y = rsqrtf(d.x);
+        const float p = __fmul_rn(y, y);
+        const float pe = __fmaf_rn(y, y, -p);
+        const float t = __fmul_rn(d.x, p);
+        const float te = __fmaf_rn(d.x, p, -t);
+        float r = __fsub_rn(1.0f, t);
+        r = __fsub_rn(r, __fmaf_rn(d.x, pe, __fmaf_rn(d.y, p, te)));
+        return df_norm(y, __fmul_rn(__fmul_rn(y, r), 0.5f));
+    }
+    static __device__ __forceinline__ T mul(T a, T b) {   // a_lo b_lo dropped
+        const float p = __fmul_rn(a.x, b.x);
+        float e = __fmaf_rn(a.x, b.x, -p);
+        e = __fmaf_rn(a.x, b.y, e);
+        e = __fmaf_rn(a.y, b.x, e);
+        return df_norm(p, e);
+    }
+    static __device__ __forceinline__ T fms(T a, T x, T y) {   // a - x y (x_lo y_lo dropped)
+        const float p = __fmul_rn(x.x, y.x);
+        float e = __fmaf_rn(x.x, y.x, -p);
+        e = __fmaf_rn(x.x, y.y, e);
+        e = __fmaf_rn(x.y, y.x, e);
+        float s, es;
+        two_sum(a.x, -p, s, es);
+        return df_renorm(s, __fadd_rn(es, __fsub_rn(a.y, e)));
+    }
+    // 1 / x: FP32 reciprocal y, then y + y r with r = 1 - x y formed to ~2^-47
+    // (x_hi y split exactly; 1 - x_hi y exact); relative error ~2^-46
+    static __device__ __forceinline__ T recip(T x) {
+        const float y = __frcp_rn(x.x);
+        const float p = __fmul_rn(x.x, y);
+        const float pe = __fmaf_rn(x.x, y, -p);
+        float r = __fsub_rn(1.0f, p);
+        r = __fsub_rn(r, __fmaf_rn(x.y, y, pe));
+        return df_norm(y, __fmul_rn(y, r));
+    }
+    static __device__ __forceinline__ T zero_value() { return make_float2(0.0f, 0.0f); }
+    __device__ __forceinline__ void zero() { h = l = 0.0f; }
+    __device__ __forceinline__ void fma_acc(T x, T y) { df_fma_acc(h, l, x, y); }
+    __device__ __forceinline__ T sub_from(T p) const {
+        float s, es;
+        two_sum(p.x, -h, s, es);
+        return df_renorm(s, __fadd_rn(es, __fsub_rn(p.y, l)));
+    }
+};
 
 // The S slice values m_j 2^(-8j) of the double-float value (hi, lo) of a row with
 // exponent e.
@@ -236,12 +316,162 @@ __device__ __forceinline__ int tri_row(int t) {
 constexpr int DB = 32;   // block size of the diagonal-tile factorisation
 constexpr size_t POTRF_MIXED_SMEM = (size_t)(PK + 3 * DB * DB) * sizeof(double);
 
-// The FP64 pipe is the bound here (FP64 issues at 1/68 of FP32 on this part),
-// so the kernel keeps every FP64 instruction lane-full and blocks the work:
-// - Cholesky in 32-column panels: each column's pivot and scale by one warp,
-//   the update of the remaining panel columns spread evenly over the block
-//   (flat index over the entries it touches); then the trailing lower triangle
-//   gets the panel's rank-32 update in 4 x 4 register tiles;
+// Cholesky of the tile in the packed lower triangle P (number type Ar::T) in
+// 32-column panels: each column's pivot and scale by warp 0, two columns per
+// block barrier (warp 0 factors column j, applies it to column j + 1 and
+// factors that; the block then applies both to the rest of the panel, each
+// entry's two updates in column order: the operations of a column-by-column
+// factorisation with half the barriers), then the panel's rank-32 update of
+// the trailing lower triangle in 4 x 4 register tiles.  A non-positive pivot
+// leaves NaN behind it; the pivot itself is kept (piv) for the status.
+template <class Ar>
+__device__ __forceinline__ void chol_tile(typename Ar::T *__restrict__ P, typename Ar::T *col,
+                                          typename Ar::T *col2, double *piv, int tid) {
+    using T = typename Ar::T;
+    const int lane = tid & 31, warp = tid >> 5;
+    for (int kb = 0; kb < TB; kb += DB) {
+        const int kend = kb + DB - 1;
+        for (int j = kb; j <= kend; j += 2) {
+            if (warp == 0) {
+                const T d = P[pk(j, j)];
+                const T rl = Ar::rsqrt_(d);
+                __syncwarp();   // every lane has read the pivot before lane 0 replaces it
+                if (lane == 0) {
+                    piv[j] = Ar::value(d);
+                    P[pk(j, j)] = Ar::mul(d, rl);
+                }
+                for (int i = j + 1 + lane; i < TB; i += 32) {
+                    const T v = Ar::mul(P[pk(i, j)], rl);
+                    P[pk(i, j)] = v;
+                    col[i] = v;
+                }
+                __syncwarp();
+                const T cj1 = col[j + 1];
+                for (int i = j + 1 + lane; i < TB; i += 32) P[pk(i, j + 1)] = Ar::fms(P[pk(i, j + 1)], col[i], cj1);
+                __syncwarp();
+                const T d2 = P[pk(j + 1, j + 1)];
+                const T rl2 = Ar::rsqrt_(d2);
+                __syncwarp();
+                if (lane == 0) {
+                    piv[j + 1] = Ar::value(d2);
+                    P[pk(j + 1, j + 1)] = Ar::mul(d2, rl2);
+                }
+                for (int i = j + 2 + lane; i < TB; i += 32) {
+                    const T v = Ar::mul(P[pk(i, j + 1)], rl2);
+                    P[pk(i, j + 1)] = v;
+                    col2[i] = v;
+                }
+            }
+            __syncthreads();
+            const int nk = kend - j - 1;   // panel columns right of j + 1
+            if (nk > 0) {
+                // rows j+2 .. kend (k <= i: a triangle), then rows below the panel (all nk columns)
+                const int tri = nk * (nk + 1) / 2;
+                const int total = tri + (TB - 1 - kend) * nk;
+                for (int t = tid; t < total; t += 256) {
+                    int i, k;
+                    if (t < tri) {
+                        const int ii = tri_row(t);
+                        i = j + 2 + ii;
+                        k = j + 2 + (t - ii * (ii + 1) / 2);
+                    } else {
+                        const int t2 = t - tri, q = t2 / nk;
+                        i = kend + 1 + q;
+                        k = j + 2 + (t2 - q * nk);
+                    }
+                    P[pk(i, k)] = Ar::fms(Ar::fms(P[pk(i, k)], col[i], col[k]), col2[i], col2[k]);
+                }
+                __syncthreads();
+            }
+        }
+        const int m = TB - 1 - kend;   // rank-32 update of the trailing lower triangle
+        if (m > 0) {
+            const int nbl = m / 4, nblocks = nbl * (nbl + 1) / 2;
+            for (int bq = tid; bq < nblocks; bq += 256) {
+                const int bi = tri_row(bq), bk = bq - bi * (bi + 1) / 2;
+                const int i0 = kend + 1 + 4 * bi, k0 = kend + 1 + 4 * bk;
+                int ra[4], rb[4];
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    ra[r] = pk(i0 + r, 0);
+                    rb[r] = pk(k0 + r, 0);
+                }
+                Ar acc[4][4];
+#pragma unroll
+                for (int r = 0; r < 4; ++r)
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) acc[r][c].zero();
+#pragma unroll 4
+                for (int q = kb; q <= kend; ++q) {
+                    T x[4], y[4];
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) {
+                        x[r] = P[ra[r] + q];
+                        y[r] = P[rb[r] + q];
+                    }
+#pragma unroll
+                    for (int r = 0; r < 4; ++r)
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) acc[r][c].fma_acc(x[r], y[c]);
+                }
+#pragma unroll
+                for (int r = 0; r < 4; ++r)
+#pragma unroll
+                    for (int c = 0; c < 4; ++c)
+                        if (k0 + c <= i0 + r) P[ra[r] + k0 + c] = acc[r][c].sub_from(P[ra[r] + k0 + c]);
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// Inverses of the four 32 x 32 diagonal blocks of L in place (block b by warps
+// 2b, 2b+1, named barrier 1 + b), right-looking by rows: row k of W is final
+// once rows < k are applied; column k of L is staged a step ahead (dlc)
+// because its slots become W's.  rd receives 1 / L_jj.
+template <class Ar>
+__device__ __forceinline__ void inv_diag_blocks(typename Ar::T *__restrict__ P, typename Ar::T *rd,
+                                                typename Ar::T (*dcol)[2][DB], typename Ar::T (*dlc)[2][DB], int tid) {
+    using T = typename Ar::T;
+    const int warp = tid >> 5;
+    if (tid < TB) rd[tid] = Ar::recip(P[pk(tid, tid)]);
+    __syncthreads();
+    const int b = warp >> 1, lt = tid & 63, base = DB * b;
+    if (lt < DB) dlc[b][0][lt] = P[pk(base + lt, base)];
+    if (lt == 0) {
+        P[pk(base, base)] = rd[base];
+        dcol[b][0][0] = rd[base];
+    }
+    tc::named_sync(1 + b, 64);
+    for (int k = 0; k < DB - 1; ++k) {
+        const T *ck = dcol[b][k & 1], *lk = dlc[b][k & 1];
+        T *cn = dcol[b][(k + 1) & 1], *ln = dlc[b][(k + 1) & 1];
+        const int ncol = k + 1, cnt = (DB - 1 - k) * ncol;
+        if (lt > k + 1 && lt < DB) ln[lt] = P[pk(base + lt, base + k + 1)];
+        const T rn = rd[base + k + 1];
+        for (int t = lt; t < cnt; t += 64) {
+            const int ii = t / ncol, c = t - ii * ncol, i = k + 1 + ii;
+            const int e = pk(base + i, base + c);
+            const T acc = (c == k) ? Ar::zero_value() : P[e];   // slot (i, k) still holds L[i][k]
+            T v = Ar::fms(acc, lk[i], ck[c]);
+            if (ii == 0) {
+                v = Ar::mul(v, rn);
+                cn[c] = v;
+            }
+            P[e] = v;
+        }
+        if (lt == 0) {
+            P[pk(base + k + 1, base + k + 1)] = rn;
+            cn[k + 1] = rn;
+        }
+        tc::named_sync(1 + b, 64);
+    }
+    __syncthreads();
+}
+
+// FP64 issues at 1/68 of FP32 on this part, so the 5-slice pass keeps FP64
+// out of the bulk of the work and the kernel blocks what remains:
+// - Cholesky (chol_tile) in double-float FP32 at 5 slices, in FP64 at 7;
 // - W = L^-1 in place: the four 32 x 32 diagonal blocks are inverted at once
 //   (two warps each, right-looking by rows: row k of W is final once rows < k
 //   are applied; column k of L is staged a step ahead because its slots become
@@ -266,162 +496,35 @@ __global__ void __launch_bounds__(256, 2) k_potrf_mixed(int J, int64_t tpo, doub
     double *T = tiles + ((int64_t)w * tpo + tile_index(J, J)) * NT;
     const float *H = reinterpret_cast<const float *>(T);
     const float *Lo = H + NT;
-    for (int e = tid; e < NT; e += 256) {
-        const int r = e >> 7, c = e & (TB - 1);
-        if (c <= r) P[pk(r, c)] = (double)H[e] + (double)Lo[e];
-    }
-    __syncthreads();
-    // ---- Cholesky (a non-positive pivot leaves NaN behind it; the pivot is
-    // kept so the status is set below)
-    for (int kb = 0; kb < TB; kb += DB) {
-        const int kend = kb + DB - 1;
-        for (int j = kb; j <= kend; j += 2) {
-            // two columns per step: warp 0 factors column j, applies it to
-            // column j + 1 (the same FMA the block update would make) and
-            // factors column j + 1; then the block applies both to the rest of
-            // the panel, each entry's two FMAs in column order (the operations
-            // of a column-by-column factorisation, with half the barriers)
-            if (warp == 0) {
-                const double d = P[pk(j, j)];
-                const double rl = rsqrt(d);
-                __syncwarp();   // every lane has read the pivot before lane 0 replaces it
-                if (lane == 0) {
-                    piv[j] = d;
-                    P[pk(j, j)] = d * rl;
-                }
-                for (int i = j + 1 + lane; i < TB; i += 32) {
-                    const double v = P[pk(i, j)] * rl;
-                    P[pk(i, j)] = v;
-                    col[i] = v;
-                }
-                __syncwarp();
-                const double cj1 = col[j + 1];
-                for (int i = j + 1 + lane; i < TB; i += 32) P[pk(i, j + 1)] = fma(-col[i], cj1, P[pk(i, j + 1)]);
-                __syncwarp();
-                const double d2 = P[pk(j + 1, j + 1)];
-                const double rl2 = rsqrt(d2);
-                __syncwarp();
-                if (lane == 0) {
-                    piv[j + 1] = d2;
-                    P[pk(j + 1, j + 1)] = d2 * rl2;
-                }
-                for (int i = j + 2 + lane; i < TB; i += 32) {
-                    const double v = P[pk(i, j + 1)] * rl2;
-                    P[pk(i, j + 1)] = v;
-                    col2[i] = v;
-                }
-            }
-            __syncthreads();
-            const int nk = kend - j - 1;   // panel columns right of j + 1
-            if (nk > 0) {
-                // rows j+2 .. kend (k <= i: a triangle), then rows below the panel (all nk columns)
-                const int tri = nk * (nk + 1) / 2;
-                const int total = tri + (TB - 1 - kend) * nk;
-                for (int t = tid; t < total; t += 256) {
-                    int i, k;
-                    if (t < tri) {
-                        const int ii = tri_row(t);
-                        i = j + 2 + ii;
-                        k = j + 2 + (t - ii * (ii + 1) / 2);
-                    } else {
-                        const int t2 = t - tri, q = t2 / nk;
-                        i = kend + 1 + q;
-                        k = j + 2 + (t2 - q * nk);
-                    }
-                    const double a = fma(-col[i], col[k], P[pk(i, k)]);
-                    P[pk(i, k)] = fma(-col2[i], col2[k], a);
-                }
-                __syncthreads();
-            }
+    if constexpr (S == 5) {
+        // double-float Cholesky
+        float2 *P2 = reinterpret_cast<float2 *>(P);
+        for (int e = tid; e < NT; e += 256) {
+            const int r = e >> 7, c = e & (TB - 1);
+            if (c <= r) P2[pk(r, c)] = ArithDF::load(H[e], Lo[e]);
         }
-        const int m = TB - 1 - kend;   // rank-32 update of the trailing lower triangle
-        if (m > 0) {
-            const int nbl = m / 4, nblocks = nbl * (nbl + 1) / 2;
-            for (int bq = tid; bq < nblocks; bq += 256) {
-                const int bi = tri_row(bq), bk = bq - bi * (bi + 1) / 2;
-                const int i0 = kend + 1 + 4 * bi, k0 = kend + 1 + 4 * bk;
-                int ra[4], rb[4];
-#pragma unroll
-                for (int r = 0; r < 4; ++r) {
-                    ra[r] = pk(i0 + r, 0);
-                    rb[r] = pk(k0 + r, 0);
-                }
-                double acc[4][4];
-#pragma unroll
-                for (int r = 0; r < 4; ++r)
-#pragma unroll
-                    for (int c = 0; c < 4; ++c) acc[r][c] = 0.0;
-#pragma unroll 4
-                for (int q = kb; q <= kend; ++q) {
-                    double x[4], y[4];
-#pragma unroll
-                    for (int r = 0; r < 4; ++r) {
-                        x[r] = P[ra[r] + q];
-                        y[r] = P[rb[r] + q];
-                    }
-#pragma unroll
-                    for (int r = 0; r < 4; ++r)
-#pragma unroll
-                        for (int c = 0; c < 4; ++c) acc[r][c] = fma(x[r], y[c], acc[r][c]);
-                }
-#pragma unroll
-                for (int r = 0; r < 4; ++r)
-#pragma unroll
-                    for (int c = 0; c < 4; ++c)
-                        if (k0 + c <= i0 + r) P[ra[r] + k0 + c] -= acc[r][c];
-            }
-            __syncthreads();
+        __syncthreads();
+        chol_tile<ArithDF>(P2, reinterpret_cast<float2 *>(col), reinterpret_cast<float2 *>(col2), piv, tid);
+    } else {
+        for (int e = tid; e < NT; e += 256) {
+            const int r = e >> 7, c = e & (TB - 1);
+            if (c <= r) P[pk(r, c)] = ArithF64::load(H[e], Lo[e]);
         }
+        __syncthreads();
+        chol_tile<ArithF64>(P, col, col2, piv, tid);
     }
     // ---- W = L^-1 in place
-    if (tid < TB) rd[tid] = 1.0 / P[pk(tid, tid)];
-    __syncthreads();
-    {   // diagonal blocks: block b by warps 2b, 2b+1 (named barrier 1 + b)
-        const int b = warp >> 1, lt = tid & 63, base = DB * b;
-        if (lt < DB) dlc[b][0][lt] = P[pk(base + lt, base)];
-        if (lt == 0) {
-            P[pk(base, base)] = rd[base];
-            dcol[b][0][0] = rd[base];
-        }
-        tc::named_sync(1 + b, 64);
-        for (int k = 0; k < DB - 1; ++k) {
-            const double *ck = dcol[b][k & 1], *lk = dlc[b][k & 1];
-            double *cn = dcol[b][(k + 1) & 1], *ln = dlc[b][(k + 1) & 1];
-            const int ncol = k + 1, cnt = (DB - 1 - k) * ncol;
-            if (lt > k + 1 && lt < DB) ln[lt] = P[pk(base + lt, base + k + 1)];
-            const double rn = rd[base + k + 1];
-            for (int t = lt; t < cnt; t += 64) {
-                const int ii = t / ncol, c = t - ii * ncol, i = k + 1 + ii;
-                const int e = pk(base + i, base + c);
-                const double acc = (c == k) ? 0.0 : P[e];   // slot (i, k) still holds L[i][k]
-                double v = fma(-lk[i], ck[c], acc);
-                if (ii == 0) {
-                    v *= rn;
-                    cn[c] = v;
-                }
-                P[e] = v;
-            }
-            if (lt == 0) {
-                P[pk(base + k + 1, base + k + 1)] = rn;
-                cn[k + 1] = rn;
-            }
-            tc::named_sync(1 + b, 64);
-        }
-    }
-    __syncthreads();
+    if constexpr (S == 5)
+        inv_diag_blocks<ArithDF>(reinterpret_cast<float2 *>(P), reinterpret_cast<float2 *>(rd),
+                                 reinterpret_cast<float2(*)[2][DB]>(dcol), reinterpret_cast<float2(*)[2][DB]>(dlc), tid);
+    else
+        inv_diag_blocks<ArithF64>(P, rd, dcol, dlc, tid);
     if constexpr (S == 5) {
         // 5 slices keep ~40 bits of L_JJ^-1: the off-diagonal blocks of the
         // inverse (most of its work) run in double-float FP32 arithmetic
-        // (~2^-46 per product, FP32 issues at 68x the FP64 rate), from the FP64
-        // factor and diagonal-block inverses converted in place
+        // (~2^-46 per product, FP32 issues at 68x the FP64 rate)
         float2 *P2 = reinterpret_cast<float2 *>(P);
         float2 *Tm2 = reinterpret_cast<float2 *>(Tm);
-        for (int e = tid; e < PK; e += 256) {
-            const double x = P[e];
-            const float h = __double2float_rn(x);
-            P2[e] = make_float2(h, __double2float_rn(x - (double)h));
-        }
-        __syncthreads();
         const float2 z2 = make_float2(0.0f, 0.0f);
         for (int c = 2; c >= 0; --c) {
             const int nres = 3 - c;
