@@ -96,6 +96,13 @@ typedef struct {
  * same shape the executable graph is only updated.  Results are identical to
  * the eager launches.  Ignored together with PLK_FLAG_KERNEL_TIMING. */
 #define PLK_FLAG_GRAPH 8
+/* flags: PLK_MIXED, run the 5-slice pass to the end on every point.  By default
+ * a point stops in that pass once the partial sum of its error bound (which
+ * only grows with further pivots) exceeds the tolerance, or its factorisation
+ * fails: it is re-evaluated with 7 slices in either case, so the results are
+ * identical with and without this flag (it exists for that check and for
+ * timing the full pass).  PLK_FLAG_NO_RETRY implies it. */
+#define PLK_FLAG_FULL_FIRST_PASS 16
 
 /* ------------------------------------------------------------------------ */
 /* Stateless device-pointer evaluation (one dataset, K points)               */

@@ -400,6 +400,8 @@ static plk_status run_mixed_batch(BatchArgs b, const Layout &L, void *ws, const 
     x.err = at<int>(ws, L.off_err);
     x.err_bound = err_bound;
     x.tol = kMixedTol;
+    // without the retry the caller gets every point's 5-slice result
+    x.early = (flags & (PLK_FLAG_NO_RETRY | PLK_FLAG_FULL_FIRST_PASS)) ? 0 : 1;
     auto first = [&]() {
         cudaError_t r = cudaMemsetAsync(x.err, 0, sizeof(int), s);
         return r == cudaSuccess ? mixed_first_pass(b, x, overlap, s) : r;

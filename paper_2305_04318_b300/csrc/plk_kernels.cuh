@@ -73,6 +73,7 @@ struct MixedArgs {
     int *err;            // 1: set by a kernel whose bounded wait gave up
     double *err_bound;   // K (global output, may be NULL)
     double tol;          // retry when the bound exceeds this
+    int early;           // 5-slice pass: stop work on a point once its partial bound exceeds tol
 };
 size_t mixed_img_bytes(int S);
 size_t mixed_slot_bytes();   // panel slot of one tile row

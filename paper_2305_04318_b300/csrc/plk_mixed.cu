@@ -314,6 +314,16 @@ __device__ __forceinline__ int tri_row(int t) {
 // Dynamic shared memory of k_potrf_mixed: the packed tile (66 KB) and three
 // 32 x 32 FP64 temporaries (24 KB); two blocks share an SM.
 constexpr int DB = 32;   // block size of the diagonal-tile factorisation
+
+// eps of the error bound E = eps (1 + nu^2) sum_j 1 / d_j: relative
+// perturbation of the updated entries.  Calibrated on the n = 4000 workload
+// against the FP64 path: with these values the bound exceeded the measured
+// |Delta l_p| on every point (5 slices: by >= 3x; 7 slices with all groups
+// exact: by >= 4.7x, on points whose own FP64 result differs from the CPU
+// oracle by up to 1e-4).
+__host__ __device__ constexpr double mixed_eps(int S) {
+    return S == 7 ? 1.4210854715202004e-14 /* 2^-46 */ : 9.313225746154785e-10 /* 2^-30 */;
+}
 constexpr size_t POTRF_MIXED_SMEM = (size_t)(PK + 3 * DB * DB) * sizeof(double);
 
 // Cholesky of the tile in the packed lower triangle P (number type Ar::T) in
@@ -481,7 +491,9 @@ __device__ __forceinline__ void inv_diag_blocks(typename Ar::T *__restrict__ P, 
 template <int S>
 __global__ void __launch_bounds__(256, 2) k_potrf_mixed(int J, int64_t tpo, double *__restrict__ tiles,
                                                         uint8_t *__restrict__ wimg, double *__restrict__ logdet,
-                                                        double *__restrict__ invsum, int *__restrict__ pstatus) {
+                                                        double *__restrict__ invsum, int *__restrict__ pstatus,
+                                                        const double *__restrict__ oconst, int *__restrict__ doomed,
+                                                        double tol) {
     extern __shared__ double sm[];
     double *P = sm;                   // packed lower triangle: the tile, then L, then W = L^-1
     double *Tm = sm + PK;             // 3 x 32 x 32 temporaries of the block inverse
@@ -493,6 +505,7 @@ __global__ void __launch_bounds__(256, 2) k_potrf_mixed(int J, int64_t tpo, doub
     __shared__ double dlc[4][2][DB];    // per diagonal block: column k of L, staged
     __shared__ double red[2][4];
     const int w = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (doomed && doomed[w]) return;   // already bound for the 7-slice tier
     double *T = tiles + ((int64_t)w * tpo + tile_index(J, J)) * NT;
     const float *H = reinterpret_cast<const float *>(T);
     const float *Lo = H + NT;
@@ -716,8 +729,19 @@ __global__ void __launch_bounds__(256, 2) k_potrf_mixed(int J, int64_t tpo, doub
             bsum += red[1][q];
         }
         logdet[w] += a;
-        invsum[w] += bsum;
+        const double isum = invsum[w] + bsum;
+        invsum[w] = isum;
         if (bad && pstatus[w] == PLK_POINT_OK) pstatus[w] = PLK_POINT_NOT_PD;
+        // early verdict (the retry rule of the 5-slice pass, applied now): the
+        // bound only grows with further pivots (all 1/d_j > 0 while the
+        // factorisation holds), so a point past the tolerance, or one whose
+        // factorisation failed, goes to the 7-slice tier whatever the remaining
+        // panels give
+        if (doomed) {
+            const int st = pstatus[w];
+            const double E = mixed_eps(S) * (1.0 + oconst[OC_N * (int64_t)w + OC_NUG]) * isum;
+            if (st == PLK_POINT_NOT_PD || (st == PLK_POINT_OK && !(E <= tol))) doomed[w] = 1;
+        }
     }
 }
 
@@ -756,7 +780,8 @@ __device__ __forceinline__ void group_value(uint32_t p0, uint32_t p1, uint32_t p
 template <int S>
 __global__ void __launch_bounds__(NTH, 1) k_trsm_split(int J, int nb, int64_t tpo, const double *__restrict__ tiles,
                                                        const uint8_t *__restrict__ wimg, uint8_t *__restrict__ pimg,
-                                                       const double *__restrict__ oconst, int *__restrict__ err) {
+                                                       const double *__restrict__ oconst, const int *__restrict__ doomed,
+                                                       int *__restrict__ err) {
     extern __shared__ uint8_t smraw[];
     uint8_t *sbase = align1024(smraw);
     uint8_t *sA = sbase;             // S blocks of the current K half of A_IJ
@@ -767,6 +792,7 @@ __global__ void __launch_bounds__(NTH, 1) k_trsm_split(int J, int nb, int64_t tp
     __shared__ int sMx[TB];                         // row max |value| as float bits (>= 0)
     __shared__ int s_ok;
     const int w = blockIdx.y, I = J + 1 + blockIdx.x;
+    if (doomed && doomed[w]) return;   // already bound for the 7-slice tier
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const float *H = reinterpret_cast<const float *>(tiles + ((int64_t)w * tpo + tile_index(I, J)) * NT);
     const float *Lo = H + NT;
@@ -990,7 +1016,8 @@ __global__ void __launch_bounds__(pipe::NTHP, 1) k_trail_pipe(int mode, int Klo,
                                                              int nb, int cnt, int64_t tpo,
                                                              const __grid_constant__ CUtensorMap tmapC,
                                                              const uint8_t *__restrict__ pimg,
-                                                             const double *__restrict__ oconst, int *__restrict__ err) {
+                                                             const double *__restrict__ oconst,
+                                                             const int *__restrict__ doomed, int *__restrict__ err) {
     using namespace pipe;
     constexpr int NSET = Cfg<S>::NSET, NA = Cfg<S>::NA, BBUF = Cfg<S>::BBUF, OFF_A = Cfg<S>::OFF_A,
                   OFF_C = Cfg<S>::OFF_C;
@@ -1061,6 +1088,7 @@ __global__ void __launch_bounds__(pipe::NTHP, 1) k_trail_pipe(int mode, int Klo,
             for (int64_t it = blockIdx.x; it < items && !stop; it += gridDim.x) {
                 int w, I, K, ch;
                 decode(it, w, I, K, ch);
+                if (doomed && doomed[w]) continue;
                 for (int ph = 0; ph < 2 * P && !stop; ++ph) {
                     const int h = ph & 1;
                     const uint8_t *ia = image(w, I, ph >> 1), *ib = image(w, K, ph >> 1);
@@ -1097,7 +1125,8 @@ __global__ void __launch_bounds__(pipe::NTHP, 1) k_trail_pipe(int mode, int Klo,
         if (lane == 0) {
             uint32_t acnt = 0, bcnt = 0, tcnt = 0;
             bool issued = false;
-            for (int64_t it = blockIdx.x; it < items && !*verr; it += gridDim.x, ++tcnt) {
+            for (int64_t it = blockIdx.x; it < items && !*verr; it += gridDim.x) {
+                if (doomed && doomed[(int)(it / (2 * T))]) continue;
                 const int set = (NSET == 2) ? (int)(tcnt & 1) : 0;
                 const uint32_t tu = (NSET == 2) ? tcnt >> 1 : tcnt;
                 if (tu > 0 && !tc::mbar_wait(&accEmpty[set], (tu - 1) & 1)) { *verr = 1; break; }
@@ -1144,6 +1173,7 @@ __global__ void __launch_bounds__(pipe::NTHP, 1) k_trail_pipe(int mode, int Klo,
                     tc::mma_commit(&bEmpty[bs]);
                 }
                 tc::mma_commit(&accFull[set]);
+                ++tcnt;
             }
             // let every issued MMA finish before the accumulators are released
             if (issued) {
@@ -1161,9 +1191,10 @@ __global__ void __launch_bounds__(pipe::NTHP, 1) k_trail_pipe(int mode, int Klo,
         const int sw = r & 7;                // 16-byte chunk k of the row sits at k ^ (r % 8)
         uint32_t tcnt = 0;
         bool c_pending = false;              // loads issued and not yet waited for
-        for (int64_t it = blockIdx.x; it < items; it += gridDim.x, ++tcnt) {
+        for (int64_t it = blockIdx.x; it < items; it += gridDim.x) {
             int w, I, K, ch;
             decode(it, w, I, K, ch);
+            if (doomed && doomed[w]) continue;
             // rows of the tile in the tensor map: H plane T*256 .. +127, L plane T*256+128 .. +255
             const int yH = (int)(((int64_t)w * tpo + tile_index(I, K)) * 256);
             if (et == 0) {
@@ -1255,6 +1286,7 @@ __global__ void __launch_bounds__(pipe::NTHP, 1) k_trail_pipe(int mode, int Klo,
                     tc::tma_store_2d(&tmapC, 64 * ch + 32 * (bx & 1), yH + 128 * (bx >> 1), sC + bx * CBOX);
                 tc::bulk_commit();
             }
+            ++tcnt;
         }
         if (et == 0) {
             tc::bulk_wait_all();
@@ -1467,7 +1499,7 @@ __global__ void __launch_bounds__(NTH, 1) k_trsm_split7x(int J, int nb, int64_t 
 // ---------------------------------------------------------------------------
 // E = eps_S * (1 + nu^2) * sum_j 1/d_j, d_j the pivots: a first-order bound on
 // |Delta log|V|| from a relative perturbation eps_S of each updated entry.
-__global__ void k_mixed_bound(int count, int64_t k0, double eps, double tol, int flag_not_pd,
+__global__ void k_mixed_bound(int count, int64_t k0, double eps, double tol, int flag_not_pd, int keep_doomed,
                               const double *__restrict__ oconst, const double *__restrict__ invsum,
                               const int *__restrict__ pstatus, const int *__restrict__ out_index, double *err_bound,
                               int *flags) {
@@ -1477,7 +1509,10 @@ __global__ void k_mixed_bound(int count, int64_t k0, double eps, double tol, int
     const int64_t k = out_index ? (int64_t)out_index[w] : k0 + w;
     if (err_bound) err_bound[k] = E;
     const int st = pstatus[w];
-    flags[w] = ((flag_not_pd && st == PLK_POINT_NOT_PD) || (st == PLK_POINT_OK && !(E <= tol))) ? 1 : 0;
+    // a point marked by the early verdict stopped part-way: its status and
+    // results are incomplete, it is re-evaluated in any case
+    const bool doomed = keep_doomed && flags[w];
+    flags[w] = (doomed || (flag_not_pd && st == PLK_POINT_NOT_PD) || (st == PLK_POINT_OK && !(E <= tol))) ? 1 : 0;
 }
 
 __global__ void k_scatter_value(int count, const int *__restrict__ idx, double v, double *out) {
@@ -1549,6 +1584,10 @@ static cudaError_t launch_mixed_steps(const BatchArgs &b, const MixedArgs &x, cu
                                   (int)POTRF_MIXED_SMEM)) != cudaSuccess)
         return e;
     cudaMemsetAsync(x.invsum, 0, sizeof(double) * cnt, s);
+    // 5-slice pass with the early verdict: flags marks the points already bound
+    // for the 7-slice tier (the bound kernel keeps the marks)
+    int *doomed = (S == 5 && x.early) ? x.flags : nullptr;
+    if (doomed) cudaMemsetAsync(doomed, 0, sizeof(int) * cnt, s);
     CUtensorMap tmapC;
     if ((e = make_tile_map(&tmapC, b.tiles, cnt, b.tpo)) != cudaSuccess) return e;
     const int sms = num_sms();
@@ -1561,7 +1600,7 @@ static cudaError_t launch_mixed_steps(const BatchArgs &b, const MixedArgs &x, cu
             return e;
         for (int J = 0; J < nb; ++J) {
             TIMED(KC_POTRF_MIXED, (k_potrf_mixed<S><<<cnt, 256, POTRF_MIXED_SMEM, s>>>(
-                                      J, b.tpo, b.tiles, x.wimg, b.ldv, x.invsum, b.pstatus)));
+                                      J, b.tpo, b.tiles, x.wimg, b.ldv, x.invsum, b.pstatus, b.oconst, nullptr, x.tol)));
             const int m = nb - J;
             TIMED(KC_TRSM_SPLIT7, (k_trsm_split7x<<<dim3(m, cnt), NTH, smem_split, s>>>(J, nb, b.tpo, b.tiles, x.wimg,
                                                                                       x.pimg, x.err)));
@@ -1569,7 +1608,7 @@ static cudaError_t launch_mixed_steps(const BatchArgs &b, const MixedArgs &x, cu
             const int64_t items = (int64_t)cnt * (m * (m + 1) / 2) * 2;
             const int grid = (int)std::min<int64_t>(items, sms);
             TIMED(KC_GEMM_SPLIT7, (k_trail_pipe<7><<<grid, pipe::NTHP, pipe::Cfg<7>::SMEM, s>>>(
-                                      0, J + 1, nb, 1, 0, 0, nb, cnt, b.tpo, tmapC, x.pimg, b.oconst, x.err)));
+                                      0, J + 1, nb, 1, 0, 0, nb, cnt, b.tpo, tmapC, x.pimg, b.oconst, nullptr, x.err)));
         }
     } else {
         if ((e = cudaFuncSetAttribute(k_trsm_split<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_split)) !=
@@ -1584,13 +1623,14 @@ static cudaError_t launch_mixed_steps(const BatchArgs &b, const MixedArgs &x, cu
             const int64_t items = (int64_t)cnt * ((mode == 0) ? m * (m + 1) / 2 : m) * 2;
             const int grid = (int)std::min<int64_t>(items, sms);
             TIMED(KC_GEMM_SPLIT, (k_trail_pipe<5><<<grid, pipe::NTHP, pipe::Cfg<5>::SMEM, s>>>(
-                                     mode, Klo, Ihi, P, sub0, sub1, nb, cnt, b.tpo, tmapC, x.pimg, b.oconst, x.err)));
+                                     mode, Klo, Ihi, P, sub0, sub1, nb, cnt, b.tpo, tmapC, x.pimg, b.oconst, doomed,
+                                     x.err)));
         };
         auto factor_panel = [&](int J) {
             TIMED(KC_POTRF_MIXED, (k_potrf_mixed<S><<<cnt, 256, POTRF_MIXED_SMEM, s>>>(
-                                      J, b.tpo, b.tiles, x.wimg, b.ldv, x.invsum, b.pstatus)));
+                                      J, b.tpo, b.tiles, x.wimg, b.ldv, x.invsum, b.pstatus, b.oconst, doomed, x.tol)));
             TIMED(KC_TRSM_SPLIT, (k_trsm_split<S><<<dim3(nb - J, cnt), NTH, smem_split, s>>>(
-                                     J, nb, b.tpo, b.tiles, x.wimg, x.pimg, b.oconst, x.err)));
+                                     J, nb, b.tpo, b.tiles, x.wimg, x.pimg, b.oconst, doomed, x.err)));
         };
         // Two-panel look-ahead: factor panel J0, bring tile column J0+1 up to
         // date with it, factor J0+1, then update the right-hand-side row with
@@ -1627,14 +1667,10 @@ cudaError_t launch_mixed_back(const BatchArgs &b, const MixedArgs &x, int S, cud
     cudaError_t e = (S == 7) ? launch_mixed_steps<7>(b, x, s) : launch_mixed_steps<5>(b, x, s);
     if (e != cudaSuccess) return e;
     if ((e = launch_finalize(b, s)) != cudaSuccess) return e;
-    // eps: relative perturbation of the updated entries.  Calibrated on the
-    // n = 4000 workload against the FP64 path: with these values the bound
-    // exceeded the measured |Delta l_p| on every point (5 slices: by >= 3x;
-    // 7 slices with all groups exact: by >= 4.7x, on points whose own FP64
-    // result differs from the CPU oracle by up to 1e-4).
-    const double eps = (S == 7) ? ldexp(1.0, -46) : ldexp(1.0, -30);
-    k_mixed_bound<<<(b.count + 127) / 128, 128, 0, s>>>(b.count, b.k0, eps, x.tol, S == 5 ? 1 : 0, b.oconst,
-                                                       x.invsum, b.pstatus, b.out_index, x.err_bound, x.flags);
+    const double eps = mixed_eps(S);
+    k_mixed_bound<<<(b.count + 127) / 128, 128, 0, s>>>(b.count, b.k0, eps, x.tol, S == 5 ? 1 : 0,
+                                                       S == 5 && x.early ? 1 : 0, b.oconst, x.invsum, b.pstatus,
+                                                       b.out_index, x.err_bound, x.flags);
     return cudaGetLastError();
 }
 

@@ -108,6 +108,32 @@ def test_mixed_overlapped_parts_identical(K):
     assert (a["status"] & 15 == 0).sum() > 0.8 * K
 
 
+@pytest.mark.parametrize("K", [80, 300])
+def test_early_verdict_identical_to_full_first_pass(K):
+    """A point stops in the 5-slice pass once its partial error bound exceeds
+    the tolerance (or its factorisation fails) and goes to the 7-slice tier,
+    as it would after the full pass: the results, statuses and bounds are the
+    same bit for bit as with the 5-slice pass run to the end on every point.
+    Ill-conditioned points (kappa = 8, long ranges, tiny nuggets) mixed with
+    points across the box; n = 700 (6 tiles, so verdicts come part-way), one
+    batch (K = 80) and overlapped parts (K = 300)."""
+    ds = synth.aniso_dataset(78, 700, math.sqrt(70), 3)
+    rng = np.random.default_rng(78)
+    ill = synth.ill_conditioned_points()
+    n_ill = min(K // 4, len(ill))
+    P = np.vstack([ill[rng.permutation(len(ill))[:n_ill]],
+                   synth.omega_from_unit(rng.uniform(size=(K - n_ill, 5)))])
+    P = P[rng.permutation(K)]
+    lams = synth.LAMBDA_GRID_9
+    a = gpu_eval(ds, P, lams, precision=nv.MIXED, batch=K)
+    b = gpu_eval(ds, P, lams, precision=nv.MIXED, batch=K, flags=nv.FLAG_FULL_FIRST_PASS)
+    for k in ("logL", "sigma2", "beta", "logdet", "status", "err_bound"):
+        np.testing.assert_array_equal(a[k], b[k], err_msg=k)
+    retried = int(((a["status"] & nv.POINT_RETRIED) != 0).sum())
+    print(json.dumps(dict(K=K, retried=retried)))
+    assert retried >= 4
+
+
 @pytest.mark.parametrize("which", [0, 2])
 def test_mixed_profile_ci_endpoints(which):
     """Likelihood-CI endpoints (eq. likelihood) from a profile job in mixed
