@@ -292,10 +292,159 @@ __global__ void __launch_bounds__(256) k_table_union(int cnt, double *__restrict
     }
 }
 
+// ---------------------------------------------------------------------------
+// Double-float (FP32 pair) arithmetic for the first pass's table
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void two_sum_f(float a, float b, float &s, float &e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+__device__ __forceinline__ void fast_two_sum_f(float a, float b, float &s, float &e) {   // |a| >= |b| or a = 0
+    s = __fadd_rn(a, b);
+    e = __fsub_rn(b, __fsub_rn(s, a));
+}
+// (ph, pl) <- (ph, pl) * (th, tl) + (ch, cl), dropping pl * tl
+__device__ __forceinline__ void df_horner_step(float &ph, float &pl, float th, float tl, float ch, float cl) {
+    const float x = __fmul_rn(ph, th);
+    float ex = __fmaf_rn(ph, th, -x);
+    ex = __fmaf_rn(ph, tl, ex);
+    ex = __fmaf_rn(pl, th, ex);
+    float s, es;
+    two_sum_f(x, ch, s, es);
+    ph = s;
+    pl = __fadd_rn(__fadd_rn(es, ex), cl);
+}
+
+// ln 2 in three parts: 16 significant bits (k LN2_HI is exact for |k| < 2^8),
+// then two FP32 parts of the remainder (from the double ln 2, ~2^-54 relative)
+constexpr double LN2_D = 0.69314718055994530942;
+constexpr float LN2_HI = 45426.0f / 65536.0f;
+constexpr float LN2_MID = (float)(LN2_D - (double)LN2_HI);
+constexpr float LN2_LO = (float)(LN2_D - (double)LN2_HI - (double)LN2_MID);
+// 1 / n! as double-float, n = 2..4 (the higher terms need only FP32)
+constexpr float IF2 = 0.5f;
+constexpr float IF3H = (float)(1.0 / 6.0), IF3L = (float)(1.0 / 6.0 - (double)IF3H);
+constexpr float IF4H = (float)(1.0 / 24.0), IF4L = (float)(1.0 / 24.0 - (double)IF4H);
+
+// exp(x) for the double-float x = xh + xl, |x| <= 86 (0 below -86): relative
+// error ~2^-45 for x >= -50 (below, the low part of the result leaves the FP32
+// normal range; such terms are far below the sums they enter).  x = k ln2 + r with k = rint(x / ln2), |r| <= ln2 / 2 formed
+// from the three-part ln 2 (k ln2_hi exact, k ln2_mid split exactly);
+// exp(r) = p(r / 4)^4 with p the Taylor polynomial of degree 9 (remainder
+// (ln2 / 8)^10 / 10! < 2^-56): terms 5..9 by Horner in FP32 (each below 2^-22,
+// so their rounding stays below 2^-46), terms 0..4 in double-float; two
+// double-float squarings; then 2^k.
+__device__ __forceinline__ void df_exp(float xh, float xl, float &yh, float &yl) {
+    if (xh != xh) {
+        yh = xh;
+        yl = 0.0f;
+        return;
+    }
+    if (xh < -86.0f) {
+        yh = yl = 0.0f;
+        return;
+    }
+    if (xh > 86.0f) {
+        yh = INFINITY;
+        yl = 0.0f;
+        return;
+    }
+    const float kf = rintf(__fmul_rn(xh, 1.44269504088896341f));
+    const float t = __fmaf_rn(-kf, LN2_HI, xh);   // exact
+    const float p = __fmul_rn(kf, LN2_MID);
+    const float pe = __fmaf_rn(kf, LN2_MID, -p);  // k ln2_mid = p + pe
+    float s, e, s2, e2;
+    two_sum_f(t, -p, s, e);
+    two_sum_f(s, xl, s2, e2);   // xl (up to 2^-24 |x|) joins exactly
+    e = __fsub_rn(__fadd_rn(e, e2), __fmaf_rn(kf, LN2_LO, pe));
+    float rh, rl;
+    two_sum_f(s2, e, rh, rl);
+    rh *= 0.25f;
+    rl *= 0.25f;
+    float q = 1.0f / 362880.0f;                 // 1/9!
+    q = __fmaf_rn(q, rh, 1.0f / 40320.0f);
+    q = __fmaf_rn(q, rh, 1.0f / 5040.0f);
+    q = __fmaf_rn(q, rh, 1.0f / 720.0f);
+    q = __fmaf_rn(q, rh, 1.0f / 120.0f);
+    float ph = q, pl = 0.0f;
+    df_horner_step(ph, pl, rh, rl, IF4H, IF4L);
+    df_horner_step(ph, pl, rh, rl, IF3H, IF3L);
+    df_horner_step(ph, pl, rh, rl, IF2, 0.0f);
+    df_horner_step(ph, pl, rh, rl, 1.0f, 0.0f);
+    df_horner_step(ph, pl, rh, rl, 1.0f, 0.0f);
+    fast_two_sum_f(ph, pl, ph, pl);
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {   // square
+        const float x = __fmul_rn(ph, ph);
+        float ex = __fmaf_rn(ph, ph, -x);
+        ex = __fmaf_rn(2.0f * ph, pl, ex);
+        fast_two_sum_f(x, ex, ph, pl);
+    }
+    const float sc = __int_as_float(((int)kf + 127) << 23);   // 2^k, k in [-125, 125]
+    yh = ph * sc;
+    yl = pl * sc;
+}
+
+// The trapezoid sum of the table's fixed grid in double-float arithmetic
+// (the first pass's table, whose entries need ~2^-40; FP64 issues at 1/68 of
+// FP32 on this part).  The terms exp(a_k), a_k = log cosh(kappa t_k) - u (cosh t_k
+// - 1), are scaled by exp(-A) with A the largest a_k (an FP32 scan), so that
+// they stay in the FP32 range (the unscaled ones reach e^350 at kappa = 20);
+// the sum and its stopping rule are those of the FP64 evaluation.  Each a_k
+// carries the double-float rounding of its two parts, ~2^-48 of the larger
+// (|a_k| <= kappa t_k): ~1e-13 of rho at kappa <= 8.
+__device__ __forceinline__ double rho_nodes_df(double u, double kap, double logc, const float2 *__restrict__ E1f,
+                                               const float2 *__restrict__ L2f) {
+    const float uh = __double2float_rn(u), ul = __double2float_rn(u - (double)uh);
+    float A = 0.0f;   // a_0 = 0
+    for (int k = 1; k < QNODES; ++k) A = fmaxf(A, __fmaf_rn(-uh, E1f[k].x, L2f[k].x));
+    float sh, sl;
+    df_exp(-A, 0.0f, sh, sl);
+    float prev = sh;
+    sh *= 0.5f;
+    sl *= 0.5f;
+    bool stop = false;
+    for (int k = 1; k < QNODES && !stop; k += 4) {
+        float gh[4], gl[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            if (k + i < QNODES) {
+                const float2 e1 = E1f[k + i], l2 = L2f[k + i];
+                // a_k - A = l2 - u e1 - A, the product split exactly
+                const float pr = __fmul_rn(uh, e1.x);
+                float pe = __fmaf_rn(uh, e1.x, -pr);
+                pe = __fmaf_rn(uh, e1.y, pe);
+                pe = __fmaf_rn(ul, e1.x, pe);
+                float s1, e1s, s2, e2s;
+                two_sum_f(l2.x, -pr, s1, e1s);
+                two_sum_f(s1, -A, s2, e2s);
+                df_exp(s2, __fadd_rn(__fadd_rn(e1s, e2s), __fsub_rn(l2.y, pe)), gh[i], gl[i]);
+            } else {
+                gh[i] = gl[i] = 0.0f;
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            if (stop || k + i >= QNODES) {
+                stop = true;
+                continue;
+            }
+            float s, e;
+            two_sum_f(sh, gh[i], s, e);
+            fast_two_sum_f(s, __fadd_rn(e, __fadd_rn(sl, gl[i])), sh, sl);
+            if (gh[i] < prev && gh[i] < 1e-18f * sh) stop = true;
+            prev = gh[i];
+        }
+    }
+    return exp(logc + kap * log(u) - u + (double)A) * (QH * ((double)sh + (double)sl));
+}
+
 // Table builder: one block of 320 threads = 32 sub-intervals x TAB_NC Chebyshev nodes.
 // F32TAB writes each sub-interval's coefficients as TAB_F32 floats instead of
 // TAB_NC doubles: c_0..c_3 as double-float pairs, c_4..c_9 rounded to FP32
-// (the layout k_build_f32 reads; it fits in the same per-point region).
+// (the layout k_build_f32 reads; it fits in the same per-point region), and
+// sums the fixed-grid trapezoid rule in double-float arithmetic (rho_nodes_df).
 // For u <= TAB_USPLIT the trapezoid nodes are the fixed grid t_k = k QH, whose
 // cosh(t_k) - 1 and log cosh(kappa t_k) are staged in shared memory, so one exp
 // per node remains.
@@ -304,6 +453,7 @@ __global__ void __launch_bounds__(320) k_matern_table(const double *__restrict__
                                                       double *__restrict__ tab, const int *__restrict__ owner) {
     __shared__ double E1[QNODES];   // cosh(t_k) - 1 = 2 sinh^2(t_k / 2)
     __shared__ double L2[QNODES];   // log cosh(kappa t_k)
+    __shared__ float2 E1f[F32TAB ? QNODES : 1], L2f[F32TAB ? QNODES : 1];   // the same as double-float
     __shared__ double F[32][TAB_NC];
     __shared__ double A[32][TAB_NC];          // Chebyshev coefficients per bucket
     __shared__ double CT[TAB_NC][TAB_NC];     // cos(pi k (m + 1/2) / NC)
@@ -325,6 +475,11 @@ __global__ void __launch_bounds__(320) k_matern_table(const double *__restrict__
         E1[k] = 2.0 * sh * sh;
         const double kt = kap * t;
         L2[k] = kt + log1p(exp(-2.0 * kt)) - 0.69314718055994530942;
+        if constexpr (F32TAB) {
+            const float eh = __double2float_rn(E1[k]), lh = __double2float_rn(L2[k]);
+            E1f[k] = make_float2(eh, __double2float_rn(E1[k] - (double)eh));
+            L2f[k] = make_float2(lh, __double2float_rn(L2[k] - (double)lh));
+        }
     }
     if (threadIdx.x < TAB_NC * TAB_NC) {
         const int k = threadIdx.x / TAB_NC, m = threadIdx.x % TAB_NC;
@@ -350,6 +505,8 @@ __global__ void __launch_bounds__(320) k_matern_table(const double *__restrict__
         double r;
         if (kap != kap || !(kap > 0.0)) {
             r = nan("");
+        } else if (F32TAB && u <= TAB_USPLIT) {
+            r = rho_nodes_df(u, kap, logc, E1f, L2f);
         } else if (u <= TAB_USPLIT) {
             // the terms of four nodes are computed ahead (independent exps),
             // then added in order with the same stopping rule
@@ -524,26 +681,6 @@ __global__ void __launch_bounds__(256) k_build(int nb, int64_t n, int64_t n_pad,
 // Against the FP64 evaluation of the same polynomial the entries differ by
 // ~1e-13 absolute, four orders below the 5-slice products' 2^-30 relative
 // error.  Pairs outside the table's octaves take the FP64 integral (rare).
-__device__ __forceinline__ void two_sum_f(float a, float b, float &s, float &e) {
-    s = __fadd_rn(a, b);
-    const float bb = __fsub_rn(s, a);
-    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-}
-__device__ __forceinline__ void fast_two_sum_f(float a, float b, float &s, float &e) {   // |a| >= |b| or a = 0
-    s = __fadd_rn(a, b);
-    e = __fsub_rn(b, __fsub_rn(s, a));
-}
-// (ph, pl) <- (ph, pl) * (th, tl) + (ch, cl), dropping pl * tl
-__device__ __forceinline__ void df_horner_step(float &ph, float &pl, float th, float tl, float ch, float cl) {
-    const float x = __fmul_rn(ph, th);
-    float ex = __fmaf_rn(ph, th, -x);
-    ex = __fmaf_rn(ph, tl, ex);
-    ex = __fmaf_rn(pl, th, ex);
-    float s, es;
-    two_sum_f(x, ch, s, es);
-    ph = s;
-    pl = __fadd_rn(__fadd_rn(es, ex), cl);
-}
 // (volatile: the load must not be moved ahead of the range checks that guard
 // its address)
 __device__ __forceinline__ void ldg_v8(const float *p, float (&v)[8]) {   // 32-byte aligned
