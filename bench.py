@@ -36,14 +36,15 @@ import numpy as np
 # DRAM traffic of the dominant mixed-path kernel, k_trail_pipe<5>, from one ncu
 # capture (dram__bytes_read.sum + dram__bytes_write.sum, a one-pass metric set)
 # of `python bench.py --precision mixed --steps 1 --warmup 1 --no-cpu-baseline
-# --no-e2e`: mean bytes per launch over the 126 launches of one 592-point
-# evaluation at n = 4000 (two parts of 296 points; every launch covers one
-# part).  Valid for that workload with parts of 296 points (batches that are
+# --no-e2e`: mean bytes per launch over the 504 launches of two 1184-point
+# evaluations at n = 4000 (four parts of 296 points each; every launch covers
+# one part; the points stopped early by the error bound skip their items).
+# Valid for that workload with parts of 296 points (batches that are
 # multiples of 296 from 592 up) and for the kernel source it was taken on
 # (SHA-256 of the trailing kernel's region and the PTX wrappers, below);
 # otherwise traffic is null.
-TRAIL_TRAFFIC = {"n": 4000, "part": 296, "bytes_per_launch": 5.105e9, "read": 3.067e9, "write": 2.038e9,
-                 "launches_per_eval": 126, "sources_sha256": "78b147b2b200c3b2b5558875e1b58c8e4a1fce8b57d9cbaa86cc8c0af1d86aa6"}
+TRAIL_TRAFFIC = {"n": 4000, "part": 296, "bytes_per_launch": 4.930e9, "read": 2.991e9, "write": 1.940e9,
+                 "launches_per_eval": 252, "sources_sha256": "30fc739bf892a24c1ebf442be7c21a3363364c7fa18c9609f98ea6a6e6766ac6"}
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
@@ -736,18 +737,22 @@ def main():
     elif dom == "trailing_split":
         n7 = int(((st & nv.POINT_RETRIED) != 0).sum())
         n64 = int(((st & nv.POINT_FP64) != 0).sum())
-        # every point runs the 5-slice pass (this kernel); retried points add a
-        # 7-slice pass in separate kernels (trailing_split7)
+        # every point enters the 5-slice pass (this kernel); a point that is
+        # re-evaluated with 7 slices (in separate kernels, trailing_split7) leaves
+        # it early once its partial error bound passes the tolerance, so only the
+        # points that complete it are counted (a lower bound: the retried
+        # points' partial work is left out)
+        n5 = n_pts - n7
         tiles = sum((nb - J) * (nb - J + 1) // 2 for J in range(nb))
-        executed = 2.0 * 128 ** 3 * tiles * split_pairs(5) * n_pts
+        executed = 2.0 * 128 ** 3 * tiles * split_pairs(5) * n5
         peak = peaks.get("bf16_tflops_sustained") or 1341.1
-        alg = tf * n_pts / (dom_ms * 1e-3) / 1e12
+        alg = tf * n5 / (dom_ms * 1e-3) / 1e12
         roof = {"bound": "tensor", "achieved": alg, "peak": peak, "unit": "TFLOP/s", "frac": alg / peak,
                 "traffic": trail_traffic(n, Bm), "kernel": "k_trail_pipe (5-slice split-bf16 trailing update, tcgen05, persistent)",
-                "achieved_is": "algorithmic FP64-equivalent trailing-update flops (n^3/3 + n^2 q per omega) / kernel time",
+                "achieved_is": "algorithmic FP64-equivalent trailing-update flops (n^3/3 + n^2 q per omega, omega that complete the 5-slice pass) / kernel time",
                 "executed_bf16_tflops": executed / (dom_ms * 1e-3) / 1e12,
                 "executed_frac": executed / (dom_ms * 1e-3) / 1e12 / peak,
-                "executed_is": "bf16 MMA flops issued by this kernel: 15 slice products per multiply-add, 128x128 tiles",
+                "executed_is": "bf16 MMA flops issued by this kernel for the omega that complete the 5-slice pass: 15 slice products per multiply-add, 128x128 tiles",
                 "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (kernel timed inside a long step)",
                 "fp64_equivalent_over_fp64_fma_peak": alg / fp64_peak,
                 "points_7slice": n7, "points_fp64": n64}
