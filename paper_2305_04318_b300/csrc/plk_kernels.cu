@@ -386,47 +386,136 @@ __device__ __forceinline__ void df_exp(float xh, float xl, float &yh, float &yl)
     yl = pl * sc;
 }
 
-// The trapezoid sum of the table's fixed grid in double-float arithmetic
-// (the first pass's table, whose entries need ~2^-40; FP64 issues at 1/68 of
-// FP32 on this part).  The terms exp(a_k), a_k = log cosh(kappa t_k) - u (cosh t_k
-// - 1), are scaled by exp(-A) with A the largest a_k (an FP32 scan), so that
-// they stay in the FP32 range (the unscaled ones reach e^350 at kappa = 20);
-// the sum and its stopping rule are those of the FP64 evaluation.  Each a_k
-// carries the double-float rounding of its two parts, ~2^-48 of the larger
-// (|a_k| <= kappa t_k): ~1e-13 of rho at kappa <= 8.
-__device__ __forceinline__ double rho_nodes_df(double u, double kap, double logc, const float2 *__restrict__ E1f,
-                                               const float2 *__restrict__ L2f) {
-    const float uh = __double2float_rn(u), ul = __double2float_rn(u - (double)uh);
-    float A = 0.0f;   // a_0 = 0
-    for (int k = 1; k < QNODES; ++k) A = fmaxf(A, __fmaf_rn(-uh, E1f[k].x, L2f[k].x));
+// 1 / a for a double-float a > 0: FP32 reciprocal y, then y + y (1 - a y) with
+// the residual formed to ~2^-47 (a_hi y split exactly)
+__device__ __forceinline__ void df_recip(float ah, float al, float &yh, float &yl) {
+    const float y = __frcp_rn(ah);
+    const float p = __fmul_rn(ah, y);
+    const float pe = __fmaf_rn(ah, y, -p);
+    const float r = __fsub_rn(__fsub_rn(1.0f, p), __fmaf_rn(al, y, pe));   // 1 - p is exact
+    fast_two_sum_f(y, __fmul_rn(y, r), yh, yl);
+}
+// (ah, al) * (bh, bl), dropping al bl, normalised
+__device__ __forceinline__ void df_mul(float ah, float al, float bh, float bl, float &ph, float &pl) {
+    const float p = __fmul_rn(ah, bh);
+    float e = __fmaf_rn(ah, bh, -p);
+    e = __fmaf_rn(ah, bl, e);
+    e = __fmaf_rn(al, bh, e);
+    fast_two_sum_f(p, e, ph, pl);
+}
+constexpr float IF5H = (float)(1.0 / 120.0), IF5L = (float)(1.0 / 120.0 - (double)IF5H);
+constexpr float IF7H = (float)(1.0 / 5040.0), IF7L = (float)(1.0 / 5040.0 - (double)IF7H);
+
+// 2 sinh^2(x) = cosh(2x) - 1 for an FP32 x >= 0 (x <= 43) as double-float,
+// relative error ~2^-45.  x < 1/2: sinh x = x sum_n y^n / (2n+1)!, y = x^2
+// (terms n >= 4 in FP32, each below 2^-26 relative; remainder y^8 / 17! <
+// 2^-64); else (e^x - e^-x) / 2 with the double-float exp and reciprocal
+// (no cancellation: e^-x <= 0.61 e^x).
+__device__ __forceinline__ void df_e1(float x, float &eh, float &el) {
     float sh, sl;
+    if (x < 0.5f) {
+        const float yh = __fmul_rn(x, x), yl = __fmaf_rn(x, x, -yh);
+        float q = 1.0f / 1307674368000.0f;        // 1/15!
+        q = __fmaf_rn(q, yh, 1.0f / 6227020800.0f);   // 1/13!
+        q = __fmaf_rn(q, yh, 1.0f / 39916800.0f);     // 1/11!
+        q = __fmaf_rn(q, yh, 1.0f / 362880.0f);       // 1/9!
+        float ph = q, pl = 0.0f;
+        df_horner_step(ph, pl, yh, yl, IF7H, IF7L);
+        df_horner_step(ph, pl, yh, yl, IF5H, IF5L);
+        df_horner_step(ph, pl, yh, yl, IF3H, IF3L);
+        df_horner_step(ph, pl, yh, yl, 1.0f, 0.0f);
+        fast_two_sum_f(ph, pl, ph, pl);
+        const float p = __fmul_rn(x, ph);
+        fast_two_sum_f(p, __fmaf_rn(x, pl, __fmaf_rn(x, ph, -p)), sh, sl);
+    } else {
+        float Eh, El, Ih, Il;
+        df_exp(x, 0.0f, Eh, El);
+        df_recip(Eh, El, Ih, Il);
+        float s, e;
+        two_sum_f(Eh, -Ih, s, e);
+        fast_two_sum_f(s, __fadd_rn(e, __fsub_rn(El, Il)), sh, sl);
+        sh *= 0.5f;
+        sl *= 0.5f;
+    }
+    df_mul(sh, sl, sh, sl, eh, el);
+    eh *= 2.0f;
+    el *= 2.0f;
+}
+
+// Trapezoid sum of the first pass's table in double-float arithmetic (its
+// entries need ~2^-40; FP64 issues at 1/68 of FP32 on this part).  With the
+// integrand written as cosh(kappa t) e^{-u (cosh t - 1)} =
+// e^{a(t)} (1 + e^{-2 kappa t}) / 2, a(t) = kappa t - u (cosh t - 1):
+//   fixed grid (u <= TAB_USPLIT): nodes t_k = k QH, cosh t_k - 1 staged in
+//     E1f; the terms are scaled by e^{-A}, A the largest a(t_k) (an FP32 scan),
+//     so that they stay in the FP32 range (a reaches 350 at kappa = 20);
+//   adaptive (u > TAB_USPLIT): step h = the power of two at or below
+//     min(0.1, 0.45 / sqrt(u)) (so that t_k = k h is exact), cosh t_k - 1 from
+//     df_e1, A = 0 (a stays below kappa^2 / (2u) < 13).
+// e^{-2 kappa t_k} = r^k by repeated double-float products.  Each a(t_k) carries
+// ~2^-48 of the larger of its two parts (<= kappa t_k): ~1e-13 of rho at
+// kappa <= 8.  The stopping rule is that of the FP64 evaluation.
+__device__ __forceinline__ double rho_df(double u, double kap, double logc, const float2 *__restrict__ E1f) {
+    const bool fixed = u <= TAB_USPLIT;
+    const float uh = __double2float_rn(u), ul = __double2float_rn(u - (double)uh);
+    const float kh = __double2float_rn(kap), kl = __double2float_rn(kap - (double)kh);
+    float h;
+    if (fixed) {
+        h = (float)QH;
+    } else {
+        int ex;
+        frexpf(fminf(0.1f, 0.45f * rsqrtf(uh)), &ex);   // value in [2^(ex-1), 2^ex)
+        h = __int_as_float((ex - 1 + 127) << 23);
+    }
+    float A = 0.0f;   // a(0) = 0
+    if (fixed)
+        for (int k = 1; k < QNODES; ++k) A = fmaxf(A, __fmaf_rn(-uh, E1f[k].x, kh * (float)k * h));
+    float rh, rl;   // r = e^{-2 kappa h}
+    {
+        const float t2 = __fmul_rn(-2.0f * kh, h), t2e = __fmaf_rn(-2.0f * kh, h, -t2);   // exact split
+        df_exp(t2, __fmaf_rn(-2.0f * kl, h, t2e), rh, rl);
+    }
+    float sh, sl;    // sum: the node t = 0 (weight 1/2, term 2 e^{-A})
     df_exp(-A, 0.0f, sh, sl);
-    float prev = sh;
-    sh *= 0.5f;
-    sl *= 0.5f;
+    float prev = 2.0f * sh;
+    float qh = 1.0f, ql = 0.0f;   // r^k
+    const int kmax = fixed ? QNODES : 8192;
     bool stop = false;
-    for (int k = 1; k < QNODES && !stop; k += 4) {
+    for (int k = 1; k < kmax && !stop; k += 4) {
         float gh[4], gl[4];
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
-            if (k + i < QNODES) {
-                const float2 e1 = E1f[k + i], l2 = L2f[k + i];
-                // a_k - A = l2 - u e1 - A, the product split exactly
-                const float pr = __fmul_rn(uh, e1.x);
-                float pe = __fmaf_rn(uh, e1.x, -pr);
-                pe = __fmaf_rn(uh, e1.y, pe);
-                pe = __fmaf_rn(ul, e1.x, pe);
-                float s1, e1s, s2, e2s;
-                two_sum_f(l2.x, -pr, s1, e1s);
-                two_sum_f(s1, -A, s2, e2s);
-                df_exp(s2, __fadd_rn(__fadd_rn(e1s, e2s), __fsub_rn(l2.y, pe)), gh[i], gl[i]);
+            gh[i] = gl[i] = 0.0f;
+            if (k + i >= kmax) continue;
+            const float t = (float)(k + i) * h;   // exact
+            float e1h, e1l;
+            if (fixed) {
+                e1h = E1f[k + i].x;
+                e1l = E1f[k + i].y;
             } else {
-                gh[i] = gl[i] = 0.0f;
+                df_e1(0.5f * t, e1h, e1l);
             }
+            // a - A = kappa t - u e1 - A, each product split exactly
+            const float kt = __fmul_rn(kh, t), kte = __fmaf_rn(kh, t, -kt);
+            const float pr = __fmul_rn(uh, e1h);
+            float pe = __fmaf_rn(uh, e1h, -pr);
+            pe = __fmaf_rn(uh, e1l, pe);
+            pe = __fmaf_rn(ul, e1h, pe);
+            float s1, c1, s2, c2;
+            two_sum_f(kt, -pr, s1, c1);
+            two_sum_f(s1, -A, s2, c2);
+            const float lo = __fadd_rn(__fadd_rn(c1, c2), __fsub_rn(__fmaf_rn(kl, t, kte), pe));
+            float xh, xl;
+            df_exp(s2, lo, xh, xl);
+            df_mul(qh, ql, rh, rl, qh, ql);   // r^(k+i)
+            float oh, ol;                      // 1 + r^(k+i)
+            two_sum_f(1.0f, qh, oh, ol);
+            ol = __fadd_rn(ol, ql);
+            df_mul(xh, xl, oh, ol, gh[i], gl[i]);
         }
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
-            if (stop || k + i >= QNODES) {
+            if (stop || k + i >= kmax) {
                 stop = true;
                 continue;
             }
@@ -437,23 +526,26 @@ __device__ __forceinline__ double rho_nodes_df(double u, double kap, double logc
             prev = gh[i];
         }
     }
-    return exp(logc + kap * log(u) - u + (double)A) * (QH * ((double)sh + (double)sl));
+    return exp(logc + kap * log(u) - u + (double)A) * (0.5 * (double)h * ((double)sh + (double)sl));
 }
 
 // Table builder: one block of 320 threads = 32 sub-intervals x TAB_NC Chebyshev nodes.
 // F32TAB writes each sub-interval's coefficients as TAB_F32 floats instead of
 // TAB_NC doubles: c_0..c_3 as double-float pairs, c_4..c_9 rounded to FP32
 // (the layout k_build_f32 reads; it fits in the same per-point region), and
-// sums the fixed-grid trapezoid rule in double-float arithmetic (rho_nodes_df).
+// sums the trapezoid rules in double-float arithmetic (rho_df).
 // For u <= TAB_USPLIT the trapezoid nodes are the fixed grid t_k = k QH, whose
 // cosh(t_k) - 1 and log cosh(kappa t_k) are staged in shared memory, so one exp
 // per node remains.
 template <bool F32TAB>
 __global__ void __launch_bounds__(320) k_matern_table(const double *__restrict__ oconst,
                                                       double *__restrict__ tab, const int *__restrict__ owner) {
-    __shared__ double E1[QNODES];   // cosh(t_k) - 1 = 2 sinh^2(t_k / 2)
-    __shared__ double L2[QNODES];   // log cosh(kappa t_k)
-    __shared__ float2 E1f[F32TAB ? QNODES : 1], L2f[F32TAB ? QNODES : 1];   // the same as double-float
+    // FP64 evaluation: cosh(t_k) - 1 = 2 sinh^2(t_k / 2) and log cosh(kappa t_k);
+    // double-float evaluation (F32TAB): cosh(t_k) - 1 as double-float
+    __shared__ double E1[F32TAB ? 1 : QNODES];
+    __shared__ double L2[F32TAB ? 1 : QNODES];
+    __shared__ float2 E1f[F32TAB ? QNODES : 1];
+    __shared__ int TMi[TAB_NC][TAB_NC];
     __shared__ double F[32][TAB_NC];
     __shared__ double A[32][TAB_NC];          // Chebyshev coefficients per bucket
     __shared__ double CT[TAB_NC][TAB_NC];     // cos(pi k (m + 1/2) / NC)
@@ -470,15 +562,19 @@ __global__ void __launch_bounds__(320) k_matern_table(const double *__restrict__
     }
     const double PI = 3.14159265358979323846;
     for (int k = threadIdx.x; k < QNODES; k += blockDim.x) {
-        const double t = k * QH;
-        const double sh = sinh(0.5 * t);
-        E1[k] = 2.0 * sh * sh;
-        const double kt = kap * t;
-        L2[k] = kt + log1p(exp(-2.0 * kt)) - 0.69314718055994530942;
         if constexpr (F32TAB) {
-            const float eh = __double2float_rn(E1[k]), lh = __double2float_rn(L2[k]);
-            E1f[k] = make_float2(eh, __double2float_rn(E1[k] - (double)eh));
-            L2f[k] = make_float2(lh, __double2float_rn(L2[k] - (double)lh));
+            // one FP64 sinh per node (kappa-independent; ~2^-48 once split,
+            // where df_e1 gives ~2^-44 and this term multiplies u)
+            const double sh = sinh(0.5 * k * QH);
+            const double e1 = 2.0 * sh * sh;
+            const float eh = __double2float_rn(e1);
+            E1f[k] = make_float2(eh, __double2float_rn(e1 - (double)eh));
+        } else {
+            const double t = k * QH;
+            const double sh = sinh(0.5 * t);
+            E1[k] = 2.0 * sh * sh;
+            const double kt = kap * t;
+            L2[k] = kt + log1p(exp(-2.0 * kt)) - 0.69314718055994530942;
         }
     }
     if (threadIdx.x < TAB_NC * TAB_NC) {
@@ -488,9 +584,14 @@ __global__ void __launch_bounds__(320) k_matern_table(const double *__restrict__
     if (threadIdx.x == 0) {   // T_0 = 1, T_1 = t, T_k = 2 t T_{k-1} - T_{k-2} (small integers)
         for (int k = 0; k < TAB_NC; ++k)
             for (int m = 0; m < TAB_NC; ++m)
-                TM[k][m] = k == 0 ? (m == 0 ? 1.0 : 0.0)
-                         : k == 1 ? (m == 1 ? 1.0 : 0.0)
-                                  : (m > 0 ? 2.0 * TM[k - 1][m - 1] : 0.0) - TM[k - 2][m];
+                TMi[k][m] = k == 0 ? (m == 0 ? 1 : 0)
+                          : k == 1 ? (m == 1 ? 1 : 0)
+                                   : (m > 0 ? 2 * TMi[k - 1][m - 1] : 0) - TMi[k - 2][m];
+    }
+    __syncthreads();
+    if (threadIdx.x < TAB_NC * TAB_NC) {
+        const int k = threadIdx.x / TAB_NC, m = threadIdx.x % TAB_NC;
+        TM[k][m] = (double)TMi[k][m];
     }
     __syncthreads();
     const int lb = threadIdx.x / TAB_NC, l = threadIdx.x % TAB_NC;
@@ -505,8 +606,8 @@ __global__ void __launch_bounds__(320) k_matern_table(const double *__restrict__
         double r;
         if (kap != kap || !(kap > 0.0)) {
             r = nan("");
-        } else if (F32TAB && u <= TAB_USPLIT) {
-            r = rho_nodes_df(u, kap, logc, E1f, L2f);
+        } else if (F32TAB) {
+            r = rho_df(u, kap, logc, E1f);
         } else if (u <= TAB_USPLIT) {
             // the terms of four nodes are computed ahead (independent exps),
             // then added in order with the same stopping rule
