@@ -28,6 +28,7 @@ import math
 import os
 import statistics
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -111,7 +112,10 @@ class ClockSampler:
     def __init__(self, index):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank_gpu{index}.csv")
+        # the raw samples go to PLK_CLOCKS_DIR (default: the system temp folder);
+        # the JSON line carries their summary
+        d = os.environ.get("PLK_CLOCKS_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(d, f"clocks_rank_gpu{index}.csv")
 
     def start(self):
         try:
