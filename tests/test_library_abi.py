@@ -64,3 +64,15 @@ def test_post_processing_rejects_bad_arguments_without_touching_the_gpu(L):
     assert L.plk_internal_params_device(None, 3, 0, None, None) == nv.PLK_E_INVALID
     # nothing to do is not an error and launches nothing
     assert L.plk_internal_params_device(None, 0, 0, None, None) == nv.PLK_OK
+
+
+def test_binding_constants_match_header():
+    """Every PLK_FLAG_* and PLK_POINT_* value of include/plk.h has the same
+    value in the Python binding (the binding restates them by hand)."""
+    import os
+    import re
+    hdr = open(os.path.join(os.path.dirname(nv.__file__), os.pardir, "include", "plk.h")).read()
+    defs = dict(re.findall(r"^#define PLK_((?:FLAG|POINT)_\w+)\s+(\d+)", hdr, re.M))
+    assert len(defs) >= 10
+    for name, value in defs.items():
+        assert getattr(nv, name) == int(value), name
