@@ -328,10 +328,11 @@ constexpr float IF3H = (float)(1.0 / 6.0), IF3L = (float)(1.0 / 6.0 - (double)IF
 constexpr float IF4H = (float)(1.0 / 24.0), IF4L = (float)(1.0 / 24.0 - (double)IF4H);
 
 // exp(x) for the double-float x = xh + xl, |x| <= 86 (0 below -86): relative
-// error ~2^-45 for x >= -50 (below, the low part of the result leaves the FP32
-// normal range; such terms are far below the sums they enter).  x = k ln2 + r with k = rint(x / ln2), |r| <= ln2 / 2 formed
-// from the three-part ln 2 (k ln2_hi exact, k ln2_mid split exactly);
-// exp(r) = p(r / 4)^4 with p the Taylor polynomial of degree 9 (remainder
+// error ~2^-45 for x >= -50 (below, the low part of the result leaves the
+// FP32 normal range; such terms are far below the sums they enter).
+// x = k ln2 + r with k = rint(x / ln2), |r| <= ln2 / 2 formed from the
+// three-part ln 2 (k ln2_hi exact, k ln2_mid split exactly); exp(r) =
+// p(r / 4)^4 with p the Taylor polynomial of degree 9 (remainder
 // (ln2 / 8)^10 / 10! < 2^-56): terms 5..9 by Horner in FP32 (each below 2^-22,
 // so their rounding stays below 2^-46), terms 0..4 in double-float; two
 // double-float squarings; then 2^k.
@@ -407,7 +408,7 @@ constexpr float IF5H = (float)(1.0 / 120.0), IF5L = (float)(1.0 / 120.0 - (doubl
 constexpr float IF7H = (float)(1.0 / 5040.0), IF7L = (float)(1.0 / 5040.0 - (double)IF7H);
 
 // 2 sinh^2(x) = cosh(2x) - 1 for an FP32 x >= 0 (x <= 43) as double-float,
-// relative error ~2^-45.  x < 1/2: sinh x = x sum_n y^n / (2n+1)!, y = x^2
+// relative error ~2^-44.  x < 1/2: sinh x = x sum_n y^n / (2n+1)!, y = x^2
 // (terms n >= 4 in FP32, each below 2^-26 relative; remainder y^8 / 17! <
 // 2^-64); else (e^x - e^-x) / 2 with the double-float exp and reciprocal
 // (no cancellation: e^-x <= 0.61 e^x).
