@@ -52,6 +52,12 @@ sys.path.insert(0, ROOT)
 
 METRIC = "profile-logL evals/s at n=4000 (FP64 vs mixed, |ΔlogL|≤1e-3); p50/p99 latency"
 UNIT = "evals/s"
+# arithmetic the path computes in: FP64 mode is FP64 throughout; mixed mode
+# splits the trailing updates and panel solves into exact bf16 slice products
+# on the tensor cores (FP32 accumulation), keeps the trailing matrix, the
+# first-pass build and the diagonal tiles in double-float FP32 (two floats per
+# value), and the log-determinant and closed form in FP64
+DTYPE = {"fp64": "f64", "mixed": "bf16 split products (5/7 slices) + f32 pairs + f64"}
 WORKLOAD = ("mixed4000: n=4000 sites on [0,20]^2, p=3, M=9 lambdas in [-0.5,1.5], "
             "K=1024 omega (960 Halton + 64 ill-conditioned), anisotropic Matern")
 
@@ -198,12 +204,50 @@ def cpu_cores():
 # reference arm: the FP64 CPU oracle
 # ---------------------------------------------------------------------------
 
-def oracle_rate(ds, P, lambdas, npts, threads):
+def oracle_rate(ds, P, lambdas, npts, threads, full=False):
     import oracle
     t0 = time.perf_counter()
     r = oracle.profile_batch(ds.coords, ds.y, ds.X, P[:npts], lambdas, nthreads=threads)
     dt = time.perf_counter() - t0
-    return npts / dt, dt, r["threads"]
+    return (npts / dt, dt, r["threads"], r) if full else (npts / dt, dt, r["threads"])
+
+
+def oracle_sample_indices(K, npts, n_ill=64):
+    """Points of the n=4000 grid in the CPU-baseline sample: the first Halton
+    points and, for a quarter of the sample, ill-conditioned points of the
+    grid's last 64 (kappa = 8, phi_X = 40, all four nuggets, both ratios), so
+    that the per-result errors cover them."""
+    k_ill = min(npts // 4, n_ill)
+    ill_pick = [56, 58, 61, 63, 48, 50, 53, 55, 40, 42, 45, 47, 32, 34, 37, 39][:k_ill]
+    return np.array(list(range(npts - k_ill)) + [K - n_ill + i for i in ill_pick])
+
+
+def per_result_errors(g, o, lam, prefix=""):
+    """Largest errors of GPU results g against the oracle's o on the same points:
+    |Delta l_p| (abs), sigma^2 (rel), beta (abs, relative to the largest |beta|),
+    log|V| and log|X'V^-1X| (abs), the status agreement, and the 95 % likelihood
+    CI of lambda from the profile over these points (endpoint error relative to
+    the oracle CI's width)."""
+    import oracle
+    st = g["status"] & 15
+    ok = (st == 0) & (o["status"] == 0)
+    r = {"points": int(len(st)), "compared": int(ok.sum()), "status_agree": int((st == o["status"]).sum())}
+    if ok.any():
+        d = np.abs(g["logL"][ok] - o["logL"][ok])
+        r["max_abs_dlogL"] = float(d.max())
+        r["max_rel_dlogL"] = float((d / np.abs(o["logL"][ok])).max())
+        r["max_rel_dsigma2"] = float(np.abs(g["sigma2"][ok] / o["sigma2"][ok] - 1).max())
+        r["max_dbeta_rel_to_max_beta"] = float(np.abs(g["beta"][ok] - o["beta"][ok]).max() / np.abs(o["beta"][ok]).max())
+        r["max_abs_dlogdet"] = float(np.abs(g["logdet"][ok] - o["logdet"][ok]).max())
+        from paper_2305_04318_b300 import native as nv
+        gp = np.nanmax(np.where(ok[:, None], g["logL"], np.nan), axis=0)
+        op = oracle.profile_max(np.where(ok[:, None], o["logL"], np.nan).T)
+        gci, oci = nv.profile_ci(lam, gp, 0.95), oracle.profile_ci(lam, op, 0.95)
+        width = oci["hi"] - oci["lo"]
+        if width > 0:
+            r["lambda_ci95_oracle"] = [oci["lo"], oci["hi"]]
+            r["max_ci_endpoint_err_rel_to_width"] = float(max(abs(gci["lo"] - oci["lo"]), abs(gci["hi"] - oci["hi"])) / width)
+    return r
 
 
 def run_reference(args):
@@ -689,7 +733,6 @@ def main():
         for s in range(warmup):
             one(s)
         barrier()
-        nv.kernel_timing(reset=True)
         clocks = ClockSampler(local) if sample_clocks else None
         if clocks:
             clocks.start()
@@ -698,16 +741,28 @@ def main():
         barrier()
         e0.record(stream)
         for s in range(warmup, warmup + steps):
-            one(s, flags=nv.FLAG_KERNEL_TIMING)
+            one(s)
         e1.record(stream)
         barrier()
         clk = clocks.stop() if clocks else None
         ms_total = max_over_ranks(e0.elapsed_time(e1))
-        timing = nv.kernel_timing(reset=True)
         status = np.concatenate([outs[s]["status"].cpu().numpy() for s in range(warmup, warmup + steps)])
+        first = {k: v.cpu().numpy() for k, v in outs[warmup].items()}
+        # per-kernel-class times: the same steps once more, outside the timed
+        # region, with CUDA events around every launch on its stream
+        nv.kernel_timing(reset=True)
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for s in range(warmup, warmup + steps):
+            one(s, flags=nv.FLAG_KERNEL_TIMING)
+        f1.record(stream)
+        barrier()
+        timing = nv.kernel_timing(reset=True)
         res = dict(value=world * B * steps / (ms_total * 1e-3), ms_per_step=ms_total / steps, timing=timing,
+                   instrumented_ms_per_step=f0.elapsed_time(f1) / steps,
                    clocks=clk, status=status, wsb=wsb, B=B, steps=steps, warmup=warmup,
-                   first=({k: v.cpu().numpy() for k, v in outs[warmup].items()}), first_params=batches[warmup])
+                   first=first, first_params=batches[warmup])
         del workspace
         torch.cuda.empty_cache()
         return res
@@ -818,12 +873,25 @@ def main():
 
     # ---- CPU baseline (oracle on the host cores), rank 0 at N = 1 only ----
     cpu = None
+    vs_oracle = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cores = cpu_cores()
         npts = args.cpu_sample or cores
-        r, dt, used = oracle_rate(ds, P, lam, npts, cores)
+        sidx = oracle_sample_indices(K, npts)
+        r, dt, used, o = oracle_rate(ds, P[sidx], lam, npts, cores, full=True)
         cpu = {"value": r, "unit": UNIT, "cores": used, "kind": "oracle",
-               "sample": f"first {npts} omega points of the n=4000 workload ({dt:.1f} s wall, one point per thread)"}
+               "sample": f"{npts} omega points of the n=4000 workload: the first {int((sidx < K - 64).sum())} "
+                         f"Halton points and {int((sidx >= K - 64).sum())} ill-conditioned ones (kappa=8, phi_X>=23; "
+                         f"the oracle stops early on the points it finds not positive definite) "
+                         f"({dt:.1f} s wall, one point per thread)"}
+        # per-result errors of both GPU paths against the oracle on these points
+        Ps = T(P[sidx])
+        vs_oracle = {"points": [int(i) for i in sidx],
+                     "what": "largest errors of each GPU path against the FP64 CPU oracle on the CPU-baseline sample"}
+        for name, prec in (("mixed", nv.MIXED), ("fp64", nv.FP64)):
+            g = nv.eval_device(coords, y, X, lamd, Ps, precision=prec, batch=len(sidx))
+            torch.cuda.synchronize()
+            vs_oracle[name] = per_result_errors({k: v.cpu().numpy() for k, v in g.items()}, o, lam)
 
     if rank == 0:
         fp64_line = None
@@ -836,14 +904,18 @@ def main():
                          "trailing_gemm_tflops": ach, "trailing_gemm_frac_of_fp64_peak": (ach / fp64_peak) if ach else None}
         line = {"metric": METRIC, "value": main_res["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": main_res["ms_per_step"], "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[head], "data": "synthetic",
                 "config": {"workload": WORKLOAD, "precision": head, "batch_per_step": Bm, "n": n, "p": p, "M": M,
                            "l2": f"inputs larger than L2: {main_res['wsb'] / 1e9:.1f} GB workspace per step",
                            "parallelism": f"omega-sharded x{world}"},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "latency_ms": lat,
                 "gpu_launches": launches, "kernel_ms": {k: round(v[0], 3) for k, v in timing.items() if v[1]},
                 "kernel_share": kernel_share, "clocks": main_res["clocks"],
-                "fp64_path": fp64_line, "mixed_vs_fp64": agree,
+                "fp64_path": fp64_line, "mixed_vs_fp64": agree, "vs_oracle": vs_oracle,
+                "instrumented_ms_per_step": main_res["instrumented_ms_per_step"],
+                "kernel_timing_is": "kernel_ms, kernel_share and the roofline's kernel time come from the timed "
+                                    "steps run once more after the timed region with CUDA events around every "
+                                    "launch (instrumented_ms_per_step); value and ms_per_step are uninstrumented",
                 "fp64_fma_peak_tflops": fp64_peak, "fp32_fma_peak_tflops": fp32_peak,
                 "points_not_ok": int(((st & 15) != 0).sum()), "points_evaluated": int(n_pts)}
         print(json.dumps(line), flush=True)

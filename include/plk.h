@@ -411,6 +411,18 @@ plk_status plk_quadratic_cloud_cb(plk_eval_fn fn, void *user, const double *omeg
  * range, PLK_E_CUDA for a CUDA error. */
 plk_status plk_selftest_bounded_wait(int32_t max_iter, void *stream);
 
+/* Self-test of the double-float exponential that the mixed path's first pass
+ * uses in its Matern table (the paper has no counterpart: it evaluates in FP64
+ * throughout).  For i < count: yh[i] + yl[i] = exp(xh[i] + xl[i]), computed
+ * the way the table does it (k ln 2 + r with a three-part ln 2, a degree-9
+ * Taylor polynomial of e^(r/4), two double-float squarings, then 2^k).  Its
+ * relative error is ~2^-45 for arguments >= -50; below -86 the result is 0,
+ * above 86 infinity.  All four arrays are device memory of `count` floats
+ * (count <= 2^31), caller-owned; asynchronous on `stream`.  PLK_E_INVALID for
+ * a bad count or a NULL pointer, PLK_E_CUDA for a launch error. */
+plk_status plk_selftest_df_exp(const float *xh, const float *xl, float *yh, float *yl, int64_t count,
+                               void *stream);
+
 /* Message describing the last error of the calling thread ("" if none). */
 const char *plk_last_error(void);
 

@@ -1300,3 +1300,12 @@ extern "C" plk_status plk_selftest_bounded_wait(int32_t max_iter, void *stream) 
     if (h) return fail(PLK_E_TIMEOUT, "a bounded device wait gave up after %d tries (self-test)", max_iter);
     return PLK_OK;
 }
+
+extern "C" plk_status plk_selftest_df_exp(const float *xh, const float *xl, float *yh, float *yl, int64_t count,
+                                         void *stream) {
+    if (count < 0 || count > ((int64_t)1 << 31)) return fail(PLK_E_INVALID, "count must be in [0, 2^31]");
+    if (count > 0 && (!xh || !xl || !yh || !yl)) return fail(PLK_E_INVALID, "NULL pointer");
+    const cudaError_t e = launch_df_exp_selftest(count, xh, xl, yh, yl, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "double-float exp self-test");
+    return PLK_OK;
+}

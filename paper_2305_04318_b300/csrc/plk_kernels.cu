@@ -1336,4 +1336,25 @@ cudaError_t launch_profile_ci(const double *grid, const double *prof, int64_t G,
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// self-test of the double-float exp (one thread per argument)
+// ---------------------------------------------------------------------------
+__global__ void k_df_exp_selftest(int64_t count, const float *__restrict__ xh, const float *__restrict__ xl,
+                                  float *__restrict__ yh, float *__restrict__ yl) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    float h, l;
+    df_exp(xh[i], xl[i], h, l);
+    yh[i] = h;
+    yl[i] = l;
+}
+
+cudaError_t launch_df_exp_selftest(int64_t count, const float *xh, const float *xl, float *yh, float *yl,
+                                   cudaStream_t s) {
+    if (count <= 0) return cudaSuccess;
+    const int64_t blocks = (count + 255) / 256;
+    k_df_exp_selftest<<<(unsigned)blocks, 256, 0, s>>>(count, xh, xl, yh, yl);
+    return cudaGetLastError();
+}
+
 }  // namespace plk

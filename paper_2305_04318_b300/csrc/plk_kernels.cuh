@@ -83,6 +83,9 @@ cudaError_t launch_mixed_back(const BatchArgs &b, const MixedArgs &x, int S, cud
 cudaError_t launch_gather_params(int count, const int *idx, const double *params, double *out, cudaStream_t s);
 // one block whose bounded wait on a barrier that nothing completes gives up and sets *err
 cudaError_t launch_wait_selftest(uint32_t max_iter, int *err, cudaStream_t s);
+// yh + yl = exp(xh + xl) by the double-float exp of the first-pass rho table
+cudaError_t launch_df_exp_selftest(int64_t count, const float *xh, const float *xl, float *yh, float *yl,
+                                   cudaStream_t s);
 cudaError_t launch_scatter_value(int count, const int *idx, double v, double *out, cudaStream_t s);
 
 cudaError_t launch_profile_max(const double *vals, int64_t G, int64_t SM, double *prof,

@@ -122,6 +122,7 @@ def lib():
                                              C.POINTER(i64), vp, vp, vp]),
         "plk_kernel_class_name": (C.c_char_p, [i32]),
         "plk_selftest_bounded_wait": (C.c_int, [i32, vp]),
+        "plk_selftest_df_exp": (C.c_int, [vp, vp, vp, vp, i64, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -249,6 +250,14 @@ def selftest_bounded_wait(max_iter=1000, stream=None):
     """Run the bounded-wait self-test (plk_selftest_bounded_wait); returns the
     status (PLK_E_TIMEOUT expected) without raising."""
     return int(lib().plk_selftest_bounded_wait(int(max_iter), _stream_handle(stream)))
+
+
+def selftest_df_exp(xh, xl, stream=None):
+    """(yh, yl) = the library's double-float exp of xh + xl (CUDA float32 tensors)."""
+    import torch
+    yh, yl = torch.empty_like(xh), torch.empty_like(xh)
+    _check(lib().plk_selftest_df_exp(_ptr(xh), _ptr(xl), _ptr(yh), _ptr(yl), xh.numel(), _stream_handle(stream)))
+    return yh, yl
 
 
 def eval_device_static(coords, y, X, lambdas, params, reml=False, stream=None, outputs=None):

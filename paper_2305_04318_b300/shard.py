@@ -28,3 +28,70 @@ def balance_by_cost(costs, world):
         owner[i] = r
         load[r] += costs[i]
     return owner
+
+
+RESULT_KEYS = ("logL", "sigma2", "beta", "logdet", "status")
+
+
+def pack_results(r):
+    """Per-point results (logL [B,M], sigma2 [B,M], beta [B,M,p], logdet
+    [B,2], status [B]) as one float64 array [B, F], F = 2M + Mp + 3 (the
+    int32 status is exact in float64)."""
+    B = r["status"].shape[0]
+    cols = [np.asarray(r[k], dtype=np.float64).reshape(B, -1) for k in RESULT_KEYS]
+    return np.ascontiguousarray(np.concatenate(cols, axis=1))
+
+
+def unpack_results(a, M, p):
+    B = a.shape[0]
+    o, out = 0, {}
+    for k, width, shape in (("logL", M, (B, M)), ("sigma2", M, (B, M)), ("beta", M * p, (B, M, p)),
+                            ("logdet", 2, (B, 2)), ("status", 1, (B,))):
+        out[k] = a[:, o:o + width].reshape(shape)
+        o += width
+    out["status"] = out["status"].astype(np.int32)
+    return out
+
+
+def gather_results(idx, results, K, M, p, device="cpu"):
+    """Merge every rank's per-point results into arrays over all K points.
+
+    idx: the global point indices this rank evaluated ([B_r], any B_r >= 0);
+    results: their per-point results (RESULT_KEYS, numpy).  Two collectives
+    on the default process group: an all_gather of the counts, then one
+    all_gather of the packed results padded to the largest count (tensors on
+    `device`: "cuda" under NCCL, "cpu" under gloo).  Every rank returns the
+    merged dict (K rows; points no rank evaluated hold NaN and status -1) and
+    the number of points evaluated by any rank.  A point evaluated by two
+    ranks must have identical results on both (every point's arithmetic
+    depends only on its own data)."""
+    import torch
+    import torch.distributed as dist
+    world = dist.get_world_size()
+    idx = np.asarray(idx, dtype=np.int64)
+    packed = pack_results(results) if len(idx) else np.zeros((0, 2 * M + M * p + 3))
+    F = 2 * M + M * p + 3
+    cnt = torch.tensor([len(idx)], dtype=torch.int64, device=device)
+    counts = [torch.zeros_like(cnt) for _ in range(world)]
+    dist.all_gather(counts, cnt)
+    counts = [int(c.item()) for c in counts]
+    Bmax = max(counts)
+    buf = np.full((Bmax, F + 1), np.nan)
+    buf[:len(idx), 0] = idx
+    buf[:len(idx), 1:] = packed
+    t = torch.as_tensor(buf, device=device)
+    parts = [torch.empty_like(t) for _ in range(world)]
+    dist.all_gather(parts, t)
+    merged = np.full((K, F), np.nan)
+    merged[:, -1] = -1
+    seen = np.zeros(K, dtype=bool)
+    for c, part in zip(counts, parts):
+        a = part.cpu().numpy()[:c]
+        ks = a[:, 0].astype(np.int64)
+        for j, k in enumerate(ks):
+            if seen[k]:
+                if not np.array_equal(merged[k], a[j, 1:], equal_nan=True):
+                    raise RuntimeError(f"point {k}: different results on two ranks")
+            merged[k] = a[j, 1:]
+            seen[k] = True
+    return unpack_results(merged, M, p), int(seen.sum())

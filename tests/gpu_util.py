@@ -41,3 +41,43 @@ def compare(g, o, rtol=RTOL_LOGL, what=""):
     bad = ~ok
     assert np.all(np.isnan(g["logL"][bad & (o["status"] != 3)]))
     return float(err.max()) if err.size else 0.0
+
+
+# Near-singularity, judged on the oracle's matrix.  The 7-slice tier of the
+# mixed path (the last one that can call a point not positive definite) keeps
+# the trailing matrix in double-float: every stored entry of a Schur
+# complement is rounded to ~2^-48 of its size (<= 1 + nu^2) at each of the
+# nb/2 two-panel updates, ~2^-44 (1 + nu^2) accumulated, so its factorisation
+# may fail where V is within n 2^-44 (1 + nu^2) of singular.  Since every
+# Cholesky pivot of an SPD matrix is >= its smallest eigenvalue, a smallest
+# pivot below that level proves V that close to singular; a factorisation that
+# fails in FP64 proves it for FP64 itself.
+def singular_threshold(n, nug, safety=4.0):
+    return safety * n * 2.0 ** -44 * (1.0 + nug)
+
+
+def min_pivot(coords, omega):
+    """Smallest Cholesky pivot L_jj^2 of the oracle's V(omega), or -inf when
+    the FP64 factorisation fails."""
+    import oracle
+    V = oracle.build_v(coords, omega)
+    try:
+        L = np.linalg.cholesky(V)
+    except np.linalg.LinAlgError:
+        return -np.inf
+    return float(np.min(np.diag(L)) ** 2)
+
+
+def check_disagreements(coords, params, idx, max_count):
+    """Every point in idx (mixed and reference statuses differ) must be near
+    singular; at most max_count of them.  Returns [(index, min pivot, threshold)]."""
+    n = coords.shape[0]
+    rows = []
+    for k in idx:
+        piv = min_pivot(coords, params[k])
+        rows.append((int(k), piv, singular_threshold(n, params[k][2])))
+    print("status disagreements (index, oracle min pivot, threshold):", rows)
+    assert len(idx) <= max_count, f"{len(idx)} status disagreements (cap {max_count}): {rows}"
+    bad = [r for r in rows if not r[1] <= r[2]]
+    assert not bad, f"status disagreement on points that are not near singular: {bad}"
+    return rows

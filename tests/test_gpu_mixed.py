@@ -8,19 +8,24 @@ import numpy as np
 import pytest
 
 from paper_2305_04318_b300 import native as nv, synth
-from gpu_util import gpu_eval, oracle_eval
+from gpu_util import check_disagreements, gpu_eval, oracle_eval
 
 pytestmark = pytest.mark.gpu
 ATOL_LOGL = 1e-3
 
 
-def mixed_compare(g, o, what, atol=ATOL_LOGL):
+def mixed_compare(g, o, what, atol=ATOL_LOGL, coords=None, params=None, max_disagree=None):
+    """Mixed results g against the reference o (the oracle, or the FP64 path):
+    |Delta l_p| <= atol on every point both sides factor, and the per-point
+    statuses equal except on points whose V the oracle shows to be near
+    singular (coords/params given; without them no disagreement is allowed).
+    At most max_disagree (default max(2, 2 % of the points)) may disagree."""
     st_g = g["status"] & ~(nv.POINT_RETRIED | nv.POINT_FP64)
     both = (st_g == 0) & (o["status"] == 0)
-    # a point only one side could factor must be a (near-)singular one
     disagree = np.flatnonzero(st_g != o["status"])
     err = np.abs(g["logL"][both] - o["logL"][both])
     stats = dict(what=what, points=int(len(st_g)), compared=int(both.sum()), status_disagree=int(len(disagree)),
+                 disagree_idx=disagree.tolist()[:16],
                  max_abs_logL=float(err.max()) if err.size else 0.0,
                  retried=int(((g["status"] & nv.POINT_RETRIED) != 0).sum()),
                  fp64=int(((g["status"] & nv.POINT_FP64) != 0).sum()))
@@ -32,6 +37,10 @@ def mixed_compare(g, o, what, atol=ATOL_LOGL):
         stats["max_abs_logdet"] = float(np.abs(g["logdet"][both] - o["logdet"][both]).max())
     print(json.dumps(stats))
     assert err.size == 0 or err.max() <= atol, stats
+    if len(disagree):
+        assert coords is not None and params is not None, f"status disagreement without a near-singular check: {stats}"
+        cap = max_disagree if max_disagree is not None else max(2, int(0.02 * len(st_g)))
+        check_disagreements(coords, params, disagree, cap)
     return stats
 
 
@@ -40,8 +49,28 @@ def test_mixed_iso100():
     ds, P = w.datasets[0], w.params[0]
     o = oracle_eval(ds, P, w.lambdas)
     g = gpu_eval(ds, P, w.lambdas, precision=nv.MIXED)
-    s = mixed_compare(g, o, "iso100")
-    assert s["status_disagree"] <= 2
+    mixed_compare(g, o, "iso100", coords=ds.coords, params=P, max_disagree=2)
+    _bound_margin(ds, P, w.lambdas, o, "iso100")
+
+
+# The a-posteriori bound E = eps_5 (1 + nu^2) sum_j 1/d_j that decides the
+# 7-slice retries was calibrated at n = 4000 (bound >= 3.99x the error there).
+# Away from that workload the measured 5-slice error must still stay below
+# half the bound (or below 1e-9, where both are rounding noise).
+BOUND_RATIO = 0.5
+
+
+def _bound_margin(ds, P, lams, o, what, g5=None):
+    if g5 is None:
+        g5 = gpu_eval(ds, P, lams, precision=nv.MIXED, flags=nv.FLAG_NO_RETRY)
+    ok = (g5["status"] == 0) & (o["status"] == 0)
+    err = np.max(np.abs(g5["logL"] - o["logL"]), axis=1)[ok]
+    eb = g5["err_bound"][ok]
+    ratio = err / np.maximum(eb, 1e-300)
+    print(json.dumps(dict(what=f"{what} 5-slice error / bound", points=int(ok.sum()),
+                          max_ratio=float(ratio.max()) if ratio.size else None,
+                          max_err=float(err.max()) if err.size else None)))
+    assert np.all((err <= BOUND_RATIO * eb) | (err <= 1e-9)), (what, float(ratio.max()))
 
 
 def test_mixed_aniso1000_subset():
@@ -49,8 +78,7 @@ def test_mixed_aniso1000_subset():
     ds, P = w.datasets[0], w.params[0]
     o = oracle_eval(ds, P, w.lambdas)
     g = gpu_eval(ds, P, w.lambdas, precision=nv.MIXED, batch=40)
-    s = mixed_compare(g, o, "aniso1000")
-    assert s["status_disagree"] == 0
+    mixed_compare(g, o, "aniso1000", max_disagree=0)
 
 
 @pytest.mark.parametrize("n,p,M", [(3, 2, 1), (129, 5, 9), (300, 2, 3)])
@@ -60,7 +88,7 @@ def test_mixed_ragged(n, p, M):
     lams = np.linspace(-0.5, 1.5, M)
     o = oracle_eval(ds, P, lams)
     g = gpu_eval(ds, P, lams, precision=nv.MIXED, batch=3)
-    mixed_compare(g, o, f"n={n}")
+    mixed_compare(g, o, f"n={n}", coords=ds.coords, params=P)
 
 
 def test_mixed_error_bound_covers_five_slice_error():
@@ -171,9 +199,12 @@ def test_mixed4000_full_size_sampled():
     g = gpu_eval(ds, P, w.lambdas, precision=nv.MIXED, batch=512)
     idx = np.array([0, 1, 333, 959, 960, 990, 1000, 1023])
     o = oracle_eval(ds, P[idx], w.lambdas)
-    mixed_compare({k: v[idx] for k, v in g.items()}, o, "mixed4000 sampled vs oracle")
+    mixed_compare({k: v[idx] for k, v in g.items()}, o, "mixed4000 sampled vs oracle", coords=ds.coords,
+                  params=P[idx])
     f = gpu_eval(ds, P, w.lambdas, precision=nv.FP64)
-    mixed_compare(g, f, "mixed4000 all vs FP64 GPU")
+    # all 1024 points, the 64 ill-conditioned ones included: a status that
+    # differs from the FP64 path's must belong to a near-singular V
+    mixed_compare(g, f, "mixed4000 all vs FP64 GPU", coords=ds.coords, params=P)
     # the 5-slice pass alone: its error bound covers the measured error on every point
     g5 = gpu_eval(ds, P, w.lambdas, precision=nv.MIXED, batch=512, flags=nv.FLAG_NO_RETRY)
     ok = (g5["status"] == 0) & (f["status"] == 0)
@@ -226,4 +257,8 @@ def test_largest_serving_size_sampled():
         ctx.release_dataset(d)
     from gpu_util import compare
     compare(f, o, what="n=8000 fp64")
-    mixed_compare(m, o, "n=8000 mixed")
+    mixed_compare(m, o, "n=8000 mixed", coords=ds.coords, params=P)
+    # the 5-slice pass alone at this size: its error against the oracle stays
+    # within half its bound
+    g5 = gpu_eval(ds, P, lams, precision=nv.MIXED, batch=3, flags=nv.FLAG_NO_RETRY)
+    _bound_margin(ds, P, lams, o, "n=8000", g5=g5)

@@ -76,3 +76,14 @@ def test_binding_constants_match_header():
     assert len(defs) >= 10
     for name, value in defs.items():
         assert getattr(nv, name) == int(value), name
+
+
+def test_static_scratch_size_matches_header():
+    """The binding's size of the allocation-free entry point's scratch array
+    equals PLK_STATIC_SCRATCH_BYTES of include/plk.h."""
+    import os
+    import re
+    hdr = open(os.path.join(os.path.dirname(nv.__file__), os.pardir, "include", "plk.h")).read()
+    m = re.search(r"#define PLK_STATIC_SCRATCH_BYTES \(\(size_t\)(\d+) << (\d+)\)", hdr)
+    assert m, "PLK_STATIC_SCRATCH_BYTES not found"
+    assert nv.STATIC_SCRATCH_BYTES == int(m.group(1)) << int(m.group(2))

@@ -31,23 +31,19 @@ def _rank_main(rank, world, port, B, steps, out):
     w = synth.aniso1000(K=24)
     ds = synth.aniso_dataset(9, 60, 2.5, 3)
     P = w.params[0]
-    mine = {}
+    idx_all, res = [], []
     for s in range(steps):
         idx = shard.step_indices(s, rank, world, B, P.shape[0])
-        r = oracle.profile_batch(ds.coords, ds.y, ds.X, P[idx], w.lambdas, nthreads=1)
-        for j, k in enumerate(idx):
-            mine[int(k)] = r["logL"][j]
-    gathered = [None] * world
-    dist.all_gather_object(gathered, mine)
+        res.append(oracle.profile_batch(ds.coords, ds.y, ds.X, P[idx], w.lambdas, nthreads=1))
+        idx_all.append(idx)
+    mine = {k: np.concatenate([r[k] for r in res]) for k in shard.RESULT_KEYS}
+    # the product's gather (the one bench.py uses under torchrun), here over
+    # gloo with the oracle as the evaluator
+    merged, covered = shard.gather_results(np.concatenate(idx_all), mine, P.shape[0], len(w.lambdas), ds.p)
     t = torch.tensor([float(rank + 1)])
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     if rank == 0:
-        merged = {}
-        for g in gathered:
-            for k, v in g.items():
-                assert k not in merged or np.array_equal(merged[k], v)
-                merged[k] = v
-        out.put((merged, float(t.item())))
+        out.put((merged, covered, float(t.item())))
     dist.destroy_process_group()
 
 
@@ -59,18 +55,71 @@ def test_two_gloo_ranks_match_single_process():
     procs = [ctx.Process(target=_rank_main, args=(r, world, port, B, steps, q)) for r in range(world)]
     for p in procs:
         p.start()
-    merged, tmax = q.get(timeout=300)
+    merged, covered, tmax = q.get(timeout=300)
     for p in procs:
         p.join(timeout=120)
         assert p.exitcode == 0
     assert tmax == float(world)
-    assert len(merged) == world * B * steps == 24
+    assert covered == world * B * steps == 24
     import oracle
     w = synth.aniso1000(K=24)
     ds = synth.aniso_dataset(9, 60, 2.5, 3)
     ref = oracle.profile_batch(ds.coords, ds.y, ds.X, w.params[0], w.lambdas, nthreads=1)
-    for k, v in merged.items():
-        np.testing.assert_array_equal(v, ref["logL"][k])
+    for k in shard.RESULT_KEYS:
+        np.testing.assert_array_equal(merged[k], ref[k], err_msg=k)
+
+
+def _uneven_rank_main(rank, world, port, out):
+    """Uneven shards (rank 1 evaluates nothing at all) and a point evaluated
+    by both ranks."""
+    import torch.distributed as dist
+
+    import oracle
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    w = synth.aniso1000(K=6)
+    ds = synth.aniso_dataset(10, 40, 2.0, 2)
+    P, lam = w.params[0], w.lambdas[:3]
+    idx = {0: np.array([0, 2, 5]), 1: np.array([], dtype=np.int64), 2: np.array([5, 1])}[rank]
+    r = oracle.profile_batch(ds.coords, ds.y, ds.X, P[idx], lam, nthreads=1) if len(idx) else None
+    merged, covered = shard.gather_results(idx, r, P.shape[0], len(lam), ds.p)
+    if rank == 0:
+        out.put((merged, covered))
+    dist.destroy_process_group()
+
+
+def test_gather_uneven_and_empty_shards():
+    world = 3
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_uneven_rank_main, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    merged, covered = q.get(timeout=300)
+    for p in procs:
+        p.join(timeout=120)
+        assert p.exitcode == 0
+    assert covered == 4
+    import oracle
+    w = synth.aniso1000(K=6)
+    ds = synth.aniso_dataset(10, 40, 2.0, 2)
+    ref = oracle.profile_batch(ds.coords, ds.y, ds.X, w.params[0], w.lambdas[:3], nthreads=1)
+    for k in (0, 1, 2, 5):
+        for key in shard.RESULT_KEYS:
+            np.testing.assert_array_equal(merged[key][k], ref[key][k])
+    assert merged["status"][3] == -1 and np.isnan(merged["logL"][3]).all()
+
+
+def test_pack_unpack_round_trip():
+    rng = np.random.default_rng(1)
+    B, M, p = 5, 4, 3
+    r = dict(logL=rng.normal(size=(B, M)), sigma2=rng.normal(size=(B, M)), beta=rng.normal(size=(B, M, p)),
+             logdet=rng.normal(size=(B, 2)), status=np.array([0, 1, 2, 3, 16 | 1], dtype=np.int32))
+    u = shard.unpack_results(shard.pack_results(r), M, p)
+    for k in shard.RESULT_KEYS:
+        np.testing.assert_array_equal(u[k], r[k])
 
 
 def test_shards_disjoint_within_a_step_and_cover_the_grid():

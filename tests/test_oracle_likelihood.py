@@ -190,3 +190,25 @@ def test_batch_equals_points():
         o = oracle.profile_point(ds.coords, ds.y, ds.X, P[k], w.lambdas)
         assert b["status"][k] == o["status"]
         np.testing.assert_array_equal(b["logL"][k], o["logL"])
+
+
+def test_near_singular_criterion_of_the_mixed_parity_tests():
+    """The criterion the mixed-precision parity tests use to accept a status
+    disagreement: a V with a duplicated site and no nugget is singular (FP64
+    Cholesky fails or leaves a pivot at rounding level), the same V with
+    nu^2 = 0.1 is far from singular, and a smooth long-range V (kappa = 8) with
+    no nugget is near singular while a small nugget moves it away."""
+    from gpu_util import min_pivot, singular_threshold
+    rng = np.random.default_rng(3)
+    c = rng.uniform(0, 1, size=(40, 2))
+    c[7] = c[3]
+    w0 = np.array([0.3, 1.0, 0.0, 1.0, 0.0])
+    assert min_pivot(c, w0) <= singular_threshold(40, 0.0)
+    w1 = w0.copy()
+    w1[2] = 0.1
+    assert min_pivot(c, w1) > 1e3 * singular_threshold(40, 0.1)
+    c2 = rng.uniform(0, 4, size=(200, 2))
+    smooth = np.array([40.0, 8.0, 0.0, 1.0, 0.0])
+    assert min_pivot(c2, smooth) <= singular_threshold(200, 0.0)
+    smooth[2] = 1e-2
+    assert min_pivot(c2, smooth) > 1e3 * singular_threshold(200, 1e-2)
