@@ -748,6 +748,18 @@ def main():
         ms_total = max_over_ranks(e0.elapsed_time(e1))
         status = np.concatenate([outs[s]["status"].cpu().numpy() for s in range(warmup, warmup + steps)])
         first = {k: v.cpu().numpy() for k, v in outs[warmup].items()}
+        gather = None
+        if world > 1 and sample_clocks:
+            # the ranks' per-point results of the timed steps to every rank in
+            # one all_gather (after the timed region)
+            g0 = time.perf_counter()
+            idx = np.concatenate([shard.step_indices(s, rank, world, B, K) for s in range(warmup, warmup + steps)])
+            mine = {k: np.concatenate([outs[s][k].cpu().numpy() for s in range(warmup, warmup + steps)])
+                    for k in shard.RESULT_KEYS}
+            merged, covered, mism = shard.gather_results(idx, mine, K, M, p, device=dev, strict=False)
+            gather = {"points_covered": covered, "of": K, "ms": 1e3 * (time.perf_counter() - g0),
+                      "repeated_points_with_different_results": mism,
+                      "what": "shard.gather_results of the timed steps' per-point results (one all_gather)"}
         # per-kernel-class times: the same steps once more, outside the timed
         # region, with CUDA events around every launch on its stream
         nv.kernel_timing(reset=True)
@@ -762,7 +774,7 @@ def main():
         res = dict(value=world * B * steps / (ms_total * 1e-3), ms_per_step=ms_total / steps, timing=timing,
                    instrumented_ms_per_step=f0.elapsed_time(f1) / steps,
                    clocks=clk, status=status, wsb=wsb, B=B, steps=steps, warmup=warmup,
-                   first=first, first_params=batches[warmup])
+                   first=first, first_params=batches[warmup], gather=gather)
         del workspace
         torch.cuda.empty_cache()
         return res
@@ -912,6 +924,7 @@ def main():
                 "gpu_launches": launches, "kernel_ms": {k: round(v[0], 3) for k, v in timing.items() if v[1]},
                 "kernel_share": kernel_share, "clocks": main_res["clocks"],
                 "fp64_path": fp64_line, "mixed_vs_fp64": agree, "vs_oracle": vs_oracle,
+                "rank_gather": main_res["gather"],
                 "instrumented_ms_per_step": main_res["instrumented_ms_per_step"],
                 "kernel_timing_is": "kernel_ms, kernel_share and the roofline's kernel time come from the timed "
                                     "steps run once more after the timed region with CUDA events around every "

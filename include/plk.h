@@ -248,6 +248,72 @@ plk_status plk_memory_stats(plk_ctx *ctx, size_t *in_use, size_t *high_water);
 /* Wait for all jobs, free everything the context owns. */
 plk_status plk_destroy(plk_ctx *ctx);
 
+/* Cancel a job (the paper has no counterpart: its back end runs a fixed grid
+ * to the end).  Batches of the job not yet launched are dropped; batches
+ * already running on the device finish (kernels are not interrupted) and
+ * their results are discarded.  Once nothing of the job is running, plk_poll
+ * returns PLK_E_CANCELLED for it and forgets it.  Cancelling a job that has
+ * already completed has no effect: plk_poll still returns its results.
+ * PLK_E_INVALID for an unknown job. */
+plk_status plk_cancel(plk_ctx *ctx, plk_job job);
+
+/* Per-job metrics as JSON lines (no counterpart in the paper).  From this call
+ * on, every job that ends (completed, failed or cancelled) appends one line to
+ * the file at `path` (opened for appending; NULL stops logging): job and
+ * dataset ids, n, p, M, K, precision, reml, points per batch, number of
+ * batches ("items"), outcome, host times t_submit / t_start / t_done (seconds
+ * since context creation), queue wait (t_start - t_submit), run time, the
+ * summed and the p50 / p99 wall time of its batches, evaluations per second,
+ * the counts of points not ok / re-evaluated with 7 slices / in FP64, and the
+ * arena's bytes in use and high-water mark.  PLK_E_INVALID if the file cannot
+ * be opened. */
+plk_status plk_set_metrics_log(plk_ctx *ctx, const char *path);
+
+/* Host-side fault hooks, for tests of failure handling without a GPU fault
+ * (no counterpart in the paper).  The next `count` events of the given kind
+ * fail (count 0 clears the hook):
+ *   PLK_FAULT_ARENA_ALLOC      a batch's workspace allocation in the arena
+ *                              fails as if the arena were full: the scheduler
+ *                              halves the batch, then waits and retries, so
+ *                              the job completes with the same results;
+ *   PLK_FAULT_BATCH            a batch fails before it is launched, as a failed
+ *                              launch would: its job stops launching and
+ *                              plk_poll returns PLK_E_CUDA with the message
+ *                              "injected batch failure (fault hook)"; other
+ *                              jobs are unaffected;
+ *   PLK_FAULT_DROP_COMPLETION  the wake-up of threads waiting in plk_poll for
+ *                              a finished job is not sent: plk_poll still sees
+ *                              the job done within 50 ms (it re-checks).
+ * Nothing here touches the GPU.  PLK_E_INVALID for an unknown kind or a
+ * negative count. */
+#define PLK_FAULT_ARENA_ALLOC 1
+#define PLK_FAULT_BATCH 2
+#define PLK_FAULT_DROP_COMPLETION 3
+plk_status plk_inject_fault(plk_ctx *ctx, int32_t kind, int32_t count);
+
+/* Evaluator of a batch of points on the host: for the `count` parameter rows
+ * `params` (count x 5) of the dataset (coords n x 2, y n, X n x p; host
+ * memory) and the M lambdas, write logL, sigma2 (count x M), beta
+ * (count x M x p), logdet (count x 2) and status (count), layouts as in
+ * plk_eval_args.  Returns 0 on success; anything else fails the batch. */
+typedef int (*plk_host_eval_fn)(void *user, int64_t n, int32_t p, const double *coords, const double *y,
+                                const double *X, const double *params, int64_t count, const double *lambdas,
+                                int32_t M, double *logL, double *sigma2, double *beta, double *logdet,
+                                int32_t *status);
+
+/* A context whose scheduler runs every batch on the host through `fn` (with
+ * `user`) on n_workers worker threads (1 .. 64), with an arena of arena_bytes
+ * of host memory, instead of launching the library's kernels on a GPU (no
+ * counterpart in the paper).  It exists to test the scheduler itself --
+ * admission, continuous batching, cancellation, the fault hooks and the
+ * metrics log -- on machines without a GPU, with any evaluator (the library's
+ * tests pass a CPU reference implementation).  It is never chosen
+ * implicitly: the GPU calls never fall back to it.  Every context call works
+ * on it except plk_autotune (PLK_E_INVALID).  Errors: PLK_E_INVALID,
+ * PLK_E_NOMEM (host arena). */
+plk_status plk_create_with_evaluator(plk_ctx **out, size_t arena_bytes, int n_workers, plk_host_eval_fn fn,
+                                     void *user);
+
 /* Autotuner of the batch schedule (the paper fixes its batch, NparamPerIter,
  * by hand for its unnamed GPU; Section 4).  Times this context's scheduler on a
  * synthetic dataset of n sites with p covariates and M lambdas: for each

@@ -17,6 +17,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <deque>
 #include <map>
@@ -731,11 +732,12 @@ struct Job {
     int batch = 1;
     int64_t next_k = 0;      // first point not yet launched
     int inflight = 0;
-    bool started = false, done = false, failed = false;
+    bool started = false, done = false, failed = false, cancelled = false;
     std::string error;
     std::vector<double> logL, s2, beta, ld;
     std::vector<int32_t> st;
     double t_submit = 0, t_start = 0, t_done = 0;
+    std::vector<double> item_s;   // wall time of every batch, launch to completion
 };
 
 struct Item {
@@ -770,6 +772,14 @@ struct plk_ctx {
     double now() const {
         return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     }
+    // host executor (plk_create_with_evaluator): batches run on the worker
+    // threads through host_fn, all buffers in host memory
+    bool host = false;
+    plk_host_eval_fn host_fn = nullptr;
+    void *host_user = nullptr;
+    // host-side fault hooks (plk_inject_fault): counts of events still to fail
+    int fault_arena = 0, fault_item = 0, fault_drop = 0;
+    FILE *metrics = nullptr;   // per-job JSON lines (plk_set_metrics_log)
 };
 
 namespace {
@@ -816,6 +826,13 @@ bool start_job(plk_ctx *c, Job *j, cudaStream_t s) {
     j->d_bt = (double *)take(sizeof(double) * (size_t)(j->M + j->p) * n_pad);
     j->d_slog = (double *)take(2 * sizeof(double));
     Dataset *d = c->datasets[j->ds].get();
+    if (c->host) {   // the evaluator forms the Box-Cox columns itself
+        std::memcpy(j->d_params, j->params.data(), sizeof(double) * 5 * j->K);
+        std::memcpy(j->d_lam, j->lambdas.data(), sizeof(double) * j->M);
+        j->started = true;
+        j->t_start = c->now();
+        return true;
+    }
     cudaMemcpyAsync(j->d_params, j->params.data(), sizeof(double) * 5 * j->K, cudaMemcpyHostToDevice, s);
     cudaMemcpyAsync(j->d_lam, j->lambdas.data(), sizeof(double) * j->M, cudaMemcpyHostToDevice, s);
     cudaError_t e = launch_boxcox(j->n, n_pad, j->p, j->M, d->y, d->X, d->coords, j->d_lam, j->d_bt, j->d_slog, s);
@@ -832,7 +849,14 @@ bool start_job(plk_ctx *c, Job *j, cudaStream_t s) {
 
 // Runs one batch of a job on stream s and waits for it (called without the
 // context lock).  Returns an error message, empty on success.
-std::string run_item(Job *j, Item &it, cudaStream_t s) {
+std::string run_item(plk_ctx *c, Job *j, Item &it, cudaStream_t s) {
+    if (c->host) {
+        const int64_t k0 = it.k0;
+        const int r = c->host_fn(c->host_user, j->n, j->p, it.ds->coords, it.ds->y, it.ds->X, j->d_params + 5 * k0,
+                                 it.count, j->d_lam, j->M, j->d_logL + k0 * j->M, j->d_s2 + k0 * j->M,
+                                 j->d_beta + k0 * j->M * j->p, j->d_ld + 2 * k0, j->d_st + k0);
+        return r == 0 ? std::string() : std::string("evaluator returned ") + std::to_string(r);
+    }
     Layout L;
     make_layout(j->n, j->p, j->M, it.count, L, j->opts.precision);
     Dataset *d = it.ds;
@@ -879,15 +903,26 @@ std::string run_item(Job *j, Item &it, cudaStream_t s) {
     return err;
 }
 
+void write_metrics(plk_ctx *c, const Job *j);
+
 void finish_job(plk_ctx *c, Job *j) {
     // all items retired: read results back (synchronously on the job's last stream)
-    j->logL.resize(j->K * j->M);
-    j->s2.resize(j->K * j->M);
-    j->beta.resize(j->K * j->M * j->p);
-    j->ld.resize(2 * j->K);
-    j->st.resize(j->K);
+    const bool copy = !j->cancelled && !j->failed && j->dev;
+    if (copy) {
+        j->logL.resize(j->K * j->M);
+        j->s2.resize(j->K * j->M);
+        j->beta.resize(j->K * j->M * j->p);
+        j->ld.resize(2 * j->K);
+        j->st.resize(j->K);
+    }
     cudaError_t e = cudaSuccess;
-    if (j->K > 0) {
+    if (copy && c->host && j->K > 0) {
+        std::memcpy(j->logL.data(), j->d_logL, sizeof(double) * j->K * j->M);
+        std::memcpy(j->s2.data(), j->d_s2, sizeof(double) * j->K * j->M);
+        std::memcpy(j->beta.data(), j->d_beta, sizeof(double) * j->K * j->M * j->p);
+        std::memcpy(j->ld.data(), j->d_ld, sizeof(double) * 2 * j->K);
+        std::memcpy(j->st.data(), j->d_st, sizeof(int32_t) * j->K);
+    } else if (copy && j->K > 0) {
         e = cudaMemcpy(j->logL.data(), j->d_logL, sizeof(double) * j->K * j->M, cudaMemcpyDeviceToHost);
         if (e == cudaSuccess) e = cudaMemcpy(j->s2.data(), j->d_s2, sizeof(double) * j->K * j->M, cudaMemcpyDeviceToHost);
         if (e == cudaSuccess) e = cudaMemcpy(j->beta.data(), j->d_beta, sizeof(double) * j->K * j->M * j->p, cudaMemcpyDeviceToHost);
@@ -905,6 +940,59 @@ void finish_job(plk_ctx *c, Job *j) {
     c->datasets[j->ds]->active_jobs--;
     j->done = true;
     j->t_done = c->now();
+    write_metrics(c, j);
+}
+
+// Wakes the threads waiting in plk_poll, unless a fault hook drops this
+// notification (plk_poll then still sees the job done within its 50 ms
+// re-check interval).  Caller holds mu.
+void notify_done(plk_ctx *c) {
+    if (c->fault_drop > 0) {
+        c->fault_drop--;
+        return;
+    }
+    c->cv_done.notify_all();
+}
+
+// Arena space for a batch's workspace; a fault hook can make the next
+// allocations fail as if the arena were full.  Caller holds mu.
+char *alloc_item(plk_ctx *c, size_t bytes) {
+    if (c->fault_arena > 0) {
+        c->fault_arena--;
+        return nullptr;
+    }
+    return c->arena.alloc(bytes);
+}
+
+// One JSON line per finished job (plk_set_metrics_log).  Caller holds mu.
+void write_metrics(plk_ctx *c, const Job *j) {
+    if (!c->metrics) return;
+    std::vector<double> it = j->item_s;
+    std::sort(it.begin(), it.end());
+    auto pct = [&](double q) { return it.empty() ? 0.0 : it[(size_t)std::min<double>(it.size() - 1, std::floor(q * it.size()))]; };
+    double busy = 0.0;
+    for (double v : it) busy += v;
+    int64_t bad = 0, retried = 0, f64 = 0;
+    for (int32_t v : j->st) {
+        bad += (v & 15) != 0;
+        retried += (v & PLK_POINT_RETRIED) != 0;
+        f64 += (v & PLK_POINT_FP64) != 0;
+    }
+    const double run = j->t_done - j->t_start;
+    const char *outcome = j->cancelled ? "cancelled" : j->failed ? "failed" : "ok";
+    std::fprintf(c->metrics,
+                 "{\"job\": %lld, \"dataset\": %lld, \"n\": %lld, \"p\": %d, \"M\": %d, \"K\": %lld, "
+                 "\"precision\": \"%s\", \"reml\": %d, \"batch\": %d, \"items\": %zu, \"outcome\": \"%s\", "
+                 "\"t_submit\": %.6f, \"t_start\": %.6f, \"t_done\": %.6f, \"queue_wait_s\": %.6f, "
+                 "\"run_s\": %.6f, \"item_busy_s\": %.6f, \"item_ms_p50\": %.3f, \"item_ms_p99\": %.3f, "
+                 "\"evals_per_s\": %.3f, \"points_not_ok\": %lld, \"points_retried\": %lld, "
+                 "\"points_fp64\": %lld, \"arena_in_use\": %zu, \"arena_high_water\": %zu}\n",
+                 (long long)j->id, (long long)j->ds, (long long)j->n, j->p, j->M, (long long)j->K,
+                 j->opts.precision == PLK_MIXED ? "mixed" : "fp64", j->opts.reml, j->batch, it.size(), outcome,
+                 j->t_submit, j->t_start, j->t_done, j->t_start - j->t_submit, run, busy, 1e3 * pct(0.5),
+                 1e3 * pct(0.99), (run > 0.0 && !j->cancelled && !j->failed) ? (double)j->K / run : 0.0,
+                 (long long)bad, (long long)retried, (long long)f64, c->arena.used(), c->arena.high());
+    std::fflush(c->metrics);
 }
 
 // One worker per stream: take the next batch of the oldest job that has work
@@ -913,8 +1001,8 @@ void finish_job(plk_ctx *c, Job *j) {
 // as soon as a worker and arena space free up, so batches of different jobs
 // overlap on the device.
 void stream_worker(plk_ctx *c, int slot) {
-    cudaSetDevice(c->device);
-    cudaStream_t s = c->streams[slot];
+    if (!c->host) cudaSetDevice(c->device);
+    cudaStream_t s = c->host ? nullptr : c->streams[slot];
     std::unique_lock<std::mutex> lk(c->mu);
     while (true) {
         Job *pick = nullptr;
@@ -937,13 +1025,15 @@ void stream_worker(plk_ctx *c, int slot) {
             if (pick->K == 0) {
                 finish_job(c, pick);
                 c->order.erase(std::find(c->order.begin(), c->order.end(), pick));
-                c->cv_done.notify_all();
+                notify_done(c);
                 continue;
             }
         }
         int count = (int)std::min<int64_t>(pick->batch, pick->K - pick->next_k);
         char *ws = nullptr;
-        while (count >= 1 && !(ws = c->arena.alloc(item_bytes(pick->n, pick->p, pick->M, count, pick->opts.precision))))
+        while (count >= 1 &&
+               !(ws = alloc_item(c, c->host ? (size_t)ALIGN * count
+                                            : item_bytes(pick->n, pick->p, pick->M, count, pick->opts.precision))))
             count /= 2;
         if (!ws) {
             c->cv_work.wait_for(lk, std::chrono::milliseconds(2));
@@ -952,19 +1042,29 @@ void stream_worker(plk_ctx *c, int slot) {
         Item it{pick, c->datasets[pick->ds].get(), pick->next_k, count, ws};
         pick->next_k += count;
         pick->inflight++;
-        lk.unlock();
-        const std::string err = run_item(pick, it, s);
-        lk.lock();
+        std::string err;
+        if (c->fault_item > 0) {   // fault hook: this batch fails as a launch would
+            c->fault_item--;
+            err = "injected batch failure (fault hook)";
+        } else {
+            lk.unlock();
+            const auto t0 = std::chrono::steady_clock::now();
+            err = run_item(c, pick, it, s);
+            const double dt = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+            lk.lock();
+            pick->item_s.push_back(dt);
+        }
         if (!err.empty()) {
             pick->failed = true;
             pick->error = err;
+            pick->next_k = pick->K;   // launch nothing more of a failed job
         }
         c->arena.release(ws);
         pick->inflight--;
         if (pick->inflight == 0 && pick->next_k >= pick->K && !pick->done) {
             finish_job(c, pick);
             c->order.erase(std::find(c->order.begin(), c->order.end(), pick));
-            c->cv_done.notify_all();
+            notify_done(c);
         }
         c->cv_work.notify_all();
     }
@@ -1042,7 +1142,7 @@ extern "C" plk_status plk_create_dataset(plk_ctx *c, const double *coords, const
         return fail(PLK_E_INVALID, "non-finite input");
     for (int64_t i = 0; i < n; ++i)
         if (!(y[i] > 0.0)) return fail(PLK_E_INVALID, "y[%lld] = %g is not > 0", (long long)i, y[i]);
-    cudaSetDevice(c->device);
+    if (!c->host) cudaSetDevice(c->device);
     std::lock_guard<std::mutex> lk(c->mu);
     auto d = std::make_unique<Dataset>();
     d->n = n;
@@ -1054,9 +1154,15 @@ extern "C" plk_status plk_create_dataset(plk_ctx *c, const double *coords, const
     d->coords = (double *)m;
     d->y = (double *)(m + bc);
     d->X = (double *)(m + bc + by);
-    cudaError_t e = cudaMemcpy(d->coords, coords, sizeof(double) * 2 * n, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(d->y, y, sizeof(double) * n, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(d->X, X, sizeof(double) * n * p, cudaMemcpyHostToDevice);
+    cudaError_t e = cudaSuccess;
+    if (c->host) {
+        std::memcpy(d->coords, coords, sizeof(double) * 2 * n);
+        std::memcpy(d->y, y, sizeof(double) * n);
+        std::memcpy(d->X, X, sizeof(double) * n * p);
+    }
+    if (!c->host) e = cudaMemcpy(d->coords, coords, sizeof(double) * 2 * n, cudaMemcpyHostToDevice);
+    if (!c->host && e == cudaSuccess) e = cudaMemcpy(d->y, y, sizeof(double) * n, cudaMemcpyHostToDevice);
+    if (!c->host && e == cudaSuccess) e = cudaMemcpy(d->X, X, sizeof(double) * n * p, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         c->arena.release(m);
         return cuda_fail(e, "dataset upload");
@@ -1080,7 +1186,7 @@ extern "C" plk_status plk_submit_profile(plk_ctx *c, plk_dataset ds, const doubl
     if (dit == c->datasets.end()) return fail(PLK_E_INVALID, "unknown dataset %lld", (long long)ds);
     Dataset *d = dit->second.get();
     if (M + d->p > 64) return fail(PLK_E_INVALID, "M + p must be <= 64");
-    const size_t need = job_io_bytes(K, M, d->p, d->n) + item_bytes(d->n, d->p, M, 1, o.precision);
+    const size_t need = job_io_bytes(K, M, d->p, d->n) + (c->host ? ALIGN : item_bytes(d->n, d->p, M, 1, o.precision));
     if (need > c->arena.size())
         return fail(PLK_E_NOMEM, "job needs at least %zu bytes, arena is %zu", need, c->arena.size());
     auto j = std::make_unique<Job>();
@@ -1111,13 +1217,22 @@ extern "C" plk_status plk_poll(plk_ctx *c, plk_job job, int32_t timeout_ms, doub
     auto it = c->jobs.find(job);
     if (it == c->jobs.end()) return fail(PLK_E_INVALID, "unknown job %lld", (long long)job);
     Job *j = it->second.get();
-    auto ready = [&] { return j->done; };
-    if (!ready()) {
+    if (!j->done) {
         if (timeout_ms == 0) return fail(PLK_E_NOT_READY, "job %lld running", (long long)job);
-        if (timeout_ms < 0)
-            c->cv_done.wait(lk, ready);
-        else if (!c->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), ready))
-            return fail(PLK_E_NOT_READY, "job %lld running", (long long)job);
+        // wait in slices: a completion whose notification was lost is still
+        // seen within one slice
+        const auto deadline = std::chrono::steady_clock::now() + std::chrono::milliseconds(timeout_ms);
+        while (!j->done) {
+            auto slice = std::chrono::steady_clock::now() + std::chrono::milliseconds(50);
+            if (timeout_ms > 0 && deadline < slice) slice = deadline;
+            c->cv_done.wait_until(lk, slice);
+            if (!j->done && timeout_ms > 0 && std::chrono::steady_clock::now() >= deadline)
+                return fail(PLK_E_NOT_READY, "job %lld running", (long long)job);
+        }
+    }
+    if (j->cancelled) {
+        c->jobs.erase(it);
+        return fail(PLK_E_CANCELLED, "job %lld was cancelled", (long long)job);
     }
     if (j->failed) {
         std::string msg = j->error;
@@ -1163,11 +1278,88 @@ extern "C" plk_status plk_destroy(plk_ctx *c) {
         c->cv_work.notify_all();
     }
     for (auto &t : c->workers) t.join();
+    if (c->metrics) std::fclose(c->metrics);
+    if (c->host) {
+        std::free(c->arena_base);
+        delete c;
+        return PLK_OK;
+    }
     cudaSetDevice(c->device);
     if (c->own_streams)
         for (auto s : c->streams) cudaStreamDestroy(s);
     if (c->own_arena) cudaFree(c->arena_base);
     delete c;
+    return PLK_OK;
+}
+
+extern "C" plk_status plk_create_with_evaluator(plk_ctx **out, size_t arena_bytes, int n_workers,
+                                                plk_host_eval_fn fn, void *user) {
+    if (!out || !fn) return fail(PLK_E_INVALID, "NULL argument");
+    if (arena_bytes < (1u << 20)) return fail(PLK_E_INVALID, "arena_bytes too small");
+    if (n_workers < 1 || n_workers > 64) return fail(PLK_E_INVALID, "n_workers must be in [1, 64]");
+    auto c = std::make_unique<plk_ctx>();
+    c->host = true;
+    c->host_fn = fn;
+    c->host_user = user;
+    c->device = -1;
+    c->t0 = std::chrono::steady_clock::now();
+    const size_t bytes = arena_bytes / ALIGN * ALIGN;
+    c->arena_base = static_cast<char *>(std::aligned_alloc(ALIGN, bytes));
+    if (!c->arena_base) return fail(PLK_E_NOMEM, "host arena of %zu bytes", bytes);
+    c->own_arena = true;
+    c->arena.init(c->arena_base, bytes);
+    for (int i = 0; i < n_workers; ++i) c->workers.emplace_back(stream_worker, c.get(), i);
+    *out = c.release();
+    return PLK_OK;
+}
+
+extern "C" plk_status plk_cancel(plk_ctx *c, plk_job job) {
+    if (!c) return fail(PLK_E_INVALID, "ctx is NULL");
+    std::lock_guard<std::mutex> lk(c->mu);
+    auto it = c->jobs.find(job);
+    if (it == c->jobs.end()) return fail(PLK_E_INVALID, "unknown job %lld", (long long)job);
+    Job *j = it->second.get();
+    if (j->done) return PLK_OK;   // finished already: its results stay available
+    j->cancelled = true;
+    j->next_k = j->K;             // no further batches
+    if (j->inflight == 0) {       // nothing running: it ends now
+        if (j->started) {
+            finish_job(c, j);
+        } else {
+            c->datasets[j->ds]->active_jobs--;
+            j->done = true;
+            j->t_done = c->now();
+            write_metrics(c, j);
+        }
+        c->order.erase(std::find(c->order.begin(), c->order.end(), j));
+        notify_done(c);
+    }
+    c->cv_work.notify_all();
+    return PLK_OK;
+}
+
+extern "C" plk_status plk_inject_fault(plk_ctx *c, int32_t kind, int32_t count) {
+    if (!c) return fail(PLK_E_INVALID, "ctx is NULL");
+    if (count < 0) return fail(PLK_E_INVALID, "count < 0");
+    std::lock_guard<std::mutex> lk(c->mu);
+    switch (kind) {
+        case PLK_FAULT_ARENA_ALLOC: c->fault_arena = count; break;
+        case PLK_FAULT_BATCH: c->fault_item = count; break;
+        case PLK_FAULT_DROP_COMPLETION: c->fault_drop = count; break;
+        default: return fail(PLK_E_INVALID, "unknown fault kind %d", kind);
+    }
+    c->cv_work.notify_all();
+    return PLK_OK;
+}
+
+extern "C" plk_status plk_set_metrics_log(plk_ctx *c, const char *path) {
+    if (!c) return fail(PLK_E_INVALID, "ctx is NULL");
+    std::lock_guard<std::mutex> lk(c->mu);
+    if (c->metrics) std::fclose(c->metrics);
+    c->metrics = nullptr;
+    if (!path) return PLK_OK;
+    c->metrics = std::fopen(path, "a");
+    if (!c->metrics) return fail(PLK_E_INVALID, "cannot open %s for appending", path);
     return PLK_OK;
 }
 
@@ -1182,6 +1374,7 @@ extern "C" plk_status plk_autotune(plk_ctx *c, int64_t n, int32_t p, int32_t M, 
                                    const int32_t *candidates, int32_t n_candidates, int32_t *best_batch,
                                    double *best_rate) {
     if (!c) return fail(PLK_E_INVALID, "ctx is NULL");
+    if (c->host) return fail(PLK_E_INVALID, "autotune needs a GPU context");
     if (!sizes_ok(n, p, M)) return fail(PLK_E_INVALID, "invalid sizes n=%lld p=%d M=%d", (long long)n, p, M);
     if (precision != PLK_FP64 && precision != PLK_MIXED) return fail(PLK_E_INVALID, "unknown precision");
     std::vector<int> cand;

@@ -58,6 +58,11 @@ class CloudOptions(C.Structure):
                 ("sphere_rounds", C.c_int32)]
 
 
+_PD = C.POINTER(C.c_double)
+HOST_EVAL_FN = C.CFUNCTYPE(C.c_int, C.c_void_p, C.c_int64, C.c_int32, _PD, _PD, _PD, _PD, C.c_int64, _PD, C.c_int32,
+                           _PD, _PD, _PD, _PD, C.POINTER(C.c_int32))
+FAULT_ARENA_ALLOC, FAULT_BATCH, FAULT_DROP_COMPLETION = 1, 2, 3
+
 EVAL_FN = C.CFUNCTYPE(C.c_int32, C.c_void_p, C.POINTER(C.c_double), C.c_int64, C.POINTER(C.c_double), C.c_int32,
                       C.POINTER(C.c_double))
 
@@ -122,6 +127,10 @@ def lib():
                                              C.POINTER(i64), vp, vp, vp]),
         "plk_kernel_class_name": (C.c_char_p, [i32]),
         "plk_selftest_bounded_wait": (C.c_int, [i32, vp]),
+        "plk_cancel": (C.c_int, [vp, i64]),
+        "plk_set_metrics_log": (C.c_int, [vp, C.c_char_p]),
+        "plk_inject_fault": (C.c_int, [vp, i32, i32]),
+        "plk_create_with_evaluator": (C.c_int, [C.POINTER(vp), sz, C.c_int, HOST_EVAL_FN, vp]),
         "plk_selftest_df_exp": (C.c_int, [vp, vp, vp, vp, i64, vp]),
     }
     for name, (res, args) in sig.items():
@@ -384,16 +393,43 @@ def internal_params_device(params, kappa_hat_large=False, out=None, stream=None)
     return out
 
 
+def _host_eval_callback(fn):
+    """Wrap fn(coords[n,2], y[n], X[n,p], params[count,5], lambdas[M]) ->
+    dict(logL, sigma2, beta, logdet, status) as a plk_host_eval_fn."""
+    def cb(user, n, p, coords, y, X, params, count, lambdas, M, logL, sigma2, beta, logdet, status):
+        try:
+            arr = np.ctypeslib.as_array
+            r = fn(arr(coords, shape=(n, 2)).copy(), arr(y, shape=(n,)).copy(), arr(X, shape=(n, p)).copy(),
+                   arr(params, shape=(count, 5)).copy(), arr(lambdas, shape=(M,)).copy())
+            arr(logL, shape=(count, M))[:] = r["logL"]
+            arr(sigma2, shape=(count, M))[:] = r["sigma2"]
+            arr(beta, shape=(count, M, p))[:] = r["beta"]
+            arr(logdet, shape=(count, 2))[:] = r["logdet"]
+            arr(status, shape=(count,))[:] = r["status"]
+            return 0
+        except Exception:
+            return 1
+    return HOST_EVAL_FN(cb)
+
+
 class Context:
     """Device-resident datasets and asynchronous profile jobs (plk_create ... plk_destroy).
 
     `arena` may be a torch uint8 CUDA tensor (PyTorch owns the memory); if None
-    the library allocates `arena_bytes` itself.
+    the library allocates `arena_bytes` itself.  With `evaluator` (a host
+    function, see _host_eval_callback) the context runs its batches on
+    `n_streams` host worker threads through it instead of on a GPU
+    (plk_create_with_evaluator: for testing the scheduler without a GPU).
     """
 
-    def __init__(self, arena_bytes, device=0, arena=None, n_streams=4, streams=None):
+    def __init__(self, arena_bytes, device=0, arena=None, n_streams=4, streams=None, evaluator=None):
         self._arena = arena
         h = C.c_void_p()
+        if evaluator is not None:
+            self._cb = _host_eval_callback(evaluator)
+            _check(lib().plk_create_with_evaluator(C.byref(h), int(arena_bytes), int(n_streams), self._cb, None))
+            self.h = h
+            return
         sarr = None
         if streams is not None:
             sarr = (C.c_void_p * len(streams))(*[s.cuda_stream for s in streams])
@@ -438,6 +474,17 @@ class Context:
 
     def release_dataset(self, ds):
         _check(lib().plk_release_dataset(self.h, ds))
+
+    def cancel(self, job):
+        _check(lib().plk_cancel(self.h, job["id"]))
+
+    def set_metrics_log(self, path):
+        _check(lib().plk_set_metrics_log(self.h, None if path is None else os.fsencode(path)))
+
+    def inject_fault(self, kind, count):
+        """Host-side fault hook (plk_inject_fault): FAULT_ARENA_ALLOC, FAULT_BATCH
+        or FAULT_DROP_COMPLETION for the next `count` events."""
+        _check(lib().plk_inject_fault(self.h, int(kind), int(count)))
 
     def autotune(self, n, p, M, precision=FP64, candidates=None):
         """Tune the points per scheduled batch for datasets of about n sites

@@ -53,7 +53,7 @@ def unpack_results(a, M, p):
     return out
 
 
-def gather_results(idx, results, K, M, p, device="cpu"):
+def gather_results(idx, results, K, M, p, device="cpu", strict=True):
     """Merge every rank's per-point results into arrays over all K points.
 
     idx: the global point indices this rank evaluated ([B_r], any B_r >= 0);
@@ -62,9 +62,10 @@ def gather_results(idx, results, K, M, p, device="cpu"):
     all_gather of the packed results padded to the largest count (tensors on
     `device`: "cuda" under NCCL, "cpu" under gloo).  Every rank returns the
     merged dict (K rows; points no rank evaluated hold NaN and status -1) and
-    the number of points evaluated by any rank.  A point evaluated by two
-    ranks must have identical results on both (every point's arithmetic
-    depends only on its own data)."""
+    the number of points evaluated by any rank.  A point evaluated twice must
+    have identical results both times (every point's arithmetic depends only
+    on its own data): strict raises otherwise; without strict the first
+    result is kept and the count of such points is returned as a third value."""
     import torch
     import torch.distributed as dist
     world = dist.get_world_size()
@@ -85,13 +86,18 @@ def gather_results(idx, results, K, M, p, device="cpu"):
     merged = np.full((K, F), np.nan)
     merged[:, -1] = -1
     seen = np.zeros(K, dtype=bool)
+    mismatches = 0
     for c, part in zip(counts, parts):
         a = part.cpu().numpy()[:c]
         ks = a[:, 0].astype(np.int64)
         for j, k in enumerate(ks):
             if seen[k]:
                 if not np.array_equal(merged[k], a[j, 1:], equal_nan=True):
-                    raise RuntimeError(f"point {k}: different results on two ranks")
+                    if strict:
+                        raise RuntimeError(f"point {k}: different results in two evaluations")
+                    mismatches += 1
+                continue
             merged[k] = a[j, 1:]
             seen[k] = True
-    return unpack_results(merged, M, p), int(seen.sum())
+    out = unpack_results(merged, M, p)
+    return (out, int(seen.sum())) if strict else (out, int(seen.sum()), mismatches)

@@ -118,3 +118,39 @@ def test_bounded_wait_gives_up_and_device_stays_usable():
     o = oracle.profile_batch(ds.coords, ds.y, ds.X, P, lams)
     ok = o["status"] == 0
     assert np.max(np.abs(g["logL"][ok] - o["logL"][ok])) <= 1e-3
+
+
+def test_cancel_and_fault_hooks_on_a_gpu_context(tmp_path):
+    """plk_cancel on a running GPU job (its in-flight batches finish, the rest
+    are dropped), an injected batch failure and arena-allocation failures,
+    all made on the host; the context keeps producing the stateless path's
+    results afterwards; every job leaves one metrics line."""
+    import json
+    ds = synth.aniso_dataset(63, 1500, math.sqrt(150.0), 3)
+    lams = synth.LAMBDA_GRID_9
+    P = synth.omega_from_unit(np.random.default_rng(63).uniform(size=(400, 5)))
+    small = P[:12]
+    ref = gpu_eval(ds, small, lams, batch=4)
+    log = tmp_path / "jobs.jsonl"
+    arena = torch.empty(6 << 30, dtype=torch.uint8, device="cuda")
+    with nv.Context(arena.numel(), arena=arena, n_streams=1) as ctx:
+        ctx.set_metrics_log(str(log))
+        d = ctx.create_dataset(ds.coords, ds.y, ds.X)
+        big = ctx.submit(d, P, lams, batch=4)           # 100 batches
+        assert ctx.poll(big, ds.p, timeout_ms=200) is None
+        ctx.cancel(big)
+        with pytest.raises(nv.PlkError) as e:
+            ctx.poll(big, ds.p)
+        assert e.value.status == nv.PLK_E_CANCELLED
+        ctx.inject_fault(nv.FAULT_BATCH, 1)
+        with pytest.raises(nv.PlkError) as e:
+            ctx.poll(ctx.submit(d, small, lams, batch=4), ds.p)
+        assert "injected batch failure" in str(e.value)
+        ctx.inject_fault(nv.FAULT_ARENA_ALLOC, 3)
+        r = ctx.poll(ctx.submit(d, small, lams, batch=4), ds.p)
+        for k in ("logL", "sigma2", "beta", "logdet", "status"):
+            np.testing.assert_array_equal(r[k], ref[k], err_msg=k)
+        ctx.release_dataset(d)
+    lines = [json.loads(x) for x in log.read_text().splitlines()]
+    assert [x["outcome"] for x in lines] == ["cancelled", "failed", "ok"]
+    assert 1 <= lines[0]["items"] < 100
