@@ -180,6 +180,24 @@ def probe_fp64_peak():
     return L.plk_probe_fp64_fma_tflops(5), L.plk_probe_fp32_fma_tflops(5)
 
 
+def probe_pipes():
+    """Live throughputs (TFLOP/s) of the pipes the design chooses between:
+    FP64 FMA (DFMA), FP64 tensor MMA (DMMA, mma.sync m8n8k4), FP32 FMA, and
+    tcgen05 bf16 MMA with both operands in shared memory at N = 64, 128, 256."""
+    import ctypes as C
+    from paper_2305_04318_b300 import build
+    L = C.CDLL(build.build_probe())
+    for f in ("plk_probe_fp64_fma_tflops", "plk_probe_fp32_fma_tflops", "plk_probe_fp64_mma_tflops",
+              "plk_probe_tcgen05_bf16_tflops"):
+        getattr(L, f).restype = C.c_double
+    L.plk_probe_tcgen05_bf16_tflops.argtypes = [C.c_int, C.c_int]
+    out = {"fp64_fma": L.plk_probe_fp64_fma_tflops(5), "fp64_dmma": L.plk_probe_fp64_mma_tflops(5),
+           "fp32_fma": L.plk_probe_fp32_fma_tflops(5)}
+    for N in (64, 128, 256):
+        out[f"tcgen05_bf16_n{N}"] = L.plk_probe_tcgen05_bf16_tflops(N, 5)
+    return {k: round(v, 2) for k, v in out.items()}
+
+
 def trailing_flops(n, q, TB=128):
     """Algorithmic flops of the trailing updates, per omega, per step J of the
     blocked factorisation: the rank-TB update of the lower triangle of the true
@@ -795,7 +813,8 @@ def main():
     dom = max(timing, key=lambda k: timing[k][0])
     dom_ms = timing[dom][0]
     launches = int(sum(c for _, c in timing.values()))
-    fp64_peak, fp32_peak = probe_fp64_peak()
+    pipes = probe_pipes()
+    fp64_peak, fp32_peak = pipes["fp64_fma"], pipes["fp32_fma"]
     tf = sum(trailing_flops(n, q))   # algorithmic trailing-update flops per omega
     roof = None
     st = main_res["status"]
@@ -929,7 +948,7 @@ def main():
                 "kernel_timing_is": "kernel_ms, kernel_share and the roofline's kernel time come from the timed "
                                     "steps run once more after the timed region with CUDA events around every "
                                     "launch (instrumented_ms_per_step); value and ms_per_step are uninstrumented",
-                "fp64_fma_peak_tflops": fp64_peak, "fp32_fma_peak_tflops": fp32_peak,
+                "fp64_fma_peak_tflops": fp64_peak, "fp32_fma_peak_tflops": fp32_peak, "pipe_probes_tflops": pipes,
                 "points_not_ok": int(((st & 15) != 0).sum()), "points_evaluated": int(n_pts)}
         print(json.dumps(line), flush=True)
     if world > 1:
