@@ -103,6 +103,16 @@ typedef struct {
  * identical with and without this flag (it exists for that check and for
  * timing the full pass).  PLK_FLAG_NO_RETRY implies it. */
 #define PLK_FLAG_FULL_FIRST_PASS 16
+/* flags: keep small datasets on the tiled path.  By default a dataset with
+ * n + M + p <= 224 is evaluated by one fused kernel per batch: one thread
+ * block per point builds the bordered matrix in shared memory, factors it and
+ * leaves the cross-products for the closed form -- in FP64 for PLK_FP64; in
+ * double-float FP32 arithmetic for PLK_MIXED, where a point whose
+ * a-posteriori bound 2^-36 (1 + nu^2) sum_j 1/d_j exceeds 1e-4 (or whose
+ * factorisation fails) is evaluated again in FP64 (status bits RETRIED and
+ * FP64, err_bound 0).  This flag selects the tiled path instead (for
+ * comparisons). */
+#define PLK_FLAG_NO_FUSED 32
 
 /* ------------------------------------------------------------------------ */
 /* Stateless device-pointer evaluation (one dataset, K points)               */

@@ -339,6 +339,9 @@ static cudaError_t launch_as_graph(cudaStream_t s, F &&enqueue) {
 }
 
 static bool use_graph(int flags) { return (flags & PLK_FLAG_GRAPH) && !(flags & PLK_FLAG_KERNEL_TIMING); }
+// Small datasets go through the fused one-CTA-per-point kernel in either
+// precision (FP64 there costs less than the tiled tensor-core path).
+static bool use_fused(int64_t n, int q, int flags) { return fused_applies(n, q) && !(flags & PLK_FLAG_NO_FUSED); }
 
 // 5-slice pass over the batch.  With `overlap` and enough points, the batch is
 // cut into parts of about 296 points (two diagonal-tile blocks per SM); the
@@ -460,10 +463,49 @@ static plk_status run_mixed_batch(BatchArgs b, const Layout &L, void *ws, const 
     return PLK_OK;
 }
 
+// Mixed precision on a small dataset: the fused kernel in double-float FP32
+// over the batch, its a-posteriori bound per point, then (unless
+// PLK_FLAG_NO_RETRY) the fused FP64 kernel on the points whose bound exceeded
+// the tolerance or whose factorisation failed (status bits RETRIED | FP64,
+// err_bound 0).  Deciding the retry set reads the flags back, so this
+// synchronizes the stream once per batch.
+static plk_status run_fused_mixed_batch(BatchArgs b, const Layout &L, void *ws, const double *params_all, int flags,
+                                        double *err_bound, cudaStream_t s) {
+    double *invsum = at<double>(ws, L.off_invsum);
+    int *fl = at<int>(ws, L.off_flags);
+    cudaError_t e = launch_fused_df_batch(b, invsum, s);
+    if (e == cudaSuccess) e = launch_mixed_bound(b, FUSED_DF_EPS, kMixedTol, 1, invsum, err_bound, fl, s);
+    if (e != cudaSuccess) return cuda_fail(e, "fused mixed launch");
+    if (flags & PLK_FLAG_NO_RETRY) return PLK_OK;
+    std::vector<int> hf(b.count);
+    e = cudaMemcpyAsync(hf.data(), fl, sizeof(int) * b.count, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "fused mixed batch");
+    std::vector<int> idx;
+    for (int w = 0; w < b.count; ++w)
+        if (hf[w]) idx.push_back((int)(b.k0 + w));
+    if (idx.empty()) return PLK_OK;
+    int *d_idx = at<int>(ws, L.off_idx);
+    double *d_par = at<double>(ws, L.off_cparams);
+    e = cudaMemcpyAsync(d_idx, idx.data(), sizeof(int) * idx.size(), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = launch_gather_params((int)idx.size(), d_idx, params_all, d_par, s);
+    BatchArgs f = b;
+    f.count = (int)idx.size();
+    f.params = d_par;
+    f.out_index = d_idx;
+    f.status_or = PLK_POINT_RETRIED | PLK_POINT_FP64;
+    if (e == cudaSuccess) e = launch_fused_batch(f, s);
+    if (e == cudaSuccess && err_bound) e = launch_scatter_value(f.count, d_idx, 0.0, err_bound, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);   // idx must outlive its copy
+    if (e != cudaSuccess) return cuda_fail(e, "fused fp64 retry");
+    return PLK_OK;
+}
+
 // Enqueue the whole evaluation on `s` given a laid-out workspace.
 static plk_status run_eval(const plk_eval_args *a, int reml, int flags, const Layout &L, void *ws,
                            cudaStream_t s) {
     KernelTimer *timer = (flags & PLK_FLAG_KERNEL_TIMING) ? &g_timer : nullptr;
+    const bool fused = use_fused(a->n, L.q, flags);
     cudaError_t e = launch_boxcox(a->n, L.n_pad, a->p, a->M, a->y, a->X, a->coords, a->lambdas,
                                   at<double>(ws, L.off_Bt), at<double>(ws, L.off_sumlog), s, timer);
     if (e != cudaSuccess) return cuda_fail(e, "boxcox launch");
@@ -499,7 +541,14 @@ static plk_status run_eval(const plk_eval_args *a, int reml, int flags, const La
         b.ssq = a->ssq_yx;
         b.status = a->status;
         b.timer = timer;
-        if (L.mixed) {
+        if (fused && L.mixed) {
+            plk_status st = run_fused_mixed_batch(b, L, ws, a->params, flags, a->err_bound, s);
+            if (st != PLK_OK) return st;
+        } else if (fused) {
+            e = use_graph(flags) ? launch_as_graph(s, [&]() { return launch_fused_batch(b, s); })
+                                 : launch_fused_batch(b, s);
+            if (e != cudaSuccess) return cuda_fail(e, "fused batch launch");
+        } else if (L.mixed) {
             plk_status st = run_mixed_batch(b, L, ws, a->params, flags, a->err_bound, true, s);
             if (st != PLK_OK) return st;
         } else {
@@ -891,7 +940,16 @@ std::string run_item(plk_ctx *c, Job *j, Item &it, cudaStream_t s) {
     b.status = j->d_st;
     cudaStreamWaitEvent(s, j->ready, 0);   // the job's B^T may come from another stream
     std::string err;
-    if (L.mixed) {
+    if (use_fused(j->n, L.q, j->opts.flags) && L.mixed) {
+        plk_status st = run_fused_mixed_batch(b, L, it.ws, j->d_params, j->opts.flags, nullptr, s);
+        if (st == PLK_OK && cudaStreamSynchronize(s) != cudaSuccess) st = PLK_E_CUDA;
+        if (st != PLK_OK) err = plk_last_error();
+    } else if (use_fused(j->n, L.q, j->opts.flags)) {
+        cudaError_t e = use_graph(j->opts.flags) ? launch_as_graph(s, [&]() { return launch_fused_batch(b, s); })
+                                                 : launch_fused_batch(b, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) err = cudaGetErrorString(e);
+    } else if (L.mixed) {
         plk_status st = run_mixed_batch(b, L, it.ws, j->d_params, j->opts.flags, nullptr, true, s);
         if (st != PLK_OK) err = plk_last_error();
     } else {

@@ -530,7 +530,9 @@ __device__ __forceinline__ double rho_df(double u, double kap, double logc, cons
     return exp(logc + kap * log(u) - u + (double)A) * (0.5 * (double)h * ((double)sh + (double)sl));
 }
 
-// Table builder: one block of 320 threads = 32 sub-intervals x TAB_NC Chebyshev nodes.
+// Table builder: one block of BPB x TAB_NC threads = BPB sub-intervals x
+// TAB_NC Chebyshev nodes (BPB = 32; 8 for the fused small-n path, whose
+// batches often share one table: four times the blocks per table).
 // F32TAB writes each sub-interval's coefficients as TAB_F32 floats instead of
 // TAB_NC doubles: c_0..c_3 as double-float pairs, c_4..c_9 rounded to FP32
 // (the layout k_build_f32 reads; it fits in the same per-point region), and
@@ -538,17 +540,18 @@ __device__ __forceinline__ double rho_df(double u, double kap, double logc, cons
 // For u <= TAB_USPLIT the trapezoid nodes are the fixed grid t_k = k QH, whose
 // cosh(t_k) - 1 and log cosh(kappa t_k) are staged in shared memory, so one exp
 // per node remains.
-template <bool F32TAB>
-__global__ void __launch_bounds__(320) k_matern_table(const double *__restrict__ oconst,
-                                                      double *__restrict__ tab, const int *__restrict__ owner) {
+template <bool F32TAB, int BPB = 32>
+__global__ void __launch_bounds__(BPB * TAB_NC) k_matern_table(const double *__restrict__ oconst,
+                                                               double *__restrict__ tab,
+                                                               const int *__restrict__ owner) {
     // FP64 evaluation: cosh(t_k) - 1 = 2 sinh^2(t_k / 2) and log cosh(kappa t_k);
     // double-float evaluation (F32TAB): cosh(t_k) - 1 as double-float
     __shared__ double E1[F32TAB ? 1 : QNODES];
     __shared__ double L2[F32TAB ? 1 : QNODES];
     __shared__ float2 E1f[F32TAB ? QNODES : 1];
     __shared__ int TMi[TAB_NC][TAB_NC];
-    __shared__ double F[32][TAB_NC];
-    __shared__ double A[32][TAB_NC];          // Chebyshev coefficients per bucket
+    __shared__ double F[BPB][TAB_NC];
+    __shared__ double A[BPB][TAB_NC];         // Chebyshev coefficients per bucket
     __shared__ double CT[TAB_NC][TAB_NC];     // cos(pi k (m + 1/2) / NC)
     __shared__ double TM[TAB_NC][TAB_NC];     // T_k(t) = sum_m TM[k][m] t^m
     const int w = blockIdx.y;
@@ -556,9 +559,9 @@ __global__ void __launch_bounds__(320) k_matern_table(const double *__restrict__
     const double *oc = oconst + OC_N * (int64_t)w;
     const double kap = oc[OC_KAPPA], logc = oc[OC_LOGC];
     const int elo = (int)oc[OC_ELO], ehi = (int)oc[OC_EHI];
-    {   // this block's buckets: octaves TAB_ELO + 32 blockIdx.x / TAB_S .. + 32 / TAB_S - 1
+    {   // this block's buckets: octaves TAB_ELO + BPB blockIdx.x / TAB_S .. + BPB / TAB_S - 1
         const int bx = (int)blockIdx.x;
-        const int e0 = TAB_ELO + (bx * 32) / TAB_S, e1 = TAB_ELO + (bx * 32 + 31) / TAB_S;
+        const int e0 = TAB_ELO + (bx * BPB) / TAB_S, e1 = TAB_ELO + (bx * BPB + BPB - 1) / TAB_S;
         if (e1 < elo || e0 >= ehi) return;   // none of them is read
     }
     const double PI = 3.14159265358979323846;
@@ -578,8 +581,8 @@ __global__ void __launch_bounds__(320) k_matern_table(const double *__restrict__
             L2[k] = kt + log1p(exp(-2.0 * kt)) - 0.69314718055994530942;
         }
     }
-    if (threadIdx.x < TAB_NC * TAB_NC) {
-        const int k = threadIdx.x / TAB_NC, m = threadIdx.x % TAB_NC;
+    for (int t = threadIdx.x; t < TAB_NC * TAB_NC; t += blockDim.x) {
+        const int k = t / TAB_NC, m = t % TAB_NC;
         CT[k][m] = cos(PI * k * (m + 0.5) / TAB_NC);
     }
     if (threadIdx.x == 0) {   // T_0 = 1, T_1 = t, T_k = 2 t T_{k-1} - T_{k-2} (small integers)
@@ -590,13 +593,13 @@ __global__ void __launch_bounds__(320) k_matern_table(const double *__restrict__
                                    : (m > 0 ? 2 * TMi[k - 1][m - 1] : 0) - TMi[k - 2][m];
     }
     __syncthreads();
-    if (threadIdx.x < TAB_NC * TAB_NC) {
-        const int k = threadIdx.x / TAB_NC, m = threadIdx.x % TAB_NC;
+    for (int t = threadIdx.x; t < TAB_NC * TAB_NC; t += blockDim.x) {
+        const int k = t / TAB_NC, m = t % TAB_NC;
         TM[k][m] = (double)TMi[k][m];
     }
     __syncthreads();
     const int lb = threadIdx.x / TAB_NC, l = threadIdx.x % TAB_NC;
-    const int bucket = blockIdx.x * 32 + lb;
+    const int bucket = blockIdx.x * BPB + lb;
     const int eb = TAB_ELO + bucket / TAB_S;
     const bool used = bucket < TAB_NBUCKET && eb >= elo && eb < ehi;
     if (used) {
@@ -791,6 +794,66 @@ __device__ __forceinline__ void ldg_v8(const float *p, float (&v)[8]) {   // 32-
                  : "l"(p));
 }
 
+// One entry rho(w_ij) of the first pass's double-float build, sites i (row)
+// and j (column) given by their double-float transformed coordinates:
+//   w = (a_i - a_j)^2 + (b_i - b_j)^2 from double-float coordinates (error-free
+//       differences and squares, a positive sum: relative error ~2^-44);
+//   sub-interval from the FP32 bits of w_hi, local variable t = t_hi + t_lo with
+//       t_hi exact (fma of the mantissa) and t_lo = w_lo scaled by a power of 2;
+//   Horner: c_9..c_4 in FP32 on t_hi (these terms are below ~1e-6 of rho),
+//       c_3..c_0 in double-float on (t_hi, t_lo).
+// Pairs outside the table's octaves take the FP64 integral (rare).
+__device__ __forceinline__ void rho_entry_df(float aih, float ail, float bih, float bil, float ajh, float ajl,
+                                             float bjh, float bjl, const float *__restrict__ tf, int elo, int ehi,
+                                             double kap, double logc, float &vh, float &vl) {
+    vl = 0.0f;
+    float s, e, dah, dal, dbh, dbl;
+    two_sum_f(aih, -ajh, s, e);
+    e = __fadd_rn(e, __fsub_rn(ail, ajl));
+    two_sum_f(s, e, dah, dal);
+    two_sum_f(bih, -bjh, s, e);
+    e = __fadd_rn(e, __fsub_rn(bil, bjl));
+    two_sum_f(s, e, dbh, dbl);
+    const float p1 = __fmul_rn(dah, dah), p2 = __fmul_rn(dbh, dbh);
+    float e1 = __fmaf_rn(dah, dah, -p1), e2 = __fmaf_rn(dbh, dbh, -p2);
+    e1 = __fmaf_rn(dah + dah, dal, e1);
+    e2 = __fmaf_rn(dbh + dbh, dbl, e2);
+    two_sum_f(p1, p2, s, e);
+    float wh, wl;
+    fast_two_sum_f(s, __fadd_rn(e, __fadd_rn(e1, e2)), wh, wl);
+    const unsigned bits = __float_as_uint(wh);
+    const int ew = (int)(bits >> 23) - 127;   // w >= 0
+    if (wh == 0.0f) {
+        vh = 1.0f;                         // coincident sites
+    } else if (ew >= TAB_EHI) {
+        vh = 0.0f;
+    } else if (ew < elo || ew >= ehi) {    // outside the octaves built for this point
+        split_df_bits(rho_integral(sqrt((double)wh + (double)wl), kap, logc), vh, vl);
+    } else {
+        const int jb = (int)(bits >> (23 - TAB_SB)) & (TAB_S - 1);
+        const float m = __uint_as_float((bits & 0x007fffffu) | 0x3f800000u);   // [1, 2)
+        const float th = __fmaf_rn(m, 2.0f * TAB_S, -(float)(2 * TAB_S + 2 * jb + 1));   // exact
+        const float tl = __fmul_rn(wl, __uint_as_float((unsigned)(127 + TAB_SB + 1 - ew) << 23));
+        const float *cb = tf + ((ew - TAB_ELO) * TAB_S + jb) * TAB_F32;
+        float q0[8], q1[8];
+        ldg_v8(cb, q0);
+        ldg_v8(cb + 8, q1);
+        // c_9 .. c_4 in FP32
+        float ph = __fmaf_rn(q1[5], th, q1[4]);
+        ph = __fmaf_rn(ph, th, q1[3]);
+        ph = __fmaf_rn(ph, th, q1[2]);
+        ph = __fmaf_rn(ph, th, q1[1]);
+        ph = __fmaf_rn(ph, th, q1[0]);
+        float pl = 0.0f;
+        // c_3 .. c_0 in double-float
+        df_horner_step(ph, pl, th, tl, q0[6], q0[7]);
+        df_horner_step(ph, pl, th, tl, q0[4], q0[5]);
+        df_horner_step(ph, pl, th, tl, q0[2], q0[3]);
+        df_horner_step(ph, pl, th, tl, q0[0], q0[1]);
+        fast_two_sum_f(ph, pl, vh, vl);
+    }
+}
+
 __global__ void __launch_bounds__(256) k_build_f32(int nb, int64_t n, int64_t n_pad, int q, int64_t tpo,
                                                    double *__restrict__ tiles,
                                                    const double *__restrict__ oconst,
@@ -840,51 +903,8 @@ __global__ void __launch_bounds__(256) k_build_f32(int nb, int64_t n, int64_t n_
         } else if (i < j) {
             vh = 0.0f;                             // upper part of a diagonal tile, unused
         } else {
-            float s, e, dah, dal, dbh, dbl;
-            two_sum_f(cf[i], -ajh, s, e);
-            e = __fadd_rn(e, __fsub_rn(cf[n_pad + i], ajl));
-            two_sum_f(s, e, dah, dal);
-            two_sum_f(cf[2 * n_pad + i], -bjh, s, e);
-            e = __fadd_rn(e, __fsub_rn(cf[3 * n_pad + i], bjl));
-            two_sum_f(s, e, dbh, dbl);
-            const float p1 = __fmul_rn(dah, dah), p2 = __fmul_rn(dbh, dbh);
-            float e1 = __fmaf_rn(dah, dah, -p1), e2 = __fmaf_rn(dbh, dbh, -p2);
-            e1 = __fmaf_rn(dah + dah, dal, e1);
-            e2 = __fmaf_rn(dbh + dbh, dbl, e2);
-            two_sum_f(p1, p2, s, e);
-            float wh, wl;
-            fast_two_sum_f(s, __fadd_rn(e, __fadd_rn(e1, e2)), wh, wl);
-            const unsigned bits = __float_as_uint(wh);
-            const int ew = (int)(bits >> 23) - 127;   // w >= 0
-            if (wh == 0.0f) {
-                vh = 1.0f;                         // coincident sites
-            } else if (ew >= TAB_EHI) {
-                vh = 0.0f;
-            } else if (ew < elo || ew >= ehi) {    // outside the octaves built for this point
-                split_df_bits(rho_integral(sqrt((double)wh + (double)wl), kap, logc), vh, vl);
-            } else {
-                const int jb = (int)(bits >> (23 - TAB_SB)) & (TAB_S - 1);
-                const float m = __uint_as_float((bits & 0x007fffffu) | 0x3f800000u);   // [1, 2)
-                const float th = __fmaf_rn(m, 2.0f * TAB_S, -(float)(2 * TAB_S + 2 * jb + 1));   // exact
-                const float tl = __fmul_rn(wl, __uint_as_float((unsigned)(127 + TAB_SB + 1 - ew) << 23));
-                const float *cb = tf + ((ew - TAB_ELO) * TAB_S + jb) * TAB_F32;
-                float q0[8], q1[8];
-                ldg_v8(cb, q0);
-                ldg_v8(cb + 8, q1);
-                // c_9 .. c_4 in FP32
-                float ph = __fmaf_rn(q1[5], th, q1[4]);
-                ph = __fmaf_rn(ph, th, q1[3]);
-                ph = __fmaf_rn(ph, th, q1[2]);
-                ph = __fmaf_rn(ph, th, q1[1]);
-                ph = __fmaf_rn(ph, th, q1[0]);
-                float pl = 0.0f;
-                // c_3 .. c_0 in double-float
-                df_horner_step(ph, pl, th, tl, q0[6], q0[7]);
-                df_horner_step(ph, pl, th, tl, q0[4], q0[5]);
-                df_horner_step(ph, pl, th, tl, q0[2], q0[3]);
-                df_horner_step(ph, pl, th, tl, q0[0], q0[1]);
-                fast_two_sum_f(ph, pl, vh, vl);
-            }
+            rho_entry_df(cf[i], cf[n_pad + i], cf[2 * n_pad + i], cf[3 * n_pad + i], ajh, ajl, bjh, bjl, tf, elo, ehi,
+                         kap, logc, vh, vl);
         }
         TH[r * TB + c] = vh;
         TL[r * TB + c] = vl;
@@ -1207,7 +1227,7 @@ const char *kernel_class_name(int c) {
     static const char *names[KC_COUNT] = {"boxcox", "omega_prep", "matern_table", "build", "potrf",
                                           "panel_trsm", "trailing_gemm", "finalize", "profile", "convert",
                                           "potrf_mixed", "panel_split", "trailing_split", "panel_split7",
-                                          "trailing_split7"};
+                                          "trailing_split7", "fused_small"};
     return (c >= 0 && c < KC_COUNT) ? names[c] : "";
 }
 
@@ -1233,7 +1253,7 @@ cudaError_t launch_boxcox(int64_t n, int64_t n_pad, int p, int M, const double *
     return cudaGetLastError();
 }
 
-cudaError_t launch_front(const BatchArgs &b, cudaStream_t s, FrontMode mode) {
+cudaError_t launch_front(const BatchArgs &b, cudaStream_t s, FrontMode mode, bool build) {
     const int cnt = b.count;
     KernelTimer *timer = b.timer;
     const int f32 = mode == FRONT_DF_FAST ? 1 : 0;
@@ -1246,8 +1266,12 @@ cudaError_t launch_front(const BatchArgs &b, cudaStream_t s, FrontMode mode) {
     }
     if (f32) {
         TIMED(KC_TABLE, (k_matern_table<true><<<tg, 320, 0, s>>>(b.oconst, b.tab, b.owner)));
-        TIMED(KC_BUILD, (k_build_f32<<<bg, 256, 0, s>>>(b.nb, b.n, b.n_pad, b.q, b.tpo, b.tiles, b.oconst,
-                                                         b.coordT, b.tab, b.Bt, b.owner)));
+        if (build)
+            TIMED(KC_BUILD, (k_build_f32<<<bg, 256, 0, s>>>(b.nb, b.n, b.n_pad, b.q, b.tpo, b.tiles, b.oconst,
+                                                             b.coordT, b.tab, b.Bt, b.owner)));
+    } else if (!build) {   // the fused path: tables spread over more blocks
+        const dim3 tg8((TAB_NBUCKET + 7) / 8, cnt);
+        TIMED(KC_TABLE, (k_matern_table<false, 8><<<tg8, 8 * TAB_NC, 0, s>>>(b.oconst, b.tab, b.owner)));
     } else {
         TIMED(KC_TABLE, (k_matern_table<false><<<tg, 320, 0, s>>>(b.oconst, b.tab, b.owner)));
         if (mode == FRONT_DF)
@@ -1334,6 +1358,368 @@ cudaError_t launch_profile_ci(const double *grid, const double *prof, int64_t G,
                               double *out, cudaStream_t s) {
     k_profile_ci<<<1, 32, 0, s>>>(grid, prof, G, half_q, out);
     return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Fused evaluation of small datasets: one CTA per point (Step 3 items 1-4)
+// ---------------------------------------------------------------------------
+// For n + q <= FUSED_MAX_R the whole bordered matrix [[V, 0], [B^T, 0]] of
+// R = n + q rows fits in shared memory as a packed lower triangle (row i at
+// i (i + 1) / 2), so one CTA builds it (V from the point's rho table, exactly
+// as k_build does, B^T from the Box-Cox rows), factors its first n columns
+// right-looking in FP64 and leaves -B^T V^-1 B in its last q x q block: no
+// 128-tile padding, no launch per tile step.  That block is written where the
+// blocked path leaves it (the last diagonal tile of the point's tile array),
+// so the same closed-form kernel finishes the point.  log|V| is the sum of the
+// logs of the n pivots, reduced over the block.
+constexpr int FUSED_THREADS = 256;
+
+__global__ void __launch_bounds__(FUSED_THREADS, 1) k_fused_small(int64_t n, int64_t n_pad, int q, int nb, int64_t tpo,
+                                                               double *__restrict__ tiles,
+                                                               const double *__restrict__ oconst,
+                                                               const double *__restrict__ coordT,
+                                                               const double *__restrict__ tab,
+                                                               const double *__restrict__ Bt,
+                                                               const int *__restrict__ owner,
+                                                               double *__restrict__ ldv, int *__restrict__ pstatus) {
+    extern __shared__ double A[];
+    const int w = blockIdx.x;
+    const int R = (int)n + q, nn = (int)n;
+    const int64_t P = (int64_t)R * (R + 1) / 2;
+    double *piv = A + P;   // the n pivots
+    __shared__ int s_fail;
+    __shared__ double red[FUSED_THREADS / 32];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = FUSED_THREADS / 32;
+    if (pstatus[w] != PLK_POINT_OK) return;   // invalid parameters: the closed form writes NaN
+    const double *oc = oconst + OC_N * (int64_t)w;
+    const double nug = oc[OC_NUG], kap = oc[OC_KAPPA], logc = oc[OC_LOGC];
+    const int ow = owner ? owner[w] : w;
+    const int elo = (int)oconst[OC_N * (int64_t)ow + OC_ELO], ehi = (int)oconst[OC_N * (int64_t)ow + OC_EHI];
+    const double *ca = coordT + (int64_t)w * 2 * n_pad;
+    const double *cb = ca + n_pad;
+    const double *tw = tab + (int64_t)ow * TAB_SIZE;
+    // build: one warp per row, lanes along the row
+    for (int i = warp; i < R; i += nw) {
+        double *row = A + (int64_t)i * (i + 1) / 2;
+        if (i < nn) {
+            const double ai = ca[i], bi = cb[i];
+            for (int k = lane; k <= i; k += 32) {
+                double v;
+                if (k == i) {
+                    v = 1.0 + nug;
+                } else {
+                    const double da = ai - ca[k], db = bi - cb[k];
+                    v = rho_table(tw, fma(da, da, db * db), kap, logc, elo, ehi);
+                }
+                row[k] = v;
+            }
+        } else {
+            const double *br = Bt + (int64_t)(i - nn) * n_pad;
+            for (int k = lane; k <= i; k += 32) row[k] = k < nn ? br[k] : 0.0;
+        }
+    }
+    if (tid == 0) s_fail = 0;
+    __syncthreads();
+    // Right-looking Cholesky of the first n columns, two per step: warp 0
+    // factors columns j and j + 1 (pivot, scale, column j applied to column
+    // j + 1, pivot, scale) while the block waits, then every warp applies both
+    // columns to the rows and columns beyond them (each entry's two updates in
+    // column order, as a column-by-column factorisation would).  FP64 issues
+    // at 0.5 DFMA per clock per SM sub-partition here, so a look-ahead (warp 0
+    // factoring the next pair beside the others' update) gains nothing: its
+    // dependent chain waits behind its partner warp's FMAs (measured slower).
+    auto col = [&](int r, int c) -> double & { return A[(int64_t)r * (r + 1) / 2 + c]; };
+    for (int j = 0; j < nn; j += 2) {
+        const bool two = j + 1 < nn;
+        if (warp == 0) {
+            bool bad = false;
+            for (int c = j; c <= (two ? j + 1 : j) && !bad; ++c) {
+                if (c > j) {
+                    // column j applied to column j + 1 (rows j + 1 ..): needs L_{j+1,j}
+                    __syncwarp();
+                    const double l1 = col(j + 1, j);
+                    for (int i = j + 1 + lane; i < R; i += 32) col(i, j + 1) = fma(-col(i, j), l1, col(i, j + 1));
+                    __syncwarp();
+                }
+                const double d = col(c, c);
+                const bool ok = d > 0.0;
+                // 1 / sqrt(d): FP32 estimate and two Newton steps in FP64 (from
+                // ~2^-23 to full precision), or FP64 sqrt and division where d
+                // is outside the FP32 range
+                double r = 0.0;
+                if (ok && d > 1e-30 && d < 1e30) {
+                    r = (double)rsqrtf((float)d);
+                    r = r * fma(-0.5 * d, r * r, 1.5);
+                    r = r * fma(-0.5 * d, r * r, 1.5);
+                } else if (ok) {
+                    r = 1.0 / sqrt(d);
+                }
+                __syncwarp();
+                if (lane == 0) {
+                    piv[c] = d;
+                    if (ok) col(c, c) = d * r;
+                    else s_fail = 1;
+                }
+                bad = !ok;
+                if (ok)
+                    for (int i = c + 1 + lane; i < R; i += 32) col(i, c) *= r;
+            }
+        }
+        __syncthreads();
+        if (s_fail) break;
+        const int k0 = two ? j + 2 : j + 1;
+        for (int i = k0 + warp; i < R; i += nw) {
+            double *row = A + (int64_t)i * (i + 1) / 2;
+            const double a0 = row[j];
+            if (two) {
+                const double a1 = row[j + 1];
+                for (int k = k0 + lane; k <= i; k += 32) {
+                    const double *rk = A + (int64_t)k * (k + 1) / 2 + j;
+                    row[k] = fma(-a1, rk[1], fma(-a0, rk[0], row[k]));
+                }
+            } else {
+                for (int k = k0 + lane; k <= i; k += 32) row[k] = fma(-a0, col(k, j), row[k]);
+            }
+        }
+        __syncthreads();
+    }
+    if (s_fail) {
+        if (tid == 0) pstatus[w] = PLK_POINT_NOT_PD;
+        return;
+    }
+    double ls = 0.0;
+    for (int j = tid; j < nn; j += FUSED_THREADS) ls += log(piv[j]);
+    for (int o = 16; o > 0; o >>= 1) ls += __shfl_xor_sync(0xffffffffu, ls, o);
+    if (lane == 0) red[warp] = ls;
+    // -B^T V^-1 B into the last diagonal tile, lower triangle
+    double *S = tiles + ((int64_t)w * tpo + tile_index(nb, nb)) * NT;
+    for (int e = tid; e < q * q; e += FUSED_THREADS) {
+        const int a = e / q, c = e - a * q;
+        if (c <= a) S[a * TB + c] = A[(int64_t)(nn + a) * (nn + a + 1) / 2 + nn + c];
+    }
+    __syncthreads();
+    if (tid == 0) {
+        double t = 0.0;
+        for (int k = 0; k < nw; ++k) t += red[k];
+        ldv[w] = t;
+    }
+}
+
+// The same fused evaluation in double-float FP32 arithmetic (two floats per
+// value, ~2^-44 per operation; FP32 issues at ~68x the FP64 rate here), for
+// the mixed precision: V from the first pass's double-float build of each
+// entry (rho_entry_df on the double-float table), the Cholesky of the
+// bordered matrix in double-float, log|V| and sum 1/d_j of the pivots in FP64.
+// A point whose a-posteriori bound FUSED_DF_EPS (1 + nu^2) sum 1/d_j exceeds
+// the tolerance, or whose factorisation fails, is evaluated again by
+// k_fused_small in FP64.
+__device__ __forceinline__ void df_mul_f(float ah, float al, float bh, float bl, float &ph, float &pl) {
+    const float p = __fmul_rn(ah, bh);
+    float e = __fmaf_rn(ah, bh, -p);
+    e = __fmaf_rn(ah, bl, e);
+    e = __fmaf_rn(al, bh, e);
+    fast_two_sum_f(p, e, ph, pl);
+}
+// a - x0 y0 - x1 y1 (x1 = y1 = 0 for one product), normalised
+__device__ __forceinline__ float2 df_sub2(float2 a, float2 x0, float2 y0, float2 x1, float2 y1) {
+    const float p0 = __fmul_rn(x0.x, y0.x), p1 = __fmul_rn(x1.x, y1.x);
+    float e0 = __fmaf_rn(x0.x, y0.x, -p0), e1 = __fmaf_rn(x1.x, y1.x, -p1);
+    e0 = __fmaf_rn(x0.x, y0.y, __fmaf_rn(x0.y, y0.x, e0));
+    e1 = __fmaf_rn(x1.x, y1.y, __fmaf_rn(x1.y, y1.x, e1));
+    float s, t, s2, t2;
+    two_sum_f(a.x, -p0, s, t);
+    two_sum_f(s, -p1, s2, t2);
+    const float lo = __fadd_rn(__fsub_rn(__fsub_rn(a.y, e0), e1), __fadd_rn(t, t2));
+    float h, l;
+    fast_two_sum_f(s2, lo, h, l);
+    return make_float2(h, l);
+}
+
+__global__ void __launch_bounds__(FUSED_THREADS, 1) k_fused_small_df(int64_t n, int64_t n_pad, int q, int nb,
+                                                                     int64_t tpo, double *__restrict__ tiles,
+                                                                     const double *__restrict__ oconst,
+                                                                     const double *__restrict__ coordT,
+                                                                     const double *__restrict__ tab,
+                                                                     const double *__restrict__ Bt,
+                                                                     const int *__restrict__ owner,
+                                                                     double *__restrict__ ldv, int *__restrict__ pstatus,
+                                                                     double *__restrict__ invsum) {
+    extern __shared__ float2 Af[];
+    const int w = blockIdx.x;
+    const int R = (int)n + q, nn = (int)n;
+    const int64_t P = (int64_t)R * (R + 1) / 2;
+    float2 *pv = Af + P;   // the n pivots
+    __shared__ int s_fail;
+    __shared__ double red[FUSED_THREADS / 32], red2[FUSED_THREADS / 32];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = FUSED_THREADS / 32;
+    if (pstatus[w] != PLK_POINT_OK) {   // invalid parameters: the closed form writes NaN
+        if (tid == 0) invsum[w] = 0.0;
+        return;
+    }
+    const double *oc = oconst + OC_N * (int64_t)w;
+    const double nug = oc[OC_NUG], kap = oc[OC_KAPPA], logc = oc[OC_LOGC];
+    const int ow = owner ? owner[w] : w;
+    const int elo = (int)oconst[OC_N * (int64_t)ow + OC_ELO], ehi = (int)oconst[OC_N * (int64_t)ow + OC_EHI];
+    const float *cf = reinterpret_cast<const float *>(coordT + (int64_t)w * 2 * n_pad);
+    const float *tf = reinterpret_cast<const float *>(tab + (int64_t)ow * TAB_SIZE);
+    float dgh, dgl;   // 1 + nu^2
+    split_df_bits(1.0 + nug, dgh, dgl);
+    auto at = [&](int r, int c) -> float2 & { return Af[(int64_t)r * (r + 1) / 2 + c]; };
+    for (int i = warp; i < R; i += nw) {
+        float2 *row = Af + (int64_t)i * (i + 1) / 2;
+        if (i < nn) {
+            const float aih = cf[i], ail = cf[n_pad + i], bih = cf[2 * n_pad + i], bil = cf[3 * n_pad + i];
+            for (int k = lane; k <= i; k += 32) {
+                float vh = dgh, vl = dgl;
+                if (k != i)
+                    rho_entry_df(aih, ail, bih, bil, cf[k], cf[n_pad + k], cf[2 * n_pad + k], cf[3 * n_pad + k], tf,
+                                 elo, ehi, kap, logc, vh, vl);
+                row[k] = make_float2(vh, vl);
+            }
+        } else {
+            const double *br = Bt + (int64_t)(i - nn) * n_pad;
+            for (int k = lane; k <= i; k += 32) {
+                float h, l;
+                split_df_bits(k < nn ? br[k] : 0.0, h, l);
+                row[k] = make_float2(h, l);
+            }
+        }
+    }
+    if (tid == 0) s_fail = 0;
+    __syncthreads();
+    const float2 z = make_float2(0.0f, 0.0f);
+    // two columns per step, as in k_fused_small
+    for (int j = 0; j < nn; j += 2) {
+        const bool two = j + 1 < nn;
+        if (warp == 0) {
+            bool bad = false;
+            for (int c = j; c <= (two ? j + 1 : j) && !bad; ++c) {
+                if (c > j) {
+                    __syncwarp();
+                    const float2 l1 = at(j + 1, j);
+                    for (int i = j + 1 + lane; i < R; i += 32) at(i, j + 1) = df_sub2(at(i, j + 1), at(i, j), l1, z, z);
+                    __syncwarp();
+                }
+                const float2 d = at(c, c);
+                const bool ok = d.x > 0.0f && d.x < INFINITY;
+                // y = 1 / sqrt(d): FP32 estimate y0, one Newton step with the
+                // residual 1 - d y0^2 formed in double-float (~2^-46)
+                float yh = 0.0f, yl = 0.0f;
+                if (ok) {
+                    const float y0 = rsqrtf(d.x);
+                    const float th = __fmul_rn(y0, y0), tl = __fmaf_rn(y0, y0, -th);
+                    const float uh = __fmul_rn(d.x, th);
+                    float ue = __fmaf_rn(d.x, th, -uh);
+                    ue = __fmaf_rn(d.x, tl, __fmaf_rn(d.y, th, ue));
+                    const float res = __fsub_rn(__fsub_rn(1.0f, uh), ue);
+                    fast_two_sum_f(y0, __fmul_rn(0.5f * y0, res), yh, yl);
+                }
+                __syncwarp();
+                if (lane == 0) {
+                    pv[c] = d;
+                    if (ok) {
+                        float lh, ll;
+                        df_mul_f(d.x, d.y, yh, yl, lh, ll);
+                        at(c, c) = make_float2(lh, ll);
+                    } else {
+                        s_fail = 1;
+                    }
+                }
+                bad = !ok;
+                if (ok)
+                    for (int i = c + 1 + lane; i < R; i += 32) {
+                        float2 &v = at(i, c);
+                        float h, l;
+                        df_mul_f(v.x, v.y, yh, yl, h, l);
+                        v = make_float2(h, l);
+                    }
+            }
+        }
+        __syncthreads();
+        if (s_fail) break;
+        const int k0 = two ? j + 2 : j + 1;
+        for (int i = k0 + warp; i < R; i += nw) {
+            float2 *row = Af + (int64_t)i * (i + 1) / 2;
+            const float2 a0 = row[j], a1 = two ? row[j + 1] : z;
+            for (int k = k0 + lane; k <= i; k += 32) {
+                const float2 *rk = Af + (int64_t)k * (k + 1) / 2 + j;
+                row[k] = df_sub2(row[k], a0, rk[0], a1, two ? rk[1] : z);
+            }
+        }
+        __syncthreads();
+    }
+    if (s_fail) {
+        if (tid == 0) {
+            pstatus[w] = PLK_POINT_NOT_PD;
+            invsum[w] = 0.0;
+        }
+        return;
+    }
+    double ls = 0.0, is = 0.0;
+    for (int j = tid; j < nn; j += FUSED_THREADS) {
+        const double d = (double)pv[j].x + (double)pv[j].y;
+        ls += log(d);
+        is += 1.0 / d;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        ls += __shfl_xor_sync(0xffffffffu, ls, o);
+        is += __shfl_xor_sync(0xffffffffu, is, o);
+    }
+    if (lane == 0) {
+        red[warp] = ls;
+        red2[warp] = is;
+    }
+    double *S = tiles + ((int64_t)w * tpo + tile_index(nb, nb)) * NT;
+    for (int e = tid; e < q * q; e += FUSED_THREADS) {
+        const int a = e / q, c = e - a * q;
+        if (c <= a) {
+            const float2 v = at(nn + a, nn + c);
+            S[a * TB + c] = (double)v.x + (double)v.y;
+        }
+    }
+    __syncthreads();
+    if (tid == 0) {
+        double t = 0.0, t2 = 0.0;
+        for (int k = 0; k < nw; ++k) {
+            t += red[k];
+            t2 += red2[k];
+        }
+        ldv[w] = t;
+        invsum[w] = t2;
+    }
+}
+
+cudaError_t launch_fused_df_batch(const BatchArgs &b, double *invsum, cudaStream_t s) {
+    const size_t smem = fused_smem_bytes(b.n, b.q);
+    cudaError_t e = cudaFuncSetAttribute(k_fused_small_df, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    KernelTimer *timer = b.timer;
+    if ((e = launch_front(b, s, FRONT_DF_FAST, false)) != cudaSuccess) return e;
+    TIMED(KC_FUSED, (k_fused_small_df<<<b.count, FUSED_THREADS, smem, s>>>(b.n, b.n_pad, b.q, b.nb, b.tpo, b.tiles,
+                                                                          b.oconst, b.coordT, b.tab, b.Bt, b.owner,
+                                                                          b.ldv, b.pstatus, invsum)));
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    return launch_finalize(b, s);
+}
+
+size_t fused_smem_bytes(int64_t n, int q) {
+    const int64_t R = n + q;
+    return sizeof(double) * (size_t)(R * (R + 1) / 2 + n);
+}
+
+bool fused_applies(int64_t n, int q) { return n + q <= FUSED_MAX_R; }
+
+cudaError_t launch_fused_batch(const BatchArgs &b, cudaStream_t s) {
+    const size_t smem = fused_smem_bytes(b.n, b.q);
+    cudaError_t e = cudaFuncSetAttribute(k_fused_small, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    KernelTimer *timer = b.timer;
+    if ((e = launch_front(b, s, FRONT_FP64, false)) != cudaSuccess) return e;
+    TIMED(KC_FUSED, (k_fused_small<<<b.count, FUSED_THREADS, smem, s>>>(b.n, b.n_pad, b.q, b.nb, b.tpo, b.tiles,
+                                                                       b.oconst, b.coordT, b.tab, b.Bt, b.owner,
+                                                                       b.ldv, b.pstatus)));
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    return launch_finalize(b, s);
 }
 
 // ---------------------------------------------------------------------------

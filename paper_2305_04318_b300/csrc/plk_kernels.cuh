@@ -7,7 +7,7 @@ namespace plk {
 
 // Kernel classes for the optional per-launch event timing.
 enum KernelClass { KC_BOXCOX = 0, KC_PREP, KC_TABLE, KC_BUILD, KC_POTRF, KC_TRSM, KC_GEMM, KC_FINAL,
-                   KC_PROFILE, KC_CONVERT, KC_POTRF_MIXED, KC_TRSM_SPLIT, KC_GEMM_SPLIT, KC_TRSM_SPLIT7, KC_GEMM_SPLIT7, KC_COUNT };
+                   KC_PROFILE, KC_CONVERT, KC_POTRF_MIXED, KC_TRSM_SPLIT, KC_GEMM_SPLIT, KC_TRSM_SPLIT7, KC_GEMM_SPLIT7, KC_FUSED, KC_COUNT };
 const char *kernel_class_name(int c);
 
 // Records a CUDA event pair around a launch on its stream (see plk_api.cu).
@@ -59,7 +59,23 @@ cudaError_t launch_fp64_batch(const BatchArgs &b, cudaStream_t s);
 // mixed path's 7-slice tier); double-float planes evaluated in FP32 pair
 // arithmetic (the mixed path's 5-slice pass)
 enum FrontMode { FRONT_FP64 = 0, FRONT_DF = 1, FRONT_DF_FAST = 2 };
-cudaError_t launch_front(const BatchArgs &b, cudaStream_t s, FrontMode mode);
+cudaError_t launch_front(const BatchArgs &b, cudaStream_t s, FrontMode mode, bool build = true);
+// Small datasets (n + q <= FUSED_MAX_R): the whole point in one CTA (build,
+// FP64 Cholesky of the bordered matrix, closed form), in either precision
+constexpr int FUSED_MAX_R = 224;
+bool fused_applies(int64_t n, int q);
+size_t fused_smem_bytes(int64_t n, int q);
+cudaError_t launch_fused_batch(const BatchArgs &b, cudaStream_t s);
+// the same in double-float FP32 (mixed precision); invsum[w] = sum_j 1/d_j of
+// the pivots (for the a-posteriori bound), 0 for points that failed
+cudaError_t launch_fused_df_batch(const BatchArgs &b, double *invsum, cudaStream_t s);
+// relative perturbation of V's entries in the double-float fused Cholesky
+// (bound E = FUSED_DF_EPS (1 + nu^2) sum_j 1 / d_j)
+constexpr double FUSED_DF_EPS = 1.4551915228366852e-11;   // 2^-36
+// flags[w] = 1 where the bound exceeds tol or (flag_not_pd) the point is not
+// positive definite; err_bound[k] = the bound
+cudaError_t launch_mixed_bound(const BatchArgs &b, double eps, double tol, int flag_not_pd, const double *invsum,
+                               double *err_bound, int *flags, cudaStream_t s);
 cudaError_t launch_finalize(const BatchArgs &b, cudaStream_t s);
 // smallest squared site distance into *min_dist2, the front in `mode`, then
 // the dense n x n matrices V of the batch into V (count x n x n)

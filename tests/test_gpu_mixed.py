@@ -45,11 +45,15 @@ def mixed_compare(g, o, what, atol=ATOL_LOGL, coords=None, params=None, max_disa
 
 
 def test_mixed_iso100():
+    """n = 100: the default (fused FP64 kernel) and the tiled split-product
+    path (PLK_FLAG_NO_FUSED) against the oracle."""
     w = synth.iso100()
     ds, P = w.datasets[0], w.params[0]
     o = oracle_eval(ds, P, w.lambdas)
     g = gpu_eval(ds, P, w.lambdas, precision=nv.MIXED)
-    mixed_compare(g, o, "iso100", coords=ds.coords, params=P, max_disagree=2)
+    mixed_compare(g, o, "iso100 fused", coords=ds.coords, params=P, max_disagree=0)
+    g = gpu_eval(ds, P, w.lambdas, precision=nv.MIXED, flags=nv.FLAG_NO_FUSED)
+    mixed_compare(g, o, "iso100 tiled", coords=ds.coords, params=P, max_disagree=2)
     _bound_margin(ds, P, w.lambdas, o, "iso100")
 
 
@@ -62,7 +66,7 @@ BOUND_RATIO = 0.5
 
 def _bound_margin(ds, P, lams, o, what, g5=None):
     if g5 is None:
-        g5 = gpu_eval(ds, P, lams, precision=nv.MIXED, flags=nv.FLAG_NO_RETRY)
+        g5 = gpu_eval(ds, P, lams, precision=nv.MIXED, flags=nv.FLAG_NO_RETRY | nv.FLAG_NO_FUSED)
     ok = (g5["status"] == 0) & (o["status"] == 0)
     err = np.max(np.abs(g5["logL"] - o["logL"]), axis=1)[ok]
     eb = g5["err_bound"][ok]
@@ -87,8 +91,9 @@ def test_mixed_ragged(n, p, M):
     P = synth.omega_from_unit(np.random.default_rng(n).uniform(size=(7, 5)))
     lams = np.linspace(-0.5, 1.5, M)
     o = oracle_eval(ds, P, lams)
-    g = gpu_eval(ds, P, lams, precision=nv.MIXED, batch=3)
-    mixed_compare(g, o, f"n={n}", coords=ds.coords, params=P)
+    for flags in (0, nv.FLAG_NO_FUSED):
+        g = gpu_eval(ds, P, lams, precision=nv.MIXED, batch=3, flags=flags)
+        mixed_compare(g, o, f"n={n} flags={flags}", coords=ds.coords, params=P)
 
 
 def test_mixed_error_bound_covers_five_slice_error():
