@@ -260,22 +260,22 @@ static void sub_batch(const BatchArgs &b, const MixedArgs &x, int off, int cnt, 
     xo.flags = x.flags + off;
 }
 
-// Two streams of the calling thread on the current device, created on first
-// use and kept for the thread's lifetime: [0] at the highest priority (the
-// factorisation), [1] at the lowest (the overlapped build).  With the build on
-// the low-priority stream, the block scheduler hands freed SM resources to the
-// factorisation kernels first.
+// Streams of the calling thread on the current device, created on first use
+// and kept for the thread's lifetime: hi at the highest priority (the
+// factorisation), lo at the lowest (the overlapped build), re at the lowest
+// (the 7-slice re-evaluation of finished parts), cp for reading flags back.
+// With the build and the re-evaluation on low-priority streams, the block
+// scheduler hands freed SM resources to the factorisation kernels first.
 struct AuxStreams {
-    cudaStream_t hi = nullptr, lo = nullptr;
+    cudaStream_t hi = nullptr, lo = nullptr, re = nullptr, cp = nullptr;
 };
 static AuxStreams aux_streams() {
     struct Table {
         std::map<int, AuxStreams> m;
         ~Table() {
-            for (auto &kv : m) {
-                cudaStreamDestroy(kv.second.hi);
-                cudaStreamDestroy(kv.second.lo);
-            }
+            for (auto &kv : m)
+                for (cudaStream_t x : {kv.second.hi, kv.second.lo, kv.second.re, kv.second.cp})
+                    if (x) cudaStreamDestroy(x);
         }
     };
     thread_local Table t;
@@ -285,11 +285,14 @@ static AuxStreams aux_streams() {
     if (it != t.m.end()) return it->second;
     int least = 0, greatest = 0;
     AuxStreams st;
-    if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess ||
-        cudaStreamCreateWithPriority(&st.hi, cudaStreamNonBlocking, greatest) != cudaSuccess)
-        return {};
-    if (cudaStreamCreateWithPriority(&st.lo, cudaStreamNonBlocking, least) != cudaSuccess) {
-        cudaStreamDestroy(st.hi);
+    if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess) return {};
+    const bool ok = cudaStreamCreateWithPriority(&st.hi, cudaStreamNonBlocking, greatest) == cudaSuccess &&
+                    cudaStreamCreateWithPriority(&st.lo, cudaStreamNonBlocking, least) == cudaSuccess &&
+                    cudaStreamCreateWithPriority(&st.re, cudaStreamNonBlocking, least) == cudaSuccess &&
+                    cudaStreamCreateWithFlags(&st.cp, cudaStreamNonBlocking) == cudaSuccess;
+    if (!ok) {
+        for (cudaStream_t x : {st.hi, st.lo, st.re, st.cp})
+            if (x) cudaStreamDestroy(x);
         return {};
     }
     t.m[dev] = st;
@@ -350,11 +353,17 @@ static bool use_fused(int64_t n, int q, int flags) { return fused_applies(n, q) 
 // the earlier parts (tensor cores) on a high-priority stream, so only the first
 // part's build is exposed.  The work is forked from `s` onto the two internal
 // streams and joined back into `s`.
-static cudaError_t mixed_first_pass(const BatchArgs &b, const MixedArgs &x, bool overlap, cudaStream_t s) {
-    constexpr int kOverlapMin = 256, kPart = PLK_MIXED_PART;
+constexpr int kOverlapMin = 256, kPart = PLK_MIXED_PART;
+static int first_pass_parts(int count) { return std::max(2, (count + kPart - 1) / kPart); }
+
+// part_done (optional): one event per part, recorded on the factorisation
+// stream when that part's pass (closed form and error bound included) is done;
+// the caller destroys them.
+static cudaError_t mixed_first_pass(const BatchArgs &b, const MixedArgs &x, bool overlap, cudaStream_t s,
+                                    std::vector<cudaEvent_t> *part_done = nullptr) {
     const AuxStreams st = overlap && b.count >= kOverlapMin ? aux_streams() : AuxStreams{};
     if (!st.hi) return launch_mixed_batch(b, x, 5, s);
-    const int nparts = std::max(2, (b.count + kPart - 1) / kPart);
+    const int nparts = first_pass_parts(b.count);
     std::vector<cudaEvent_t> ev(nparts + 2, nullptr);   // [0] fork, [1 + p] front of part p done, [nparts + 1] join
     cudaError_t e = cudaSuccess;
     for (size_t i = 0; i < ev.size() && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming);
@@ -381,6 +390,12 @@ static cudaError_t mixed_first_pass(const BatchArgs &b, const MixedArgs &x, bool
         part(p, bp, xp);
         if (p > 0) e = cudaStreamWaitEvent(st.hi, ev[1 + p], 0);
         if (e == cudaSuccess) e = launch_mixed_back(bp, xp, 5, st.hi);
+        if (e == cudaSuccess && part_done) {
+            cudaEvent_t d = nullptr;
+            e = cudaEventCreateWithFlags(&d, cudaEventDisableTiming);
+            if (e == cudaSuccess) part_done->push_back(d);
+            if (e == cudaSuccess) e = cudaEventRecord(d, st.hi);
+        }
     }
     if (forked) {   // join, also after a failed launch: nothing may run on past `s`
         cudaEventRecord(ev[nparts], st.lo);
@@ -392,6 +407,116 @@ static cudaError_t mixed_first_pass(const BatchArgs &b, const MixedArgs &x, bool
     for (auto &v : ev)
         if (v) cudaEventDestroy(v);   // released once the recorded work completes
     return e;
+}
+
+// FP64 tier: the points idx (global indices) re-evaluated in FP64, in slots
+// 0 .. of the batch workspace (every earlier pass of the batch has finished).
+static plk_status fp64_tier(const BatchArgs &b, const Layout &L, void *ws, const double *params_all,
+                            double *err_bound, const std::vector<int> &idx2, cudaStream_t s) {
+    if (idx2.empty()) return PLK_OK;
+    int *d_idx = at<int>(ws, L.off_idx);
+    double *d_par = at<double>(ws, L.off_cparams);
+    cudaError_t e = cudaMemcpyAsync(d_idx, idx2.data(), sizeof(int) * idx2.size(), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = launch_gather_params((int)idx2.size(), d_idx, params_all, d_par, s);
+    if (e != cudaSuccess) return cuda_fail(e, "fp64 retry gather");
+    BatchArgs f = b;
+    f.count = (int)idx2.size();
+    f.params = d_par;
+    f.out_index = d_idx;
+    f.status_or = PLK_POINT_RETRIED | PLK_POINT_FP64;
+    e = launch_fp64_batch(f, s);
+    if (e == cudaSuccess && err_bound) e = launch_scatter_value(f.count, d_idx, 0.0, err_bound, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);   // idx2 must outlive its copy
+    if (e != cudaSuccess) return cuda_fail(e, "fp64 retry");
+    return PLK_OK;
+}
+
+// The 5-slice pass in parts (mixed_first_pass) with the 7-slice tier
+// pipelined behind it: as soon as a part is done, its flags are read back and
+// its points bound for 7 slices are re-evaluated on the low-priority stream,
+// in that part's own workspace slots, while the later parts' passes run on
+// the high-priority stream (the re-evaluation fills the SMs their
+// latency-bound diagonal-tile and panel kernels leave idle).  The FP64 tier,
+// if any point needs it, follows once everything else is done.  Results are
+// those of the sequential order: every point's arithmetic depends only on its
+// own data.
+static plk_status run_mixed_pipelined(const BatchArgs &b, const Layout &L, void *ws, const MixedArgs &x,
+                                      const double *params_all, int flags, double *err_bound, cudaStream_t s) {
+    const AuxStreams st = aux_streams();
+    const int nparts = first_pass_parts(b.count);
+    std::vector<cudaEvent_t> done;
+    cudaEvent_t joined = nullptr;
+    auto cleanup = [&]() {
+        for (cudaEvent_t ev : done) cudaEventDestroy(ev);
+        if (joined) cudaEventDestroy(joined);
+    };
+    cudaError_t e = cudaMemsetAsync(x.err, 0, sizeof(int), s);
+    if (e == cudaSuccess) e = mixed_first_pass(b, x, true, s, &done);
+    if (e == cudaSuccess && (int)done.size() != nparts) e = cudaErrorInvalidValue;
+    if (e != cudaSuccess) {
+        cleanup();
+        return cuda_fail(e, "mixed batch launch");
+    }
+    int *d_idx = at<int>(ws, L.off_idx);
+    double *d_par = at<double>(ws, L.off_cparams);
+    std::vector<std::vector<int>> idx(nparts);   // kept until the copies from them are done
+    std::vector<int> h;
+    int dev_err = 0;
+    bool retried = false;
+    for (int p = 0; p < nparts && e == cudaSuccess; ++p) {
+        const int lo = (int)((int64_t)b.count * p / nparts), cnt = (int)((int64_t)b.count * (p + 1) / nparts) - lo;
+        h.assign(cnt + 1, 0);
+        e = cudaStreamWaitEvent(st.cp, done[p], 0);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(h.data(), x.flags + lo, sizeof(int) * cnt, cudaMemcpyDeviceToHost, st.cp);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(h.data() + cnt, x.err, sizeof(int), cudaMemcpyDeviceToHost, st.cp);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st.cp);   // waits for part p only
+        if (e != cudaSuccess) break;
+        if (h[cnt]) dev_err = 1;
+        for (int w = 0; w < cnt; ++w)
+            if (h[w]) idx[p].push_back((int)(b.k0 + lo + w));
+        if (idx[p].empty() || dev_err) continue;
+        BatchArgs r;
+        MixedArgs xr;
+        sub_batch(b, x, lo, (int)idx[p].size(), r, xr);
+        r.params = d_par + 5 * (size_t)lo;
+        r.out_index = d_idx + lo;
+        r.status_or = PLK_POINT_RETRIED;
+        e = cudaStreamWaitEvent(st.re, done[p], 0);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(d_idx + lo, idx[p].data(), sizeof(int) * idx[p].size(), cudaMemcpyHostToDevice, st.re);
+        if (e == cudaSuccess) e = launch_gather_params(r.count, d_idx + lo, params_all, d_par + 5 * (size_t)lo, st.re);
+        if (e == cudaSuccess) e = launch_mixed_batch(r, xr, 7, st.re);
+        retried = true;
+    }
+    // join the re-evaluation back into s, also after a failed launch
+    cudaError_t j = cudaEventCreateWithFlags(&joined, cudaEventDisableTiming);
+    if (j == cudaSuccess) j = cudaEventRecord(joined, st.re);
+    if (j == cudaSuccess) j = cudaStreamWaitEvent(s, joined, 0);
+    if (e == cudaSuccess) e = j;
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        cleanup();
+        return cuda_fail(e, "mixed batch");
+    }
+    std::vector<int> idx2;
+    if (retried && !dev_err) {
+        for (int p = 0; p < nparts && e == cudaSuccess; ++p) {
+            if (idx[p].empty()) continue;
+            const int lo = (int)((int64_t)b.count * p / nparts), m = (int)idx[p].size();
+            h.assign(m + 1, 0);
+            e = cudaMemcpyAsync(h.data(), x.flags + lo, sizeof(int) * m, cudaMemcpyDeviceToHost, st.cp);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(h.data() + m, x.err, sizeof(int), cudaMemcpyDeviceToHost, st.cp);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st.cp);
+            if (e == cudaSuccess && h[m]) dev_err = 1;
+            if (!(flags & PLK_FLAG_NO_FP64_TIER))
+                for (int w = 0; w < m; ++w)
+                    if (h[w]) idx2.push_back(idx[p][w]);
+        }
+    }
+    cleanup();
+    if (e != cudaSuccess) return cuda_fail(e, "mixed retry");
+    if (dev_err) return fail(PLK_E_TIMEOUT, "a tensor-core wait gave up (device error flag set)");
+    return fp64_tier(b, L, ws, params_all, err_bound, idx2, s);
 }
 
 static plk_status run_mixed_batch(BatchArgs b, const Layout &L, void *ws, const double *params_all, int flags,
@@ -406,6 +531,9 @@ static plk_status run_mixed_batch(BatchArgs b, const Layout &L, void *ws, const 
     x.tol = kMixedTol;
     // without the retry the caller gets every point's 5-slice result
     x.early = (flags & (PLK_FLAG_NO_RETRY | PLK_FLAG_FULL_FIRST_PASS)) ? 0 : 1;
+    if ((flags & PLK_FLAG_PIPELINED_RETRY) && overlap && b.count >= kOverlapMin && !use_graph(flags) &&
+        !(flags & PLK_FLAG_NO_RETRY) && aux_streams().re)
+        return run_mixed_pipelined(b, L, ws, x, params_all, flags, err_bound, s);
     auto first = [&]() {
         cudaError_t r = cudaMemsetAsync(x.err, 0, sizeof(int), s);
         return r == cudaSuccess ? mixed_first_pass(b, x, overlap, s) : r;

@@ -85,9 +85,17 @@ __global__ void __launch_bounds__(256) k_omega_prep(const double *__restrict__ p
     const bool ok = (phix > 0.0) && (kap > 0.0) && (nug >= 0.0) && (ratio > 0.0) &&
                     isfinite(phix) && isfinite(kap) && isfinite(nug) && isfinite(ratio) &&
                     isfinite(ang);
-    const double c = cos(ang), s = sin(ang);
-    const double s8k = sqrt(8.0 * kap);
-    const double ia = s8k / phix, ib = s8k * ratio / phix;
+    // the point's transcendentals once per block (FP64 issues at 1/68 of FP32)
+    __shared__ double sc[5];
+    if (threadIdx.x == 0) {
+        sc[0] = cos(ang);
+        sc[1] = sin(ang);
+        sc[2] = sqrt(8.0 * kap);
+        sc[3] = sc[2] / phix;
+        sc[4] = sc[2] * ratio / phix;
+    }
+    __syncthreads();
+    const double c = sc[0], s = sc[1], s8k = sc[2], ia = sc[3], ib = sc[4];
     if (threadIdx.x == 0) {
         double *oc = oconst + OC_N * (int64_t)w;
         oc[OC_KAPPA] = kap;
@@ -176,8 +184,9 @@ __global__ void __launch_bounds__(256) k_omega_prep(const double *__restrict__ p
 }
 
 // Smallest squared distance between two sites (min over i < j), into *out
-// (which holds a large positive value beforehand): one block per pair of
-// 128-site tiles, non-negative doubles compared through their bit patterns.
+// (which holds a large positive value beforehand): gridDim.y (1, 2, 4 or 8)
+// blocks per pair of 128-site tiles, non-negative doubles compared through
+// their bit patterns.
 __global__ void __launch_bounds__(256) k_min_dist2(int64_t n, const double *__restrict__ coords,
                                                    double *__restrict__ out) {
     const int t = blockIdx.x;
@@ -194,7 +203,9 @@ __global__ void __launch_bounds__(256) k_min_dist2(int64_t n, const double *__re
     }
     __syncthreads();
     double best = INFINITY;
-    for (int r = threadIdx.x; r < 128 * 128; r += blockDim.x) {
+    // gridDim.y blocks share the tile pair (few pairs: small n)
+    const int per = 128 * 128 / (int)gridDim.y, r0 = (int)blockIdx.y * per;
+    for (int r = r0 + threadIdx.x; r < r0 + per; r += blockDim.x) {
         const int64_t i = i0 + (r >> 7), j = j0 + (r & 127);
         if (i < n && j < i) {
             const double dx = coords[2 * i] - xj[r & 127], dy = coords[2 * i + 1] - yj[r & 127];
@@ -1238,6 +1249,12 @@ const char *kernel_class_name(int c) {
         if (timer) timer->end(cls, s);      \
     } while (0)
 
+// blocks per tile pair of k_min_dist2: enough pairs x splits to reach ~148 blocks
+static unsigned min_dist_split(int64_t nt) {
+    const int64_t pairs = nt * (nt + 1) / 2;
+    return pairs >= 148 ? 1u : pairs >= 74 ? 2u : pairs >= 37 ? 4u : 8u;
+}
+
 cudaError_t launch_boxcox(int64_t n, int64_t n_pad, int p, int M, const double *y, const double *X,
                           const double *coords, const double *lam, double *Bt, double *sumlogy, cudaStream_t s,
                           KernelTimer *timer) {
@@ -1249,7 +1266,8 @@ cudaError_t launch_boxcox(int64_t n, int64_t n_pad, int p, int M, const double *
     if (e != cudaSuccess) return e;
     TIMED(KC_BOXCOX, (k_boxcox_rows<<<blocks, 256, 0, s>>>(n, n_pad, p, M, y, X, lam, Bt),
                       k_sumlog<<<1, 1024, 0, s>>>(n, y, sumlogy),
-                      k_min_dist2<<<(unsigned)(nt * (nt + 1) / 2), 256, 0, s>>>(n, coords, sumlogy + 1)));
+                      k_min_dist2<<<dim3((unsigned)(nt * (nt + 1) / 2), min_dist_split(nt)), 256, 0, s>>>(
+                          n, coords, sumlogy + 1)));
     return cudaGetLastError();
 }
 
@@ -1264,7 +1282,10 @@ cudaError_t launch_front(const BatchArgs &b, cudaStream_t s, FrontMode mode, boo
         k_table_owner<<<cnt, 256, 0, s>>>(cnt, b.oconst, b.pstatus, b.owner);
         k_table_union<<<cnt, 256, 0, s>>>(cnt, b.oconst, b.owner);
     }
-    if (f32) {
+    if (f32 && !build) {   // the fused path: tables spread over more blocks
+        const dim3 tg8((TAB_NBUCKET + 7) / 8, cnt);
+        TIMED(KC_TABLE, (k_matern_table<true, 8><<<tg8, 8 * TAB_NC, 0, s>>>(b.oconst, b.tab, b.owner)));
+    } else if (f32) {
         TIMED(KC_TABLE, (k_matern_table<true><<<tg, 320, 0, s>>>(b.oconst, b.tab, b.owner)));
         if (build)
             TIMED(KC_BUILD, (k_build_f32<<<bg, 256, 0, s>>>(b.nb, b.n, b.n_pad, b.q, b.tpo, b.tiles, b.oconst,
@@ -1311,7 +1332,7 @@ cudaError_t launch_covariance(const BatchArgs &b, FrontMode mode, double *min_di
     const int64_t nt = (b.n + 127) / 128;
     cudaError_t e = cudaMemsetAsync(min_dist2, 0x7f, sizeof(double), s);   // 0x7f7f.. ~ 1.4e306
     if (e != cudaSuccess) return e;
-    k_min_dist2<<<(unsigned)(nt * (nt + 1) / 2), 256, 0, s>>>(b.n, b.coords, min_dist2);
+    k_min_dist2<<<dim3((unsigned)(nt * (nt + 1) / 2), min_dist_split(nt)), 256, 0, s>>>(b.n, b.coords, min_dist2);
     if ((e = launch_front(b, s, mode)) != cudaSuccess) return e;
     const unsigned data_tiles = (unsigned)((int64_t)b.nb * (b.nb + 1) / 2);
     k_tiles_to_dense<<<dim3(data_tiles, b.count), 256, 0, s>>>(b.nb, b.n, b.tpo, b.tiles, mode == FRONT_FP64 ? 0 : 1,
@@ -1372,7 +1393,8 @@ cudaError_t launch_profile_ci(const double *grid, const double *prof, int64_t G,
 // blocked path leaves it (the last diagonal tile of the point's tile array),
 // so the same closed-form kernel finishes the point.  log|V| is the sum of the
 // logs of the n pivots, reduced over the block.
-constexpr int FUSED_THREADS = 256;
+constexpr int FUSED_THREADS = 256;      // FP64 kernel (the FP64 pipe is the bound)
+constexpr int FUSED_DF_THREADS = 512;   // double-float kernel: more warps for its dependent FP32 chains
 
 __global__ void __launch_bounds__(FUSED_THREADS, 1) k_fused_small(int64_t n, int64_t n_pad, int q, int nb, int64_t tpo,
                                                                double *__restrict__ tiles,
@@ -1535,7 +1557,7 @@ __device__ __forceinline__ float2 df_sub2(float2 a, float2 x0, float2 y0, float2
     return make_float2(h, l);
 }
 
-__global__ void __launch_bounds__(FUSED_THREADS, 1) k_fused_small_df(int64_t n, int64_t n_pad, int q, int nb,
+__global__ void __launch_bounds__(FUSED_DF_THREADS, 1) k_fused_small_df(int64_t n, int64_t n_pad, int q, int nb,
                                                                      int64_t tpo, double *__restrict__ tiles,
                                                                      const double *__restrict__ oconst,
                                                                      const double *__restrict__ coordT,
@@ -1550,8 +1572,8 @@ __global__ void __launch_bounds__(FUSED_THREADS, 1) k_fused_small_df(int64_t n, 
     const int64_t P = (int64_t)R * (R + 1) / 2;
     float2 *pv = Af + P;   // the n pivots
     __shared__ int s_fail;
-    __shared__ double red[FUSED_THREADS / 32], red2[FUSED_THREADS / 32];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = FUSED_THREADS / 32;
+    __shared__ double red[FUSED_DF_THREADS / 32], red2[FUSED_DF_THREADS / 32];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = FUSED_DF_THREADS / 32;
     if (pstatus[w] != PLK_POINT_OK) {   // invalid parameters: the closed form writes NaN
         if (tid == 0) invsum[w] = 0.0;
         return;
@@ -1641,7 +1663,16 @@ __global__ void __launch_bounds__(FUSED_THREADS, 1) k_fused_small_df(int64_t n, 
         for (int i = k0 + warp; i < R; i += nw) {
             float2 *row = Af + (int64_t)i * (i + 1) / 2;
             const float2 a0 = row[j], a1 = two ? row[j + 1] : z;
-            for (int k = k0 + lane; k <= i; k += 32) {
+            int k = k0 + lane;
+            for (; k + 32 <= i; k += 64) {   // two independent entries per iteration
+                const float2 *rk = Af + (int64_t)k * (k + 1) / 2 + j;
+                const float2 *rk2 = Af + (int64_t)(k + 32) * (k + 33) / 2 + j;
+                const float2 u = df_sub2(row[k], a0, rk[0], a1, two ? rk[1] : z);
+                const float2 v = df_sub2(row[k + 32], a0, rk2[0], a1, two ? rk2[1] : z);
+                row[k] = u;
+                row[k + 32] = v;
+            }
+            if (k <= i) {
                 const float2 *rk = Af + (int64_t)k * (k + 1) / 2 + j;
                 row[k] = df_sub2(row[k], a0, rk[0], a1, two ? rk[1] : z);
             }
@@ -1656,7 +1687,7 @@ __global__ void __launch_bounds__(FUSED_THREADS, 1) k_fused_small_df(int64_t n, 
         return;
     }
     double ls = 0.0, is = 0.0;
-    for (int j = tid; j < nn; j += FUSED_THREADS) {
+    for (int j = tid; j < nn; j += FUSED_DF_THREADS) {
         const double d = (double)pv[j].x + (double)pv[j].y;
         ls += log(d);
         is += 1.0 / d;
@@ -1670,7 +1701,7 @@ __global__ void __launch_bounds__(FUSED_THREADS, 1) k_fused_small_df(int64_t n, 
         red2[warp] = is;
     }
     double *S = tiles + ((int64_t)w * tpo + tile_index(nb, nb)) * NT;
-    for (int e = tid; e < q * q; e += FUSED_THREADS) {
+    for (int e = tid; e < q * q; e += FUSED_DF_THREADS) {
         const int a = e / q, c = e - a * q;
         if (c <= a) {
             const float2 v = at(nn + a, nn + c);
@@ -1695,7 +1726,7 @@ cudaError_t launch_fused_df_batch(const BatchArgs &b, double *invsum, cudaStream
     if (e != cudaSuccess) return e;
     KernelTimer *timer = b.timer;
     if ((e = launch_front(b, s, FRONT_DF_FAST, false)) != cudaSuccess) return e;
-    TIMED(KC_FUSED, (k_fused_small_df<<<b.count, FUSED_THREADS, smem, s>>>(b.n, b.n_pad, b.q, b.nb, b.tpo, b.tiles,
+    TIMED(KC_FUSED, (k_fused_small_df<<<b.count, FUSED_DF_THREADS, smem, s>>>(b.n, b.n_pad, b.q, b.nb, b.tpo, b.tiles,
                                                                           b.oconst, b.coordT, b.tab, b.Bt, b.owner,
                                                                           b.ldv, b.pstatus, invsum)));
     if ((e = cudaGetLastError()) != cudaSuccess) return e;

@@ -218,9 +218,10 @@ __host__ __device__ constexpr size_t img_bytes() {
     return (size_t)S * 2 * SBLK + 1024;
 }
 
-// Panel slot of one tile row: two 5-slice images (panels J with J % 2 = 0, 1;
-// the two-panel trailing update needs both) or one 7-slice image.
-constexpr size_t SLOT = 2 * img_bytes<5>() > img_bytes<7>() ? 2 * img_bytes<5>() : img_bytes<7>();
+// Panel slot of one tile row: four 5-slice images (panels J with J % 4 = 0 .. 3;
+// the trailing update of the data triangle applies up to four panels at once)
+// or one 7-slice image.
+constexpr size_t SLOT = 4 * img_bytes<5>() > img_bytes<7>() ? 4 * img_bytes<5>() : img_bytes<7>();
 
 // Exponent shared by every row and panel of L (data rows): |L_rk| <= sqrt(V_rr)
 // = sqrt(1 + nu^2), with a margin for the rounding of the computed factor.
@@ -956,7 +957,7 @@ __global__ void __launch_bounds__(NTH, 1) k_trsm_split(int J, int nb, int64_t tp
         }
     }
     __syncthreads();
-    uint8_t *dst = pimg + ((int64_t)w * (nb + 1) + I) * SLOT + (size_t)(J & 1) * img_bytes<S>();
+    uint8_t *dst = pimg + ((int64_t)w * (nb + 1) + I) * SLOT + (size_t)(J & 3) * img_bytes<S>();
     if (ok) {
         const uint4 *src4 = reinterpret_cast<const uint4 *>(sbase);
         uint4 *dst4 = reinterpret_cast<uint4 *>(dst);
@@ -1008,11 +1009,15 @@ struct Cfg {
 }  // namespace pipe
 
 // Item sets: mode 0 = the triangle Klo <= K <= I <= Ihi; mode 1 = the column
-// K = Klo, Klo <= I <= Ihi; mode 2 = the row I = Ihi, Klo <= K <= Ihi.  Each
-// item applies the P (1 or 2) panels in sub-slots sub0, sub1; with P = 2 both
-// operands use the common exponent (data rows only; 5 slices only).
+// K = Klo, Klo <= I <= Ihi; mode 2 = the row I = Ihi, Klo <= K <= Ihi; mode 3 =
+// the columns Klo <= K <= Khi, K <= I <= Ihi.  Each item applies P (1 to 4)
+// consecutive panels, the p-th in sub-slot (sub0 + p) % 4; with P >= 2 both
+// operands use the common exponent (data rows only; 5 slices only).  The
+// FP32 accumulators of groups 0-2 stay exact up to K = 4 x 128: with every
+// data row of L bounded by sqrt(1 + nu^2) < 2^e (Cauchy-Schwarz over the
+// leading digits), group 2's sums stay below 2^23.2 units.
 template <int S>
-__global__ void __launch_bounds__(pipe::NTHP, 1) k_trail_pipe(int mode, int Klo, int Ihi, int P, int sub0, int sub1,
+__global__ void __launch_bounds__(pipe::NTHP, 1) k_trail_pipe(int mode, int Klo, int Khi, int Ihi, int P, int sub0,
                                                              int nb, int cnt, int64_t tpo,
                                                              const __grid_constant__ CUtensorMap tmapC,
                                                              const uint8_t *__restrict__ pimg,
@@ -1029,8 +1034,8 @@ __global__ void __launch_bounds__(pipe::NTHP, 1) k_trail_pipe(int mode, int Klo,
     __shared__ int s_err, s_stop;
     volatile int *verr = &s_err;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int m = Ihi - Klo + 1;
-    const int T = (mode == 0) ? m * (m + 1) / 2 : m;
+    const int m = Ihi - Klo + 1, nK = Khi - Klo + 1;
+    const int T = (mode == 0) ? m * (m + 1) / 2 : (mode == 3) ? nK * m - nK * (nK - 1) / 2 : m;
     const int64_t items = (int64_t)cnt * T * 2;
     if (tid == 0) {
         for (int i = 0; i < 2; ++i) {
@@ -1067,13 +1072,21 @@ __global__ void __launch_bounds__(pipe::NTHP, 1) k_trail_pipe(int mode, int Klo,
         } else if (mode == 1) {
             K = Klo;
             I = Klo + t;
-        } else {
+        } else if (mode == 2) {
             I = Ihi;
             K = Klo + t;
+        } else {
+            int r = t;
+            K = Klo;
+            while (r >= Ihi - K + 1) {
+                r -= Ihi - K + 1;
+                ++K;
+            }
+            I = K + r;
         }
     };
     auto image = [&](int w, int R, int p) {
-        return pimg + ((int64_t)w * (nb + 1) + R) * SLOT + (size_t)(p ? sub1 : sub0) * img_bytes<S>();
+        return pimg + ((int64_t)w * (nb + 1) + R) * SLOT + (size_t)((sub0 + p) & 3) * img_bytes<S>();
     };
 
     if (warp == 0) {
@@ -1154,17 +1167,31 @@ __global__ void __launch_bounds__(pipe::NTHP, 1) k_trail_pipe(int mode, int Klo,
                         for (int kk = 0; kk < 4; ++kk) {
                             const uint64_t ad = a0 + 2 * kk, bk = b0 + 2 * kk;
                             const uint32_t acc = (h == 0 && kk == 0 && i == 0) ? 0u : 1u;
+                            // Where one A slice feeds two MMAs, the first keeps it in
+                            // the tensor core's collector buffer and the second takes it
+                            // from there: A is read from shared memory once per K step.
                             if (S == 5) {
-                                if (i < 4) tc::mma_bf16(dacc + 64 * i, ad, bk, tc::idesc_bf16_f32(128, 64 * (4 - i)), acc);
-                                tc::mma_bf16(dacc + 3 * 64, ad, bk + (uint64_t)(((4 - i) * HBLK) >> 4), IDESC_N64, 1u);
+                                if (i < 4) {
+                                    tc::mma_bf16_ca<tc::Collector::FILL>(dacc + 64 * i, ad, bk,
+                                                                         tc::idesc_bf16_f32(128, 64 * (4 - i)), acc);
+                                    tc::mma_bf16_ca<tc::Collector::LASTUSE>(
+                                        dacc + 3 * 64, ad, bk + (uint64_t)(((4 - i) * HBLK) >> 4), IDESC_N64, 1u);
+                                } else {
+                                    tc::mma_bf16(dacc + 3 * 64, ad, bk + (uint64_t)(((4 - i) * HBLK) >> 4), IDESC_N64, 1u);
+                                }
                             } else {
                                 // every group exact: slices j = 0 .. S-1-i into accumulators
                                 // i .. S-1, at most four slices (N = 256) per MMA
                                 const int nj = S - i, n1 = nj < 4 ? nj : 4;
-                                tc::mma_bf16(dacc + 64 * i, ad, bk, tc::idesc_bf16_f32(128, 64 * n1), acc);
-                                if (nj > 4)
-                                    tc::mma_bf16(dacc + 64 * (i + 4), ad, bk + (uint64_t)((4 * HBLK) >> 4),
-                                                 tc::idesc_bf16_f32(128, 64 * (nj - 4)), acc);
+                                if (nj > 4) {
+                                    tc::mma_bf16_ca<tc::Collector::FILL>(dacc + 64 * i, ad, bk,
+                                                                         tc::idesc_bf16_f32(128, 64 * n1), acc);
+                                    tc::mma_bf16_ca<tc::Collector::LASTUSE>(dacc + 64 * (i + 4), ad,
+                                                                            bk + (uint64_t)((4 * HBLK) >> 4),
+                                                                            tc::idesc_bf16_f32(128, 64 * (nj - 4)), acc);
+                                } else {
+                                    tc::mma_bf16(dacc + 64 * i, ad, bk, tc::idesc_bf16_f32(128, 64 * n1), acc);
+                                }
                             }
                         }
                         issued = true;
@@ -1206,7 +1233,7 @@ __global__ void __launch_bounds__(pipe::NTHP, 1) k_trail_pipe(int mode, int Klo,
                     tc::tma_load_2d(sC + bx * CBOX, &tmapC, 64 * ch + 32 * (bx & 1), yH + 128 * (bx >> 1), &cFull);
                 c_pending = true;
             }
-            if (P == 2) {
+            if (P >= 2) {
                 const short ec = (short)common_exp(oconst[OC_N * (int64_t)w + OC_NUG]);
                 if (et < TB) sEA[et] = ec;
                 else if (et < TB + 64) sEB[et - TB] = ec;
@@ -1608,7 +1635,8 @@ static cudaError_t launch_mixed_steps(const BatchArgs &b, const MixedArgs &x, cu
             const int64_t items = (int64_t)cnt * (m * (m + 1) / 2) * 2;
             const int grid = (int)std::min<int64_t>(items, sms);
             TIMED(KC_GEMM_SPLIT7, (k_trail_pipe<7><<<grid, pipe::NTHP, pipe::Cfg<7>::SMEM, s>>>(
-                                      0, J + 1, nb, 1, 0, 0, nb, cnt, b.tpo, tmapC, x.pimg, b.oconst, nullptr, x.err)));
+                                      0, J + 1, J + 1, nb, 1, 0, nb, cnt, b.tpo, tmapC, x.pimg, b.oconst, nullptr,
+                                      x.err)));
         }
     } else {
         if ((e = cudaFuncSetAttribute(k_trsm_split<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_split)) !=
@@ -1617,13 +1645,14 @@ static cudaError_t launch_mixed_steps(const BatchArgs &b, const MixedArgs &x, cu
         if ((e = cudaFuncSetAttribute(k_trail_pipe<5>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       pipe::Cfg<5>::SMEM)) != cudaSuccess)
             return e;
-        auto trail = [&](int mode, int Klo, int Ihi, int P, int sub0, int sub1) {
-            const int m = Ihi - Klo + 1;
-            if (m <= 0) return;
-            const int64_t items = (int64_t)cnt * ((mode == 0) ? m * (m + 1) / 2 : m) * 2;
+        auto trail = [&](int mode, int Klo, int Khi, int Ihi, int P, int sub0) {
+            const int m = Ihi - Klo + 1, nK = Khi - Klo + 1;
+            if (m <= 0 || (mode == 3 && nK <= 0)) return;
+            const int64_t T = (mode == 0) ? (int64_t)m * (m + 1) / 2 : (mode == 3) ? (int64_t)nK * m - nK * (nK - 1) / 2 : m;
+            const int64_t items = (int64_t)cnt * T * 2;
             const int grid = (int)std::min<int64_t>(items, sms);
             TIMED(KC_GEMM_SPLIT, (k_trail_pipe<5><<<grid, pipe::NTHP, pipe::Cfg<5>::SMEM, s>>>(
-                                     mode, Klo, Ihi, P, sub0, sub1, nb, cnt, b.tpo, tmapC, x.pimg, b.oconst, doomed,
+                                     mode, Klo, Khi, Ihi, P, sub0, nb, cnt, b.tpo, tmapC, x.pimg, b.oconst, doomed,
                                      x.err)));
         };
         auto factor_panel = [&](int J) {
@@ -1632,23 +1661,23 @@ static cudaError_t launch_mixed_steps(const BatchArgs &b, const MixedArgs &x, cu
             TIMED(KC_TRSM_SPLIT, (k_trsm_split<S><<<dim3(nb - J, cnt), NTH, smem_split, s>>>(
                                      J, nb, b.tpo, b.tiles, x.wimg, x.pimg, b.oconst, doomed, x.err)));
         };
-        // Two-panel look-ahead: factor panel J0, bring tile column J0+1 up to
-        // date with it, factor J0+1, then update the right-hand-side row with
-        // each panel (own exponents) and the data triangle with both panels
-        // at once (K = 256 in one accumulator set: one read-modify-write
-        // of every trailing tile per two panels).
-        for (int J0 = 0; J0 < nb; J0 += 2) {
-            const int J1 = J0 + 1;
-            factor_panel(J0);
-            if (J1 >= nb) {
-                trail(0, J0 + 1, nb, 1, J0 & 1, 0);   // remaining: the right-hand-side block
-                break;
+        // Panels in groups of up to four with look-ahead inside the group:
+        // factor panel J and bring the group's later tile columns (data rows
+        // and the RHS row) up to date with it, panel after panel; then update
+        // the right-hand-side row beyond the group with each panel (own
+        // exponents) and the data triangle beyond the group with all of the
+        // group's panels at once (K = 512 in one accumulator set: one
+        // read-modify-write of every trailing tile per four panels -- the
+        // epilogue's read-modify-write, not the MMAs, bounds this kernel).
+        constexpr int GP = 4;
+        for (int J0 = 0; J0 < nb; J0 += GP) {
+            const int G = std::min(GP, nb - J0), Jend = J0 + G;   // panels J0 .. Jend - 1
+            for (int J = J0; J < Jend; ++J) {
+                factor_panel(J);
+                trail(3, J + 1, Jend - 1, nb, 1, J & 3);          // the group's later columns
             }
-            trail(1, J1, nb, 1, J0 & 1, 0);           // column J1 (data rows and the RHS row)
-            factor_panel(J1);
-            trail(2, J1 + 1, nb, 1, J0 & 1, 0);       // RHS row with panel J0
-            trail(2, J1 + 1, nb, 1, J1 & 1, 0);       // RHS row with panel J1
-            trail(0, J1 + 1, nb - 1, 2, J0 & 1, J1 & 1);   // data triangle with both panels
+            for (int J = J0; J < Jend; ++J) trail(2, Jend, Jend, nb, 1, J & 3);   // RHS row, incl. the corner
+            trail(0, Jend, Jend, nb - 1, G, J0 & 3);               // data triangle with the group's panels
         }
     }
     TIMED(KC_CONVERT, (k_tile_to_fp64<<<cnt, 256, 0, s>>>(b.tpo, tile_index(nb, nb), b.tiles)));

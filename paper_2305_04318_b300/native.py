@@ -177,6 +177,7 @@ FLAG_NO_FP64_TIER = 4
 FLAG_GRAPH = 8
 FLAG_FULL_FIRST_PASS = 16
 FLAG_NO_FUSED = 32
+FLAG_PIPELINED_RETRY = 64
 
 
 def kernel_timing(reset=True):

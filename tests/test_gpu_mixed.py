@@ -267,3 +267,24 @@ def test_largest_serving_size_sampled():
     # within half its bound
     g5 = gpu_eval(ds, P, lams, precision=nv.MIXED, batch=3, flags=nv.FLAG_NO_RETRY)
     _bound_margin(ds, P, lams, o, "n=8000", g5=g5)
+
+
+@pytest.mark.parametrize("K", [300, 900])
+def test_pipelined_retry_identical_to_serial(K):
+    """The 7-slice re-evaluation once after the whole 5-slice pass (default)
+    or part by part on its own stream beside the later parts
+    (PLK_FLAG_PIPELINED_RETRY): results, statuses and bounds are the same bit
+    for bit; ill-conditioned points make every part send some points to 7
+    slices."""
+    ds = synth.aniso_dataset(79, 700, math.sqrt(70), 3)
+    rng = np.random.default_rng(79)
+    ill = synth.ill_conditioned_points()
+    n_ill = min(K // 5, len(ill))
+    P = np.vstack([ill[rng.permutation(len(ill))[:n_ill]], synth.omega_from_unit(rng.uniform(size=(K - n_ill, 5)))])
+    P = P[rng.permutation(K)]
+    lams = synth.LAMBDA_GRID_9
+    a = gpu_eval(ds, P, lams, precision=nv.MIXED, batch=K)
+    b = gpu_eval(ds, P, lams, precision=nv.MIXED, batch=K, flags=nv.FLAG_PIPELINED_RETRY)
+    for k in ("logL", "sigma2", "beta", "logdet", "status", "err_bound"):
+        np.testing.assert_array_equal(a[k], b[k], err_msg=k)
+    assert ((a["status"] & nv.POINT_RETRIED) != 0).sum() >= 8
