@@ -95,6 +95,9 @@ def parse():
                     help="serving: sub-grid values of each other parameter (the full job: 4)")
     ap.add_argument("--serve-batch", type=int, default=16, help="serving: points per scheduled batch")
     ap.add_argument("--capacity-jobs", type=int, default=6, help="serving: jobs run one after another for the capacity")
+    ap.add_argument("--level-seconds", type=float, default=0.0,
+                    help="serving: run each load level for this long (arrivals stop then, the jobs in flight finish) "
+                         "instead of a fixed number of jobs")
     ap.add_argument("--streams", type=int, default=4, help="uneven/serving: scheduler streams")
     ap.add_argument("--graph", type=int, default=0,
                     help="uneven: launch batches as CUDA graphs (1) or eagerly (0, default: measured faster)")
@@ -368,7 +371,8 @@ def run_uneven(args):
     ns = np.array([d.n for d in w.datasets])
     line = {"metric": "profile-logL evals/s, batched uneven datasets", "value": npts / dt, "unit": UNIT,
             "n_gpus": world, "steps": 1, "warmup": 1, "ms_per_step": dt * 1e3, "higher_is_better": True,
-            "scaling": "strong", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "scaling": "strong", "vs_baseline": None, "dtype": DTYPE["mixed" if prec == nv.MIXED else "fp64"],
+            "data": "synthetic",
             "config": {"workload": f"uneven: {D} datasets, n log-uniform in [200,3000] (median {int(np.median(ns))}), "
                                    f"p in {{2,3,5}}, {args.points} points each, 9 lambdas",
                        "precision": "mixed" if prec == nv.MIXED else "fp64", "streams": args.streams,
@@ -432,15 +436,20 @@ def run_serving(args):
         levels = {}
         for rho in (0.5, 0.9):
             rate = rho * cap
-            arrivals = np.cumsum(rng.exponential(1.0 / rate, size=args.jobs))
+            if args.level_seconds > 0:   # arrivals for level_seconds, then drain
+                arr = np.cumsum(rng.exponential(1.0 / rate, size=int(rate * args.level_seconds * 3) + 10))
+                arrivals = arr[arr <= args.level_seconds]
+            else:
+                arrivals = np.cumsum(rng.exponential(1.0 / rate, size=args.jobs))
+            njobs = len(arrivals)
             lat = []
             pending = []
             t0 = time.perf_counter()
             k = 0
             done = 0
-            while done < args.jobs:
+            while done < njobs:
                 now = time.perf_counter() - t0
-                while k < args.jobs and arrivals[k] <= now:
+                while k < njobs and arrivals[k] <= now:
                     d_i, which = job_spec(k)
                     jb = ctx.submit(ids[d_i], grids[which][1], lam, precision=prec, batch=args.serve_batch)
                     pending.append((jb, d_i, which, t0 + arrivals[k]))
@@ -459,14 +468,16 @@ def run_serving(args):
                 pending = still
                 time.sleep(0.001)
             span = time.perf_counter() - t0
-            levels[str(rho)] = {"offered_jobs_per_s": rate, "jobs": args.jobs, "throughput_jobs_per_s": args.jobs / span,
-                                "evals_per_s": args.jobs * G * sub ** 4 / span,
-                                "p50_ms": 1e3 * float(np.percentile(lat, 50)), "p99_ms": 1e3 * float(np.percentile(lat, 99))}
+            levels[str(rho)] = {"offered_jobs_per_s": rate, "jobs": njobs, "seconds": span,
+                                "throughput_jobs_per_s": njobs / span, "evals_per_s": njobs * G * sub ** 4 / span,
+                                "p50_ms": 1e3 * float(np.percentile(lat, 50)), "p99_ms": 1e3 * float(np.percentile(lat, 99)),
+                                "max_ms": 1e3 * float(np.max(lat))}
         _, high = ctx.memory_stats()
     top = levels["0.9"]
     line = {"metric": "profile jobs: throughput and p50/p99 job latency (serving)", "value": top["evals_per_s"],
-            "unit": UNIT, "n_gpus": 1, "steps": args.jobs, "warmup": cap_jobs, "ms_per_step": top["p50_ms"],
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "unit": UNIT, "n_gpus": 1, "steps": top["jobs"], "warmup": cap_jobs, "ms_per_step": top["p50_ms"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": DTYPE["mixed" if prec == nv.MIXED else "fp64"], "data": "synthetic",
             "config": {"workload": f"serving: {D} resident datasets, n log-uniform in [500,8000], p=3; job = one "
                                    f"parameter's {G}-point profile x {sub}^4 sub-grid x 9 lambdas ({G * sub ** 4} omega), "
                                    "then profile max + 95% CI on the device; Poisson arrivals",
@@ -554,7 +565,7 @@ def run_pipeline(args):
     line = {"metric": "profile-likelihood method, Steps 1-6 on one dataset", "value": K * M / times["step3_eval_s"],
             "unit": "(omega, lambda) evals/s in Step 3", "n_gpus": 1, "steps": 1, "warmup": 1,
             "ms_per_step": 1e3 * total, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64", "data": "synthetic",
+            "dtype": DTYPE["mixed" if prec == nv.MIXED else "fp64"], "data": "synthetic",
             "config": {"workload": f"pipeline: n={n} sites on a square of side {math.sqrt(n / 100.0):.2f}, p=2, "
                                    "truth kappa=1, phi_X=0.2, nu^2=0.1, ratio 1.5, lambda 0.5",
                        "precision": "mixed" if prec == nv.MIXED else "fp64", "K": int(K), "M": int(M)},
@@ -666,8 +677,9 @@ def trail_kernel_sha256(root):
 def trail_launches(n, part, TB=128, GP=4):
     """(items, panels) of every k_trail_pipe<5> launch of the 5-slice pass over
     one part of `part` points at n sites: the schedule of launch_mixed_steps
-    (panels in groups of GP: the group's later columns after each panel, the
-    right-hand-side row with each panel, the data triangle with the group)."""
+    (panels in groups of GP: before each panel its column's data rows with the
+    group's earlier panels, after it the right-hand-side row, after the group
+    the data triangle with all its panels)."""
     nb = -(-n // TB)
     out = []
 
@@ -681,9 +693,9 @@ def trail_launches(n, part, TB=128, GP=4):
         G = min(GP, nb - J0)
         Jend = J0 + G
         for J in range(J0, Jend):
-            add(3, J + 1, Jend - 1, nb, 1)
-        for J in range(J0, Jend):
-            add(2, Jend, Jend, nb, 1)
+            if J > J0:
+                add(1, J, J, nb - 1, J - J0)
+            add(2, J + 1, J + 1, nb, 1)
         add(0, Jend, Jend, nb - 1, G)
     return out
 

@@ -1020,6 +1020,7 @@ template <int S>
 __global__ void __launch_bounds__(pipe::NTHP, 1) k_trail_pipe(int mode, int Klo, int Khi, int Ihi, int P, int sub0,
                                                              int nb, int cnt, int64_t tpo,
                                                              const __grid_constant__ CUtensorMap tmapC,
+                                                             const __grid_constant__ CUtensorMap tmapR, int qr,
                                                              const uint8_t *__restrict__ pimg,
                                                              const double *__restrict__ oconst,
                                                              const int *__restrict__ doomed, int *__restrict__ err) {
@@ -1224,13 +1225,19 @@ __global__ void __launch_bounds__(pipe::NTHP, 1) k_trail_pipe(int mode, int Klo,
             if (doomed && doomed[w]) continue;
             // rows of the tile in the tensor map: H plane T*256 .. +127, L plane T*256+128 .. +255
             const int yH = (int)(((int64_t)w * tpo + tile_index(I, K)) * 256);
+            // a tile of the right-hand-side row holds M + p <= 64 non-zero rows:
+            // only its first qr rows (M + p rounded up to 8) are read, updated
+            // and written back, through the map with qr-row boxes
+            const bool rhs = I == nb;
+            const int rows = rhs ? qr : TB;
+            const CUtensorMap *tm = rhs ? &tmapR : &tmapC;
             if (et == 0) {
                 // the previous item's stores have read the buffer: load this item's half tile
                 tc::bulk_wait_read_all();
-                tc::mbar_arrive_expect_tx(&cFull, 4 * CBOX);
+                tc::mbar_arrive_expect_tx(&cFull, 4 * rows * 128);
 #pragma unroll
                 for (int bx = 0; bx < 4; ++bx)
-                    tc::tma_load_2d(sC + bx * CBOX, &tmapC, 64 * ch + 32 * (bx & 1), yH + 128 * (bx >> 1), &cFull);
+                    tc::tma_load_2d(sC + bx * CBOX, tm, 64 * ch + 32 * (bx & 1), yH + 128 * (bx >> 1), &cFull);
                 c_pending = true;
             }
             if (P >= 2) {
@@ -1254,53 +1261,55 @@ __global__ void __launch_bounds__(pipe::NTHP, 1) k_trail_pipe(int mode, int Klo,
             tc::named_sync(1, NEPI);       // exponents and C visible; stop decision uniform
             if (s_stop) break;
             tc::fence_after_sync();
-            const uint32_t a = tb + set * 256 + ((uint32_t)(32 * (warp & 3)) << 16) + 32 * q;
-            const int ea = sEA[r] - 14;
-            const short *eb = sEB + 32 * q;
+            if (32 * (warp & 3) < rows) {   // warps whose rows all lie beyond an RHS tile's rows skip
+                const uint32_t a = tb + set * 256 + ((uint32_t)(32 * (warp & 3)) << 16) + 32 * q;
+                const int ea = sEA[r] - 14;
+                const short *eb = sEB + 32 * q;
 #pragma unroll 1
-            for (int c0 = 0; c0 < 32; c0 += 16) {
-                float dh[16], dl[16];
-                if (S == 5) {
-                    uint32_t p0[16], p1[16], p2[16], p3[16];
-                    tc::tmem_ld16(a + 0 * 64 + c0, p0);
-                    tc::tmem_ld16(a + 1 * 64 + c0, p1);
-                    tc::tmem_ld16(a + 2 * 64 + c0, p2);
-                    tc::tmem_ld16(a + 3 * 64 + c0, p3);
-                    tc::tmem_wait_ld();
-#pragma unroll
-                    for (int c = 0; c < 16; ++c) group_value(p0[c], p1[c], p2[c], p3[c], ea + eb[c0 + c], dh[c], dl[c]);
-                } else {
-#pragma unroll 1
-                    for (int g = 0; g < S; ++g) {
-                        uint32_t pg[16];
-                        tc::tmem_ld16(a + g * 64 + c0, pg);
+                for (int c0 = 0; c0 < 32; c0 += 16) {
+                    float dh[16], dl[16];
+                    if (S == 5) {
+                        uint32_t p0[16], p1[16], p2[16], p3[16];
+                        tc::tmem_ld16(a + 0 * 64 + c0, p0);
+                        tc::tmem_ld16(a + 1 * 64 + c0, p1);
+                        tc::tmem_ld16(a + 2 * 64 + c0, p2);
+                        tc::tmem_ld16(a + 3 * 64 + c0, p3);
                         tc::tmem_wait_ld();
 #pragma unroll
-                        for (int c = 0; c < 16; ++c) {
-                            const float v = __uint_as_float(pg[c]) * pow2f(ea + eb[c0 + c]);
-                            if (g == 0) {
-                                dh[c] = v;
-                                dl[c] = 0.0f;
-                            } else {
-                                df_add(dh[c], dl[c], v);
+                        for (int c = 0; c < 16; ++c) group_value(p0[c], p1[c], p2[c], p3[c], ea + eb[c0 + c], dh[c], dl[c]);
+                    } else {
+#pragma unroll 1
+                        for (int g = 0; g < S; ++g) {
+                            uint32_t pg[16];
+                            tc::tmem_ld16(a + g * 64 + c0, pg);
+                            tc::tmem_wait_ld();
+#pragma unroll
+                            for (int c = 0; c < 16; ++c) {
+                                const float v = __uint_as_float(pg[c]) * pow2f(ea + eb[c0 + c]);
+                                if (g == 0) {
+                                    dh[c] = v;
+                                    dl[c] = 0.0f;
+                                } else {
+                                    df_add(dh[c], dl[c], v);
+                                }
                             }
                         }
                     }
-                }
 #pragma unroll
-                for (int k4 = 0; k4 < 4; ++k4) {
-                    const int kc = ((c0 >> 2) + k4) ^ sw;
-                    float4 h = rowH[kc], l = rowL[kc];
-                    df_add(h.x, l.x, -dh[4 * k4 + 0]);
-                    df_add(h.x, l.x, -dl[4 * k4 + 0]);
-                    df_add(h.y, l.y, -dh[4 * k4 + 1]);
-                    df_add(h.y, l.y, -dl[4 * k4 + 1]);
-                    df_add(h.z, l.z, -dh[4 * k4 + 2]);
-                    df_add(h.z, l.z, -dl[4 * k4 + 2]);
-                    df_add(h.w, l.w, -dh[4 * k4 + 3]);
-                    df_add(h.w, l.w, -dl[4 * k4 + 3]);
-                    rowH[kc] = h;
-                    rowL[kc] = l;
+                    for (int k4 = 0; k4 < 4; ++k4) {
+                        const int kc = ((c0 >> 2) + k4) ^ sw;
+                        float4 h = rowH[kc], l = rowL[kc];
+                        df_add(h.x, l.x, -dh[4 * k4 + 0]);
+                        df_add(h.x, l.x, -dl[4 * k4 + 0]);
+                        df_add(h.y, l.y, -dh[4 * k4 + 1]);
+                        df_add(h.y, l.y, -dl[4 * k4 + 1]);
+                        df_add(h.z, l.z, -dh[4 * k4 + 2]);
+                        df_add(h.z, l.z, -dl[4 * k4 + 2]);
+                        df_add(h.w, l.w, -dh[4 * k4 + 3]);
+                        df_add(h.w, l.w, -dl[4 * k4 + 3]);
+                        rowH[kc] = h;
+                        rowL[kc] = l;
+                    }
                 }
             }
             tc::fence_proxy_async();        // these writes are read by the TMA store
@@ -1310,7 +1319,7 @@ __global__ void __launch_bounds__(pipe::NTHP, 1) k_trail_pipe(int mode, int Klo,
                 tc::mbar_arrive(&accEmpty[set]);   // the MMA warp may reuse this set
 #pragma unroll
                 for (int bx = 0; bx < 4; ++bx)
-                    tc::tma_store_2d(&tmapC, 64 * ch + 32 * (bx & 1), yH + 128 * (bx >> 1), sC + bx * CBOX);
+                    tc::tma_store_2d(tm, 64 * ch + 32 * (bx & 1), yH + 128 * (bx >> 1), sC + bx * CBOX);
                 tc::bulk_commit();
             }
             ++tcnt;
@@ -1577,7 +1586,7 @@ static int num_sms() {
 // (global index w * tpo + t) holds its H plane in rows 256 T .. 256 T + 127 and
 // its L plane in the next 128 rows.  Box: 32 floats x 128 rows, 128-byte
 // swizzle (the trailing update's C half tile is four boxes).
-static cudaError_t make_tile_map(CUtensorMap *m, double *tiles, int count, int64_t tpo) {
+static cudaError_t make_tile_map(CUtensorMap *m, double *tiles, int count, int64_t tpo, int box_rows = TB) {
     static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
     static std::once_flag once;
     std::call_once(once, [] {
@@ -1593,7 +1602,7 @@ static cudaError_t make_tile_map(CUtensorMap *m, double *tiles, int count, int64
     if (rows > (int64_t)INT32_MAX) return cudaErrorInvalidValue;   // row coordinates are 32-bit
     const cuuint64_t dims[2] = {(cuuint64_t)TB, (cuuint64_t)rows};
     const cuuint64_t strides[1] = {(cuuint64_t)TB * sizeof(float)};
-    const cuuint32_t box[2] = {32, (cuuint32_t)TB};
+    const cuuint32_t box[2] = {32, (cuuint32_t)box_rows};
     const cuuint32_t estr[2] = {1, 1};
     const CUresult r = encode(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, tiles, dims, strides, box, estr,
                               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -1615,8 +1624,10 @@ static cudaError_t launch_mixed_steps(const BatchArgs &b, const MixedArgs &x, cu
     // for the 7-slice tier (the bound kernel keeps the marks)
     int *doomed = (S == 5 && x.early) ? x.flags : nullptr;
     if (doomed) cudaMemsetAsync(doomed, 0, sizeof(int) * cnt, s);
-    CUtensorMap tmapC;
+    CUtensorMap tmapC, tmapR;
+    const int qr = std::min(TB, (b.q + 7) / 8 * 8);   // rows of a right-hand-side tile that can be non-zero
     if ((e = make_tile_map(&tmapC, b.tiles, cnt, b.tpo)) != cudaSuccess) return e;
+    if ((e = make_tile_map(&tmapR, b.tiles, cnt, b.tpo, qr)) != cudaSuccess) return e;
     const int sms = num_sms();
     if constexpr (S == 7) {
         if ((e = cudaFuncSetAttribute(k_trsm_split7x, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_split)) !=
@@ -1635,7 +1646,7 @@ static cudaError_t launch_mixed_steps(const BatchArgs &b, const MixedArgs &x, cu
             const int64_t items = (int64_t)cnt * (m * (m + 1) / 2) * 2;
             const int grid = (int)std::min<int64_t>(items, sms);
             TIMED(KC_GEMM_SPLIT7, (k_trail_pipe<7><<<grid, pipe::NTHP, pipe::Cfg<7>::SMEM, s>>>(
-                                      0, J + 1, J + 1, nb, 1, 0, nb, cnt, b.tpo, tmapC, x.pimg, b.oconst, nullptr,
+                                      0, J + 1, J + 1, nb, 1, 0, nb, cnt, b.tpo, tmapC, tmapR, qr, x.pimg, b.oconst, nullptr,
                                       x.err)));
         }
     } else {
@@ -1652,7 +1663,7 @@ static cudaError_t launch_mixed_steps(const BatchArgs &b, const MixedArgs &x, cu
             const int64_t items = (int64_t)cnt * T * 2;
             const int grid = (int)std::min<int64_t>(items, sms);
             TIMED(KC_GEMM_SPLIT, (k_trail_pipe<5><<<grid, pipe::NTHP, pipe::Cfg<5>::SMEM, s>>>(
-                                     mode, Klo, Khi, Ihi, P, sub0, nb, cnt, b.tpo, tmapC, x.pimg, b.oconst, doomed,
+                                     mode, Klo, Khi, Ihi, P, sub0, nb, cnt, b.tpo, tmapC, tmapR, qr, x.pimg, b.oconst, doomed,
                                      x.err)));
         };
         auto factor_panel = [&](int J) {
@@ -1661,22 +1672,21 @@ static cudaError_t launch_mixed_steps(const BatchArgs &b, const MixedArgs &x, cu
             TIMED(KC_TRSM_SPLIT, (k_trsm_split<S><<<dim3(nb - J, cnt), NTH, smem_split, s>>>(
                                      J, nb, b.tpo, b.tiles, x.wimg, x.pimg, b.oconst, doomed, x.err)));
         };
-        // Panels in groups of up to four with look-ahead inside the group:
-        // factor panel J and bring the group's later tile columns (data rows
-        // and the RHS row) up to date with it, panel after panel; then update
-        // the right-hand-side row beyond the group with each panel (own
-        // exponents) and the data triangle beyond the group with all of the
-        // group's panels at once (K = 512 in one accumulator set: one
-        // read-modify-write of every trailing tile per four panels -- the
-        // epilogue's read-modify-write, not the MMAs, bounds this kernel).
+        // Panels in groups of up to four: before panel J is factored, its tile
+        // column's data rows receive the group's earlier panels in one launch
+        // (one read-modify-write per tile); after it, the right-hand-side row
+        // (K = J + 1 .. nb, own exponents) receives panel J; after the group,
+        // the data triangle beyond it receives all of the group's panels at
+        // once (K = 512 in one accumulator set: one read-modify-write of every
+        // trailing tile per four panels).
         constexpr int GP = 4;
         for (int J0 = 0; J0 < nb; J0 += GP) {
             const int G = std::min(GP, nb - J0), Jend = J0 + G;   // panels J0 .. Jend - 1
             for (int J = J0; J < Jend; ++J) {
+                if (J > J0) trail(1, J, J, nb - 1, J - J0, J0 & 3);   // column J with panels J0 .. J - 1
                 factor_panel(J);
-                trail(3, J + 1, Jend - 1, nb, 1, J & 3);          // the group's later columns
+                trail(2, J + 1, J + 1, nb, 1, J & 3);                  // RHS row with panel J, incl. the corner
             }
-            for (int J = J0; J < Jend; ++J) trail(2, Jend, Jend, nb, 1, J & 3);   // RHS row, incl. the corner
             trail(0, Jend, Jend, nb - 1, G, J0 & 3);               // data triangle with the group's panels
         }
     }
