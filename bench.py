@@ -99,6 +99,8 @@ def parse():
                     help="serving: run each load level for this long (arrivals stop then, the jobs in flight finish) "
                          "instead of a fixed number of jobs")
     ap.add_argument("--streams", type=int, default=4, help="uneven/serving: scheduler streams")
+    ap.add_argument("--policy", default="largest", choices=["fifo", "largest"],
+                    help="uneven: which job a free scheduler stream serves next (largest dataset first, or oldest)")
     ap.add_argument("--graph", type=int, default=0,
                     help="uneven: launch batches as CUDA graphs (1) or eagerly (0, default: measured faster)")
     return ap.parse_args()
@@ -340,6 +342,7 @@ def run_uneven(args):
         torch.cuda.synchronize()
 
     with nv.Context(arena_bytes, device=local, arena=arena, n_streams=args.streams) as ctx:
+        ctx.set_schedule_policy(nv.SCHED_LARGEST_FIRST if args.policy == "largest" else nv.SCHED_FIFO)
         t_tune = time.perf_counter()
         if args.item_batch <= 0:
             buckets = sorted({int(round(2 * math.log2(w.datasets[i].n))) for i in mine})
@@ -378,6 +381,7 @@ def run_uneven(args):
                        "precision": "mixed" if prec == nv.MIXED else "fp64", "streams": args.streams,
                        "batch_per_item": args.item_batch if args.item_batch > 0 else "autotuned",
                        "cuda_graphs": bool(args.graph), "arena_gb": arena_bytes / 1e9,
+                       "schedule_policy": args.policy,
                        "parallelism": f"datasets balanced by points x n^3 over {world} rank(s)"},
             "autotune": {"seconds": round(t_tune, 2), "by_n": tune,
                          "what": "plk_autotune per half-octave of n, before the timed region (rank 0's)"},
@@ -683,20 +687,20 @@ def trail_launches(n, part, TB=128, GP=4):
     nb = -(-n // TB)
     out = []
 
-    def add(mode, Klo, Khi, Ihi, P):
-        m, nK = Ihi - Klo + 1, Khi - Klo + 1
-        if m <= 0 or (mode == 3 and nK <= 0):
+    def add(mode, Klo, Ihi, P):
+        m = Ihi - Klo + 1
+        if m <= 0:
             return
-        T = m * (m + 1) // 2 if mode == 0 else nK * m - nK * (nK - 1) // 2 if mode == 3 else m
+        T = m * (m + 1) // 2 if mode == 0 else m
         out.append((part * T * 2, P))
     for J0 in range(0, nb, GP):
         G = min(GP, nb - J0)
         Jend = J0 + G
         for J in range(J0, Jend):
             if J > J0:
-                add(1, J, J, nb - 1, J - J0)
-            add(2, J + 1, J + 1, nb, 1)
-        add(0, Jend, Jend, nb - 1, G)
+                add(1, J, nb - 1, J - J0)
+            add(2, J + 1, nb, 1)
+        add(0, Jend, nb - 1, G)
     return out
 
 

@@ -275,6 +275,19 @@ plk_status plk_destroy(plk_ctx *ctx);
  * PLK_E_INVALID for an unknown job. */
 plk_status plk_cancel(plk_ctx *ctx, plk_job job);
 
+/* Which job's next batch a free scheduler stream takes (no counterpart in
+ * the paper, whose back end runs one grid at a time):
+ *   PLK_SCHED_FIFO           the oldest job with work left (the default;
+ *                            serving: the earliest request is served first);
+ *   PLK_SCHED_LARGEST_FIRST  the job on the largest dataset (cost per point
+ *                            ~ n^3), the oldest among equals (many jobs
+ *                            submitted together: the small ones fill the end
+ *                            instead of a large one running alone).
+ * Results do not depend on the policy.  PLK_E_INVALID for an unknown policy. */
+#define PLK_SCHED_FIFO 0
+#define PLK_SCHED_LARGEST_FIRST 1
+plk_status plk_set_schedule_policy(plk_ctx *ctx, int32_t policy);
+
 /* Per-job metrics as JSON lines (no counterpart in the paper).  From this call
  * on, every job that ends (completed, failed or cancelled) appends one line to
  * the file at `path` (opened for appending; NULL stops logging): job and

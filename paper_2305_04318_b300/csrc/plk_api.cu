@@ -957,6 +957,7 @@ struct plk_ctx {
     // host-side fault hooks (plk_inject_fault): counts of events still to fail
     int fault_arena = 0, fault_item = 0, fault_drop = 0;
     FILE *metrics = nullptr;   // per-job JSON lines (plk_set_metrics_log)
+    int policy = PLK_SCHED_FIFO;   // which job's batch a free stream takes next
 };
 
 namespace {
@@ -1193,10 +1194,13 @@ void stream_worker(plk_ctx *c, int slot) {
     while (true) {
         Job *pick = nullptr;
         for (Job *j : c->order) {
-            if (j->next_k < j->K || (!j->started && j->K == 0)) {
+            if (!(j->next_k < j->K || (!j->started && j->K == 0))) continue;
+            if (c->policy == PLK_SCHED_FIFO) {   // the oldest job with work left
                 pick = j;
                 break;
             }
+            // largest first: the job with the largest dataset (cost per point ~ n^3), oldest on ties
+            if (!pick || j->n > pick->n) pick = j;
         }
         if (!pick) {
             if (c->stop && c->order.empty()) break;
@@ -1535,6 +1539,14 @@ extern "C" plk_status plk_inject_fault(plk_ctx *c, int32_t kind, int32_t count) 
         default: return fail(PLK_E_INVALID, "unknown fault kind %d", kind);
     }
     c->cv_work.notify_all();
+    return PLK_OK;
+}
+
+extern "C" plk_status plk_set_schedule_policy(plk_ctx *c, int32_t policy) {
+    if (!c) return fail(PLK_E_INVALID, "ctx is NULL");
+    if (policy != PLK_SCHED_FIFO && policy != PLK_SCHED_LARGEST_FIRST) return fail(PLK_E_INVALID, "unknown policy %d", policy);
+    std::lock_guard<std::mutex> lk(c->mu);
+    c->policy = policy;
     return PLK_OK;
 }
 

@@ -1009,15 +1009,15 @@ struct Cfg {
 }  // namespace pipe
 
 // Item sets: mode 0 = the triangle Klo <= K <= I <= Ihi; mode 1 = the column
-// K = Klo, Klo <= I <= Ihi; mode 2 = the row I = Ihi, Klo <= K <= Ihi; mode 3 =
-// the columns Klo <= K <= Khi, K <= I <= Ihi.  Each item applies P (1 to 4)
+// K = Klo, Klo <= I <= Ihi; mode 2 = the row I = Ihi, Klo <= K <= Ihi.  Each
+// item applies P (1 to 4)
 // consecutive panels, the p-th in sub-slot (sub0 + p) % 4; with P >= 2 both
 // operands use the common exponent (data rows only; 5 slices only).  The
 // FP32 accumulators of groups 0-2 stay exact up to K = 4 x 128: with every
 // data row of L bounded by sqrt(1 + nu^2) < 2^e (Cauchy-Schwarz over the
 // leading digits), group 2's sums stay below 2^23.2 units.
 template <int S>
-__global__ void __launch_bounds__(pipe::NTHP, 1) k_trail_pipe(int mode, int Klo, int Khi, int Ihi, int P, int sub0,
+__global__ void __launch_bounds__(pipe::NTHP, 1) k_trail_pipe(int mode, int Klo, int Ihi, int P, int sub0,
                                                              int nb, int cnt, int64_t tpo,
                                                              const __grid_constant__ CUtensorMap tmapC,
                                                              const __grid_constant__ CUtensorMap tmapR, int qr,
@@ -1035,8 +1035,8 @@ __global__ void __launch_bounds__(pipe::NTHP, 1) k_trail_pipe(int mode, int Klo,
     __shared__ int s_err, s_stop;
     volatile int *verr = &s_err;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int m = Ihi - Klo + 1, nK = Khi - Klo + 1;
-    const int T = (mode == 0) ? m * (m + 1) / 2 : (mode == 3) ? nK * m - nK * (nK - 1) / 2 : m;
+    const int m = Ihi - Klo + 1;
+    const int T = (mode == 0) ? m * (m + 1) / 2 : m;
     const int64_t items = (int64_t)cnt * T * 2;
     if (tid == 0) {
         for (int i = 0; i < 2; ++i) {
@@ -1073,17 +1073,9 @@ __global__ void __launch_bounds__(pipe::NTHP, 1) k_trail_pipe(int mode, int Klo,
         } else if (mode == 1) {
             K = Klo;
             I = Klo + t;
-        } else if (mode == 2) {
+        } else {
             I = Ihi;
             K = Klo + t;
-        } else {
-            int r = t;
-            K = Klo;
-            while (r >= Ihi - K + 1) {
-                r -= Ihi - K + 1;
-                ++K;
-            }
-            I = K + r;
         }
     };
     auto image = [&](int w, int R, int p) {
@@ -1646,7 +1638,7 @@ static cudaError_t launch_mixed_steps(const BatchArgs &b, const MixedArgs &x, cu
             const int64_t items = (int64_t)cnt * (m * (m + 1) / 2) * 2;
             const int grid = (int)std::min<int64_t>(items, sms);
             TIMED(KC_GEMM_SPLIT7, (k_trail_pipe<7><<<grid, pipe::NTHP, pipe::Cfg<7>::SMEM, s>>>(
-                                      0, J + 1, J + 1, nb, 1, 0, nb, cnt, b.tpo, tmapC, tmapR, qr, x.pimg, b.oconst, nullptr,
+                                      0, J + 1, nb, 1, 0, nb, cnt, b.tpo, tmapC, tmapR, qr, x.pimg, b.oconst, nullptr,
                                       x.err)));
         }
     } else {
@@ -1656,14 +1648,14 @@ static cudaError_t launch_mixed_steps(const BatchArgs &b, const MixedArgs &x, cu
         if ((e = cudaFuncSetAttribute(k_trail_pipe<5>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       pipe::Cfg<5>::SMEM)) != cudaSuccess)
             return e;
-        auto trail = [&](int mode, int Klo, int Khi, int Ihi, int P, int sub0) {
-            const int m = Ihi - Klo + 1, nK = Khi - Klo + 1;
-            if (m <= 0 || (mode == 3 && nK <= 0)) return;
-            const int64_t T = (mode == 0) ? (int64_t)m * (m + 1) / 2 : (mode == 3) ? (int64_t)nK * m - nK * (nK - 1) / 2 : m;
+        auto trail = [&](int mode, int Klo, int Ihi, int P, int sub0) {
+            const int m = Ihi - Klo + 1;
+            if (m <= 0) return;
+            const int64_t T = (mode == 0) ? (int64_t)m * (m + 1) / 2 : m;
             const int64_t items = (int64_t)cnt * T * 2;
             const int grid = (int)std::min<int64_t>(items, sms);
             TIMED(KC_GEMM_SPLIT, (k_trail_pipe<5><<<grid, pipe::NTHP, pipe::Cfg<5>::SMEM, s>>>(
-                                     mode, Klo, Khi, Ihi, P, sub0, nb, cnt, b.tpo, tmapC, tmapR, qr, x.pimg, b.oconst, doomed,
+                                     mode, Klo, Ihi, P, sub0, nb, cnt, b.tpo, tmapC, tmapR, qr, x.pimg, b.oconst, doomed,
                                      x.err)));
         };
         auto factor_panel = [&](int J) {
@@ -1683,11 +1675,11 @@ static cudaError_t launch_mixed_steps(const BatchArgs &b, const MixedArgs &x, cu
         for (int J0 = 0; J0 < nb; J0 += GP) {
             const int G = std::min(GP, nb - J0), Jend = J0 + G;   // panels J0 .. Jend - 1
             for (int J = J0; J < Jend; ++J) {
-                if (J > J0) trail(1, J, J, nb - 1, J - J0, J0 & 3);   // column J with panels J0 .. J - 1
+                if (J > J0) trail(1, J, nb - 1, J - J0, J0 & 3);   // column J with panels J0 .. J - 1
                 factor_panel(J);
-                trail(2, J + 1, J + 1, nb, 1, J & 3);                  // RHS row with panel J, incl. the corner
+                trail(2, J + 1, nb, 1, J & 3);                      // RHS row with panel J, incl. the corner
             }
-            trail(0, Jend, Jend, nb - 1, G, J0 & 3);               // data triangle with the group's panels
+            trail(0, Jend, nb - 1, G, J0 & 3);                      // data triangle with the group's panels
         }
     }
     TIMED(KC_CONVERT, (k_tile_to_fp64<<<cnt, 256, 0, s>>>(b.tpo, tile_index(nb, nb), b.tiles)));

@@ -62,6 +62,7 @@ _PD = C.POINTER(C.c_double)
 HOST_EVAL_FN = C.CFUNCTYPE(C.c_int, C.c_void_p, C.c_int64, C.c_int32, _PD, _PD, _PD, _PD, C.c_int64, _PD, C.c_int32,
                            _PD, _PD, _PD, _PD, C.POINTER(C.c_int32))
 FAULT_ARENA_ALLOC, FAULT_BATCH, FAULT_DROP_COMPLETION = 1, 2, 3
+SCHED_FIFO, SCHED_LARGEST_FIRST = 0, 1
 
 EVAL_FN = C.CFUNCTYPE(C.c_int32, C.c_void_p, C.POINTER(C.c_double), C.c_int64, C.POINTER(C.c_double), C.c_int32,
                       C.POINTER(C.c_double))
@@ -129,6 +130,7 @@ def lib():
         "plk_selftest_bounded_wait": (C.c_int, [i32, vp]),
         "plk_cancel": (C.c_int, [vp, i64]),
         "plk_set_metrics_log": (C.c_int, [vp, C.c_char_p]),
+        "plk_set_schedule_policy": (C.c_int, [vp, i32]),
         "plk_inject_fault": (C.c_int, [vp, i32, i32]),
         "plk_create_with_evaluator": (C.c_int, [C.POINTER(vp), sz, C.c_int, HOST_EVAL_FN, vp]),
         "plk_selftest_df_exp": (C.c_int, [vp, vp, vp, vp, i64, vp]),
@@ -479,6 +481,10 @@ class Context:
 
     def cancel(self, job):
         _check(lib().plk_cancel(self.h, job["id"]))
+
+    def set_schedule_policy(self, policy):
+        """SCHED_FIFO (default) or SCHED_LARGEST_FIRST (plk_set_schedule_policy)."""
+        _check(lib().plk_set_schedule_policy(self.h, int(policy)))
 
     def set_metrics_log(self, path):
         _check(lib().plk_set_metrics_log(self.h, None if path is None else os.fsencode(path)))

@@ -192,3 +192,31 @@ def test_host_context_refuses_autotune_and_bad_faults():
             ctx.inject_fault(99, 1)
         with pytest.raises(nv.PlkError):
             ctx.inject_fault(nv.FAULT_BATCH, -1)
+
+
+def test_largest_first_policy_orders_jobs_by_dataset_size(tmp_path):
+    """With one worker busy on a first job, three jobs queue; FIFO starts them
+    in submission order, largest-first by decreasing n; results are the same."""
+    small, mid, large = (_problem(s, n=n, K=4) for s, n in ((1, 20), (2, 35), (3, 50)))
+    order = {}
+    for policy in (nv.SCHED_FIFO, nv.SCHED_LARGEST_FIRST):
+        log = tmp_path / f"m{policy}.jsonl"
+        with nv.Context(64 << 20, n_streams=1, evaluator=oracle_fn(delay=0.05)) as ctx:
+            ctx.set_schedule_policy(policy)
+            ctx.set_metrics_log(str(log))
+            ids = {name: ctx.create_dataset(ds.coords, ds.y, ds.X) for name, (ds, _, _) in
+                   zip(("small", "mid", "large"), (small, mid, large))}
+            first = ctx.submit(ids["small"], small[1], small[2], batch=4)
+            time.sleep(0.01)
+            jobs = {name: ctx.submit(ids[name], prob[1], prob[2], batch=4)
+                    for name, prob in (("small", small), ("mid", mid), ("large", large))}
+            ctx.poll(first, 3)
+            for name, prob in (("small", small), ("mid", mid), ("large", large)):
+                _same(ctx.poll(jobs[name], 3), _ref(*prob))
+        lines = [json.loads(x) for x in log.read_text().splitlines()][1:]
+        order[policy] = [x["n"] for x in sorted(lines, key=lambda x: x["t_start"])]
+    assert order[nv.SCHED_FIFO] == [20, 35, 50]
+    assert order[nv.SCHED_LARGEST_FIRST] == [50, 35, 20]
+    with nv.Context(64 << 20, n_streams=1, evaluator=oracle_fn()) as ctx:
+        with pytest.raises(nv.PlkError):
+            ctx.set_schedule_policy(7)

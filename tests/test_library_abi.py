@@ -72,7 +72,7 @@ def test_binding_constants_match_header():
     import os
     import re
     hdr = open(os.path.join(os.path.dirname(nv.__file__), os.pardir, "include", "plk.h")).read()
-    defs = dict(re.findall(r"^#define PLK_((?:FLAG|POINT|FAULT)_\w+)\s+(\d+)", hdr, re.M))
+    defs = dict(re.findall(r"^#define PLK_((?:FLAG|POINT|FAULT|SCHED)_\w+)\s+(\d+)", hdr, re.M))
     assert len(defs) >= 10
     for name, value in defs.items():
         assert getattr(nv, name) == int(value), name
