@@ -35,21 +35,24 @@ import time
 import numpy as np
 
 # DRAM traffic model of the dominant mixed-path kernel, k_trail_pipe<5> (the
-# 5-slice trailing update): bytes per launch = A x items + B x items x panels,
-# where items are the half-tile work items of the launch (both column halves of
-# every tile it updates, over all points of the part) and panels the panels
-# each item applies (1, or up to 4 in the data triangle).  A (the C half tile's
-# read-modify-write) and B (the operand slices per panel) are fitted by least
-# squares to dram__bytes_read.sum + dram__bytes_write.sum of every
-# k_trail_pipe<5> launch in one ncu capture (a one-pass metric set) of the
-# small case `python bench.py --precision mixed --n 2000 --batch 148 --steps 1
-# --warmup 1 --no-cpu-baseline --no-e2e`, then evaluated on the bench's own
-# launches (the full-size workload exceeds the capture size rule).  Points that
-# the early verdict stops skip their items, so at full size this is an upper
-# bound.  Valid for the kernel source it was taken on (SHA-256 below), else
-# traffic is null.
-TRAIL_TRAFFIC = {"bytes_per_item": 161520.0, "bytes_per_item_panel": 5654.7, "fit_rel_rms": 0.130,
-                 "sources_sha256": "1dbdd3cbcb40ed073a06c6661909bf881a62e3fdd7fa112c80f7e92770a12780"}
+# 5-slice trailing update), per kind of launch, in bytes per half-tile work
+# item (both column halves of every tile a launch updates, over all points of
+# the part): the data triangle (four panels per item; each operand image is
+# re-read by many items, mostly from L2), one tile column's data rows (the
+# group's earlier panels: every item reads its own operand images, so they
+# come from DRAM: a term per item and panel) and the right-hand-side row (its
+# epilogue moves only M + p rows).  Fitted by least squares to
+# dram__bytes_read.sum + dram__bytes_write.sum of every k_trail_pipe<5> launch
+# in one ncu capture (a one-pass metric set) of the small case
+# `python bench.py --precision mixed --n 2000 --batch 148 --steps 1 --warmup 1
+# --no-cpu-baseline --no-e2e`, then evaluated on the bench's own launches (the
+# full-size workload exceeds the capture-size rule).  Points that the early
+# verdict stops skip their items, so at full size this is an upper bound.
+# Valid for the kernel source it was taken on (SHA-256 below), else traffic is
+# null.
+TRAIL_TRAFFIC = {"tri_item": 184153.5, "col_item": 115898.4, "col_item_panel": 84351.8, "rhs_item": 95822.8,
+                 "fit_rel_rms": 0.083,
+                 "sources_sha256": "610d2856d64f6eafce1bfa8e4e9a93ad34ce7f8fdf6bd369e9c658c1834fc417"}
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
@@ -73,7 +76,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="auto", choices=["auto", "fp64", "mixed"])
-    ap.add_argument("--batch", type=int, default=0, help="omega points per step (default: 1184 = 8 x 148 mixed, 128 fp64)")
+    ap.add_argument("--batch", type=int, default=0, help="omega points per step (default: 1776 = 12 x 148 mixed, 128 fp64)")
     ap.add_argument("--n", type=int, default=4000)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -679,7 +682,7 @@ def trail_kernel_sha256(root):
 
 
 def trail_launches(n, part, TB=128, GP=4):
-    """(items, panels) of every k_trail_pipe<5> launch of the 5-slice pass over
+    """(items, panels, mode) of every k_trail_pipe<5> launch of the 5-slice pass over
     one part of `part` points at n sites: the schedule of launch_mixed_steps
     (panels in groups of GP: before each panel its column's data rows with the
     group's earlier panels, after it the right-hand-side row, after the group
@@ -692,7 +695,7 @@ def trail_launches(n, part, TB=128, GP=4):
         if m <= 0:
             return
         T = m * (m + 1) // 2 if mode == 0 else m
-        out.append((part * T * 2, P))
+        out.append((part * T * 2, P, mode))   # 0: data triangle, 1: one column's data rows, 2: right-hand-side row
     for J0 in range(0, nb, GP):
         G = min(GP, nb - J0)
         Jend = J0 + G
@@ -719,8 +722,15 @@ def trail_traffic(n, B):
     if TRAIL_TRAFFIC["sources_sha256"] is None or trail_kernel_sha256(root) != TRAIL_TRAFFIC["sources_sha256"]:
         return None
     L = [x for c in first_pass_parts(B) for x in trail_launches(n, c)]
-    a, b = TRAIL_TRAFFIC["bytes_per_item"], TRAIL_TRAFFIC["bytes_per_item_panel"]
-    return sum(a * it + b * it * P for it, P in L) / len(L)
+    t = TRAIL_TRAFFIC
+
+    def launch_bytes(it, P, mode):
+        if mode == 0:
+            return t["tri_item"] * it
+        if mode == 1:
+            return t["col_item"] * it + t["col_item_panel"] * it * P
+        return t["rhs_item"] * it
+    return sum(launch_bytes(*x) for x in L) / len(L)
 
 
 def split_pairs(S):
@@ -852,7 +862,7 @@ def main():
         torch.cuda.empty_cache()
         return res
 
-    Bm = args.batch or (1184 if head == "mixed" else 128)   # mixed: 8 x 148 SMs per step, parts of 296
+    Bm = args.batch or (1776 if head == "mixed" else 128)   # mixed: 12 x 148 points per step, parts of 296
     main_res = measure(head, Bm, args.steps, args.warmup, True)
     fp64_res = None
     if head == "mixed":

@@ -595,37 +595,20 @@ static plk_status run_mixed_batch(BatchArgs b, const Layout &L, void *ws, const 
 // over the batch, its a-posteriori bound per point, then (unless
 // PLK_FLAG_NO_RETRY) the fused FP64 kernel on the points whose bound exceeded
 // the tolerance or whose factorisation failed (status bits RETRIED | FP64,
-// err_bound 0).  Deciding the retry set reads the flags back, so this
-// synchronizes the stream once per batch.
-static plk_status run_fused_mixed_batch(BatchArgs b, const Layout &L, void *ws, const double *params_all, int flags,
-                                        double *err_bound, cudaStream_t s) {
+// err_bound 0), gated on the device by the bound's flags: one asynchronous
+// sequence with no host read-back (a CUDA graph with PLK_FLAG_GRAPH).
+static plk_status run_fused_mixed_batch(BatchArgs b, const Layout &L, void *ws, int flags, double *err_bound,
+                                        cudaStream_t s) {
     double *invsum = at<double>(ws, L.off_invsum);
     int *fl = at<int>(ws, L.off_flags);
-    cudaError_t e = launch_fused_df_batch(b, invsum, s);
-    if (e == cudaSuccess) e = launch_mixed_bound(b, FUSED_DF_EPS, kMixedTol, 1, invsum, err_bound, fl, s);
-    if (e != cudaSuccess) return cuda_fail(e, "fused mixed launch");
-    if (flags & PLK_FLAG_NO_RETRY) return PLK_OK;
-    std::vector<int> hf(b.count);
-    e = cudaMemcpyAsync(hf.data(), fl, sizeof(int) * b.count, cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    auto seq = [&]() {
+        cudaError_t e = launch_fused_df_batch(b, invsum, s);
+        if (e == cudaSuccess) e = launch_mixed_bound(b, FUSED_DF_EPS, kMixedTol, 1, invsum, err_bound, fl, s);
+        if (e == cudaSuccess && !(flags & PLK_FLAG_NO_RETRY)) e = launch_fused_fp64_gated(b, fl, err_bound, s);
+        return e;
+    };
+    const cudaError_t e = use_graph(flags) ? launch_as_graph(s, seq) : seq();
     if (e != cudaSuccess) return cuda_fail(e, "fused mixed batch");
-    std::vector<int> idx;
-    for (int w = 0; w < b.count; ++w)
-        if (hf[w]) idx.push_back((int)(b.k0 + w));
-    if (idx.empty()) return PLK_OK;
-    int *d_idx = at<int>(ws, L.off_idx);
-    double *d_par = at<double>(ws, L.off_cparams);
-    e = cudaMemcpyAsync(d_idx, idx.data(), sizeof(int) * idx.size(), cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = launch_gather_params((int)idx.size(), d_idx, params_all, d_par, s);
-    BatchArgs f = b;
-    f.count = (int)idx.size();
-    f.params = d_par;
-    f.out_index = d_idx;
-    f.status_or = PLK_POINT_RETRIED | PLK_POINT_FP64;
-    if (e == cudaSuccess) e = launch_fused_batch(f, s);
-    if (e == cudaSuccess && err_bound) e = launch_scatter_value(f.count, d_idx, 0.0, err_bound, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);   // idx must outlive its copy
-    if (e != cudaSuccess) return cuda_fail(e, "fused fp64 retry");
     return PLK_OK;
 }
 
@@ -670,7 +653,7 @@ static plk_status run_eval(const plk_eval_args *a, int reml, int flags, const La
         b.status = a->status;
         b.timer = timer;
         if (fused && L.mixed) {
-            plk_status st = run_fused_mixed_batch(b, L, ws, a->params, flags, a->err_bound, s);
+            plk_status st = run_fused_mixed_batch(b, L, ws, flags, a->err_bound, s);
             if (st != PLK_OK) return st;
         } else if (fused) {
             e = use_graph(flags) ? launch_as_graph(s, [&]() { return launch_fused_batch(b, s); })
@@ -1070,7 +1053,7 @@ std::string run_item(plk_ctx *c, Job *j, Item &it, cudaStream_t s) {
     cudaStreamWaitEvent(s, j->ready, 0);   // the job's B^T may come from another stream
     std::string err;
     if (use_fused(j->n, L.q, j->opts.flags) && L.mixed) {
-        plk_status st = run_fused_mixed_batch(b, L, it.ws, j->d_params, j->opts.flags, nullptr, s);
+        plk_status st = run_fused_mixed_batch(b, L, it.ws, j->opts.flags, nullptr, s);
         if (st == PLK_OK && cudaStreamSynchronize(s) != cudaSuccess) st = PLK_E_CUDA;
         if (st != PLK_OK) err = plk_last_error();
     } else if (use_fused(j->n, L.q, j->opts.flags)) {

@@ -78,8 +78,10 @@ __global__ void __launch_bounds__(256) k_omega_prep(const double *__restrict__ p
                                                     const double *__restrict__ coords,
                                                     const double *__restrict__ sumlogy, double *__restrict__ oconst,
                                                     double *__restrict__ coordT, double *__restrict__ logdet,
-                                                    int *__restrict__ pstatus, int f32coords) {
+                                                    int *__restrict__ pstatus, int f32coords,
+                                                    const int *__restrict__ gate) {
     const int w = blockIdx.x;
+    if (gate && !gate[w]) return;   // gated pass: only the flagged slots
     const double *om = params + 5 * (int64_t)w;
     const double phix = om[0], kap = om[1], nug = om[2], ratio = om[3], ang = om[4];
     const bool ok = (phix > 0.0) && (kap > 0.0) && (nug >= 0.0) && (ratio > 0.0) &&
@@ -554,7 +556,8 @@ __device__ __forceinline__ double rho_df(double u, double kap, double logc, cons
 template <bool F32TAB, int BPB = 32>
 __global__ void __launch_bounds__(BPB * TAB_NC) k_matern_table(const double *__restrict__ oconst,
                                                                double *__restrict__ tab,
-                                                               const int *__restrict__ owner) {
+                                                               const int *__restrict__ owner,
+                                                               const int *__restrict__ gate = nullptr) {
     // FP64 evaluation: cosh(t_k) - 1 = 2 sinh^2(t_k / 2) and log cosh(kappa t_k);
     // double-float evaluation (F32TAB): cosh(t_k) - 1 as double-float
     __shared__ double E1[F32TAB ? 1 : QNODES];
@@ -567,6 +570,7 @@ __global__ void __launch_bounds__(BPB * TAB_NC) k_matern_table(const double *__r
     __shared__ double TM[TAB_NC][TAB_NC];     // T_k(t) = sum_m TM[k][m] t^m
     const int w = blockIdx.y;
     if (owner && owner[w] != w) return;   // this slot reads another slot's table (same kappa)
+    if (gate && !gate[w]) return;         // gated pass: only the flagged slots
     const double *oc = oconst + OC_N * (int64_t)w;
     const double kap = oc[OC_KAPPA], logc = oc[OC_LOGC];
     const int elo = (int)oc[OC_ELO], ehi = (int)oc[OC_EHI];
@@ -1069,9 +1073,10 @@ __global__ void k_finalize(int count, int64_t k0, int M, int p, int64_t n, int n
                            const double *__restrict__ sumlogy, const double *__restrict__ lambdas,
                            double *logL, double *sigma2, double *beta, double *logdet,
                            double *ssq, int32_t *status, const int *__restrict__ out_index,
-                           int32_t status_or) {
+                           int32_t status_or, const int *__restrict__ gate) {
     const int w = blockIdx.x * blockDim.x + threadIdx.x;
     if (w >= count) return;
+    if (gate && !gate[w]) return;   // gated pass: only the flagged slots
     const int64_t k = out_index ? (int64_t)out_index[w] : k0 + w;
     const double *S = tiles + ((int64_t)w * tpo + tile_index(nb, nb)) * NT;   // -B^T V^-1 B
     int st = pstatus[w];
@@ -1276,7 +1281,7 @@ cudaError_t launch_front(const BatchArgs &b, cudaStream_t s, FrontMode mode, boo
     KernelTimer *timer = b.timer;
     const int f32 = mode == FRONT_DF_FAST ? 1 : 0;
     TIMED(KC_PREP, (k_omega_prep<<<cnt, 256, 0, s>>>(b.params, b.n, b.n_pad, b.coords, b.sumlogy, b.oconst,
-                                                      b.coordT, b.ldv, b.pstatus, f32)));
+                                                      b.coordT, b.ldv, b.pstatus, f32, nullptr)));
     const dim3 tg((TAB_NBUCKET + 31) / 32, cnt), bg((unsigned)b.tpo, cnt);
     if (b.owner) {   // slots with the same kappa share one table
         k_table_owner<<<cnt, 256, 0, s>>>(cnt, b.oconst, b.pstatus, b.owner);
@@ -1346,7 +1351,7 @@ cudaError_t launch_finalize(const BatchArgs &b, cudaStream_t s) {
     TIMED(KC_FINAL, (k_finalize<<<(cnt + 63) / 64, 64, 0, s>>>(
                         cnt, b.k0, b.M, b.p, b.n, b.nb, b.reml, b.tpo, b.tiles, b.ldv, b.pstatus,
                         b.sumlogy, b.lambdas, b.logL, b.sigma2, b.beta, b.logdet, b.ssq, b.status, b.out_index,
-                        b.status_or)));
+                        b.status_or, nullptr)));
     return cudaGetLastError();
 }
 
@@ -1403,9 +1408,11 @@ __global__ void __launch_bounds__(FUSED_THREADS, 1) k_fused_small(int64_t n, int
                                                                const double *__restrict__ tab,
                                                                const double *__restrict__ Bt,
                                                                const int *__restrict__ owner,
-                                                               double *__restrict__ ldv, int *__restrict__ pstatus) {
+                                                               double *__restrict__ ldv, int *__restrict__ pstatus,
+                                                               const int *__restrict__ gate) {
     extern __shared__ double A[];
     const int w = blockIdx.x;
+    if (gate && !gate[w]) return;   // gated pass: only the flagged slots
     const int R = (int)n + q, nn = (int)n;
     const int64_t P = (int64_t)R * (R + 1) / 2;
     double *piv = A + P;   // the n pivots
@@ -1748,9 +1755,41 @@ cudaError_t launch_fused_batch(const BatchArgs &b, cudaStream_t s) {
     if ((e = launch_front(b, s, FRONT_FP64, false)) != cudaSuccess) return e;
     TIMED(KC_FUSED, (k_fused_small<<<b.count, FUSED_THREADS, smem, s>>>(b.n, b.n_pad, b.q, b.nb, b.tpo, b.tiles,
                                                                        b.oconst, b.coordT, b.tab, b.Bt, b.owner,
-                                                                       b.ldv, b.pstatus)));
+                                                                       b.ldv, b.pstatus, nullptr)));
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     return launch_finalize(b, s);
+}
+
+// The FP64 fused evaluation of the slots flagged in gate[w] (set by the
+// double-float pass's bound kernel), in place, with every kernel launched over
+// the whole batch and exiting for the other slots: no host read-back, so the
+// double-float pass and its re-evaluation form one asynchronous sequence (and
+// can be captured in a graph).  Tables are per slot (no sharing by kappa).
+__global__ void k_clear_gated(int count, int64_t k0, const int *__restrict__ gate, double *__restrict__ out) {
+    const int w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (w < count && gate[w]) out[k0 + w] = 0.0;
+}
+
+cudaError_t launch_fused_fp64_gated(const BatchArgs &b, const int *gate, double *err_bound, cudaStream_t s) {
+    const size_t smem = fused_smem_bytes(b.n, b.q);
+    cudaError_t e = cudaFuncSetAttribute(k_fused_small, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    KernelTimer *timer = b.timer;
+    const int cnt = b.count;
+    const int32_t sor = PLK_POINT_RETRIED | PLK_POINT_FP64;
+    TIMED(KC_PREP, (k_omega_prep<<<cnt, 256, 0, s>>>(b.params, b.n, b.n_pad, b.coords, b.sumlogy, b.oconst, b.coordT,
+                                                      b.ldv, b.pstatus, 0, gate)));
+    const dim3 tg8((TAB_NBUCKET + 7) / 8, cnt);
+    TIMED(KC_TABLE, (k_matern_table<false, 8><<<tg8, 8 * TAB_NC, 0, s>>>(b.oconst, b.tab, nullptr, gate)));
+    TIMED(KC_FUSED, (k_fused_small<<<cnt, FUSED_THREADS, smem, s>>>(b.n, b.n_pad, b.q, b.nb, b.tpo, b.tiles, b.oconst,
+                                                                   b.coordT, b.tab, b.Bt, nullptr, b.ldv, b.pstatus,
+                                                                   gate)));
+    TIMED(KC_FINAL, (k_finalize<<<(cnt + 63) / 64, 64, 0, s>>>(cnt, b.k0, b.M, b.p, b.n, b.nb, b.reml, b.tpo, b.tiles,
+                                                                b.ldv, b.pstatus, b.sumlogy, b.lambdas, b.logL,
+                                                                b.sigma2, b.beta, b.logdet, b.ssq, b.status,
+                                                                b.out_index, sor, gate)));
+    if (err_bound) k_clear_gated<<<(cnt + 127) / 128, 128, 0, s>>>(cnt, b.k0, gate, err_bound);
+    return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------

@@ -69,6 +69,9 @@ cudaError_t launch_fused_batch(const BatchArgs &b, cudaStream_t s);
 // the same in double-float FP32 (mixed precision); invsum[w] = sum_j 1/d_j of
 // the pivots (for the a-posteriori bound), 0 for points that failed
 cudaError_t launch_fused_df_batch(const BatchArgs &b, double *invsum, cudaStream_t s);
+// the FP64 fused evaluation of the slots w with gate[w] != 0 (device flags),
+// in place (status bits RETRIED | FP64, err_bound 0), without a host read-back
+cudaError_t launch_fused_fp64_gated(const BatchArgs &b, const int *gate, double *err_bound, cudaStream_t s);
 // relative perturbation of V's entries in the double-float fused Cholesky
 // (bound E = FUSED_DF_EPS (1 + nu^2) sum_j 1 / d_j)
 constexpr double FUSED_DF_EPS = 1.4551915228366852e-11;   // 2^-36
