@@ -469,7 +469,16 @@ __device__ __forceinline__ void df_e1(float x, float &eh, float &el) {
 // e^{-2 kappa t_k} = r^k by repeated double-float products.  Each a(t_k) carries
 // ~2^-48 of the larger of its two parts (<= kappa t_k): ~1e-13 of rho at
 // kappa <= 8.  The stopping rule is that of the FP64 evaluation.
-__device__ __forceinline__ double rho_df(double u, double kap, double logc, const float2 *__restrict__ E1f) {
+// S > 1: the S consecutive lanes sub = 0 .. S - 1 of a group share one node;
+// lane sub sums the terms k = 1 + sub, 1 + sub + S, ... (r^k from r^(1+sub)
+// by products with r^S; the node t = 0 in lane 0), and the partial sums are
+// added in a fixed order by shuffles (every lane of the warp takes part, so
+// the caller calls this in all lanes, with any u > 0 in unused ones); A is
+// the maximum over all nodes, reduced the same way (exact).  All S lanes
+// return the same value.
+template <int S = 1>
+__device__ __forceinline__ double rho_df(double u, double kap, double logc, const float2 *__restrict__ E1f,
+                                         int sub = 0) {
     const bool fixed = u <= TAB_USPLIT;
     const float uh = __double2float_rn(u), ul = __double2float_rn(u - (double)uh);
     const float kh = __double2float_rn(kap), kl = __double2float_rn(kap - (double)kh);
@@ -483,29 +492,37 @@ __device__ __forceinline__ double rho_df(double u, double kap, double logc, cons
     }
     float A = 0.0f;   // a(0) = 0
     if (fixed)
-        for (int k = 1; k < QNODES; ++k) A = fmaxf(A, __fmaf_rn(-uh, E1f[k].x, kh * (float)k * h));
+        for (int k = 1 + sub; k < QNODES; k += S) A = fmaxf(A, __fmaf_rn(-uh, E1f[k].x, kh * (float)k * h));
+    if constexpr (S > 1) {
+#pragma unroll
+        for (int o = 1; o < S; o <<= 1) A = fmaxf(A, __shfl_xor_sync(0xffffffffu, A, o));
+    }
     float rh, rl;   // r = e^{-2 kappa h}
     {
         const float t2 = __fmul_rn(-2.0f * kh, h), t2e = __fmaf_rn(-2.0f * kh, h, -t2);   // exact split
         df_exp(t2, __fmaf_rn(-2.0f * kl, h, t2e), rh, rl);
     }
-    float sh, sl;    // sum: the node t = 0 (weight 1/2, term 2 e^{-A})
-    df_exp(-A, 0.0f, sh, sl);
-    float prev = 2.0f * sh;
-    float qh = 1.0f, ql = 0.0f;   // r^k
+    float sh = 0.0f, sl = 0.0f;   // sum: the node t = 0 (weight 1/2, term 2 e^{-A}) in lane 0
+    if (sub == 0) df_exp(-A, 0.0f, sh, sl);
+    float prev = sub == 0 ? 2.0f * sh : INFINITY;
+    float qh = rh, ql = rl;   // r^k for this lane's next term k = 1 + sub (then + S per term)
+    for (int i = 0; i < sub; ++i) df_mul(qh, ql, rh, rl, qh, ql);
+    float sth = rh, stl = rl;   // r^S
+    for (int i = 1; i < S; ++i) df_mul(sth, stl, rh, rl, sth, stl);
     const int kmax = fixed ? QNODES : 8192;
     bool stop = false;
-    for (int k = 1; k < kmax && !stop; k += 4) {
+    for (int k = 1 + sub; k < kmax && !stop; k += 4 * S) {
         float gh[4], gl[4];
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             gh[i] = gl[i] = 0.0f;
-            if (k + i >= kmax) continue;
-            const float t = (float)(k + i) * h;   // exact
+            const int kk = k + i * S;
+            if (kk >= kmax) continue;
+            const float t = (float)kk * h;   // exact
             float e1h, e1l;
             if (fixed) {
-                e1h = E1f[k + i].x;
-                e1l = E1f[k + i].y;
+                e1h = E1f[kk].x;
+                e1l = E1f[kk].y;
             } else {
                 df_e1(0.5f * t, e1h, e1l);
             }
@@ -521,15 +538,15 @@ __device__ __forceinline__ double rho_df(double u, double kap, double logc, cons
             const float lo = __fadd_rn(__fadd_rn(c1, c2), __fsub_rn(__fmaf_rn(kl, t, kte), pe));
             float xh, xl;
             df_exp(s2, lo, xh, xl);
-            df_mul(qh, ql, rh, rl, qh, ql);   // r^(k+i)
-            float oh, ol;                      // 1 + r^(k+i)
+            float oh, ol;                      // 1 + r^kk
             two_sum_f(1.0f, qh, oh, ol);
             ol = __fadd_rn(ol, ql);
             df_mul(xh, xl, oh, ol, gh[i], gl[i]);
+            df_mul(qh, ql, sth, stl, qh, ql);  // r^(kk + S)
         }
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
-            if (stop || k + i >= kmax) {
+            if (stop || k + i * S >= kmax) {
                 stop = true;
                 continue;
             }
@@ -538,6 +555,17 @@ __device__ __forceinline__ double rho_df(double u, double kap, double logc, cons
             fast_two_sum_f(s, __fadd_rn(e, __fadd_rn(sl, gl[i])), sh, sl);
             if (gh[i] < prev && gh[i] < 1e-18f * sh) stop = true;
             prev = gh[i];
+        }
+    }
+    if constexpr (S > 1) {
+#pragma unroll
+        for (int o = 1; o < S; o <<= 1) {   // lanes (sub, sub ^ o): lower sub first
+            const float oh = __shfl_xor_sync(0xffffffffu, sh, o), ol = __shfl_xor_sync(0xffffffffu, sl, o);
+            const bool low = (sub & o) == 0;
+            const float ah = low ? sh : oh, al = low ? sl : ol, bh = low ? oh : sh, bl = low ? ol : sl;
+            float s, e;
+            two_sum_f(ah, bh, s, e);
+            fast_two_sum_f(s, __fadd_rn(e, __fadd_rn(al, bl)), sh, sl);
         }
     }
     return exp(logc + kap * log(u) - u + (double)A) * (0.5 * (double)h * ((double)sh + (double)sl));
@@ -553,8 +581,8 @@ __device__ __forceinline__ double rho_df(double u, double kap, double logc, cons
 // For u <= TAB_USPLIT the trapezoid nodes are the fixed grid t_k = k QH, whose
 // cosh(t_k) - 1 and log cosh(kappa t_k) are staged in shared memory, so one exp
 // per node remains.
-template <bool F32TAB, int BPB = 32>
-__global__ void __launch_bounds__(BPB * TAB_NC) k_matern_table(const double *__restrict__ oconst,
+template <bool F32TAB, int BPB = 32, int SPLIT = 1>
+__global__ void __launch_bounds__(BPB * TAB_NC * SPLIT) k_matern_table(const double *__restrict__ oconst,
                                                                double *__restrict__ tab,
                                                                const int *__restrict__ owner,
                                                                const int *__restrict__ gate = nullptr) {
@@ -613,11 +641,21 @@ __global__ void __launch_bounds__(BPB * TAB_NC) k_matern_table(const double *__r
         TM[k][m] = (double)TMi[k][m];
     }
     __syncthreads();
-    const int lb = threadIdx.x / TAB_NC, l = threadIdx.x % TAB_NC;
+    // SPLIT > 1 (double-float tables only): SPLIT consecutive lanes per node,
+    // each summing every SPLIT-th trapezoid term (rho_df<SPLIT>); all lanes
+    // call it, unused ones at a dummy argument
+    const int node = threadIdx.x / SPLIT, sub = threadIdx.x % SPLIT;
+    const int lb = node / TAB_NC, l = node % TAB_NC;
     const int bucket = blockIdx.x * BPB + lb;
     const int eb = TAB_ELO + bucket / TAB_S;
     const bool used = bucket < TAB_NBUCKET && eb >= elo && eb < ehi;
-    if (used) {
+    if constexpr (F32TAB && SPLIT > 1) {
+        const int e = TAB_ELO + bucket / TAB_S, j = bucket % TAB_S;
+        const double tl = CT[1][l];
+        const double u = used ? sqrt(ldexp(1.0 + (j + 0.5 * (tl + 1.0)) / TAB_S, e)) : 1.0;
+        const double r = (kap != kap || !(kap > 0.0)) ? nan("") : rho_df<SPLIT>(u, kap, logc, E1f, sub);
+        if (used && sub == 0) F[lb][l] = r;
+    } else if (used) {
         const int e = TAB_ELO + bucket / TAB_S, j = bucket % TAB_S;
         const double tl = CT[1][l];   // cos(pi (l + 1/2) / NC): the Chebyshev node
         const double wv = ldexp(1.0 + (j + 0.5 * (tl + 1.0)) / TAB_S, e);
@@ -656,13 +694,13 @@ __global__ void __launch_bounds__(BPB * TAB_NC) k_matern_table(const double *__r
     __syncthreads();
     // Chebyshev coefficient a_l of the bucket's interpolant (thread l), then the
     // monomial coefficient c_l of t^l (thread l)
-    if (used) {
+    if (used && sub == 0) {
         double s2 = 0.0;
         for (int m = 0; m < TAB_NC; ++m) s2 += F[lb][m] * CT[l][m];
         A[lb][l] = (l == 0 ? 1.0 : 2.0) * s2 / TAB_NC;
     }
     __syncthreads();
-    if (used) {
+    if (used && sub == 0) {
         double c = 0.0;
         for (int k = 0; k < TAB_NC; ++k) c += A[lb][k] * TM[k][l];
         if (F32TAB) {
@@ -1289,7 +1327,7 @@ cudaError_t launch_front(const BatchArgs &b, cudaStream_t s, FrontMode mode, boo
     }
     if (f32 && !build) {   // the fused path: tables spread over more blocks
         const dim3 tg8((TAB_NBUCKET + 7) / 8, cnt);
-        TIMED(KC_TABLE, (k_matern_table<true, 8><<<tg8, 8 * TAB_NC, 0, s>>>(b.oconst, b.tab, b.owner)));
+        TIMED(KC_TABLE, (k_matern_table<true, 8, 4><<<tg8, 8 * TAB_NC * 4, 0, s>>>(b.oconst, b.tab, b.owner)));
     } else if (f32) {
         TIMED(KC_TABLE, (k_matern_table<true><<<tg, 320, 0, s>>>(b.oconst, b.tab, b.owner)));
         if (build)
@@ -1537,8 +1575,8 @@ __global__ void __launch_bounds__(FUSED_THREADS, 1) k_fused_small(int64_t n, int
 // The same fused evaluation in double-float FP32 arithmetic (two floats per
 // value, ~2^-44 per operation; FP32 issues at ~68x the FP64 rate here), for
 // the mixed precision: V from the first pass's double-float build of each
-// entry (rho_entry_df on the double-float table), the Cholesky of the
-// bordered matrix in double-float, log|V| and sum 1/d_j of the pivots in FP64.
+// entry (rho_entry_df on the double-float table), the L D L^T elimination of
+// the bordered matrix in double-float, log|V| and sum 1/d_j of the pivots in FP64.
 // A point whose a-posteriori bound FUSED_DF_EPS (1 + nu^2) sum 1/d_j exceeds
 // the tolerance, or whose factorisation fails, is evaluated again by
 // k_fused_small in FP64.
@@ -1564,6 +1602,29 @@ __device__ __forceinline__ float2 df_sub2(float2 a, float2 x0, float2 y0, float2
     return make_float2(h, l);
 }
 
+// a - x y, normalised
+__device__ __forceinline__ float2 df_sub1(float2 a, float2 x, float2 y) {
+    const float p = __fmul_rn(x.x, y.x);
+    float e = __fmaf_rn(x.x, y.x, -p);
+    e = __fmaf_rn(x.x, y.y, __fmaf_rn(x.y, y.x, e));
+    float s, t;
+    two_sum_f(a.x, -p, s, t);
+    float h, l;
+    fast_two_sum_f(s, __fadd_rn(__fsub_rn(a.y, e), t), h, l);
+    return make_float2(h, l);
+}
+// 1 / d in double-float for d > 0: FP32 reciprocal r0 and one Newton step
+// r0 + r0 (1 - d r0), the residual formed in double-float (1 - d_hi r0 is
+// exact by Sterbenz; ~2^-46 overall)
+__device__ __forceinline__ float2 df_rcp_f(float2 d) {
+    const float r0 = __frcp_rn(d.x);
+    const float p = __fmul_rn(d.x, r0), pe = __fmaf_rn(d.x, r0, -p);
+    const float res = __fsub_rn(__fsub_rn(__fsub_rn(1.0f, p), pe), __fmul_rn(d.y, r0));
+    float h, l;
+    fast_two_sum_f(r0, __fmul_rn(r0, res), h, l);
+    return make_float2(h, l);
+}
+
 __global__ void __launch_bounds__(FUSED_DF_THREADS, 1) k_fused_small_df(int64_t n, int64_t n_pad, int q, int nb,
                                                                      int64_t tpo, double *__restrict__ tiles,
                                                                      const double *__restrict__ oconst,
@@ -1578,7 +1639,6 @@ __global__ void __launch_bounds__(FUSED_DF_THREADS, 1) k_fused_small_df(int64_t 
     const int R = (int)n + q, nn = (int)n;
     const int64_t P = (int64_t)R * (R + 1) / 2;
     float2 *pv = Af + P;   // the n pivots
-    __shared__ int s_fail;
     __shared__ double red[FUSED_DF_THREADS / 32], red2[FUSED_DF_THREADS / 32];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = FUSED_DF_THREADS / 32;
     if (pstatus[w] != PLK_POINT_OK) {   // invalid parameters: the closed form writes NaN
@@ -1614,79 +1674,96 @@ __global__ void __launch_bounds__(FUSED_DF_THREADS, 1) k_fused_small_df(int64_t 
             }
         }
     }
-    if (tid == 0) s_fail = 0;
     __syncthreads();
-    const float2 z = make_float2(0.0f, 0.0f);
-    // two columns per step, as in k_fused_small
-    for (int j = 0; j < nn; j += 2) {
-        const bool two = j + 1 < nn;
-        if (warp == 0) {
-            bool bad = false;
-            for (int c = j; c <= (two ? j + 1 : j) && !bad; ++c) {
-                if (c > j) {
-                    __syncwarp();
-                    const float2 l1 = at(j + 1, j);
-                    for (int i = j + 1 + lane; i < R; i += 32) at(i, j + 1) = df_sub2(at(i, j + 1), at(i, j), l1, z, z);
-                    __syncwarp();
-                }
-                const float2 d = at(c, c);
-                const bool ok = d.x > 0.0f && d.x < INFINITY;
-                // y = 1 / sqrt(d): FP32 estimate y0, one Newton step with the
-                // residual 1 - d y0^2 formed in double-float (~2^-46)
-                float yh = 0.0f, yl = 0.0f;
-                if (ok) {
-                    const float y0 = rsqrtf(d.x);
-                    const float th = __fmul_rn(y0, y0), tl = __fmaf_rn(y0, y0, -th);
-                    const float uh = __fmul_rn(d.x, th);
-                    float ue = __fmaf_rn(d.x, th, -uh);
-                    ue = __fmaf_rn(d.x, tl, __fmaf_rn(d.y, th, ue));
-                    const float res = __fsub_rn(__fsub_rn(1.0f, uh), ue);
-                    fast_two_sum_f(y0, __fmul_rn(0.5f * y0, res), yh, yl);
-                }
-                __syncwarp();
-                if (lane == 0) {
-                    pv[c] = d;
-                    if (ok) {
-                        float lh, ll;
-                        df_mul_f(d.x, d.y, yh, yl, lh, ll);
-                        at(c, c) = make_float2(lh, ll);
-                    } else {
-                        s_fail = 1;
-                    }
-                }
-                bad = !ok;
-                if (ok)
-                    for (int i = c + 1 + lane; i < R; i += 32) {
-                        float2 &v = at(i, c);
-                        float h, l;
-                        df_mul_f(v.x, v.y, yh, yl, h, l);
-                        v = make_float2(h, l);
-                    }
-            }
+    // L D L^T elimination of the first n columns, right-looking, two columns
+    // (c, c + 1) per step and no square roots.  The pivots d_c are the squares
+    // of the Cholesky factor's diagonal and the last q x q block ends as
+    // -B^T V^-1 B, all that the closed form needs (L itself is never formed).
+    // Columns c and c + 1 are read from contiguous copies that the owners of
+    // their rows wrote in the previous step.  Every thread forms the 2 x 2
+    // pivot block itself (a few FP32 operations, identical in all threads):
+    //   d_c, m = A(c+1, c) / d_c, d_{c+1} = A(c+1, c+1) - m A(c+1, c);
+    // then (a) column c + 1 takes column c, A'(i, c+1) = A(i, c+1) - m A(i, c),
+    // one row per thread, and (b) after a barrier every entry takes both,
+    //   A(i, k) -= (A(i, c) / d_c) A(k, c) + (A'(i, c+1) / d_{c+1}) A'(k, c+1),
+    // the right-looking Cholesky's two updates in order, in L D L^T form.  Two
+    // barriers per two columns; no warp factors a panel while the others wait,
+    // and a failed pivot ends the loop in all threads at the same step.
+    float2 *cb = pv + nn;   // [cur c | cur c+1 | next c | next c+1 | A'(., c+1)], R entries each
+    for (int k = tid; k < R; k += FUSED_DF_THREADS) {
+        const float2 *rowk = Af + (int64_t)k * (k + 1) / 2;
+        cb[k] = rowk[0];
+        if (k >= 1) cb[R + k] = rowk[1];
+    }
+    __syncthreads();
+    bool fail = false;
+    auto bad = [](float2 d) { return !(d.x > 0.0f && d.x < INFINITY); };
+    int par = 0;   // which pair of copies holds the current columns
+    int c = 0;
+    for (; c + 1 < nn; c += 2, par ^= 1) {
+        const float2 *c0 = cb + (2 * par) * R, *c1 = c0 + R;
+        float2 *n0 = cb + (2 * (par ^ 1)) * R, *n1 = n0 + R, *c1p = cb + 4 * R;
+        const float2 d0 = c0[c];
+        if (bad(d0)) {
+            fail = true;
+            break;
         }
+        const float2 r0 = df_rcp_f(d0);
+        float2 m;
+        df_mul_f(c0[c + 1].x, c0[c + 1].y, r0.x, r0.y, m.x, m.y);
+        const float2 d1 = df_sub1(c1[c + 1], m, c0[c + 1]);
+        if (bad(d1)) {
+            fail = true;
+            break;
+        }
+        const float2 r1 = df_rcp_f(d1);
+        if (tid == 0) {
+            pv[c] = d0;
+            pv[c + 1] = d1;
+        }
+        for (int i = c + 2 + tid; i < R; i += FUSED_DF_THREADS) c1p[i] = df_sub1(c1[i], m, c0[i]);
         __syncthreads();
-        if (s_fail) break;
-        const int k0 = two ? j + 2 : j + 1;
-        for (int i = k0 + warp; i < R; i += nw) {
+        for (int i = c + 2 + warp; i < R; i += nw) {
             float2 *row = Af + (int64_t)i * (i + 1) / 2;
-            const float2 a0 = row[j], a1 = two ? row[j + 1] : z;
-            int k = k0 + lane;
+            float2 s0, s1;
+            df_mul_f(c0[i].x, c0[i].y, r0.x, r0.y, s0.x, s0.y);
+            df_mul_f(c1p[i].x, c1p[i].y, r1.x, r1.y, s1.x, s1.y);
+            int k = c + 2 + lane;
+            if (k <= i) {   // the first entry: column c + 2 or c + 3, copied for the next step
+                const float2 v = df_sub2(row[k], s0, c0[k], s1, c1p[k]);
+                row[k] = v;
+                if (k == c + 2) n0[i] = v;
+                else if (k == c + 3) n1[i] = v;
+                k += 32;
+            }
             for (; k + 32 <= i; k += 64) {   // two independent entries per iteration
-                const float2 *rk = Af + (int64_t)k * (k + 1) / 2 + j;
-                const float2 *rk2 = Af + (int64_t)(k + 32) * (k + 33) / 2 + j;
-                const float2 u = df_sub2(row[k], a0, rk[0], a1, two ? rk[1] : z);
-                const float2 v = df_sub2(row[k + 32], a0, rk2[0], a1, two ? rk2[1] : z);
+                const float2 u = df_sub2(row[k], s0, c0[k], s1, c1p[k]);
+                const float2 v = df_sub2(row[k + 32], s0, c0[k + 32], s1, c1p[k + 32]);
                 row[k] = u;
                 row[k + 32] = v;
             }
-            if (k <= i) {
-                const float2 *rk = Af + (int64_t)k * (k + 1) / 2 + j;
-                row[k] = df_sub2(row[k], a0, rk[0], a1, two ? rk[1] : z);
-            }
+            if (k <= i) row[k] = df_sub2(row[k], s0, c0[k], s1, c1p[k]);
         }
         __syncthreads();
     }
-    if (s_fail) {
+    if (!fail && c < nn) {   // odd n: the last column alone
+        const float2 *c0 = cb + (2 * par) * R;
+        const float2 d0 = c0[c];
+        if (bad(d0)) {
+            fail = true;
+        } else {
+            const float2 r0 = df_rcp_f(d0);
+            if (tid == 0) pv[c] = d0;
+            for (int i = c + 1 + warp; i < R; i += nw) {
+                float2 *row = Af + (int64_t)i * (i + 1) / 2;
+                float2 s0;
+                df_mul_f(c0[i].x, c0[i].y, r0.x, r0.y, s0.x, s0.y);
+                for (int k = c + 1 + lane; k <= i; k += 32) row[k] = df_sub1(row[k], s0, c0[k]);
+            }
+            __syncthreads();
+        }
+    }
+    if (fail) {
         if (tid == 0) {
             pstatus[w] = PLK_POINT_NOT_PD;
             invsum[w] = 0.0;
@@ -1740,9 +1817,9 @@ cudaError_t launch_fused_df_batch(const BatchArgs &b, double *invsum, cudaStream
     return launch_finalize(b, s);
 }
 
-size_t fused_smem_bytes(int64_t n, int q) {
+size_t fused_smem_bytes(int64_t n, int q) {   // packed matrix, n pivots, five column copies
     const int64_t R = n + q;
-    return sizeof(double) * (size_t)(R * (R + 1) / 2 + n);
+    return sizeof(double) * (size_t)(R * (R + 1) / 2 + n + 5 * R);
 }
 
 bool fused_applies(int64_t n, int q) { return n + q <= FUSED_MAX_R; }
