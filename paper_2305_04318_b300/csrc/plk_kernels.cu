@@ -87,14 +87,22 @@ __global__ void __launch_bounds__(256) k_omega_prep(const double *__restrict__ p
     const bool ok = (phix > 0.0) && (kap > 0.0) && (nug >= 0.0) && (ratio > 0.0) &&
                     isfinite(phix) && isfinite(kap) && isfinite(nug) && isfinite(ratio) &&
                     isfinite(ang);
-    // the point's transcendentals once per block (FP64 issues at 1/68 of FP32)
-    __shared__ double sc[5];
-    if (threadIdx.x == 0) {
-        sc[0] = cos(ang);
-        sc[1] = sin(ang);
-        sc[2] = sqrt(8.0 * kap);
-        sc[3] = sc[2] / phix;
-        sc[4] = sc[2] * ratio / phix;
+    // the point's transcendentals once per block, one per warp 0..3 (one per
+    // SM sub-partition: an FP64 warp instruction holds its sub-partition's
+    // FP64 pipe for 64 cycles, so four short chains run side by side)
+    __shared__ double sc[6];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) {
+        if (warp == 0) sc[0] = cos(ang);
+        else if (warp == 1) sc[1] = sin(ang);
+        else if (warp == 2) {
+            sc[2] = sqrt(8.0 * kap);
+            const double iphi = 1.0 / phix;
+            sc[3] = sc[2] * iphi;
+            sc[4] = sc[2] * ratio * iphi;
+        } else if (warp == 3) {
+            sc[5] = (1.0 - kap) * 0.69314718055994530942 - lgamma(kap);
+        }
     }
     __syncthreads();
     const double c = sc[0], s = sc[1], s8k = sc[2], ia = sc[3], ib = sc[4];
@@ -102,7 +110,7 @@ __global__ void __launch_bounds__(256) k_omega_prep(const double *__restrict__ p
         double *oc = oconst + OC_N * (int64_t)w;
         oc[OC_KAPPA] = kap;
         oc[OC_NUG] = nug;
-        oc[OC_LOGC] = (1.0 - kap) * 0.69314718055994530942 - lgamma(kap);
+        oc[OC_LOGC] = sc[5];
         oc[OC_S8K] = s8k;
         oc[OC_COS] = c;
         oc[OC_SIN] = s;
@@ -117,18 +125,20 @@ __global__ void __launch_bounds__(256) k_omega_prep(const double *__restrict__ p
     float *af = reinterpret_cast<float *>(a);
     // bounding box of the transformed sites: w = |a_i - a_j|^2 + |b_i - b_j|^2 is
     // at most its squared diagonal, and at least min(ia, ib)^2 times the
-    // smallest squared site distance (the rotation keeps lengths)
-    double alo = INFINITY, ahi = -INFINITY, blo = INFINITY, bhi = -INFINITY;
+    // smallest squared site distance (the rotation keeps lengths).  The box is
+    // reduced in FP32 with its edges rounded outwards (it only chooses table
+    // octaves, with a margin).
+    float alo = INFINITY, ahi = -INFINITY, blo = INFINITY, bhi = -INFINITY;
     for (int64_t i = threadIdx.x; i < n_pad; i += blockDim.x) {
         double ai = 0.0, bi = 0.0;
         if (i < n && ok) {
             const double x = coords[2 * i], yv = coords[2 * i + 1];
             ai = (c * x - s * yv) * ia;
             bi = (s * x + c * yv) * ib;
-            alo = fmin(alo, ai);
-            ahi = fmax(ahi, ai);
-            blo = fmin(blo, bi);
-            bhi = fmax(bhi, bi);
+            alo = fminf(alo, __double2float_rd(ai));
+            ahi = fmaxf(ahi, __double2float_ru(ai));
+            blo = fminf(blo, __double2float_rd(bi));
+            bhi = fmaxf(bhi, __double2float_ru(bi));
         }
         if (f32coords) {
             const float ah = __double2float_rn(ai), bh = __double2float_rn(bi);
@@ -141,14 +151,13 @@ __global__ void __launch_bounds__(256) k_omega_prep(const double *__restrict__ p
             b[i] = bi;
         }
     }
-    __shared__ double red[4][8];
+    __shared__ float red[4][8];
     for (int o = 16; o > 0; o >>= 1) {
-        alo = fmin(alo, __shfl_xor_sync(0xffffffffu, alo, o));
-        ahi = fmax(ahi, __shfl_xor_sync(0xffffffffu, ahi, o));
-        blo = fmin(blo, __shfl_xor_sync(0xffffffffu, blo, o));
-        bhi = fmax(bhi, __shfl_xor_sync(0xffffffffu, bhi, o));
+        alo = fminf(alo, __shfl_xor_sync(0xffffffffu, alo, o));
+        ahi = fmaxf(ahi, __shfl_xor_sync(0xffffffffu, ahi, o));
+        blo = fminf(blo, __shfl_xor_sync(0xffffffffu, blo, o));
+        bhi = fmaxf(bhi, __shfl_xor_sync(0xffffffffu, bhi, o));
     }
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (lane == 0) {
         red[0][warp] = alo;
         red[1][warp] = ahi;
@@ -158,14 +167,14 @@ __global__ void __launch_bounds__(256) k_omega_prep(const double *__restrict__ p
     __syncthreads();
     if (threadIdx.x == 0) {
         for (int q = 1; q < (int)(blockDim.x >> 5); ++q) {
-            alo = fmin(alo, red[0][q]);
-            ahi = fmax(ahi, red[1][q]);
-            blo = fmin(blo, red[2][q]);
-            bhi = fmax(bhi, red[3][q]);
+            alo = fminf(alo, red[0][q]);
+            ahi = fmaxf(ahi, red[1][q]);
+            blo = fminf(blo, red[2][q]);
+            bhi = fmaxf(bhi, red[3][q]);
         }
         int elo = TAB_ELO, ehi = TAB_EHI;
         if (ok && n > 1) {
-            const double da = ahi - alo, db = bhi - blo;
+            const double da = (double)ahi - (double)alo, db = (double)bhi - (double)blo;
             const double whi = da * da + db * db;
             const double sc = fmin(ia, ib);
             const double wlo = sc * sc * sumlogy[1];
@@ -469,28 +478,29 @@ __device__ __forceinline__ void df_e1(float x, float &eh, float &el) {
 // e^{-2 kappa t_k} = r^k by repeated double-float products.  Each a(t_k) carries
 // ~2^-48 of the larger of its two parts (<= kappa t_k): ~1e-13 of rho at
 // kappa <= 8.  The stopping rule is that of the FP64 evaluation.
+// The trapezoid step: QH on the fixed grid (u <= TAB_USPLIT), else the power of
+// two at or below min(0.1, 0.45 / sqrt(u)).
+__device__ __forceinline__ float rho_df_step(float uh) {
+    if (uh <= (float)TAB_USPLIT) return (float)QH;
+    int ex;
+    frexpf(fminf(0.1f, 0.45f * rsqrtf(uh)), &ex);   // value in [2^(ex-1), 2^ex)
+    return __int_as_float((ex - 1 + 127) << 23);
+}
+
+// The scaled double-float trapezoid sum sum_k w_k e^{a(t_k) - A} (1 + r^k) of
+// one node (u = uh + ul, kappa = kh + kl, step h), and its offset A.
 // S > 1: the S consecutive lanes sub = 0 .. S - 1 of a group share one node;
 // lane sub sums the terms k = 1 + sub, 1 + sub + S, ... (r^k from r^(1+sub)
 // by products with r^S; the node t = 0 in lane 0), and the partial sums are
 // added in a fixed order by shuffles (every lane of the warp takes part, so
-// the caller calls this in all lanes, with any u > 0 in unused ones); A is
-// the maximum over all nodes, reduced the same way (exact).  All S lanes
-// return the same value.
+// the caller calls this in all lanes, with any u in (0, TAB_USPLIT] in unused
+// ones); A is the maximum over all nodes, reduced the same way (exact).  All S
+// lanes return the same sum and A.
 template <int S = 1>
-__device__ __forceinline__ double rho_df(double u, double kap, double logc, const float2 *__restrict__ E1f,
-                                         int sub = 0) {
-    const bool fixed = u <= TAB_USPLIT;
-    const float uh = __double2float_rn(u), ul = __double2float_rn(u - (double)uh);
-    const float kh = __double2float_rn(kap), kl = __double2float_rn(kap - (double)kh);
-    float h;
-    if (fixed) {
-        h = (float)QH;
-    } else {
-        int ex;
-        frexpf(fminf(0.1f, 0.45f * rsqrtf(uh)), &ex);   // value in [2^(ex-1), 2^ex)
-        h = __int_as_float((ex - 1 + 127) << 23);
-    }
-    float A = 0.0f;   // a(0) = 0
+__device__ __forceinline__ float2 rho_df_sum(float uh, float ul, float kh, float kl, float h,
+                                             const float2 *__restrict__ E1f, int sub, float &A) {
+    const bool fixed = uh <= (float)TAB_USPLIT;
+    A = 0.0f;   // a(0) = 0
     if (fixed)
         for (int k = 1 + sub; k < QNODES; k += S) A = fmaxf(A, __fmaf_rn(-uh, E1f[k].x, kh * (float)k * h));
     if constexpr (S > 1) {
@@ -568,34 +578,57 @@ __device__ __forceinline__ double rho_df(double u, double kap, double logc, cons
             fast_two_sum_f(s, __fadd_rn(e, __fadd_rn(al, bl)), sh, sl);
         }
     }
-    return exp(logc + kap * log(u) - u + (double)A) * (0.5 * (double)h * ((double)sh + (double)sl));
+    return make_float2(sh, sl);
 }
 
-// Table builder: one block of BPB x TAB_NC threads = BPB sub-intervals x
-// TAB_NC Chebyshev nodes (BPB = 32; 8 for the fused small-n path, whose
-// batches often share one table: four times the blocks per table).
-// F32TAB writes each sub-interval's coefficients as TAB_F32 floats instead of
-// TAB_NC doubles: c_0..c_3 as double-float pairs, c_4..c_9 rounded to FP32
-// (the layout k_build_f32 reads; it fits in the same per-point region), and
-// sums the trapezoid rules in double-float arithmetic (rho_df).
+// rho(u) = c_kappa u^kappa e^{-u} e^A (h / 2) sum (FP64 from here)
+__device__ __forceinline__ double rho_df_finish(double u, double kap, double logc, float A, float h, float2 sum) {
+    return exp(logc + kap * log(u) - u + (double)A) * (0.5 * (double)h * ((double)sum.x + (double)sum.y));
+}
+
+__device__ __forceinline__ double rho_df(double u, double kap, double logc, const float2 *__restrict__ E1f) {
+    const float uh = __double2float_rn(u), ul = __double2float_rn(u - (double)uh);
+    const float kh = __double2float_rn(kap), kl = __double2float_rn(kap - (double)kh);
+    const float h = rho_df_step(uh);
+    float A;
+    const float2 sum = rho_df_sum<1>(uh, ul, kh, kl, h, E1f, 0, A);
+    return rho_df_finish(u, kap, logc, A, h, sum);
+}
+
+#include "plk_quad_consts.inc"   // QUAD_E1, QUAD_E1F_HI/LO, QUAD_CT, QUAD_TM
+
+// Table builder: one block per BPB sub-intervals (buckets) of a slot's table,
+// TAB_NC Chebyshev nodes each (BPB = 32 for the tiled paths; fewer for the
+// fused small-n path, whose batches often share one table: more blocks per
+// table).  F32TAB writes each sub-interval's coefficients as TAB_F32 floats
+// instead of TAB_NC doubles: c_0..c_3 as double-float pairs, c_4..c_9 rounded
+// to FP32 (the layout k_build_f32 reads; it fits in the same per-point
+// region), and sums the trapezoid rules in double-float arithmetic.
 // For u <= TAB_USPLIT the trapezoid nodes are the fixed grid t_k = k QH, whose
-// cosh(t_k) - 1 and log cosh(kappa t_k) are staged in shared memory, so one exp
-// per node remains.
+// cosh(t_k) - 1 (QUAD_E1, kappa-independent, correctly rounded constants) and
+// log cosh(kappa t_k) are staged in shared memory, so one exp per node remains.
+// SPLIT > 1 (double-float tables): SPLIT consecutive lanes per node share its
+// trapezoid sum (rho_df_sum<SPLIT>); the FP64 steps around it (the node u,
+// the final scaling, the Chebyshev fit) run in BPB x TAB_NC threads only, in
+// separate phases, since an FP64 warp instruction costs the same issue time
+// with one lane active as with 32.
 template <bool F32TAB, int BPB = 32, int SPLIT = 1>
 __global__ void __launch_bounds__(BPB * TAB_NC * SPLIT) k_matern_table(const double *__restrict__ oconst,
                                                                double *__restrict__ tab,
                                                                const int *__restrict__ owner,
                                                                const int *__restrict__ gate = nullptr) {
-    // FP64 evaluation: cosh(t_k) - 1 = 2 sinh^2(t_k / 2) and log cosh(kappa t_k);
-    // double-float evaluation (F32TAB): cosh(t_k) - 1 as double-float
-    __shared__ double E1[F32TAB ? 1 : QNODES];
-    __shared__ double L2[F32TAB ? 1 : QNODES];
-    __shared__ float2 E1f[F32TAB ? QNODES : 1];
-    __shared__ int TMi[TAB_NC][TAB_NC];
-    __shared__ double F[BPB][TAB_NC];
-    __shared__ double A[BPB][TAB_NC];         // Chebyshev coefficients per bucket
-    __shared__ double CT[TAB_NC][TAB_NC];     // cos(pi k (m + 1/2) / NC)
-    __shared__ double TM[TAB_NC][TAB_NC];     // T_k(t) = sum_m TM[k][m] t^m
+    static_assert(SPLIT == 1 || F32TAB, "lane-split sums are double-float only");
+    constexpr int NN = BPB * TAB_NC;   // nodes per block
+    __shared__ double E1[F32TAB ? 1 : QNODES];   // FP64: cosh(t_k) - 1
+    __shared__ double L2[F32TAB ? 1 : QNODES];   // FP64: log cosh(kappa t_k)
+    __shared__ float2 E1f[F32TAB ? QNODES : 1];  // double-float: cosh(t_k) - 1
+    __shared__ double F[NN];
+    __shared__ double Ach[NN];                   // Chebyshev coefficients per bucket
+    __shared__ double CT[TAB_NC * TAB_NC];       // cos(pi k (m + 1/2) / NC)
+    __shared__ double TM[TAB_NC * TAB_NC];       // T_k(t) = sum_m TM[k][m] t^m
+    __shared__ double Us[SPLIT > 1 ? NN : 1];    // SPLIT > 1: node u, partial results
+    __shared__ float2 Ss[SPLIT > 1 ? NN : 1];
+    __shared__ float As[SPLIT > 1 ? NN : 1];
     const int w = blockIdx.y;
     if (owner && owner[w] != w) return;   // this slot reads another slot's table (same kappa)
     if (gate && !gate[w]) return;         // gated pass: only the flagged slots
@@ -607,102 +640,98 @@ __global__ void __launch_bounds__(BPB * TAB_NC * SPLIT) k_matern_table(const dou
         const int e0 = TAB_ELO + (bx * BPB) / TAB_S, e1 = TAB_ELO + (bx * BPB + BPB - 1) / TAB_S;
         if (e1 < elo || e0 >= ehi) return;   // none of them is read
     }
-    const double PI = 3.14159265358979323846;
+    const bool kap_ok = !(kap != kap) && kap > 0.0;
     for (int k = threadIdx.x; k < QNODES; k += blockDim.x) {
         if constexpr (F32TAB) {
-            // one FP64 sinh per node (kappa-independent; ~2^-48 once split,
-            // where df_e1 gives ~2^-44 and this term multiplies u)
-            const double sh = sinh(0.5 * k * QH);
-            const double e1 = 2.0 * sh * sh;
-            const float eh = __double2float_rn(e1);
-            E1f[k] = make_float2(eh, __double2float_rn(e1 - (double)eh));
+            E1f[k] = make_float2(QUAD_E1F_HI[k], QUAD_E1F_LO[k]);
         } else {
-            const double t = k * QH;
-            const double sh = sinh(0.5 * t);
-            E1[k] = 2.0 * sh * sh;
-            const double kt = kap * t;
+            E1[k] = QUAD_E1[k];
+            const double kt = kap * (k * QH);
             L2[k] = kt + log1p(exp(-2.0 * kt)) - 0.69314718055994530942;
         }
     }
     for (int t = threadIdx.x; t < TAB_NC * TAB_NC; t += blockDim.x) {
-        const int k = t / TAB_NC, m = t % TAB_NC;
-        CT[k][m] = cos(PI * k * (m + 0.5) / TAB_NC);
+        CT[t] = QUAD_CT[t];
+        TM[t] = (double)QUAD_TM[t];
     }
-    if (threadIdx.x == 0) {   // T_0 = 1, T_1 = t, T_k = 2 t T_{k-1} - T_{k-2} (small integers)
-        for (int k = 0; k < TAB_NC; ++k)
-            for (int m = 0; m < TAB_NC; ++m)
-                TMi[k][m] = k == 0 ? (m == 0 ? 1 : 0)
-                          : k == 1 ? (m == 1 ? 1 : 0)
-                                   : (m > 0 ? 2 * TMi[k - 1][m - 1] : 0) - TMi[k - 2][m];
-    }
-    __syncthreads();
-    for (int t = threadIdx.x; t < TAB_NC * TAB_NC; t += blockDim.x) {
-        const int k = t / TAB_NC, m = t % TAB_NC;
-        TM[k][m] = (double)TMi[k][m];
-    }
-    __syncthreads();
-    // SPLIT > 1 (double-float tables only): SPLIT consecutive lanes per node,
-    // each summing every SPLIT-th trapezoid term (rho_df<SPLIT>); all lanes
-    // call it, unused ones at a dummy argument
-    const int node = threadIdx.x / SPLIT, sub = threadIdx.x % SPLIT;
-    const int lb = node / TAB_NC, l = node % TAB_NC;
+    // node nd = (bucket lb, Chebyshev node l): u = sqrt(w) at the node
+    const int nd = threadIdx.x, lb = nd / TAB_NC, l = nd % TAB_NC;
     const int bucket = blockIdx.x * BPB + lb;
     const int eb = TAB_ELO + bucket / TAB_S;
-    const bool used = bucket < TAB_NBUCKET && eb >= elo && eb < ehi;
-    if constexpr (F32TAB && SPLIT > 1) {
+    const bool used = nd < NN && bucket < TAB_NBUCKET && eb >= elo && eb < ehi;
+    auto node_u = [&]() {
         const int e = TAB_ELO + bucket / TAB_S, j = bucket % TAB_S;
-        const double tl = CT[1][l];
-        const double u = used ? sqrt(ldexp(1.0 + (j + 0.5 * (tl + 1.0)) / TAB_S, e)) : 1.0;
-        const double r = (kap != kap || !(kap > 0.0)) ? nan("") : rho_df<SPLIT>(u, kap, logc, E1f, sub);
-        if (used && sub == 0) F[lb][l] = r;
-    } else if (used) {
-        const int e = TAB_ELO + bucket / TAB_S, j = bucket % TAB_S;
-        const double tl = CT[1][l];   // cos(pi (l + 1/2) / NC): the Chebyshev node
-        const double wv = ldexp(1.0 + (j + 0.5 * (tl + 1.0)) / TAB_S, e);
-        const double u = sqrt(wv);
-        double r;
-        if (kap != kap || !(kap > 0.0)) {
-            r = nan("");
-        } else if (F32TAB) {
-            r = rho_df(u, kap, logc, E1f);
-        } else if (u <= TAB_USPLIT) {
-            // the terms of four nodes are computed ahead (independent exps),
-            // then added in order with the same stopping rule
-            double sum = 0.5, prev = 1.0;
-            bool stop = false;
-            for (int k = 1; k < QNODES && !stop; k += 4) {
-                double g[4];
-#pragma unroll
-                for (int i = 0; i < 4; ++i) g[i] = (k + i < QNODES) ? exp(L2[k + i] - u * E1[k + i]) : 0.0;
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    if (stop || k + i >= QNODES) {
-                        stop = true;
-                        continue;
-                    }
-                    sum += g[i];
-                    if (g[i] < prev && g[i] < 1e-18 * sum) stop = true;
-                    prev = g[i];
-                }
+        const double tl = QUAD_CT[TAB_NC + l];   // cos(pi (l + 1/2) / NC): the Chebyshev node
+        return sqrt(ldexp(1.0 + (j + 0.5 * (tl + 1.0)) / TAB_S, e));
+    };
+    if constexpr (SPLIT > 1) {
+        if (nd < NN) Us[nd] = used ? node_u() : 1.0;   // unused: any u on the fixed grid
+        __syncthreads();
+        if (kap_ok) {   // block-uniform: every lane reaches the shuffles
+            const int node = threadIdx.x / SPLIT, sub = threadIdx.x % SPLIT;
+            const double u = Us[node];
+            const float uh = __double2float_rn(u), ul = __double2float_rn(u - (double)uh);
+            const float kh = __double2float_rn(kap), kl = __double2float_rn(kap - (double)kh);
+            float Av;
+            const float2 sum = rho_df_sum<SPLIT>(uh, ul, kh, kl, rho_df_step(uh), E1f, sub, Av);
+            if (sub == 0) {
+                Ss[node] = sum;
+                As[node] = Av;
             }
-            r = exp(logc + kap * log(u) - u) * (QH * sum);
-        } else {
-            r = rho_integral(u, kap, logc);
         }
-        F[lb][l] = r;
+        __syncthreads();
+        if (used) {
+            const double u = Us[nd];
+            F[nd] = kap_ok ? rho_df_finish(u, kap, logc, As[nd], rho_df_step(__double2float_rn(u)), Ss[nd]) : nan("");
+        }
+    } else {
+        __syncthreads();
+        if (used) {
+            const double u = node_u();
+            double r;
+            if (!kap_ok) {
+                r = nan("");
+            } else if (F32TAB) {
+                r = rho_df(u, kap, logc, E1f);
+            } else if (u <= TAB_USPLIT) {
+                // the terms of four nodes are computed ahead (independent exps),
+                // then added in order with the same stopping rule
+                double sum = 0.5, prev = 1.0;
+                bool stop = false;
+                for (int k = 1; k < QNODES && !stop; k += 4) {
+                    double g[4];
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) g[i] = (k + i < QNODES) ? exp(L2[k + i] - u * E1[k + i]) : 0.0;
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        if (stop || k + i >= QNODES) {
+                            stop = true;
+                            continue;
+                        }
+                        sum += g[i];
+                        if (g[i] < prev && g[i] < 1e-18 * sum) stop = true;
+                        prev = g[i];
+                    }
+                }
+                r = exp(logc + kap * log(u) - u) * (QH * sum);
+            } else {
+                r = rho_integral(u, kap, logc);
+            }
+            F[nd] = r;
+        }
     }
     __syncthreads();
     // Chebyshev coefficient a_l of the bucket's interpolant (thread l), then the
     // monomial coefficient c_l of t^l (thread l)
-    if (used && sub == 0) {
+    if (used) {
         double s2 = 0.0;
-        for (int m = 0; m < TAB_NC; ++m) s2 += F[lb][m] * CT[l][m];
-        A[lb][l] = (l == 0 ? 1.0 : 2.0) * s2 / TAB_NC;
+        for (int m = 0; m < TAB_NC; ++m) s2 += F[lb * TAB_NC + m] * CT[l * TAB_NC + m];
+        Ach[nd] = (l == 0 ? 1.0 : 2.0) * s2 / TAB_NC;
     }
     __syncthreads();
-    if (used && sub == 0) {
+    if (used) {
         double c = 0.0;
-        for (int k = 0; k < TAB_NC; ++k) c += A[lb][k] * TM[k][l];
+        for (int k = 0; k < TAB_NC; ++k) c += Ach[lb * TAB_NC + k] * TM[k * TAB_NC + l];
         if (F32TAB) {
             float *dst = reinterpret_cast<float *>(tab + (int64_t)w * TAB_SIZE) + (int64_t)bucket * TAB_F32;
             if (l < TAB_DF) {
@@ -1119,12 +1148,20 @@ __global__ void k_finalize(int count, int64_t k0, int M, int p, int64_t n, int n
     const double *S = tiles + ((int64_t)w * tpo + tile_index(nb, nb)) * NT;   // -B^T V^-1 B
     int st = pstatus[w];
     const double NaN = nan("");
+    // One thread per point: every FP64 instruction here holds its warp's
+    // sub-partition pipe for 64 cycles whatever the active lanes, so the chain
+    // is kept short: 1 / l_jj = rsqrt(d_jj) once per pivot, multiplications
+    // instead of divisions, and log|X^T V^-1 X| = log of the pivots' product
+    // (renormalised by frexp) instead of p logs.
     double Q[16 * 16];
+    double il[16];   // 1 / l_jj
     double cv[16], bv[16];
     double ldx = NaN;
     if (st == PLK_POINT_OK) {
         for (int a = 0; a < p; ++a)
             for (int b = 0; b <= a; ++b) Q[a * p + b] = -S[(M + a) * TB + (M + b)];
+        double prod = 1.0;
+        int pex = 0;
         for (int jj = 0; jj < p && st == PLK_POINT_OK; ++jj) {
             double d = Q[jj * p + jj];
             for (int kk = 0; kk < jj; ++kk) d -= Q[jj * p + kk] * Q[jj * p + kk];
@@ -1132,18 +1169,19 @@ __global__ void k_finalize(int count, int64_t k0, int M, int p, int64_t n, int n
                 st = PLK_POINT_NOT_PD;
                 break;
             }
-            const double l = sqrt(d);
-            Q[jj * p + jj] = l;
+            int e;
+            prod = frexp(prod * d, &e);
+            pex += e;
+            const double r = rsqrt(d);
+            il[jj] = r;
+            Q[jj * p + jj] = d * r;
             for (int i = jj + 1; i < p; ++i) {
                 double s = Q[i * p + jj];
                 for (int kk = 0; kk < jj; ++kk) s -= Q[i * p + kk] * Q[jj * p + kk];
-                Q[i * p + jj] = s / l;
+                Q[i * p + jj] = s * r;
             }
         }
-        if (st == PLK_POINT_OK) {
-            ldx = 0.0;
-            for (int jj = 0; jj < p; ++jj) ldx += 2.0 * log(Q[jj * p + jj]);
-        }
+        if (st == PLK_POINT_OK) ldx = log(prod) + (double)pex * 0.69314718055994530942;
     }
     const bool good = (st == PLK_POINT_OK);
     const double ld = good ? ldv[w] : NaN;
@@ -1155,7 +1193,7 @@ __global__ void k_finalize(int count, int64_t k0, int M, int p, int64_t n, int n
             for (int a = 0; a < p; ++a) {
                 double tt = -S[(M + a) * TB + m];
                 for (int kk = 0; kk < a; ++kk) tt -= Q[a * p + kk] * cv[kk];
-                cv[a] = tt / Q[a * p + a];
+                cv[a] = tt * il[a];
             }
             double sbh = 0.0;
             for (int a = 0; a < p; ++a) sbh += cv[a] * cv[a];
@@ -1163,7 +1201,7 @@ __global__ void k_finalize(int count, int64_t k0, int M, int p, int64_t n, int n
             for (int a = p - 1; a >= 0; --a) {
                 double tt = cv[a];
                 for (int kk = a + 1; kk < p; ++kk) tt -= Q[kk * p + a] * bv[kk];
-                bv[a] = tt / Q[a * p + a];
+                bv[a] = tt * il[a];
             }
             const double jac = -2.0 * (lambdas[m] - 1.0) * slog;
             double m2;
@@ -1325,9 +1363,9 @@ cudaError_t launch_front(const BatchArgs &b, cudaStream_t s, FrontMode mode, boo
         k_table_owner<<<cnt, 256, 0, s>>>(cnt, b.oconst, b.pstatus, b.owner);
         k_table_union<<<cnt, 256, 0, s>>>(cnt, b.oconst, b.owner);
     }
-    if (f32 && !build) {   // the fused path: tables spread over more blocks
-        const dim3 tg8((TAB_NBUCKET + 7) / 8, cnt);
-        TIMED(KC_TABLE, (k_matern_table<true, 8, 4><<<tg8, 8 * TAB_NC * 4, 0, s>>>(b.oconst, b.tab, b.owner)));
+    if (f32 && !build) {   // the fused path: tables spread over more blocks, 8 lanes per node
+        const dim3 tg4((TAB_NBUCKET + 3) / 4, cnt);
+        TIMED(KC_TABLE, (k_matern_table<true, 4, 8><<<tg4, 4 * TAB_NC * 8, 0, s>>>(b.oconst, b.tab, b.owner)));
     } else if (f32) {
         TIMED(KC_TABLE, (k_matern_table<true><<<tg, 320, 0, s>>>(b.oconst, b.tab, b.owner)));
         if (build)

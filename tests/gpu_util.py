@@ -89,12 +89,19 @@ def compare_fp64_singular(g, o, coords, params, rtol=RTOL_LOGL, max_count=None, 
     """compare() for FP64 results where some V are singular to working
     precision: a point whose status differs from the oracle's must have a V
     within FP64 rounding of singular (smallest oracle pivot below
-    4 n 2^-52 (1 + nu^2), or an FP64 factorisation that fails); the other
-    points are compared as usual."""
+    4 n 2^-52 (1 + nu^2), or an FP64 factorisation that fails).  Such a
+    point's log-likelihood, where both sides return one, is decided by a pivot
+    of rounding size (log|V| holds the log of that pivot, and the exact value
+    is -inf), so it is left out of the comparison too; the other points are
+    compared as usual."""
     diff = np.flatnonzero(g["status"] != o["status"])
     if len(diff):
         check_disagreements(coords, params, diff, len(params) if max_count is None else max_count,
                             unit=2.0 ** -52)
+    n = coords.shape[0]
     keep = g["status"] == o["status"]
+    for k in np.flatnonzero(keep & (o["status"] == 0)):
+        if min_pivot(coords, params[k]) <= singular_threshold(n, params[k][2], unit=2.0 ** -52):
+            keep[k] = False
     return compare({k: v[keep] for k, v in g.items()},
                    {k: v[keep] for k, v in o.items() if k != "threads"}, rtol=rtol, what=what)
