@@ -210,6 +210,18 @@ def probe_pipes():
     return {k: round(v, 2) for k, v in out.items()}
 
 
+def probe_fp64_lanes():
+    """SM cycles per FP64 FMA warp instruction of a dependent chain, for 1 and
+    4 warps in one block and 1 or 32 active lanes: whether FP64 issue cost
+    depends on the active lanes (it decides how FP64 work is laid out)."""
+    import ctypes as C
+    from paper_2305_04318_b300 import build
+    L = C.CDLL(build.build_probe())
+    f = L.plk_probe_fp64_cycles_per_warp_fma
+    f.restype, f.argtypes = C.c_double, [C.c_int, C.c_int]
+    return {f"warps{w}_lanes{a}": round(f(w, a), 2) for w in (1, 4) for a in (1, 32)}
+
+
 def trailing_flops(n, q, TB=128):
     """Algorithmic flops of the trailing updates, per omega, per step J of the
     blocked factorisation: the rank-TB update of the lower triangle of the true
@@ -382,6 +394,7 @@ def run_uneven(args):
             "config": {"workload": f"uneven: {D} datasets, n log-uniform in [200,3000] (median {int(np.median(ns))}), "
                                    f"p in {{2,3,5}}, {args.points} points each, 9 lambdas",
                        "precision": "mixed" if prec == nv.MIXED else "fp64", "streams": args.streams,
+                       "mixed_tolerance": nv.get_mixed_tolerance(),
                        "batch_per_item": args.item_batch if args.item_batch > 0 else "autotuned",
                        "cuda_graphs": bool(args.graph), "arena_gb": arena_bytes / 1e9,
                        "schedule_policy": args.policy,
@@ -489,6 +502,7 @@ def run_serving(args):
                                    f"parameter's {G}-point profile x {sub}^4 sub-grid x 9 lambdas ({G * sub ** 4} omega), "
                                    "then profile max + 95% CI on the device; Poisson arrivals",
                        "precision": "mixed" if prec == nv.MIXED else "fp64", "streams": args.streams,
+                       "mixed_tolerance": nv.get_mixed_tolerance(),
                        "batch_per_item": args.serve_batch},
             "capacity_jobs_per_s": cap, "levels": levels, "hbm_high_water_gb": high / 1e9,
             "latency_ms": {"p50": top["p50_ms"], "p99": top["p99_ms"], "what": "job latency at offered load 0.9"}}
@@ -575,7 +589,8 @@ def run_pipeline(args):
             "dtype": DTYPE["mixed" if prec == nv.MIXED else "fp64"], "data": "synthetic",
             "config": {"workload": f"pipeline: n={n} sites on a square of side {math.sqrt(n / 100.0):.2f}, p=2, "
                                    "truth kappa=1, phi_X=0.2, nu^2=0.1, ratio 1.5, lambda 0.5",
-                       "precision": "mixed" if prec == nv.MIXED else "fp64", "K": int(K), "M": int(M)},
+                       "precision": "mixed" if prec == nv.MIXED else "fp64", "K": int(K), "M": int(M),
+                       "mixed_tolerance": nv.get_mixed_tolerance()},
             "times_s": {k: round(v, 4) for k, v in times.items()},
             "mle": {"omega": fit["omega"].tolist(), "lambda": fit["lam"], "logL": fit["logL"],
                     "iterations": fit["iterations"],
@@ -664,8 +679,9 @@ def run_small_config(args):
             "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": out["fp64"]["ms_per_step"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": f"{args.workload}: n={n}, p={ds.p}, K={K}, M={M}", "precision": "fp64 (headline), mixed",
+                       "mixed_tolerance": nv.get_mixed_tolerance(),
                        "cuda_graphs": bool(args.graph)},
-            "fp64": out["fp64"], "mixed": out["mixed"],
+            "fp64": out["fp64"], "mixed": out["mixed"], "fp64_warp_fma_cycles": probe_fp64_lanes(),
             "cpu_baseline": {"value": len(sample) / t_or, "unit": UNIT, "cores": o["threads"], "kind": "oracle",
                              "sample": f"{len(sample)} of the {K} points ({t_or:.1f} s wall)"}}
     print(json.dumps(line), flush=True)
@@ -1006,6 +1022,7 @@ def main():
                 "warmup": args.warmup, "ms_per_step": main_res["ms_per_step"], "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[head], "data": "synthetic",
                 "config": {"workload": WORKLOAD, "precision": head, "batch_per_step": Bm, "n": n, "p": p, "M": M,
+                           "mixed_tolerance": nv.get_mixed_tolerance(),
                            "l2": f"inputs larger than L2: {main_res['wsb'] / 1e9:.1f} GB workspace per step",
                            "parallelism": f"omega-sharded x{world}"},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "latency_ms": lat,
@@ -1018,7 +1035,9 @@ def main():
                                     "steps run once more after the timed region with CUDA events around every "
                                     "launch (instrumented_ms_per_step); value and ms_per_step are uninstrumented",
                 "fp64_fma_peak_tflops": fp64_peak, "fp32_fma_peak_tflops": fp32_peak, "pipe_probes_tflops": pipes,
-                "points_not_ok": int(((st & 15) != 0).sum()), "points_evaluated": int(n_pts)}
+                "points_not_ok": int(((st & 15) != 0).sum()), "points_evaluated": int(n_pts),
+                "points_retried_7slice": int(((st & nv.POINT_RETRIED) != 0).sum()),
+                "points_fp64_tier": int(((st & nv.POINT_FP64) != 0).sum())}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

@@ -108,7 +108,8 @@ typedef struct {
  * block per point builds the bordered matrix in shared memory, factors it and
  * leaves the cross-products for the closed form -- in FP64 for PLK_FP64; in
  * double-float FP32 arithmetic for PLK_MIXED, where a point whose
- * a-posteriori bound 2^-36 (1 + nu^2) sum_j 1/d_j exceeds 1e-4 (or whose
+ * a-posteriori bound 2^-36 (1 + nu^2) sum_j 1/d_j exceeds the mixed tolerance
+ * (plk_set_mixed_tolerance; or whose
  * factorisation fails) is evaluated again in FP64 (status bits RETRIED and
  * FP64, err_bound 0).  This flag selects the tiled path instead (for
  * comparisons). */
@@ -157,6 +158,15 @@ typedef struct {
  * Returns 0 for invalid sizes. */
 size_t plk_eval_workspace_bytes(int64_t n, int32_t p, int32_t M, int32_t batch,
                                 int32_t precision);
+
+/* Tolerance of the PLK_MIXED retry rule: a point whose a-posteriori bound on
+ * |Delta l_p| exceeds it is evaluated again (5 slices -> 7 slices -> FP64; for
+ * small datasets double-float -> FP64).  Process-wide, read when a batch is
+ * enqueued; default 1e-3 (the mixed mode's accuracy target in absolute log-L
+ * units).  A smaller value sends more points to the slower tiers.
+ * Errors: PLK_E_INVALID unless 0 < tol <= 1 (the setting is unchanged). */
+plk_status plk_set_mixed_tolerance(double tol);
+double plk_get_mixed_tolerance(void);
 
 /* Evaluate all K points of `args` on `stream` (a cudaStream_t, 0 = legacy
  * default stream), in batches of opts->batch points, using only the caller's

@@ -237,7 +237,8 @@ extern "C" const char *plk_kernel_class_name(int32_t c) { return kernel_class_na
 // a 7-slice pass over the points whose error bound exceeded the tolerance or
 // whose factorisation failed.  Deciding the retry set reads the flags back, so
 // this synchronizes the stream once per batch.
-static const double kMixedTol = 1e-4;   // bound on |Delta log L| that triggers the retry
+// bound on |Delta log L| above which a mixed-precision point is re-evaluated
+static std::atomic<double> g_mixed_tol{1e-3};
 
 // Slots [off, off + cnt) of a mixed batch as a batch of their own.
 static void sub_batch(const BatchArgs &b, const MixedArgs &x, int off, int cnt, BatchArgs &bo, MixedArgs &xo) {
@@ -528,7 +529,7 @@ static plk_status run_mixed_batch(BatchArgs b, const Layout &L, void *ws, const 
     x.flags = at<int>(ws, L.off_flags);
     x.err = at<int>(ws, L.off_err);
     x.err_bound = err_bound;
-    x.tol = kMixedTol;
+    x.tol = g_mixed_tol.load();
     // without the retry the caller gets every point's 5-slice result
     x.early = (flags & (PLK_FLAG_NO_RETRY | PLK_FLAG_FULL_FIRST_PASS)) ? 0 : 1;
     if ((flags & PLK_FLAG_PIPELINED_RETRY) && overlap && b.count >= kOverlapMin && !use_graph(flags) &&
@@ -603,7 +604,7 @@ static plk_status run_fused_mixed_batch(BatchArgs b, const Layout &L, void *ws, 
     int *fl = at<int>(ws, L.off_flags);
     auto seq = [&]() {
         cudaError_t e = launch_fused_df_batch(b, invsum, s);
-        if (e == cudaSuccess) e = launch_mixed_bound(b, FUSED_DF_EPS, kMixedTol, 1, invsum, err_bound, fl, s);
+        if (e == cudaSuccess) e = launch_mixed_bound(b, FUSED_DF_EPS, g_mixed_tol.load(), 1, invsum, err_bound, fl, s);
         if (e == cudaSuccess && !(flags & PLK_FLAG_NO_RETRY)) e = launch_fused_fp64_gated(b, fl, err_bound, s);
         return e;
     };
@@ -1524,6 +1525,14 @@ extern "C" plk_status plk_inject_fault(plk_ctx *c, int32_t kind, int32_t count) 
     c->cv_work.notify_all();
     return PLK_OK;
 }
+
+extern "C" plk_status plk_set_mixed_tolerance(double tol) {
+    if (!(tol > 0.0 && tol <= 1.0)) return fail(PLK_E_INVALID, "mixed tolerance %g outside (0, 1]", tol);
+    g_mixed_tol.store(tol);
+    return PLK_OK;
+}
+
+extern "C" double plk_get_mixed_tolerance(void) { return g_mixed_tol.load(); }
 
 extern "C" plk_status plk_set_schedule_policy(plk_ctx *c, int32_t policy) {
     if (!c) return fail(PLK_E_INVALID, "ctx is NULL");

@@ -1,5 +1,6 @@
 // peak_probe.cu -- live throughput probes of the FP64 and FP32 FMA pipes, the
-// FP64 tensor MMA (DMMA) and the tcgen05 bf16 MMA
+// FP64 tensor MMA (DMMA) and the tcgen05 bf16 MMA, and the FP64 issue cost
+// against active lanes
 // (libplk_probe.so).  Used by the benchmark to state its roofline denominator
 // for FP64-pipe-bound kernels: MEASURED_PEAKS-style numbers exist only for HBM
 // copy and bf16 GEMM, not for FP64.  Not part of the paper's method.
@@ -50,6 +51,48 @@ static double run(int reps) {
 
 extern "C" double plk_probe_fp64_fma_tflops(int reps) { return run<double>(reps); }
 extern "C" double plk_probe_fp32_fma_tflops(int reps) { return run<float>(reps); }
+
+// ---------------------------------------------------------------------------
+// FP64 issue cost against active lanes: one block of `warps` warps, in each
+// warp the lanes below `active` run a dependent chain of ITERS FP64 FMAs,
+// timed by clock64 between two block barriers.  Returns SM cycles per warp
+// FMA instruction (per warp: the chain length over ITERS).
+// ---------------------------------------------------------------------------
+template <int ITERS>
+__global__ void fp64_lane_chain(double *out, int active, long long *cyc) {
+    const int lane = threadIdx.x & 31;
+    double a = 1.0 + threadIdx.x * 1e-9;
+    const double b = 0.999999, c = 1e-7;
+    __syncthreads();
+    const long long t0 = clock64();
+    if (lane < active) {
+#pragma unroll 16
+        for (int i = 0; i < ITERS; ++i) a = fma(a, b, c);
+    }
+    __syncthreads();
+    const long long t1 = clock64();
+    if (threadIdx.x == 0) *cyc = t1 - t0;
+    out[threadIdx.x] = a;
+}
+
+extern "C" double plk_probe_fp64_cycles_per_warp_fma(int warps, int active) {
+    if (warps < 1 || warps > 16 || active < 1 || active > 32) return -1.0;
+    constexpr int IT = 4096;
+    double *out = nullptr;
+    long long *cyc = nullptr, h = 0;
+    if (cudaMalloc(&out, sizeof(double) * 32 * 16) != cudaSuccess) return -1.0;
+    if (cudaMalloc(&cyc, sizeof(long long)) != cudaSuccess) {
+        cudaFree(out);
+        return -1.0;
+    }
+    fp64_lane_chain<IT><<<1, 32 * warps>>>(out, active, cyc);   // warm-up
+    fp64_lane_chain<IT><<<1, 32 * warps>>>(out, active, cyc);
+    const bool ok = cudaMemcpy(&h, cyc, sizeof(h), cudaMemcpyDeviceToHost) == cudaSuccess;
+    cudaFree(out);
+    cudaFree(cyc);
+    if (!ok || cudaGetLastError() != cudaSuccess) return -1.0;
+    return (double)h / IT;
+}
 
 // ---------------------------------------------------------------------------
 // FP64 tensor-core MMA (DMMA, mma.sync m8n8k4 f64): eight independent

@@ -131,6 +131,8 @@ def lib():
         "plk_cancel": (C.c_int, [vp, i64]),
         "plk_set_metrics_log": (C.c_int, [vp, C.c_char_p]),
         "plk_set_schedule_policy": (C.c_int, [vp, i32]),
+        "plk_set_mixed_tolerance": (C.c_int, [C.c_double]),
+        "plk_get_mixed_tolerance": (C.c_double, []),
         "plk_inject_fault": (C.c_int, [vp, i32, i32]),
         "plk_create_with_evaluator": (C.c_int, [C.POINTER(vp), sz, C.c_int, HOST_EVAL_FN, vp]),
         "plk_selftest_df_exp": (C.c_int, [vp, vp, vp, vp, i64, vp]),
@@ -180,6 +182,16 @@ FLAG_GRAPH = 8
 FLAG_FULL_FIRST_PASS = 16
 FLAG_NO_FUSED = 32
 FLAG_PIPELINED_RETRY = 64
+
+
+def set_mixed_tolerance(tol):
+    """Tolerance of the mixed-precision retry rule on |Delta l_p| (process-wide;
+    default 1e-3): plk_set_mixed_tolerance."""
+    _check(lib().plk_set_mixed_tolerance(float(tol)))
+
+
+def get_mixed_tolerance():
+    return float(lib().plk_get_mixed_tolerance())
 
 
 def kernel_timing(reset=True):

@@ -67,7 +67,8 @@ def test_fused_mixed_double_float(n, p, M):
     """PLK_MIXED on small datasets: the fused kernel in double-float FP32
     within 1e-3 of the oracle (statuses equal but on near-singular points);
     its bound 2^-36 (1 + nu^2) sum 1/d_j stays above twice the measured error;
-    the points it sends to FP64 (bound above 1e-4, or a failed factorisation)
+    the points it sends to FP64 (bound above the mixed tolerance, or a failed
+    factorisation)
     carry the FP64 fused kernel's results exactly."""
     from test_gpu_mixed import mixed_compare
     ds = synth.aniso_dataset(600 + n, n, math.sqrt(max(n, 10) / 10), p)

@@ -220,6 +220,32 @@ def test_mixed4000_full_size_sampled():
     assert np.all(err[ok] <= BOUND_RATIO * g5["err_bound"][ok])
 
 
+def test_mixed_tolerance_decides_the_retries():
+    """plk_set_mixed_tolerance: at 1e-3 (the default) and at 1e-4, every point
+    kept at 5 slices has its bound within the tolerance and its |Delta l_p|
+    against the FP64 path within the tolerance (and within BOUND_RATIO of its
+    bound); the tighter tolerance sends more points to the 7-slice tier."""
+    w = synth.mixed4000()
+    ds, P = w.datasets[0], w.params[0][::2]
+    f = gpu_eval(ds, P, w.lambdas, precision=nv.FP64)
+    retried = {}
+    try:
+        for tol in (1e-3, 1e-4):
+            nv.set_mixed_tolerance(tol)
+            g = gpu_eval(ds, P, w.lambdas, precision=nv.MIXED)
+            kept = (g["status"] == 0) & (f["status"] == 0)
+            eb = g["err_bound"][kept]
+            err = np.max(np.abs(g["logL"][kept] - f["logL"][kept]), axis=1)
+            assert np.all(eb <= tol), eb.max()
+            assert np.all((err <= BOUND_RATIO * eb) | (err <= 1e-9)) and err.max() <= tol
+            retried[tol] = int(((g["status"] & nv.POINT_RETRIED) != 0).sum())
+            mixed_compare(g, f, f"tolerance {tol:g} vs FP64 GPU", coords=ds.coords, params=P)
+    finally:
+        nv.set_mixed_tolerance(1e-3)
+    print(json.dumps(dict(what="retried points per tolerance", points=len(P), retried=retried)))
+    assert retried[1e-4] > retried[1e-3]
+
+
 @pytest.mark.parametrize("precision", [nv.FP64, nv.MIXED])
 def test_graph_launch_identical_to_eager(precision):
     """PLK_FLAG_GRAPH: the batch captured and replayed as a CUDA graph gives the

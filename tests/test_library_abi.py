@@ -87,3 +87,19 @@ def test_static_scratch_size_matches_header():
     m = re.search(r"#define PLK_STATIC_SCRATCH_BYTES \(\(size_t\)(\d+) << (\d+)\)", hdr)
     assert m, "PLK_STATIC_SCRATCH_BYTES not found"
     assert nv.STATIC_SCRATCH_BYTES == int(m.group(1)) << int(m.group(2))
+
+
+def test_mixed_tolerance_setting(L):
+    """plk_set_mixed_tolerance: default 1e-3, values in (0, 1] taken, others
+    refused with the setting unchanged (no GPU needed)."""
+    from paper_2305_04318_b300 import native as nv
+    assert nv.get_mixed_tolerance() == 1e-3
+    try:
+        nv.set_mixed_tolerance(1e-4)
+        assert nv.get_mixed_tolerance() == 1e-4
+        for bad in (0.0, -1e-3, 2.0, float("nan"), float("inf")):
+            with pytest.raises(RuntimeError):
+                nv.set_mixed_tolerance(bad)
+            assert nv.get_mixed_tolerance() == 1e-4
+    finally:
+        nv.set_mixed_tolerance(1e-3)
