@@ -80,7 +80,7 @@ struct Layout {
     // mixed precision only
     bool mixed = false;
     size_t img = 0, off_wimg = 0, off_pimg = 0, off_invsum = 0, off_flags = 0, off_idx = 0,
-           off_cparams = 0, off_err = 0;
+           off_cparams = 0, off_err = 0, off_idx2 = 0, off_cnt = 0;
 };
 
 bool sizes_ok(int64_t n, int32_t p, int32_t M) {
@@ -124,6 +124,8 @@ bool make_layout(int64_t n, int32_t p, int32_t M, int32_t batch, Layout &L, int 
         L.off_idx = take(sizeof(int) * (size_t)batch);
         L.off_cparams = take(sizeof(double) * 5 * (size_t)batch);
         L.off_err = take(sizeof(int));
+        L.off_idx2 = take(sizeof(int) * (size_t)batch);   // the FP64 tier's points
+        L.off_cnt = take(2 * sizeof(int));                 // device-side counts of the two tiers
     }
     L.total = off;
     return true;
@@ -535,59 +537,56 @@ static plk_status run_mixed_batch(BatchArgs b, const Layout &L, void *ws, const 
     if ((flags & PLK_FLAG_PIPELINED_RETRY) && overlap && b.count >= kOverlapMin && !use_graph(flags) &&
         !(flags & PLK_FLAG_NO_RETRY) && aux_streams().re)
         return run_mixed_pipelined(b, L, ws, x, params_all, flags, err_bound, s);
-    auto first = [&]() {
-        cudaError_t r = cudaMemsetAsync(x.err, 0, sizeof(int), s);
-        return r == cudaSuccess ? mixed_first_pass(b, x, overlap, s) : r;
+    // The batch up to its 7-slice tier is one asynchronous sequence (one CUDA
+    // graph with PLK_FLAG_GRAPH): the 5-slice pass; on the device, the
+    // compaction of the points whose bound it flags and the gather of their
+    // parameters; the 7-slice pass over them, launched over the batch's slots
+    // with the device-side count deciding which are live; the compaction of the
+    // points still flagged.  No decision reads the flags back.  The one read at
+    // the end takes the device error flag (a tensor-core wait that gave up) and
+    // the FP64 tier's count: in the rare batch where it is not zero, the FP64
+    // pass follows over exactly those points (launched over the whole batch
+    // instead, it would cost ~2 % of a step in empty thread blocks).
+    int *d_idx = at<int>(ws, L.off_idx), *d_idx2 = at<int>(ws, L.off_idx2), *d_cnt = at<int>(ws, L.off_cnt);
+    double *d_par = at<double>(ws, L.off_cparams);
+    const bool fp64_tier = !(flags & (PLK_FLAG_NO_RETRY | PLK_FLAG_NO_FP64_TIER));
+    auto seq = [&]() {
+        cudaError_t e = cudaMemsetAsync(x.err, 0, sizeof(int), s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(d_cnt, 0, 2 * sizeof(int), s);
+        if (e == cudaSuccess) e = mixed_first_pass(b, x, overlap, s);
+        if (e != cudaSuccess || (flags & PLK_FLAG_NO_RETRY)) return e;
+        e = launch_compact_flags(b.count, x.flags, nullptr, b.k0, nullptr, d_idx, d_cnt, s);
+        if (e == cudaSuccess) e = launch_gather_params(b.count, d_idx, params_all, d_par, s, d_cnt);
+        if (e != cudaSuccess) return e;
+        BatchArgs r = b;
+        r.params = d_par;
+        r.out_index = d_idx;
+        r.status_or = PLK_POINT_RETRIED;
+        r.dcount = d_cnt;
+        e = launch_mixed_batch(r, x, 7, s);   // flags[j] <- the 7-slice verdict of live slot j
+        if (e == cudaSuccess && fp64_tier)
+            e = launch_compact_flags(b.count, x.flags, d_cnt, 0, d_idx, d_idx2, d_cnt + 1, s);
+        return e;
     };
     if (use_graph(flags) && overlap) aux_streams();   // create the helper streams outside the capture
-    cudaError_t e = use_graph(flags) ? launch_as_graph(s, first) : first();
+    cudaError_t e = use_graph(flags) ? launch_as_graph(s, seq) : seq();
     if (e != cudaSuccess) return cuda_fail(e, "mixed batch launch");
-    std::vector<int> hf(b.count + 1);
-    e = cudaMemcpyAsync(hf.data(), x.flags, sizeof(int) * b.count, cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(hf.data() + b.count, x.err, sizeof(int), cudaMemcpyDeviceToHost, s);
+    int h[3] = {0, 0, 0};   // error flag, counts of the 7-slice and FP64 tiers
+    e = cudaMemcpyAsync(h, x.err, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h + 1, d_cnt, 2 * sizeof(int), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(e, "mixed batch");
-    if (hf[b.count]) return fail(PLK_E_TIMEOUT, "a tensor-core wait gave up (device error flag set)");
-    if (flags & PLK_FLAG_NO_RETRY) return PLK_OK;
-    std::vector<int> idx;
-    for (int w = 0; w < b.count; ++w)
-        if (hf[w]) idx.push_back((int)(b.k0 + w));
-    if (idx.empty()) return PLK_OK;
-    int *d_idx = at<int>(ws, L.off_idx);
-    double *d_par = at<double>(ws, L.off_cparams);
-    e = cudaMemcpyAsync(d_idx, idx.data(), sizeof(int) * idx.size(), cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = launch_gather_params((int)idx.size(), d_idx, params_all, d_par, s);
-    if (e != cudaSuccess) return cuda_fail(e, "mixed retry gather");
-    BatchArgs r = b;
-    r.count = (int)idx.size();
-    r.params = d_par;
-    r.out_index = d_idx;
-    r.status_or = PLK_POINT_RETRIED;
-    e = launch_mixed_batch(r, x, 7, s);
-    if (e != cudaSuccess) return cuda_fail(e, "mixed retry launch");
-    // third tier: points whose 7-slice bound is still above the tolerance, in FP64
-    std::vector<int> hf7(r.count + 1);
-    e = cudaMemcpyAsync(hf7.data(), x.flags, sizeof(int) * r.count, cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(hf7.data() + r.count, x.err, sizeof(int), cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);   // also keeps idx alive until its copy is done
-    if (e != cudaSuccess) return cuda_fail(e, "mixed retry");
-    if (hf7[r.count]) return fail(PLK_E_TIMEOUT, "a tensor-core wait gave up (device error flag set)");
-    std::vector<int> idx2;
-    if (!(flags & PLK_FLAG_NO_FP64_TIER))
-        for (int w = 0; w < r.count; ++w)
-            if (hf7[w]) idx2.push_back(idx[w]);
-    if (idx2.empty()) return PLK_OK;
-    e = cudaMemcpyAsync(d_idx, idx2.data(), sizeof(int) * idx2.size(), cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = launch_gather_params((int)idx2.size(), d_idx, params_all, d_par, s);
-    if (e != cudaSuccess) return cuda_fail(e, "fp64 retry gather");
+    if (h[0]) return fail(PLK_E_TIMEOUT, "a tensor-core wait gave up (device error flag set)");
+    if (!fp64_tier || h[2] == 0) return PLK_OK;
     BatchArgs f = b;
-    f.count = (int)idx2.size();
+    f.count = h[2];
     f.params = d_par;
-    f.out_index = d_idx;
+    f.out_index = d_idx2;
     f.status_or = PLK_POINT_RETRIED | PLK_POINT_FP64;
-    e = launch_fp64_batch(f, s);
-    if (e == cudaSuccess && err_bound) e = launch_scatter_value(f.count, d_idx, 0.0, err_bound, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);   // idx2 must outlive its copy
+    e = launch_gather_params(f.count, d_idx2, params_all, d_par, s);
+    if (e == cudaSuccess) e = launch_fp64_batch(f, s);
+    if (e == cudaSuccess && err_bound) e = launch_scatter_value(f.count, d_idx2, 0.0, err_bound, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(e, "fp64 retry");
     return PLK_OK;
 }

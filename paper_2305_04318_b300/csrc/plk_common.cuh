@@ -72,4 +72,9 @@ __device__ inline void decode_trailing(int t, int J, int &I, int &K) {
     K = J + 1 + (t - ir * (ir + 1) / 2);
 }
 
+// A batch whose points were compacted on the device (the mixed path's retry
+// tiers) is launched over its upper bound of slots; slots at or beyond the
+// device-side count *dcount return at once (dcount NULL: every slot is live).
+__device__ __forceinline__ bool beyond(const int *dcount, int w) { return dcount && w >= *dcount; }
+
 }  // namespace plk

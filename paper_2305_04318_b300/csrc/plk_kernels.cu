@@ -79,9 +79,10 @@ __global__ void __launch_bounds__(256) k_omega_prep(const double *__restrict__ p
                                                     const double *__restrict__ sumlogy, double *__restrict__ oconst,
                                                     double *__restrict__ coordT, double *__restrict__ logdet,
                                                     int *__restrict__ pstatus, int f32coords,
-                                                    const int *__restrict__ gate) {
+                                                    const int *__restrict__ gate, const int *__restrict__ dcount = nullptr) {
     const int w = blockIdx.x;
     if (gate && !gate[w]) return;   // gated pass: only the flagged slots
+    if (beyond(dcount, w)) return;  // slots past the device-side count of a compacted batch
     const double *om = params + 5 * (int64_t)w;
     const double phix = om[0], kap = om[1], nug = om[2], ratio = om[3], ang = om[4];
     const bool ok = (phix > 0.0) && (kap > 0.0) && (nug >= 0.0) && (ratio > 0.0) &&
@@ -262,8 +263,10 @@ __device__ double rho_integral(double u, double kap, double logc) {
 // read one table.  owner[w] = the smallest slot with the same kappa (bit
 // pattern) and a valid parameter row; an invalid row keeps its own.
 __global__ void __launch_bounds__(256) k_table_owner(int cnt, const double *__restrict__ oconst,
-                                                     const int *__restrict__ pstatus, int *__restrict__ owner) {
+                                                     const int *__restrict__ pstatus, int *__restrict__ owner,
+                                                     const int *__restrict__ dcount = nullptr) {
     const int w = blockIdx.x;
+    if (beyond(dcount, w)) return;
     __shared__ int best[8];
     int b = w;
     if (pstatus[w] == PLK_POINT_OK) {
@@ -285,9 +288,11 @@ __global__ void __launch_bounds__(256) k_table_owner(int cnt, const double *__re
 }
 
 // The owner's table covers the union of its sharers' octave ranges.
-__global__ void __launch_bounds__(256) k_table_union(int cnt, double *__restrict__ oconst, const int *__restrict__ owner) {
+__global__ void __launch_bounds__(256) k_table_union(int cnt, double *__restrict__ oconst, const int *__restrict__ owner,
+                                                     const int *__restrict__ dcount = nullptr) {
     const int w = blockIdx.x;
-    if (owner[w] != w) return;
+    if (dcount) cnt = min(cnt, *dcount);
+    if (w >= cnt || owner[w] != w) return;
     __shared__ int sl[8], sh[8];
     int lo = (int)oconst[OC_N * (int64_t)w + OC_ELO], hi = (int)oconst[OC_N * (int64_t)w + OC_EHI];
     for (int v = w + 1 + threadIdx.x; v < cnt; v += blockDim.x)
@@ -616,7 +621,8 @@ template <bool F32TAB, int BPB = 32, int SPLIT = 1>
 __global__ void __launch_bounds__(BPB * TAB_NC * SPLIT) k_matern_table(const double *__restrict__ oconst,
                                                                double *__restrict__ tab,
                                                                const int *__restrict__ owner,
-                                                               const int *__restrict__ gate = nullptr) {
+                                                               const int *__restrict__ gate = nullptr,
+                                                               const int *__restrict__ dcount = nullptr) {
     static_assert(SPLIT == 1 || F32TAB, "lane-split sums are double-float only");
     constexpr int NN = BPB * TAB_NC;   // nodes per block
     __shared__ double E1[F32TAB ? 1 : QNODES];   // FP64: cosh(t_k) - 1
@@ -630,6 +636,7 @@ __global__ void __launch_bounds__(BPB * TAB_NC * SPLIT) k_matern_table(const dou
     __shared__ float2 Ss[SPLIT > 1 ? NN : 1];
     __shared__ float As[SPLIT > 1 ? NN : 1];
     const int w = blockIdx.y;
+    if (beyond(dcount, w)) return;        // past the device-side count of a compacted batch
     if (owner && owner[w] != w) return;   // this slot reads another slot's table (same kappa)
     if (gate && !gate[w]) return;         // gated pass: only the flagged slots
     const double *oc = oconst + OC_N * (int64_t)w;
@@ -799,8 +806,10 @@ __global__ void __launch_bounds__(256) k_build(int nb, int64_t n, int64_t n_pad,
                                                const double *__restrict__ oconst,
                                                const double *__restrict__ coordT,
                                                const double *__restrict__ tab,
-                                               const double *__restrict__ Bt, const int *__restrict__ owner) {
+                                               const double *__restrict__ Bt, const int *__restrict__ owner,
+                                               const int *__restrict__ dcount = nullptr) {
     const int w = blockIdx.y;
+    if (beyond(dcount, w)) return;
     const int t = blockIdx.x;
     int I = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
     while ((I + 1) * (I + 2) / 2 <= t) ++I;
@@ -999,13 +1008,14 @@ __global__ void __launch_bounds__(256) k_build_f32(int nb, int64_t n, int64_t n_
 __global__ void __launch_bounds__(256) k_potrf(int J, int64_t tpo, double *__restrict__ tiles,
                                                double *__restrict__ inv,
                                                double *__restrict__ logdet,
-                                               int *__restrict__ pstatus) {
+                                               int *__restrict__ pstatus, const int *__restrict__ dcount = nullptr) {
     extern __shared__ double sm[];
     double *P = sm;         // packed lower L
     double *Wp = sm + PK;   // packed lower L^-1
     __shared__ double s_ld;
     __shared__ int s_bad;
     const int w = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (beyond(dcount, w)) return;
     double *T = tiles + ((int64_t)w * tpo + tile_index(J, J)) * NT;
     for (int e = tid; e < NT; e += 256) {
         const int r = e >> 7, c = e & (TB - 1);
@@ -1071,10 +1081,11 @@ __global__ void __launch_bounds__(256) k_potrf(int J, int64_t tpo, double *__res
 // ---------------------------------------------------------------------------
 template <int MODE>
 __global__ void __launch_bounds__(256, 1) k_gemm_nt(int J, int64_t tpo, double *tiles,
-                                                    const double *__restrict__ inv) {
+                                                    const double *__restrict__ inv, const int *__restrict__ dcount = nullptr) {
     __shared__ double As[16][TB + 2];
     __shared__ double Bs[16][TB + 2];
     const int w = blockIdx.y, t = blockIdx.x, tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    if (beyond(dcount, w)) return;
     double *base = tiles + (int64_t)w * tpo * NT;
     const double *A;
     const double *B;
@@ -1140,9 +1151,9 @@ __global__ void k_finalize(int count, int64_t k0, int M, int p, int64_t n, int n
                            const double *__restrict__ sumlogy, const double *__restrict__ lambdas,
                            double *logL, double *sigma2, double *beta, double *logdet,
                            double *ssq, int32_t *status, const int *__restrict__ out_index,
-                           int32_t status_or, const int *__restrict__ gate) {
+                           int32_t status_or, const int *__restrict__ gate, const int *__restrict__ dcount = nullptr) {
     const int w = blockIdx.x * blockDim.x + threadIdx.x;
-    if (w >= count) return;
+    if (w >= count || beyond(dcount, w)) return;
     if (gate && !gate[w]) return;   // gated pass: only the flagged slots
     const int64_t k = out_index ? (int64_t)out_index[w] : k0 + w;
     const double *S = tiles + ((int64_t)w * tpo + tile_index(nb, nb)) * NT;   // -B^T V^-1 B
@@ -1357,17 +1368,17 @@ cudaError_t launch_front(const BatchArgs &b, cudaStream_t s, FrontMode mode, boo
     KernelTimer *timer = b.timer;
     const int f32 = mode == FRONT_DF_FAST ? 1 : 0;
     TIMED(KC_PREP, (k_omega_prep<<<cnt, 256, 0, s>>>(b.params, b.n, b.n_pad, b.coords, b.sumlogy, b.oconst,
-                                                      b.coordT, b.ldv, b.pstatus, f32, nullptr)));
+                                                      b.coordT, b.ldv, b.pstatus, f32, nullptr, b.dcount)));
     const dim3 tg((TAB_NBUCKET + 31) / 32, cnt), bg((unsigned)b.tpo, cnt);
     if (b.owner) {   // slots with the same kappa share one table
-        k_table_owner<<<cnt, 256, 0, s>>>(cnt, b.oconst, b.pstatus, b.owner);
-        k_table_union<<<cnt, 256, 0, s>>>(cnt, b.oconst, b.owner);
+        k_table_owner<<<cnt, 256, 0, s>>>(cnt, b.oconst, b.pstatus, b.owner, b.dcount);
+        k_table_union<<<cnt, 256, 0, s>>>(cnt, b.oconst, b.owner, b.dcount);
     }
     if (f32 && !build) {   // the fused path: tables spread over more blocks, 8 lanes per node
         const dim3 tg4((TAB_NBUCKET + 3) / 4, cnt);
         TIMED(KC_TABLE, (k_matern_table<true, 4, 8><<<tg4, 4 * TAB_NC * 8, 0, s>>>(b.oconst, b.tab, b.owner)));
     } else if (f32) {
-        TIMED(KC_TABLE, (k_matern_table<true><<<tg, 320, 0, s>>>(b.oconst, b.tab, b.owner)));
+        TIMED(KC_TABLE, (k_matern_table<true><<<tg, 320, 0, s>>>(b.oconst, b.tab, b.owner, nullptr, b.dcount)));
         if (build)
             TIMED(KC_BUILD, (k_build_f32<<<bg, 256, 0, s>>>(b.nb, b.n, b.n_pad, b.q, b.tpo, b.tiles, b.oconst,
                                                              b.coordT, b.tab, b.Bt, b.owner)));
@@ -1375,13 +1386,13 @@ cudaError_t launch_front(const BatchArgs &b, cudaStream_t s, FrontMode mode, boo
         const dim3 tg8((TAB_NBUCKET + 7) / 8, cnt);
         TIMED(KC_TABLE, (k_matern_table<false, 8><<<tg8, 8 * TAB_NC, 0, s>>>(b.oconst, b.tab, b.owner)));
     } else {
-        TIMED(KC_TABLE, (k_matern_table<false><<<tg, 320, 0, s>>>(b.oconst, b.tab, b.owner)));
+        TIMED(KC_TABLE, (k_matern_table<false><<<tg, 320, 0, s>>>(b.oconst, b.tab, b.owner, nullptr, b.dcount)));
         if (mode == FRONT_DF)
             TIMED(KC_BUILD, (k_build<true><<<bg, 256, 0, s>>>(b.nb, b.n, b.n_pad, b.q, b.tpo, b.tiles, b.oconst,
-                                                               b.coordT, b.tab, b.Bt, b.owner)));
+                                                               b.coordT, b.tab, b.Bt, b.owner, b.dcount)));
         else
             TIMED(KC_BUILD, (k_build<false><<<bg, 256, 0, s>>>(b.nb, b.n, b.n_pad, b.q, b.tpo, b.tiles, b.oconst,
-                                                                b.coordT, b.tab, b.Bt, b.owner)));
+                                                                b.coordT, b.tab, b.Bt, b.owner, b.dcount)));
     }
     return cudaGetLastError();
 }
@@ -1427,7 +1438,7 @@ cudaError_t launch_finalize(const BatchArgs &b, cudaStream_t s) {
     TIMED(KC_FINAL, (k_finalize<<<(cnt + 63) / 64, 64, 0, s>>>(
                         cnt, b.k0, b.M, b.p, b.n, b.nb, b.reml, b.tpo, b.tiles, b.ldv, b.pstatus,
                         b.sumlogy, b.lambdas, b.logL, b.sigma2, b.beta, b.logdet, b.ssq, b.status, b.out_index,
-                        b.status_or, nullptr)));
+                        b.status_or, nullptr, b.dcount)));
     return cudaGetLastError();
 }
 
@@ -1441,10 +1452,10 @@ cudaError_t launch_fp64_batch(const BatchArgs &b, cudaStream_t s) {
     if ((e = launch_front(b, s, FRONT_FP64)) != cudaSuccess) return e;
     for (int J = 0; J < b.nb; ++J) {
         TIMED(KC_POTRF, (k_potrf<<<cnt, 256, 2 * PK * sizeof(double), s>>>(J, b.tpo, b.tiles, b.inv,
-                                                                            b.ldv, b.pstatus)));
+                                                                            b.ldv, b.pstatus, b.dcount)));
         const int m = b.nb - J;   // tile rows below the diagonal, RHS row included
-        TIMED(KC_TRSM, (k_gemm_nt<0><<<dim3(m, cnt), 256, 0, s>>>(J, b.tpo, b.tiles, b.inv)));
-        TIMED(KC_GEMM, (k_gemm_nt<1><<<dim3(m * (m + 1) / 2, cnt), 256, 0, s>>>(J, b.tpo, b.tiles, b.inv)));
+        TIMED(KC_TRSM, (k_gemm_nt<0><<<dim3(m, cnt), 256, 0, s>>>(J, b.tpo, b.tiles, b.inv, b.dcount)));
+        TIMED(KC_GEMM, (k_gemm_nt<1><<<dim3(m * (m + 1) / 2, cnt), 256, 0, s>>>(J, b.tpo, b.tiles, b.inv, b.dcount)));
     }
     return launch_finalize(b, s);
 }

@@ -45,6 +45,7 @@ struct BatchArgs {
     const int *out_index = nullptr;   // when set, batch slot w writes output row out_index[w]
     int32_t status_or = 0;            // bits OR-ed into every written status
     int *owner = nullptr;             // count: slot whose rho table this slot reads (NULL: its own)
+    const int *dcount = nullptr;      // device: live slots 0 .. *dcount - 1 of the count (NULL: all)
 };
 
 // Sets the calling thread's message returned by plk_last_error().
@@ -99,13 +100,20 @@ size_t mixed_slot_bytes();   // panel slot of one tile row
 cudaError_t launch_mixed_batch(const BatchArgs &b, const MixedArgs &x, int S, cudaStream_t s);
 // the batch after launch_front(b, s, FRONT_DF or FRONT_DF_FAST): factorisation, closed form, error bound
 cudaError_t launch_mixed_back(const BatchArgs &b, const MixedArgs &x, int S, cudaStream_t s);
-cudaError_t launch_gather_params(int count, const int *idx, const double *params, double *out, cudaStream_t s);
+// out_idx[j] = output row of the j-th slot w < min(count, *live) with flags[w]
+// set (map[w], or k0 + w), *out_count = their number; one block, slot order
+cudaError_t launch_compact_flags(int count, const int *flags, const int *live, int64_t k0, const int *map,
+                                 int *out_idx, int *out_count, cudaStream_t s);
+// dcount (device, optional): only entries 0 .. *dcount - 1 of the count
+cudaError_t launch_gather_params(int count, const int *idx, const double *params, double *out, cudaStream_t s,
+                                 const int *dcount = nullptr);
 // one block whose bounded wait on a barrier that nothing completes gives up and sets *err
 cudaError_t launch_wait_selftest(uint32_t max_iter, int *err, cudaStream_t s);
 // yh + yl = exp(xh + xl) by the double-float exp of the first-pass rho table
 cudaError_t launch_df_exp_selftest(int64_t count, const float *xh, const float *xl, float *yh, float *yl,
                                    cudaStream_t s);
-cudaError_t launch_scatter_value(int count, const int *idx, double v, double *out, cudaStream_t s);
+cudaError_t launch_scatter_value(int count, const int *idx, double v, double *out, cudaStream_t s,
+                                 const int *dcount = nullptr);
 
 cudaError_t launch_profile_max(const double *vals, int64_t G, int64_t SM, double *prof,
                                cudaStream_t s);

@@ -285,7 +285,8 @@ __device__ __forceinline__ void issue_split_mmas(uint32_t tb, const uint8_t *sA,
 // ---------------------------------------------------------------------------
 // double-float planes -> FP64 (the last diagonal tile, read by the closed form)
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_tile_to_fp64(int64_t tpo, int64_t tile, double *tiles) {
+__global__ void __launch_bounds__(256) k_tile_to_fp64(int64_t tpo, int64_t tile, double *tiles, const int *__restrict__ dcount = nullptr) {
+    if (beyond(dcount, (int)blockIdx.x)) return;
     double *T = tiles + ((int64_t)blockIdx.x * tpo + tile) * NT;
     const float *H = reinterpret_cast<const float *>(T);
     const float *L = H + NT;
@@ -494,7 +495,7 @@ __global__ void __launch_bounds__(256, 2) k_potrf_mixed(int J, int64_t tpo, doub
                                                         uint8_t *__restrict__ wimg, double *__restrict__ logdet,
                                                         double *__restrict__ invsum, int *__restrict__ pstatus,
                                                         const double *__restrict__ oconst, int *__restrict__ doomed,
-                                                        double tol) {
+                                                        double tol, const int *__restrict__ dcount = nullptr) {
     extern __shared__ double sm[];
     double *P = sm;                   // packed lower triangle: the tile, then L, then W = L^-1
     double *Tm = sm + PK;             // 3 x 32 x 32 temporaries of the block inverse
@@ -507,6 +508,7 @@ __global__ void __launch_bounds__(256, 2) k_potrf_mixed(int J, int64_t tpo, doub
     __shared__ double red[2][4];
     const int w = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (doomed && doomed[w]) return;   // already bound for the 7-slice tier
+    if (beyond(dcount, w)) return;
     double *T = tiles + ((int64_t)w * tpo + tile_index(J, J)) * NT;
     const float *H = reinterpret_cast<const float *>(T);
     const float *Lo = H + NT;
@@ -1023,7 +1025,8 @@ __global__ void __launch_bounds__(pipe::NTHP, 1) k_trail_pipe(int mode, int Klo,
                                                              const __grid_constant__ CUtensorMap tmapR, int qr,
                                                              const uint8_t *__restrict__ pimg,
                                                              const double *__restrict__ oconst,
-                                                             const int *__restrict__ doomed, int *__restrict__ err) {
+                                                             const int *__restrict__ doomed, int *__restrict__ err,
+                                                             const int *__restrict__ dcount = nullptr) {
     using namespace pipe;
     constexpr int NSET = Cfg<S>::NSET, NA = Cfg<S>::NA, BBUF = Cfg<S>::BBUF, OFF_A = Cfg<S>::OFF_A,
                   OFF_C = Cfg<S>::OFF_C;
@@ -1037,6 +1040,7 @@ __global__ void __launch_bounds__(pipe::NTHP, 1) k_trail_pipe(int mode, int Klo,
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int m = Ihi - Klo + 1;
     const int T = (mode == 0) ? m * (m + 1) / 2 : m;
+    if (dcount) cnt = min(cnt, *dcount);   // a compacted batch: its live slots only
     const int64_t items = (int64_t)cnt * T * 2;
     if (tid == 0) {
         for (int i = 0; i < 2; ++i) {
@@ -1386,7 +1390,7 @@ __device__ __forceinline__ void exact_values7(uint32_t tb, int warp, int cb, con
 // scratch.
 __global__ void __launch_bounds__(NTH, 1) k_trsm_split7x(int J, int nb, int64_t tpo, const double *__restrict__ tiles,
                                                          const uint8_t *__restrict__ wimg, uint8_t *__restrict__ pimg,
-                                                         int *__restrict__ err) {
+                                                         int *__restrict__ err, const int *__restrict__ dcount = nullptr) {
     extern __shared__ uint8_t smraw[];
     uint8_t *sbase = align1024(smraw);
     uint8_t *sA = sbase;
@@ -1397,6 +1401,7 @@ __global__ void __launch_bounds__(NTH, 1) k_trsm_split7x(int J, int nb, int64_t 
     __shared__ int sMx[TB];
     __shared__ int s_ok;
     const int w = blockIdx.y, I = J + 1 + blockIdx.x;
+    if (beyond(dcount, w)) return;   // before any barrier or TMEM allocation
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const float *H = reinterpret_cast<const float *>(tiles + ((int64_t)w * tpo + tile_index(I, J)) * NT);
     const float *Lo = H + NT;
@@ -1530,9 +1535,13 @@ __global__ void __launch_bounds__(NTH, 1) k_trsm_split7x(int J, int nb, int64_t 
 __global__ void k_mixed_bound(int count, int64_t k0, double eps, double tol, int flag_not_pd, int keep_doomed,
                               const double *__restrict__ oconst, const double *__restrict__ invsum,
                               const int *__restrict__ pstatus, const int *__restrict__ out_index, double *err_bound,
-                              int *flags) {
+                              int *flags, const int *__restrict__ dcount = nullptr) {
     const int w = blockIdx.x * blockDim.x + threadIdx.x;
     if (w >= count) return;
+    if (beyond(dcount, w)) {   // not a live slot: nothing to re-evaluate
+        flags[w] = 0;
+        return;
+    }
     const double E = eps * (1.0 + oconst[OC_N * w + OC_NUG]) * invsum[w];
     const int64_t k = out_index ? (int64_t)out_index[w] : k0 + w;
     if (err_bound) err_bound[k] = E;
@@ -1543,15 +1552,63 @@ __global__ void k_mixed_bound(int count, int64_t k0, double eps, double tol, int
     flags[w] = (doomed || (flag_not_pd && st == PLK_POINT_NOT_PD) || (st == PLK_POINT_OK && !(E <= tol))) ? 1 : 0;
 }
 
-__global__ void k_scatter_value(int count, const int *__restrict__ idx, double v, double *out) {
+// Stream compaction of the flagged slots of a batch, in slot order, by one
+// block: out_idx[j] = the j-th flagged slot w's output row (map[w], or k0 + w
+// without a map), *out_count = their number.  Only slots below *live (when
+// given) are considered.  The mixed path's retry tiers run over these lists
+// with no host read-back of the flags.
+__global__ void __launch_bounds__(1024) k_compact_flags(int count, const int *__restrict__ flags,
+                                                        const int *__restrict__ live, int64_t k0,
+                                                        const int *__restrict__ map, int *__restrict__ out_idx,
+                                                        int *__restrict__ out_count) {
+    __shared__ int wsum[32];
+    __shared__ int s_base, s_total;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int n = live ? min(count, *live) : count;
+    if (tid == 0) s_base = 0;
+    __syncthreads();
+    for (int c0 = 0; c0 < n; c0 += 1024) {
+        const int w = c0 + tid;
+        const int f = (w < n && flags[w]) ? 1 : 0;
+        const unsigned bal = __ballot_sync(0xffffffffu, f);
+        const int before = __popc(bal & ((1u << lane) - 1u));   // flagged lanes below this one
+        if (lane == 0) wsum[warp] = __popc(bal);
+        __syncthreads();
+        if (warp == 0) {   // exclusive prefix over the 32 warps
+            const int v = wsum[lane];
+            int incl = v;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int t = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += t;
+            }
+            wsum[lane] = incl - v;
+            if (lane == 31) s_total = incl;
+        }
+        __syncthreads();
+        if (f) out_idx[s_base + wsum[warp] + before] = map ? map[w] : (int)(k0 + w);
+        __syncthreads();
+        if (tid == 0) s_base += s_total;
+        __syncthreads();
+    }
+    if (tid == 0) *out_count = s_base;
+}
+
+cudaError_t launch_compact_flags(int count, const int *flags, const int *live, int64_t k0, const int *map,
+                                 int *out_idx, int *out_count, cudaStream_t s) {
+    k_compact_flags<<<1, 1024, 0, s>>>(count, flags, live, k0, map, out_idx, out_count);
+    return cudaGetLastError();
+}
+
+__global__ void k_scatter_value(int count, const int *__restrict__ idx, double v, double *out, const int *__restrict__ dcount = nullptr) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t < count) out[idx[t]] = v;
+    if (t < count && !beyond(dcount, t)) out[idx[t]] = v;
 }
 
 __global__ void k_gather_params(int count, const int *__restrict__ idx, const double *__restrict__ params,
-                                double *__restrict__ out) {
+                                double *__restrict__ out, const int *__restrict__ dcount = nullptr) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= count * 5) return;
+    if (t >= count * 5 || beyond(dcount, t / 5)) return;
     out[t] = params[(int64_t)idx[t / 5] * 5 + t % 5];
 }
 
@@ -1630,16 +1687,17 @@ static cudaError_t launch_mixed_steps(const BatchArgs &b, const MixedArgs &x, cu
             return e;
         for (int J = 0; J < nb; ++J) {
             TIMED(KC_POTRF_MIXED, (k_potrf_mixed<S><<<cnt, 256, POTRF_MIXED_SMEM, s>>>(
-                                      J, b.tpo, b.tiles, x.wimg, b.ldv, x.invsum, b.pstatus, b.oconst, nullptr, x.tol)));
+                                      J, b.tpo, b.tiles, x.wimg, b.ldv, x.invsum, b.pstatus, b.oconst, nullptr, x.tol,
+                                      b.dcount)));
             const int m = nb - J;
             TIMED(KC_TRSM_SPLIT7, (k_trsm_split7x<<<dim3(m, cnt), NTH, smem_split, s>>>(J, nb, b.tpo, b.tiles, x.wimg,
-                                                                                      x.pimg, x.err)));
+                                                                                      x.pimg, x.err, b.dcount)));
             // trailing triangle J+1 <= K <= I <= nb (data rows and the right-hand-side row)
             const int64_t items = (int64_t)cnt * (m * (m + 1) / 2) * 2;
             const int grid = (int)std::min<int64_t>(items, sms);
             TIMED(KC_GEMM_SPLIT7, (k_trail_pipe<7><<<grid, pipe::NTHP, pipe::Cfg<7>::SMEM, s>>>(
                                       0, J + 1, nb, 1, 0, nb, cnt, b.tpo, tmapC, tmapR, qr, x.pimg, b.oconst, nullptr,
-                                      x.err)));
+                                      x.err, b.dcount)));
         }
     } else {
         if ((e = cudaFuncSetAttribute(k_trsm_split<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_split)) !=
@@ -1682,7 +1740,7 @@ static cudaError_t launch_mixed_steps(const BatchArgs &b, const MixedArgs &x, cu
             trail(0, Jend, nb - 1, G, J0 & 3);                      // data triangle with the group's panels
         }
     }
-    TIMED(KC_CONVERT, (k_tile_to_fp64<<<cnt, 256, 0, s>>>(b.tpo, tile_index(nb, nb), b.tiles)));
+    TIMED(KC_CONVERT, (k_tile_to_fp64<<<cnt, 256, 0, s>>>(b.tpo, tile_index(nb, nb), b.tiles, b.dcount)));
     return cudaGetLastError();
 }
 
@@ -1701,7 +1759,7 @@ cudaError_t launch_mixed_back(const BatchArgs &b, const MixedArgs &x, int S, cud
     const double eps = mixed_eps(S);
     k_mixed_bound<<<(b.count + 127) / 128, 128, 0, s>>>(b.count, b.k0, eps, x.tol, S == 5 ? 1 : 0,
                                                        S == 5 && x.early ? 1 : 0, b.oconst, x.invsum, b.pstatus,
-                                                       b.out_index, x.err_bound, x.flags);
+                                                       b.out_index, x.err_bound, x.flags, b.dcount);
     return cudaGetLastError();
 }
 
@@ -1730,13 +1788,15 @@ cudaError_t launch_mixed_bound(const BatchArgs &b, double eps, double tol, int f
     return cudaGetLastError();
 }
 
-cudaError_t launch_scatter_value(int count, const int *idx, double v, double *out, cudaStream_t s) {
-    k_scatter_value<<<(count + 127) / 128, 128, 0, s>>>(count, idx, v, out);
+cudaError_t launch_scatter_value(int count, const int *idx, double v, double *out, cudaStream_t s,
+                                 const int *dcount) {
+    k_scatter_value<<<(count + 127) / 128, 128, 0, s>>>(count, idx, v, out, dcount);
     return cudaGetLastError();
 }
 
-cudaError_t launch_gather_params(int count, const int *idx, const double *params, double *out, cudaStream_t s) {
-    k_gather_params<<<(count * 5 + 255) / 256, 256, 0, s>>>(count, idx, params, out);
+cudaError_t launch_gather_params(int count, const int *idx, const double *params, double *out, cudaStream_t s,
+                                 const int *dcount) {
+    k_gather_params<<<(count * 5 + 255) / 256, 256, 0, s>>>(count, idx, params, out, dcount);
     return cudaGetLastError();
 }
 

@@ -246,6 +246,33 @@ def test_mixed_tolerance_decides_the_retries():
     assert retried[1e-4] > retried[1e-3]
 
 
+@pytest.mark.parametrize("graph", [False, True])
+def test_retry_tiers_on_the_device(graph):
+    """The retry tiers run on the device (compaction of the flagged points,
+    device-side counts): at a tolerance no 5- or 7-slice bound meets (1e-12 <
+    2^-46 n), every point passes through both and ends in the FP64 tier, whose
+    results equal the FP64 path's bit for bit (status bits RETRIED | FP64,
+    err_bound 0), eagerly and as one CUDA graph; at the default tolerance the
+    same call gives the usual mixed results."""
+    w = synth.aniso1000(K=20)
+    ds, P = w.datasets[0], w.params[0]
+    f = gpu_eval(ds, P, w.lambdas, precision=nv.FP64)
+    fl = nv.FLAG_GRAPH if graph else 0
+    try:
+        nv.set_mixed_tolerance(1e-12)
+        g = gpu_eval(ds, P, w.lambdas, precision=nv.MIXED, batch=12, flags=fl)
+    finally:
+        nv.set_mixed_tolerance(1e-3)
+    live = f["status"] == 0
+    assert np.all((g["status"][live] & (nv.POINT_RETRIED | nv.POINT_FP64)) == (nv.POINT_RETRIED | nv.POINT_FP64))
+    np.testing.assert_array_equal(g["status"] & 15, f["status"])
+    assert np.all(g["err_bound"][live] == 0.0)
+    for k in ("logL", "sigma2", "beta", "logdet"):
+        np.testing.assert_array_equal(g[k][live], f[k][live], err_msg=k)
+    m = gpu_eval(ds, P, w.lambdas, precision=nv.MIXED, batch=12, flags=fl)
+    mixed_compare(m, f, "default tolerance vs FP64 GPU", coords=ds.coords, params=P)
+
+
 @pytest.mark.parametrize("precision", [nv.FP64, nv.MIXED])
 def test_graph_launch_identical_to_eager(precision):
     """PLK_FLAG_GRAPH: the batch captured and replayed as a CUDA graph gives the
