@@ -106,6 +106,9 @@ def parse():
                     help="uneven: which job a free scheduler stream serves next (largest dataset first, or oldest)")
     ap.add_argument("--graph", type=int, default=0,
                     help="uneven, iso100, aniso1000: launch batches as CUDA graphs (1) or eagerly (0, default)")
+    ap.add_argument("--pipe-counters", action="store_true",
+                    help="diagnostic: one mixed step of the n=4000 workload through the library built with the "
+                         "trailing update's wait-cycle counters (libplk_counters.so); prints their breakdown")
     return ap.parse_args()
 
 
@@ -757,8 +760,42 @@ def split_pairs(S):
     return S * (S + 1) // 2
 
 
+def run_pipe_counters(args):
+    """Where the 5-slice trailing update's roles wait, per launch mode: one
+    warm-up and one counted mixed evaluation of a bench step (the n=4000
+    workload's points tiled to the step batch) through the diagnostic build."""
+    from paper_2305_04318_b300 import build
+    os.environ["PLK_LIBRARY"] = build.build_counters()
+    import torch
+    from paper_2305_04318_b300 import native as nv, synth
+    w = synth.mixed4000()
+    ds, P = w.datasets[0], w.params[0]
+    B = args.batch or 1776
+    T = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64), device="cuda")
+    xs = (T(ds.coords), T(ds.y), T(ds.X), T(w.lambdas), T(np.resize(P, (B, 5))))
+    nv.eval_device(*xs, precision=nv.MIXED, batch=B)
+    torch.cuda.synchronize()
+    nv.pipe_counters(reset=True)
+    nv.eval_device(*xs, precision=nv.MIXED, batch=B)
+    torch.cuda.synchronize()
+    c = nv.pipe_counters(reset=True)
+    out = {}
+    for mode, v in c.items():
+        loop, items = v["loop_cycles"], max(v["items"], 1)
+        out[mode] = {"items": v["items"], "cycles_per_item": round(loop / items),
+                     "share_of_loop": {k: round(v[k] / loop, 4) for k in nv.PIPE_COUNTER_NAMES[2:]} if loop else {},
+                     "per_item": {k: round(v[k] / items) for k in nv.PIPE_COUNTER_NAMES[2:]}}
+    print(json.dumps({"diagnostic": "trailing-update wait cycles (k_trail_pipe<5>, one thread block per SM; "
+                                    "MMA waits are the MMA thread's, epilogue waits its first thread's)",
+                      "workload": f"mixed4000: n={ds.n}, p={ds.p}, M={len(w.lambdas)}, batch={B}",
+                      "modes": out}))
+
+
 def main():
     args = parse()
+    if args.pipe_counters:
+        run_pipe_counters(args)
+        return
     if args.impl == "reference":
         run_reference(args)
         return

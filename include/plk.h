@@ -161,6 +161,19 @@ typedef struct {
 size_t plk_eval_workspace_bytes(int64_t n, int32_t p, int32_t M, int32_t batch,
                                 int32_t precision);
 
+/* Diagnostics of a library built with -DPLK_PIPE_COUNTERS (libplk_counters.so,
+ * paper_2305_04318_b300/build.py): cycles the 5-slice trailing update's roles
+ * spent waiting, per launch mode (0 the trailing triangle, 1 a tile column, 2
+ * the right-hand-side row), summed over its thread blocks since the last
+ * reset.  out (host, 27 values): [mode * 9 + k], k = 0 cycles of the blocks'
+ * work loops, 1 items, 2 MMA issue waiting for a free accumulator set, 3 ...
+ * for a B operand buffer, 4 ... for an A stage, 5 epilogue waiting for the
+ * item's MMAs, 6 ... for its C half tile, 7 ... for the previous stores to
+ * read the C buffer, 8 epilogue update.  reset != 0 zeroes the counters after
+ * reading.  Errors: PLK_E_INVALID (NULL out, or a library built without the
+ * counters), PLK_E_CUDA. */
+plk_status plk_pipe_counters(uint64_t *out, int32_t reset);
+
 /* Tolerance of the PLK_MIXED retry rule: a point whose a-posteriori bound on
  * |Delta l_p| exceeds it is evaluated again (5 slices -> 7 slices -> FP64; for
  * small datasets double-float -> FP64).  Process-wide, read when a batch is

@@ -15,6 +15,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libplk.so")
+COUNTERS_LIB = os.path.join(HERE, "libplk_counters.so")
 PROBE_SRC = os.path.join(HERE, "csrc_probe", "peak_probe.cu")
 PROBE_LIB = os.path.join(HERE, "libplk_probe.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -29,10 +30,11 @@ def _deps():
             glob.glob(os.path.join(INCLUDE, "*.h")))
 
 
-def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+def up_to_date(lib: str = None) -> bool:
+    lib = lib or LIB
+    if not os.path.exists(lib):
         return False
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return all(os.path.getmtime(f) <= t for f in _deps())
 
 
@@ -47,19 +49,31 @@ def build_probe(force: bool = False) -> str:
     return PROBE_LIB
 
 
+def _build_lib(out: str, defines=(), verbose: bool = False) -> str:
+    nvcc = os.environ.get("NVCC", "nvcc")
+    tmp = out + f".tmp{os.getpid()}"
+    cmd = [nvcc, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-shared", "-Xcompiler", "-fPIC",
+           *[f"-D{d}" for d in defines], "-I", INCLUDE, "-o", tmp, *sources(), "-lpthread"]
+    if verbose:
+        print(" ".join(cmd))
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, out)
+    return out
+
+
 def build(force: bool = False, verbose: bool = False) -> str:
     build_probe(force)
     if not force and up_to_date():
         return LIB
-    nvcc = os.environ.get("NVCC", "nvcc")
-    tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [nvcc, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-shared", "-Xcompiler", "-fPIC",
-           "-I", INCLUDE, "-o", tmp, *sources(), "-lpthread"]
-    if verbose:
-        print(" ".join(cmd))
-    subprocess.run(cmd, check=True)
-    os.replace(tmp, LIB)
-    return LIB
+    return _build_lib(LIB, verbose=verbose)
+
+
+def build_counters(force: bool = False, verbose: bool = False) -> str:
+    """The diagnostic build with the trailing update's wait-cycle counters
+    (-DPLK_PIPE_COUNTERS; plk_pipe_counters), next to the library."""
+    if not force and up_to_date(COUNTERS_LIB):
+        return COUNTERS_LIB
+    return _build_lib(COUNTERS_LIB, defines=("PLK_PIPE_COUNTERS",), verbose=verbose)
 
 
 if __name__ == "__main__":

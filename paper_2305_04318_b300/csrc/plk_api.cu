@@ -1525,6 +1525,14 @@ extern "C" plk_status plk_inject_fault(plk_ctx *c, int32_t kind, int32_t count) 
     return PLK_OK;
 }
 
+extern "C" plk_status plk_pipe_counters(uint64_t *out, int32_t reset) {
+    if (!out) return fail(PLK_E_INVALID, "out is NULL");
+    const cudaError_t e = pipe_counters(reinterpret_cast<unsigned long long *>(out), reset);
+    if (e == cudaErrorNotSupported) return fail(PLK_E_INVALID, "library built without PLK_PIPE_COUNTERS");
+    if (e != cudaSuccess) return cuda_fail(e, "pipe counters");
+    return PLK_OK;
+}
+
 extern "C" plk_status plk_set_mixed_tolerance(double tol) {
     if (!(tol > 0.0 && tol <= 1.0)) return fail(PLK_E_INVALID, "mixed tolerance %g outside (0, 1]", tol);
     g_mixed_tol.store(tol);

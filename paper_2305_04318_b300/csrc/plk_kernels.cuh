@@ -100,6 +100,9 @@ size_t mixed_slot_bytes();   // panel slot of one tile row
 cudaError_t launch_mixed_batch(const BatchArgs &b, const MixedArgs &x, int S, cudaStream_t s);
 // the batch after launch_front(b, s, FRONT_DF or FRONT_DF_FAST): factorisation, closed form, error bound
 cudaError_t launch_mixed_back(const BatchArgs &b, const MixedArgs &x, int S, cudaStream_t s);
+// Wait-cycle counters of the 5-slice trailing update (3 launch modes x 9;
+// cudaErrorNotSupported unless built with -DPLK_PIPE_COUNTERS)
+cudaError_t pipe_counters(unsigned long long *out, int reset);
 // out_idx[j] = output row of the j-th slot w < min(count, *live) with flags[w]
 // set (map[w], or k0 + w), *out_count = their number; one block, slot order
 cudaError_t launch_compact_flags(int count, const int *flags, const int *live, int64_t k0, const int *map,

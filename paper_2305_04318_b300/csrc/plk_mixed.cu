@@ -994,6 +994,27 @@ __global__ void __launch_bounds__(NTH, 1) k_trsm_split(int J, int nb, int64_t tp
 // parity (u & 1); the producer reusing a slot for use u >= 1 first waits for
 // the consumer's release of use u - 1.
 // ---------------------------------------------------------------------------
+// Wait-cycle counters of the 5-slice trailing update, compiled in only with
+// -DPLK_PIPE_COUNTERS (a diagnostic build of the library): per launch mode
+// (0 triangle, 1 column, 2 right-hand-side row), summed over thread blocks,
+// [0] cycles of the block's work loop, [1] items, [2] MMA warp waiting for a
+// free accumulator set, [3] ... for B, [4] ... for an A stage, [5] epilogue
+// waiting for the item's MMAs, [6] ... for its C half tile, [7] ... for the
+// previous stores to read the C buffer, [8] epilogue update (TMEM to C).
+#ifdef PLK_PIPE_COUNTERS
+constexpr int PIPE_NCOUNT = 9;
+__device__ unsigned long long g_pipe_counters[3][PIPE_NCOUNT];
+#define PIPE_TIMED(k, expr)                                   \
+    ([&]() {                                                  \
+        const long long _t0 = clock64();                      \
+        const auto _r = (expr);                               \
+        pc[k] += (unsigned long long)(clock64() - _t0);       \
+        return _r;                                            \
+    }())
+#else
+#define PIPE_TIMED(k, expr) (expr)
+#endif
+
 namespace pipe {
 constexpr int NTHP = 384;                   // warps 0-3 roles, warps 4-11 epilogue
 constexpr int NEPI = NTHP - 128;
@@ -1066,6 +1087,10 @@ __global__ void __launch_bounds__(pipe::NTHP, 1) k_trail_pipe(int mode, int Klo,
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tb = tmem_base;
+#ifdef PLK_PIPE_COUNTERS
+    const long long pc_start = clock64();
+    unsigned long long pc[PIPE_NCOUNT] = {0};
+#endif
 
     auto decode = [&](int64_t it, int &w, int &I, int &K, int &ch) {
         w = (int)(it / (2 * T));
@@ -1139,19 +1164,19 @@ __global__ void __launch_bounds__(pipe::NTHP, 1) k_trail_pipe(int mode, int Klo,
                 if (doomed && doomed[(int)(it / (2 * T))]) continue;
                 const int set = (NSET == 2) ? (int)(tcnt & 1) : 0;
                 const uint32_t tu = (NSET == 2) ? tcnt >> 1 : tcnt;
-                if (tu > 0 && !tc::mbar_wait(&accEmpty[set], (tu - 1) & 1)) { *verr = 1; break; }
+                if (tu > 0 && !PIPE_TIMED(2, tc::mbar_wait(&accEmpty[set], (tu - 1) & 1))) { *verr = 1; break; }
                 tc::fence_after_sync();
                 const uint32_t dacc = tb + set * 256;
                 for (int ph = 0; ph < 2 * P && !*verr; ++ph) {
                     const int h = ph;   // first K half of the first panel starts the accumulators
                     const int bs = bcnt & 1;
-                    if (!tc::mbar_wait(&bFull[bs], (bcnt >> 1) & 1)) { *verr = 1; break; }
+                    if (!PIPE_TIMED(3, tc::mbar_wait(&bFull[bs], (bcnt >> 1) & 1))) { *verr = 1; break; }
                     ++bcnt;
                     const uint64_t b0 = tc::sdesc_sw128(tc::smem_u32(sbase + bs * BBUF));
 #pragma unroll
                     for (int i = 0; i < S; ++i) {
                         const int as = acnt % NA;
-                        if (!tc::mbar_wait(&aFull[as], (acnt / NA) & 1)) { *verr = 1; break; }
+                        if (!PIPE_TIMED(4, tc::mbar_wait(&aFull[as], (acnt / NA) & 1))) { *verr = 1; break; }
                         ++acnt;
                         tc::fence_after_sync();
                         const uint64_t a0 = tc::sdesc_sw128(tc::smem_u32(sbase + OFF_A + as * SBLK));
@@ -1229,7 +1254,7 @@ __global__ void __launch_bounds__(pipe::NTHP, 1) k_trail_pipe(int mode, int Klo,
             const CUtensorMap *tm = rhs ? &tmapR : &tmapC;
             if (et == 0) {
                 // the previous item's stores have read the buffer: load this item's half tile
-                tc::bulk_wait_read_all();
+                PIPE_TIMED(7, (tc::bulk_wait_read_all(), 0));
                 tc::mbar_arrive_expect_tx(&cFull, 4 * rows * 128);
 #pragma unroll
                 for (int bx = 0; bx < 4; ++bx)
@@ -1248,8 +1273,11 @@ __global__ void __launch_bounds__(pipe::NTHP, 1) k_trail_pipe(int mode, int Klo,
             }
             const int set = (NSET == 2) ? (int)(tcnt & 1) : 0;
             if (et == 0) {   // one thread waits and decides for all
-                const bool ok = tc::mbar_wait(&accFull[set], ((NSET == 2) ? tcnt >> 1 : tcnt) & 1) &&
-                                tc::mbar_wait(&cFull, tcnt & 1);
+                const bool ok = PIPE_TIMED(5, tc::mbar_wait(&accFull[set], ((NSET == 2) ? tcnt >> 1 : tcnt) & 1)) &&
+                                PIPE_TIMED(6, tc::mbar_wait(&cFull, tcnt & 1));
+#ifdef PLK_PIPE_COUNTERS
+                pc[1] += 1;
+#endif
                 if (ok) c_pending = false;
                 if (!ok) *verr = 1;
                 s_stop = (!ok || *verr) ? 1 : 0;
@@ -1257,6 +1285,9 @@ __global__ void __launch_bounds__(pipe::NTHP, 1) k_trail_pipe(int mode, int Klo,
             tc::named_sync(1, NEPI);       // exponents and C visible; stop decision uniform
             if (s_stop) break;
             tc::fence_after_sync();
+#ifdef PLK_PIPE_COUNTERS
+            const long long pc_upd = clock64();
+#endif
             if (32 * (warp & 3) < rows) {   // warps whose rows all lie beyond an RHS tile's rows skip
                 const uint32_t a = tb + set * 256 + ((uint32_t)(32 * (warp & 3)) << 16) + 32 * q;
                 const int ea = sEA[r] - 14;
@@ -1311,6 +1342,9 @@ __global__ void __launch_bounds__(pipe::NTHP, 1) k_trail_pipe(int mode, int Klo,
             tc::fence_proxy_async();        // these writes are read by the TMA store
             tc::fence_before_sync();
             tc::named_sync(1, NEPI);
+#ifdef PLK_PIPE_COUNTERS
+            pc[8] += (unsigned long long)(clock64() - pc_upd);
+#endif
             if (et == 0) {
                 tc::mbar_arrive(&accEmpty[set]);   // the MMA warp may reuse this set
 #pragma unroll
@@ -1326,6 +1360,17 @@ __global__ void __launch_bounds__(pipe::NTHP, 1) k_trail_pipe(int mode, int Klo,
         }
     }
     __syncthreads();
+#ifdef PLK_PIPE_COUNTERS
+    if (S == 5 && (tid == 32 || tid == 128) && mode >= 0 && mode < 3) {   // the MMA thread, the epilogue's first
+        if (tid == 32) {
+            atomicAdd(&g_pipe_counters[mode][0], (unsigned long long)(clock64() - pc_start));
+            for (int k = 2; k <= 4; ++k) atomicAdd(&g_pipe_counters[mode][k], pc[k]);
+        } else {
+            atomicAdd(&g_pipe_counters[mode][1], pc[1]);
+            for (int k = 5; k <= 8; ++k) atomicAdd(&g_pipe_counters[mode][k], pc[k]);
+        }
+    }
+#endif
     if (*verr && tid == 0) atomicExch(err, 1);
     tc::fence_before_sync();
     __syncthreads();
@@ -1592,6 +1637,21 @@ __global__ void __launch_bounds__(1024) k_compact_flags(int count, const int *__
         __syncthreads();
     }
     if (tid == 0) *out_count = s_base;
+}
+
+cudaError_t pipe_counters(unsigned long long *out, int reset) {
+#ifdef PLK_PIPE_COUNTERS
+    cudaError_t e = cudaMemcpyFromSymbol(out, g_pipe_counters, sizeof(g_pipe_counters));
+    if (e == cudaSuccess && reset) {
+        static const unsigned long long zero[3 * PIPE_NCOUNT] = {};
+        e = cudaMemcpyToSymbol(g_pipe_counters, zero, sizeof(zero));
+    }
+    return e;
+#else
+    (void)out;
+    (void)reset;
+    return cudaErrorNotSupported;
+#endif
 }
 
 cudaError_t launch_compact_flags(int count, const int *flags, const int *live, int64_t k0, const int *map,

@@ -132,6 +132,7 @@ def lib():
         "plk_set_metrics_log": (C.c_int, [vp, C.c_char_p]),
         "plk_set_schedule_policy": (C.c_int, [vp, i32]),
         "plk_set_mixed_tolerance": (C.c_int, [C.c_double]),
+        "plk_pipe_counters": (C.c_int, [vp, i32]),
         "plk_get_mixed_tolerance": (C.c_double, []),
         "plk_inject_fault": (C.c_int, [vp, i32, i32]),
         "plk_create_with_evaluator": (C.c_int, [C.POINTER(vp), sz, C.c_int, HOST_EVAL_FN, vp]),
@@ -182,6 +183,20 @@ FLAG_GRAPH = 8
 FLAG_FULL_FIRST_PASS = 16
 FLAG_NO_FUSED = 32
 FLAG_PIPELINED_RETRY = 64
+
+
+PIPE_COUNTER_NAMES = ("loop_cycles", "items", "mma_wait_accumulators", "mma_wait_B", "mma_wait_A",
+                      "epilogue_wait_mma", "epilogue_wait_C", "epilogue_wait_store_read", "epilogue_update")
+PIPE_MODES = ("triangle", "column", "rhs_row")
+
+
+def pipe_counters(reset=True):
+    """Wait-cycle counters of the 5-slice trailing update (a library built with
+    -DPLK_PIPE_COUNTERS; plk_pipe_counters): {mode: {name: cycles}}."""
+    buf = (C.c_uint64 * (3 * len(PIPE_COUNTER_NAMES)))()
+    _check(lib().plk_pipe_counters(C.cast(buf, C.c_void_p), int(bool(reset))))
+    n = len(PIPE_COUNTER_NAMES)
+    return {m: {k: int(buf[i * n + j]) for j, k in enumerate(PIPE_COUNTER_NAMES)} for i, m in enumerate(PIPE_MODES)}
 
 
 def set_mixed_tolerance(tol):

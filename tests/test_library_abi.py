@@ -103,3 +103,11 @@ def test_mixed_tolerance_setting(L):
             assert nv.get_mixed_tolerance() == 1e-4
     finally:
         nv.set_mixed_tolerance(1e-3)
+
+
+def test_pipe_counters_absent_from_the_plain_build(L):
+    """plk_pipe_counters exists in every build; without -DPLK_PIPE_COUNTERS it
+    refuses (no GPU needed)."""
+    buf = (C.c_uint64 * 27)()
+    assert L.plk_pipe_counters(C.cast(buf, C.c_void_p), 0) == nv.PLK_E_INVALID
+    assert b"PLK_PIPE_COUNTERS" in L.plk_last_error()
