@@ -1077,7 +1077,90 @@ __global__ void __launch_bounds__(256) k_potrf(int J, int64_t tpo, double *__res
 
 // ---------------------------------------------------------------------------
 // Panel solve (MODE 0: C = A B^T, B = L_JJ^-1, in place) and trailing update
-// (MODE 1: C -= A B^T), FP64, 128 x 128 tiles, 8 x 8 outputs per thread.
+// (MODE 1: C -= A B^T), FP64, 128 x 128 tiles, 8 x 8 outputs per thread
+// (rows ty + 16 i, columns tx + 16 j).  RB < 8: only the first 16 RB rows of
+// A and C (a tile of the right-hand-side row, whose rows from q on are zero
+// in A: the skipped rows of C would stay as they are, zero or unchanged).
+// ---------------------------------------------------------------------------
+template <int MODE, int RB>
+__device__ __forceinline__ void gemm_tile(const double *__restrict__ A, const double *__restrict__ B, double *C,
+                                          double (*As)[TB + 2], double (*Bs)[TB + 2], int tid) {
+    const int tx = tid & 15, ty = tid >> 4;
+    double acc[RB][8];
+#pragma unroll
+    for (int i = 0; i < RB; ++i)
+#pragma unroll
+        for (int jj = 0; jj < 8; ++jj) acc[i][jj] = 0.0;
+    for (int k0 = 0; k0 < TB; k0 += 16) {
+#pragma unroll
+        for (int l = 0; l < 8; ++l) {
+            const int e = tid + 256 * l;
+            const int r = e >> 4, kk = e & 15;
+            if (l < RB) As[kk][r] = A[r * TB + k0 + kk];
+            Bs[kk][r] = B[r * TB + k0 + kk];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < 16; ++kk) {
+            double a[RB], b[8];
+#pragma unroll
+            for (int i = 0; i < RB; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+            for (int jj = 0; jj < 8; ++jj) b[jj] = Bs[kk][tx + 16 * jj];
+#pragma unroll
+            for (int i = 0; i < RB; ++i)
+#pragma unroll
+                for (int jj = 0; jj < 8; ++jj) acc[i][jj] = fma(a[i], b[jj], acc[i][jj]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < RB; ++i)
+#pragma unroll
+        for (int jj = 0; jj < 8; ++jj) {
+            const int idx = (ty + 16 * i) * TB + tx + 16 * jj;
+            if (MODE == 0)
+                C[idx] = acc[i][jj];
+            else
+                C[idx] -= acc[i][jj];
+        }
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(256, 1) k_gemm_nt(int J, int64_t tpo, double *tiles,
+                                                    const double *__restrict__ inv, int nb, int q,
+                                                    const int *__restrict__ dcount = nullptr) {
+    __shared__ double As[16][TB + 2];
+    __shared__ double Bs[16][TB + 2];
+    const int w = blockIdx.y, t = blockIdx.x, tid = threadIdx.x;
+    if (beyond(dcount, w)) return;
+    double *base = tiles + (int64_t)w * tpo * NT;
+    const double *A;
+    const double *B;
+    double *C;
+    int I;
+    if (MODE == 0) {
+        I = J + 1 + t;
+        C = base + tile_index(I, J) * NT;
+        A = C;
+        B = inv + (int64_t)w * NT;
+    } else {
+        int K;
+        decode_trailing(t, J, I, K);
+        A = base + tile_index(I, J) * NT;
+        B = base + tile_index(K, J) * NT;
+        C = base + tile_index(I, K) * NT;
+    }
+    if (I == nb && q <= 16)   // the right-hand-side row: q = M + p <= 64 non-zero rows
+        gemm_tile<MODE, 1>(A, B, C, As, Bs, tid);
+    else if (I == nb && q <= 32)
+        gemm_tile<MODE, 2>(A, B, C, As, Bs, tid);
+    else if (I == nb && q <= 64)
+        gemm_tile<MODE, 4>(A, B, C, As, Bs, tid);
+    else
+        gemm_tile<MODE, 8>(A, B, C, As, Bs, tid);
+}
+
 // ---------------------------------------------------------------------------
 template <int MODE>
 __global__ void __launch_bounds__(256, 1) k_gemm_nt(int J, int64_t tpo, double *tiles,
@@ -1454,8 +1537,9 @@ cudaError_t launch_fp64_batch(const BatchArgs &b, cudaStream_t s) {
         TIMED(KC_POTRF, (k_potrf<<<cnt, 256, 2 * PK * sizeof(double), s>>>(J, b.tpo, b.tiles, b.inv,
                                                                             b.ldv, b.pstatus, b.dcount)));
         const int m = b.nb - J;   // tile rows below the diagonal, RHS row included
-        TIMED(KC_TRSM, (k_gemm_nt<0><<<dim3(m, cnt), 256, 0, s>>>(J, b.tpo, b.tiles, b.inv, b.dcount)));
-        TIMED(KC_GEMM, (k_gemm_nt<1><<<dim3(m * (m + 1) / 2, cnt), 256, 0, s>>>(J, b.tpo, b.tiles, b.inv, b.dcount)));
+        TIMED(KC_TRSM, (k_gemm_nt<0><<<dim3(m, cnt), 256, 0, s>>>(J, b.tpo, b.tiles, b.inv, b.nb, b.q, b.dcount)));
+        TIMED(KC_GEMM, (k_gemm_nt<1><<<dim3(m * (m + 1) / 2, cnt), 256, 0, s>>>(J, b.tpo, b.tiles, b.inv, b.nb, b.q,
+                                                                                    b.dcount)));
     }
     return launch_finalize(b, s);
 }
