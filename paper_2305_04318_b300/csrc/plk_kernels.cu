@@ -602,6 +602,71 @@ __device__ __forceinline__ double rho_df(double u, double kap, double logc, cons
 
 #include "plk_quad_consts.inc"   // QUAD_E1, QUAD_E1F_HI/LO, QUAD_CT, QUAD_TM
 
+// FP64 trapezoid sum of rho(u) / (c u^kappa e^{-u} h) at one table node,
+// shared by the S consecutive lanes sub = 0 .. S - 1 of a group (the terms
+// k = 1 + sub, 1 + sub + S, ...; the node t = 0, weight 1/2, in lane 0; each
+// lane stops by the FP64 evaluation's rule on its own terms; the partial sums
+// added in a fixed order by shuffles, so every lane of the group returns the
+// same sum and every lane of the warp must call this).  Fixed grid t_k = k QH
+// (u <= TAB_USPLIT: terms exp(log cosh(kappa t_k) - u (cosh t_k - 1)) from E1,
+// L2), else the step h = min(0.1, 0.45 / sqrt(u)) with cosh(kappa t) e^{-u cosh t}
+// written as e^{kappa t - u (cosh t - 1)} (1 + e^{-2 kappa t}) / 2 and
+// e^{-2 kappa t_k} = r^k by products.  *h_out receives the step.
+template <int S>
+__device__ __forceinline__ double rho_fp64_sum(double u, double kap, const double *__restrict__ E1,
+                                               const double *__restrict__ L2, int sub, double *h_out) {
+    double sum = sub == 0 ? 0.5 : 0.0, prev = sub == 0 ? 1.0 : INFINITY;
+    if (u <= TAB_USPLIT) {
+        *h_out = QH;
+        bool stop = false;
+        for (int k = 1 + sub; k < QNODES && !stop; k += 4 * S) {
+            double g[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int kk = k + i * S;
+                g[i] = (kk < QNODES) ? exp(L2[kk] - u * E1[kk]) : 0.0;
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                if (stop || k + i * S >= QNODES) {
+                    stop = true;
+                    continue;
+                }
+                sum += g[i];
+                if (g[i] < prev && g[i] < 1e-18 * sum) stop = true;
+                prev = g[i];
+            }
+        }
+    } else {
+        double h = 0.45 * rsqrt(u);
+        if (h > 0.1) h = 0.1;
+        *h_out = h;
+        const double r = exp(-2.0 * kap * h);
+        double rS = r, rk = r;   // r^S, r^(1 + sub)
+        for (int i = 1; i < S; ++i) rS *= r;
+        for (int i = 0; i < sub; ++i) rk *= r;
+        for (int k = 1 + sub; k < 20000; k += S) {
+            const double t = k * h;
+            const double sh = sinh(0.5 * t);
+            const double g = exp(kap * t - 0.69314718055994530942 - 2.0 * u * sh * sh) * (1.0 + rk);
+            rk *= rS;
+            sum += g;
+            if (g < prev && g < 1e-18 * sum) break;
+            prev = g;
+        }
+    }
+    if constexpr (S > 1) {
+#pragma unroll
+        for (int o = 1; o < S; o <<= 1) {   // lanes (sub, sub ^ o): lower sub first
+            const double other = __shfl_xor_sync(0xffffffffu, sum, o);
+            sum = ((sub & o) == 0) ? sum + other : other + sum;
+        }
+    }
+    return sum;
+}
+
+
+
 // Table builder: one block per BPB sub-intervals (buckets) of a slot's table,
 // TAB_NC Chebyshev nodes each (BPB = 32 for the tiled paths; fewer for the
 // fused small-n path, whose batches often share one table: more blocks per
@@ -623,7 +688,6 @@ __global__ void __launch_bounds__(BPB * TAB_NC * SPLIT) k_matern_table(const dou
                                                                const int *__restrict__ owner,
                                                                const int *__restrict__ gate = nullptr,
                                                                const int *__restrict__ dcount = nullptr) {
-    static_assert(SPLIT == 1 || F32TAB, "lane-split sums are double-float only");
     constexpr int NN = BPB * TAB_NC;   // nodes per block
     __shared__ double E1[F32TAB ? 1 : QNODES];   // FP64: cosh(t_k) - 1
     __shared__ double L2[F32TAB ? 1 : QNODES];   // FP64: log cosh(kappa t_k)
@@ -632,9 +696,10 @@ __global__ void __launch_bounds__(BPB * TAB_NC * SPLIT) k_matern_table(const dou
     __shared__ double Ach[NN];                   // Chebyshev coefficients per bucket
     __shared__ double CT[TAB_NC * TAB_NC];       // cos(pi k (m + 1/2) / NC)
     __shared__ double TM[TAB_NC * TAB_NC];       // T_k(t) = sum_m TM[k][m] t^m
-    __shared__ double Us[SPLIT > 1 ? NN : 1];    // SPLIT > 1: node u, partial results
-    __shared__ float2 Ss[SPLIT > 1 ? NN : 1];
-    __shared__ float As[SPLIT > 1 ? NN : 1];
+    __shared__ double Us[SPLIT > 1 ? NN : 1];    // SPLIT > 1: node u, then its sum, offset, step
+    __shared__ float2 Ss[SPLIT > 1 && F32TAB ? NN : 1];
+    __shared__ float As[SPLIT > 1 && F32TAB ? NN : 1];
+    __shared__ double Sd[SPLIT > 1 && !F32TAB ? NN : 1], Hd[SPLIT > 1 && !F32TAB ? NN : 1];
     const int w = blockIdx.y;
     if (beyond(dcount, w)) return;        // past the device-side count of a compacted batch
     if (owner && owner[w] != w) return;   // this slot reads another slot's table (same kappa)
@@ -677,19 +742,31 @@ __global__ void __launch_bounds__(BPB * TAB_NC * SPLIT) k_matern_table(const dou
         if (kap_ok) {   // block-uniform: every lane reaches the shuffles
             const int node = threadIdx.x / SPLIT, sub = threadIdx.x % SPLIT;
             const double u = Us[node];
-            const float uh = __double2float_rn(u), ul = __double2float_rn(u - (double)uh);
-            const float kh = __double2float_rn(kap), kl = __double2float_rn(kap - (double)kh);
-            float Av;
-            const float2 sum = rho_df_sum<SPLIT>(uh, ul, kh, kl, rho_df_step(uh), E1f, sub, Av);
-            if (sub == 0) {
-                Ss[node] = sum;
-                As[node] = Av;
+            if constexpr (F32TAB) {
+                const float uh = __double2float_rn(u), ul = __double2float_rn(u - (double)uh);
+                const float kh = __double2float_rn(kap), kl = __double2float_rn(kap - (double)kh);
+                float Av;
+                const float2 sum = rho_df_sum<SPLIT>(uh, ul, kh, kl, rho_df_step(uh), E1f, sub, Av);
+                if (sub == 0) {
+                    Ss[node] = sum;
+                    As[node] = Av;
+                }
+            } else {
+                double h;
+                const double sum = rho_fp64_sum<SPLIT>(u, kap, E1, L2, sub, &h);
+                if (sub == 0) {
+                    Sd[node] = sum;
+                    Hd[node] = h;
+                }
             }
         }
         __syncthreads();
         if (used) {
             const double u = Us[nd];
-            F[nd] = kap_ok ? rho_df_finish(u, kap, logc, As[nd], rho_df_step(__double2float_rn(u)), Ss[nd]) : nan("");
+            if constexpr (F32TAB)
+                F[nd] = kap_ok ? rho_df_finish(u, kap, logc, As[nd], rho_df_step(__double2float_rn(u)), Ss[nd]) : nan("");
+            else
+                F[nd] = kap_ok ? exp(logc + kap * log(u) - u) * (Hd[nd] * Sd[nd]) : nan("");
         }
     } else {
         __syncthreads();
@@ -1465,9 +1542,9 @@ cudaError_t launch_front(const BatchArgs &b, cudaStream_t s, FrontMode mode, boo
         if (build)
             TIMED(KC_BUILD, (k_build_f32<<<bg, 256, 0, s>>>(b.nb, b.n, b.n_pad, b.q, b.tpo, b.tiles, b.oconst,
                                                              b.coordT, b.tab, b.Bt, b.owner)));
-    } else if (!build) {   // the fused path: tables spread over more blocks
-        const dim3 tg8((TAB_NBUCKET + 7) / 8, cnt);
-        TIMED(KC_TABLE, (k_matern_table<false, 8><<<tg8, 8 * TAB_NC, 0, s>>>(b.oconst, b.tab, b.owner)));
+    } else if (!build) {   // the fused path: tables spread over more blocks, 4 lanes per node
+        const dim3 tg4((TAB_NBUCKET + 3) / 4, cnt);
+        TIMED(KC_TABLE, (k_matern_table<false, 4, 4><<<tg4, 4 * TAB_NC * 4, 0, s>>>(b.oconst, b.tab, b.owner)));
     } else {
         TIMED(KC_TABLE, (k_matern_table<false><<<tg, 320, 0, s>>>(b.oconst, b.tab, b.owner, nullptr, b.dcount)));
         if (mode == FRONT_DF)
@@ -1989,8 +2066,8 @@ cudaError_t launch_fused_fp64_gated(const BatchArgs &b, const int *gate, double 
     const int32_t sor = PLK_POINT_RETRIED | PLK_POINT_FP64;
     TIMED(KC_PREP, (k_omega_prep<<<cnt, 256, 0, s>>>(b.params, b.n, b.n_pad, b.coords, b.sumlogy, b.oconst, b.coordT,
                                                       b.ldv, b.pstatus, 0, gate)));
-    const dim3 tg8((TAB_NBUCKET + 7) / 8, cnt);
-    TIMED(KC_TABLE, (k_matern_table<false, 8><<<tg8, 8 * TAB_NC, 0, s>>>(b.oconst, b.tab, nullptr, gate)));
+    const dim3 tg4((TAB_NBUCKET + 3) / 4, cnt);
+    TIMED(KC_TABLE, (k_matern_table<false, 4, 4><<<tg4, 4 * TAB_NC * 4, 0, s>>>(b.oconst, b.tab, nullptr, gate)));
     TIMED(KC_FUSED, (k_fused_small<<<cnt, FUSED_THREADS, smem, s>>>(b.n, b.n_pad, b.q, b.nb, b.tpo, b.tiles, b.oconst,
                                                                    b.coordT, b.tab, b.Bt, nullptr, b.ldv, b.pstatus,
                                                                    gate)));
