@@ -31,13 +31,13 @@ namespace plk {
 // Box-Cox rows and sum of log y
 // ---------------------------------------------------------------------------
 
-__global__ void k_boxcox_rows(int64_t n, int64_t n_pad, int p, int M, const double *__restrict__ y,
-                              const double *__restrict__ X, const double *__restrict__ lam,
-                              double *__restrict__ Bt) {
+// Box-Cox rows, as block bid of nblk blocks
+__device__ __forceinline__ void boxcox_rows_part(int bid, int nblk, int64_t n, int64_t n_pad, int p, int M,
+                                                 const double *__restrict__ y, const double *__restrict__ X,
+                                                 const double *__restrict__ lam, double *__restrict__ Bt) {
     const int q = M + p;
     const int64_t total = (int64_t)q * n_pad;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
-         e += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t e = bid * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)nblk * blockDim.x) {
         const int r = (int)(e / n_pad);
         const int64_t i = e - (int64_t)r * n_pad;
         double v = 0.0;
@@ -54,7 +54,8 @@ __global__ void k_boxcox_rows(int64_t n, int64_t n_pad, int p, int M, const doub
     }
 }
 
-__global__ void k_sumlog(int64_t n, const double *__restrict__ y, double *__restrict__ out) {
+// sum_i log y_i by one block (a fixed summation order)
+__device__ __forceinline__ void sumlog_part(int64_t n, const double *__restrict__ y, double *__restrict__ out) {
     __shared__ double red[32];
     double s = 0.0;
     for (int64_t i = threadIdx.x; i < n; i += blockDim.x) s += log(y[i]);
@@ -199,9 +200,8 @@ __global__ void __launch_bounds__(256) k_omega_prep(const double *__restrict__ p
 // (which holds a large positive value beforehand): gridDim.y (1, 2, 4 or 8)
 // blocks per pair of 128-site tiles, non-negative doubles compared through
 // their bit patterns.
-__global__ void __launch_bounds__(256) k_min_dist2(int64_t n, const double *__restrict__ coords,
-                                                   double *__restrict__ out) {
-    const int t = blockIdx.x;
+__device__ __forceinline__ void min_dist2_part(int t, int split, int ys, int64_t n,
+                                               const double *__restrict__ coords, double *__restrict__ out) {
     int I = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
     while ((I + 1) * (I + 2) / 2 <= t) ++I;
     while (I * (I + 1) / 2 > t) --I;
@@ -215,8 +215,8 @@ __global__ void __launch_bounds__(256) k_min_dist2(int64_t n, const double *__re
     }
     __syncthreads();
     double best = INFINITY;
-    // gridDim.y blocks share the tile pair (few pairs: small n)
-    const int per = 128 * 128 / (int)gridDim.y, r0 = (int)blockIdx.y * per;
+    // split blocks share the tile pair (few pairs: small n); this is block ys
+    const int per = 128 * 128 / split, r0 = ys * per;
     for (int r = r0 + threadIdx.x; r < r0 + per; r += blockDim.x) {
         const int64_t i = i0 + (r >> 7), j = j0 + (r & 127);
         if (i < n && j < i) {
@@ -227,6 +227,31 @@ __global__ void __launch_bounds__(256) k_min_dist2(int64_t n, const double *__re
     for (int o = 16; o > 0; o >>= 1) best = fmin(best, __shfl_xor_sync(0xffffffffu, best, o));
     if ((threadIdx.x & 31) == 0 && best < INFINITY)
         atomicMin(reinterpret_cast<unsigned long long *>(out), (unsigned long long)__double_as_longlong(best));
+}
+
+__global__ void __launch_bounds__(256) k_min_dist2(int64_t n, const double *__restrict__ coords,
+                                                   double *__restrict__ out) {
+    min_dist2_part((int)blockIdx.x, (int)gridDim.y, (int)blockIdx.y, n, coords, out);
+}
+
+// The dataset's per-call preprocessing in one launch (the three parts are
+// independent): blocks 0 .. nbox - 1 write the Box-Cox rows B^T, block nbox
+// sums log y, the rest (split per tile pair) take the smallest squared site
+// distance.
+__global__ void __launch_bounds__(256) k_dataset_front(int nbox, int split, int64_t n, int64_t n_pad, int p, int M,
+                                                       const double *__restrict__ y, const double *__restrict__ X,
+                                                       const double *__restrict__ lam, double *__restrict__ Bt,
+                                                       const double *__restrict__ coords,
+                                                       double *__restrict__ sumlogy) {
+    const int b = (int)blockIdx.x;
+    if (b < nbox) {
+        boxcox_rows_part(b, nbox, n, n_pad, p, M, y, X, lam, Bt);
+    } else if (b == nbox) {
+        sumlog_part(n, y, sumlogy);
+    } else {
+        const int r = b - nbox - 1;
+        min_dist2_part(r / split, split, r % split, n, coords, sumlogy + 1);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -1516,10 +1541,10 @@ cudaError_t launch_boxcox(int64_t n, int64_t n_pad, int p, int M, const double *
     const int64_t nt = (n + 127) / 128;
     cudaError_t e = cudaMemsetAsync(sumlogy + 1, 0x7f, sizeof(double), s);   // 0x7f7f.. ~ 1.4e306
     if (e != cudaSuccess) return e;
-    TIMED(KC_BOXCOX, (k_boxcox_rows<<<blocks, 256, 0, s>>>(n, n_pad, p, M, y, X, lam, Bt),
-                      k_sumlog<<<1, 1024, 0, s>>>(n, y, sumlogy),
-                      k_min_dist2<<<dim3((unsigned)(nt * (nt + 1) / 2), min_dist_split(nt)), 256, 0, s>>>(
-                          n, coords, sumlogy + 1)));
+    const int split = (int)min_dist_split(nt);
+    const int64_t grid = blocks + 1 + nt * (nt + 1) / 2 * split;
+    TIMED(KC_BOXCOX, (k_dataset_front<<<(unsigned)grid, 256, 0, s>>>(blocks, split, n, n_pad, p, M, y, X, lam, Bt,
+                                                                     coords, sumlogy)));
     return cudaGetLastError();
 }
 
