@@ -313,6 +313,50 @@ __global__ void __launch_bounds__(256) k_table_owner(int cnt, const double *__re
 }
 
 // The owner's table covers the union of its sharers' octave ranges.
+// Both steps for a batch of at most 256 slots in one block (one launch
+// instead of two where the batch is small): the keys in shared memory, then
+// every slot's owner, then every owner's octave range over its members.
+constexpr int TABLE_SHARE_SMALL = 256;
+__global__ void __launch_bounds__(TABLE_SHARE_SMALL) k_table_share_small(int cnt, double *__restrict__ oconst,
+                                                                         const int *__restrict__ pstatus,
+                                                                         int *__restrict__ owner,
+                                                                         const int *__restrict__ dcount = nullptr) {
+    __shared__ unsigned long long key[TABLE_SHARE_SMALL];
+    __shared__ int okw[TABLE_SHARE_SMALL], own[TABLE_SHARE_SMALL], elo[TABLE_SHARE_SMALL], ehi[TABLE_SHARE_SMALL];
+    if (dcount) cnt = min(cnt, *dcount);
+    const int w = threadIdx.x;
+    if (w < cnt) {
+        const double *oc = oconst + OC_N * (int64_t)w;
+        key[w] = (unsigned long long)__double_as_longlong(oc[OC_KAPPA]);
+        okw[w] = pstatus[w] == PLK_POINT_OK;
+        elo[w] = (int)oc[OC_ELO];
+        ehi[w] = (int)oc[OC_EHI];
+    }
+    __syncthreads();
+    int b = w;
+    if (w < cnt && okw[w])
+        for (int v = 0; v < w; ++v)
+            if (okw[v] && key[v] == key[w]) {
+                b = v;
+                break;
+            }
+    if (w < cnt) {
+        own[w] = b;
+        owner[w] = b;
+    }
+    __syncthreads();
+    if (w < cnt && own[w] == w) {
+        int lo = elo[w], hi = ehi[w];
+        for (int v = w + 1; v < cnt; ++v)
+            if (own[v] == w) {
+                lo = min(lo, elo[v]);
+                hi = max(hi, ehi[v]);
+            }
+        oconst[OC_N * (int64_t)w + OC_ELO] = lo;
+        oconst[OC_N * (int64_t)w + OC_EHI] = hi;
+    }
+}
+
 __global__ void __launch_bounds__(256) k_table_union(int cnt, double *__restrict__ oconst, const int *__restrict__ owner,
                                                      const int *__restrict__ dcount = nullptr) {
     const int w = blockIdx.x;
@@ -1556,8 +1600,12 @@ cudaError_t launch_front(const BatchArgs &b, cudaStream_t s, FrontMode mode, boo
                                                       b.coordT, b.ldv, b.pstatus, f32, nullptr, b.dcount)));
     const dim3 tg((TAB_NBUCKET + 31) / 32, cnt), bg((unsigned)b.tpo, cnt);
     if (b.owner) {   // slots with the same kappa share one table
-        k_table_owner<<<cnt, 256, 0, s>>>(cnt, b.oconst, b.pstatus, b.owner, b.dcount);
-        k_table_union<<<cnt, 256, 0, s>>>(cnt, b.oconst, b.owner, b.dcount);
+        if (cnt <= TABLE_SHARE_SMALL) {
+            k_table_share_small<<<1, TABLE_SHARE_SMALL, 0, s>>>(cnt, b.oconst, b.pstatus, b.owner, b.dcount);
+        } else {
+            k_table_owner<<<cnt, 256, 0, s>>>(cnt, b.oconst, b.pstatus, b.owner, b.dcount);
+            k_table_union<<<cnt, 256, 0, s>>>(cnt, b.oconst, b.owner, b.dcount);
+        }
     }
     if (f32 && !build) {   // the fused path: tables spread over more blocks, 8 lanes per node
         const dim3 tg4((TAB_NBUCKET + 3) / 4, cnt);
