@@ -602,8 +602,7 @@ static plk_status run_fused_mixed_batch(BatchArgs b, const Layout &L, void *ws, 
     double *invsum = at<double>(ws, L.off_invsum);
     int *fl = at<int>(ws, L.off_flags);
     auto seq = [&]() {
-        cudaError_t e = launch_fused_df_batch(b, invsum, s);
-        if (e == cudaSuccess) e = launch_mixed_bound(b, FUSED_DF_EPS, g_mixed_tol.load(), 1, invsum, err_bound, fl, s);
+        cudaError_t e = launch_fused_df_batch(b, invsum, FUSED_DF_EPS, g_mixed_tol.load(), err_bound, fl, s);
         if (e == cudaSuccess && !(flags & PLK_FLAG_NO_RETRY)) e = launch_fused_fp64_gated(b, fl, err_bound, s);
         return e;
     };

@@ -1380,7 +1380,8 @@ __global__ void k_finalize(int count, int64_t k0, int M, int p, int64_t n, int n
                            const double *__restrict__ sumlogy, const double *__restrict__ lambdas,
                            double *logL, double *sigma2, double *beta, double *logdet,
                            double *ssq, int32_t *status, const int *__restrict__ out_index,
-                           int32_t status_or, const int *__restrict__ gate, const int *__restrict__ dcount = nullptr) {
+                           int32_t status_or, const int *__restrict__ gate, const int *__restrict__ dcount = nullptr,
+                           double *__restrict__ err_zero = nullptr) {
     const int w = blockIdx.x * blockDim.x + threadIdx.x;
     if (w >= count || beyond(dcount, w)) return;
     if (gate && !gate[w]) return;   // gated pass: only the flagged slots
@@ -1477,6 +1478,7 @@ __global__ void k_finalize(int count, int64_t k0, int M, int p, int64_t n, int n
                 o[a * q + c] = good ? -S[(a >= c ? a : c) * TB + (a >= c ? c : a)] : NaN;
     }
     if (status) status[k] = st | status_or;
+    if (err_zero) err_zero[k] = 0.0;   // an FP64 re-evaluation: no bound to carry
 }
 
 // ---------------------------------------------------------------------------
@@ -1916,7 +1918,9 @@ __global__ void __launch_bounds__(FUSED_DF_THREADS, 1) k_fused_small_df(int64_t 
                                                                      const double *__restrict__ Bt,
                                                                      const int *__restrict__ owner,
                                                                      double *__restrict__ ldv, int *__restrict__ pstatus,
-                                                                     double *__restrict__ invsum) {
+                                                                     double *__restrict__ invsum, int64_t k0,
+                                                                     double eps, double tol, double *err_bound,
+                                                                     int *__restrict__ flags) {
     extern __shared__ float2 Af[];
     const int w = blockIdx.x;
     const int R = (int)n + q, nn = (int)n;
@@ -1924,8 +1928,16 @@ __global__ void __launch_bounds__(FUSED_DF_THREADS, 1) k_fused_small_df(int64_t 
     float2 *pv = Af + P;   // the n pivots
     __shared__ double red[FUSED_DF_THREADS / 32], red2[FUSED_DF_THREADS / 32];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = FUSED_DF_THREADS / 32;
+    // the a-posteriori bound E = eps (1 + nu^2) sum 1/d_j of each point and
+    // its re-evaluation flag (E > tol or a failed factorisation), by thread 0
+    auto verdict = [&](double isum, bool not_pd) {
+        invsum[w] = isum;
+        const double E = eps * (1.0 + oconst[OC_N * (int64_t)w + OC_NUG]) * isum;
+        if (err_bound) err_bound[k0 + w] = E;
+        flags[w] = (not_pd || (pstatus[w] == PLK_POINT_OK && !(E <= tol))) ? 1 : 0;
+    };
     if (pstatus[w] != PLK_POINT_OK) {   // invalid parameters: the closed form writes NaN
-        if (tid == 0) invsum[w] = 0.0;
+        if (tid == 0) verdict(0.0, false);
         return;
     }
     const double *oc = oconst + OC_N * (int64_t)w;
@@ -2049,7 +2061,7 @@ __global__ void __launch_bounds__(FUSED_DF_THREADS, 1) k_fused_small_df(int64_t 
     if (fail) {
         if (tid == 0) {
             pstatus[w] = PLK_POINT_NOT_PD;
-            invsum[w] = 0.0;
+            verdict(0.0, true);
         }
         return;
     }
@@ -2083,11 +2095,12 @@ __global__ void __launch_bounds__(FUSED_DF_THREADS, 1) k_fused_small_df(int64_t 
             t2 += red2[k];
         }
         ldv[w] = t;
-        invsum[w] = t2;
+        verdict(t2, false);
     }
 }
 
-cudaError_t launch_fused_df_batch(const BatchArgs &b, double *invsum, cudaStream_t s) {
+cudaError_t launch_fused_df_batch(const BatchArgs &b, double *invsum, double eps, double tol, double *err_bound,
+                                  int *flags, cudaStream_t s) {
     const size_t smem = fused_smem_bytes(b.n, b.q);
     cudaError_t e = cudaFuncSetAttribute(k_fused_small_df, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -2095,7 +2108,8 @@ cudaError_t launch_fused_df_batch(const BatchArgs &b, double *invsum, cudaStream
     if ((e = launch_front(b, s, FRONT_DF_FAST, false)) != cudaSuccess) return e;
     TIMED(KC_FUSED, (k_fused_small_df<<<b.count, FUSED_DF_THREADS, smem, s>>>(b.n, b.n_pad, b.q, b.nb, b.tpo, b.tiles,
                                                                           b.oconst, b.coordT, b.tab, b.Bt, b.owner,
-                                                                          b.ldv, b.pstatus, invsum)));
+                                                                          b.ldv, b.pstatus, invsum, b.k0, eps, tol,
+                                                                          err_bound, flags)));
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     return launch_finalize(b, s);
 }
@@ -2125,11 +2139,6 @@ cudaError_t launch_fused_batch(const BatchArgs &b, cudaStream_t s) {
 // the whole batch and exiting for the other slots: no host read-back, so the
 // double-float pass and its re-evaluation form one asynchronous sequence (and
 // can be captured in a graph).  Tables are per slot (no sharing by kappa).
-__global__ void k_clear_gated(int count, int64_t k0, const int *__restrict__ gate, double *__restrict__ out) {
-    const int w = blockIdx.x * blockDim.x + threadIdx.x;
-    if (w < count && gate[w]) out[k0 + w] = 0.0;
-}
-
 cudaError_t launch_fused_fp64_gated(const BatchArgs &b, const int *gate, double *err_bound, cudaStream_t s) {
     const size_t smem = fused_smem_bytes(b.n, b.q);
     cudaError_t e = cudaFuncSetAttribute(k_fused_small, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -2147,8 +2156,7 @@ cudaError_t launch_fused_fp64_gated(const BatchArgs &b, const int *gate, double 
     TIMED(KC_FINAL, (k_finalize<<<(cnt + 63) / 64, 64, 0, s>>>(cnt, b.k0, b.M, b.p, b.n, b.nb, b.reml, b.tpo, b.tiles,
                                                                 b.ldv, b.pstatus, b.sumlogy, b.lambdas, b.logL,
                                                                 b.sigma2, b.beta, b.logdet, b.ssq, b.status,
-                                                                b.out_index, sor, gate)));
-    if (err_bound) k_clear_gated<<<(cnt + 127) / 128, 128, 0, s>>>(cnt, b.k0, gate, err_bound);
+                                                                b.out_index, sor, gate, nullptr, err_bound)));
     return cudaGetLastError();
 }
 

@@ -69,17 +69,19 @@ size_t fused_smem_bytes(int64_t n, int q);
 cudaError_t launch_fused_batch(const BatchArgs &b, cudaStream_t s);
 // the same in double-float FP32 (mixed precision); invsum[w] = sum_j 1/d_j of
 // the pivots (for the a-posteriori bound), 0 for points that failed
-cudaError_t launch_fused_df_batch(const BatchArgs &b, double *invsum, cudaStream_t s);
+// ... with each point's bound eps (1 + nu^2) sum 1/d_j into err_bound (may be
+// NULL) and its re-evaluation flag (bound above tol, or a failed
+// factorisation) into flags
+cudaError_t launch_fused_df_batch(const BatchArgs &b, double *invsum, double eps, double tol, double *err_bound,
+                                  int *flags, cudaStream_t s);
 // the FP64 fused evaluation of the slots w with gate[w] != 0 (device flags),
 // in place (status bits RETRIED | FP64, err_bound 0), without a host read-back
 cudaError_t launch_fused_fp64_gated(const BatchArgs &b, const int *gate, double *err_bound, cudaStream_t s);
 // relative perturbation of V's entries in the double-float fused Cholesky
 // (bound E = FUSED_DF_EPS (1 + nu^2) sum_j 1 / d_j)
 constexpr double FUSED_DF_EPS = 1.4551915228366852e-11;   // 2^-36
-// flags[w] = 1 where the bound exceeds tol or (flag_not_pd) the point is not
-// positive definite; err_bound[k] = the bound
-cudaError_t launch_mixed_bound(const BatchArgs &b, double eps, double tol, int flag_not_pd, const double *invsum,
-                               double *err_bound, int *flags, cudaStream_t s);
+// closed form (beta, sigma^2, l_p, Table-1 cross-products) from the last
+// diagonal tile of every point of the batch
 cudaError_t launch_finalize(const BatchArgs &b, cudaStream_t s);
 // smallest squared site distance into *min_dist2, the front in `mode`, then
 // the dense n x n matrices V of the batch into V (count x n x n)

@@ -1841,13 +1841,6 @@ cudaError_t launch_wait_selftest(uint32_t max_iter, int *err, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_mixed_bound(const BatchArgs &b, double eps, double tol, int flag_not_pd, const double *invsum,
-                               double *err_bound, int *flags, cudaStream_t s) {
-    k_mixed_bound<<<(b.count + 127) / 128, 128, 0, s>>>(b.count, b.k0, eps, tol, flag_not_pd, 0, b.oconst, invsum,
-                                                       b.pstatus, b.out_index, err_bound, flags);
-    return cudaGetLastError();
-}
-
 cudaError_t launch_scatter_value(int count, const int *idx, double v, double *out, cudaStream_t s,
                                  const int *dcount) {
     k_scatter_value<<<(count + 127) / 128, 128, 0, s>>>(count, idx, v, out, dcount);
