@@ -2,7 +2,8 @@
 // (Xu & Brown, arXiv 2305.04318, Section 3.3 "Step 3" and Table 2), for sm_103a.
 //
 // Pipeline for a batch of parameter points omega (one CUDA block grid per step):
-//   k_boxcox_rows   B^T = [y'(lambda_1..lambda_M) | X]^T           (Section 2 Box-Cox)
+//   k_dataset_front B^T = [y'(lambda_1..lambda_M) | X]^T, sum log y  (Section 2 Box-Cox)
+//                   and the smallest site distance, in one launch
 //   k_omega_prep    per-omega constants, rotated/scaled coordinates  (eq. matern)
 //   k_matern_table  per-omega piecewise polynomial of rho(w), w = 8 kappa d^2
 //   k_build         bordered matrix tiles: V = R + nu^2 I and B^T     (Step 3 item 1)
