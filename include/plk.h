@@ -90,10 +90,12 @@ typedef struct {
  * for measuring the 7-slice error itself). */
 #define PLK_FLAG_NO_FP64_TIER 4
 /* flags: launch each batch's kernel sequence as one CUDA graph (PLK_FP64: the
- * whole batch; PLK_MIXED: the 5-slice first pass and the 7-slice tier, whose
- * points are compacted on the device and whose kernels take their live count
- * from device memory; only an FP64 tier, in the rare batch where a point needs
- * one, runs eagerly after the graph).  The sequence is captured from
+ * whole batch; PLK_MIXED: the whole batch too -- the 5-slice pass, the 7-slice
+ * tier, whose points are compacted on the device and whose kernels take their
+ * live count from device memory, and the FP64 tier as the body of a
+ * conditional node that runs only when its device-side count is positive).
+ * On the legacy default stream, which cannot be captured, the launches stay
+ * eager.  The sequence is captured from
  * the stream with the same launch code and replayed; between batches of the
  * same shape the executable graph is only updated.  Results are identical to
  * the eager launches.  Ignored together with PLK_FLAG_KERNEL_TIMING. */

@@ -345,6 +345,56 @@ static cudaError_t launch_as_graph(cudaStream_t s, F &&enqueue) {
 }
 
 static bool use_graph(int flags) { return (flags & PLK_FLAG_GRAPH) && !(flags & PLK_FLAG_KERNEL_TIMING); }
+
+// A stream of this thread for capturing conditional bodies (created outside
+// any capture, on first use per device).
+static cudaStream_t body_stream() {
+    thread_local std::map<int, cudaStream_t> m;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+    cudaStream_t &x = m[dev];
+    if (!x && cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking) != cudaSuccess) x = nullptr;
+    return x;
+}
+
+// Inside a capture of s: the work `body` enqueues on the stream it is given
+// becomes the body of a conditional node that runs only when *count > 0 at
+// that point of the graph (the condition is set on the device by a one-thread
+// kernel), so a device-side count decides without a host read-back.
+template <class F>
+static cudaError_t enqueue_if_positive(cudaStream_t s, const int *count, F &&body) {
+    cudaStream_t bs = body_stream();
+    if (!bs) return cudaErrorNotReady;
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t g = nullptr;
+    const cudaGraphNode_t *deps = nullptr;
+    const cudaGraphEdgeData *edges = nullptr;
+    size_t nd = 0;
+    cudaError_t e = cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, &deps, &edges, &nd);
+    if (e != cudaSuccess) return e;
+    if (cs != cudaStreamCaptureStatusActive) return cudaErrorStreamCaptureUnmatched;
+    cudaGraphConditionalHandle h;
+    if ((e = cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault)) != cudaSuccess) return e;
+    if ((e = launch_set_condition(h, count, s)) != cudaSuccess) return e;
+    if ((e = cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, &deps, &edges, &nd)) != cudaSuccess) return e;
+    cudaGraphNodeParams p = {};
+    p.type = cudaGraphNodeTypeConditional;
+    p.conditional.handle = h;
+    p.conditional.type = cudaGraphCondTypeIf;
+    p.conditional.size = 1;
+    cudaGraphNode_t node;
+    if ((e = cudaGraphAddNode(&node, g, deps, edges, nd, &p)) != cudaSuccess) return e;
+    if ((e = cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies)) !=
+        cudaSuccess)
+        return e;
+    if ((e = cudaStreamBeginCaptureToGraph(bs, p.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                           cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+        return e;
+    const cudaError_t le = body(bs);
+    cudaGraph_t out = nullptr;
+    e = cudaStreamEndCapture(bs, &out);
+    return le != cudaSuccess ? le : e;
+}
 // Small datasets go through the fused one-CTA-per-point kernel in either
 // precision (FP64 there costs less than the tiled tensor-core path).
 static bool use_fused(int64_t n, int q, int flags) { return fused_applies(n, q) && !(flags & PLK_FLAG_NO_FUSED); }
@@ -542,14 +592,19 @@ static plk_status run_mixed_batch(BatchArgs b, const Layout &L, void *ws, const 
     // compaction of the points whose bound it flags and the gather of their
     // parameters; the 7-slice pass over them, launched over the batch's slots
     // with the device-side count deciding which are live; the compaction of the
-    // points still flagged.  No decision reads the flags back.  The one read at
-    // the end takes the device error flag (a tensor-core wait that gave up) and
-    // the FP64 tier's count: in the rare batch where it is not zero, the FP64
-    // pass follows over exactly those points (launched over the whole batch
-    // instead, it would cost ~2 % of a step in empty thread blocks).
+    // points still flagged.  No decision reads the flags back.  As a graph,
+    // the FP64 pass over those points is the body of a conditional node that
+    // runs only when their count is positive (set on the device).  Eagerly,
+    // the one read at the end takes the device error flag (a tensor-core wait
+    // that gave up) and that count, and in the rare batch where it is not
+    // zero the FP64 pass follows over exactly those points (launched
+    // unconditionally over the whole batch, it would cost ~2 % of a step in
+    // empty thread blocks).
     int *d_idx = at<int>(ws, L.off_idx), *d_idx2 = at<int>(ws, L.off_idx2), *d_cnt = at<int>(ws, L.off_cnt);
     double *d_par = at<double>(ws, L.off_cparams);
     const bool fp64_tier = !(flags & (PLK_FLAG_NO_RETRY | PLK_FLAG_NO_FP64_TIER));
+    // a graph only where launch_as_graph captures (not on the legacy stream)
+    const bool graph = use_graph(flags) && s != nullptr && s != cudaStreamLegacy;
     auto seq = [&]() {
         cudaError_t e = cudaMemsetAsync(x.err, 0, sizeof(int), s);
         if (e == cudaSuccess) e = cudaMemsetAsync(d_cnt, 0, 2 * sizeof(int), s);
@@ -566,10 +621,25 @@ static plk_status run_mixed_batch(BatchArgs b, const Layout &L, void *ws, const 
         e = launch_mixed_batch(r, x, 7, s);   // flags[j] <- the 7-slice verdict of live slot j
         if (e == cudaSuccess && fp64_tier)
             e = launch_compact_flags(b.count, x.flags, d_cnt, 0, d_idx, d_idx2, d_cnt + 1, s);
+        if (e == cudaSuccess && fp64_tier && graph)   // the FP64 tier inside the graph, run if its count > 0
+            e = enqueue_if_positive(s, d_cnt + 1, [&](cudaStream_t bs) {
+                BatchArgs f = b;
+                f.params = d_par;
+                f.out_index = d_idx2;
+                f.status_or = PLK_POINT_RETRIED | PLK_POINT_FP64;
+                f.dcount = d_cnt + 1;
+                cudaError_t fe = launch_gather_params(b.count, d_idx2, params_all, d_par, bs, d_cnt + 1);
+                if (fe == cudaSuccess) fe = launch_fp64_batch(f, bs);
+                if (fe == cudaSuccess && err_bound) fe = launch_scatter_value(b.count, d_idx2, 0.0, err_bound, bs, d_cnt + 1);
+                return fe;
+            });
         return e;
     };
-    if (use_graph(flags) && overlap) aux_streams();   // create the helper streams outside the capture
-    cudaError_t e = use_graph(flags) ? launch_as_graph(s, seq) : seq();
+    if (graph) {   // create the helper streams outside the capture
+        if (overlap) aux_streams();
+        body_stream();
+    }
+    cudaError_t e = graph ? launch_as_graph(s, seq) : seq();
     if (e != cudaSuccess) return cuda_fail(e, "mixed batch launch");
     int h[3] = {0, 0, 0};   // error flag, counts of the 7-slice and FP64 tiers
     e = cudaMemcpyAsync(h, x.err, sizeof(int), cudaMemcpyDeviceToHost, s);
@@ -577,7 +647,7 @@ static plk_status run_mixed_batch(BatchArgs b, const Layout &L, void *ws, const 
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(e, "mixed batch");
     if (h[0]) return fail(PLK_E_TIMEOUT, "a tensor-core wait gave up (device error flag set)");
-    if (!fp64_tier || h[2] == 0) return PLK_OK;
+    if (!fp64_tier || graph || h[2] == 0) return PLK_OK;   // in a graph the tier has run already
     BatchArgs f = b;
     f.count = h[2];
     f.params = d_par;

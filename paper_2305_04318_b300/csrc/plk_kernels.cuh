@@ -105,6 +105,8 @@ cudaError_t launch_mixed_back(const BatchArgs &b, const MixedArgs &x, int S, cud
 // Wait-cycle counters of the 5-slice trailing update (3 launch modes x 9;
 // cudaErrorNotSupported unless built with -DPLK_PIPE_COUNTERS)
 cudaError_t pipe_counters(unsigned long long *out, int reset);
+// sets the graph conditional h to (*count > 0) on the device
+cudaError_t launch_set_condition(cudaGraphConditionalHandle h, const int *count, cudaStream_t s);
 // out_idx[j] = output row of the j-th slot w < min(count, *live) with flags[w]
 // set (map[w], or k0 + w), *out_count = their number; one block, slot order
 cudaError_t launch_compact_flags(int count, const int *flags, const int *live, int64_t k0, const int *map,

@@ -1654,6 +1654,17 @@ cudaError_t pipe_counters(unsigned long long *out, int reset) {
 #endif
 }
 
+// The IF condition of a graph's conditional node from a device-side count
+// (one thread): the node's body runs only where *count > 0.
+__global__ void k_set_condition(cudaGraphConditionalHandle h, const int *__restrict__ count) {
+    if (threadIdx.x == 0) cudaGraphSetConditional(h, *count > 0 ? 1u : 0u);
+}
+
+cudaError_t launch_set_condition(cudaGraphConditionalHandle h, const int *count, cudaStream_t s) {
+    k_set_condition<<<1, 32, 0, s>>>(h, count);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_compact_flags(int count, const int *flags, const int *live, int64_t k0, const int *map,
                                  int *out_idx, int *out_count, cudaStream_t s) {
     k_compact_flags<<<1, 1024, 0, s>>>(count, flags, live, k0, map, out_idx, out_count);

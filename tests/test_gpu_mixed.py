@@ -254,13 +254,18 @@ def test_retry_tiers_on_the_device(graph):
     results equal the FP64 path's bit for bit (status bits RETRIED | FP64,
     err_bound 0), eagerly and as one CUDA graph; at the default tolerance the
     same call gives the usual mixed results."""
+    import torch
     w = synth.aniso1000(K=20)
     ds, P = w.datasets[0], w.params[0]
     f = gpu_eval(ds, P, w.lambdas, precision=nv.FP64)
     fl = nv.FLAG_GRAPH if graph else 0
+    # a graph is captured on a stream of its own (the legacy default stream
+    # cannot be captured); there the FP64 tier is a conditional node's body
+    st = torch.cuda.Stream() if graph else None
     try:
         nv.set_mixed_tolerance(1e-12)
-        g = gpu_eval(ds, P, w.lambdas, precision=nv.MIXED, batch=12, flags=fl)
+        with torch.cuda.stream(st) if st is not None else torch.cuda.stream(torch.cuda.current_stream()):
+            g = gpu_eval(ds, P, w.lambdas, precision=nv.MIXED, batch=12, flags=fl)
     finally:
         nv.set_mixed_tolerance(1e-3)
     live = f["status"] == 0
@@ -269,7 +274,8 @@ def test_retry_tiers_on_the_device(graph):
     assert np.all(g["err_bound"][live] == 0.0)
     for k in ("logL", "sigma2", "beta", "logdet"):
         np.testing.assert_array_equal(g[k][live], f[k][live], err_msg=k)
-    m = gpu_eval(ds, P, w.lambdas, precision=nv.MIXED, batch=12, flags=fl)
+    with torch.cuda.stream(st) if st is not None else torch.cuda.stream(torch.cuda.current_stream()):
+        m = gpu_eval(ds, P, w.lambdas, precision=nv.MIXED, batch=12, flags=fl)
     mixed_compare(m, f, "default tolerance vs FP64 GPU", coords=ds.coords, params=P)
 
 
