@@ -329,53 +329,47 @@ __host__ __device__ constexpr double mixed_eps(int S) {
 constexpr size_t POTRF_MIXED_SMEM = (size_t)(PK + 3 * DB * DB) * sizeof(double);
 
 // Cholesky of the tile in the packed lower triangle P (number type Ar::T) in
-// 32-column panels: each column's pivot and scale by warp 0, two columns per
-// block barrier (warp 0 factors column j, applies it to column j + 1 and
-// factors that; the block then applies both to the rest of the panel, each
-// entry's two updates in column order: the operations of a column-by-column
-// factorisation with half the barriers), then the panel's rank-32 update of
-// the trailing lower triangle in 4 x 4 register tiles.  A non-positive pivot
-// leaves NaN behind it; the pivot itself is kept (piv) for the status.
+// 32-column panels, two columns per block barrier: every thread forms the
+// pair's pivots itself (1/sqrt(d_j), L_{j+1,j}, d_{j+1} and its 1/sqrt: the
+// same operations in every thread), then one thread per row scales its entry
+// of column j, applies it to column j + 1 and scales that -- a row's
+// operations exactly as a column-by-column factorisation orders them -- and,
+// after the barrier, thread 0 writes the pair's diagonal entries while the
+// block applies both columns to the rest of the panel; then the panel's
+// rank-32 update of the trailing lower triangle in 4 x 4 register tiles.  A
+// non-positive pivot leaves NaN behind it; the pivot itself is kept (piv) for
+// the status.
 template <class Ar>
 __device__ __forceinline__ void chol_tile(typename Ar::T *__restrict__ P, typename Ar::T *col,
                                           typename Ar::T *col2, double *piv, int tid) {
     using T = typename Ar::T;
-    const int lane = tid & 31, warp = tid >> 5;
     for (int kb = 0; kb < TB; kb += DB) {
         const int kend = kb + DB - 1;
         for (int j = kb; j <= kend; j += 2) {
-            if (warp == 0) {
-                const T d = P[pk(j, j)];
-                const T rl = Ar::rsqrt_(d);
-                __syncwarp();   // every lane has read the pivot before lane 0 replaces it
-                if (lane == 0) {
-                    piv[j] = Ar::value(d);
-                    P[pk(j, j)] = Ar::mul(d, rl);
-                }
-                for (int i = j + 1 + lane; i < TB; i += 32) {
-                    const T v = Ar::mul(P[pk(i, j)], rl);
-                    P[pk(i, j)] = v;
-                    col[i] = v;
-                }
-                __syncwarp();
-                const T cj1 = col[j + 1];
-                for (int i = j + 1 + lane; i < TB; i += 32) P[pk(i, j + 1)] = Ar::fms(P[pk(i, j + 1)], col[i], cj1);
-                __syncwarp();
-                const T d2 = P[pk(j + 1, j + 1)];
-                const T rl2 = Ar::rsqrt_(d2);
-                __syncwarp();
-                if (lane == 0) {
-                    piv[j + 1] = Ar::value(d2);
-                    P[pk(j + 1, j + 1)] = Ar::mul(d2, rl2);
-                }
-                for (int i = j + 2 + lane; i < TB; i += 32) {
-                    const T v = Ar::mul(P[pk(i, j + 1)], rl2);
-                    P[pk(i, j + 1)] = v;
-                    col2[i] = v;
-                }
+            const T d = P[pk(j, j)];
+            const T rl = Ar::rsqrt_(d);
+            const T cj1 = Ar::mul(P[pk(j + 1, j)], rl);   // L_{j+1,j}
+            const T d2 = Ar::fms(P[pk(j + 1, j + 1)], cj1, cj1);
+            const T rl2 = Ar::rsqrt_(d2);
+            const int i = j + 2 + tid;                       // this thread's row
+            if (i < TB) {
+                const T v = Ar::mul(P[pk(i, j)], rl);
+                P[pk(i, j)] = v;
+                col[i] = v;
+                const T v2 = Ar::mul(Ar::fms(P[pk(i, j + 1)], v, cj1), rl2);
+                P[pk(i, j + 1)] = v2;
+                col2[i] = v2;
             }
             __syncthreads();
+            if (tid == 0) {   // every thread has read the pair's entries
+                piv[j] = Ar::value(d);
+                piv[j + 1] = Ar::value(d2);
+                P[pk(j, j)] = Ar::mul(d, rl);
+                P[pk(j + 1, j)] = cj1;
+                P[pk(j + 1, j + 1)] = Ar::mul(d2, rl2);
+            }
             const int nk = kend - j - 1;   // panel columns right of j + 1
+            if (nk == 0) __syncthreads();   // no panel update follows: publish thread 0's writes
             if (nk > 0) {
                 // rows j+2 .. kend (k <= i: a triangle), then rows below the panel (all nk columns)
                 const int tri = nk * (nk + 1) / 2;
