@@ -329,7 +329,7 @@ __host__ __device__ constexpr double mixed_eps(int S) {
 constexpr size_t POTRF_MIXED_SMEM = (size_t)(PK + 3 * DB * DB) * sizeof(double);
 
 // Cholesky of the tile in the packed lower triangle P (number type Ar::T) in
-// 32-column panels, two columns per block barrier: every thread forms the
+// 32-column panels, two columns per block barrier: each of warps 0-3 forms the
 // pair's pivots itself (1/sqrt(d_j), L_{j+1,j}, d_{j+1} and its 1/sqrt: the
 // same operations in every thread), then one thread per row scales its entry
 // of column j, applies it to column j + 1 and scales that -- a row's
@@ -346,19 +346,25 @@ __device__ __forceinline__ void chol_tile(typename Ar::T *__restrict__ P, typena
     for (int kb = 0; kb < TB; kb += DB) {
         const int kend = kb + DB - 1;
         for (int j = kb; j <= kend; j += 2) {
-            const T d = P[pk(j, j)];
-            const T rl = Ar::rsqrt_(d);
-            const T cj1 = Ar::mul(P[pk(j + 1, j)], rl);   // L_{j+1,j}
-            const T d2 = Ar::fms(P[pk(j + 1, j + 1)], cj1, cj1);
-            const T rl2 = Ar::rsqrt_(d2);
-            const int i = j + 2 + tid;                       // this thread's row
-            if (i < TB) {
-                const T v = Ar::mul(P[pk(i, j)], rl);
-                P[pk(i, j)] = v;
-                col[i] = v;
-                const T v2 = Ar::mul(Ar::fms(P[pk(i, j + 1)], v, cj1), rl2);
-                P[pk(i, j + 1)] = v2;
-                col2[i] = v2;
+            // warps 0-3 (one per SM sub-partition; 128 threads cover the <= 126
+            // rows): the FP64 instance issues the pivots' square roots once per
+            // sub-partition, not per warp
+            T d, rl, cj1, d2, rl2;
+            if (tid < 128) {
+                d = P[pk(j, j)];
+                rl = Ar::rsqrt_(d);
+                cj1 = Ar::mul(P[pk(j + 1, j)], rl);   // L_{j+1,j}
+                d2 = Ar::fms(P[pk(j + 1, j + 1)], cj1, cj1);
+                rl2 = Ar::rsqrt_(d2);
+                const int i = j + 2 + tid;              // this thread's row
+                if (i < TB) {
+                    const T v = Ar::mul(P[pk(i, j)], rl);
+                    P[pk(i, j)] = v;
+                    col[i] = v;
+                    const T v2 = Ar::mul(Ar::fms(P[pk(i, j + 1)], v, cj1), rl2);
+                    P[pk(i, j + 1)] = v2;
+                    col2[i] = v2;
+                }
             }
             __syncthreads();
             if (tid == 0) {   // every thread has read the pair's entries
