@@ -35,9 +35,9 @@ import time
 import numpy as np
 
 # DRAM traffic model of the dominant mixed-path kernel, k_trail_pipe<5> (the
-# 5-slice trailing update), per kind of launch, in bytes per half-tile work
-# item (both column halves of every tile a launch updates, over all points of
-# the part): the data triangle (four panels per item; each operand image is
+# 5-slice trailing update), per kind of launch, in bytes per work item (a
+# half tile for the data rows, a whole tile for the right-hand-side row, over
+# all points of the part): the data triangle (four panels per item; each operand image is
 # re-read by many items, mostly from L2), one tile column's data rows (the
 # group's earlier panels: every item reads its own operand images, so they
 # come from DRAM: a term per item and panel) and the right-hand-side row (its
@@ -50,9 +50,9 @@ import numpy as np
 # verdict stops skip their items, so at full size this is an upper bound.
 # Valid for the kernel source it was taken on (SHA-256 below), else traffic is
 # null.
-TRAIL_TRAFFIC = {"tri_item": 184208.8, "col_item": 115834.3, "col_item_panel": 84547.9, "rhs_item": 95921.9,
+TRAIL_TRAFFIC = {"tri_item": 184226.6, "col_item": 115869.1, "col_item_panel": 84528.1, "rhs_item": 191195.1,
                  "fit_rel_rms": 0.081,
-                 "sources_sha256": "0363894af3e228ef31935b554b0e52b9869e3c9e9139dc5566e2b72e830c35ed"}
+                 "sources_sha256": "64e808de636ca4a592c060a2fc52f9cd2a5a26704e425e440f6342611c489c63"}
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
@@ -718,7 +718,9 @@ def trail_launches(n, part, TB=128, GP=4):
         if m <= 0:
             return
         T = m * (m + 1) // 2 if mode == 0 else m
-        out.append((part * T * 2, P, mode))   # 0: data triangle, 1: one column's data rows, 2: right-hand-side row
+        # 0: data triangle, 1: one column's data rows (half-tile items);
+        # 2: right-hand-side row (whole-tile items, run transposed)
+        out.append((part * T * (1 if mode == 2 else 2), P, mode))
     for J0 in range(0, nb, GP):
         G = min(GP, nb - J0)
         Jend = J0 + G
@@ -955,8 +957,12 @@ def main():
         # points that complete it are counted (a lower bound: the retried
         # points' partial work is left out)
         n5 = n_pts - n7
-        tiles = sum((nb - J) * (nb - J + 1) // 2 for J in range(nb))
-        executed = 2.0 * 128 ** 3 * tiles * split_pairs(5) * n5
+        # per panel J: the data tiles (m (m - 1) / 2, m = nb - J) are 128 x 128 x 128
+        # products; the m right-hand-side tiles run transposed with N = the
+        # right-hand-side rows rounded up to 8, then to 32
+        nr = -(-(-(-q // 8) * 8) // 32) * 32
+        cols = sum((nb - J) * (nb - J - 1) // 2 * 128 + (nb - J) * nr for J in range(nb))
+        executed = 2.0 * 128 ** 2 * cols * split_pairs(5) * n5
         peak = peaks.get("bf16_tflops_sustained") or 1341.1
         alg = tf * n5 / (dom_ms * 1e-3) / 1e12
         roof = {"bound": "tensor", "achieved": alg, "peak": peak, "unit": "TFLOP/s", "frac": alg / peak,
@@ -964,7 +970,7 @@ def main():
                 "achieved_is": "algorithmic FP64-equivalent trailing-update flops (n^3/3 + n^2 q per omega, omega that complete the 5-slice pass) / kernel time",
                 "executed_bf16_tflops": executed / (dom_ms * 1e-3) / 1e12,
                 "executed_frac": executed / (dom_ms * 1e-3) / 1e12 / peak,
-                "executed_is": "bf16 MMA flops issued by this kernel for the omega that complete the 5-slice pass: 15 slice products per multiply-add, 128x128 tiles",
+                "executed_is": "bf16 MMA flops issued by this kernel for the omega that complete the 5-slice pass: 15 slice products per multiply-add, 128x128 data tiles, 128 x NR right-hand-side tiles (NR = M + p rounded up to 32)",
                 "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (kernel timed inside a long step)",
                 "fp64_equivalent_over_fp64_fma_peak": alg / fp64_peak,
                 "points_7slice": n7, "points_fp64": n64}

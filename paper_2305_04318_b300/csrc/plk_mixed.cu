@@ -1039,7 +1039,7 @@ struct Cfg {
 // FP32 accumulators of groups 0-2 stay exact up to K = 4 x 128: with every
 // data row of L bounded by sqrt(1 + nu^2) < 2^e (Cauchy-Schwarz over the
 // leading digits), group 2's sums stay below 2^23.2 units.
-template <int S>
+template <int S, bool RT = false>
 __global__ void __launch_bounds__(pipe::NTHP, 1) k_trail_pipe(int mode, int Klo, int Ihi, int P, int sub0,
                                                              int nb, int cnt, int64_t tpo,
                                                              const __grid_constant__ CUtensorMap tmapC,
@@ -1061,8 +1061,17 @@ __global__ void __launch_bounds__(pipe::NTHP, 1) k_trail_pipe(int mode, int Klo,
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int m = Ihi - Klo + 1;
     const int T = (mode == 0) ? m * (m + 1) / 2 : m;
+    // RT (5 slices, mode 2 only): the right-hand-side row runs transposed, one
+    // item per tile (I = nb, K) with the tile of L_K (128 rows) as the M
+    // operand and the right-hand-side image's first NR rows (qr rounded up to
+    // 32; M + p <= 64 keeps NR <= 64) as B, so that C(nb, K)^T -= L_K R^T: its
+    // q <= 64 live rows cost N = NR columns instead of M = 128 rows twice.  A
+    // template argument, so that the other item sets compile without it.
+    constexpr bool rt = RT && S == 5;
+    const int NH = rt ? 1 : 2;             // items per tile (column halves)
+    const int NR = (qr + 31) & ~31;
     if (dcount) cnt = min(cnt, *dcount);   // a compacted batch: its live slots only
-    const int64_t items = (int64_t)cnt * T * 2;
+    const int64_t items = (int64_t)cnt * T * NH;
     if (tid == 0) {
         for (int i = 0; i < 2; ++i) {
             tc::mbar_init(&bFull[i], S);   // one arrival (with its bytes) per slice lane
@@ -1093,10 +1102,10 @@ __global__ void __launch_bounds__(pipe::NTHP, 1) k_trail_pipe(int mode, int Klo,
 #endif
 
     auto decode = [&](int64_t it, int &w, int &I, int &K, int &ch) {
-        w = (int)(it / (2 * T));
-        const int rem = (int)(it - (int64_t)w * 2 * T);
-        ch = rem & 1;
-        const int t = rem >> 1;
+        w = (int)(it / (NH * T));
+        const int rem = (int)(it - (int64_t)w * NH * T);
+        ch = (NH == 2) ? rem & 1 : 0;
+        const int t = (NH == 2) ? rem >> 1 : rem;
         if (mode == 0) {
             decode_trailing(t, Klo - 1, I, K);
         } else if (mode == 1) {
@@ -1126,7 +1135,7 @@ __global__ void __launch_bounds__(pipe::NTHP, 1) k_trail_pipe(int mode, int Klo,
                 if (doomed && doomed[w]) continue;
                 for (int ph = 0; ph < 2 * P && !stop; ++ph) {
                     const int h = ph & 1;
-                    const uint8_t *ia = image(w, I, ph >> 1), *ib = image(w, K, ph >> 1);
+                    const uint8_t *ia = image(w, rt ? K : I, ph >> 1), *ib = image(w, rt ? I : K, ph >> 1);
                     const int bs = bcnt & 1;
                     const uint32_t bu = bcnt >> 1;
                     ++bcnt;
@@ -1137,8 +1146,11 @@ __global__ void __launch_bounds__(pipe::NTHP, 1) k_trail_pipe(int mode, int Klo,
                             stop = true;
                             break;
                         }
-                        tc::mbar_arrive_expect_tx(&bFull[bs], HBLK);
-                        tc::bulk_g2s(sbase + bs * BBUF + j * HBLK, ib + (size_t)(j * 2 + h) * SBLK + ch * HBLK, HBLK,
+                        // B slice j: rows 64 ch .. +63 of the K tile, or the first
+                        // NR rows of the right-hand-side image (slices NR rows apart)
+                        const uint32_t bb = rt ? (uint32_t)NR * 128u : (uint32_t)HBLK;
+                        tc::mbar_arrive_expect_tx(&bFull[bs], bb);
+                        tc::bulk_g2s(sbase + bs * BBUF + j * bb, ib + (size_t)(j * 2 + h) * SBLK + ch * HBLK, bb,
                                      &bFull[bs]);
                     }
                     for (int i = 0; i < S; ++i, ++acnt) {
@@ -1161,7 +1173,7 @@ __global__ void __launch_bounds__(pipe::NTHP, 1) k_trail_pipe(int mode, int Klo,
             uint32_t acnt = 0, bcnt = 0, tcnt = 0;
             bool issued = false;
             for (int64_t it = blockIdx.x; it < items && !*verr; it += gridDim.x) {
-                if (doomed && doomed[(int)(it / (2 * T))]) continue;
+                if (doomed && doomed[(int)(it / (NH * T))]) continue;
                 const int set = (NSET == 2) ? (int)(tcnt & 1) : 0;
                 const uint32_t tu = (NSET == 2) ? tcnt >> 1 : tcnt;
                 if (tu > 0 && !PIPE_TIMED(2, tc::mbar_wait(&accEmpty[set], (tu - 1) & 1))) { *verr = 1; break; }
@@ -1192,7 +1204,24 @@ __global__ void __launch_bounds__(pipe::NTHP, 1) k_trail_pipe(int mode, int Klo,
                             // Where one A slice feeds two MMAs, the first keeps it in
                             // the tensor core's collector buffer and the second takes it
                             // from there: A is read from shared memory once per K step.
-                            if (S == 5) {
+                            if (S == 5 && rt && NR == 32) {
+                                // five 32-column accumulators (group g at column 32 g):
+                                // B slices 0 .. 4 - i in one MMA into groups i .. 4
+                                tc::mma_bf16(dacc + 32 * i, ad, bk, tc::idesc_bf16_f32(128, 32 * (5 - i)), acc);
+                            } else if (S == 5 && rt) {
+                                // NR = 64: the half-tile group layout with 64-column
+                                // accumulators (groups 0-3; group 4 into 3), B slices
+                                // 64 rows apart
+                                const uint32_t nrd = (uint32_t)NR * 128u >> 4;
+                                if (i < 4) {
+                                    tc::mma_bf16_ca<tc::Collector::FILL>(dacc + NR * i, ad, bk,
+                                                                         tc::idesc_bf16_f32(128, NR * (4 - i)), acc);
+                                    tc::mma_bf16_ca<tc::Collector::LASTUSE>(dacc + 3 * NR, ad, bk + (4 - i) * nrd,
+                                                                            tc::idesc_bf16_f32(128, NR), 1u);
+                                } else {
+                                    tc::mma_bf16(dacc + 3 * NR, ad, bk, tc::idesc_bf16_f32(128, NR), 1u);
+                                }
+                            } else if (S == 5) {
                                 if (i < 4) {
                                     tc::mma_bf16_ca<tc::Collector::FILL>(dacc + 64 * i, ad, bk,
                                                                          tc::idesc_bf16_f32(128, 64 * (4 - i)), acc);
@@ -1255,10 +1284,17 @@ __global__ void __launch_bounds__(pipe::NTHP, 1) k_trail_pipe(int mode, int Klo,
             if (et == 0) {
                 // the previous item's stores have read the buffer: load this item's half tile
                 PIPE_TIMED(7, (tc::bulk_wait_read_all(), 0));
-                tc::mbar_arrive_expect_tx(&cFull, 4 * rows * 128);
+                if (rt) {   // the whole tile width: boxes [H, 32 b | L, 32 b], qr rows each
+                    tc::mbar_arrive_expect_tx(&cFull, 8 * qr * 128);
 #pragma unroll
-                for (int bx = 0; bx < 4; ++bx)
-                    tc::tma_load_2d(sC + bx * CBOX, tm, 64 * ch + 32 * (bx & 1), yH + 128 * (bx >> 1), &cFull);
+                    for (int bx = 0; bx < 8; ++bx)
+                        tc::tma_load_2d(sC + bx * qr * 128, tm, 32 * (bx & 3), yH + 128 * (bx >> 2), &cFull);
+                } else {
+                    tc::mbar_arrive_expect_tx(&cFull, 4 * rows * 128);
+#pragma unroll
+                    for (int bx = 0; bx < 4; ++bx)
+                        tc::tma_load_2d(sC + bx * CBOX, tm, 64 * ch + 32 * (bx & 1), yH + 128 * (bx >> 1), &cFull);
+                }
                 c_pending = true;
             }
             if (P >= 2) {
@@ -1266,7 +1302,7 @@ __global__ void __launch_bounds__(pipe::NTHP, 1) k_trail_pipe(int mode, int Klo,
                 if (et < TB) sEA[et] = ec;
                 else if (et < TB + 64) sEB[et - TB] = ec;
             } else {
-                const uint8_t *ia = image(w, I, 0), *ib = image(w, K, 0);
+                const uint8_t *ia = image(w, rt ? K : I, 0), *ib = image(w, rt ? I : K, 0);
                 if (et < TB) sEA[et] = (short)reinterpret_cast<const int *>(ia + (size_t)S * 2 * SBLK)[et];
                 else if (et < TB + 64)
                     sEB[et - TB] = (short)reinterpret_cast<const int *>(ib + (size_t)S * 2 * SBLK)[64 * ch + et - TB];
@@ -1288,7 +1324,41 @@ __global__ void __launch_bounds__(pipe::NTHP, 1) k_trail_pipe(int mode, int Klo,
 #ifdef PLK_PIPE_COUNTERS
             const long long pc_upd = clock64();
 #endif
-            if (32 * (warp & 3) < rows) {   // warps whose rows all lie beyond an RHS tile's rows skip
+            if (rt) {
+                // transposed right-hand-side item: this thread's TMEM lane r is
+                // column r of the C tile; warps 4-7 take rows 0-7, 16-23, ...,
+                // warps 8-11 rows 8-15, 24-31, ... (qr is a multiple of 8)
+                const uint32_t a = tb + set * 256 + ((uint32_t)(32 * (warp & 3)) << 16);
+                const int ea = sEA[r] - 14;
+                float *cH = reinterpret_cast<float *>(sC + (r >> 5) * qr * 128);
+                float *cL = reinterpret_cast<float *>(sC + (4 + (r >> 5)) * qr * 128);
+                const int kc = (r & 31) >> 2, kw = r & 3;
+#pragma unroll 1
+                for (int rb = 8 * q; rb < qr; rb += 16) {
+                    uint32_t p0[8], p1[8], p2[8], p3[8], p4[8];
+                    tc::tmem_ld8(a + 0 * NR + rb, p0);
+                    tc::tmem_ld8(a + 1 * NR + rb, p1);
+                    tc::tmem_ld8(a + 2 * NR + rb, p2);
+                    tc::tmem_ld8(a + 3 * NR + rb, p3);
+                    if (NR == 32) tc::tmem_ld8(a + 4 * NR + rb, p4);   // group 4's own accumulator
+                    tc::tmem_wait_ld();
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) {
+                        const int rr = rb + c;
+                        // groups 3 and 4 summed in FP32, as one shared accumulator would
+                        const uint32_t g3 =
+                            NR == 32 ? __float_as_uint(__uint_as_float(p3[c]) + __uint_as_float(p4[c])) : p3[c];
+                        float dh, dl;
+                        group_value(p0[c], p1[c], p2[c], g3, ea + sEB[rr], dh, dl);
+                        const int x = rr * 32 + ((kc ^ (rr & 7)) << 2) + kw;
+                        float h = cH[x], l = cL[x];
+                        df_add(h, l, -dh);
+                        df_add(h, l, -dl);
+                        cH[x] = h;
+                        cL[x] = l;
+                    }
+                }
+            } else if (32 * (warp & 3) < rows) {   // warps whose rows all lie beyond an RHS tile's rows skip
                 const uint32_t a = tb + set * 256 + ((uint32_t)(32 * (warp & 3)) << 16) + 32 * q;
                 const int ea = sEA[r] - 14;
                 const short *eb = sEB + 32 * q;
@@ -1347,9 +1417,15 @@ __global__ void __launch_bounds__(pipe::NTHP, 1) k_trail_pipe(int mode, int Klo,
 #endif
             if (et == 0) {
                 tc::mbar_arrive(&accEmpty[set]);   // the MMA warp may reuse this set
+                if (rt) {
 #pragma unroll
-                for (int bx = 0; bx < 4; ++bx)
-                    tc::tma_store_2d(tm, 64 * ch + 32 * (bx & 1), yH + 128 * (bx >> 1), sC + bx * CBOX);
+                    for (int bx = 0; bx < 8; ++bx)
+                        tc::tma_store_2d(tm, 32 * (bx & 3), yH + 128 * (bx >> 2), sC + bx * qr * 128);
+                } else {
+#pragma unroll
+                    for (int bx = 0; bx < 4; ++bx)
+                        tc::tma_store_2d(tm, 64 * ch + 32 * (bx & 1), yH + 128 * (bx >> 1), sC + bx * CBOX);
+                }
                 tc::bulk_commit();
             }
             ++tcnt;
@@ -1775,17 +1851,20 @@ static cudaError_t launch_mixed_steps(const BatchArgs &b, const MixedArgs &x, cu
             cudaSuccess)
             return e;
         if ((e = cudaFuncSetAttribute(k_trail_pipe<5>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      pipe::Cfg<5>::SMEM)) != cudaSuccess ||
+            (e = cudaFuncSetAttribute(k_trail_pipe<5, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       pipe::Cfg<5>::SMEM)) != cudaSuccess)
             return e;
         auto trail = [&](int mode, int Klo, int Ihi, int P, int sub0) {
             const int m = Ihi - Klo + 1;
             if (m <= 0) return;
             const int64_t T = (mode == 0) ? (int64_t)m * (m + 1) / 2 : m;
-            const int64_t items = (int64_t)cnt * T * 2;
+            const int64_t items = (int64_t)cnt * T * (mode == 2 ? 1 : 2);   // mode 2: whole tiles
             const int grid = (int)std::min<int64_t>(items, sms);
-            TIMED(KC_GEMM_SPLIT, (k_trail_pipe<5><<<grid, pipe::NTHP, pipe::Cfg<5>::SMEM, s>>>(
+            auto *kern = (mode == 2) ? k_trail_pipe<5, true> : k_trail_pipe<5, false>;   // mode 2 transposed
+            TIMED(KC_GEMM_SPLIT, (kern<<<grid, pipe::NTHP, pipe::Cfg<5>::SMEM, s>>>(
                                      mode, Klo, Ihi, P, sub0, nb, cnt, b.tpo, tmapC, tmapR, qr, x.pimg, b.oconst, doomed,
-                                     x.err)));
+                                     x.err, nullptr)));
         };
         auto factor_panel = [&](int J) {
             TIMED(KC_POTRF_MIXED, (k_potrf_mixed<S><<<cnt, 256, POTRF_MIXED_SMEM, s>>>(

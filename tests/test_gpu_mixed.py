@@ -85,7 +85,9 @@ def test_mixed_aniso1000_subset():
     mixed_compare(g, o, "aniso1000", max_disagree=0)
 
 
-@pytest.mark.parametrize("n,p,M", [(3, 2, 1), (129, 5, 9), (300, 2, 3)])
+# M + p = 40 and 64: right-hand-side tiles of 40 and 64 rows (the largest
+# allowed), beside 3, 14 and 5
+@pytest.mark.parametrize("n,p,M", [(3, 2, 1), (129, 5, 9), (300, 2, 3), (260, 3, 37), (300, 4, 60)])
 def test_mixed_ragged(n, p, M):
     ds = synth.aniso_dataset(100 + n, n, math.sqrt(n / 10), p)
     P = synth.omega_from_unit(np.random.default_rng(n).uniform(size=(7, 5)))
